@@ -1,0 +1,539 @@
+/*
+ * FP64 CPU oracle for the TRED hot path (arXiv 2602.12052).
+ *
+ * TEST INFRASTRUCTURE ONLY.  This file is compiled into liboracle.so and loaded by
+ * tests/, by __graft_entry__.smoke() and by bench.py's cpu_baseline / reference leg.
+ * The CUDA product path never links, loads or calls it, and it shares no code with
+ * the CUDA path (no header, helper or table in common).
+ *
+ * Plain, slow, obviously correct.  Each function cites the passage it follows.
+ * Compile with -O2 -ffp-contract=off (no FMA contraction): the window arithmetic
+ * below is a fixed sequence of correctly rounded binary64 operations, and the CUDA
+ * path evaluates the same sequence, so the integer windows (and hence the active
+ * block list and its occupancy) agree bit for bit.
+ *
+ * Parity pins (tests/test_oracle_*.py): Gauss-Legendre polynomial exactness and
+ * textbook nodes; charge conservation of the effective charge (partition of unity
+ * of the linear interpolation); closed-form erf cell integrals (exact-tent mode vs
+ * numerical quadrature, GL-N -> exact-tent as N grows); GL-1 == grid sampling;
+ * sigma -> 0 limit giving the interpolated response at the impact position;
+ * brute-force fine-grid correlation on tiny grids; translation and mirror symmetry;
+ * hand-computed readout waveforms; brute-force block enumeration; finite differences
+ * for the adjoint.
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+/* All geometry and physics constants are binary32 values (as a caller would pass
+ * them); the oracle promotes them exactly to binary64. */
+typedef struct {
+    float pitch_cm;
+    int32_t n_sub;
+    float tick_us;
+    int32_t npx_x, npx_y, nt;
+    int32_t bp, bt;
+    float v_cm_per_us, DL_cm2_per_s, DT_cm2_per_s, lifetime_us;
+    float sigma0_cells_xy, sigma0_ticks, nsigma;
+    int32_t gl_order;
+    int32_t effq_mode;   /* 0 = Gauss-Legendre, 1 = exact tent (closed-form erf) */
+} orc_params;
+
+/* Drifted deposit, all in grid units (sub-cells for x, y; ticks for t). */
+typedef struct {
+    double mu[3];     /* mean position: x, y in sub-cell units, t in ticks */
+    double sig[3];    /* widths in the same units */
+    double q;         /* electrons after attachment */
+    int32_t lo[3];    /* quadrature cells [lo, hi] per axis (unclipped) */
+    int32_t hi[3];
+    int32_t valid;
+} orc_dep;
+
+/* ------------------------------------------------------------------------- */
+/* Gauss-Legendre rule on [-1, 1] (Sec. II-C: the N-point rule {xi_i, w_i}).   */
+/* Newton iteration on the Legendre polynomial P_n, three-term recurrence.     */
+/* Nodes returned in ascending order.                                          */
+/* ------------------------------------------------------------------------- */
+int orc_gl_rule(int n, double *xi, double *w)
+{
+    if (n < 1 || n > 64) return -1;
+    for (int i = 0; i < n; ++i) {
+        double x = cos(M_PI * (i + 0.75) / (n + 0.5));
+        double dp = 1.0;
+        for (int it = 0; it < 100; ++it) {
+            double p0 = 1.0, p1 = x;
+            if (n == 1) { p1 = x; p0 = 1.0; }
+            for (int k = 2; k <= n; ++k) {
+                double p2 = ((2.0 * k - 1.0) * x * p1 - (k - 1.0) * p0) / k;
+                p0 = p1;
+                p1 = p2;
+            }
+            /* p1 = P_n(x), p0 = P_{n-1}(x) */
+            dp = n * (x * p1 - p0) / (x * x - 1.0);
+            double dx = p1 / dp;
+            x -= dx;
+            if (fabs(dx) < 1e-16) break;
+        }
+        /* recompute derivative at the converged node */
+        {
+            double p0 = 1.0, p1 = x;
+            for (int k = 2; k <= n; ++k) {
+                double p2 = ((2.0 * k - 1.0) * x * p1 - (k - 1.0) * p0) / k;
+                p0 = p1;
+                p1 = p2;
+            }
+            dp = n * (x * p1 - p0) / (x * x - 1.0);
+        }
+        xi[n - 1 - i] = x;                   /* cos gives descending nodes */
+        w[n - 1 - i] = 2.0 / ((1.0 - x * x) * dp * dp);
+    }
+    if (n % 2 == 1) xi[n / 2] = 0.0;          /* exact centre node */
+    return 0;
+}
+
+/* ------------------------------------------------------------------------- */
+/* Transport [A;D] (Sec. II-A; Fig. 2 steps A and D): drift time, attachment,  */
+/* diffusion width with a floor added in quadrature, and the raster window.    */
+/* The window is a fixed sequence of correctly rounded binary64 operations.    */
+/* ------------------------------------------------------------------------- */
+void orc_drift(const orc_params *p, int n, const float *x, const float *y,
+               const float *z, const float *t0, const float *ne, orc_dep *out)
+{
+    const double v = (double)p->v_cm_per_us;
+    const double tick = (double)p->tick_us;
+    const double h = (double)p->pitch_cm / (double)p->n_sub;
+    const double width_x = (double)p->npx_x * (double)p->pitch_cm;
+    const double width_y = (double)p->npx_y * (double)p->pitch_cm;
+    const double DT = (double)p->DT_cm2_per_s, DL = (double)p->DL_cm2_per_s;
+    const double s0 = (double)p->sigma0_cells_xy, s0t = (double)p->sigma0_ticks;
+    const double ns = (double)p->nsigma;
+    const double tau = (double)p->lifetime_us;
+    for (int i = 0; i < n; ++i) {
+        orc_dep *d = &out[i];
+        const double xd = x[i], yd = y[i], zd = z[i], t0d = t0[i], ned = ne[i];
+        int ok = isfinite(xd) && isfinite(yd) && isfinite(zd) && isfinite(t0d)
+                 && isfinite(ned) && zd >= 0.0 && ned >= 0.0
+                 && xd >= 0.0 && xd < width_x && yd >= 0.0 && yd < width_y;
+        d->valid = ok;
+        if (!ok) {
+            memset(d, 0, sizeof(*d));
+            for (int a = 0; a < 3; ++a) { d->lo[a] = 0; d->hi[a] = -1; }
+            d->valid = 0;
+            continue;
+        }
+        double td = zd / v;                   /* drift time (us) */
+        double ta = t0d + td;                 /* arrival time at the reference plane */
+        d->mu[2] = ta / tick;                 /* grid points at integer ticks */
+        d->mu[0] = xd / h - 0.5;              /* grid points at sub-cell centres */
+        d->mu[1] = yd / h - 0.5;
+        double a = DT * 2.0;
+        a = a * 1e-6;
+        a = a * td;
+        double b = h * h;
+        a = a / b;
+        double c = s0 * s0;
+        double sxy = sqrt(a + c);
+        a = DL * 2.0;
+        a = a * 1e-6;
+        a = a * td;
+        b = v * tick;
+        b = b * b;
+        a = a / b;
+        c = s0t * s0t;
+        double st = sqrt(a + c);
+        d->sig[0] = sxy;
+        d->sig[1] = sxy;
+        d->sig[2] = st;
+        d->q = ned * exp(-td / tau);          /* finite electron lifetime */
+        for (int ax = 0; ax < 3; ++ax) {
+            double K = ns * d->sig[ax];
+            d->lo[ax] = (int32_t)floor(d->mu[ax] - K);
+            d->hi[ax] = (int32_t)ceil(d->mu[ax] + K);
+        }
+    }
+}
+
+/* Unit normal density in grid units. */
+static double normal_pdf(double xx, double mu, double sig)
+{
+    double u = (xx - mu) / sig;
+    return exp(-0.5 * u * u) / (sig * sqrt(2.0 * M_PI));
+}
+
+/* ------------------------------------------------------------------------- */
+/* One-axis effective-charge weights, Gauss-Legendre form.                     */
+/* Eq. (cub): quadrature inside each cell C; Eq. (trilinear): the response at a */
+/* node is interpolated linearly between the centre of C and the neighbouring   */
+/* centre on the node's side; Eq. (eff_q): regrouping by grid point gives       */
+/*   e[g] = sum_C sum_l (w_l / 2) phi(C + s_l) u_l(g - C),  s_l = xi_l / 2,      */
+/* with u_l(0) = 1 - |s_l| and u_l(sign s_l) = |s_l|.  For a point deposit the    */
+/* 3-D effective charge is Q e_x[gx] e_y[gy] e_t[gt] (Sec. II-C, point-like     */
+/* charge).  Output e has hi - lo + 3 entries, for g = lo - 1 .. hi + 1.         */
+/* ------------------------------------------------------------------------- */
+void orc_weights_gl(int nl, const double *xi, const double *wl, double mu,
+                    double sig, int lo, int hi, double *e)
+{
+    int n = hi - lo + 3;
+    for (int k = 0; k < n; ++k) e[k] = 0.0;
+    for (int C = lo; C <= hi; ++C) {
+        for (int l = 0; l < nl; ++l) {
+            double s = 0.5 * xi[l];
+            double val = 0.5 * wl[l] * normal_pdf((double)C + s, mu, sig);
+            int k = C - (lo - 1);
+            if (s > 0.0) {
+                e[k] += val * (1.0 - s);
+                e[k + 1] += val * s;
+            } else if (s < 0.0) {
+                e[k] += val * (1.0 + s);
+                e[k - 1] += val * (-s);
+            } else {
+                e[k] += val;
+            }
+        }
+    }
+}
+
+/* Normal CDF difference Phi(b) - Phi(a) for b >= a, evaluated with erfc in the
+ * tails so that same-sign tails do not cancel. */
+static double normal_mass(double a, double b, double mu, double sig)
+{
+    double za = (a - mu) / (sig * M_SQRT2), zb = (b - mu) / (sig * M_SQRT2);
+    if (za >= 0.0) return 0.5 * (erfc(za) - erfc(zb));
+    if (zb <= 0.0) return 0.5 * (erfc(-zb) - erfc(-za));
+    return 0.5 * (erf(zb) - erf(za));
+}
+
+/* integral_a^b (x - m) N(x; mu, sig) dx = (mu - m)[Phi]_a^b - sig^2 [N]_a^b */
+static double first_moment(double a, double b, double m, double mu, double sig)
+{
+    if (b <= a) return 0.0;
+    return (mu - m) * normal_mass(a, b, mu, sig)
+           - sig * sig * (normal_pdf(b, mu, sig) - normal_pdf(a, mu, sig));
+}
+
+/* ------------------------------------------------------------------------- */
+/* One-axis effective-charge weights, exact-tent form: the continuum limit of   */
+/* Eq. (eff_q) as the number of nodes grows.  Linear interpolation between grid */
+/* points is the hat function Lambda, so                                        */
+/*   e[g] = integral over [lo - 1/2, hi + 1/2] of N(x; mu, sig) Lambda(x - g) dx  */
+/* in closed form with erf/erfc (cf. the erf cell integrals of Eq. (qline)).    */
+/* ------------------------------------------------------------------------- */
+void orc_weights_tent(double mu, double sig, int lo, int hi, double *e)
+{
+    double A = lo - 0.5, B = hi + 0.5;
+    int n = hi - lo + 3;
+    for (int k = 0; k < n; ++k) {
+        double g = (double)(lo - 1 + k);
+        /* left half [g-1, g]: Lambda = x - (g - 1) */
+        double a = fmax(g - 1.0, A), b = fmin(g, B);
+        double left = first_moment(a, b, g - 1.0, mu, sig);
+        /* right half [g, g+1]: Lambda = (g + 1) - x */
+        a = fmax(g, A);
+        b = fmin(g + 1.0, B);
+        double right = -first_moment(a, b, g + 1.0, mu, sig);
+        e[k] = left + right;
+    }
+}
+
+/* Weights of one deposit on one axis (dispatch on the mode). */
+static void axis_weights(const orc_params *p, const double *xi, const double *wl,
+                         const orc_dep *d, int ax, double *e)
+{
+    if (p->effq_mode == 1)
+        orc_weights_tent(d->mu[ax], d->sig[ax], d->lo[ax], d->hi[ax], e);
+    else
+        orc_weights_gl(p->gl_order, xi, wl, d->mu[ax], d->sig[ax], d->lo[ax],
+                       d->hi[ax], e);
+}
+
+/* Effective-charge support [lo - 1, hi + 1] of a deposit, clipped to the grid. */
+static int support(const orc_params *p, const orc_dep *d, int ax, int *a, int *b)
+{
+    int n = ax == 0 ? p->npx_x * p->n_sub : ax == 1 ? p->npx_y * p->n_sub : p->nt;
+    if (!d->valid) return 0;
+    *a = d->lo[ax] - 1;
+    *b = d->hi[ax] + 1;
+    if (*a < 0) *a = 0;
+    if (*b > n - 1) *b = n - 1;
+    return *a <= *b;
+}
+
+/* ------------------------------------------------------------------------- */
+/* Block-sparse binning (Sec. III-B-1): blocks of bp x bp pixels x bt ticks     */
+/* aligned to the volume's bin boundaries; a block is active iff the clipped    */
+/* support box of some deposit intersects it; its occupancy is the number of    */
+/* such deposits.  Block id = (by * NBx + bx) * NBt + bt.                       */
+/* counts must hold NBx*NBy*NBt entries (zeroed here).  Returns the number of   */
+/* (deposit, block) incidences.                                                 */
+/* ------------------------------------------------------------------------- */
+long orc_block_counts(const orc_params *p, int n, const orc_dep *d, int32_t *counts)
+{
+    const int nbx = p->npx_x / p->bp, nby = p->npx_y / p->bp, nbt = p->nt / p->bt;
+    memset(counts, 0, sizeof(int32_t) * (size_t)nbx * nby * nbt);
+    long pairs = 0;
+    for (int i = 0; i < n; ++i) {
+        int ga[3], gb[3];
+        int ok = 1;
+        for (int ax = 0; ax < 3; ++ax) ok &= support(p, &d[i], ax, &ga[ax], &gb[ax]);
+        if (!ok) continue;
+        int bx0 = (ga[0] / p->n_sub) / p->bp, bx1 = (gb[0] / p->n_sub) / p->bp;
+        int by0 = (ga[1] / p->n_sub) / p->bp, by1 = (gb[1] / p->n_sub) / p->bp;
+        int bt0 = ga[2] / p->bt, bt1 = gb[2] / p->bt;
+        for (int by = by0; by <= by1; ++by)
+            for (int bx = bx0; bx <= bx1; ++bx)
+                for (int bt = bt0; bt <= bt1; ++bt) {
+                    counts[((long)by * nbx + bx) * nbt + bt] += 1;
+                    ++pairs;
+                }
+    }
+    return pairs;
+}
+
+/* Deposit list of one block, ascending deposit index.  Returns the count. */
+int orc_block_deposits(const orc_params *p, int n, const orc_dep *d, int32_t block,
+                       int32_t *idx, int cap)
+{
+    const int nbx = p->npx_x / p->bp, nbt = p->nt / p->bt;
+    int bt = block % nbt, bxy = block / nbt, bx = bxy % nbx, by = bxy / nbx;
+    int m = 0;
+    for (int i = 0; i < n; ++i) {
+        int ga[3], gb[3];
+        int ok = 1;
+        for (int ax = 0; ax < 3; ++ax) ok &= support(p, &d[i], ax, &ga[ax], &gb[ax]);
+        if (!ok) continue;
+        int x0 = bx * p->bp * p->n_sub, x1 = x0 + p->bp * p->n_sub - 1;
+        int y0 = by * p->bp * p->n_sub, y1 = y0 + p->bp * p->n_sub - 1;
+        int t0 = bt * p->bt, t1 = t0 + p->bt - 1;
+        if (gb[0] < x0 || ga[0] > x1 || gb[1] < y0 || ga[1] > y1 || gb[2] < t0
+            || ga[2] > t1)
+            continue;
+        if (m < cap) idx[m] = i;
+        ++m;
+    }
+    return m;
+}
+
+/* ------------------------------------------------------------------------- */
+/* Effective charge of the listed blocks (Eq. (eff_q), separable point form),   */
+/* layout [block][jy][jx][py][px][t] with gx = (bx*bp + px)*n_sub + jx etc.     */
+/* ------------------------------------------------------------------------- */
+void orc_qeff_blocks(const orc_params *p, int n, const orc_dep *d, int nb,
+                     const int32_t *blocks, double *qeff)
+{
+    const int ns = p->n_sub, bp = p->bp, btk = p->bt;
+    const int nbx = p->npx_x / p->bp, nbt = p->nt / p->bt;
+    const size_t per_block = (size_t)ns * ns * bp * bp * btk;
+    double xi[64], wl[64];
+    orc_gl_rule(p->gl_order, xi, wl);
+    memset(qeff, 0, sizeof(double) * per_block * nb);
+#pragma omp parallel for schedule(dynamic)
+    for (int b = 0; b < nb; ++b) {
+        int blk = blocks[b];
+        int bt = blk % nbt, bxy = blk / nbt, bx = bxy % nbx, by = bxy / nbx;
+        int x0 = bx * bp * ns, y0 = by * bp * ns, t0 = bt * btk;
+        double *Q = qeff + per_block * b;
+        for (int i = 0; i < n; ++i) {
+            int ga[3], gb[3];
+            int ok = 1;
+            for (int ax = 0; ax < 3; ++ax) ok &= support(p, &d[i], ax, &ga[ax], &gb[ax]);
+            if (!ok) continue;
+            if (gb[0] < x0 || ga[0] > x0 + bp * ns - 1 || gb[1] < y0
+                || ga[1] > y0 + bp * ns - 1 || gb[2] < t0 || ga[2] > t0 + btk - 1)
+                continue;
+            double *e[3];
+            for (int ax = 0; ax < 3; ++ax) {
+                e[ax] = (double *)malloc(sizeof(double) * (d[i].hi[ax] - d[i].lo[ax] + 3));
+                axis_weights(p, xi, wl, &d[i], ax, e[ax]);
+            }
+            for (int gy = ga[1] > y0 ? ga[1] : y0; gy <= gb[1] && gy < y0 + bp * ns; ++gy)
+                for (int gx = ga[0] > x0 ? ga[0] : x0; gx <= gb[0] && gx < x0 + bp * ns; ++gx) {
+                    int jy = gy % ns, py = gy / ns - by * bp;
+                    int jx = gx % ns, px = gx / ns - bx * bp;
+                    double exy = d[i].q * e[1][gy - (d[i].lo[1] - 1)] * e[0][gx - (d[i].lo[0] - 1)];
+                    double *col = Q + ((((size_t)jy * ns + jx) * bp + py) * bp + px) * btk;
+                    for (int gt = ga[2] > t0 ? ga[2] : t0; gt <= gb[2] && gt < t0 + btk; ++gt)
+                        col[gt - t0] += exy * e[2][gt - (d[i].lo[2] - 1)];
+                }
+            for (int ax = 0; ax < 3; ++ax) free(e[ax]);
+        }
+    }
+}
+
+/* ------------------------------------------------------------------------- */
+/* Induced current on listed pixels (Sec. II-D, Eq. (interlaced) before the     */
+/* R = i[j, -k] relabelling):                                                   */
+/*   I[P, t] = sum_j sum_K sum_tau Qeff[j, P + K, t - tau] i[j, K, tau]          */
+/* a correlation over the pixel plane and a convolution along time.  The        */
+/* effective charge is built locally on the sub-cells of pixels P + K,          */
+/* K in [-R, R]^2, from every deposit whose support reaches them; output ticks  */
+/* are [0, nt).  resp layout [Ky][Kx][jy][jx][tau], K index = K + R.            */
+/* wave: [npix][nt].                                                            */
+/* ------------------------------------------------------------------------- */
+void orc_pixel_currents(const orc_params *p, int n, const orc_dep *d,
+                        const float *resp, int kp, int nr, int npix,
+                        const int32_t *pixel_ids, double *wave)
+{
+    const int ns = p->n_sub, R = (kp - 1) / 2;
+    const int ngx = p->npx_x * ns, ngy = p->npx_y * ns, nt = p->nt;
+    double xi[64], wl[64];
+    orc_gl_rule(p->gl_order, xi, wl);
+#pragma omp parallel for schedule(dynamic)
+    for (int ip = 0; ip < npix; ++ip) {
+        double *I = wave + (size_t)ip * nt;
+        memset(I, 0, sizeof(double) * nt);
+        int P = pixel_ids[ip];
+        int Px = P % p->npx_x, Py = P / p->npx_x;
+        /* source sub-cell region of pixels Px-R .. Px+R (clipped) */
+        int gx0 = (Px - R) * ns, gx1 = (Px + R + 1) * ns - 1;
+        int gy0 = (Py - R) * ns, gy1 = (Py + R + 1) * ns - 1;
+        if (gx0 < 0) gx0 = 0;
+        if (gy0 < 0) gy0 = 0;
+        if (gx1 > ngx - 1) gx1 = ngx - 1;
+        if (gy1 > ngy - 1) gy1 = ngy - 1;
+        int W = gx1 - gx0 + 1, H = gy1 - gy0 + 1;
+        /* time range of the deposits that reach the region */
+        int tmin = nt, tmax = -1;
+        for (int i = 0; i < n; ++i) {
+            int ga[3], gb[3];
+            int ok = 1;
+            for (int ax = 0; ax < 3; ++ax) ok &= support(p, &d[i], ax, &ga[ax], &gb[ax]);
+            if (!ok || gb[0] < gx0 || ga[0] > gx1 || gb[1] < gy0 || ga[1] > gy1) continue;
+            if (ga[2] < tmin) tmin = ga[2];
+            if (gb[2] > tmax) tmax = gb[2];
+        }
+        if (tmax < tmin) continue;
+        int T = tmax - tmin + 1;
+        double *Q = (double *)calloc((size_t)W * H * T, sizeof(double));
+        int *cmin = (int *)malloc(sizeof(int) * W * H);
+        int *cmax = (int *)malloc(sizeof(int) * W * H);
+        for (int k = 0; k < W * H; ++k) { cmin[k] = T; cmax[k] = -1; }
+        for (int i = 0; i < n; ++i) {
+            int ga[3], gb[3];
+            int ok = 1;
+            for (int ax = 0; ax < 3; ++ax) ok &= support(p, &d[i], ax, &ga[ax], &gb[ax]);
+            if (!ok || gb[0] < gx0 || ga[0] > gx1 || gb[1] < gy0 || ga[1] > gy1) continue;
+            double *e[3];
+            for (int ax = 0; ax < 3; ++ax) {
+                e[ax] = (double *)malloc(sizeof(double) * (d[i].hi[ax] - d[i].lo[ax] + 3));
+                axis_weights(p, xi, wl, &d[i], ax, e[ax]);
+            }
+            for (int gy = ga[1] > gy0 ? ga[1] : gy0; gy <= gb[1] && gy <= gy1; ++gy)
+                for (int gx = ga[0] > gx0 ? ga[0] : gx0; gx <= gb[0] && gx <= gx1; ++gx) {
+                    int c = (gy - gy0) * W + (gx - gx0);
+                    double exy = d[i].q * e[1][gy - (d[i].lo[1] - 1)] * e[0][gx - (d[i].lo[0] - 1)];
+                    double *col = Q + (size_t)c * T;
+                    for (int gt = ga[2]; gt <= gb[2]; ++gt)
+                        col[gt - tmin] += exy * e[2][gt - (d[i].lo[2] - 1)];
+                    if (ga[2] - tmin < cmin[c]) cmin[c] = ga[2] - tmin;
+                    if (gb[2] - tmin > cmax[c]) cmax[c] = gb[2] - tmin;
+                }
+            for (int ax = 0; ax < 3; ++ax) free(e[ax]);
+        }
+        for (int gy = gy0; gy <= gy1; ++gy)
+            for (int gx = gx0; gx <= gx1; ++gx) {
+                int c = (gy - gy0) * W + (gx - gx0);
+                if (cmax[c] < cmin[c]) continue;
+                int Ky = gy / ns - Py, Kx = gx / ns - Px;
+                int jy = gy % ns, jx = gx % ns;
+                const float *ir = resp + ((((size_t)(Ky + R) * kp + (Kx + R)) * ns + jy) * ns + jx) * nr;
+                const double *col = Q + (size_t)c * T;
+                for (int tl = cmin[c]; tl <= cmax[c]; ++tl) {
+                    double q = col[tl];
+                    if (q == 0.0) continue;
+                    int ts = tl + tmin;
+                    for (int tau = 0; tau < nr && ts + tau < nt; ++tau)
+                        I[ts + tau] += q * (double)ir[tau];
+                }
+            }
+        free(Q);
+        free(cmin);
+        free(cmax);
+    }
+}
+
+/* ------------------------------------------------------------------------- */
+/* Active pixels: every in-plane pixel in the output footprint of an active     */
+/* block, i.e. pixels [bx*bp - R, bx*bp + bp + R) x (same in y), since the      */
+/* convolution enlarges a block by the response half-width (Sec. III-B-1).      */
+/* flags: [npx_y * npx_x] (written).  Returns the count.                        */
+/* ------------------------------------------------------------------------- */
+int orc_active_pixels(const orc_params *p, int nb, const int32_t *blocks, int kp,
+                      uint8_t *flags)
+{
+    const int R = (kp - 1) / 2, nbx = p->npx_x / p->bp, nbt = p->nt / p->bt;
+    memset(flags, 0, (size_t)p->npx_x * p->npx_y);
+    for (int b = 0; b < nb; ++b) {
+        int bxy = blocks[b] / nbt, bx = bxy % nbx, by = bxy / nbx;
+        for (int y = by * p->bp - R; y < by * p->bp + p->bp + R; ++y)
+            for (int x = bx * p->bp - R; x < bx * p->bp + p->bp + R; ++x)
+                if (x >= 0 && x < p->npx_x && y >= 0 && y < p->npx_y)
+                    flags[(size_t)y * p->npx_x + x] = 1;
+    }
+    int m = 0;
+    for (size_t k = 0; k < (size_t)p->npx_x * p->npx_y; ++k) m += flags[k];
+    return m;
+}
+
+/* ------------------------------------------------------------------------- */
+/* Trigger-reset readout (Sec. II-E, Fig. 6).  Per pixel, the charge C is the   */
+/* running sum of the current since the end of the last reset.  At each clock   */
+/* edge k (k a multiple of clock) with k >= start: if C(k) >= threshold the     */
+/* channel triggers; the charge is sampled at k + hold and a hit               */
+/* (pixel, k + hold, C(k + hold)) is emitted if k + hold < nt; then C restarts  */
+/* at k + hold + reset + 1.  Also reports, per pixel, the first edge whose C    */
+/* lies within tol of the threshold (-1 if none): hit lists may legitimately    */
+/* differ from that edge on.                                                    */
+/* Returns the number of hits (written up to cap).                              */
+/* ------------------------------------------------------------------------- */
+long orc_readout(int npix, int nt, const int32_t *pixel_ids, const double *wave,
+                 double thr, int clock, int hold, int reset, double tol,
+                 int32_t *hit_pixel, int32_t *hit_tick, double *hit_charge, long cap,
+                 int32_t *first_ambiguous)
+{
+    long m = 0;
+    for (int ip = 0; ip < npix; ++ip) {
+        const double *I = wave + (size_t)ip * nt;
+        first_ambiguous[ip] = -1;
+        int start = 0;
+        double C = 0.0;
+        int t = 0;           /* next tick to add into C */
+        while (1) {
+            int k = ((start + clock - 1) / clock) * clock;   /* first edge >= start */
+            int fired = 0;
+            for (; k < nt; k += clock) {
+                while (t <= k) C += I[t++];
+                if (first_ambiguous[ip] < 0 && fabs(C - thr) <= tol) first_ambiguous[ip] = k;
+                if (C >= thr) { fired = 1; break; }
+            }
+            if (!fired) break;
+            int ts = k + hold;
+            if (ts >= nt) break;
+            while (t <= ts) C += I[t++];
+            if (m < cap) {
+                hit_pixel[m] = pixel_ids[ip];
+                hit_tick[m] = ts;
+                hit_charge[m] = C;
+            }
+            ++m;
+            start = ts + reset + 1;
+            C = 0.0;
+            t = start;
+            if (start >= nt) break;
+        }
+    }
+    return m;
+}
+
+int orc_num_threads(void)
+{
+#ifdef _OPENMP
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
+}
