@@ -1,0 +1,329 @@
+#!/usr/bin/env python
+"""Benchmark of the TRED hot path on B300: deposits/s to pixel currents.
+
+One step = drift -> blockbin -> effq -> convolve -> gather -> readout (all hot-path
+stages) over one synthetic event already resident in HBM: the module-plane
+workload (512 x 512 pixels x 6,400 ticks, tracks drawn until >= 1e6 deposits,
+9 x 9 pixel x 100 impact x 200 tick response, 8 x 8 pixel x 256 tick blocks, FFT
+16 x 16 x 512, GL-2).  The response spectrum (computed once per response) is timed
+separately.  Under torchrun each rank simulates its own independent event (weak
+scaling; no collective on the data path, a barrier and a max-reduce for timing).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl tred|reference]
+
+Prints one JSON line (rank 0).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "depos/s to pixel currents at <=1e-5 rel L2 vs FP64 oracle; % of HBM/TC roofline"
+WORKLOAD = "module1M"
+# Algorithmic FLOPs of one block's convolution: 50 packed forward 3-D FFTs of
+# N = 16*16*512 points at 5 N log2 N, 50 spectrum products at 8 N, one inverse FFT.
+_N = 16 * 16 * 512
+CONV_FLOP_PER_BLOCK = 50 * 5 * _N * 17 + 50 * 8 * _N + 5 * _N * 17
+# FP32 ALU peak from unit counts and the maximum clock: 148 SMs x 128 FP32 lanes x
+# 2 flop (FMA) x 2.032 GHz.
+SMS, FP32_LANES, SM_MAX_GHZ = 148, 128, 2.032
+FP32_PEAK_TFLOPS = SMS * FP32_LANES * 2 * SM_MAX_GHZ / 1e3
+
+
+def _args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="tred", choices=["tred", "reference"])
+    ap.add_argument("--config", default=WORKLOAD)
+    ap.add_argument("--cpu-sample", type=int, default=12000,
+                    help="deposits of the workload timed through the CPU oracle")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    return ap.parse_args()
+
+
+def _dist():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        self.p = None
+
+    def __enter__(self):
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.Q}",
+                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                      stdout=self.f, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.p = None
+        return self
+
+    def __exit__(self, *a):
+        if self.p is not None:
+            self.p.terminate()
+            try:
+                self.p.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.p.kill()
+
+    def summary(self):
+        self.f.flush()
+        self.f.seek(0)
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.f.read().splitlines():
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx = float(parts[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        os.unlink(self.f.name)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def cpu_baseline(cfg, dep, resp, sample: int):
+    """The FP64 oracle as it stands, on the first `sample` deposits of the workload."""
+    import oracle
+    sub = {k: v[:sample] for k, v in dep.items()}
+    t = time.perf_counter()
+    r = oracle.simulate(cfg, sub, resp)
+    dt = time.perf_counter() - t
+    return {"value": sample / dt, "unit": "depos/s", "cores": oracle.num_threads(), "kind": "oracle",
+            "sample": (f"first {sample} deposits of the {cfg.name} event, full path to pixel currents "
+                       f"({len(r['block_ids'])} blocks, {len(r['pixel_ids'])} pixels), {dt:.1f} s")}
+
+
+def run_reference(args):
+    rank, world, _ = _dist()
+    if rank != 0:
+        return
+    import synth
+    cfg = synth.get_config(args.config)
+    dep, resp = synth.make_event(cfg)
+    sample = max(1000, args.cpu_sample // 3)
+    times = []
+    for k in range(args.warmup + args.steps):
+        off = (k * sample) % max(1, len(dep["x"]) - sample)
+        sub = {kk: v[off:off + sample] for kk, v in dep.items()}
+        import oracle
+        t = time.perf_counter()
+        oracle.simulate(cfg, sub, resp)
+        if k >= args.warmup:
+            times.append(time.perf_counter() - t)
+    import oracle
+    ms = 1e3 * statistics.mean(times)
+    value = sample / (ms / 1e3)
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "depos/s", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": f"{cfg.name}: 512x512 px x 6400 ticks, {len(dep['x'])} deposits",
+                   "sample_per_step": sample},
+        "cpu_baseline": {"value": value, "unit": "depos/s", "cores": oracle.num_threads(),
+                         "kind": "oracle",
+                         "sample": f"{sample} consecutive deposits of the {cfg.name} event per step"},
+        "e2e": {"value": value, "unit": "depos/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = _args()
+    if args.impl == "reference":
+        run_reference(args)
+        return
+    import numpy as np
+    import torch
+
+    import synth
+    from paper_2602_12052_b300 import build as lib_build
+    from paper_2602_12052_b300 import tred
+
+    rank, world, local = _dist()
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    lib_build.build()
+    cfg = synth.get_config(args.config)
+    dep = synth.make_deposits(cfg, seed=cfg.seed + 7919 * rank)
+    resp = synth.make_response(cfg)
+    n = len(dep["x"])
+    dev = torch.device("cuda", local)
+    max_blocks = 10000 if cfg.npx >= 512 else cfg.n_blocks
+    max_pixels = 320000 if cfg.npx >= 512 else cfg.npx * cfg.npx
+    max_hits = 4 * max_pixels
+    sim = tred.Simulator(cfg, torch.from_numpy(resp), max_deposits=n, max_blocks=max_blocks,
+                         max_pixels=max_pixels, max_hits=max_hits, device=dev)
+    # response spectrum, timed separately (once per response)
+    torch.cuda.synchronize()
+    t = time.perf_counter()
+    tred.tred_set_response(sim.h, sim.resp)
+    torch.cuda.synchronize()
+    set_response_ms = 1e3 * (time.perf_counter() - t)
+
+    x = {k: torch.from_numpy(v).to(dev) for k, v in dep.items()}
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)   # > L2 (126 MB)
+
+    stage_names = ["drift", "blockbin", "effq", "convolve", "gather", "readout"]
+
+    def step(events=None):
+        h = sim.h
+        ev = events or [None] * 7
+
+        def rec(i):
+            if ev[i] is not None:
+                ev[i].record(stream)
+        rec(0)
+        tred.tred_drift(h, n, x["x"], x["y"], x["z"], x["t0"], x["ne"], sim.deps)
+        rec(1)
+        tred.tred_blockbin(h, n, sim.deps, sim.block_ids, sim.block_counts, sim.dep_offsets,
+                           sim.dep_index, sim.n_blocks_dev)
+        rec(2)
+        tred.tred_effq(h, n, sim.deps, sim.block_ids, sim.dep_offsets, sim.dep_index,
+                       sim.n_blocks_dev, sim.qeff)
+        rec(3)
+        tred.tred_convolve(h, sim.block_ids, sim.n_blocks_dev, sim.qeff, sim.out_blocks)
+        rec(4)
+        tred.tred_gather_pixels(h, sim.block_ids, sim.n_blocks_dev, sim.out_blocks, sim.pixel_ids,
+                                sim.waveforms, sim.n_pixels_dev)
+        rec(5)
+        tred.tred_readout(h, sim.rp, sim.pixel_ids, sim.waveforms, sim.n_pixels_dev, sim.hit_pixel,
+                          sim.hit_tick, sim.hit_charge, sim.n_hits_dev)
+        rec(6)
+
+    tred.tred_reset_status(sim.h)
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    status = tred.tred_sync_status(sim.h)
+    if status[0] != 0:
+        raise RuntimeError(f"device status after warm-up: {status}")
+    nb, npix, nh = (int(v) for v in sim.counts[:3].cpu())
+
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(7)] for _ in range(args.steps)]
+    launches0 = tred.tred_launch_count(sim.h)
+    with ClockSampler(local) as clk:
+        time.sleep(0.3)
+        for k in range(args.steps):
+            flush.zero_()                       # L2 flushed between timed steps (outside events)
+            step(evs[k])
+        torch.cuda.synchronize()
+    launches = tred.tred_launch_count(sim.h) - launches0
+    clocks = clk.summary()
+    if world > 1:
+        torch.distributed.barrier()
+    step_ms = [evs[k][0].elapsed_time(evs[k][6]) for k in range(args.steps)]
+    stage_ms = {nm: statistics.mean(evs[k][i].elapsed_time(evs[k][i + 1]) for k in range(args.steps))
+                for i, nm in enumerate(stage_names)}
+    ms = statistics.mean(step_ms)
+    if world > 1:
+        t_ = torch.tensor([ms], device=dev)
+        torch.distributed.all_reduce(t_, op=torch.distributed.ReduceOp.MAX)
+        ms = float(t_.item())
+    value = n * world / (ms / 1e3)
+
+    # end to end through the public API: pinned host inputs -> device, step,
+    # counts + hit list -> pinned host, every step inside the timed region
+    e2e = None
+    if not args.no_e2e:
+        host = {k: torch.from_numpy(v).pin_memory() for k, v in dep.items()}
+        h_counts = torch.empty(4, dtype=torch.int32).pin_memory()
+        h_hp = torch.empty(max_hits, dtype=torch.int32).pin_memory()
+        h_ht = torch.empty(max_hits, dtype=torch.int32).pin_memory()
+        h_hc = torch.empty(max_hits, dtype=torch.float32).pin_memory()
+        h2d = sum(v.numel() * v.element_size() for v in host.values())
+        d2h = h_counts.numel() * 4 + 12 * max_hits
+        e_ms = []
+        for k in range(args.warmup + args.steps):
+            flush.zero_()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            for kk in x:
+                x[kk].copy_(host[kk], non_blocking=True)
+            step()
+            h_counts.copy_(sim.counts, non_blocking=True)
+            h_hp.copy_(sim.hit_pixel, non_blocking=True)
+            h_ht.copy_(sim.hit_tick, non_blocking=True)
+            h_hc.copy_(sim.hit_charge, non_blocking=True)
+            b.record(stream)
+            b.synchronize()
+            if k >= args.warmup:
+                e_ms.append(a.elapsed_time(b))
+        em = statistics.mean(e_ms)
+        if world > 1:
+            t_ = torch.tensor([em], device=dev)
+            torch.distributed.all_reduce(t_, op=torch.distributed.ReduceOp.MAX)
+            em = float(t_.item())
+        e2e = {"value": n * world / (em / 1e3), "unit": "depos/s", "h2d_bytes_per_step": h2d,
+               "d2h_bytes_per_step": d2h, "ms_per_step": em}
+
+    conv_ms = stage_ms["convolve"]
+    achieved = CONV_FLOP_PER_BLOCK * nb / (conv_ms / 1e3) / 1e12
+    roofline = {"bound": "alu", "kernel": "tred_convolve (k_conv_spec + k_conv_itime)",
+                "achieved": achieved, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
+                "frac": achieved / FP32_PEAK_TFLOPS, "traffic": None,
+                "peak_source": "148 SMs x 128 FP32 lanes x 2 flop x 2.032 GHz (unit counts, max clock)",
+                "flop_per_block": CONV_FLOP_PER_BLOCK, "blocks": nb}
+    if clocks.get("sm_mhz"):
+        roofline["frac_at_observed_clock"] = achieved / (FP32_PEAK_TFLOPS * clocks["sm_mhz"] / 2032.0)
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": "depos/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": (f"{cfg.name}: one event of {n} point deposits on a "
+                                    f"{cfg.npx}x{cfg.npx} pixel plane x {cfg.nt} ticks, GL-{cfg.gl_order}, "
+                                    f"{cfg.kp}x{cfg.kp}x{cfg.n_sub}x{cfg.n_sub}x{cfg.nr} response, "
+                                    f"{cfg.bp}x{cfg.bp}x{cfg.bt} blocks, FFT 16x16x{cfg.lt}, MPCP"),
+                       "deposits": n, "active_blocks": nb, "active_pixels": npix, "hits": nh,
+                       "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
+                       "l2": "flushed between timed steps (256 MB write, outside the step events)"},
+            "stages_ms": stage_ms, "set_response_ms": set_response_ms,
+            "gpu_launches": launches, "clocks": clocks, "roofline": roofline, "e2e": e2e,
+        }
+        if world == 1 and not args.no_cpu_baseline:
+            line["cpu_baseline"] = cpu_baseline(cfg, dep, resp, args.cpu_sample)
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,212 @@
+/*
+ * libtred -- C ABI of the B300 (sm_103a) hot path of TRED (arXiv 2602.12052):
+ * effective charge of drifted, diffused ionisation deposits on a sub-pixel x tick
+ * grid, block-sparse binning, interlaced FFT convolution with the field response,
+ * electrode gather and trigger-reset readout.
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ *  - Every call returns int32_t: TRED_OK (0) or a TRED_ERR_* code; nothing throws.
+ *    tred_last_error(h) returns a message for the last failing call on h.
+ *  - Pointers named *_dev, and every array argument unless stated otherwise, are
+ *    DEVICE pointers owned by the caller, 256-byte aligned (any cudaMalloc /
+ *    torch allocation qualifies).  The handle owns only the response spectrum and
+ *    internal scratch, allocated once in tred_create from the capacities.
+ *  - `stream` is a cudaStream_t (NULL = legacy default stream).  Work is enqueued
+ *    asynchronously; no call synchronises the host except tred_sync_status.
+ *  - Counts produced on the device (active blocks, pixels, hits) stay on the device
+ *    (*_dev arguments) so that a whole step can be captured in a CUDA graph.
+ *    Downstream calls read them there.  Overflow of a capacity sets a bit of the
+ *    device status word (TRED_ST_*) and truncates; read it with tred_sync_status.
+ *  - Grid units: x, y in sub-cells of size h = pitch / n_sub with grid points at
+ *    sub-cell centres (mu_x = x / h - 1/2); t in ticks with grid points at integer
+ *    ticks.  Pixel id = py * npx_x + px.  Block id = (by * NBx + bx) * NBt + bt
+ *    with NBx = npx_x / bp, NBt = nt / bt.
+ */
+#ifndef TRED_H
+#define TRED_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum {
+    TRED_OK = 0,
+    TRED_ERR_INVALID_ARG = 1,  /* bad pointer, size, geometry or parameter */
+    TRED_ERR_CUDA = 2,         /* a CUDA runtime call failed (message has the name) */
+    TRED_ERR_CAPACITY = 3,     /* a capacity given to tred_create is too small */
+    TRED_ERR_TIMEOUT = 4,      /* a bounded device wait gave up */
+    TRED_ERR_NOT_READY = 5     /* call made before tred_set_response */
+};
+
+/* Bits of the device status word (host_status[0] of tred_sync_status). */
+enum {
+    TRED_ST_BLOCK_OVERFLOW = 1 << 0,   /* more active blocks than max_blocks */
+    TRED_ST_PAIR_OVERFLOW = 1 << 1,    /* more (deposit, block) pairs than max_pairs */
+    TRED_ST_PIXEL_OVERFLOW = 1 << 2,   /* more active pixels than max_pixels */
+    TRED_ST_HIT_OVERFLOW = 1 << 3,     /* more hits than max_hits */
+    TRED_ST_DRIFT_RANGE = 1 << 4,      /* a deposit drifted farther than max_drift_cm */
+    TRED_ST_TIMEOUT = 1 << 5           /* a bounded device wait expired */
+};
+
+#define TRED_STATUS_WORDS 8
+/* host_status layout: [0] status bits, [1] deposits dropped at drift (off the plane,
+ * negative z or n_e, non-finite), [2] active blocks, [3] (deposit, block) pairs,
+ * [4] active pixels, [5] hits, [6] reserved, [7] reserved. */
+
+typedef struct tred_handle tred_handle;
+
+/* Detector geometry and block decomposition (Sec. II-B, II-D, III-B).  All floating
+ * constants are binary32; the window arithmetic promotes them exactly. */
+typedef struct {
+    float pitch_cm;      /* pixel pitch a */
+    int32_t n_sub;       /* impact positions per pixel axis (even; grid G is n_sub x finer) */
+    float tick_us;       /* sampling tick */
+    int32_t npx_x, npx_y;/* plane size in pixels (multiples of bp) */
+    int32_t nt;          /* readout window in ticks (multiple of bt) */
+    int32_t bp, bt;      /* block shape: bp x bp pixels x bt ticks */
+    int32_t kp, nr;      /* field response: kp x kp pixels (odd), nr ticks */
+    int32_t lt;          /* FFT length along time: 512 or 1024, >= bt + nr - 1 */
+} tred_geometry;
+
+/* Transport and method switches. */
+typedef struct {
+    float v_cm_per_us;       /* drift velocity */
+    float DL_cm2_per_s;      /* longitudinal diffusion coefficient */
+    float DT_cm2_per_s;      /* transverse diffusion coefficient */
+    float lifetime_us;       /* electron lifetime (attachment) */
+    float sigma0_cells_xy;   /* diffusion floor (sub-cells), added in quadrature */
+    float sigma0_ticks;      /* diffusion floor (ticks), added in quadrature */
+    float nsigma;            /* raster half-width in units of sigma */
+    float max_drift_cm;      /* largest drift distance the window capacity covers */
+    int32_t gl_order;        /* Gauss-Legendre points per axis, 1..8 */
+    int32_t effq_mode;       /* 0: Gauss-Legendre (FP32); 1: exact tent, FP64 erf tails */
+    int32_t conv_mode;       /* 0: FP32 shared-memory FFT */
+    int32_t mpcp;            /* 1: mirror-pair complex packing (needs a mirror-
+                                symmetric response); 0: one channel per FFT */
+    int32_t compensated_gather; /* 1: accumulate overlapping blocks in FP64 */
+} tred_params;
+
+/* Trigger-reset readout (Sec. II-E). */
+typedef struct {
+    float threshold_e;       /* trigger threshold on the integrated charge */
+    int32_t clock_ticks;     /* clock period: triggers are tested at multiples of it */
+    int32_t hold_ticks;      /* charge is sampled hold_ticks after the trigger edge */
+    int32_t reset_ticks;     /* dead time after the sample */
+} tred_readout_params;
+
+/* Drifted deposits, structure of arrays, caller-owned device arrays of length
+ * >= n each.  Written by tred_drift, read by tred_blockbin and tred_effq.
+ * cell = floor(mu), frac = mu - cell in [0,1) (computed in binary64, rounded),
+ * sigma in grid units, [lo, hi] the quadrature cells (effective charge support is
+ * [lo - 1, hi + 1]), q the electrons after attachment.  A dropped deposit has
+ * q = 0 and lo > hi on every axis. */
+typedef struct {
+    int32_t *cell_x, *cell_y, *cell_t;
+    float *frac_x, *frac_y, *frac_t;
+    float *sigma_x, *sigma_y, *sigma_t;
+    int32_t *lo_x, *lo_y, *lo_t;
+    int32_t *hi_x, *hi_y, *hi_t;
+    float *q;
+} tred_deposits;
+
+/* Create a handle on the current CUDA device.  Capacities: max_deposits per call,
+ * max_blocks active blocks, max_pixels active pixels.  Allocates the response
+ * spectrum and scratch (cudaMalloc).  On error *out is NULL. */
+int32_t tred_create(const tred_geometry *geom, const tred_params *params,
+                    int32_t max_deposits, int32_t max_blocks, int32_t max_pixels,
+                    tred_handle **out);
+
+/* Free the handle and its device memory (after the caller's streams are idle). */
+int32_t tred_destroy(tred_handle *h);
+
+/* Message of the last failing call on h (static storage owned by h). */
+const char *tred_last_error(const tred_handle *h);
+
+/* Device status word and counters (TRED_STATUS_WORDS int32 into host_status);
+ * synchronises `stream`.  Does not clear them; tred_reset_status does. */
+int32_t tred_sync_status(tred_handle *h, void *stream, int32_t *host_status);
+int32_t tred_reset_status(tred_handle *h, void *stream);
+
+/* Number of kernels this handle has launched so far (host-side counter, no device
+ * access; diagnostics for benchmarks). */
+int32_t tred_launch_count(const tred_handle *h, int64_t *count);
+
+/* a0. Response spectrum (Sec. III-A-2: "with precomputed FFT(R^j)"; Eq. interlaced,
+ * R[j, k] = i[j, -k]).  resp_dev: [kp][kp][n_sub][n_sub][nr] float32, index
+ * [Ky + R][Kx + R][jy][jx][tau] = current on the central electrode from unit charge
+ * at impact (jx, jy) of the pixel at offset K, tau ticks after crossing the
+ * reference plane.  Computed once in FP64 (direct DFT) and stored in complex64,
+ * pre-scaled by 1/(16*16*lt).  With mpcp=1 the response must be mirror symmetric,
+ * i[-j][-K] = i[j][K] (Eq. multch); only one impact of each mirror pair is kept. */
+int32_t tred_set_response(tred_handle *h, const float *resp_dev, void *stream);
+
+/* a1. Transport (Sec. II-A; Fig. 2 steps A, D).  Inputs x, y (cm, on the plane from
+ * its lower corner), z (drift distance to the response reference plane, cm), t0
+ * (us), ne (electrons), device float32[n].  Per deposit: t_d = z / v, arrival tick
+ * mu_t = (t0 + t_d) / tick, mu_x = x / h - 1/2, sigma_xy = sqrt(2 DT t_d / h^2 +
+ * s0^2), sigma_t = sqrt(2 DL t_d / (v tick)^2 + s0t^2), q = ne exp(-t_d / tau),
+ * window lo = floor(mu - nsigma sigma), hi = ceil(mu + nsigma sigma).  The window is
+ * one fixed sequence of correctly rounded binary64 operations (no contraction), so
+ * any IEEE binary64 implementation of it gives the same integers. */
+int32_t tred_drift(tred_handle *h, int32_t n, const float *x, const float *y,
+                   const float *z, const float *t0, const float *ne,
+                   const tred_deposits *out, void *stream);
+
+/* a2. Block-sparse binning (Sec. III-B-1).  A block is active iff the clipped
+ * support box of some deposit intersects it; its count is the number of such
+ * deposits.  Output (device): block_ids[nb] ascending, block_counts[nb],
+ * dep_offsets[nb + 1] (CSR), dep_index[pairs] (deposit ids of each block, in no
+ * particular order within a block), n_blocks_dev[0] = nb.  Capacities: max_blocks
+ * (tred_create) and max_pairs. */
+int32_t tred_blockbin(tred_handle *h, int32_t n, const tred_deposits *deps,
+                      int32_t *block_ids, int32_t *block_counts, int32_t *dep_offsets,
+                      int32_t *dep_index, int32_t max_pairs, int32_t *n_blocks_dev,
+                      void *stream);
+
+/* a3. Effective charge (Sec. II-C, Eqs. cub, trilinear, eff_q; point-like charge):
+ * per axis e[g] = sum_C sum_l (w_l / 2) phi(C + xi_l / 2) u_l(g - C) (Gauss-Legendre)
+ * or the exact tent integral (effq_mode 1); Qeff = q e_x e_y e_t summed over the
+ * block's deposits.  qeff_dev: [max_blocks][n_sub][n_sub][bp][bp][bt] float32,
+ * index [slot][jy][jx][py][px][t], grid point gx = (bx bp + px) n_sub + jx. */
+int32_t tred_effq(tred_handle *h, int32_t n, const tred_deposits *deps,
+                  const int32_t *block_ids, const int32_t *dep_offsets,
+                  const int32_t *dep_index, const int32_t *n_blocks_dev, float *qeff,
+                  void *stream);
+
+/* a4. Interlaced convolution (Sec. II-D, Eq. interlaced; Sec. III-A-2, Eq. multch):
+ *   I[P, t] = sum_j sum_K sum_tau Qeff[j, P + K, t - tau] i[j, K, tau]
+ * for each active block, by FFT over the padded 16 x 16 x lt grid, with MPCP when
+ * params.mpcp = 1.  out_blocks: [max_blocks][16][16][lt] float32, index
+ * [slot][uy][ux][t]: block-local output pixel (by bp + uy - R, bx bp + ux - R) at
+ * tick bt*bt_len + t, R = (kp - 1) / 2; only t < bt + nr - 1 is meaningful. */
+int32_t tred_convolve(tred_handle *h, const int32_t *block_ids,
+                      const int32_t *n_blocks_dev, const float *qeff, float *out_blocks,
+                      void *stream);
+
+/* a5. Electrode gather (Fig. 2 "bin & accumulate on unique electrodes"): every
+ * in-plane pixel of an active block's output footprint is active; its waveform
+ * [0, nt) is the sum, in a fixed order, of the overlapping blocks' outputs.
+ * pixel_ids[npix] ascending, waveforms [max_pixels][nt], n_pixels_dev[0] = npix. */
+int32_t tred_gather_pixels(tred_handle *h, const int32_t *block_ids,
+                           const int32_t *n_blocks_dev, const float *out_blocks,
+                           int32_t *pixel_ids, float *waveforms, int32_t *n_pixels_dev,
+                           void *stream);
+
+/* a6. Trigger-reset readout (Sec. II-E, Fig. 6).  C = running sum of the current
+ * since the end of the last reset; at clock edges k >= start, if C(k) >= threshold
+ * a hit (pixel, k + hold, C(k + hold)) is emitted when k + hold < nt and C restarts
+ * at k + hold + reset + 1.  Hits sorted by (pixel, tick); n_hits_dev[0] = count. */
+int32_t tred_readout(tred_handle *h, const tred_readout_params *rp,
+                     const int32_t *pixel_ids, const float *waveforms,
+                     const int32_t *n_pixels_dev, int32_t *hit_pixel, int32_t *hit_tick,
+                     float *hit_charge, int32_t *n_hits_dev, int32_t max_hits,
+                     void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* TRED_H */

@@ -1,0 +1,249 @@
+// a2. Block-sparse binning (Sec. III-B-1): occupancy of every block, warp-ballot
+// + prefix-scan compaction into the ascending active-block list, block -> slot map
+// and the per-block deposit CSR.
+//
+//   k_bb_count   one thread per deposit: clipped support box -> touched blocks,
+//                atomicAdd on the block's count
+//   k_bb_chunk   one 1024-wide chunk of blocks per CTA: ballot/popc counts of
+//                active blocks and their occupancy sum
+//   k_bb_top     one CTA: exclusive scan of the chunk totals; writes nb
+//   k_bb_emit    per chunk: ballot + warp/CTA prefix -> slot of each active block
+//   k_bb_fill    one thread per deposit: CSR fill through per-slot cursors
+#include "tred_internal.cuh"
+
+namespace tred {
+
+struct BinGeom {
+    int ns, bp, bt, ngx, ngy, nt, nbx, nby, nbt;
+};
+
+__device__ __forceinline__ bool support_box(const tred_deposits &d, int i, const BinGeom &g,
+                                            int &bx0, int &bx1, int &by0, int &by1, int &bt0,
+                                            int &bt1) {
+    int xa = d.lo_x[i] - 1, xb = d.hi_x[i] + 1;
+    int ya = d.lo_y[i] - 1, yb = d.hi_y[i] + 1;
+    int ta = d.lo_t[i] - 1, tb = d.hi_t[i] + 1;
+    if (d.lo_x[i] > d.hi_x[i]) return false;   // dropped deposit
+    xa = max(xa, 0);
+    ya = max(ya, 0);
+    ta = max(ta, 0);
+    xb = min(xb, g.ngx - 1);
+    yb = min(yb, g.ngy - 1);
+    tb = min(tb, g.nt - 1);
+    if (xa > xb || ya > yb || ta > tb) return false;
+    bx0 = (xa / g.ns) / g.bp;
+    bx1 = (xb / g.ns) / g.bp;
+    by0 = (ya / g.ns) / g.bp;
+    by1 = (yb / g.ns) / g.bp;
+    bt0 = ta / g.bt;
+    bt1 = tb / g.bt;
+    return true;
+}
+
+__global__ void __launch_bounds__(256) k_bb_count(int n, tred_deposits d, BinGeom g,
+                                                  int32_t *__restrict__ count) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    int bx0, bx1, by0, by1, bt0, bt1;
+    if (!support_box(d, i, g, bx0, bx1, by0, by1, bt0, bt1)) return;
+    for (int by = by0; by <= by1; ++by)
+        for (int bx = bx0; bx <= bx1; ++bx)
+            for (int bt = bt0; bt <= bt1; ++bt)
+                atomicAdd(&count[((int64_t)by * g.nbx + bx) * g.nbt + bt], 1);
+}
+
+// Per 1024-block chunk: number of active blocks and sum of their counts.
+__global__ void __launch_bounds__(1024) k_bb_chunk(int64_t nblk, const int32_t *__restrict__ count,
+                                                   int32_t *__restrict__ part, int64_t nchunks) {
+    __shared__ int s_act[32], s_sum[32];
+    const int64_t id = blockIdx.x * 1024ll + threadIdx.x;
+    const int c = id < nblk ? count[id] : 0;
+    const unsigned bal = __ballot_sync(0xffffffffu, c > 0);
+    int sum = c;
+#pragma unroll
+    for (int o = 16; o; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (lane == 0) {
+        s_act[warp] = __popc(bal);
+        s_sum[warp] = sum;
+    }
+    __syncthreads();
+    if (warp == 0) {
+        int a = s_act[lane], s = s_sum[lane];
+#pragma unroll
+        for (int o = 16; o; o >>= 1) {
+            a += __shfl_xor_sync(0xffffffffu, a, o);
+            s += __shfl_xor_sync(0xffffffffu, s, o);
+        }
+        if (lane == 0) {
+            part[blockIdx.x] = a;
+            part[nchunks + blockIdx.x] = s;
+        }
+    }
+}
+
+// Exclusive scan of the chunk totals in place (one CTA, any number of chunks);
+// part[2*nchunks + 0] = active blocks, part[2*nchunks + 1] = pairs.
+__global__ void __launch_bounds__(1024) k_bb_top(int64_t nchunks, int32_t *__restrict__ part,
+                                                 int32_t max_blocks, int32_t max_pairs,
+                                                 int32_t *__restrict__ n_blocks_dev,
+                                                 int32_t *__restrict__ status) {
+    __shared__ int s_a[32], s_s[32];
+    __shared__ int carry_a, carry_s;
+    if (threadIdx.x == 0) carry_a = carry_s = 0;
+    __syncthreads();
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    for (int64_t base = 0; base < nchunks; base += 1024) {
+        const int64_t i = base + threadIdx.x;
+        int a = i < nchunks ? part[i] : 0;
+        int s = i < nchunks ? part[nchunks + i] : 0;
+        int ia = a, is = s;   // inclusive warp scan
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            int ta = __shfl_up_sync(0xffffffffu, ia, o), ts = __shfl_up_sync(0xffffffffu, is, o);
+            if (lane >= o) { ia += ta; is += ts; }
+        }
+        if (lane == 31) { s_a[warp] = ia; s_s[warp] = is; }
+        __syncthreads();
+        if (warp == 0) {
+            int wa = s_a[lane], wsum = s_s[lane];
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                int ta = __shfl_up_sync(0xffffffffu, wa, o), ts = __shfl_up_sync(0xffffffffu, wsum, o);
+                if (lane >= o) { wa += ta; wsum += ts; }
+            }
+            s_a[lane] = wa;
+            s_s[lane] = wsum;
+        }
+        __syncthreads();
+        const int wa = warp ? s_a[warp - 1] : 0, wsum = warp ? s_s[warp - 1] : 0;
+        if (i < nchunks) {
+            part[i] = carry_a + wa + ia - a;
+            part[nchunks + i] = carry_s + wsum + is - s;
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            carry_a += s_a[31];
+            carry_s += s_s[31];
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        int nb = carry_a;
+        if (nb > max_blocks) {
+            atomicOr(&status[0], TRED_ST_BLOCK_OVERFLOW);
+            nb = max_blocks;
+        }
+        if (carry_s > max_pairs) atomicOr(&status[0], TRED_ST_PAIR_OVERFLOW);
+        n_blocks_dev[0] = nb;
+        status[2] = carry_a;
+        status[3] = carry_s;
+        part[2 * nchunks] = carry_a;
+        part[2 * nchunks + 1] = carry_s;
+    }
+}
+
+__global__ void __launch_bounds__(1024) k_bb_emit(int64_t nblk, const int32_t *__restrict__ count,
+                                                  const int32_t *__restrict__ part, int64_t nchunks,
+                                                  int32_t max_blocks, int32_t max_pairs,
+                                                  int32_t *__restrict__ slot_of,
+                                                  int32_t *__restrict__ block_ids,
+                                                  int32_t *__restrict__ block_counts,
+                                                  int32_t *__restrict__ dep_offsets,
+                                                  int32_t *__restrict__ fill) {
+    __shared__ int s_a[32], s_s[32];
+    const int64_t id = blockIdx.x * 1024ll + threadIdx.x;
+    const int c = id < nblk ? count[id] : 0;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const unsigned bal = __ballot_sync(0xffffffffu, c > 0);
+    const int rank = __popc(bal & ((1u << lane) - 1u));
+    int is = c;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        int t = __shfl_up_sync(0xffffffffu, is, o);
+        if (lane >= o) is += t;
+    }
+    if (lane == 31) {
+        s_a[warp] = __popc(bal);
+        s_s[warp] = is;
+    }
+    __syncthreads();
+    if (warp == 0) {
+        int a = s_a[lane], s = s_s[lane];
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            int ta = __shfl_up_sync(0xffffffffu, a, o), ts = __shfl_up_sync(0xffffffffu, s, o);
+            if (lane >= o) { a += ta; s += ts; }
+        }
+        s_a[lane] = a - s_a[lane];   // exclusive
+        s_s[lane] = s - s_s[lane];
+    }
+    __syncthreads();
+    if (id >= nblk) return;
+    if (c == 0) {
+        slot_of[id] = -1;
+        return;
+    }
+    const int slot = part[blockIdx.x] + s_a[warp] + rank;
+    const int off = part[nchunks + blockIdx.x] + s_s[warp] + is - c;
+    if (slot >= max_blocks) {
+        slot_of[id] = -1;
+        return;
+    }
+    slot_of[id] = slot;
+    block_ids[slot] = (int32_t)id;
+    block_counts[slot] = c;
+    // offsets are clamped to max_pairs so that an overflowing CSR (status bit set)
+    // never sends a reader past the dep_index capacity
+    dep_offsets[slot] = min(off, max_pairs);
+    fill[slot] = 0;
+    // the CSR end of the last kept slot
+    const int nb = min(part[2 * nchunks], max_blocks);
+    if (slot == nb - 1) dep_offsets[nb] = min(off + c, max_pairs);
+}
+
+__global__ void __launch_bounds__(256) k_bb_fill(int n, tred_deposits d, BinGeom g,
+                                                 const int32_t *__restrict__ slot_of,
+                                                 const int32_t *__restrict__ dep_offsets,
+                                                 int32_t *__restrict__ fill,
+                                                 int32_t *__restrict__ dep_index, int32_t max_pairs) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    int bx0, bx1, by0, by1, bt0, bt1;
+    if (!support_box(d, i, g, bx0, bx1, by0, by1, bt0, bt1)) return;
+    for (int by = by0; by <= by1; ++by)
+        for (int bx = bx0; bx <= bx1; ++bx)
+            for (int bt = bt0; bt <= bt1; ++bt) {
+                const int s = slot_of[((int64_t)by * g.nbx + bx) * g.nbt + bt];
+                if (s < 0) continue;
+                const int pos = dep_offsets[s] + atomicAdd(&fill[s], 1);
+                if (pos < max_pairs) dep_index[pos] = i;
+            }
+}
+
+// Zero-block case: dep_offsets[0] = 0 must still hold.
+__global__ void k_bb_offsets0(int32_t *dep_offsets, const int32_t *n_blocks_dev) {
+    if (n_blocks_dev[0] == 0) dep_offsets[0] = 0;
+}
+
+int launch_blockbin(tred_handle *h, int n, const tred_deposits &deps, int32_t *block_ids,
+                    int32_t *block_counts, int32_t *dep_offsets, int32_t *dep_index,
+                    int32_t max_pairs, int32_t *n_blocks_dev, cudaStream_t s) {
+    BinGeom g{h->g.n_sub, h->g.bp, h->g.bt, h->d.ngx, h->d.ngy, h->g.nt, h->d.nbx, h->d.nby, h->d.nbt};
+    int rc = check_cuda(h, cudaMemsetAsync(h->blk_count, 0, sizeof(int32_t) * h->d.nblk, s), "clear counts");
+    if (rc) return rc;
+    if (n > 0) k_bb_count<<<(n + 255) / 256, 256, 0, s>>>(n, deps, g, h->blk_count);
+    k_bb_chunk<<<(unsigned)h->nchunks, 1024, 0, s>>>(h->d.nblk, h->blk_count, h->scan_part, h->nchunks);
+    k_bb_top<<<1, 1024, 0, s>>>(h->nchunks, h->scan_part, h->max_blocks, max_pairs, n_blocks_dev, h->status);
+    k_bb_emit<<<(unsigned)h->nchunks, 1024, 0, s>>>(h->d.nblk, h->blk_count, h->scan_part, h->nchunks,
+                                                    h->max_blocks, max_pairs, h->blk_slot, block_ids,
+                                                    block_counts, dep_offsets, h->blk_fill);
+    k_bb_offsets0<<<1, 1, 0, s>>>(dep_offsets, n_blocks_dev);
+    if (n > 0)
+        k_bb_fill<<<(n + 255) / 256, 256, 0, s>>>(n, deps, g, h->blk_slot, dep_offsets, h->blk_fill,
+                                                  dep_index, max_pairs);
+    h->launches += 4 + (n > 0 ? 2 : 0);
+    return check_cuda(h, cudaGetLastError(), "blockbin launch");
+}
+
+}  // namespace tred

@@ -1,0 +1,361 @@
+// a4. Interlaced convolution with the field response (Sec. II-D, Eq. interlaced)
+// evaluated by FFT with Mirror-Pair Complex Packing (Sec. III-A-2, Eq. multch).
+//
+// Per active block and impact pair (j, j') with j' the mirror impact of j, the
+// packed input is Z = Qeff[j] + i * flip(Qeff[j']) (flip = spatial reflection inside
+// the block), zero padded to 16 x 16 x lt.  With the mirror symmetry i[-j, -K] =
+// i[j, K] of the response, one complex FFT per pair, a product with the
+// precomputed spectrum Rhat[j] and a single inverse FFT of the sum over pairs give
+//     out[u] = Re C[(u - R) mod 16] + Im C[(bp - 1 + R - u) mod 16]   (per axis).
+// Without MPCP each impact is its own (real) channel and out[u] = Re C[...].
+//
+// Work split (B300: 148 SMs, 227 KB shared memory per CTA):
+//   k_conv_spec   one CTA (512 threads) per (block, time-frequency class k1):
+//                 the class owns the 64 bins f = k1 + G k2.  Stage A computes, per
+//                 column, the time DFT restricted to the class (an in-lane
+//                 pre-butterfly over the nonzero n1 = 0..bt/64-1 blocks of the
+//                 input followed by a 64-point FFT across the warp); stage B does
+//                 the 16 x 16 spatial FFT of every bin (8-point in-lane FFTs and a
+//                 per-warp shared transpose) and accumulates Rhat * Z in shared
+//                 memory.  The epilogue inverts the spatial FFT and writes the bins
+//                 of the class to the per-chunk spectrum buffer.
+//   k_conv_itime  one CTA per (block, mirror row pair, half): inverse time FFT of
+//                 16 columns (8 mirror pairs) and the MPCP recombination.
+#include <utility>
+
+#include "tred_internal.cuh"
+
+namespace tred {
+
+struct ConvConst {
+    int ns, bp, bt, nch, npairs, G, lt, R, mpcp;
+};
+
+constexpr int SPEC_THREADS = 512;
+constexpr int SPEC_WARPS = SPEC_THREADS / 32;
+constexpr int ACC_ROW = 17;                 // padded row (float2) of the accumulator
+constexpr int ACC_BIN = LP * ACC_ROW;       // 272 float2 per bin
+constexpr int ZT_ROW = 9;                   // padded px row of the bin-major transpose
+constexpr int ZT_BIN = 8 * ZT_ROW;          // [py][px] for py, px < 8
+constexpr int TB_ROW = 9;                   // per-warp transpose rows [kx][py]
+constexpr int TB_BIN = LP * TB_ROW;
+
+constexpr size_t SPEC_SMEM = sizeof(float2) * ((size_t)BINS * ACC_BIN + (size_t)BINS * ZT_BIN +
+                                               (size_t)SPEC_WARPS * 2 * TB_BIN + 32 + 16 + 8 + 64);
+
+template <int NB1, int G>
+__global__ void __launch_bounds__(SPEC_THREADS, 1)
+    k_conv_spec(const int32_t *__restrict__ n_blocks_dev, const float *__restrict__ qeff,
+                const uint64_t *__restrict__ colmask, const float2 *__restrict__ rhat,
+                const int32_t *__restrict__ pair_j, const float2 *__restrict__ tw, ConvConst c,
+                float2 *__restrict__ yspec, int slot_base, int slot_count) {
+    constexpr int LT = 64 * G;
+    extern __shared__ float2 smem[];
+    float2 *acc = smem;                               // [64][16][17]
+    float2 *zt = acc + BINS * ACC_BIN;                // [64][8][9]
+    float2 *tbuf = zt + BINS * ZT_BIN;                // [warps][2][16][9]
+    float2 *w32 = tbuf + SPEC_WARPS * 2 * TB_BIN;     // W_32
+    float2 *w16 = w32 + 32;                           // W_16
+    float2 *w8 = w16 + 16;                            // W_8
+    float2 *w64 = w8 + 8;                             // W_64
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    if (tid < 32) w32[tid] = tw[TW_32 + tid];
+    if (tid < 16) w16[tid] = tw[TW_16 + tid];
+    if (tid < 8) w8[tid] = tw[TW_8 + tid];
+    if (tid < 64) w64[tid] = tw[TW_64 + tid];
+    for (int k = tid; k < BINS * ZT_BIN; k += SPEC_THREADS) zt[k] = make_float2(0.f, 0.f);
+    __syncthreads();
+
+    const int nb = n_blocks_dev[0];
+    const int nloc = min(slot_count, nb - slot_base);
+    if (nloc <= 0) return;
+    const int cols = c.bp * c.bp;
+    const int slab = cols * c.bt;
+    const int items = nloc * G;
+    float2 *tb = tbuf + warp * 2 * TB_BIN;
+
+    for (int item = blockIdx.x; item < items; item += gridDim.x) {
+        const int sl = item / G, k1 = item % G;
+        const int slot = slot_base + sl;
+        // per-lane stage A twiddles for this class
+        float2 wg[NB1];
+#pragma unroll
+        for (int n1 = 0; n1 < NB1; ++n1) wg[n1] = tw[TW_LT + ((64 * k1 * n1) % LT)];
+        const float2 wl0 = tw[TW_LT + (k1 * lane) % LT];
+        const float2 wl1 = tw[TW_LT + (k1 * (lane + 32)) % LT];
+        const float2 w64l = w64[lane];
+        for (int k = tid; k < BINS * ACC_BIN; k += SPEC_THREADS) acc[k] = make_float2(0.f, 0.f);
+        __syncthreads();
+
+        const float *qblk = qeff + (size_t)slot * c.nch * slab;
+        const uint64_t *mrow = colmask + (size_t)slot * c.nch;
+        for (int p = 0; p < c.npairs; ++p) {
+            const int j1 = pair_j[2 * p], j2 = pair_j[2 * p + 1];
+            uint64_t pm = mrow[j1];
+            if (j2 >= 0) pm |= __brevll(mrow[j2]) >> (64 - cols);
+            // ---------------- stage A: class-restricted time DFT per column
+            for (int col = warp; col < cols; col += SPEC_WARPS) {
+                const int py = col / c.bp, px = col - py * c.bp;
+                float2 *zdst = zt + py * ZT_ROW + px;
+                const int b5 = bitrev<32>(lane);
+                if (!((pm >> col) & 1ull)) {
+                    zdst[(2 * b5) * ZT_BIN] = make_float2(0.f, 0.f);
+                    zdst[(2 * b5 + 1) * ZT_BIN] = make_float2(0.f, 0.f);
+                    continue;
+                }
+                const float *q1 = qblk + (size_t)j1 * slab + (size_t)col * c.bt;
+                const float *q2 = j2 >= 0 ? qblk + (size_t)j2 * slab + (size_t)(cols - 1 - col) * c.bt : nullptr;
+                float2 y0 = make_float2(0.f, 0.f), y1 = make_float2(0.f, 0.f);
+#pragma unroll
+                for (int n1 = 0; n1 < NB1; ++n1) {
+                    const int t0 = lane + 64 * n1, t1 = t0 + 32;
+                    const float2 z0 = make_float2(__ldg(q1 + t0), q2 ? __ldg(q2 + t0) : 0.f);
+                    const float2 z1 = make_float2(__ldg(q1 + t1), q2 ? __ldg(q2 + t1) : 0.f);
+                    y0 = cfma(z0, wg[n1], y0);
+                    y1 = cfma(z1, wg[n1], y1);
+                }
+                y0 = cmul(y0, wl0);
+                y1 = cmul(y1, wl1);
+                float2 v0 = cadd(y0, y1);
+                float2 v1 = cmul(csub(y0, y1), w64l);
+                v0 = fft32_lanes<false>(v0, w32, lane);
+                v1 = fft32_lanes<false>(v1, w32, lane);
+                zdst[(2 * b5) * ZT_BIN] = v0;          // bin k2 = a + 2 b
+                zdst[(2 * b5 + 1) * ZT_BIN] = v1;
+            }
+            __syncthreads();
+            // ---------------- stage B: spatial FFT per bin, product with Rhat, accumulate
+            const float2 *rp = rhat + ((size_t)k1 * c.npairs + p) * BINS * (LP * LP);
+#pragma unroll 1
+            for (int it = 0; it < BINS / (2 * SPEC_WARPS); ++it) {
+                const int b = lane >> 4;
+                const int k2 = (BINS / SPEC_WARPS) * warp + 2 * it + b;
+                // prefetch this lane's Rhat column (kx = lane & 15) for the y stage
+                const int kx = lane & 15;
+                float2 rr[LP];
+                const float2 *rsrc = rp + (size_t)k2 * (LP * LP) + kx;
+#pragma unroll
+                for (int ky = 0; ky < LP; ++ky) rr[ky] = __ldg(rsrc + ky * LP);
+                // x stage: lane = (b, py, h): 8-point FFT of the (twiddled) row
+                {
+                    const int py = (lane >> 1) & 7, h = lane & 1;
+                    const float2 *zrow = zt + k2 * ZT_BIN + py * ZT_ROW;
+                    float2 v[8];
+#pragma unroll
+                    for (int x = 0; x < 8; ++x) {
+                        float2 z = zrow[x];
+                        if (h) z = cmul(z, w16[x]);
+                        v[x] = z;
+                    }
+                    fft_reg_dif<8, false>(v, w8);
+                    float2 *dst = tb + b * TB_BIN + py;
+#pragma unroll
+                    for (int k = 0; k < 8; ++k) dst[(2 * bitrev<8>(k) + h) * TB_ROW] = v[k];
+                }
+                __syncwarp();
+                // y stage: lane = (b, kx): 16-point FFT of 8 nonzero inputs
+                {
+                    const float2 *src = tb + b * TB_BIN + kx * TB_ROW;
+                    float2 e[8], o[8];
+#pragma unroll
+                    for (int y = 0; y < 8; ++y) {
+                        e[y] = src[y];
+                        o[y] = cmul(e[y], w16[y]);
+                    }
+                    fft_reg_dif<8, false>(e, w8);
+                    fft_reg_dif<8, false>(o, w8);
+                    float2 *ab = acc + k2 * ACC_BIN + kx;
+#pragma unroll
+                    for (int k = 0; k < 8; ++k) {
+                        const int ky = 2 * bitrev<8>(k);
+                        float2 a0 = ab[ky * ACC_ROW];
+                        float2 a1 = ab[(ky + 1) * ACC_ROW];
+                        ab[ky * ACC_ROW] = cfma(e[k], rr[ky], a0);
+                        ab[(ky + 1) * ACC_ROW] = cfma(o[k], rr[ky + 1], a1);
+                    }
+                }
+                __syncwarp();
+            }
+            __syncthreads();
+        }
+        // ---------------- epilogue: inverse spatial FFT of every bin, in place
+#pragma unroll 1
+        for (int it = 0; it < BINS / (2 * SPEC_WARPS); ++it) {
+            const int b = lane >> 4, r = lane & 15;
+            const int k2 = (BINS / SPEC_WARPS) * warp + 2 * it + b;
+            float2 *ab = acc + k2 * ACC_BIN;
+            float2 v[LP];
+#pragma unroll
+            for (int x = 0; x < LP; ++x) v[x] = ab[r * ACC_ROW + x];        // row ky = r
+            fft_reg_dif<LP, true>(v, w16);
+#pragma unroll
+            for (int k = 0; k < LP; ++k) ab[r * ACC_ROW + bitrev<LP>(k)] = v[k];
+            __syncwarp();
+#pragma unroll
+            for (int y = 0; y < LP; ++y) v[y] = ab[y * ACC_ROW + r];        // column cx = r
+            fft_reg_dif<LP, true>(v, w16);
+            __syncwarp();
+#pragma unroll
+            for (int k = 0; k < LP; ++k) ab[bitrev<LP>(k) * ACC_ROW + r] = v[k];
+            __syncwarp();
+        }
+        __syncthreads();
+        // write the class's bins: yspec[sl][f][cy*16+cx], f = k1 + G k2
+        for (int k = tid; k < BINS * LP * LP; k += SPEC_THREADS) {
+            const int k2 = k >> 8, cidx = k & 255;
+            const int cy = cidx >> 4, cx = cidx & 15;
+            yspec[((size_t)sl * LT + (k1 + G * k2)) * (LP * LP) + cidx] = acc[k2 * ACC_BIN + cy * ACC_ROW + cx];
+        }
+        __syncthreads();
+    }
+}
+
+// Inverse time FFT of 8 mirror column pairs + MPCP recombination.
+template <int G>
+__global__ void __launch_bounds__(256) k_conv_itime(const int32_t *__restrict__ n_blocks_dev,
+                                                    const float2 *__restrict__ yspec,
+                                                    const float2 *__restrict__ tw, ConvConst c,
+                                                    float *__restrict__ out, int slot_base,
+                                                    int slot_count) {
+    constexpr int LT = 64 * G;
+    constexpr int NPL = LT / 32;          // values per lane
+    constexpr int SROW = LT + 1;
+    extern __shared__ float2 sm[];
+    float2 *S = sm;                       // [16][LT + 1]
+    float2 *wlt = S + 16 * SROW;          // W_LT
+    float2 *w32 = wlt + LT;
+    float2 *wn = w32 + 32;                // W_NPL
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    for (int k = tid; k < LT; k += blockDim.x) wlt[k] = tw[TW_LT + k];
+    if (tid < 32) w32[tid] = tw[TW_32 + tid];
+    if (tid < NPL) wn[tid] = tw[TW_LT + tid * 32];        // W_NPL^m = W_LT^{32 m}
+    const int nb = n_blocks_dev[0];
+    const int nloc = min(slot_count, nb - slot_base);
+    if (nloc <= 0) return;
+    const int items = nloc * 16;
+    for (int item = blockIdx.x; item < items; item += gridDim.x) {
+        const int sl = item >> 4, rp = (item >> 1) & 7, half = item & 1;
+        // mirror map on cyclic indices: m(c) = (bp - 1 - c) mod 16; row pairs {a, m(a)}
+        int a = -1, cnt = 0;
+        for (int r = 0; r < LP; ++r) {
+            const int m = (c.bp - 1 - r + 2 * LP) % LP;
+            if (r < m) {
+                if (cnt == rp) { a = r; break; }
+                ++cnt;
+            }
+        }
+        const int bro = (c.bp - 1 - a + 2 * LP) % LP;
+        __syncthreads();
+        // load 16 columns: q < 8 -> (a, cx = 8 half + q); q >= 8 -> (bro, m(8 half + q - 8))
+        for (int k = tid; k < 16 * LT; k += blockDim.x) {
+            const int q = k & 15, f = k >> 4;
+            const int cx0 = 8 * half + (q & 7);
+            const int cy = q < 8 ? a : bro;
+            const int cx = q < 8 ? cx0 : (c.bp - 1 - cx0 + 2 * LP) % LP;
+            S[q * SROW + f] = yspec[((size_t)sl * LT + f) * (LP * LP) + cy * LP + cx];
+        }
+        __syncthreads();
+        if (warp < 8) {
+            const int q = warp;                       // pair (q, q + 8)
+            const int cx1 = 8 * half + q;
+            const int cx2 = (c.bp - 1 - cx1 + 2 * LP) % LP;
+            float2 x1[NPL], x2[NPL];
+            for (int which = 0; which < 2; ++which) {
+                const float2 *src = S + (which ? q + 8 : q) * SROW;
+                float2 v[NPL];
+#pragma unroll
+                for (int m = 0; m < NPL; ++m) v[m] = src[lane + 32 * m];
+                fft_reg_dif<NPL, true>(v, wn);        // v[k] = u[bitrev(k)]
+#pragma unroll
+                for (int k = 0; k < NPL; ++k) {
+                    const int aa = bitrev<NPL>(k);
+                    float2 w = wlt[(lane * aa) % LT];
+                    w.y = -w.y;
+                    v[k] = fft32_lanes<true>(cmul(v[k], w), w32, lane);
+                }
+#pragma unroll
+                for (int k = 0; k < NPL; ++k) {
+                    if (which) x2[k] = v[k];
+                    else x1[k] = v[k];
+                }
+            }
+            // lane holds t = NPL * bitrev5(lane) + bitrev(k) in register k
+            const int uy1 = (a + c.R) % LP, ux1 = (cx1 + c.R) % LP;
+            const int uy2 = (bro + c.R) % LP, ux2 = (cx2 + c.R) % LP;
+            const int slot = slot_base + sl;
+            float *o1 = out + (((size_t)slot * LP + uy1) * LP + ux1) * LT + NPL * bitrev<32>(lane);
+            float *o2 = out + (((size_t)slot * LP + uy2) * LP + ux2) * LT + NPL * bitrev<32>(lane);
+            float r1[NPL], r2[NPL];
+#pragma unroll
+            for (int k = 0; k < NPL; ++k) {
+                const int t = bitrev<NPL>(k);
+                r1[t] = c.mpcp ? x1[k].x + x2[k].y : x1[k].x;
+                r2[t] = c.mpcp ? x2[k].x + x1[k].y : x2[k].x;
+            }
+#pragma unroll
+            for (int k = 0; k < NPL; k += 4) {
+                *reinterpret_cast<float4 *>(o1 + k) = make_float4(r1[k], r1[k + 1], r1[k + 2], r1[k + 3]);
+                *reinterpret_cast<float4 *>(o2 + k) = make_float4(r2[k], r2[k + 1], r2[k + 2], r2[k + 3]);
+            }
+        }
+    }
+}
+
+template <int NB1, int G>
+static int run_conv(tred_handle *h, const int32_t *n_blocks_dev, const float *qeff, float *out,
+                    const ConvConst &c, cudaStream_t s) {
+    static bool attr = false;
+    const size_t itime_smem = sizeof(float2) * (16 * (64 * G + 1) + 64 * G + 32 + 64 * G / 32);
+    if (!attr) {
+        cudaFuncSetAttribute(k_conv_spec<NB1, G>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SPEC_SMEM);
+        cudaFuncSetAttribute(k_conv_itime<G>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)itime_smem);
+        attr = true;
+    }
+    const int sms = num_sms(h);
+    const int chunk = h->yspec_blocks;
+    for (int base = 0; base < h->max_blocks; base += chunk) {
+        k_conv_spec<NB1, G><<<sms, SPEC_THREADS, SPEC_SMEM, s>>>(n_blocks_dev, qeff, h->colmask, h->rhat,
+                                                                 h->pair_j, h->tw, c, h->yspec, base, chunk);
+        k_conv_itime<G><<<sms * 2, 256, itime_smem, s>>>(n_blocks_dev, h->yspec, h->tw, c, out, base, chunk);
+        h->launches += 2;
+    }
+    return check_cuda(h, cudaGetLastError(), "convolve launch");
+}
+
+int launch_convolve(tred_handle *h, const int32_t *block_ids, const int32_t *n_blocks_dev,
+                    const float *qeff, float *out, cudaStream_t s) {
+    (void)block_ids;
+    ConvConst c;
+    c.ns = h->g.n_sub;
+    c.bp = h->g.bp;
+    c.bt = h->g.bt;
+    c.nch = c.ns * c.ns;
+    c.npairs = h->d.npairs;
+    c.G = h->d.G;
+    c.lt = h->g.lt;
+    c.R = h->d.R;
+    c.mpcp = h->p.mpcp;
+    const int nb1 = h->g.bt / 64;
+    if (c.G == 8) {
+        switch (nb1) {
+            case 1: return run_conv<1, 8>(h, n_blocks_dev, qeff, out, c, s);
+            case 2: return run_conv<2, 8>(h, n_blocks_dev, qeff, out, c, s);
+            case 3: return run_conv<3, 8>(h, n_blocks_dev, qeff, out, c, s);
+            case 4: return run_conv<4, 8>(h, n_blocks_dev, qeff, out, c, s);
+            case 5: return run_conv<5, 8>(h, n_blocks_dev, qeff, out, c, s);
+            case 6: return run_conv<6, 8>(h, n_blocks_dev, qeff, out, c, s);
+            case 7: return run_conv<7, 8>(h, n_blocks_dev, qeff, out, c, s);
+            default: break;
+        }
+    } else if (c.G == 16) {
+        switch (nb1) {
+            case 2: return run_conv<2, 16>(h, n_blocks_dev, qeff, out, c, s);
+            case 4: return run_conv<4, 16>(h, n_blocks_dev, qeff, out, c, s);
+            case 8: return run_conv<8, 16>(h, n_blocks_dev, qeff, out, c, s);
+            default: break;
+        }
+    }
+    return set_error(h, TRED_ERR_INVALID_ARG, "convolve: unsupported bt=%d lt=%d", h->g.bt, h->g.lt);
+}
+
+}  // namespace tred

@@ -1,0 +1,231 @@
+// a5. Electrode gather (Fig. 2: "bin & accumulate on unique electrodes").
+//
+//   k_px_mark    flag every in-plane pixel of each active block's output footprint
+//                [bx bp - R, bx bp + bp + R) x (same in y)
+//   k_px_chunk / k_px_top / k_px_emit
+//                ballot + prefix compaction of the flags into the ascending pixel
+//                list; the flag array then holds each pixel's row (or -1)
+//   k_px_wave    one warp per active pixel, 128 ticks per step (float4 per lane):
+//                sum, in a fixed order (by, bx, bt ascending), the outputs of the
+//                overlapping blocks; deterministic, no atomics.  Optional FP64
+//                accumulation (compensated mode).
+#include "tred_internal.cuh"
+
+namespace tred {
+
+struct GatherConst {
+    int npx_x, npx_y, nt, bp, bt, nr, lt, R, nbx, nby, nbt, comp;
+};
+
+__global__ void k_px_mark(const int32_t *__restrict__ block_ids, const int32_t *__restrict__ n_blocks_dev,
+                          GatherConst c, int32_t *__restrict__ flags) {
+    const int nb = n_blocks_dev[0];
+    const int side = c.bp + 2 * c.R;
+    const int64_t total = (int64_t)nb * side * side;
+    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < total;
+         k += (int64_t)gridDim.x * blockDim.x) {
+        const int slot = (int)(k / (side * side));
+        const int r = (int)(k % (side * side));
+        const int blk = block_ids[slot];
+        const int bxy = blk / c.nbt, bx = bxy % c.nbx, by = bxy / c.nbx;
+        const int x = bx * c.bp - c.R + r % side, y = by * c.bp - c.R + r / side;
+        if (x >= 0 && x < c.npx_x && y >= 0 && y < c.npx_y) flags[(int64_t)y * c.npx_x + x] = 1;
+    }
+}
+
+__global__ void __launch_bounds__(1024) k_px_chunk(int64_t n, const int32_t *__restrict__ flags,
+                                                   int32_t *__restrict__ part) {
+    __shared__ int s[32];
+    const int64_t id = blockIdx.x * 1024ll + threadIdx.x;
+    const unsigned bal = __ballot_sync(0xffffffffu, id < n && flags[id] != 0);
+    if ((threadIdx.x & 31) == 0) s[threadIdx.x >> 5] = __popc(bal);
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        int a = s[threadIdx.x];
+#pragma unroll
+        for (int o = 16; o; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
+        if (threadIdx.x == 0) part[blockIdx.x] = a;
+    }
+}
+
+// Generic single-CTA exclusive scan of part[0..n) in place; total to part[n] and,
+// capped at cap, to *count_dev; sets status bit `flag` and word `word` on overflow.
+__global__ void __launch_bounds__(1024) k_scan_small(int64_t n, int32_t *__restrict__ part, int32_t cap,
+                                                     int32_t *__restrict__ count_dev,
+                                                     int32_t *__restrict__ status, int flag, int word) {
+    __shared__ int s[32];
+    __shared__ int carry;
+    if (threadIdx.x == 0) carry = 0;
+    __syncthreads();
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    for (int64_t base = 0; base < n; base += 1024) {
+        const int64_t i = base + threadIdx.x;
+        const int v = i < n ? part[i] : 0;
+        int x = v;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            int t = __shfl_up_sync(0xffffffffu, x, o);
+            if (lane >= o) x += t;
+        }
+        if (lane == 31) s[warp] = x;
+        __syncthreads();
+        if (warp == 0) {
+            int w = s[lane];
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                int t = __shfl_up_sync(0xffffffffu, w, o);
+                if (lane >= o) w += t;
+            }
+            s[lane] = w;
+        }
+        __syncthreads();
+        if (i < n) part[i] = carry + (warp ? s[warp - 1] : 0) + x - v;
+        __syncthreads();
+        if (threadIdx.x == 0) carry += s[31];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        part[n] = carry;
+        int m = carry;
+        if (m > cap) {
+            atomicOr(&status[0], flag);
+            m = cap;
+        }
+        *count_dev = m;
+        status[word] = carry;
+    }
+}
+
+__global__ void __launch_bounds__(1024) k_px_emit(int64_t n, int32_t *__restrict__ flags,
+                                                  const int32_t *__restrict__ part, int32_t cap,
+                                                  int32_t *__restrict__ pixel_ids) {
+    __shared__ int s[32];
+    const int64_t id = blockIdx.x * 1024ll + threadIdx.x;
+    const bool on = id < n && flags[id] != 0;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const unsigned bal = __ballot_sync(0xffffffffu, on);
+    if (lane == 0) s[warp] = __popc(bal);
+    __syncthreads();
+    if (warp == 0) {
+        int a = s[lane];
+        int x = a;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            int t = __shfl_up_sync(0xffffffffu, x, o);
+            if (lane >= o) x += t;
+        }
+        s[lane] = x - a;
+    }
+    __syncthreads();
+    if (id >= n) return;
+    if (!on) {
+        flags[id] = -1;
+        return;
+    }
+    const int row = part[blockIdx.x] + s[warp] + __popc(bal & ((1u << lane) - 1u));
+    if (row < cap) {
+        pixel_ids[row] = (int32_t)id;
+        flags[id] = row;
+    } else {
+        flags[id] = -1;
+    }
+}
+
+template <bool COMP>
+__global__ void __launch_bounds__(256) k_px_wave(const int32_t *__restrict__ pixel_ids,
+                                                 const int32_t *__restrict__ n_pixels_dev,
+                                                 const int32_t *__restrict__ slot_of,
+                                                 const float *__restrict__ out, GatherConst c,
+                                                 float *__restrict__ wave) {
+    const int np = n_pixels_dev[0];
+    const int lane = threadIdx.x & 31;
+    const int nwarps = (gridDim.x * blockDim.x) >> 5;
+    const int span = c.bt + c.nr - 1;      // meaningful ticks of a block's output
+    for (int row = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; row < np; row += nwarps) {
+        const int pid = pixel_ids[row];
+        const int x = pid % c.npx_x, y = pid / c.npx_x;
+        const int bx_lo = max(0, floordiv(x - c.bp - c.R, c.bp) + 1), bx_hi = min(c.nbx - 1, floordiv(x + c.R, c.bp));
+        const int by_lo = max(0, floordiv(y - c.bp - c.R, c.bp) + 1), by_hi = min(c.nby - 1, floordiv(y + c.R, c.bp));
+        float *dst = wave + (size_t)row * c.nt;
+        for (int T0 = 0; T0 < c.nt; T0 += 128) {
+            const int t = T0 + 4 * lane;
+            double ad[4] = {0, 0, 0, 0};
+            float af[4] = {0, 0, 0, 0};
+            // blocks whose output range [bt*BT, bt*BT + span) meets [T0, T0 + 128)
+            const int bt_lo = max(0, floordiv(T0 - span, c.bt) + 1);
+            const int bt_hi = min(c.nbt - 1, floordiv(T0 + 127, c.bt));
+            for (int by = by_lo; by <= by_hi; ++by)
+                for (int bx = bx_lo; bx <= bx_hi; ++bx)
+                    for (int bt = bt_lo; bt <= bt_hi; ++bt) {
+                        const int slot = slot_of[((int64_t)by * c.nbx + bx) * c.nbt + bt];
+                        if (slot < 0) continue;
+                        const int uy = y - by * c.bp + c.R, ux = x - bx * c.bp + c.R;
+                        const int tl = t - bt * c.bt;     // multiple of 4
+                        if (tl + 3 < 0 || tl >= span) continue;
+                        const float *src = out + (((size_t)slot * LP + uy) * LP + ux) * c.lt;
+                        float4 v;
+                        if (tl >= 0 && tl + 3 < span) {
+                            v = *reinterpret_cast<const float4 *>(src + tl);
+                        } else {
+                            v.x = (tl >= 0 && tl < span) ? src[tl] : 0.f;
+                            v.y = (tl + 1 >= 0 && tl + 1 < span) ? src[tl + 1] : 0.f;
+                            v.z = (tl + 2 >= 0 && tl + 2 < span) ? src[tl + 2] : 0.f;
+                            v.w = (tl + 3 >= 0 && tl + 3 < span) ? src[tl + 3] : 0.f;
+                        }
+                        if (COMP) {
+                            ad[0] += v.x; ad[1] += v.y; ad[2] += v.z; ad[3] += v.w;
+                        } else {
+                            af[0] += v.x; af[1] += v.y; af[2] += v.z; af[3] += v.w;
+                        }
+                    }
+            if (t < c.nt) {
+                float4 o = COMP ? make_float4((float)ad[0], (float)ad[1], (float)ad[2], (float)ad[3])
+                                : make_float4(af[0], af[1], af[2], af[3]);
+                *reinterpret_cast<float4 *>(dst + t) = o;
+            }
+        }
+    }
+}
+
+// block -> slot map of the listed active blocks (the rest -1)
+__global__ void k_slot_map(const int32_t *__restrict__ block_ids, const int32_t *__restrict__ n_blocks_dev,
+                           int32_t *__restrict__ slot_of) {
+    const int nb = n_blocks_dev[0];
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < nb; k += gridDim.x * blockDim.x)
+        slot_of[block_ids[k]] = k;
+}
+
+int launch_gather(tred_handle *h, const int32_t *block_ids, const int32_t *n_blocks_dev,
+                  const float *out, int32_t *pixel_ids, float *wave, int32_t *n_pixels_dev,
+                  cudaStream_t s) {
+    GatherConst c{h->g.npx_x, h->g.npx_y, h->g.nt, h->g.bp, h->g.bt, h->g.nr, h->g.lt, h->d.R,
+                  h->d.nbx, h->d.nby, h->d.nbt, h->p.compensated_gather};
+    const int64_t npx = (int64_t)h->g.npx_x * h->g.npx_y;
+    int rc = check_cuda(h, cudaMemsetAsync(h->pix_flag, 0, sizeof(int32_t) * npx, s), "clear pixel flags");
+    if (rc) return rc;
+    const int sms = num_sms(h);
+    rc = check_cuda(h, cudaMemsetAsync(h->blk_slot, 0xff, sizeof(int32_t) * h->d.nblk, s), "clear slots");
+    if (rc) return rc;
+    k_slot_map<<<sms * 2, 256, 0, s>>>(block_ids, n_blocks_dev, h->blk_slot);
+    k_px_mark<<<sms * 8, 256, 0, s>>>(block_ids, n_blocks_dev, c, h->pix_flag);
+    k_px_chunk<<<(unsigned)h->pix_chunks, 1024, 0, s>>>(npx, h->pix_flag, h->pix_part);
+    k_scan_small<<<1, 1024, 0, s>>>(h->pix_chunks, h->pix_part, h->max_pixels, n_pixels_dev, h->status,
+                                    TRED_ST_PIXEL_OVERFLOW, 4);
+    k_px_emit<<<(unsigned)h->pix_chunks, 1024, 0, s>>>(npx, h->pix_flag, h->pix_part, h->max_pixels, pixel_ids);
+    if (c.comp)
+        k_px_wave<true><<<sms * 8, 256, 0, s>>>(pixel_ids, n_pixels_dev, h->blk_slot, out, c, wave);
+    else
+        k_px_wave<false><<<sms * 8, 256, 0, s>>>(pixel_ids, n_pixels_dev, h->blk_slot, out, c, wave);
+    h->launches += 6;
+    return check_cuda(h, cudaGetLastError(), "gather launch");
+}
+
+// exported for the readout
+int launch_scan_small(tred_handle *h, int64_t n, int32_t *part, int32_t cap, int32_t *count_dev,
+                      int flag, int word, cudaStream_t s) {
+    k_scan_small<<<1, 1024, 0, s>>>(n, part, cap, count_dev, h->status, flag, word);
+    h->launches += 1;
+    return check_cuda(h, cudaGetLastError(), "scan launch");
+}
+
+}  // namespace tred

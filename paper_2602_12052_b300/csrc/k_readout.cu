@@ -1,0 +1,136 @@
+// a6. Trigger-reset readout (Sec. II-E, Fig. 6: LArPix trigger-reset scheme).
+//
+// One warp per pixel walks the waveform 32 ticks at a time: a warp scan gives the
+// running charge inside the step (FP32), the charge carried between steps is kept
+// in FP64.  Clock edges k >= start with C(k) >= threshold are found with a ballot;
+// the charge is sampled at k + hold, the hit (pixel, k + hold, C) is emitted, and
+// integration restarts at k + hold + reset + 1.
+//
+//   k_ro_count   count hits per pixel; cache the first HIT_TMP hits
+//   (scan)       hit offsets and the total
+//   k_ro_emit    copy cached hits to their sorted position; pixels with more than
+//                HIT_TMP hits are walked again and written directly
+#include "tred_internal.cuh"
+
+namespace tred {
+
+int launch_scan_small(tred_handle *h, int64_t n, int32_t *part, int32_t cap, int32_t *count_dev,
+                      int flag, int word, cudaStream_t s);
+
+struct RoConst {
+    int nt, clock, hold, reset;
+    float thr;
+};
+
+// Walk one pixel; for each hit call sink(index, tick, charge).  Returns the count.
+template <typename Sink>
+__device__ int walk_pixel(const float *__restrict__ I, const RoConst &c, int lane, Sink sink) {
+    int nh = 0;
+    int pos = 0;              // first tick of the current step
+    double base = 0.0;        // charge integrated before pos since the last restart
+    int mode = 0;             // 0: looking for a trigger; 1: waiting for the sample tick
+    int ts = 0;
+    while (pos < c.nt) {
+        const int t = pos + lane;
+        float v = t < c.nt ? I[t] : 0.f;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            float u = __shfl_up_sync(0xffffffffu, v, o);
+            if (lane >= o) v += u;
+        }
+        const double C = base + (double)v;          // C(t) for this lane's tick
+        if (mode == 0) {
+            const bool edge = t < c.nt && (t % c.clock) == 0 && C >= (double)c.thr;
+            const unsigned bal = __ballot_sync(0xffffffffu, edge);
+            if (bal) {
+                const int k = pos + __ffs(bal) - 1;
+                ts = k + c.hold;
+                if (ts >= c.nt) break;                  // sample falls outside the window
+                mode = 1;
+            }
+        }
+        if (mode == 1 && ts < pos + 32) {
+            const double Cs = __shfl_sync(0xffffffffu, C, ts - pos);
+            sink(nh, ts, (float)Cs);
+            ++nh;
+            pos = ts + c.reset + 1;
+            base = 0.0;
+            mode = 0;
+            continue;
+        }
+        base = __shfl_sync(0xffffffffu, C, 31);
+        pos += 32;
+    }
+    return nh;
+}
+
+__global__ void __launch_bounds__(256) k_ro_count(const float *__restrict__ wave,
+                                                  const int32_t *__restrict__ n_pixels_dev, RoConst c,
+                                                  int32_t *__restrict__ cnt, int32_t *__restrict__ tmp_t,
+                                                  float *__restrict__ tmp_c) {
+    const int np = n_pixels_dev[0];
+    const int lane = threadIdx.x & 31;
+    const int nwarps = (gridDim.x * blockDim.x) >> 5;
+    for (int row = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; row < np; row += nwarps) {
+        const float *I = wave + (size_t)row * c.nt;
+        const int nh = walk_pixel(I, c, lane, [&](int k, int t, float q) {
+            if (lane == 0 && k < HIT_TMP) {
+                tmp_t[(size_t)row * HIT_TMP + k] = t;
+                tmp_c[(size_t)row * HIT_TMP + k] = q;
+            }
+        });
+        if (lane == 0) cnt[row] = nh;
+    }
+}
+
+__global__ void __launch_bounds__(256) k_ro_emit(const float *__restrict__ wave,
+                                                 const int32_t *__restrict__ pixel_ids,
+                                                 const int32_t *__restrict__ n_pixels_dev, RoConst c,
+                                                 const int32_t *__restrict__ off,
+                                                 const int32_t *__restrict__ tmp_t,
+                                                 const float *__restrict__ tmp_c, int32_t max_hits,
+                                                 int32_t *__restrict__ hp, int32_t *__restrict__ ht,
+                                                 float *__restrict__ hc) {
+    const int np = n_pixels_dev[0];
+    const int lane = threadIdx.x & 31;
+    const int nwarps = (gridDim.x * blockDim.x) >> 5;
+    for (int row = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; row < np; row += nwarps) {
+        const int o = off[row], nh = off[row + 1] - o;
+        const int pid = pixel_ids[row];
+        if (nh <= HIT_TMP) {
+            if (lane < nh && o + lane < max_hits) {
+                hp[o + lane] = pid;
+                ht[o + lane] = tmp_t[(size_t)row * HIT_TMP + lane];
+                hc[o + lane] = tmp_c[(size_t)row * HIT_TMP + lane];
+            }
+        } else {
+            walk_pixel(wave + (size_t)row * c.nt, c, lane, [&](int k, int t, float q) {
+                if (lane == 0 && o + k < max_hits) {
+                    hp[o + k] = pid;
+                    ht[o + k] = t;
+                    hc[o + k] = q;
+                }
+            });
+        }
+    }
+}
+
+int launch_readout(tred_handle *h, const tred_readout_params &rp, const int32_t *pixel_ids,
+                   const float *wave, const int32_t *n_pixels_dev, int32_t *hit_pixel,
+                   int32_t *hit_tick, float *hit_charge, int32_t *n_hits_dev, int32_t max_hits,
+                   cudaStream_t s) {
+    RoConst c{h->g.nt, rp.clock_ticks, rp.hold_ticks, rp.reset_ticks, rp.threshold_e};
+    const int sms = num_sms(h);
+    int rc = check_cuda(h, cudaMemsetAsync(h->hit_cnt, 0, sizeof(int32_t) * ((size_t)h->max_pixels + 1), s),
+                        "clear hit counts");
+    if (rc) return rc;
+    k_ro_count<<<sms * 8, 256, 0, s>>>(wave, n_pixels_dev, c, h->hit_cnt, h->hit_tmp, h->hit_tmpc);
+    rc = launch_scan_small(h, h->max_pixels, h->hit_cnt, max_hits, n_hits_dev, TRED_ST_HIT_OVERFLOW, 5, s);
+    if (rc) return rc;
+    k_ro_emit<<<sms * 8, 256, 0, s>>>(wave, pixel_ids, n_pixels_dev, c, h->hit_cnt, h->hit_tmp, h->hit_tmpc,
+                                      max_hits, hit_pixel, hit_tick, hit_charge);
+    h->launches += 2;
+    return check_cuda(h, cudaGetLastError(), "readout launch");
+}
+
+}  // namespace tred

