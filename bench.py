@@ -124,6 +124,28 @@ def cpu_baseline(cfg, dep, resp, sample: int):
                        f"({len(r['block_ids'])} blocks, {len(r['pixel_ids'])} pixels), {dt:.1f} s")}
 
 
+def probe_capacities(cfg, dep, dev):
+    """Active blocks of this event (drift + blockbin through the ABI, untimed set-up)
+    so that the device buffers are sized to the workload."""
+    import torch
+    from paper_2602_12052_b300 import tred
+    n = len(dep["x"])
+    h = tred.Handle(tred.geometry(cfg), tred.params(cfg), n, cfg.n_blocks, 1)
+    deps = tred.DepositBuffers(n, dev)
+    x = {k: torch.from_numpy(v).to(dev) for k, v in dep.items()}
+    ids = torch.zeros(cfg.n_blocks, dtype=torch.int32, device=dev)
+    cnt = torch.zeros_like(ids)
+    off = torch.zeros(cfg.n_blocks + 1, dtype=torch.int32, device=dev)
+    idx = torch.zeros(8 * n, dtype=torch.int32, device=dev)
+    nbd = torch.zeros(1, dtype=torch.int32, device=dev)
+    tred.tred_drift(h, n, x["x"], x["y"], x["z"], x["t0"], x["ne"], deps)
+    tred.tred_blockbin(h, n, deps, ids, cnt, off, idx, nbd)
+    nb = int(nbd.item())
+    h.close()
+    side = cfg.bp + cfg.kp - 1
+    return max(nb, 1) + 8, min(cfg.npx * cfg.npx, max(nb, 1) * side * side)
+
+
 def run_reference(args):
     rank, world, _ = _dist()
     if rank != 0:
@@ -181,8 +203,7 @@ def main():
     resp = synth.make_response(cfg)
     n = len(dep["x"])
     dev = torch.device("cuda", local)
-    max_blocks = 10000 if cfg.npx >= 512 else cfg.n_blocks
-    max_pixels = 320000 if cfg.npx >= 512 else cfg.npx * cfg.npx
+    max_blocks, max_pixels = probe_capacities(cfg, dep, dev)
     max_hits = 4 * max_pixels
     sim = tred.Simulator(cfg, torch.from_numpy(resp), max_deposits=n, max_blocks=max_blocks,
                          max_pixels=max_pixels, max_hits=max_hits, device=dev)

@@ -36,7 +36,11 @@ constexpr int SPEC_WARPS = SPEC_THREADS / 32;
 constexpr int ACC_ROW = 17;                 // padded row (float2) of the accumulator
 constexpr int ACC_BIN = LP * ACC_ROW;       // 272 float2 per bin
 constexpr int ZT_ROW = 9;                   // padded px row of the bin-major transpose
-constexpr int ZT_BIN = 8 * ZT_ROW;          // [py][px] for py, px < 8
+constexpr int ZT_BIN = 8 * ZT_ROW + 1;      // [py][px] for py, px < 8, odd stride
+// Bin order inside the transpose buffer: stage A lanes store bins 2 b + a with b a
+// bit-reversed lane index, so even and odd bins go to separate halves and the 32
+// lanes of one store hit 16 distinct 8-byte bank pairs.
+__device__ __forceinline__ int zt_slot(int k2) { return ((k2 & 1) << 5) | (k2 >> 1); }
 constexpr int TB_ROW = 9;                   // per-warp transpose rows [kx][py]
 constexpr int TB_BIN = LP * TB_ROW;
 
@@ -99,8 +103,8 @@ __global__ void __launch_bounds__(SPEC_THREADS, 1)
                 float2 *zdst = zt + py * ZT_ROW + px;
                 const int b5 = bitrev<32>(lane);
                 if (!((pm >> col) & 1ull)) {
-                    zdst[(2 * b5) * ZT_BIN] = make_float2(0.f, 0.f);
-                    zdst[(2 * b5 + 1) * ZT_BIN] = make_float2(0.f, 0.f);
+                    zdst[zt_slot(2 * b5) * ZT_BIN] = make_float2(0.f, 0.f);
+                    zdst[zt_slot(2 * b5 + 1) * ZT_BIN] = make_float2(0.f, 0.f);
                     continue;
                 }
                 const float *q1 = qblk + (size_t)j1 * slab + (size_t)col * c.bt;
@@ -120,8 +124,8 @@ __global__ void __launch_bounds__(SPEC_THREADS, 1)
                 float2 v1 = cmul(csub(y0, y1), w64l);
                 v0 = fft32_lanes<false>(v0, w32, lane);
                 v1 = fft32_lanes<false>(v1, w32, lane);
-                zdst[(2 * b5) * ZT_BIN] = v0;          // bin k2 = a + 2 b
-                zdst[(2 * b5 + 1) * ZT_BIN] = v1;
+                zdst[zt_slot(2 * b5) * ZT_BIN] = v0;          // bin k2 = a + 2 b
+                zdst[zt_slot(2 * b5 + 1) * ZT_BIN] = v1;
             }
             __syncthreads();
             // ---------------- stage B: spatial FFT per bin, product with Rhat, accumulate
@@ -139,7 +143,7 @@ __global__ void __launch_bounds__(SPEC_THREADS, 1)
                 // x stage: lane = (b, py, h): 8-point FFT of the (twiddled) row
                 {
                     const int py = (lane >> 1) & 7, h = lane & 1;
-                    const float2 *zrow = zt + k2 * ZT_BIN + py * ZT_ROW;
+                    const float2 *zrow = zt + zt_slot(k2) * ZT_BIN + py * ZT_ROW;
                     float2 v[8];
 #pragma unroll
                     for (int x = 0; x < 8; ++x) {

@@ -12,13 +12,24 @@
 //
 //   k_effq_weights  one warp per deposit: the three 1-D weight vectors over the
 //                   support [lo-1, hi+1], stored contiguously per deposit
-//   k_effq_blocks   persistent CTAs over (active block, impact channel) items: a
-//                   bp x bp x bt slab accumulated in shared memory from the block's
-//                   deposits, written once with 16-byte stores, plus the mask of
-//                   its non-empty (py, px) columns
+//   k_effq_blocks   persistent CTAs over active blocks, 8-tick tiles of all
+//                   channels x columns in shared memory; each deposit is visited once
+//                   per tile it overlaps; tiles written as full 32-byte sectors; plus
+//                   the mask of non-empty (py, px) columns per channel
 #include "tred_internal.cuh"
 
 namespace tred {
+
+// Per-deposit record for the block kernel (48 bytes), written by k_effq_weights.
+struct DepRec {
+    int gx0, gy0, gt0;             // lo - 1 per axis: index base of the weight vectors
+    int x0, x1, y0, y1, t0, t1;    // support [lo - 1, hi + 1] clipped to the grid
+    float q;
+    int idx;                       // deposit index (row of the weight buffer)
+    int pad;
+};
+
+static_assert(sizeof(DepRec) == 48, "record size is part of the scratch layout");
 
 struct EffqConst {
     int ns, bp, bt, ngx, ngy, nt, nbx, nbt, wx, wt, wstride, gl, mode;
@@ -88,7 +99,7 @@ __device__ float weight_tent(int g, int cell, float frac, float sig, int lo, int
 }
 
 __global__ void __launch_bounds__(256) k_effq_weights(int n, tred_deposits d, EffqConst c,
-                                                      float *__restrict__ wts) {
+                                                      float *__restrict__ wts, DepRec *__restrict__ recs) {
     const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
     if (warp >= n) return;
@@ -99,6 +110,22 @@ __global__ void __launch_bounds__(256) k_effq_weights(int n, tred_deposits d, Ef
     const float frac[3] = {d.frac_x[i], d.frac_y[i], d.frac_t[i]};
     const float sig[3] = {d.sigma_x[i], d.sigma_y[i], d.sigma_t[i]};
     float *w = wts + (size_t)i * c.wstride;
+    if (lane == 0) {
+        DepRec r;
+        r.gx0 = lo[0] - 1;
+        r.gy0 = lo[1] - 1;
+        r.gt0 = lo[2] - 1;
+        r.x0 = max(lo[0] - 1, 0);
+        r.x1 = min(hi[0] + 1, c.ngx - 1);
+        r.y0 = max(lo[1] - 1, 0);
+        r.y1 = min(hi[1] + 1, c.ngy - 1);
+        r.t0 = max(lo[2] - 1, 0);
+        r.t1 = min(hi[2] + 1, c.nt - 1);
+        r.q = d.q[i];
+        r.idx = i;
+        r.pad = 0;
+        recs[i] = r;
+    }
     if (lo[0] > hi[0]) return;   // dropped deposit: never read
 #pragma unroll
     for (int ax = 0; ax < 3; ++ax) {
@@ -113,69 +140,110 @@ __global__ void __launch_bounds__(256) k_effq_weights(int n, tred_deposits d, Ef
     }
 }
 
-// Persistent CTAs over (slot, channel) items.  Shared slab [bp*bp][bt] floats.
-__global__ void __launch_bounds__(256) k_effq_blocks(const int32_t *__restrict__ block_ids,
-                                                     const int32_t *__restrict__ dep_offsets,
-                                                     const int32_t *__restrict__ dep_index,
-                                                     const int32_t *__restrict__ n_blocks_dev,
-                                                     tred_deposits d, EffqConst c,
-                                                     const float *__restrict__ wts,
-                                                     float *__restrict__ qeff,
-                                                     uint64_t *__restrict__ colmask) {
-    extern __shared__ float slab[];
-    __shared__ unsigned s_mask[2];
-    const int nb = n_blocks_dev[0];
+// Persistent CTAs over active blocks, time-tiled.  One tile holds every impact
+// channel and pixel column of the block for EQ_TT consecutive ticks
+// (n_sub^2 x bp^2 x 8 floats, 200 KB at 10 x 10 x 8 x 8), so each deposit is
+// visited once per tile it overlaps and all its sub-cells are handled in that
+// visit: lanes over the deposit's sub-cells (two rows of 16), 8 tick updates per
+// lane from the tile's time weights held in registers.  The tile is written with
+// full 32-byte sectors per column.  Inside a column segment the 8 ticks are rotated
+// by (channel + column / 4) so that lanes updating neighbouring impact channels
+// (segment stride bp^2) land in different banks.
+constexpr int EQ_THREADS = 512;
+constexpr int EQ_TT = 8;
+constexpr int EQ_CACHE = 256;      // deposit records staged per pass
+
+__device__ __forceinline__ int eq_swz(int ch, int col, int cols, int t) {
+    return (ch * cols + col) * EQ_TT + ((t + ch + (col >> 2)) & (EQ_TT - 1));
+}
+
+__global__ void __launch_bounds__(EQ_THREADS, 1) k_effq_blocks(const int32_t *__restrict__ block_ids,
+                                                            const int32_t *__restrict__ dep_offsets,
+                                                            const int32_t *__restrict__ dep_index,
+                                                            const int32_t *__restrict__ n_blocks_dev,
+                                                            EffqConst c, const float *__restrict__ wts,
+                                                            const DepRec *__restrict__ recs,
+                                                            float *__restrict__ qeff,
+                                                            uint64_t *__restrict__ colmask) {
+    extern __shared__ float smem_e[];
     const int nch = c.ns * c.ns;
     const int cols = c.bp * c.bp;
-    const int slab_n = cols * c.bt;
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarps = blockDim.x >> 5;
-    const int64_t items = (int64_t)nb * nch;
-    for (int64_t item = blockIdx.x; item < items; item += gridDim.x) {
-        const int slot = (int)(item / nch), ch = (int)(item % nch);
-        const int jy = ch / c.ns, jx = ch % c.ns;
+    const int nseg = nch * cols;
+    const int side = c.bp * c.ns;
+    float *tile = smem_e;                                                     // [nseg][8]
+    DepRec *rc = reinterpret_cast<DepRec *>(tile + nseg * EQ_TT);             // [EQ_CACHE]
+    unsigned long long *mask = reinterpret_cast<unsigned long long *>(rc + EQ_CACHE);  // [nch]
+    unsigned char *dv = reinterpret_cast<unsigned char *>(mask + nch);        // [side] sub-cell / ns
+    unsigned char *md = dv + side;                                            // [side] sub-cell % ns
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31, nwarps = EQ_THREADS / 32;
+    for (int k = tid; k < side; k += EQ_THREADS) {
+        dv[k] = (unsigned char)(k / c.ns);
+        md[k] = (unsigned char)(k % c.ns);
+    }
+    const int nb = n_blocks_dev[0];
+    for (int slot = blockIdx.x; slot < nb; slot += gridDim.x) {
         const int blk = block_ids[slot];
         const int bt = blk % c.nbt, bxy = blk / c.nbt, bx = bxy % c.nbx, by = bxy / c.nbx;
-        const int gx0 = bx * c.bp * c.ns + jx;    // sub-cell of px = 0 in this channel
-        const int gy0 = by * c.bp * c.ns + jy;
-        const int t0 = bt * c.bt;
-        for (int k = threadIdx.x; k < slab_n; k += blockDim.x) slab[k] = 0.f;
-        if (threadIdx.x < 2) s_mask[threadIdx.x] = 0u;
-        __syncthreads();
+        const int X0 = bx * side, Y0 = by * side, T0 = bt * c.bt;
         const int beg = dep_offsets[slot], end = dep_offsets[slot + 1];
-        for (int k = beg + warp; k < end; k += nwarps) {
-            const int i = dep_index[k];
-            const int lox = d.lo_x[i], hix = d.hi_x[i], loy = d.lo_y[i], hiy = d.hi_y[i];
-            const int lot = d.lo_t[i], hit = d.hi_t[i];
-            const int xa = max(lox - 1, 0), xb = min(hix + 1, c.ngx - 1);
-            const int ya = max(loy - 1, 0), yb = min(hiy + 1, c.ngy - 1);
-            const int ta = max(max(lot - 1, 0), t0), tb = min(min(hit + 1, c.nt - 1), t0 + c.bt - 1);
-            if (ta > tb) continue;
-            const int px0 = max(0, -floordiv(gx0 - xa, c.ns)), px1 = min(c.bp - 1, floordiv(xb - gx0, c.ns));
-            const int py0 = max(0, -floordiv(gy0 - ya, c.ns)), py1 = min(c.bp - 1, floordiv(yb - gy0, c.ns));
-            if (px0 > px1 || py0 > py1) continue;
-            const float q = d.q[i];
-            const float *w = wts + (size_t)i * c.wstride;
-            const float *wxv = w, *wyv = w + c.wx, *wtv = w + 2 * c.wx;
-            for (int py = py0; py <= py1; ++py) {
-                const float ay = q * wyv[gy0 + py * c.ns - (loy - 1)];
-                for (int px = px0; px <= px1; ++px) {
-                    const float a = ay * wxv[gx0 + px * c.ns - (lox - 1)];
-                    float *col = slab + (py * c.bp + px) * c.bt - t0;
-                    for (int t = ta + lane; t <= tb; t += 32)
-                        atomicAdd(&col[t], a * wtv[t - (lot - 1)]);
-                    if (lane == 0) {
-                        const int bit = py * c.bp + px;
-                        atomicOr(&s_mask[bit >> 5], 1u << (bit & 31));
+        const int passes = max(1, (end - beg + EQ_CACHE - 1) / EQ_CACHE);
+        for (int k = tid; k < nch; k += EQ_THREADS) mask[k] = 0ull;
+        for (int tt = 0; tt < c.bt; tt += EQ_TT) {
+            const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
+            for (int k = tid; k < nseg * (EQ_TT / 4); k += EQ_THREADS) reinterpret_cast<float4 *>(tile)[k] = z4;
+            const int ta = T0 + tt, tb = ta + EQ_TT - 1;   // absolute ticks of the tile
+            for (int pass = 0; pass < passes; ++pass) {
+                const int pb = beg + pass * EQ_CACHE;
+                const int pn = min(EQ_CACHE, end - pb);
+                if (tt == 0 || passes > 1) {
+                    __syncthreads();
+                    for (int k = tid; k < pn; k += EQ_THREADS) rc[k] = recs[dep_index[pb + k]];
+                }
+                __syncthreads();
+                for (int k = warp; k < pn; k += nwarps) {
+                    const DepRec r = rc[k];
+                    if (r.t1 < ta || r.t0 > tb) continue;
+                    const int xa = max(r.x0, X0) - X0, xb = min(r.x1, X0 + side - 1) - X0;
+                    const int ya = max(r.y0, Y0) - Y0, yb = min(r.y1, Y0 + side - 1) - Y0;
+                    if (xa > xb || ya > yb) continue;
+                    const float *w = wts + (size_t)r.idx * c.wstride;
+                    const float *wxv = w + (X0 - r.gx0);            // indexed by block-local gx
+                    const float *wyv = w + c.wx + (Y0 - r.gy0);     // indexed by block-local gy
+                    float wt[EQ_TT];
+#pragma unroll
+                    for (int e = 0; e < EQ_TT; ++e) {
+                        const int t = ta + e;
+                        wt[e] = (t >= r.t0 && t <= r.t1) ? __ldg(w + 2 * c.wx + (t - r.gt0)) : 0.f;
+                    }
+                    for (int gy = ya + (lane >> 4); gy <= yb; gy += 2) {
+                        const int jy = md[gy], py = dv[gy];
+                        const float ay = r.q * __ldg(wyv + gy);
+                        for (int gx = xa + (lane & 15); gx <= xb; gx += 16) {
+                            const int jx = md[gx], px = dv[gx];
+                            const float a = ay * __ldg(wxv + gx);
+                            const int ch = jy * c.ns + jx, col = py * c.bp + px;
+#pragma unroll
+                            for (int e = 0; e < EQ_TT; ++e) atomicAdd(&tile[eq_swz(ch, col, cols, e)], a * wt[e]);
+                            if (tt == 0 || r.t0 >= ta) atomicOr(&mask[ch], 1ull << col);
+                        }
                     }
                 }
             }
+            __syncthreads();
+            // write the tile: two float4 per column segment (one 32-byte sector)
+            for (int k = tid; k < nseg * 2; k += EQ_THREADS) {
+                const int seg = k >> 1, h = k & 1;
+                const int ch = seg / cols, col = seg - ch * cols;
+                float4 v;
+                v.x = tile[eq_swz(ch, col, cols, 4 * h + 0)];
+                v.y = tile[eq_swz(ch, col, cols, 4 * h + 1)];
+                v.z = tile[eq_swz(ch, col, cols, 4 * h + 2)];
+                v.w = tile[eq_swz(ch, col, cols, 4 * h + 3)];
+                *reinterpret_cast<float4 *>(qeff + ((size_t)slot * nseg + seg) * c.bt + tt + 4 * h) = v;
+            }
+            __syncthreads();
         }
-        __syncthreads();
-        float4 *dst = reinterpret_cast<float4 *>(qeff + ((size_t)slot * nch + ch) * slab_n);
-        const float4 *src = reinterpret_cast<const float4 *>(slab);
-        for (int k = threadIdx.x; k < slab_n / 4; k += blockDim.x) dst[k] = src[k];
-        if (threadIdx.x == 0)
-            colmask[(size_t)slot * nch + ch] = ((uint64_t)s_mask[1] << 32) | s_mask[0];
+        for (int k = tid; k < nch; k += EQ_THREADS) colmask[(size_t)slot * nch + k] = mask[k];
         __syncthreads();
     }
 }
@@ -204,18 +272,21 @@ int launch_effq(tred_handle *h, int n, const tred_deposits &deps, const int32_t 
     if (n > 0) {
         const int threads = 256;
         const int64_t blocks = ((int64_t)n * 32 + threads - 1) / threads;
-        k_effq_weights<<<(unsigned)blocks, threads, 0, s>>>(n, deps, c, h->wts);
+        k_effq_weights<<<(unsigned)blocks, threads, 0, s>>>(n, deps, c, h->wts, reinterpret_cast<DepRec *>(h->recs));
     }
-    const size_t smem = sizeof(float) * (size_t)c.bp * c.bp * c.bt;
+    const int nch = c.ns * c.ns;
+    const size_t smem = sizeof(float) * (size_t)nch * c.bp * c.bp * EQ_TT + sizeof(DepRec) * EQ_CACHE +
+                        sizeof(unsigned long long) * nch + 2 * (size_t)c.bp * c.ns;
     static bool attr_set = false;
     if (!attr_set) {
-        cudaFuncSetAttribute(k_effq_blocks, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+        cudaFuncSetAttribute(k_effq_blocks, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
         attr_set = true;
     }
-    if (smem > 200 * 1024) return set_error(h, TRED_ERR_INVALID_ARG, "effq slab too large");
-    const int grid = num_sms(h) * 3;
-    k_effq_blocks<<<grid, 256, smem, s>>>(block_ids, dep_offsets, dep_index, n_blocks_dev, deps, c,
-                                          h->wts, qeff, h->colmask);
+    if (smem > 227 * 1024)
+        return set_error(h, TRED_ERR_INVALID_ARG, "effq: tile of n_sub^2 bp^2 x 8 ticks exceeds shared memory");
+    const int grid = num_sms(h);
+    k_effq_blocks<<<grid, EQ_THREADS, smem, s>>>(block_ids, dep_offsets, dep_index, n_blocks_dev, c, h->wts,
+                                                 reinterpret_cast<const DepRec *>(h->recs), qeff, h->colmask);
     h->launches += 1 + (n > 0 ? 1 : 0);
     return check_cuda(h, cudaGetLastError(), "effq launch");
 }

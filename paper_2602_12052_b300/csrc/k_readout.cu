@@ -1,8 +1,8 @@
 // a6. Trigger-reset readout (Sec. II-E, Fig. 6: LArPix trigger-reset scheme).
 //
-// One warp per pixel walks the waveform 32 ticks at a time: a warp scan gives the
-// running charge inside the step (FP32), the charge carried between steps is kept
-// in FP64.  Clock edges k >= start with C(k) >= threshold are found with a ballot;
+// One warp per pixel walks the waveform 128 ticks at a time (4 per lane): lane and
+// warp scans give the running charge inside the step (FP32), the charge carried
+// between steps is kept in FP64.  Clock edges k >= start with C(k) >= threshold are found with a ballot;
 // the charge is sampled at k + hold, the hit (pixel, k + hold, C) is emitted, and
 // integration restarts at k + hold + reset + 1.
 //
@@ -22,7 +22,8 @@ struct RoConst {
     float thr;
 };
 
-// Walk one pixel; for each hit call sink(index, tick, charge).  Returns the count.
+// Walk one pixel 128 ticks per step (4 consecutive ticks per lane); for each hit
+// call sink(index, tick, charge).  Returns the hit count.
 template <typename Sink>
 __device__ int walk_pixel(const float *__restrict__ I, const RoConst &c, int lane, Sink sink) {
     int nh = 0;
@@ -31,26 +32,45 @@ __device__ int walk_pixel(const float *__restrict__ I, const RoConst &c, int lan
     int mode = 0;             // 0: looking for a trigger; 1: waiting for the sample tick
     int ts = 0;
     while (pos < c.nt) {
-        const int t = pos + lane;
-        float v = t < c.nt ? I[t] : 0.f;
+        const int t0 = pos + 4 * lane;
+        float v[4];
+#pragma unroll
+        for (int e = 0; e < 4; ++e) v[e] = (t0 + e < c.nt) ? __ldg(I + t0 + e) : 0.f;
+        v[1] += v[0];
+        v[2] += v[1];
+        v[3] += v[2];
+        float x = v[3];
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
-            float u = __shfl_up_sync(0xffffffffu, v, o);
-            if (lane >= o) v += u;
+            const float u = __shfl_up_sync(0xffffffffu, x, o);
+            if (lane >= o) x += u;
         }
-        const double C = base + (double)v;          // C(t) for this lane's tick
+        const float excl = x - v[3];
+        double C[4];
+#pragma unroll
+        for (int e = 0; e < 4; ++e) C[e] = base + (double)(excl + v[e]);
         if (mode == 0) {
-            const bool edge = t < c.nt && (t % c.clock) == 0 && C >= (double)c.thr;
-            const unsigned bal = __ballot_sync(0xffffffffu, edge);
+            int first = 4;
+#pragma unroll
+            for (int e = 3; e >= 0; --e) {
+                const int t = t0 + e;
+                if (t < c.nt && (t % c.clock) == 0 && C[e] >= (double)c.thr) first = e;
+            }
+            const unsigned bal = __ballot_sync(0xffffffffu, first < 4);
             if (bal) {
-                const int k = pos + __ffs(bal) - 1;
+                const int src = __ffs(bal) - 1;
+                const int fe = __shfl_sync(0xffffffffu, first, src);
+                const int k = pos + 4 * src + fe;
                 ts = k + c.hold;
                 if (ts >= c.nt) break;                  // sample falls outside the window
                 mode = 1;
             }
         }
-        if (mode == 1 && ts < pos + 32) {
-            const double Cs = __shfl_sync(0xffffffffu, C, ts - pos);
+        if (mode == 1 && ts < pos + 128) {
+            const int off = ts - pos;
+            const int e = off & 3;
+            const double mine = e == 0 ? C[0] : e == 1 ? C[1] : e == 2 ? C[2] : C[3];
+            const double Cs = __shfl_sync(0xffffffffu, mine, off >> 2);
             sink(nh, ts, (float)Cs);
             ++nh;
             pos = ts + c.reset + 1;
@@ -58,8 +78,8 @@ __device__ int walk_pixel(const float *__restrict__ I, const RoConst &c, int lan
             mode = 0;
             continue;
         }
-        base = __shfl_sync(0xffffffffu, C, 31);
-        pos += 32;
+        base = __shfl_sync(0xffffffffu, C[3], 31);
+        pos += 128;
     }
     return nh;
 }

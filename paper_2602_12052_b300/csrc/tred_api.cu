@@ -77,6 +77,7 @@ static int validate(const tred_geometry *g, const tred_params *p, char *msg, siz
     auto bad = [&](const char *m) { snprintf(msg, len, "%s", m); return TRED_ERR_INVALID_ARG; };
     if (!(g->pitch_cm > 0 && g->tick_us > 0)) return bad("pitch and tick must be > 0");
     if (g->n_sub < 2 || g->n_sub % 2 || g->n_sub > 32) return bad("n_sub must be even, 2..32");
+    if ((int64_t)g->n_sub * g->n_sub * g->bp * g->bp > 6400) return bad("n_sub^2 bp^2 must be <= 6400");
     if (g->bp != 4 && g->bp != 8) return bad("bp must be 4 or 8 (padded extent 16)");
     if (g->kp < 1 || g->kp % 2 == 0 || g->bp + g->kp - 1 > LP) return bad("kp odd with bp + kp - 1 <= 16");
     if (g->lt != 512 && g->lt != 1024) return bad("lt must be 512 or 1024");
@@ -163,13 +164,14 @@ int32_t tred_create(const tred_geometry *geom, const tred_params *params, int32_
     alloc((void **)&h->rhat, sizeof(float2) * (size_t)G * NP * BINS * LP * LP, "alloc spectrum");
     alloc((void **)&h->pair_j, sizeof(int32_t) * 2 * NP, "alloc pairs");
     alloc((void **)&h->wts, sizeof(float) * (size_t)max_deposits * d.wstride, "alloc weights");
+    alloc((void **)&h->recs, 48 * (size_t)max_deposits, "alloc deposit records");
     alloc((void **)&h->blk_count, sizeof(int32_t) * (size_t)d.nblk, "alloc block counts");
     alloc((void **)&h->blk_slot, sizeof(int32_t) * (size_t)d.nblk, "alloc block slots");
     alloc((void **)&h->blk_fill, sizeof(int32_t) * (size_t)max_blocks, "alloc fill");
     h->nchunks = (d.nblk + 1023) / 1024;
     alloc((void **)&h->scan_part, sizeof(int32_t) * (size_t)(2 * h->nchunks + 8), "alloc scan");
     alloc((void **)&h->colmask, sizeof(uint64_t) * (size_t)max_blocks * ns * ns, "alloc masks");
-    h->yspec_blocks = max_blocks < 256 ? max_blocks : 256;
+    h->yspec_blocks = max_blocks < 1024 ? max_blocks : 1024;
     alloc((void **)&h->yspec, sizeof(float2) * (size_t)h->yspec_blocks * geom->lt * LP * LP, "alloc yspec");
     alloc((void **)&h->pix_flag, sizeof(int32_t) * (size_t)geom->npx_x * geom->npx_y, "alloc pixel flags");
     h->pix_chunks = ((int64_t)geom->npx_x * geom->npx_y + 1023) / 1024;
@@ -223,7 +225,7 @@ int32_t tred_create(const tred_geometry *geom, const tred_params *params, int32_
 
 int32_t tred_destroy(tred_handle *h) {
     if (!h) return TRED_ERR_INVALID_ARG;
-    void *ptrs[] = {h->rhat, h->pair_j, h->wts, h->blk_count, h->blk_slot, h->blk_fill,
+    void *ptrs[] = {h->rhat, h->pair_j, h->wts, h->recs, h->blk_count, h->blk_slot, h->blk_fill,
                     h->scan_part, h->colmask, h->yspec, h->pix_flag, h->pix_part, h->hit_cnt,
                     h->hit_tmp, h->hit_tmpc, h->status, h->tw};
     for (void *p : ptrs)

@@ -40,6 +40,7 @@ struct tred_handle {
     float2 *rhat;          // [G][npairs][64][16*16] response spectrum
     int32_t *pair_j;       // [npairs][2] impact channel indices (second = -1 without MPCP)
     float *wts;            // [max_deposits][wstride] per-deposit 1-D weights
+    void *recs;            // [max_deposits] 48-byte per-deposit records for effq
     int32_t *blk_count;    // [nblk] occupancy
     int32_t *blk_slot;     // [nblk] slot of an active block or -1
     int32_t *blk_fill;     // [max_blocks] CSR fill cursors

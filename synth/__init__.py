@@ -91,6 +91,10 @@ CONFIGS = {
         name="module1M", npx=512, nt=6400, kind="tracks", n_tracks=0,
         min_deposits=1_000_000, track_len_cm=(1.0, 100.0), z_range_cm=(0.0, 50.0),
         ne_mean=60.0, seed=1002),
+    # A 20-track module plane (a few hundred active blocks): profiling captures.
+    "module20": Config(
+        name="module20", npx=512, nt=6400, kind="tracks", n_tracks=20,
+        track_len_cm=(1.0, 100.0), z_range_cm=(0.0, 50.0), ne_mean=60.0, seed=1020),
     # Spill-scale plane: GL-3, 13 x 13 pixel x 400 tick response, 4 x 4 pixel blocks
     # (so the padded spatial extent stays 16), FFT length 1024 along time.
     "spill_plane": Config(
