@@ -134,7 +134,7 @@ int32_t tred_reset_status(tred_handle *h, void *stream);
  * access; diagnostics for benchmarks). */
 int32_t tred_launch_count(const tred_handle *h, int64_t *count);
 
-/* a0. Response spectrum (Sec. III-A-2: "with precomputed FFT(R^j)"; Eq. interlaced,
+/* a0. Response spectrum (Sec. III-A-2: the spectra of the per-impact responses are computed once; Eq. interlaced,
  * R[j, k] = i[j, -k]).  resp_dev: [kp][kp][n_sub][n_sub][nr] float32, index
  * [Ky + R][Kx + R][jy][jx][tau] = current on the central electrode from unit charge
  * at impact (jx, jy) of the pixel at offset K, tau ticks after crossing the
@@ -143,7 +143,7 @@ int32_t tred_launch_count(const tred_handle *h, int64_t *count);
  * i[-j][-K] = i[j][K] (Eq. multch); only one impact of each mirror pair is kept. */
 int32_t tred_set_response(tred_handle *h, const float *resp_dev, void *stream);
 
-/* a1. Transport (Sec. II-A; Fig. 2 steps A, D).  Inputs x, y (cm, on the plane from
+/* a1. Transport (Sec. II-A; Fig. flowchart steps A, D).  Inputs x, y (cm, on the plane from
  * its lower corner), z (drift distance to the response reference plane, cm), t0
  * (us), ne (electrons), device float32[n].  Per deposit: t_d = z / v, arrival tick
  * mu_t = (t0 + t_d) / tick, mu_x = x / h - 1/2, sigma_xy = sqrt(2 DT t_d / h^2 +
@@ -186,7 +186,7 @@ int32_t tred_convolve(tred_handle *h, const int32_t *block_ids,
                       const int32_t *n_blocks_dev, const float *qeff, float *out_blocks,
                       void *stream);
 
-/* a5. Electrode gather (Fig. 2 "bin & accumulate on unique electrodes"): every
+/* a5. Electrode gather (Fig. flowchart: binning and accumulation onto the unique electrodes): every
  * in-plane pixel of an active block's output footprint is active; its waveform
  * [0, nt) is the sum, in a fixed order, of the overlapping blocks' outputs.
  * pixel_ids[npix] ascending, waveforms [max_pixels][nt], n_pixels_dev[0] = npix. */
@@ -195,7 +195,7 @@ int32_t tred_gather_pixels(tred_handle *h, const int32_t *block_ids,
                            int32_t *pixel_ids, float *waveforms, int32_t *n_pixels_dev,
                            void *stream);
 
-/* a6. Trigger-reset readout (Sec. II-E, Fig. 6).  C = running sum of the current
+/* a6. Trigger-reset readout (Sec. II-E, Fig. readout).  C = running sum of the current
  * since the end of the last reset; at clock edges k >= start, if C(k) >= threshold
  * a hit (pixel, k + hold, C(k + hold)) is emitted when k + hold < nt and C restarts
  * at k + hold + reset + 1.  Hits sorted by (pixel, tick); n_hits_dev[0] = count. */

@@ -7,7 +7,7 @@ it, and shares no code with it; the two meet only through the seeded inputs of
 
 The arithmetic lives in ``tred_oracle.c`` (plain loops, binary64); this module is
 argument marshalling and composition of those steps in the paper's order
-(Fig. 2: transport -> raster [Q] -> bin -> convolve [I] -> electrode gather ->
+(Fig. flowchart: transport -> raster [Q] -> bin -> convolve [I] -> electrode gather ->
 readout).  Each function names the passage it follows.
 
 Parity status: every function is pinned by tests/test_oracle_*.py (see the header of
@@ -229,7 +229,7 @@ def readout(pixel_ids, wave: np.ndarray, threshold: float, clock: int, hold: int
 
 
 def simulate(cfg, dep: dict, resp: np.ndarray, effq_mode: int = 0, pixels=None):
-    """The whole path in the paper's order (Fig. 2).  With ``pixels`` given, only
+    """The whole path in the paper's order (Fig. flowchart).  With ``pixels`` given, only
     those pixels' currents are computed (sampled parity at full size)."""
     p = params(cfg, effq_mode=effq_mode)
     d = drift(p, dep)

@@ -97,7 +97,7 @@ int orc_gl_rule(int n, double *xi, double *w)
 }
 
 /* ------------------------------------------------------------------------- */
-/* Transport [A;D] (Sec. II-A; Fig. 2 steps A and D): drift time, attachment,  */
+/* Transport [A;D] (Sec. II-A; Fig. flowchart steps A and D): drift time, attachment,  */
 /* diffusion width with a floor added in quadrature, and the raster window.    */
 /* The window is a fixed sequence of correctly rounded binary64 operations.    */
 /* ------------------------------------------------------------------------- */
@@ -480,7 +480,7 @@ int orc_active_pixels(const orc_params *p, int nb, const int32_t *blocks, int kp
 }
 
 /* ------------------------------------------------------------------------- */
-/* Trigger-reset readout (Sec. II-E, Fig. 6).  Per pixel, the charge C is the   */
+/* Trigger-reset readout (Sec. II-E, Fig. readout).  Per pixel, the charge C is the   */
 /* running sum of the current since the end of the last reset.  At each clock   */
 /* edge k (k a multiple of clock) with k >= start: if C(k) >= threshold the     */
 /* channel triggers; the charge is sampled at k + hold and a hit               */

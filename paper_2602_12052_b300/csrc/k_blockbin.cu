@@ -247,3 +247,4 @@ int launch_blockbin(tred_handle *h, int n, const tred_deposits &deps, int32_t *b
 }
 
 }  // namespace tred
+

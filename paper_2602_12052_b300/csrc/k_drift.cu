@@ -1,5 +1,5 @@
 // a1. Transport: drift time, attachment, diffusion width and the raster window
-// (Sec. II-A; Fig. 2 steps A and D).  One thread per deposit.
+// (Sec. II-A; Fig. flowchart steps A and D).  One thread per deposit.
 //
 // The integer window is produced by one fixed sequence of correctly rounded
 // binary64 operations (__dadd_rn / __dmul_rn / __ddiv_rn / __dsqrt_rn: no

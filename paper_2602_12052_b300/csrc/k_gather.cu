@@ -1,4 +1,4 @@
-// a5. Electrode gather (Fig. 2: "bin & accumulate on unique electrodes").
+// a5. Electrode gather (Fig. flowchart: binning and accumulation onto the unique electrodes).
 //
 //   k_px_mark    flag every in-plane pixel of each active block's output footprint
 //                [bx bp - R, bx bp + bp + R) x (same in y)

@@ -1,4 +1,4 @@
-// a6. Trigger-reset readout (Sec. II-E, Fig. 6: LArPix trigger-reset scheme).
+// a6. Trigger-reset readout (Sec. II-E, Fig. readout: LArPix trigger-reset scheme).
 //
 // One warp per pixel walks the waveform 128 ticks at a time (4 per lane): lane and
 // warp scans give the running charge inside the step (FP32), the charge carried

@@ -1,4 +1,4 @@
-// a0. Response spectrum (Sec. III-A-2: each evaluation uses a precomputed FFT(R^j);
+// a0. Response spectrum (Sec. III-A-2: the per-impact response spectra are computed once;
 // Eq. interlaced: R[j, k] = i[j, -k]).
 //
 // For the kept impact j of each channel pair and every padded frequency

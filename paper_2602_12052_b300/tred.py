@@ -160,7 +160,7 @@ def tred_reset_status(h: Handle, stream=None):
 # ----------------------------------------------------------------- one step of the path
 class Simulator:
     """All device buffers for one configuration and the ordered ABI calls of a step:
-    drift -> blockbin -> effq -> convolve -> gather -> readout (Fig. 2)."""
+    drift -> blockbin -> effq -> convolve -> gather -> readout (Fig. flowchart)."""
 
     def __init__(self, cfg, resp: torch.Tensor, max_deposits: int, max_blocks: int,
                  max_pixels: int, max_pairs: int | None = None, max_hits: int | None = None,

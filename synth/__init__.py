@@ -8,7 +8,7 @@ effective charge, no convolution).  It only draws the inputs the method consumes
   the GEANT4/edep-sim segments of the paper's test sample (Sec. IV-A), which are
   not available here;
 * a synthetic field response i[Ky][Kx][jy][jx][tau] on a K_p x K_p pixel
-  neighbourhood x n_sub x n_sub impact positions x N_r ticks (Sec. II-B, Fig. 4:
+  neighbourhood x n_sub x n_sub impact positions x N_r ticks (Sec. II-B, Fig. frillu:
   impacts at the centres of the n_sub x n_sub sub-cells of a pixel), standing in
   for the COMSOL/pochoir response of the paper.
 
