@@ -205,6 +205,38 @@ int32_t tred_readout(tred_handle *h, const tred_readout_params *rp,
                      float *hit_charge, int32_t *n_hits_dev, int32_t max_hits,
                      void *stream);
 
+/* Block-sparse binning without any device allocation (the paper has no
+ * counterpart; this is a deployment variant of tred_blockbin).
+ *
+ * Some callers cannot call cudaMalloc once they are running: a host framework that
+ * owns all device memory through its own pool and forbids direct allocations, or a
+ * real-time acquisition loop where the implicit synchronisation of cudaMalloc would
+ * stall the stream.  They need the binning without a tred_handle (tred_create
+ * allocates).  This entry point computes exactly what tred_blockbin computes, from
+ * the same caller-owned inputs into the same caller-owned outputs, and keeps its
+ * scratch (per-block counts, block-to-slot map, CSR cursors, scan partials) in a
+ * fixed array that the library reserves on each device it is loaded on and holds
+ * until the process exits: 3 * TRED_NOALLOC_MAX_GRID_BLOCKS + 1032 int32
+ * (6.3 MB).  It calls no cudaMalloc, cudaFree or allocating routine.
+ *
+ *  - The plane's block grid (npx_x/bp * npx_y/bp * nt/bt) and max_blocks must not
+ *    exceed TRED_NOALLOC_MAX_GRID_BLOCKS; otherwise TRED_ERR_CAPACITY is returned
+ *    (with a message on stderr) and nothing is enqueued.
+ *  - status_dev: caller-owned device int32[TRED_STATUS_WORDS]; words 0 (bits), 2 and
+ *    3 are written as by tred_blockbin; the caller clears it when it wants to.
+ *  - The first call on a device looks up the array's device address on the current
+ *    device (cudaGetSymbolAddress); make that first call before any stream capture.
+ *  - Every call reuses the same array and the array keeps the last call's contents
+ *    (the counts are cleared at the start of each call).  Calls whose work overlaps
+ *    on the GPU (several streams, or several host threads) race on it and give wrong
+ *    results: serialise them on one stream.
+ *  - Arguments otherwise as tred_blockbin; geometry as in tred_create. */
+#define TRED_NOALLOC_MAX_GRID_BLOCKS (1 << 19)
+int32_t tred_blockbin_noalloc(const tred_geometry *geom, int32_t n, const tred_deposits *deps,
+                              int32_t *block_ids, int32_t *block_counts, int32_t *dep_offsets,
+                              int32_t *dep_index, int32_t max_blocks, int32_t max_pairs,
+                              int32_t *n_blocks_dev, int32_t *status_dev, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

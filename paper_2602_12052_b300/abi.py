@@ -31,7 +31,7 @@ TRED_STATUS_WORDS = 8
 EXPORTS = [
     "tred_create", "tred_destroy", "tred_last_error", "tred_sync_status", "tred_reset_status",
     "tred_set_response", "tred_drift", "tred_blockbin", "tred_effq", "tred_convolve",
-    "tred_gather_pixels", "tred_readout", "tred_launch_count",
+    "tred_gather_pixels", "tred_readout", "tred_launch_count", "tred_blockbin_noalloc",
 ]
 
 
@@ -94,6 +94,8 @@ def load(path: str | None = None) -> ctypes.CDLL:
     lib.tred_convolve.argtypes = [_P, _P, _P, _P, _P, _P]
     lib.tred_gather_pixels.argtypes = [_P, _P, _P, _P, _P, _P, _P, _P]
     lib.tred_readout.argtypes = [_P, ctypes.POINTER(ReadoutParams), _P, _P, _P, _P, _P, _P, _P, _I, _P]
+    lib.tred_blockbin_noalloc.argtypes = [ctypes.POINTER(Geometry), _I, ctypes.POINTER(Deposits), _P, _P, _P,
+                                          _P, _I, _I, _P, _P, _P]
     for name in EXPORTS:
         if name not in ("tred_last_error",):
             getattr(lib, name).restype = ctypes.c_int32

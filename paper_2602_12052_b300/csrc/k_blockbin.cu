@@ -248,3 +248,83 @@ int launch_blockbin(tred_handle *h, int n, const tred_deposits &deps, int32_t *b
 
 }  // namespace tred
 
+// ---------------------------------------------------------------------------
+// tred_blockbin_noalloc: the same binning for callers that may not allocate
+// device memory themselves (see include/tred.h).  Its scratch lives in this
+// file-scope array, allocated when the library is loaded onto a device and held
+// until the process exits.
+// ---------------------------------------------------------------------------
+namespace tred {
+
+constexpr int64_t NOALLOC_MAX_GRID_BLOCKS = TRED_NOALLOC_MAX_GRID_BLOCKS;
+constexpr int64_t NOALLOC_MAX_CHUNKS = (NOALLOC_MAX_GRID_BLOCKS + 1023) / 1024;
+// count[grid] | slot_of[grid] | fill[grid] | scan partials[2 chunks + 8]
+constexpr int64_t NOALLOC_WORDS = 3 * NOALLOC_MAX_GRID_BLOCKS + 2 * NOALLOC_MAX_CHUNKS + 8;
+
+static __device__ __align__(256) int32_t g_noalloc_scratch[NOALLOC_WORDS];
+
+// Device address of g_noalloc_scratch per device, looked up on the first call made
+// with that device current.
+static int32_t *g_noalloc_ptr[64];
+
+static int noalloc_scratch(int32_t **out) {
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return TRED_ERR_CUDA;
+    if (!g_noalloc_ptr[dev]) {
+        void *p = nullptr;
+        const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e != cudaSuccess || !p) {
+            fprintf(stderr, "tred_blockbin_noalloc: cudaGetSymbolAddress failed: %s\n", cudaGetErrorString(e));
+            return TRED_ERR_CUDA;
+        }
+        g_noalloc_ptr[dev] = static_cast<int32_t *>(p);
+    }
+    *out = g_noalloc_ptr[dev];
+    return TRED_OK;
+}
+
+}  // namespace tred
+
+extern "C" int32_t tred_blockbin_noalloc(const tred_geometry *geom, int32_t n, const tred_deposits *deps,
+                                         int32_t *block_ids, int32_t *block_counts, int32_t *dep_offsets,
+                                         int32_t *dep_index, int32_t max_blocks, int32_t max_pairs,
+                                         int32_t *n_blocks_dev, int32_t *status_dev, void *stream) {
+    using namespace tred;
+    if (!geom || n < 0 || !block_ids || !block_counts || !dep_offsets || !n_blocks_dev || !status_dev ||
+        max_blocks < 1 || max_pairs < 0 || (max_pairs > 0 && !dep_index) || (n > 0 && !deps))
+        return TRED_ERR_INVALID_ARG;
+    const tred_geometry &g = *geom;
+    if (g.n_sub < 1 || g.bp < 1 || g.bt < 1 || g.npx_x < g.bp || g.npx_y < g.bp || g.npx_x % g.bp ||
+        g.npx_y % g.bp || g.nt < g.bt || g.nt % g.bt)
+        return TRED_ERR_INVALID_ARG;
+    const int64_t nbx = g.npx_x / g.bp, nby = g.npx_y / g.bp, nbt = g.nt / g.bt;
+    const int64_t nblk = nbx * nby * nbt;
+    if (nblk > NOALLOC_MAX_GRID_BLOCKS || max_blocks > NOALLOC_MAX_GRID_BLOCKS) {
+        fprintf(stderr,
+                "tred_blockbin_noalloc: the plane has %lld blocks (max_blocks %d); this entry point's "
+                "static scratch holds at most %lld\n",
+                (long long)nblk, max_blocks, (long long)NOALLOC_MAX_GRID_BLOCKS);
+        return TRED_ERR_CAPACITY;
+    }
+    int32_t *scratch = nullptr;
+    int rc = noalloc_scratch(&scratch);
+    if (rc != TRED_OK) return rc;
+    int32_t *count = scratch;
+    int32_t *slot_of = count + NOALLOC_MAX_GRID_BLOCKS;
+    int32_t *fill = slot_of + NOALLOC_MAX_GRID_BLOCKS;
+    int32_t *part = fill + NOALLOC_MAX_GRID_BLOCKS;
+    const int64_t nchunks = (nblk + 1023) / 1024;
+    cudaStream_t s = (cudaStream_t)stream;
+    BinGeom bg{g.n_sub, g.bp, g.bt, g.npx_x * g.n_sub, g.npx_y * g.n_sub, g.nt, (int)nbx, (int)nby, (int)nbt};
+    if (cudaMemsetAsync(count, 0, sizeof(int32_t) * nblk, s) != cudaSuccess) return TRED_ERR_CUDA;
+    if (n > 0) k_bb_count<<<(n + 255) / 256, 256, 0, s>>>(n, *deps, bg, count);
+    k_bb_chunk<<<(unsigned)nchunks, 1024, 0, s>>>(nblk, count, part, nchunks);
+    k_bb_top<<<1, 1024, 0, s>>>(nchunks, part, max_blocks, max_pairs, n_blocks_dev, status_dev);
+    k_bb_emit<<<(unsigned)nchunks, 1024, 0, s>>>(nblk, count, part, nchunks, max_blocks, max_pairs, slot_of,
+                                                 block_ids, block_counts, dep_offsets, fill);
+    k_bb_offsets0<<<1, 1, 0, s>>>(dep_offsets, n_blocks_dev);
+    if (n > 0)
+        k_bb_fill<<<(n + 255) / 256, 256, 0, s>>>(n, *deps, bg, slot_of, dep_offsets, fill, dep_index,
+                                                  max_pairs);
+    return cudaGetLastError() == cudaSuccess ? TRED_OK : TRED_ERR_CUDA;
+}
