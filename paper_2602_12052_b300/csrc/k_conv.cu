@@ -33,14 +33,15 @@ struct ConvConst {
 
 constexpr int SPEC_THREADS = 512;
 constexpr int SPEC_WARPS = SPEC_THREADS / 32;
-constexpr int ACC_ROW = 17;                 // padded row (float2) of the accumulator
-constexpr int ACC_BIN = LP * ACC_ROW;       // 272 float2 per bin
+constexpr int ACC_ROW = 18;                 // padded kx row (float2) of the accumulator: 16 ky + 2
+constexpr int ACC_BIN = LP * ACC_ROW;       // 288 float2 per bin; layout [k2][kx][ky]
 constexpr int ZT_ROW = 9;                   // padded px row of the bin-major transpose
 constexpr int ZT_BIN = 8 * ZT_ROW + 1;      // [py][px] for py, px < 8, odd stride
-// Bin order inside the transpose buffer: stage A lanes store bins 2 b + a with b a
-// bit-reversed lane index, so even and odd bins go to separate halves and the 32
-// lanes of one store hit 16 distinct 8-byte bank pairs.
-__device__ __forceinline__ int zt_slot(int k2) { return ((k2 & 1) << 5) | (k2 >> 1); }
+// Bin order inside the transpose buffer.  Stage A lane l stores bins k2 = a + 2 b
+// with b = bitrev5(l): the 16 lanes of a half warp hold the even b, the other 16
+// the odd ones.  k2 = 4 c + 2 d + a goes to slot 32 a + 16 d + c so that each half
+// warp's 16 stores land on 16 distinct 8-byte bank pairs (odd bin stride).
+__device__ __forceinline__ int zt_slot(int k2) { return ((k2 & 1) << 5) | (((k2 >> 1) & 1) << 4) | (k2 >> 2); }
 constexpr int TB_ROW = 9;                   // per-warp transpose rows [kx][py]
 constexpr int TB_BIN = LP * TB_ROW;
 
@@ -55,7 +56,7 @@ __global__ void __launch_bounds__(SPEC_THREADS, 1)
                 float2 *__restrict__ yspec, int slot_base, int slot_count) {
     constexpr int LT = 64 * G;
     extern __shared__ float2 smem[];
-    float2 *acc = smem;                               // [64][16][17]
+    float2 *acc = smem;                               // [64][16 kx][18]
     float2 *zt = acc + BINS * ACC_BIN;                // [64][8][9]
     float2 *tbuf = zt + BINS * ZT_BIN;                // [warps][2][16][9]
     float2 *w32 = tbuf + SPEC_WARPS * 2 * TB_BIN;     // W_32
@@ -134,7 +135,8 @@ __global__ void __launch_bounds__(SPEC_THREADS, 1)
             for (int it = 0; it < BINS / (2 * SPEC_WARPS); ++it) {
                 const int b = lane >> 4;
                 const int k2 = (BINS / SPEC_WARPS) * warp + 2 * it + b;
-                // prefetch this lane's Rhat column (kx = lane & 15) for the y stage
+                // prefetch this lane's Rhat column (kx = lane & 15) for the y stage; the
+                // 16 lanes of a bin read one contiguous 128-byte ky row per load
                 const int kx = lane & 15;
                 float2 rr[LP];
                 const float2 *rsrc = rp + (size_t)k2 * (LP * LP) + kx;
@@ -147,11 +149,11 @@ __global__ void __launch_bounds__(SPEC_THREADS, 1)
                     float2 v[8];
 #pragma unroll
                     for (int x = 0; x < 8; ++x) {
-                        float2 z = zrow[x];
-                        if (h) z = cmul(z, w16[x]);
-                        v[x] = z;
+                        const float2 z = zrow[x];
+                        const float wr = h ? w32c(2 * x) : 1.f, wi = h ? w32s(2 * x) : 0.f;
+                        v[x] = make_float2(z.x * wr - z.y * wi, z.x * wi + z.y * wr);
                     }
-                    fft_reg_dif<8, false>(v, w8);
+                    fft_reg_dif_c<8, false>(v);
                     float2 *dst = tb + b * TB_BIN + py;
 #pragma unroll
                     for (int k = 0; k < 8; ++k) dst[(2 * bitrev<8>(k) + h) * TB_ROW] = v[k];
@@ -164,18 +166,19 @@ __global__ void __launch_bounds__(SPEC_THREADS, 1)
 #pragma unroll
                     for (int y = 0; y < 8; ++y) {
                         e[y] = src[y];
-                        o[y] = cmul(e[y], w16[y]);
+                        const float wr = w32c(2 * y), wi = w32s(2 * y);     // W_16^y
+                        o[y] = make_float2(e[y].x * wr - e[y].y * wi, e[y].x * wi + e[y].y * wr);
                     }
-                    fft_reg_dif<8, false>(e, w8);
-                    fft_reg_dif<8, false>(o, w8);
-                    float2 *ab = acc + k2 * ACC_BIN + kx;
+                    fft_reg_dif_c<8, false>(e);
+                    fft_reg_dif_c<8, false>(o);
+                    float4 *ab = reinterpret_cast<float4 *>(acc + k2 * ACC_BIN + kx * ACC_ROW);
 #pragma unroll
                     for (int k = 0; k < 8; ++k) {
-                        const int ky = 2 * bitrev<8>(k);
-                        float2 a0 = ab[ky * ACC_ROW];
-                        float2 a1 = ab[(ky + 1) * ACC_ROW];
-                        ab[ky * ACC_ROW] = cfma(e[k], rr[ky], a0);
-                        ab[(ky + 1) * ACC_ROW] = cfma(o[k], rr[ky + 1], a1);
+                        const int q = bitrev<8>(k);            // ky pair (2q, 2q + 1)
+                        const float4 a = ab[q];
+                        const float2 a0 = cfma(e[k], rr[2 * q], make_float2(a.x, a.y));
+                        const float2 a1 = cfma(o[k], rr[2 * q + 1], make_float2(a.z, a.w));
+                        ab[q] = make_float4(a0.x, a0.y, a1.x, a1.y);
                     }
                 }
                 __syncwarp();
@@ -190,17 +193,17 @@ __global__ void __launch_bounds__(SPEC_THREADS, 1)
             float2 *ab = acc + k2 * ACC_BIN;
             float2 v[LP];
 #pragma unroll
-            for (int x = 0; x < LP; ++x) v[x] = ab[r * ACC_ROW + x];        // row ky = r
-            fft_reg_dif<LP, true>(v, w16);
+            for (int y = 0; y < LP; ++y) v[y] = ab[r * ACC_ROW + y];        // kx = r: over ky
+            fft_reg_dif_c<LP, true>(v);
 #pragma unroll
-            for (int k = 0; k < LP; ++k) ab[r * ACC_ROW + bitrev<LP>(k)] = v[k];
+            for (int k = 0; k < LP; ++k) ab[r * ACC_ROW + bitrev<LP>(k)] = v[k];   // -> [kx][cy]
             __syncwarp();
 #pragma unroll
-            for (int y = 0; y < LP; ++y) v[y] = ab[y * ACC_ROW + r];        // column cx = r
-            fft_reg_dif<LP, true>(v, w16);
+            for (int x = 0; x < LP; ++x) v[x] = ab[x * ACC_ROW + r];        // cy = r: over kx
+            fft_reg_dif_c<LP, true>(v);
             __syncwarp();
 #pragma unroll
-            for (int k = 0; k < LP; ++k) ab[bitrev<LP>(k) * ACC_ROW + r] = v[k];
+            for (int k = 0; k < LP; ++k) ab[bitrev<LP>(k) * ACC_ROW + r] = v[k];   // -> [cx][cy]
             __syncwarp();
         }
         __syncthreads();
@@ -208,7 +211,7 @@ __global__ void __launch_bounds__(SPEC_THREADS, 1)
         for (int k = tid; k < BINS * LP * LP; k += SPEC_THREADS) {
             const int k2 = k >> 8, cidx = k & 255;
             const int cy = cidx >> 4, cx = cidx & 15;
-            yspec[((size_t)sl * LT + (k1 + G * k2)) * (LP * LP) + cidx] = acc[k2 * ACC_BIN + cy * ACC_ROW + cx];
+            yspec[((size_t)sl * LT + (k1 + G * k2)) * (LP * LP) + cidx] = acc[k2 * ACC_BIN + cx * ACC_ROW + cy];
         }
         __syncthreads();
     }
@@ -269,7 +272,7 @@ __global__ void __launch_bounds__(256) k_conv_itime(const int32_t *__restrict__ 
                 float2 v[NPL];
 #pragma unroll
                 for (int m = 0; m < NPL; ++m) v[m] = src[lane + 32 * m];
-                fft_reg_dif<NPL, true>(v, wn);        // v[k] = u[bitrev(k)]
+                fft_reg_dif_c<NPL, true>(v);          // v[k] = u[bitrev(k)]
 #pragma unroll
                 for (int k = 0; k < NPL; ++k) {
                     const int aa = bitrev<NPL>(k);

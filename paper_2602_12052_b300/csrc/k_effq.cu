@@ -33,6 +33,7 @@ static_assert(sizeof(DepRec) == 48, "record size is part of the scratch layout")
 
 struct EffqConst {
     int ns, bp, bt, ngx, ngy, nt, nbx, nbt, wx, wt, wstride, gl, mode;
+    int cols_log2;                 // log2(bp * bp)
     float xi[MAX_GL], wl[MAX_GL];
 };
 
@@ -140,22 +141,18 @@ __global__ void __launch_bounds__(256) k_effq_weights(int n, tred_deposits d, Ef
     }
 }
 
-// Persistent CTAs over active blocks, time-tiled.  One tile holds every impact
-// channel and pixel column of the block for EQ_TT consecutive ticks
-// (n_sub^2 x bp^2 x 8 floats, 200 KB at 10 x 10 x 8 x 8), so each deposit is
-// visited once per tile it overlaps and all its sub-cells are handled in that
-// visit: lanes over the deposit's sub-cells (two rows of 16), 8 tick updates per
-// lane from the tile's time weights held in registers.  The tile is written with
-// full 32-byte sectors per column.  Inside a column segment the 8 ticks are rotated
-// by (channel + column / 4) so that lanes updating neighbouring impact channels
-// (segment stride bp^2) land in different banks.
-constexpr int EQ_THREADS = 512;
+// Persistent CTAs over active blocks, time-tiled.  One tile holds the block's whole
+// sub-cell plane for EQ_TT consecutive ticks, indexed by sub-cell ([t][gy][gx],
+// (bp n_sub)^2 x 8 floats = 200 KB at 80 x 80 x 8), so each deposit is visited once
+// per tile it overlaps and all its sub-cells are handled in that visit: lanes over
+// two rows of 16 sub-cells (banks gx and gx + 16: no conflicts), 8 tick updates
+// per lane from the tile's time weights held in registers.  The write pass gathers
+// each (channel, column) segment's 8 ticks into one 32-byte sector of the
+// [jy][jx][py][px][t] layout and zeroes the tile for the next tick range; the
+// non-empty column masks come from the data written.
+constexpr int EQ_THREADS = 1024;
 constexpr int EQ_TT = 8;
 constexpr int EQ_CACHE = 256;      // deposit records staged per pass
-
-__device__ __forceinline__ int eq_swz(int ch, int col, int cols, int t) {
-    return (ch * cols + col) * EQ_TT + ((t + ch + (col >> 2)) & (EQ_TT - 1));
-}
 
 __global__ void __launch_bounds__(EQ_THREADS, 1) k_effq_blocks(const int32_t *__restrict__ block_ids,
                                                             const int32_t *__restrict__ dep_offsets,
@@ -168,17 +165,15 @@ __global__ void __launch_bounds__(EQ_THREADS, 1) k_effq_blocks(const int32_t *__
     extern __shared__ float smem_e[];
     const int nch = c.ns * c.ns;
     const int cols = c.bp * c.bp;
-    const int nseg = nch * cols;
     const int side = c.bp * c.ns;
-    float *tile = smem_e;                                                     // [nseg][8]
-    DepRec *rc = reinterpret_cast<DepRec *>(tile + nseg * EQ_TT);             // [EQ_CACHE]
+    const int plane = side * side;                                            // == nch * cols
+    float *tile = smem_e;                                                     // [8][side][side]
+    DepRec *rc = reinterpret_cast<DepRec *>(tile + plane * EQ_TT);            // [EQ_CACHE]
     unsigned long long *mask = reinterpret_cast<unsigned long long *>(rc + EQ_CACHE);  // [nch]
-    unsigned char *dv = reinterpret_cast<unsigned char *>(mask + nch);        // [side] sub-cell / ns
-    unsigned char *md = dv + side;                                            // [side] sub-cell % ns
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31, nwarps = EQ_THREADS / 32;
-    for (int k = tid; k < side; k += EQ_THREADS) {
-        dv[k] = (unsigned char)(k / c.ns);
-        md[k] = (unsigned char)(k % c.ns);
+    {
+        const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
+        for (int k = tid; k < plane * (EQ_TT / 4); k += EQ_THREADS) reinterpret_cast<float4 *>(tile)[k] = z4;
     }
     const int nb = n_blocks_dev[0];
     for (int slot = blockIdx.x; slot < nb; slot += gridDim.x) {
@@ -188,9 +183,8 @@ __global__ void __launch_bounds__(EQ_THREADS, 1) k_effq_blocks(const int32_t *__
         const int beg = dep_offsets[slot], end = dep_offsets[slot + 1];
         const int passes = max(1, (end - beg + EQ_CACHE - 1) / EQ_CACHE);
         for (int k = tid; k < nch; k += EQ_THREADS) mask[k] = 0ull;
+        uint32_t nz = 0u;                       // per-lane non-empty flags of its (col, ch) segments
         for (int tt = 0; tt < c.bt; tt += EQ_TT) {
-            const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
-            for (int k = tid; k < nseg * (EQ_TT / 4); k += EQ_THREADS) reinterpret_cast<float4 *>(tile)[k] = z4;
             const int ta = T0 + tt, tb = ta + EQ_TT - 1;   // absolute ticks of the tile
             for (int pass = 0; pass < passes; ++pass) {
                 const int pb = beg + pass * EQ_CACHE;
@@ -201,8 +195,9 @@ __global__ void __launch_bounds__(EQ_THREADS, 1) k_effq_blocks(const int32_t *__
                 }
                 __syncthreads();
                 for (int k = warp; k < pn; k += nwarps) {
+                    const int rt0 = rc[k].t0, rt1 = rc[k].t1;
+                    if (rt1 < ta || rt0 > tb) continue;
                     const DepRec r = rc[k];
-                    if (r.t1 < ta || r.t0 > tb) continue;
                     const int xa = max(r.x0, X0) - X0, xb = min(r.x1, X0 + side - 1) - X0;
                     const int ya = max(r.y0, Y0) - Y0, yb = min(r.y1, Y0 + side - 1) - Y0;
                     if (xa > xb || ya > yb) continue;
@@ -216,33 +211,47 @@ __global__ void __launch_bounds__(EQ_THREADS, 1) k_effq_blocks(const int32_t *__
                         wt[e] = (t >= r.t0 && t <= r.t1) ? __ldg(w + 2 * c.wx + (t - r.gt0)) : 0.f;
                     }
                     for (int gy = ya + (lane >> 4); gy <= yb; gy += 2) {
-                        const int jy = md[gy], py = dv[gy];
                         const float ay = r.q * __ldg(wyv + gy);
                         for (int gx = xa + (lane & 15); gx <= xb; gx += 16) {
-                            const int jx = md[gx], px = dv[gx];
                             const float a = ay * __ldg(wxv + gx);
-                            const int ch = jy * c.ns + jx, col = py * c.bp + px;
+                            float *cell = tile + gy * side + gx;
 #pragma unroll
-                            for (int e = 0; e < EQ_TT; ++e) atomicAdd(&tile[eq_swz(ch, col, cols, e)], a * wt[e]);
-                            if (tt == 0 || r.t0 >= ta) atomicOr(&mask[ch], 1ull << col);
+                            for (int e = 0; e < EQ_TT; ++e) atomicAdd(cell + e * plane, a * wt[e]);
                         }
                     }
                 }
             }
             __syncthreads();
-            // write the tile: two float4 per column segment (one 32-byte sector)
-            for (int k = tid; k < nseg * 2; k += EQ_THREADS) {
-                const int seg = k >> 1, h = k & 1;
-                const int ch = seg / cols, col = seg - ch * cols;
-                float4 v;
-                v.x = tile[eq_swz(ch, col, cols, 4 * h + 0)];
-                v.y = tile[eq_swz(ch, col, cols, 4 * h + 1)];
-                v.z = tile[eq_swz(ch, col, cols, 4 * h + 2)];
-                v.w = tile[eq_swz(ch, col, cols, 4 * h + 3)];
-                *reinterpret_cast<float4 *>(qeff + ((size_t)slot * nseg + seg) * c.bt + tt + 4 * h) = v;
+            // write the tile (one 32-byte sector per (channel, column) segment), zero it
+            int bit = 0;
+            for (int col = warp; col < cols; col += nwarps) {
+                const int py = col / c.bp, px = col - py * c.bp;
+                for (int ch = lane; ch < nch; ch += 32, ++bit) {
+                    const int jy = ch / c.ns, jx = ch - jy * c.ns;
+                    float *cell = tile + (py * c.ns + jy) * side + px * c.ns + jx;
+                    float v[EQ_TT];
+                    bool any = false;
+#pragma unroll
+                    for (int e = 0; e < EQ_TT; ++e) {
+                        v[e] = cell[e * plane];
+                        cell[e * plane] = 0.f;
+                        any |= v[e] != 0.f;
+                    }
+                    if (any) nz |= 1u << bit;
+                    float4 *dst = reinterpret_cast<float4 *>(qeff + (((size_t)slot * nch + ch) * cols + col) * c.bt + tt);
+                    dst[0] = make_float4(v[0], v[1], v[2], v[3]);
+                    dst[1] = make_float4(v[4], v[5], v[6], v[7]);
+                }
             }
             __syncthreads();
         }
+        {
+            int bit = 0;
+            for (int col = warp; col < cols; col += nwarps)
+                for (int ch = lane; ch < nch; ch += 32, ++bit)
+                    if ((nz >> bit) & 1u) atomicOr(&mask[ch], 1ull << col);
+        }
+        __syncthreads();
         for (int k = tid; k < nch; k += EQ_THREADS) colmask[(size_t)slot * nch + k] = mask[k];
         __syncthreads();
     }
@@ -265,6 +274,7 @@ int launch_effq(tred_handle *h, int n, const tred_deposits &deps, const int32_t 
     c.wstride = h->d.wstride;
     c.gl = h->p.gl_order;
     c.mode = h->p.effq_mode;
+    c.cols_log2 = h->g.bp == 8 ? 6 : 4;
     for (int l = 0; l < MAX_GL; ++l) {
         c.xi[l] = l < c.gl ? h->gl_xi[l] : 0.f;
         c.wl[l] = l < c.gl ? h->gl_wi[l] : 0.f;
@@ -276,7 +286,7 @@ int launch_effq(tred_handle *h, int n, const tred_deposits &deps, const int32_t 
     }
     const int nch = c.ns * c.ns;
     const size_t smem = sizeof(float) * (size_t)nch * c.bp * c.bp * EQ_TT + sizeof(DepRec) * EQ_CACHE +
-                        sizeof(unsigned long long) * nch + 2 * (size_t)c.bp * c.ns;
+                        sizeof(unsigned long long) * nch;
     static bool attr_set = false;
     if (!attr_set) {
         cudaFuncSetAttribute(k_effq_blocks, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);

@@ -152,6 +152,45 @@ __device__ __forceinline__ void fft_reg_dif(float2 (&v)[N], const float2 *__rest
     }
 }
 
+// exp(-2 pi i m / 32) as compile-time constants (cos and -sin rounded to binary32),
+// used by the in-register FFTs of size <= 32 so that twiddles fold into the code.
+__host__ __device__ constexpr float w32c(int m) {
+    constexpr float c[32] = {1.000000000e+00f, 9.807852804e-01f, 9.238795325e-01f, 8.314696123e-01f, 7.071067812e-01f, 5.555702330e-01f, 3.826834324e-01f, 1.950903220e-01f, 0.0f, -1.950903220e-01f, -3.826834324e-01f, -5.555702330e-01f, -7.071067812e-01f, -8.314696123e-01f, -9.238795325e-01f, -9.807852804e-01f, -1.000000000e+00f, -9.807852804e-01f, -9.238795325e-01f, -8.314696123e-01f, -7.071067812e-01f, -5.555702330e-01f, -3.826834324e-01f, -1.950903220e-01f, 0.0f, 1.950903220e-01f, 3.826834324e-01f, 5.555702330e-01f, 7.071067812e-01f, 8.314696123e-01f, 9.238795325e-01f, 9.807852804e-01f};
+    return c[m & 31];
+}
+__host__ __device__ constexpr float w32s(int m) {
+    constexpr float s[32] = {0.0f, -1.950903220e-01f, -3.826834324e-01f, -5.555702330e-01f, -7.071067812e-01f, -8.314696123e-01f, -9.238795325e-01f, -9.807852804e-01f, -1.000000000e+00f, -9.807852804e-01f, -9.238795325e-01f, -8.314696123e-01f, -7.071067812e-01f, -5.555702330e-01f, -3.826834324e-01f, -1.950903220e-01f, 0.0f, 1.950903220e-01f, 3.826834324e-01f, 5.555702330e-01f, 7.071067812e-01f, 8.314696123e-01f, 9.238795325e-01f, 9.807852804e-01f, 1.000000000e+00f, 9.807852804e-01f, 9.238795325e-01f, 8.314696123e-01f, 7.071067812e-01f, 5.555702330e-01f, 3.826834324e-01f, 1.950903220e-01f};
+    return s[m & 31];
+}
+
+// Radix-2 DIF FFT in registers, N <= 32, twiddles as constants.  Output v[k] = X[bitrev(k)].
+template <int N, bool INV>
+__device__ __forceinline__ void fft_reg_dif_c(float2 (&v)[N]) {
+    static_assert(N >= 2 && N <= 32 && (N & (N - 1)) == 0, "N must be a power of two <= 32");
+#pragma unroll
+    for (int span = N / 2; span >= 1; span >>= 1) {
+#pragma unroll
+        for (int start = 0; start < N; start += 2 * span) {
+#pragma unroll
+            for (int i = 0; i < span; ++i) {
+                float2 a = v[start + i], b = v[start + i + span];
+                v[start + i] = cadd(a, b);
+                float2 d = csub(a, b);
+                const int m = i * (N / (2 * span));        // exponent on W_N
+                const int m32 = m * (32 / N);               // same angle on W_32
+                if (m == 0) {
+                    v[start + i + span] = d;
+                } else if (4 * m == N) {
+                    v[start + i + span] = mul_mi<INV>(d);
+                } else {
+                    const float wr = w32c(m32), wi = INV ? -w32s(m32) : w32s(m32);
+                    v[start + i + span] = make_float2(d.x * wr - d.y * wi, d.x * wi + d.y * wr);
+                }
+            }
+        }
+    }
+}
+
 template <int N>
 __host__ __device__ constexpr int bitrev(int x) {
     int r = 0;
