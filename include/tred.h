@@ -205,6 +205,45 @@ int32_t tred_readout(tred_handle *h, const tred_readout_params *rp,
                      float *hit_charge, int32_t *n_hits_dev, int32_t max_hits,
                      void *stream);
 
+/* ---- Differentiable simulation (Sec. V-C).  Loss L = 1/2 sum (I - I*)^2 over
+ * pixels and ticks; gradients through the whole path with the raster windows held
+ * fixed (they are piecewise constant) and the quadrature recomputed, not stored.
+ * Gauss-Legendre mode only. */
+
+/* Replace the transport constants (v, DL, DT, lifetime, sigma floors, nsigma,
+ * max_drift) of a handle, e.g. between gradient steps.  The method switches must
+ * not change; TRED_ERR_CAPACITY if the new diffusion needs wider windows than
+ * tred_create provisioned (2x the diffusion constants given there). */
+int32_t tred_set_transport(tred_handle *h, const tred_params *params);
+
+/* resid = I - I* on the current pixel list (target rows matched by pixel id in the
+ * ascending target_ids[n_target]; missing rows count as zero) and
+ * loss_dev[0] = 1/2 sum over the union of both lists of (I - I*)^2 (FP64).
+ * resid: [max_pixels][nt]. */
+int32_t tred_residual(tred_handle *h, const int32_t *pixel_ids, const int32_t *n_pixels_dev,
+                      const float *waveforms, const int32_t *target_ids, int32_t n_target,
+                      const float *target_waves, float *resid, double *loss_dev, void *stream);
+
+/* Adjoint of drift -> effq -> convolve -> gather for dL/dI = resid on the current
+ * pixel list.  dL/dQeff[j, P', t'] = sum_K sum_tau r[P' - K, t' + tau] i[j, K, tau]
+ * (the transpose of Eq. interlaced) is formed per active block by FFT with the
+ * conjugate response spectrum (MPCP read backwards) into dqeff (the layout of
+ * tred_effq's qeff; the forward's qeff buffer may be reused), then the chain rule
+ * through the separable quadrature gives grad7[d][7] = dL/d(q, mu_x, mu_y, mu_t,
+ * sigma_x, sigma_y, sigma_t) in grid units.  The first call allocates the adjoint
+ * scratch (3 floats per weight of each deposit, a pixel map and 32 blocks of
+ * spectra). */
+int32_t tred_adjoint(tred_handle *h, int32_t n, const tred_deposits *deps, const int32_t *block_ids,
+                     const int32_t *dep_offsets, const int32_t *dep_index, const int32_t *n_blocks_dev,
+                     const int32_t *pixel_ids, const int32_t *n_pixels_dev, const float *resid,
+                     float *dqeff, float *grad7, void *stream);
+
+/* Chain rule through the transport step (Sec. II-A): grad_inputs[d][4] =
+ * dL/d(x, y, t0, ne), grad_global[3] = dL/d(DL, DT, lifetime) (FP64).  z: the
+ * drift distances given to tred_drift. */
+int32_t tred_param_grads(tred_handle *h, int32_t n, const float *z, const tred_deposits *deps,
+                         const float *grad7, float *grad_inputs, double *grad_global, void *stream);
+
 /* Block-sparse binning without any device allocation (the paper has no
  * counterpart; this is a deployment variant of tred_blockbin).
  *

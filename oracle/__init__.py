@@ -92,6 +92,11 @@ def _setup(L):
                               _P, _P, _P, ctypes.c_long, _P]
     L.orc_readout.restype = ctypes.c_long
     L.orc_num_threads.restype = ctypes.c_int
+    L.orc_weights_gl_grad.argtypes = [ctypes.c_int, _P, _P, ctypes.c_double, ctypes.c_double,
+                                      ctypes.c_int, ctypes.c_int, _P, _P, _P]
+    L.orc_adjoint.argtypes = [_P, ctypes.c_int, _P, _P, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                              _P, _P, _P]
+    L.orc_param_grads.argtypes = [_P, ctypes.c_int, _P, _P, _P, _P, _P, _P]
 
 
 def _ptr(a: np.ndarray):
@@ -238,3 +243,45 @@ def simulate(cfg, dep: dict, resp: np.ndarray, effq_mode: int = 0, pixels=None):
     wave = pixel_currents(p, d, resp, pix)
     return {"params": p, "deps": d, "block_ids": ids, "block_counts": counts,
             "pixel_ids": pix, "waveforms": wave}
+
+
+# ----------------------------------------------------------------- differentiation
+def weights_gl_grad(nl: int, mu: float, sig: float, lo: int, hi: int):
+    """GL weights and their derivatives in mu and sigma (window held fixed)."""
+    xi, w = gl_rule(nl)
+    e, dm, ds = (np.zeros(hi - lo + 3) for _ in range(3))
+    lib().orc_weights_gl_grad(nl, _ptr(xi), _ptr(w), mu, sig, lo, hi, _ptr(e), _ptr(dm), _ptr(ds))
+    return e, dm, ds
+
+
+def adjoint(p: Params, d: np.ndarray, resp: np.ndarray, pixel_ids, resid: np.ndarray) -> np.ndarray:
+    """dL/d(q, mu_x, mu_y, mu_t, sig_x, sig_y, sig_t) per deposit for L = 1/2 sum r^2,
+    given r = dL/dI on the listed pixels (Sec. V-C; windows held fixed)."""
+    resp = np.ascontiguousarray(resp, dtype=np.float32)
+    kp, nr = resp.shape[0], resp.shape[-1]
+    pixel_ids = np.ascontiguousarray(pixel_ids, dtype=np.int32)
+    resid = np.ascontiguousarray(resid, dtype=np.float64)
+    g = np.zeros((len(d), 7))
+    lib().orc_adjoint(ctypes.byref(p), len(d), _ptr(d), _ptr(resp), kp, nr, len(pixel_ids),
+                      _ptr(pixel_ids), _ptr(resid), _ptr(g))
+    return g
+
+
+def param_grads(p: Params, dep: dict, d: np.ndarray, grad7: np.ndarray):
+    """Per deposit dL/d(x, y, t0, ne) and global dL/d(DL, DT, tau) from grad7."""
+    z = np.ascontiguousarray(dep["z"], dtype=np.float32)
+    ne = np.ascontiguousarray(dep["ne"], dtype=np.float32)
+    out = np.zeros((len(d), 4))
+    glob = np.zeros(3)
+    lib().orc_param_grads(ctypes.byref(p), len(d), _ptr(z), _ptr(ne), _ptr(d),
+                          _ptr(np.ascontiguousarray(grad7)), _ptr(out), _ptr(glob))
+    return out, glob
+
+
+def currents_frozen(p: Params, dep: dict, frozen: np.ndarray, resp, pixel_ids):
+    """Pixel currents with the windows of `frozen` (the unperturbed drift) kept: the
+    loss is then smooth in the inputs, as the adjoint assumes."""
+    d = drift(p, dep)
+    d["lo"] = frozen["lo"]
+    d["hi"] = frozen["hi"]
+    return pixel_currents(p, d, resp, pixel_ids)

@@ -537,3 +537,215 @@ int orc_num_threads(void)
     return 1;
 #endif
 }
+
+/* ========================================================================= */
+/* Differentiable simulation (Sec. V-C): gradient of L = 1/2 sum (I - I*)^2.    */
+/* ========================================================================= */
+
+/* Derivatives of the GL weights with respect to the mean and the width, with the
+ * window [lo, hi] held fixed (it is piecewise constant in mu and sigma):
+ *   d phi/d mu = phi (x - mu) / sig^2,  d phi/d sig = phi ((x - mu)^2 / sig^3 - 1/sig). */
+void orc_weights_gl_grad(int nl, const double *xi, const double *wl, double mu, double sig,
+                         int lo, int hi, double *e, double *de_dmu, double *de_dsig)
+{
+    int n = hi - lo + 3;
+    for (int k = 0; k < n; ++k) e[k] = de_dmu[k] = de_dsig[k] = 0.0;
+    for (int C = lo; C <= hi; ++C) {
+        for (int l = 0; l < nl; ++l) {
+            double s = 0.5 * xi[l];
+            double xx = (double)C + s;
+            double ph = normal_pdf(xx, mu, sig);
+            double dm = ph * (xx - mu) / (sig * sig);
+            double ds = ph * ((xx - mu) * (xx - mu) / (sig * sig * sig) - 1.0 / sig);
+            double wv = 0.5 * wl[l];
+            int k = C - (lo - 1);
+            int k2 = s > 0.0 ? k + 1 : k - 1;
+            double u0 = 1.0 - fabs(s), u1 = fabs(s);
+            e[k] += wv * ph * u0;
+            de_dmu[k] += wv * dm * u0;
+            de_dsig[k] += wv * ds * u0;
+            if (s != 0.0) {
+                e[k2] += wv * ph * u1;
+                de_dmu[k2] += wv * dm * u1;
+                de_dsig[k2] += wv * ds * u1;
+            }
+        }
+    }
+}
+
+typedef struct { int gy, gx, dep; } orc_cellref;
+
+static int cmp_cellref(const void *a, const void *b)
+{
+    const orc_cellref *x = (const orc_cellref *)a, *y = (const orc_cellref *)b;
+    if (x->gy != y->gy) return x->gy < y->gy ? -1 : 1;
+    if (x->gx != y->gx) return x->gx < y->gx ? -1 : 1;
+    return x->dep < y->dep ? -1 : (x->dep > y->dep);
+}
+
+/* Adjoint of the whole path for the loss L = 1/2 sum_{P in pixel_ids, t} r^2 with
+ * r = dL/dI given per listed pixel (resid [npix][nt]; unlisted pixels have r = 0).
+ *   G[j, P', t'] = dL/dQeff = sum_K sum_tau r[P' - K, t' + tau] i[j, K, tau]
+ * (the transpose of the interlaced convolution, Sec. II-D), then the chain rule
+ * through Qeff = q e_x e_y e_t with the windows held fixed.
+ * Output per deposit, grad[d][7] = dL/d(q, mu_x, mu_y, mu_t, sig_x, sig_y, sig_t)
+ * in grid units (GL mode). */
+void orc_adjoint(const orc_params *p, int n, const orc_dep *d, const float *resp, int kp,
+                 int nr, int npix, const int32_t *pixel_ids, const double *resid, double *grad)
+{
+    const int ns = p->n_sub, R = (kp - 1) / 2, nt = p->nt;
+    const int ngx = p->npx_x * ns, ngy = p->npx_y * ns;
+    double xi[64], wl[64];
+    orc_gl_rule(p->gl_order, xi, wl);
+    int32_t *row_of = (int32_t *)malloc(sizeof(int32_t) * (size_t)p->npx_x * p->npx_y);
+    for (size_t k = 0; k < (size_t)p->npx_x * p->npx_y; ++k) row_of[k] = -1;
+    for (int i = 0; i < npix; ++i) row_of[pixel_ids[i]] = i;
+    /* every (column, deposit) incidence, sorted by column */
+    long m = 0;
+    for (int i = 0; i < n; ++i) {
+        int ga[3], gb[3], ok = 1;
+        for (int ax = 0; ax < 3; ++ax) ok &= support(p, &d[i], ax, &ga[ax], &gb[ax]);
+        if (ok) m += (long)(gb[0] - ga[0] + 1) * (gb[1] - ga[1] + 1);
+    }
+    orc_cellref *refs = (orc_cellref *)malloc(sizeof(orc_cellref) * (m > 0 ? m : 1));
+    m = 0;
+    for (int i = 0; i < n; ++i) {
+        int ga[3], gb[3], ok = 1;
+        for (int ax = 0; ax < 3; ++ax) ok &= support(p, &d[i], ax, &ga[ax], &gb[ax]);
+        if (!ok) continue;
+        for (int gy = ga[1]; gy <= gb[1]; ++gy)
+            for (int gx = ga[0]; gx <= gb[0]; ++gx) {
+                refs[m].gy = gy;
+                refs[m].gx = gx;
+                refs[m].dep = i;
+                ++m;
+            }
+    }
+    qsort(refs, m, sizeof(orc_cellref), cmp_cellref);
+    /* column runs */
+    long nrun = 0;
+    for (long k = 0; k < m; ++k)
+        if (k == 0 || refs[k].gy != refs[k - 1].gy || refs[k].gx != refs[k - 1].gx) ++nrun;
+    long *run_beg = (long *)malloc(sizeof(long) * (nrun + 1));
+    nrun = 0;
+    for (long k = 0; k < m; ++k)
+        if (k == 0 || refs[k].gy != refs[k - 1].gy || refs[k].gx != refs[k - 1].gx) run_beg[nrun++] = k;
+    run_beg[nrun] = m;
+    for (int i = 0; i < n * 7; ++i) grad[i] = 0.0;
+#pragma omp parallel
+    {
+        double *G = (double *)malloc(sizeof(double) * nt);
+        double *gloc = (double *)calloc((size_t)n * 7, sizeof(double));
+#pragma omp for schedule(dynamic)
+        for (long c = 0; c < nrun; ++c) {
+            const int gy = refs[run_beg[c]].gy, gx = refs[run_beg[c]].gx;
+            const int Py = gy / ns, Px = gx / ns, jy = gy % ns, jx = gx % ns;
+            /* time range of this column's deposits */
+            int ta = nt, tb = -1;
+            for (long k = run_beg[c]; k < run_beg[c + 1]; ++k) {
+                int a, b;
+                support(p, &d[refs[k].dep], 2, &a, &b);
+                if (a < ta) ta = a;
+                if (b > tb) tb = b;
+            }
+            for (int t = ta; t <= tb; ++t) G[t] = 0.0;
+            for (int Ky = -R; Ky <= R; ++Ky)
+                for (int Kx = -R; Kx <= R; ++Kx) {
+                    int qy = Py - Ky, qx = Px - Kx;     /* electrode seeing this cell through i[j, K] */
+                    if (qy < 0 || qy >= p->npx_y || qx < 0 || qx >= p->npx_x) continue;
+                    int row = row_of[qy * p->npx_x + qx];
+                    if (row < 0) continue;
+                    const double *rr = resid + (size_t)row * nt;
+                    const float *ir = resp + ((((size_t)(Ky + R) * kp + (Kx + R)) * ns + jy) * ns + jx) * nr;
+                    for (int t = ta; t <= tb; ++t) {
+                        double s = 0.0;
+                        for (int tau = 0; tau < nr && t + tau < nt; ++tau) s += rr[t + tau] * (double)ir[tau];
+                        G[t] += s;
+                    }
+                }
+            for (long k = run_beg[c]; k < run_beg[c + 1]; ++k) {
+                const int i = refs[k].dep;
+                const orc_dep *dd = &d[i];
+                int a, b;
+                support(p, dd, 2, &a, &b);
+                double e[3][3];   /* [axis][value, d/dmu, d/dsig] at this column / summed in t */
+                /* x and y weights at this column */
+                for (int ax = 0; ax < 2; ++ax) {
+                    int len = dd->hi[ax] - dd->lo[ax] + 3;
+                    double *w0 = (double *)malloc(sizeof(double) * len * 3);
+                    orc_weights_gl_grad(p->gl_order, xi, wl, dd->mu[ax], dd->sig[ax], dd->lo[ax],
+                                        dd->hi[ax], w0, w0 + len, w0 + 2 * len);
+                    int g = (ax == 0 ? gx : gy) - (dd->lo[ax] - 1);
+                    e[ax][0] = w0[g];
+                    e[ax][1] = w0[len + g];
+                    e[ax][2] = w0[2 * len + g];
+                    free(w0);
+                }
+                int len = dd->hi[2] - dd->lo[2] + 3;
+                double *w0 = (double *)malloc(sizeof(double) * len * 3);
+                orc_weights_gl_grad(p->gl_order, xi, wl, dd->mu[2], dd->sig[2], dd->lo[2], dd->hi[2],
+                                    w0, w0 + len, w0 + 2 * len);
+                double st0 = 0, st1 = 0, st2 = 0;
+                for (int t = a; t <= b; ++t) {
+                    int g = t - (dd->lo[2] - 1);
+                    st0 += G[t] * w0[g];
+                    st1 += G[t] * w0[len + g];
+                    st2 += G[t] * w0[2 * len + g];
+                }
+                free(w0);
+                e[2][0] = st0;
+                e[2][1] = st1;
+                e[2][2] = st2;
+                double *gd = gloc + (size_t)i * 7;
+                const double q = dd->q;
+                gd[0] += e[0][0] * e[1][0] * e[2][0];
+                gd[1] += q * e[0][1] * e[1][0] * e[2][0];
+                gd[2] += q * e[0][0] * e[1][1] * e[2][0];
+                gd[3] += q * e[0][0] * e[1][0] * e[2][1];
+                gd[4] += q * e[0][2] * e[1][0] * e[2][0];
+                gd[5] += q * e[0][0] * e[1][2] * e[2][0];
+                gd[6] += q * e[0][0] * e[1][0] * e[2][2];
+            }
+        }
+#pragma omp critical
+        for (int i = 0; i < n * 7; ++i) grad[i] += gloc[i];
+        free(gloc);
+        free(G);
+    }
+    free(run_beg);
+    free(refs);
+    free(row_of);
+}
+
+/* Chain rule from the per-deposit gradients dL/d(q, mu, sigma) (grid units) to the
+ * inputs of the transport step (Sec. II-A) and its global constants:
+ *   mu_x = x / h - 1/2, mu_t = (t0 + z / v) / tick, q = ne exp(-t_d / tau),
+ *   sig_xy^2 = 2 DT 1e-6 t_d / h^2 + s0^2, sig_t^2 = 2 DL 1e-6 t_d / (v tick)^2 + s0t^2.
+ * Per deposit out[d][4] = dL/d(x, y, t0, ne); glob[3] = dL/d(DL, DT, tau). */
+void orc_param_grads(const orc_params *p, int n, const float *z, const float *ne, const orc_dep *d,
+                     const double *grad7, double *out, double *glob)
+{
+    const double v = p->v_cm_per_us, tick = p->tick_us, tau = p->lifetime_us;
+    const double h = (double)p->pitch_cm / (double)p->n_sub;
+    double gDL = 0, gDT = 0, gtau = 0;
+    for (int i = 0; i < n; ++i) {
+        const double *g = grad7 + (size_t)i * 7;
+        double *o = out + (size_t)i * 4;
+        if (!d[i].valid) {
+            o[0] = o[1] = o[2] = o[3] = 0.0;
+            continue;
+        }
+        const double td = (double)z[i] / v;
+        o[0] = g[1] / h;
+        o[1] = g[2] / h;
+        o[2] = g[3] / tick;
+        o[3] = g[0] * exp(-td / tau);
+        gtau += g[0] * d[i].q * td / (tau * tau);
+        gDT += (g[4] + g[5]) * 1e-6 * td / (h * h * d[i].sig[0]);
+        gDL += g[6] * 1e-6 * td / (v * tick * v * tick * d[i].sig[2]);
+    }
+    glob[0] = gDL;
+    glob[1] = gDT;
+    glob[2] = gtau;
+    (void)ne;
+}

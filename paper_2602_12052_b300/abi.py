@@ -32,6 +32,7 @@ EXPORTS = [
     "tred_create", "tred_destroy", "tred_last_error", "tred_sync_status", "tred_reset_status",
     "tred_set_response", "tred_drift", "tred_blockbin", "tred_effq", "tred_convolve",
     "tred_gather_pixels", "tred_readout", "tred_launch_count", "tred_blockbin_noalloc",
+    "tred_set_transport", "tred_residual", "tred_adjoint", "tred_param_grads",
 ]
 
 
@@ -94,6 +95,10 @@ def load(path: str | None = None) -> ctypes.CDLL:
     lib.tred_convolve.argtypes = [_P, _P, _P, _P, _P, _P]
     lib.tred_gather_pixels.argtypes = [_P, _P, _P, _P, _P, _P, _P, _P]
     lib.tred_readout.argtypes = [_P, ctypes.POINTER(ReadoutParams), _P, _P, _P, _P, _P, _P, _P, _I, _P]
+    lib.tred_set_transport.argtypes = [_P, ctypes.POINTER(Params)]
+    lib.tred_residual.argtypes = [_P, _P, _P, _P, _P, _I, _P, _P, _P, _P]
+    lib.tred_adjoint.argtypes = [_P, _I, ctypes.POINTER(Deposits), _P, _P, _P, _P, _P, _P, _P, _P, _P, _P]
+    lib.tred_param_grads.argtypes = [_P, _I, _P, ctypes.POINTER(Deposits), _P, _P, _P, _P]
     lib.tred_blockbin_noalloc.argtypes = [ctypes.POINTER(Geometry), _I, ctypes.POINTER(Deposits), _P, _P, _P,
                                           _P, _I, _I, _P, _P, _P]
     for name in EXPORTS:

@@ -131,13 +131,14 @@ int32_t tred_create(const tred_geometry *geom, const tred_params *params, int32_
     d.R = (geom->kp - 1) / 2;
     d.G = geom->lt / BINS;
     d.npairs = params->mpcp ? geom->n_sub * geom->n_sub / 2 : geom->n_sub * geom->n_sub;
-    // Window capacity from the largest drift: width = hi - lo + 3 <= 2 K + 5.
+    // Window capacity from the largest drift: width = hi - lo + 3 <= 2 K + 5.  The
+    // diffusion constants get a 2x margin so that tred_set_transport may raise them.
     {
         double td = (double)params->max_drift_cm / (double)params->v_cm_per_us;
-        double sx = std::sqrt(2.0 * params->DT_cm2_per_s * 1e-6 * td / (d.h * d.h)
+        double sx = std::sqrt(2.0 * 2.0 * params->DT_cm2_per_s * 1e-6 * td / (d.h * d.h)
                               + (double)params->sigma0_cells_xy * params->sigma0_cells_xy);
         double vt = (double)params->v_cm_per_us * geom->tick_us;
-        double st = std::sqrt(2.0 * params->DL_cm2_per_s * 1e-6 * td / (vt * vt)
+        double st = std::sqrt(2.0 * 2.0 * params->DL_cm2_per_s * 1e-6 * td / (vt * vt)
                               + (double)params->sigma0_ticks * params->sigma0_ticks);
         d.wx = (int)std::ceil(2.0 * params->nsigma * sx * (1 + 1e-9)) + 6;
         d.wt = (int)std::ceil(2.0 * params->nsigma * st * (1 + 1e-9)) + 6;
@@ -225,7 +226,7 @@ int32_t tred_create(const tred_geometry *geom, const tred_params *params, int32_
 
 int32_t tred_destroy(tred_handle *h) {
     if (!h) return TRED_ERR_INVALID_ARG;
-    void *ptrs[] = {h->rhat, h->pair_j, h->wts, h->recs, h->blk_count, h->blk_slot, h->blk_fill,
+    void *ptrs[] = {h->wts2, h->pix_row, h->gspec, h->rhat, h->pair_j, h->wts, h->recs, h->blk_count, h->blk_slot, h->blk_fill,
                     h->scan_part, h->colmask, h->yspec, h->pix_flag, h->pix_part, h->hit_cnt,
                     h->hit_tmp, h->hit_tmpc, h->status, h->tw};
     for (void *p : ptrs)
@@ -241,6 +242,76 @@ int32_t tred_sync_status(tred_handle *h, void *stream, int32_t *host_status) {
                                            cudaMemcpyDeviceToHost, s), "read status");
     if (rc) return rc;
     return check_cuda(h, cudaStreamSynchronize(s), "sync status");
+}
+
+static bool deps_ok(const tred_deposits *d) {
+    return d && d->cell_x && d->cell_y && d->cell_t && d->frac_x && d->frac_y && d->frac_t &&
+           d->sigma_x && d->sigma_y && d->sigma_t && d->lo_x && d->lo_y && d->lo_t && d->hi_x &&
+           d->hi_y && d->hi_t && d->q;
+}
+
+int32_t tred_set_transport(tred_handle *h, const tred_params *params) {
+    if (!h || !params) return TRED_ERR_INVALID_ARG;
+    char msg[256];
+    if (validate(&h->g, params, msg, sizeof msg) != TRED_OK) return set_error(h, TRED_ERR_INVALID_ARG, "%s", msg);
+    if (params->gl_order != h->p.gl_order || params->effq_mode != h->p.effq_mode || params->mpcp != h->p.mpcp ||
+        params->conv_mode != h->p.conv_mode)
+        return set_error(h, TRED_ERR_INVALID_ARG, "tred_set_transport: only transport constants may change");
+    const double td = (double)params->max_drift_cm / (double)params->v_cm_per_us;
+    const double sx = std::sqrt(2.0 * params->DT_cm2_per_s * 1e-6 * td / (h->d.h * h->d.h) +
+                                (double)params->sigma0_cells_xy * params->sigma0_cells_xy);
+    const double vt = (double)params->v_cm_per_us * h->g.tick_us;
+    const double st = std::sqrt(2.0 * params->DL_cm2_per_s * 1e-6 * td / (vt * vt) +
+                                (double)params->sigma0_ticks * params->sigma0_ticks);
+    if ((int)std::ceil(2.0 * params->nsigma * sx) + 6 > h->d.wx || (int)std::ceil(2.0 * params->nsigma * st) + 6 > h->d.wt)
+        return set_error(h, TRED_ERR_CAPACITY, "tred_set_transport: diffusion beyond the window capacity of tred_create");
+    h->p = *params;
+    return TRED_OK;
+}
+
+int32_t tred_residual(tred_handle *h, const int32_t *pixel_ids, const int32_t *n_pixels_dev, const float *waveforms,
+                      const int32_t *target_ids, int32_t n_target, const float *target_waves, float *resid,
+                      double *loss_dev, void *stream) {
+    if (!h) return TRED_ERR_INVALID_ARG;
+    if (!pixel_ids || !n_pixels_dev || !waveforms || !resid || !loss_dev || n_target < 0 ||
+        (n_target > 0 && (!target_ids || !target_waves)))
+        return set_error(h, TRED_ERR_INVALID_ARG, "tred_residual: null pointer");
+    return launch_residual(h, pixel_ids, n_pixels_dev, waveforms, target_ids, n_target, target_waves, resid, loss_dev,
+                           (cudaStream_t)stream);
+}
+
+int32_t tred_adjoint(tred_handle *h, int32_t n, const tred_deposits *deps, const int32_t *block_ids,
+                     const int32_t *dep_offsets, const int32_t *dep_index, const int32_t *n_blocks_dev,
+                     const int32_t *pixel_ids, const int32_t *n_pixels_dev, const float *resid, float *dqeff,
+                     float *grad7, void *stream) {
+    if (!h) return TRED_ERR_INVALID_ARG;
+    if (!h->response_ready) return set_error(h, TRED_ERR_NOT_READY, "tred_adjoint: call tred_set_response first");
+    if (h->p.effq_mode != 0) return set_error(h, TRED_ERR_INVALID_ARG, "tred_adjoint: Gauss-Legendre mode only");
+    if (n < 0 || n > h->max_deposits) return set_error(h, TRED_ERR_CAPACITY, "tred_adjoint: bad n");
+    if ((n > 0 && (!deps_ok(deps) || !grad7)) || !block_ids || !dep_offsets || !dep_index || !n_blocks_dev ||
+        !pixel_ids || !n_pixels_dev || !resid || !dqeff)
+        return set_error(h, TRED_ERR_INVALID_ARG, "tred_adjoint: null pointer");
+    if (!h->wts2) {   // first call: adjoint scratch
+        h->adj_chunk = h->max_blocks < 32 ? h->max_blocks : 32;
+        const size_t b1 = sizeof(float) * 3 * (size_t)h->max_deposits * h->d.wstride;
+        const size_t b2 = sizeof(int32_t) * (size_t)h->g.npx_x * h->g.npx_y;
+        const size_t b3 = sizeof(float2) * (size_t)h->adj_chunk * h->d.npairs * h->g.lt * 64;
+        int rc = check_cuda(h, cudaMalloc(&h->wts2, b1), "alloc adjoint weights");
+        if (!rc) rc = check_cuda(h, cudaMalloc(&h->pix_row, b2), "alloc pixel rows");
+        if (!rc) rc = check_cuda(h, cudaMalloc(&h->gspec, b3), "alloc adjoint spectra");
+        if (rc) return rc;
+    }
+    return launch_adjoint(h, n, n > 0 ? *deps : tred_deposits{}, block_ids, dep_offsets, dep_index, n_blocks_dev,
+                          pixel_ids, n_pixels_dev, resid, dqeff, grad7, (cudaStream_t)stream);
+}
+
+int32_t tred_param_grads(tred_handle *h, int32_t n, const float *z, const tred_deposits *deps, const float *grad7,
+                         float *grad_inputs, double *grad_global, void *stream) {
+    if (!h) return TRED_ERR_INVALID_ARG;
+    if (n < 0 || n > h->max_deposits || (n > 0 && (!z || !deps_ok(deps) || !grad7 || !grad_inputs)) || !grad_global)
+        return set_error(h, TRED_ERR_INVALID_ARG, "tred_param_grads: bad arguments");
+    return launch_param_grads(h, n, z, n > 0 ? *deps : tred_deposits{}, grad7, grad_inputs, grad_global,
+                              (cudaStream_t)stream);
 }
 
 int32_t tred_launch_count(const tred_handle *h, int64_t *count) {
@@ -263,11 +334,6 @@ int32_t tred_set_response(tred_handle *h, const float *resp_dev, void *stream) {
     return rc;
 }
 
-static bool deps_ok(const tred_deposits *d) {
-    return d && d->cell_x && d->cell_y && d->cell_t && d->frac_x && d->frac_y && d->frac_t &&
-           d->sigma_x && d->sigma_y && d->sigma_t && d->lo_x && d->lo_y && d->lo_t && d->hi_x &&
-           d->hi_y && d->hi_t && d->q;
-}
 
 int32_t tred_drift(tred_handle *h, int32_t n, const float *x, const float *y, const float *z,
                    const float *t0, const float *ne, const tred_deposits *out, void *stream) {

@@ -59,6 +59,11 @@ struct tred_handle {
     float2 *tw;            // twiddle tables (see tred_api.cu)
     double *gl_x, *gl_w;   // host copies unused on device; kept for reference
     float gl_xi[tred::MAX_GL], gl_wi[tred::MAX_GL];
+    // adjoint scratch (allocated on the first tred_adjoint call)
+    float *wts2;           // [max_deposits][3][wstride] weights, d/dmu, d/dsigma
+    int32_t *pix_row;      // [npx_x * npx_y] row of a pixel in the current list or -1
+    float2 *gspec;         // [adj_chunk][npairs][lt][64] adjoint spectra of the input pixels
+    int32_t adj_chunk;
     int64_t launches;      // kernels launched through this handle (diagnostics)
     char err[512];
 };
@@ -98,6 +103,16 @@ int launch_readout(tred_handle *h, const tred_readout_params &rp, const int32_t 
                    const float *wave, const int32_t *n_pixels_dev, int32_t *hit_pixel,
                    int32_t *hit_tick, float *hit_charge, int32_t *n_hits_dev,
                    int32_t max_hits, cudaStream_t s);
+
+int launch_residual(tred_handle *h, const int32_t *pix, const int32_t *n_pix_dev, const float *wave,
+                    const int32_t *tpix, int n_target, const float *twave, float *resid, double *loss,
+                    cudaStream_t s);
+int launch_adjoint(tred_handle *h, int n, const tred_deposits &deps, const int32_t *block_ids,
+                   const int32_t *dep_offsets, const int32_t *dep_index, const int32_t *n_blocks_dev,
+                   const int32_t *pixel_ids, const int32_t *n_pixels_dev, const float *resid, float *gq,
+                   float *grad7, cudaStream_t s);
+int launch_param_grads(tred_handle *h, int n, const float *z, const tred_deposits &deps, const float *grad7,
+                       float *gin, double *gglob, cudaStream_t s);
 
 int num_sms(tred_handle *h);
 

@@ -153,6 +153,32 @@ def tred_launch_count(h: Handle) -> int:
     return int(c.value)
 
 
+def tred_set_transport(h: Handle, prm: Params):
+    h.check(h.lib.tred_set_transport(h.h, ctypes.byref(prm)))
+    h.prm = prm
+
+
+def tred_residual(h: Handle, pixel_ids, n_pixels_dev, waveforms, target_ids, target_waves, resid,
+                  loss_dev, stream=None):
+    h.check(h.lib.tred_residual(h.h, _ptr(pixel_ids), _ptr(n_pixels_dev), _ptr(waveforms),
+                                _ptr(target_ids), target_ids.numel(), _ptr(target_waves),
+                                _ptr(resid), _ptr(loss_dev), _stream(stream)))
+
+
+def tred_adjoint(h: Handle, n: int, deps: DepositBuffers, block_ids, dep_offsets, dep_index,
+                 n_blocks_dev, pixel_ids, n_pixels_dev, resid, dqeff, grad7, stream=None):
+    h.check(h.lib.tred_adjoint(h.h, n, ctypes.byref(deps.struct), _ptr(block_ids), _ptr(dep_offsets),
+                               _ptr(dep_index), _ptr(n_blocks_dev), _ptr(pixel_ids),
+                               _ptr(n_pixels_dev), _ptr(resid), _ptr(dqeff), _ptr(grad7),
+                               _stream(stream)))
+
+
+def tred_param_grads(h: Handle, n: int, z, deps: DepositBuffers, grad7, grad_inputs, grad_global,
+                     stream=None):
+    h.check(h.lib.tred_param_grads(h.h, n, _ptr(z), ctypes.byref(deps.struct), _ptr(grad7),
+                                   _ptr(grad_inputs), _ptr(grad_global), _stream(stream)))
+
+
 def tred_reset_status(h: Handle, stream=None):
     h.check(h.lib.tred_reset_status(h.h, _stream(stream)))
 
@@ -166,6 +192,7 @@ class Simulator:
                  max_pixels: int, max_pairs: int | None = None, max_hits: int | None = None,
                  effq_mode=0, mpcp=1, compensated_gather=0, device=None):
         self.cfg = cfg
+        self.mpcp = mpcp
         self.device = torch.device(device or "cuda")
         self.h = Handle(geometry(cfg), params(cfg, effq_mode, mpcp, compensated_gather),
                         max_deposits, max_blocks, max_pixels)
@@ -231,3 +258,53 @@ class Simulator:
             "hit_tick": self.hit_tick[:nh].cpu().numpy(),
             "hit_charge": self.hit_charge[:nh].cpu().numpy(),
         }
+
+
+# ----------------------------------------------------------------- differentiation
+class DiffState:
+    """Buffers of the backward pass bound to a Simulator."""
+
+    def __init__(self, sim: "Simulator"):
+        d = sim.device
+        self.sim = sim
+        self.resid = torch.zeros((sim.h.max_pixels, sim.cfg.nt), dtype=torch.float32, device=d)
+        self.loss = torch.zeros(1, dtype=torch.float64, device=d)
+        self.grad7 = torch.zeros((sim.h.max_deposits, 7), dtype=torch.float32, device=d)
+        self.gin = torch.zeros((sim.h.max_deposits, 4), dtype=torch.float32, device=d)
+        self.gglob = torch.zeros(3, dtype=torch.float64, device=d)
+
+
+class TredLoss(torch.autograd.Function):
+    """L = 1/2 sum over pixels and ticks of (I - I*)^2 for one event, differentiable in
+    the deposits' x, y, t0, n_e and in the transport constants DL, DT and lifetime
+    (Sec. V-C).  Forward: the CUDA hot path (drift -> blockbin -> effq -> convolve ->
+    gather) and the residual against the target rows; backward: tred_adjoint and
+    tred_param_grads (windows held fixed, quadrature recomputed)."""
+
+    @staticmethod
+    def forward(ctx, state: DiffState, target_ids, target_waves, x, y, z, t0, ne, DL, DT, tau):
+        sim = state.sim
+        prm = params(sim.cfg, mpcp=sim.mpcp)
+        prm.DL_cm2_per_s, prm.DT_cm2_per_s, prm.lifetime_us = float(DL), float(DT), float(tau)
+        tred_set_transport(sim.h, prm)
+        n = x.numel()
+        sim.step(n, x, y, z, t0, ne, readout=False)
+        tred_residual(sim.h, sim.pixel_ids, sim.n_pixels_dev, sim.waveforms, target_ids, target_waves,
+                      state.resid, state.loss)
+        ctx.state, ctx.n = state, n
+        ctx.pdev = [v.device if torch.is_tensor(v) else None for v in (DL, DT, tau)]
+        ctx.save_for_backward(z)
+        return state.loss.to(torch.float32).reshape(())
+
+    @staticmethod
+    def backward(ctx, g):
+        state, n = ctx.state, ctx.n
+        (z,) = ctx.saved_tensors
+        sim = state.sim
+        tred_adjoint(sim.h, n, sim.deps, sim.block_ids, sim.dep_offsets, sim.dep_index, sim.n_blocks_dev,
+                     sim.pixel_ids, sim.n_pixels_dev, state.resid, sim.qeff, state.grad7)
+        tred_param_grads(sim.h, n, z, sim.deps, state.grad7, state.gin, state.gglob)
+        gin = state.gin[:n] * g.to(state.gin.device)
+        gg = (state.gglob * g.to(state.gglob.device).double()).to(torch.float32)
+        gp = [gg[k].to(dv) if dv is not None else None for k, dv in enumerate(ctx.pdev)]
+        return (None, None, None, gin[:, 0], gin[:, 1], None, gin[:, 2], gin[:, 3], gp[0], gp[1], gp[2])

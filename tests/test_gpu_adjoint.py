@@ -1,0 +1,140 @@
+"""GPU differentiable simulation (Sec. V-C) against the FP64 oracle's gradient, which
+itself is pinned by central finite differences (tests/test_oracle_adjoint.py)."""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+pytestmark = pytest.mark.gpu
+
+
+def _event(n=None, start=0):
+    cfg = synth.get_config("tiny")
+    dep, resp = synth.make_event(cfg)
+    if n is not None:
+        dep = {k: v[start:start + n].copy() for k, v in dep.items()}
+    return cfg, dep, resp
+
+
+def _target(cfg, dep, resp, scale=(1.3, 0.75, 0.5)):
+    pt = oracle.params(cfg, DL_cm2_per_s=cfg.DL_cm2_per_s * scale[0],
+                       DT_cm2_per_s=cfg.DT_cm2_per_s * scale[1], lifetime_us=cfg.lifetime_us * scale[2])
+    r = oracle.simulate(cfg.with_(DL_cm2_per_s=pt.DL_cm2_per_s, DT_cm2_per_s=pt.DT_cm2_per_s,
+                                  lifetime_us=pt.lifetime_us), dep, resp)
+    return r["pixel_ids"], r["waveforms"]
+
+
+def _gpu_backward(cfg, dep, resp, tid, twave):
+    import torch
+    from parity_util import make_sim
+    from paper_2602_12052_b300 import tred
+    n = len(dep["x"])
+    sim = make_sim(cfg, resp, n)
+    st = tred.DiffState(sim)
+    x = {k: torch.from_numpy(v).cuda() for k, v in dep.items()}
+    sim.step(n, x["x"], x["y"], x["z"], x["t0"], x["ne"], readout=False)
+    tid_d = torch.from_numpy(tid).cuda()
+    tw_d = torch.from_numpy(twave.astype(np.float32)).cuda()
+    tred.tred_residual(sim.h, sim.pixel_ids, sim.n_pixels_dev, sim.waveforms, tid_d, tw_d, st.resid, st.loss)
+    tred.tred_adjoint(sim.h, n, sim.deps, sim.block_ids, sim.dep_offsets, sim.dep_index, sim.n_blocks_dev,
+                      sim.pixel_ids, sim.n_pixels_dev, st.resid, sim.qeff, st.grad7)
+    tred.tred_param_grads(sim.h, n, x["z"], sim.deps, st.grad7, st.gin, st.gglob)
+    torch.cuda.synchronize()
+    assert sim.status()[0] == 0
+    return (float(st.loss.item()), st.grad7[:n].cpu().numpy().astype(np.float64),
+            st.gin[:n].cpu().numpy().astype(np.float64), st.gglob.cpu().numpy())
+
+
+def _oracle_backward(cfg, dep, resp, tid, twave):
+    p = oracle.params(cfg)
+    d = oracle.drift(p, dep)
+    ids, _ = oracle.active_blocks(p, d)
+    pix = oracle.active_pixels(p, ids, cfg.kp)
+    w = oracle.pixel_currents(p, d, resp, pix)
+    tw = np.zeros_like(w)
+    pos = {int(q): k for k, q in enumerate(tid)}
+    for r, q in enumerate(pix):
+        if int(q) in pos:
+            tw[r] = twave[pos[int(q)]].astype(np.float32)
+    resid = w - tw
+    extra = sum(0.5 * np.sum(twave[k].astype(np.float32).astype(np.float64) ** 2)
+                for q, k in pos.items() if q not in set(int(v) for v in pix))
+    loss = 0.5 * np.sum(resid ** 2) + extra
+    g7 = oracle.adjoint(p, d, resp, pix, resid)
+    gin, gglob = oracle.param_grads(p, dep, d, g7)
+    return loss, g7, gin, gglob
+
+
+@pytest.mark.parametrize("n,start", [(120, 200), (500, 0)])
+def test_adjoint_matches_oracle_gradient(n, start):
+    cfg, dep, resp = _event(n, start)
+    tid, twave = _target(cfg, dep, resp)
+    loss, g7, gin, gglob = _gpu_backward(cfg, dep, resp, tid, twave)
+    rloss, rg7, rgin, rgglob = _oracle_backward(cfg, dep, resp, tid, twave)
+    assert abs(loss - rloss) <= 1e-5 * rloss
+    for k in range(7):
+        scale = np.abs(rg7[:, k]).max()
+        err = np.abs(g7[:, k] - rg7[:, k]).max()
+        assert err <= 1e-4 * scale, (k, err, scale)
+    for k in range(4):
+        scale = np.abs(rgin[:, k]).max()
+        assert np.abs(gin[:, k] - rgin[:, k]).max() <= 1e-4 * scale, k
+    np.testing.assert_allclose(gglob, rgglob, rtol=1e-4)
+
+
+def test_autograd_function_matches_oracle():
+    import torch
+    from parity_util import make_sim
+    from paper_2602_12052_b300 import tred
+    cfg, dep, resp = _event(300, 100)
+    tid, twave = _target(cfg, dep, resp)
+    n = len(dep["x"])
+    sim = make_sim(cfg, resp, n)
+    st = tred.DiffState(sim)
+    x = {k: torch.from_numpy(v).cuda().requires_grad_(k in ("x", "y", "t0", "ne")) for k, v in dep.items()}
+    DL = torch.tensor(cfg.DL_cm2_per_s, requires_grad=True)
+    DT = torch.tensor(cfg.DT_cm2_per_s, requires_grad=True)
+    tau = torch.tensor(cfg.lifetime_us, requires_grad=True)
+    loss = tred.TredLoss.apply(st, torch.from_numpy(tid).cuda(), torch.from_numpy(twave.astype(np.float32)).cuda(),
+                               x["x"], x["y"], x["z"], x["t0"], x["ne"], DL, DT, tau)
+    loss.backward()
+    rloss, rg7, rgin, rgglob = _oracle_backward(cfg, dep, resp, tid, twave)
+    assert abs(float(loss) - rloss) <= 1e-5 * rloss
+    for k, name in enumerate(["x", "y", "t0", "ne"]):
+        g = x[name].grad.cpu().numpy().astype(np.float64)
+        assert np.abs(g - rgin[:, k]).max() <= 1e-4 * np.abs(rgin[:, k]).max(), name
+    np.testing.assert_allclose([DL.grad.item(), DT.grad.item(), tau.grad.item()], rgglob, rtol=1e-4)
+
+
+def test_recovers_transport_constants_from_perturbed_starts():
+    """Gradient descent on (DL, DT, lifetime) from +-30% starts back to the values
+    that made the target waveforms (the paper's lifetime-recovery demonstration,
+    extended to both diffusion constants)."""
+    import torch
+    from parity_util import make_sim
+    from paper_2602_12052_b300 import tred
+    cfg, dep, resp = _event()
+    truth = np.array([cfg.DL_cm2_per_s, cfg.DT_cm2_per_s, cfg.lifetime_us])
+    n = len(dep["x"])
+    sim = make_sim(cfg, resp, n)
+    x = {k: torch.from_numpy(v).cuda() for k, v in dep.items()}
+    sim.step(n, x["x"], x["y"], x["z"], x["t0"], x["ne"], readout=False)
+    npix = int(sim.counts[1].item())
+    tid = sim.pixel_ids[:npix].clone()
+    twave = sim.waveforms[:npix].clone()
+    st = tred.DiffState(sim)
+    rng = np.random.default_rng(11)
+    signs = rng.choice([-1.0, 1.0], 3)
+    logp = torch.tensor(np.log(truth * (1 + 0.3 * signs)), requires_grad=True)
+    opt = torch.optim.Adam([logp], lr=0.05)
+    for it in range(250):
+        opt.zero_grad()
+        p = torch.exp(logp)
+        loss = tred.TredLoss.apply(st, tid, twave, x["x"], x["y"], x["z"], x["t0"], x["ne"], p[0], p[1], p[2])
+        loss.backward()
+        opt.step()
+    final = torch.exp(logp).detach().numpy()
+    rel = np.abs(final / truth - 1)
+    assert rel[0] < 0.02 and rel[1] < 0.02, (final, truth)
+    assert rel[2] < 0.1, (final, truth)
