@@ -51,6 +51,10 @@ def _args():
                     help="deposits of the workload timed through the CPU oracle")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--mode", default="step", choices=["step", "batched", "adjoint", "spill"],
+                    help="step: one event (default); batched: 64 uneven events, autotuned, CUDA graph; "
+                         "adjoint: forward + backward; spill: 35 planes in sequence")
+    ap.add_argument("--events", type=int, default=64)
     return ap.parse_args()
 
 
@@ -180,10 +184,175 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def _line(metric, value, unit, ms, args, cfg_extra, **kw):
+    line = {"metric": metric, "value": value, "unit": unit, "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic", "config": cfg_extra}
+    line.update(kw)
+    print(json.dumps(line), flush=True)
+
+
+def _timed(fn, steps, warmup):
+    import torch
+    for _ in range(warmup):
+        fn()
+    torch.cuda.synchronize()
+    evs = []
+    for _ in range(steps):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        fn()
+        b.record()
+        evs.append((a, b))
+    torch.cuda.synchronize()
+    return statistics.mean(a.elapsed_time(b) for a, b in evs)
+
+
+def run_batched(args):
+    """Config 3: uneven events (deposit counts log-uniform in [1e3, 1e6]) in one pass
+    per kernel over the global active-block list, captured in a CUDA graph, with the
+    block shape and FFT length picked by the autotuner; against one event at a time."""
+    import torch
+    import synth
+    from paper_2602_12052_b300 import autotune, tred
+    torch.cuda.set_device(0)
+    base = synth.get_config("module200")
+    resp = torch.from_numpy(synth.make_response(base))
+    events = synth.make_events(base, args.events, 1000, 1_000_000, seed=3003)
+    ntot = sum(len(e["x"]) for e in events)
+    t = time.perf_counter()
+    best, timings = autotune.autotune(base, events, resp, sample=8)
+    tune_s = time.perf_counter() - t
+    cfg = base.with_(bp=best[0], bt=best[1], lt=best[2])
+    sim = autotune.make_batch(cfg, events, resp, chunk_blocks=2048)
+    sim.step()
+    torch.cuda.synchronize()
+    st = sim.status()
+    if st[0] != 0:
+        raise RuntimeError(f"device status {st}")
+    nb, npix, nh = (int(v) for v in sim.counts[:3].cpu())
+    sim.capture()
+    with ClockSampler(0) as clk:
+        ms_graph = _timed(sim.replay, args.steps, 1)
+    clocks = clk.summary()
+    launches_per_step = None
+    del sim
+    torch.cuda.empty_cache()
+    # one event at a time through the same kernels (no graph, one launch sequence each)
+    nmax = max(len(e["x"]) for e in events)
+    bmax = max(autotune.probe_blocks(cfg, [e], resp)[0] for e in events)
+    one = tred.BatchSimulator(cfg, resp, [events[0]], max_blocks=bmax + 8,
+                              max_pixels=min(cfg.npx * cfg.npx, (bmax + 8) * (cfg.bp + cfg.kp - 1) ** 2),
+                              chunk_blocks=2048, n_events=1, max_deposits=nmax)
+    per_event = []
+    for e in events:
+        one.load([e])
+        per_event.append(_timed(one.step, 1, 1))
+    ms_single = sum(per_event)
+    _line("events/s and depos/s, 64 uneven events batched in one CUDA graph vs one at a time",
+          ntot / (ms_graph / 1e3), "depos/s", ms_graph, args,
+          {"workload": f"{args.events} events, deposits log-uniform in [1e3, 1e6] (total {ntot}), "
+                       "512x512 px x 6400 ticks each, 9x9x10x10x200 response",
+           "active_blocks": nb, "active_pixels": npix, "hits": nh,
+           "autotuned_shape": {"bp": best[0], "bt": best[1], "lt": best[2]},
+           "autotune_ms_per_kdepos": {f"{k[0]}x{k[0]}x{k[1]}/lt{k[2]}": 1e3 * v for k, v in timings.items()},
+           "autotune_s": tune_s},
+          events_per_s=args.events / (ms_graph / 1e3),
+          per_event={"ms_total": ms_single, "depos_per_s": ntot / (ms_single / 1e3),
+                     "events_per_s": args.events / (ms_single / 1e3)},
+          speedup_vs_per_event=ms_single / ms_graph, clocks=clocks)
+
+
+def run_adjoint(args):
+    """Config 4: forward + backward (adjoint) deposits/s and peak device memory."""
+    import torch
+    import synth
+    from paper_2602_12052_b300 import tred
+    torch.cuda.set_device(0)
+    cfg = synth.get_config("module200")
+    dep, resp = synth.make_event(cfg)
+    n = len(dep["x"])
+    dev = torch.device("cuda")
+    max_blocks, max_pixels = probe_capacities(cfg, dep, dev)
+    max_blocks = int(max_blocks * 1.3) + 8
+    max_pixels = min(cfg.npx * cfg.npx, int(max_pixels * 1.3))
+    free0, total = torch.cuda.mem_get_info()
+    sim = tred.Simulator(cfg, torch.from_numpy(resp), max_deposits=n, max_blocks=max_blocks,
+                         max_pixels=max_pixels, device=dev)
+    x = {k: torch.from_numpy(v).to(dev) for k, v in dep.items()}
+    sim.step(n, x["x"], x["y"], x["z"], x["t0"], x["ne"], readout=False)
+    npix = int(sim.counts[1].item())
+    tid, twave = sim.pixel_ids[:npix].clone(), sim.waveforms[:npix].clone()
+    st = tred.DiffState(sim)
+    p = [torch.tensor(v * 1.3, requires_grad=True) for v in (cfg.DL_cm2_per_s, cfg.DT_cm2_per_s, cfg.lifetime_us)]
+
+    def fwd_bwd():
+        loss = tred.TredLoss.apply(st, tid, twave, x["x"], x["y"], x["z"], x["t0"], x["ne"], *p)
+        loss.backward()
+
+    with ClockSampler(0) as clk:
+        ms = _timed(fwd_bwd, args.steps, args.warmup)
+    free1, _ = torch.cuda.mem_get_info()
+    nb = int(sim.counts[0].item())
+    stored_gb = nb * cfg.n_sub ** 2 * cfg.bp ** 2 * cfg.bt * 4 * (1 + 2 * cfg.gl_order ** 3) / 1e9
+    _line("forward+backward depos/s (gradients of an L2 loss w.r.t. deposit x/y/t0/ne, DL, DT, lifetime)",
+          n / (ms / 1e3), "depos/s", ms, args,
+          {"workload": f"module200 event: {n} deposits, 512x512 px x 6400 ticks, GL-2, starts at 1.3x truth",
+           "active_blocks": nb},
+          memory={"device_bytes_in_use": int(total - free1), "before_handle": int(total - free0),
+                  "note": "quadrature recomputed in the backward; dL/dQeff reuses the forward's Q^eff buffer",
+                  "stored_quadrature_estimate_gb": stored_gb},
+          clocks=clk.summary())
+
+
+def run_spill(args):
+    """Config 5: ~1e7 deposits over 35 module planes, processed one plane after the
+    other on one GPU; GL-3, 13x13x10x10x400 response, 4x4x256 blocks, FFT 16x16x1024."""
+    import torch
+    import synth
+    from paper_2602_12052_b300 import autotune, tred
+    torch.cuda.set_device(0)
+    cfg = synth.get_config("spill_plane")
+    resp = torch.from_numpy(synth.make_response(cfg))
+    planes = [synth.make_deposits(cfg, seed=cfg.seed * 100 + k) for k in range(35)]
+    ntot = sum(len(p["x"]) for p in planes)
+    nmax = max(len(p["x"]) for p in planes)
+    bmax = max(autotune.probe_blocks(cfg, [p], resp)[0] for p in planes[:6]) * 2
+    free0, total = torch.cuda.mem_get_info()
+    one = tred.BatchSimulator(cfg, resp, [planes[0]], max_blocks=bmax,
+                              max_pixels=min(cfg.npx * cfg.npx, bmax * (cfg.bp + cfg.kp - 1) ** 2),
+                              chunk_blocks=4096, n_events=1, max_deposits=nmax)
+    dev_planes = [{k: torch.from_numpy(v).cuda() for k, v in p.items()} for p in planes]
+
+    def all_planes():
+        for p in dev_planes:
+            n = p["x"].numel()
+            for k in ("x", "y", "z", "t0", "ne"):
+                one.inputs[k][:n].copy_(p[k])
+            one.n = n
+            one.step()
+
+    with ClockSampler(0) as clk:
+        ms = _timed(all_planes, max(1, args.steps // 2), 1)
+    free1, _ = torch.cuda.mem_get_info()
+    st = one.status()
+    dense = 35 * cfg.npx * cfg.npx * cfg.nt * 4
+    _line("depos/s over 35 module planes in sequence (spill scale)", ntot / (ms / 1e3), "depos/s", ms, args,
+          {"workload": f"35 planes x 512x512 px x 6400 ticks, {ntot} deposits, GL-3, 13x13x10x10x400 response, "
+                       "4x4x256 blocks, FFT 16x16x1024"},
+          memory={"device_bytes_in_use": int(total - free1),
+                  "dense_pixel_current_estimate_bytes": dense,
+                  "dense_subpixel_qeff_estimate_bytes": dense * cfg.n_sub ** 2},
+          status=st[:2], clocks=clk.summary())
+
+
 def main():
     args = _args()
     if args.impl == "reference":
         run_reference(args)
+        return
+    if args.mode != "step":
+        {"batched": run_batched, "adjoint": run_adjoint, "spill": run_spill}[args.mode](args)
         return
     import numpy as np
     import torch

@@ -69,6 +69,10 @@ typedef struct {
     int32_t bp, bt;      /* block shape: bp x bp pixels x bt ticks */
     int32_t kp, nr;      /* field response: kp x kp pixels (odd), nr ticks */
     int32_t lt;          /* FFT length along time: 512 or 1024, >= bt + nr - 1 */
+    int32_t n_events;    /* independent events stacked along y (0 or 1: a single event).
+                            Event e occupies pixel rows [e npx_y, (e + 1) npx_y); no support,
+                            footprint or gather crosses an event boundary, so a batch of
+                            events is simulated exactly as each event alone. */
 } tred_geometry;
 
 /* Transport and method switches. */
@@ -155,6 +159,15 @@ int32_t tred_drift(tred_handle *h, int32_t n, const float *x, const float *y,
                    const float *z, const float *t0, const float *ne,
                    const tred_deposits *out, void *stream);
 
+/* tred_drift for a batch of events: event[n] (device int32) gives each deposit's
+ * event in [0, n_events); x, y stay event-local.  The window is computed in
+ * event-local coordinates and shifted by whole cells (e npx_y n_sub), so it equals
+ * the single-event window bit for bit.  The handle remembers each deposit's event
+ * for the later calls on the same deposits.  tred_drift = this with all events 0. */
+int32_t tred_drift_events(tred_handle *h, int32_t n, const float *x, const float *y,
+                          const float *z, const float *t0, const float *ne, const int32_t *event,
+                          const tred_deposits *out, void *stream);
+
 /* a2. Block-sparse binning (Sec. III-B-1).  A block is active iff the clipped
  * support box of some deposit intersects it; its count is the number of such
  * deposits.  Output (device): block_ids[nb] ascending, block_counts[nb],
@@ -176,6 +189,17 @@ int32_t tred_effq(tred_handle *h, int32_t n, const tred_deposits *deps,
                   const int32_t *dep_index, const int32_t *n_blocks_dev, float *qeff,
                   void *stream);
 
+/* tred_effq restricted to the active-block slots [slot_base, slot_base + slot_count)
+ * (clipped to the device count): the sub-batches of Sec. III-B-2, so that the
+ * effective charge of a large batch is produced chunk by chunk.  qeff holds
+ * slot_count blocks; slot s is written at row s - slot_base.  The call with
+ * slot_base = 0 also computes the per-deposit weights that the later ranges of the
+ * same pass reuse: call it first. */
+int32_t tred_effq_range(tred_handle *h, int32_t n, const tred_deposits *deps,
+                        const int32_t *block_ids, const int32_t *dep_offsets,
+                        const int32_t *dep_index, const int32_t *n_blocks_dev, int32_t slot_base,
+                        int32_t slot_count, float *qeff, void *stream);
+
 /* a4. Interlaced convolution (Sec. II-D, Eq. interlaced; Sec. III-A-2, Eq. multch):
  *   I[P, t] = sum_j sum_K sum_tau Qeff[j, P + K, t - tau] i[j, K, tau]
  * for each active block, by FFT over the padded 16 x 16 x lt grid, with MPCP when
@@ -185,6 +209,13 @@ int32_t tred_effq(tred_handle *h, int32_t n, const tred_deposits *deps,
 int32_t tred_convolve(tred_handle *h, const int32_t *block_ids,
                       const int32_t *n_blocks_dev, const float *qeff, float *out_blocks,
                       void *stream);
+
+/* tred_convolve restricted to slots [slot_base, slot_base + slot_count): qeff is
+ * the chunk written by tred_effq_range with the same slot_base; out_blocks is
+ * indexed by absolute slot. */
+int32_t tred_convolve_range(tred_handle *h, const int32_t *block_ids, const int32_t *n_blocks_dev,
+                            int32_t slot_base, int32_t slot_count, const float *qeff,
+                            float *out_blocks, void *stream);
 
 /* a5. Electrode gather (Fig. flowchart: binning and accumulation onto the unique electrodes): every
  * in-plane pixel of an active block's output footprint is active; its waveform

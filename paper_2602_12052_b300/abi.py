@@ -33,6 +33,7 @@ EXPORTS = [
     "tred_set_response", "tred_drift", "tred_blockbin", "tred_effq", "tred_convolve",
     "tred_gather_pixels", "tred_readout", "tred_launch_count", "tred_blockbin_noalloc",
     "tred_set_transport", "tred_residual", "tred_adjoint", "tred_param_grads",
+    "tred_drift_events", "tred_effq_range", "tred_convolve_range",
 ]
 
 
@@ -40,7 +41,7 @@ class Geometry(ctypes.Structure):
     _fields_ = [("pitch_cm", ctypes.c_float), ("n_sub", ctypes.c_int32), ("tick_us", ctypes.c_float),
                 ("npx_x", ctypes.c_int32), ("npx_y", ctypes.c_int32), ("nt", ctypes.c_int32),
                 ("bp", ctypes.c_int32), ("bt", ctypes.c_int32), ("kp", ctypes.c_int32),
-                ("nr", ctypes.c_int32), ("lt", ctypes.c_int32)]
+                ("nr", ctypes.c_int32), ("lt", ctypes.c_int32), ("n_events", ctypes.c_int32)]
 
 
 class Params(ctypes.Structure):
@@ -95,6 +96,9 @@ def load(path: str | None = None) -> ctypes.CDLL:
     lib.tred_convolve.argtypes = [_P, _P, _P, _P, _P, _P]
     lib.tred_gather_pixels.argtypes = [_P, _P, _P, _P, _P, _P, _P, _P]
     lib.tred_readout.argtypes = [_P, ctypes.POINTER(ReadoutParams), _P, _P, _P, _P, _P, _P, _P, _I, _P]
+    lib.tred_drift_events.argtypes = [_P, _I, _P, _P, _P, _P, _P, _P, ctypes.POINTER(Deposits), _P]
+    lib.tred_effq_range.argtypes = [_P, _I, ctypes.POINTER(Deposits), _P, _P, _P, _P, _I, _I, _P, _P]
+    lib.tred_convolve_range.argtypes = [_P, _P, _P, _I, _I, _P, _P, _P]
     lib.tred_set_transport.argtypes = [_P, ctypes.POINTER(Params)]
     lib.tred_residual.argtypes = [_P, _P, _P, _P, _P, _I, _P, _P, _P, _P]
     lib.tred_adjoint.argtypes = [_P, _I, ctypes.POINTER(Deposits), _P, _P, _P, _P, _P, _P, _P, _P, _P, _P]

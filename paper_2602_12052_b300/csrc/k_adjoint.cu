@@ -76,6 +76,7 @@ __global__ void k_row_map(const int32_t *__restrict__ pix, const int32_t *__rest
 // ------------------------------------------------------------------ adjoint convolution
 struct AdjConst {
     int ns, bp, bt, nr, nt, nch, npairs, R, mpcp, nbx, nbt, npx_x, npx_y;
+    int npy_e, nby_e;              // pixel rows and block rows of one event
 };
 
 constexpr int AS_THREADS = 512;
@@ -108,6 +109,7 @@ __global__ void __launch_bounds__(AS_THREADS, 1)
         const int blk = block_ids[slot];
         const int bt = blk % c.nbt, bxy = blk / c.nbt, bx = bxy % c.nbx, by = bxy / c.nbx;
         const int T0 = bt * c.bt;
+        const int ylo = (by / c.nby_e) * c.npy_e, yhi = ylo + c.npy_e;   // the block's event band
         const float2 wl0 = tw[TW_LT + (k1 * lane) % LT];
         const float2 wl1 = tw[TW_LT + (k1 * (lane + 32)) % LT];
         const float2 w64l = tw[TW_64 + lane];
@@ -119,9 +121,9 @@ __global__ void __launch_bounds__(AS_THREADS, 1)
             const int uy2 = (c.bp - 1 + c.R - cy + 2 * LP) % LP, ux2 = (c.bp - 1 + c.R - cx + 2 * LP) % LP;
             const int Y1 = by * c.bp + uy1 - c.R, X1 = bx * c.bp + ux1 - c.R;
             const int Y2 = by * c.bp + uy2 - c.R, X2 = bx * c.bp + ux2 - c.R;
-            const int r1 = (uy1 < c.bp + 2 * c.R && ux1 < c.bp + 2 * c.R && Y1 >= 0 && Y1 < c.npx_y && X1 >= 0 &&
+            const int r1 = (uy1 < c.bp + 2 * c.R && ux1 < c.bp + 2 * c.R && Y1 >= ylo && Y1 < yhi && X1 >= 0 &&
                             X1 < c.npx_x) ? row_of[Y1 * c.npx_x + X1] : -1;
-            const int r2 = (c.mpcp && uy2 < c.bp + 2 * c.R && ux2 < c.bp + 2 * c.R && Y2 >= 0 && Y2 < c.npx_y &&
+            const int r2 = (c.mpcp && uy2 < c.bp + 2 * c.R && ux2 < c.bp + 2 * c.R && Y2 >= ylo && Y2 < yhi &&
                             X2 >= 0 && X2 < c.npx_x) ? row_of[Y2 * c.npx_x + X2] : -1;
             const float *a1 = r1 >= 0 ? resid + (size_t)r1 * c.nt + T0 : nullptr;
             const float *a2 = r2 >= 0 ? resid + (size_t)r2 * c.nt + T0 : nullptr;
@@ -295,6 +297,7 @@ __global__ void __launch_bounds__(256) k_adj_itime(const int32_t *__restrict__ n
 // ------------------------------------------------------------------ chain rule
 struct ChainConst {
     int ns, bp, bt, ngx, ngy, nt, nbx, nbt, wx, wt, wstride, nch, gl;
+    int ngy_e;                     // sub-cells of one event along y
     float xi[MAX_GL], wl[MAX_GL];
 };
 
@@ -362,6 +365,7 @@ __global__ void __launch_bounds__(256) k_adj_chain(const int32_t *__restrict__ b
                                                    const int32_t *__restrict__ dep_index,
                                                    const int32_t *__restrict__ n_blocks_dev, tred_deposits d,
                                                    ChainConst c, const float *__restrict__ wts2,
+                                                   const int32_t *__restrict__ dep_event,
                                                    const float *__restrict__ gq, float *__restrict__ grad7) {
     const int nb = n_blocks_dev[0];
     if (nb <= 0) return;
@@ -385,7 +389,8 @@ __global__ void __launch_bounds__(256) k_adj_chain(const int32_t *__restrict__ b
         const int lox = d.lo_x[i], hix = d.hi_x[i], loy = d.lo_y[i], hiy = d.hi_y[i];
         const int lot = d.lo_t[i], hit = d.hi_t[i];
         const int xa = max(max(lox - 1, 0), X0), xb = min(min(hix + 1, c.ngx - 1), X0 + side - 1);
-        const int ya = max(max(loy - 1, 0), Y0), yb = min(min(hiy + 1, c.ngy - 1), Y0 + side - 1);
+        const int ev = dep_event[i];
+        const int ya = max(max(loy - 1, ev * c.ngy_e), Y0), yb = min(min(hiy + 1, (ev + 1) * c.ngy_e - 1), Y0 + side - 1);
         const int ta = max(max(lot - 1, 0), T0), tb = min(min(hit + 1, c.nt - 1), T0 + c.bt - 1);
         if (xa > xb || ya > yb || ta > tb) continue;
         const float *w = wts2 + (size_t)i * 3 * c.wstride;
@@ -504,7 +509,7 @@ int launch_adjoint(tred_handle *h, int n, const tred_deposits &deps, const int32
                    const int32_t *dep_offsets, const int32_t *dep_index, const int32_t *n_blocks_dev,
                    const int32_t *pixel_ids, const int32_t *n_pixels_dev, const float *resid, float *gq,
                    float *grad7, cudaStream_t s) {
-    const int64_t npx = (int64_t)h->g.npx_x * h->g.npx_y;
+    const int64_t npx = (int64_t)h->g.npx_x * h->d.npy;
     int rc = check_cuda(h, cudaMemsetAsync(h->pix_row, 0xff, sizeof(int32_t) * npx, s), "clear rows");
     if (!rc) rc = check_cuda(h, cudaMemsetAsync(grad7, 0, sizeof(float) * 7 * (size_t)n, s), "clear grads");
     if (rc) return rc;
@@ -512,7 +517,7 @@ int launch_adjoint(tred_handle *h, int n, const tred_deposits &deps, const int32
     k_row_map<<<sms * 2, 256, 0, s>>>(pixel_ids, n_pixels_dev, h->pix_row);
     h->launches += 1;
     AdjConst c{h->g.n_sub, h->g.bp, h->g.bt, h->g.nr, h->g.nt, h->g.n_sub * h->g.n_sub, h->d.npairs, h->d.R,
-               h->p.mpcp, h->d.nbx, h->d.nbt, h->g.npx_x, h->g.npx_y};
+               h->p.mpcp, h->d.nbx, h->d.nbt, h->g.npx_x, h->d.npy, h->d.npy_e, h->d.nby_e};
     if (h->d.G == 8) rc = run_adjoint_conv<8>(h, block_ids, n_blocks_dev, resid, gq, c, s);
     else if (h->d.G == 16) rc = run_adjoint_conv<16>(h, block_ids, n_blocks_dev, resid, gq, c, s);
     else rc = set_error(h, TRED_ERR_INVALID_ARG, "adjoint: unsupported lt");
@@ -531,6 +536,7 @@ int launch_adjoint(tred_handle *h, int n, const tred_deposits &deps, const int32
     cc.wstride = h->d.wstride;
     cc.nch = h->g.n_sub * h->g.n_sub;
     cc.gl = h->p.gl_order;
+    cc.ngy_e = h->d.ngy_e;
     for (int l = 0; l < MAX_GL; ++l) {
         cc.xi[l] = l < cc.gl ? h->gl_xi[l] : 0.f;
         cc.wl[l] = l < cc.gl ? h->gl_wi[l] : 0.f;
@@ -538,7 +544,7 @@ int launch_adjoint(tred_handle *h, int n, const tred_deposits &deps, const int32
     if (n > 0) {
         k_adj_weights<<<(unsigned)(((int64_t)n * 32 + 255) / 256), 256, 0, s>>>(n, deps, cc, h->wts2);
         k_adj_chain<<<sms * 16, 256, 0, s>>>(block_ids, dep_offsets, dep_index, n_blocks_dev, deps, cc, h->wts2,
-                                             gq, grad7);
+                                             h->dep_event, gq, grad7);
         h->launches += 2;
     }
     return check_cuda(h, cudaGetLastError(), "adjoint launch");

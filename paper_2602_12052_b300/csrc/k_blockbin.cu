@@ -15,20 +15,23 @@ namespace tred {
 
 struct BinGeom {
     int ns, bp, bt, ngx, ngy, nt, nbx, nby, nbt;
+    int ngy_e;                      // sub-cells of one event along y
+    const int32_t *event;           // event of each deposit (nullptr: one event)
 };
 
 __device__ __forceinline__ bool support_box(const tred_deposits &d, int i, const BinGeom &g,
                                             int &bx0, int &bx1, int &by0, int &by1, int &bt0,
                                             int &bt1) {
+    const int ev = g.event ? g.event[i] : 0;
     int xa = d.lo_x[i] - 1, xb = d.hi_x[i] + 1;
     int ya = d.lo_y[i] - 1, yb = d.hi_y[i] + 1;
     int ta = d.lo_t[i] - 1, tb = d.hi_t[i] + 1;
     if (d.lo_x[i] > d.hi_x[i]) return false;   // dropped deposit
     xa = max(xa, 0);
-    ya = max(ya, 0);
+    ya = max(ya, ev * g.ngy_e);
     ta = max(ta, 0);
     xb = min(xb, g.ngx - 1);
-    yb = min(yb, g.ngy - 1);
+    yb = min(yb, (ev + 1) * g.ngy_e - 1);
     tb = min(tb, g.nt - 1);
     if (xa > xb || ya > yb || ta > tb) return false;
     bx0 = (xa / g.ns) / g.bp;
@@ -229,7 +232,8 @@ __global__ void k_bb_offsets0(int32_t *dep_offsets, const int32_t *n_blocks_dev)
 int launch_blockbin(tred_handle *h, int n, const tred_deposits &deps, int32_t *block_ids,
                     int32_t *block_counts, int32_t *dep_offsets, int32_t *dep_index,
                     int32_t max_pairs, int32_t *n_blocks_dev, cudaStream_t s) {
-    BinGeom g{h->g.n_sub, h->g.bp, h->g.bt, h->d.ngx, h->d.ngy, h->g.nt, h->d.nbx, h->d.nby, h->d.nbt};
+    BinGeom g{h->g.n_sub, h->g.bp, h->g.bt, h->d.ngx, h->d.ngy, h->g.nt, h->d.nbx, h->d.nby, h->d.nbt,
+              h->d.ngy_e, h->dep_event};
     int rc = check_cuda(h, cudaMemsetAsync(h->blk_count, 0, sizeof(int32_t) * h->d.nblk, s), "clear counts");
     if (rc) return rc;
     if (n > 0) k_bb_count<<<(n + 255) / 256, 256, 0, s>>>(n, deps, g, h->blk_count);
@@ -294,6 +298,7 @@ extern "C" int32_t tred_blockbin_noalloc(const tred_geometry *geom, int32_t n, c
         max_blocks < 1 || max_pairs < 0 || (max_pairs > 0 && !dep_index) || (n > 0 && !deps))
         return TRED_ERR_INVALID_ARG;
     const tred_geometry &g = *geom;
+    if (g.n_events > 1) return TRED_ERR_INVALID_ARG;   // single event only
     if (g.n_sub < 1 || g.bp < 1 || g.bt < 1 || g.npx_x < g.bp || g.npx_y < g.bp || g.npx_x % g.bp ||
         g.npx_y % g.bp || g.nt < g.bt || g.nt % g.bt)
         return TRED_ERR_INVALID_ARG;
@@ -315,7 +320,8 @@ extern "C" int32_t tred_blockbin_noalloc(const tred_geometry *geom, int32_t n, c
     int32_t *part = fill + NOALLOC_MAX_GRID_BLOCKS;
     const int64_t nchunks = (nblk + 1023) / 1024;
     cudaStream_t s = (cudaStream_t)stream;
-    BinGeom bg{g.n_sub, g.bp, g.bt, g.npx_x * g.n_sub, g.npx_y * g.n_sub, g.nt, (int)nbx, (int)nby, (int)nbt};
+    BinGeom bg{g.n_sub, g.bp, g.bt, g.npx_x * g.n_sub, g.npx_y * g.n_sub, g.nt, (int)nbx, (int)nby, (int)nbt,
+               g.npx_y * g.n_sub, nullptr};
     if (cudaMemsetAsync(count, 0, sizeof(int32_t) * nblk, s) != cudaSuccess) return TRED_ERR_CUDA;
     if (n > 0) k_bb_count<<<(n + 255) / 256, 256, 0, s>>>(n, *deps, bg, count);
     k_bb_chunk<<<(unsigned)nchunks, 1024, 0, s>>>(nblk, count, part, nchunks);

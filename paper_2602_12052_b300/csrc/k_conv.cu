@@ -53,7 +53,7 @@ __global__ void __launch_bounds__(SPEC_THREADS, 1)
     k_conv_spec(const int32_t *__restrict__ n_blocks_dev, const float *__restrict__ qeff,
                 const uint64_t *__restrict__ colmask, const float2 *__restrict__ rhat,
                 const int32_t *__restrict__ pair_j, const float2 *__restrict__ tw, ConvConst c,
-                float2 *__restrict__ yspec, int slot_base, int slot_count) {
+                float2 *__restrict__ yspec, int slot_base, int slot_count, int qbase) {
     constexpr int LT = 64 * G;
     extern __shared__ float2 smem[];
     float2 *acc = smem;                               // [64][16 kx][18]
@@ -92,7 +92,7 @@ __global__ void __launch_bounds__(SPEC_THREADS, 1)
         for (int k = tid; k < BINS * ACC_BIN; k += SPEC_THREADS) acc[k] = make_float2(0.f, 0.f);
         __syncthreads();
 
-        const float *qblk = qeff + (size_t)slot * c.nch * slab;
+        const float *qblk = qeff + (size_t)(slot - qbase) * c.nch * slab;
         const uint64_t *mrow = colmask + (size_t)slot * c.nch;
         for (int p = 0; p < c.npairs; ++p) {
             const int j1 = pair_j[2 * p], j2 = pair_j[2 * p + 1];
@@ -310,7 +310,7 @@ __global__ void __launch_bounds__(256) k_conv_itime(const int32_t *__restrict__ 
 
 template <int NB1, int G>
 static int run_conv(tred_handle *h, const int32_t *n_blocks_dev, const float *qeff, float *out,
-                    const ConvConst &c, cudaStream_t s) {
+                    const ConvConst &c, int slot_base, int slot_count, cudaStream_t s) {
     static bool attr = false;
     const size_t itime_smem = sizeof(float2) * (16 * (64 * G + 1) + 64 * G + 32 + 64 * G / 32);
     if (!attr) {
@@ -320,17 +320,20 @@ static int run_conv(tred_handle *h, const int32_t *n_blocks_dev, const float *qe
     }
     const int sms = num_sms(h);
     const int chunk = h->yspec_blocks;
-    for (int base = 0; base < h->max_blocks; base += chunk) {
+    const int end = slot_base + slot_count;
+    for (int base = slot_base; base < end; base += chunk) {
+        const int cnt = chunk < end - base ? chunk : end - base;
         k_conv_spec<NB1, G><<<sms, SPEC_THREADS, SPEC_SMEM, s>>>(n_blocks_dev, qeff, h->colmask, h->rhat,
-                                                                 h->pair_j, h->tw, c, h->yspec, base, chunk);
-        k_conv_itime<G><<<sms * 2, 256, itime_smem, s>>>(n_blocks_dev, h->yspec, h->tw, c, out, base, chunk);
+                                                                 h->pair_j, h->tw, c, h->yspec, base, cnt,
+                                                                 slot_base);
+        k_conv_itime<G><<<sms * 2, 256, itime_smem, s>>>(n_blocks_dev, h->yspec, h->tw, c, out, base, cnt);
         h->launches += 2;
     }
     return check_cuda(h, cudaGetLastError(), "convolve launch");
 }
 
 int launch_convolve(tred_handle *h, const int32_t *block_ids, const int32_t *n_blocks_dev,
-                    const float *qeff, float *out, cudaStream_t s) {
+                    const float *qeff, float *out, int slot_base, int slot_count, cudaStream_t s) {
     (void)block_ids;
     ConvConst c;
     c.ns = h->g.n_sub;
@@ -345,20 +348,22 @@ int launch_convolve(tred_handle *h, const int32_t *block_ids, const int32_t *n_b
     const int nb1 = h->g.bt / 64;
     if (c.G == 8) {
         switch (nb1) {
-            case 1: return run_conv<1, 8>(h, n_blocks_dev, qeff, out, c, s);
-            case 2: return run_conv<2, 8>(h, n_blocks_dev, qeff, out, c, s);
-            case 3: return run_conv<3, 8>(h, n_blocks_dev, qeff, out, c, s);
-            case 4: return run_conv<4, 8>(h, n_blocks_dev, qeff, out, c, s);
-            case 5: return run_conv<5, 8>(h, n_blocks_dev, qeff, out, c, s);
-            case 6: return run_conv<6, 8>(h, n_blocks_dev, qeff, out, c, s);
-            case 7: return run_conv<7, 8>(h, n_blocks_dev, qeff, out, c, s);
+            case 1: return run_conv<1, 8>(h, n_blocks_dev, qeff, out, c, slot_base, slot_count, s);
+            case 2: return run_conv<2, 8>(h, n_blocks_dev, qeff, out, c, slot_base, slot_count, s);
+            case 3: return run_conv<3, 8>(h, n_blocks_dev, qeff, out, c, slot_base, slot_count, s);
+            case 4: return run_conv<4, 8>(h, n_blocks_dev, qeff, out, c, slot_base, slot_count, s);
+            case 5: return run_conv<5, 8>(h, n_blocks_dev, qeff, out, c, slot_base, slot_count, s);
+            case 6: return run_conv<6, 8>(h, n_blocks_dev, qeff, out, c, slot_base, slot_count, s);
+            case 7: return run_conv<7, 8>(h, n_blocks_dev, qeff, out, c, slot_base, slot_count, s);
             default: break;
         }
     } else if (c.G == 16) {
         switch (nb1) {
-            case 2: return run_conv<2, 16>(h, n_blocks_dev, qeff, out, c, s);
-            case 4: return run_conv<4, 16>(h, n_blocks_dev, qeff, out, c, s);
-            case 8: return run_conv<8, 16>(h, n_blocks_dev, qeff, out, c, s);
+            case 2: return run_conv<2, 16>(h, n_blocks_dev, qeff, out, c, slot_base, slot_count, s);
+            case 4: return run_conv<4, 16>(h, n_blocks_dev, qeff, out, c, slot_base, slot_count, s);
+            case 5: return run_conv<5, 16>(h, n_blocks_dev, qeff, out, c, slot_base, slot_count, s);
+            case 8: return run_conv<8, 16>(h, n_blocks_dev, qeff, out, c, slot_base, slot_count, s);
+            case 10: return run_conv<10, 16>(h, n_blocks_dev, qeff, out, c, slot_base, slot_count, s);
             default: break;
         }
     }

@@ -11,20 +11,25 @@ namespace tred {
 
 struct DriftConst {
     double v, tick, h, width_x, width_y, DT, DL, s0, s0t, ns, tau, max_td;
+    int n_events, ngy_e;
 };
 
 __global__ void __launch_bounds__(256) k_drift(int n, const float *__restrict__ x,
                                                const float *__restrict__ y,
                                                const float *__restrict__ z,
                                                const float *__restrict__ t0,
-                                               const float *__restrict__ ne, DriftConst c,
-                                               tred_deposits out, int32_t *status) {
+                                               const float *__restrict__ ne,
+                                               const int32_t *__restrict__ event, DriftConst c,
+                                               tred_deposits out, int32_t *__restrict__ dep_event,
+                                               int32_t *status) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     const double xd = x[i], yd = y[i], zd = z[i], t0d = t0[i], ned = ne[i];
+    const int ev = event ? event[i] : 0;
+    dep_event[i] = ev;
     const bool ok = isfinite(xd) && isfinite(yd) && isfinite(zd) && isfinite(t0d) && isfinite(ned) &&
                     zd >= 0.0 && ned >= 0.0 && xd >= 0.0 && xd < c.width_x && yd >= 0.0 &&
-                    yd < c.width_y;
+                    yd < c.width_y && ev >= 0 && ev < c.n_events;
     const double td = __ddiv_rn(zd, c.v);
     if (!ok || !(td <= c.max_td)) {
         if (ok) atomicOr(&status[0], TRED_ST_DRIFT_RANGE);
@@ -63,21 +68,24 @@ __global__ void __launch_bounds__(256) k_drift(int n, const float *__restrict__ 
     float *sig[3] = {out.sigma_x, out.sigma_y, out.sigma_t};
     int32_t *lo[3] = {out.lo_x, out.lo_y, out.lo_t};
     int32_t *hi[3] = {out.hi_x, out.hi_y, out.hi_t};
+    // event-local window; events are stacked along y by whole cells
+    const int shift[3] = {0, ev * c.ngy_e, 0};
 #pragma unroll
     for (int ax = 0; ax < 3; ++ax) {
         const double K = __dmul_rn(c.ns, sg[ax]);
         const double fl = floor(mu[ax]);
-        cell[ax][i] = (int32_t)fl;
+        cell[ax][i] = (int32_t)fl + shift[ax];
         frac[ax][i] = (float)(mu[ax] - fl);   // exact in binary64, then rounded
         sig[ax][i] = (float)sg[ax];
-        lo[ax][i] = (int32_t)floor(__dadd_rn(mu[ax], -K));
-        hi[ax][i] = (int32_t)ceil(__dadd_rn(mu[ax], K));
+        lo[ax][i] = (int32_t)floor(__dadd_rn(mu[ax], -K)) + shift[ax];
+        hi[ax][i] = (int32_t)ceil(__dadd_rn(mu[ax], K)) + shift[ax];
     }
     out.q[i] = (float)(ned * exp(-td / c.tau));
 }
 
 int launch_drift(tred_handle *h, int n, const float *x, const float *y, const float *z,
-                 const float *t0, const float *ne, const tred_deposits &out, cudaStream_t s) {
+                 const float *t0, const float *ne, const int32_t *event, const tred_deposits &out,
+                 cudaStream_t s) {
     DriftConst c;
     c.v = (double)h->p.v_cm_per_us;
     c.tick = (double)h->g.tick_us;
@@ -91,7 +99,9 @@ int launch_drift(tred_handle *h, int n, const float *x, const float *y, const fl
     c.ns = (double)h->p.nsigma;
     c.tau = (double)h->p.lifetime_us;
     c.max_td = (double)h->p.max_drift_cm / (double)h->p.v_cm_per_us;
-    k_drift<<<(n + 255) / 256, 256, 0, s>>>(n, x, y, z, t0, ne, c, out, h->status);
+    c.n_events = h->d.n_events;
+    c.ngy_e = h->d.ngy_e;
+    k_drift<<<(n + 255) / 256, 256, 0, s>>>(n, x, y, z, t0, ne, event, c, out, h->dep_event, h->status);
     h->launches += 1;
     return check_cuda(h, cudaGetLastError(), "k_drift launch");
 }

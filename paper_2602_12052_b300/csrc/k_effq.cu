@@ -33,6 +33,7 @@ static_assert(sizeof(DepRec) == 48, "record size is part of the scratch layout")
 
 struct EffqConst {
     int ns, bp, bt, ngx, ngy, nt, nbx, nbt, wx, wt, wstride, gl, mode;
+    int ngy_e;                     // sub-cells of one event along y
     int cols_log2;                 // log2(bp * bp)
     float xi[MAX_GL], wl[MAX_GL];
 };
@@ -100,6 +101,7 @@ __device__ float weight_tent(int g, int cell, float frac, float sig, int lo, int
 }
 
 __global__ void __launch_bounds__(256) k_effq_weights(int n, tred_deposits d, EffqConst c,
+                                                      const int32_t *__restrict__ dep_event,
                                                       float *__restrict__ wts, DepRec *__restrict__ recs) {
     const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
@@ -118,8 +120,9 @@ __global__ void __launch_bounds__(256) k_effq_weights(int n, tred_deposits d, Ef
         r.gt0 = lo[2] - 1;
         r.x0 = max(lo[0] - 1, 0);
         r.x1 = min(hi[0] + 1, c.ngx - 1);
-        r.y0 = max(lo[1] - 1, 0);
-        r.y1 = min(hi[1] + 1, c.ngy - 1);
+        const int ev = dep_event[i];
+        r.y0 = max(lo[1] - 1, ev * c.ngy_e);
+        r.y1 = min(hi[1] + 1, (ev + 1) * c.ngy_e - 1);
         r.t0 = max(lo[2] - 1, 0);
         r.t1 = min(hi[2] + 1, c.nt - 1);
         r.q = d.q[i];
@@ -161,7 +164,8 @@ __global__ void __launch_bounds__(EQ_THREADS, 1) k_effq_blocks(const int32_t *__
                                                             EffqConst c, const float *__restrict__ wts,
                                                             const DepRec *__restrict__ recs,
                                                             float *__restrict__ qeff,
-                                                            uint64_t *__restrict__ colmask) {
+                                                            uint64_t *__restrict__ colmask, int slot_base,
+                                                            int slot_count) {
     extern __shared__ float smem_e[];
     const int nch = c.ns * c.ns;
     const int cols = c.bp * c.bp;
@@ -175,11 +179,12 @@ __global__ void __launch_bounds__(EQ_THREADS, 1) k_effq_blocks(const int32_t *__
         const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
         for (int k = tid; k < plane * (EQ_TT / 4); k += EQ_THREADS) reinterpret_cast<float4 *>(tile)[k] = z4;
     }
-    const int nb = n_blocks_dev[0];
-    for (int slot = blockIdx.x; slot < nb; slot += gridDim.x) {
+    const int nb = min(n_blocks_dev[0], slot_base + slot_count);
+    for (int slot = slot_base + blockIdx.x; slot < nb; slot += gridDim.x) {
         const int blk = block_ids[slot];
         const int bt = blk % c.nbt, bxy = blk / c.nbt, bx = bxy % c.nbx, by = bxy / c.nbx;
         const int X0 = bx * side, Y0 = by * side, T0 = bt * c.bt;
+        const size_t qslot = (size_t)(slot - slot_base);   // row of the caller's qeff buffer
         const int beg = dep_offsets[slot], end = dep_offsets[slot + 1];
         const int passes = max(1, (end - beg + EQ_CACHE - 1) / EQ_CACHE);
         for (int k = tid; k < nch; k += EQ_THREADS) mask[k] = 0ull;
@@ -238,7 +243,7 @@ __global__ void __launch_bounds__(EQ_THREADS, 1) k_effq_blocks(const int32_t *__
                         any |= v[e] != 0.f;
                     }
                     if (any) nz |= 1u << bit;
-                    float4 *dst = reinterpret_cast<float4 *>(qeff + (((size_t)slot * nch + ch) * cols + col) * c.bt + tt);
+                    float4 *dst = reinterpret_cast<float4 *>(qeff + ((qslot * nch + ch) * cols + col) * c.bt + tt);
                     dst[0] = make_float4(v[0], v[1], v[2], v[3]);
                     dst[1] = make_float4(v[4], v[5], v[6], v[7]);
                 }
@@ -259,13 +264,14 @@ __global__ void __launch_bounds__(EQ_THREADS, 1) k_effq_blocks(const int32_t *__
 
 int launch_effq(tred_handle *h, int n, const tred_deposits &deps, const int32_t *block_ids,
                 const int32_t *dep_offsets, const int32_t *dep_index, const int32_t *n_blocks_dev,
-                float *qeff, cudaStream_t s) {
+                float *qeff, int slot_base, int slot_count, cudaStream_t s) {
     EffqConst c;
     c.ns = h->g.n_sub;
     c.bp = h->g.bp;
     c.bt = h->g.bt;
     c.ngx = h->d.ngx;
     c.ngy = h->d.ngy;
+    c.ngy_e = h->d.ngy_e;
     c.nt = h->g.nt;
     c.nbx = h->d.nbx;
     c.nbt = h->d.nbt;
@@ -279,10 +285,11 @@ int launch_effq(tred_handle *h, int n, const tred_deposits &deps, const int32_t 
         c.xi[l] = l < c.gl ? h->gl_xi[l] : 0.f;
         c.wl[l] = l < c.gl ? h->gl_wi[l] : 0.f;
     }
-    if (n > 0) {
+    if (n > 0 && slot_base == 0) {   // once per pass: the range starting at slot 0 computes the weights
         const int threads = 256;
         const int64_t blocks = ((int64_t)n * 32 + threads - 1) / threads;
-        k_effq_weights<<<(unsigned)blocks, threads, 0, s>>>(n, deps, c, h->wts, reinterpret_cast<DepRec *>(h->recs));
+        k_effq_weights<<<(unsigned)blocks, threads, 0, s>>>(n, deps, c, h->dep_event, h->wts,
+                                                             reinterpret_cast<DepRec *>(h->recs));
     }
     const int nch = c.ns * c.ns;
     const size_t smem = sizeof(float) * (size_t)nch * c.bp * c.bp * EQ_TT + sizeof(DepRec) * EQ_CACHE +
@@ -296,8 +303,9 @@ int launch_effq(tred_handle *h, int n, const tred_deposits &deps, const int32_t 
         return set_error(h, TRED_ERR_INVALID_ARG, "effq: tile of n_sub^2 bp^2 x 8 ticks exceeds shared memory");
     const int grid = num_sms(h);
     k_effq_blocks<<<grid, EQ_THREADS, smem, s>>>(block_ids, dep_offsets, dep_index, n_blocks_dev, c, h->wts,
-                                                 reinterpret_cast<const DepRec *>(h->recs), qeff, h->colmask);
-    h->launches += 1 + (n > 0 ? 1 : 0);
+                                                 reinterpret_cast<const DepRec *>(h->recs), qeff, h->colmask,
+                                                 slot_base, slot_count);
+    h->launches += 1 + (n > 0 && slot_base == 0 ? 1 : 0);
     return check_cuda(h, cudaGetLastError(), "effq launch");
 }
 

@@ -15,6 +15,7 @@ namespace tred {
 
 struct GatherConst {
     int npx_x, npx_y, nt, bp, bt, nr, lt, R, nbx, nby, nbt, comp;
+    int npy_e, nby_e;              // pixel rows and block rows of one event
 };
 
 __global__ void k_px_mark(const int32_t *__restrict__ block_ids, const int32_t *__restrict__ n_blocks_dev,
@@ -29,7 +30,8 @@ __global__ void k_px_mark(const int32_t *__restrict__ block_ids, const int32_t *
         const int blk = block_ids[slot];
         const int bxy = blk / c.nbt, bx = bxy % c.nbx, by = bxy / c.nbx;
         const int x = bx * c.bp - c.R + r % side, y = by * c.bp - c.R + r / side;
-        if (x >= 0 && x < c.npx_x && y >= 0 && y < c.npx_y) flags[(int64_t)y * c.npx_x + x] = 1;
+        const int ev = by / c.nby_e;
+        if (x >= 0 && x < c.npx_x && y >= ev * c.npy_e && y < (ev + 1) * c.npy_e) flags[(int64_t)y * c.npx_x + x] = 1;
     }
 }
 
@@ -145,7 +147,9 @@ __global__ void __launch_bounds__(256) k_px_wave(const int32_t *__restrict__ pix
         const int pid = pixel_ids[row];
         const int x = pid % c.npx_x, y = pid / c.npx_x;
         const int bx_lo = max(0, floordiv(x - c.bp - c.R, c.bp) + 1), bx_hi = min(c.nbx - 1, floordiv(x + c.R, c.bp));
-        const int by_lo = max(0, floordiv(y - c.bp - c.R, c.bp) + 1), by_hi = min(c.nby - 1, floordiv(y + c.R, c.bp));
+        const int ev = y / c.npy_e;
+        const int by_lo = max(ev * c.nby_e, floordiv(y - c.bp - c.R, c.bp) + 1);
+        const int by_hi = min((ev + 1) * c.nby_e - 1, floordiv(y + c.R, c.bp));
         float *dst = wave + (size_t)row * c.nt;
         for (int T0 = 0; T0 < c.nt; T0 += 128) {
             const int t = T0 + 4 * lane;
@@ -198,9 +202,9 @@ __global__ void k_slot_map(const int32_t *__restrict__ block_ids, const int32_t 
 int launch_gather(tred_handle *h, const int32_t *block_ids, const int32_t *n_blocks_dev,
                   const float *out, int32_t *pixel_ids, float *wave, int32_t *n_pixels_dev,
                   cudaStream_t s) {
-    GatherConst c{h->g.npx_x, h->g.npx_y, h->g.nt, h->g.bp, h->g.bt, h->g.nr, h->g.lt, h->d.R,
-                  h->d.nbx, h->d.nby, h->d.nbt, h->p.compensated_gather};
-    const int64_t npx = (int64_t)h->g.npx_x * h->g.npx_y;
+    GatherConst c{h->g.npx_x, h->d.npy, h->g.nt, h->g.bp, h->g.bt, h->g.nr, h->g.lt, h->d.R,
+                  h->d.nbx, h->d.nby, h->d.nbt, h->p.compensated_gather, h->d.npy_e, h->d.nby_e};
+    const int64_t npx = (int64_t)h->g.npx_x * h->d.npy;
     int rc = check_cuda(h, cudaMemsetAsync(h->pix_flag, 0, sizeof(int32_t) * npx, s), "clear pixel flags");
     if (rc) return rc;
     const int sms = num_sms(h);

@@ -87,7 +87,9 @@ static int validate(const tred_geometry *g, const tred_params *p, char *msg, siz
     if (g->npx_x < g->bp || g->npx_y < g->bp || g->npx_x % g->bp || g->npx_y % g->bp)
         return bad("plane must be a multiple of bp pixels");
     if (g->nt < g->bt || g->nt % g->bt) return bad("nt must be a multiple of bt");
-    if ((int64_t)g->npx_x * g->n_sub > (1 << 28) || (int64_t)g->npx_y * g->n_sub > (1 << 28))
+    if (g->n_events < 0 || g->n_events > 4096) return bad("n_events must be in [0, 4096]");
+    if ((int64_t)g->npx_x * g->n_sub > (1 << 28) ||
+        (int64_t)g->npx_y * g->n_sub * (g->n_events > 1 ? g->n_events : 1) > (1 << 28))
         return bad("plane too large");
     if (!(p->v_cm_per_us > 0 && p->lifetime_us > 0 && p->DL_cm2_per_s >= 0 && p->DT_cm2_per_s >= 0))
         return bad("bad transport constants");
@@ -123,9 +125,14 @@ int32_t tred_create(const tred_geometry *geom, const tred_params *params, int32_
     Derived &d = h->d;
     d.h = (double)geom->pitch_cm / (double)geom->n_sub;
     d.ngx = geom->npx_x * geom->n_sub;
-    d.ngy = geom->npx_y * geom->n_sub;
+    d.n_events = geom->n_events > 1 ? geom->n_events : 1;
+    d.ngy_e = geom->npx_y * geom->n_sub;
+    d.nby_e = geom->npx_y / geom->bp;
+    d.npy_e = geom->npx_y;
+    d.npy = geom->npx_y * d.n_events;
+    d.ngy = d.ngy_e * d.n_events;
     d.nbx = geom->npx_x / geom->bp;
-    d.nby = geom->npx_y / geom->bp;
+    d.nby = d.nby_e * d.n_events;
     d.nbt = geom->nt / geom->bt;
     d.nblk = (int64_t)d.nbx * d.nby * d.nbt;
     d.R = (geom->kp - 1) / 2;
@@ -164,6 +171,7 @@ int32_t tred_create(const tred_geometry *geom, const tred_params *params, int32_
     const int G = d.G, NP = d.npairs, ns = geom->n_sub;
     alloc((void **)&h->rhat, sizeof(float2) * (size_t)G * NP * BINS * LP * LP, "alloc spectrum");
     alloc((void **)&h->pair_j, sizeof(int32_t) * 2 * NP, "alloc pairs");
+    alloc((void **)&h->dep_event, sizeof(int32_t) * (size_t)max_deposits, "alloc deposit events");
     alloc((void **)&h->wts, sizeof(float) * (size_t)max_deposits * d.wstride, "alloc weights");
     alloc((void **)&h->recs, 48 * (size_t)max_deposits, "alloc deposit records");
     alloc((void **)&h->blk_count, sizeof(int32_t) * (size_t)d.nblk, "alloc block counts");
@@ -174,8 +182,8 @@ int32_t tred_create(const tred_geometry *geom, const tred_params *params, int32_
     alloc((void **)&h->colmask, sizeof(uint64_t) * (size_t)max_blocks * ns * ns, "alloc masks");
     h->yspec_blocks = max_blocks < 1024 ? max_blocks : 1024;
     alloc((void **)&h->yspec, sizeof(float2) * (size_t)h->yspec_blocks * geom->lt * LP * LP, "alloc yspec");
-    alloc((void **)&h->pix_flag, sizeof(int32_t) * (size_t)geom->npx_x * geom->npx_y, "alloc pixel flags");
-    h->pix_chunks = ((int64_t)geom->npx_x * geom->npx_y + 1023) / 1024;
+    alloc((void **)&h->pix_flag, sizeof(int32_t) * (size_t)geom->npx_x * d.npy, "alloc pixel flags");
+    h->pix_chunks = ((int64_t)geom->npx_x * d.npy + 1023) / 1024;
     alloc((void **)&h->pix_part, sizeof(int32_t) * (size_t)(h->pix_chunks + 8), "alloc pixel scan");
     alloc((void **)&h->hit_cnt, sizeof(int32_t) * ((size_t)max_pixels + 8), "alloc hit counts");
     alloc((void **)&h->hit_tmp, sizeof(int32_t) * (size_t)max_pixels * HIT_TMP, "alloc hit cache");
@@ -226,7 +234,7 @@ int32_t tred_create(const tred_geometry *geom, const tred_params *params, int32_
 
 int32_t tred_destroy(tred_handle *h) {
     if (!h) return TRED_ERR_INVALID_ARG;
-    void *ptrs[] = {h->wts2, h->pix_row, h->gspec, h->rhat, h->pair_j, h->wts, h->recs, h->blk_count, h->blk_slot, h->blk_fill,
+    void *ptrs[] = {h->dep_event, h->wts2, h->pix_row, h->gspec, h->rhat, h->pair_j, h->wts, h->recs, h->blk_count, h->blk_slot, h->blk_fill,
                     h->scan_part, h->colmask, h->yspec, h->pix_flag, h->pix_part, h->hit_cnt,
                     h->hit_tmp, h->hit_tmpc, h->status, h->tw};
     for (void *p : ptrs)
@@ -294,7 +302,7 @@ int32_t tred_adjoint(tred_handle *h, int32_t n, const tred_deposits *deps, const
     if (!h->wts2) {   // first call: adjoint scratch
         h->adj_chunk = h->max_blocks < 32 ? h->max_blocks : 32;
         const size_t b1 = sizeof(float) * 3 * (size_t)h->max_deposits * h->d.wstride;
-        const size_t b2 = sizeof(int32_t) * (size_t)h->g.npx_x * h->g.npx_y;
+        const size_t b2 = sizeof(int32_t) * (size_t)h->g.npx_x * h->d.npy;
         const size_t b3 = sizeof(float2) * (size_t)h->adj_chunk * h->d.npairs * h->g.lt * 64;
         int rc = check_cuda(h, cudaMalloc(&h->wts2, b1), "alloc adjoint weights");
         if (!rc) rc = check_cuda(h, cudaMalloc(&h->pix_row, b2), "alloc pixel rows");
@@ -343,7 +351,20 @@ int32_t tred_drift(tred_handle *h, int32_t n, const float *x, const float *y, co
     if (n > 0 && (!x || !y || !z || !t0 || !ne || !deps_ok(out)))
         return set_error(h, TRED_ERR_INVALID_ARG, "tred_drift: null pointer");
     if (n == 0) return TRED_OK;
-    return launch_drift(h, n, x, y, z, t0, ne, *out, (cudaStream_t)stream);
+    return launch_drift(h, n, x, y, z, t0, ne, nullptr, *out, (cudaStream_t)stream);
+}
+
+int32_t tred_drift_events(tred_handle *h, int32_t n, const float *x, const float *y, const float *z,
+                          const float *t0, const float *ne, const int32_t *event, const tred_deposits *out,
+                          void *stream) {
+    if (!h) return TRED_ERR_INVALID_ARG;
+    if (n < 0 || n > h->max_deposits)
+        return set_error(h, TRED_ERR_CAPACITY, "tred_drift_events: n=%d outside [0, max_deposits=%d]", n,
+                         h->max_deposits);
+    if (n > 0 && (!x || !y || !z || !t0 || !ne || !event || !deps_ok(out)))
+        return set_error(h, TRED_ERR_INVALID_ARG, "tred_drift_events: null pointer");
+    if (n == 0) return TRED_OK;
+    return launch_drift(h, n, x, y, z, t0, ne, event, *out, (cudaStream_t)stream);
 }
 
 int32_t tred_blockbin(tred_handle *h, int32_t n, const tred_deposits *deps, int32_t *block_ids,
@@ -368,7 +389,20 @@ int32_t tred_effq(tred_handle *h, int32_t n, const tred_deposits *deps, const in
     if ((n > 0 && !deps_ok(deps)) || !block_ids || !dep_offsets || !n_blocks_dev || !qeff)
         return set_error(h, TRED_ERR_INVALID_ARG, "tred_effq: null pointer");
     return launch_effq(h, n, n > 0 ? *deps : tred_deposits{}, block_ids, dep_offsets, dep_index,
-                       n_blocks_dev, qeff, (cudaStream_t)stream);
+                       n_blocks_dev, qeff, 0, h->max_blocks, (cudaStream_t)stream);
+}
+
+int32_t tred_effq_range(tred_handle *h, int32_t n, const tred_deposits *deps, const int32_t *block_ids,
+                        const int32_t *dep_offsets, const int32_t *dep_index, const int32_t *n_blocks_dev,
+                        int32_t slot_base, int32_t slot_count, float *qeff, void *stream) {
+    if (!h) return TRED_ERR_INVALID_ARG;
+    if (n < 0 || n > h->max_deposits)
+        return set_error(h, TRED_ERR_CAPACITY, "tred_effq_range: n=%d outside [0, max_deposits]", n);
+    if ((n > 0 && !deps_ok(deps)) || !block_ids || !dep_offsets || !n_blocks_dev || !qeff || slot_base < 0 ||
+        slot_count < 0)
+        return set_error(h, TRED_ERR_INVALID_ARG, "tred_effq_range: bad arguments");
+    return launch_effq(h, n, n > 0 ? *deps : tred_deposits{}, block_ids, dep_offsets, dep_index, n_blocks_dev,
+                       qeff, slot_base, slot_count, (cudaStream_t)stream);
 }
 
 int32_t tred_convolve(tred_handle *h, const int32_t *block_ids, const int32_t *n_blocks_dev,
@@ -378,7 +412,19 @@ int32_t tred_convolve(tred_handle *h, const int32_t *block_ids, const int32_t *n
         return set_error(h, TRED_ERR_NOT_READY, "tred_convolve: call tred_set_response first");
     if (!block_ids || !n_blocks_dev || !qeff || !out_blocks)
         return set_error(h, TRED_ERR_INVALID_ARG, "tred_convolve: null pointer");
-    return launch_convolve(h, block_ids, n_blocks_dev, qeff, out_blocks, (cudaStream_t)stream);
+    return launch_convolve(h, block_ids, n_blocks_dev, qeff, out_blocks, 0, h->max_blocks, (cudaStream_t)stream);
+}
+
+int32_t tred_convolve_range(tred_handle *h, const int32_t *block_ids, const int32_t *n_blocks_dev,
+                            int32_t slot_base, int32_t slot_count, const float *qeff, float *out_blocks,
+                            void *stream) {
+    if (!h) return TRED_ERR_INVALID_ARG;
+    if (!h->response_ready)
+        return set_error(h, TRED_ERR_NOT_READY, "tred_convolve_range: call tred_set_response first");
+    if (!block_ids || !n_blocks_dev || !qeff || !out_blocks || slot_base < 0 || slot_count < 0)
+        return set_error(h, TRED_ERR_INVALID_ARG, "tred_convolve_range: bad arguments");
+    return launch_convolve(h, block_ids, n_blocks_dev, qeff, out_blocks, slot_base, slot_count,
+                           (cudaStream_t)stream);
 }
 
 int32_t tred_gather_pixels(tred_handle *h, const int32_t *block_ids, const int32_t *n_blocks_dev,

@@ -16,8 +16,11 @@ constexpr int BINS = 64;             // time-frequency bins owned by one conv CT
 constexpr int MAX_GL = 8;
 
 struct Derived {
-    int ngx, ngy;          // sub-cell grid size
-    int nbx, nby, nbt;     // blocks per axis
+    int ngx, ngy;          // sub-cell grid size (y: all events)
+    int nbx, nby, nbt;     // blocks per axis (y: all events)
+    int n_events;          // events stacked along y
+    int ngy_e, nby_e, npy_e;  // sub-cells, blocks and pixels of one event along y
+    int npy;               // pixel rows of all events
     int64_t nblk;          // blocks in the plane
     int R;                 // response half width in pixels
     int G;                 // time-frequency classes = lt / 64
@@ -39,6 +42,7 @@ struct tred_handle {
     // device memory owned by the handle
     float2 *rhat;          // [G][npairs][64][16*16] response spectrum
     int32_t *pair_j;       // [npairs][2] impact channel indices (second = -1 without MPCP)
+    int32_t *dep_event;    // [max_deposits] event of each deposit (written by drift)
     float *wts;            // [max_deposits][wstride] per-deposit 1-D weights
     void *recs;            // [max_deposits] 48-byte per-deposit records for effq
     int32_t *blk_count;    // [nblk] occupancy
@@ -85,17 +89,17 @@ int check_cuda(tred_handle *h, cudaError_t e, const char *what);
 
 // kernel launchers (each .cu file)
 int launch_drift(tred_handle *h, int n, const float *x, const float *y, const float *z,
-                 const float *t0, const float *ne, const tred_deposits &out,
+                 const float *t0, const float *ne, const int32_t *event, const tred_deposits &out,
                  cudaStream_t s);
 int launch_blockbin(tred_handle *h, int n, const tred_deposits &deps, int32_t *block_ids,
                     int32_t *block_counts, int32_t *dep_offsets, int32_t *dep_index,
                     int32_t max_pairs, int32_t *n_blocks_dev, cudaStream_t s);
 int launch_effq(tred_handle *h, int n, const tred_deposits &deps, const int32_t *block_ids,
                 const int32_t *dep_offsets, const int32_t *dep_index,
-                const int32_t *n_blocks_dev, float *qeff, cudaStream_t s);
+                const int32_t *n_blocks_dev, float *qeff, int slot_base, int slot_count, cudaStream_t s);
 int launch_response(tred_handle *h, const float *resp, cudaStream_t s);
 int launch_convolve(tred_handle *h, const int32_t *block_ids, const int32_t *n_blocks_dev,
-                    const float *qeff, float *out, cudaStream_t s);
+                    const float *qeff, float *out, int slot_base, int slot_count, cudaStream_t s);
 int launch_gather(tred_handle *h, const int32_t *block_ids, const int32_t *n_blocks_dev,
                   const float *out, int32_t *pixel_ids, float *wave, int32_t *n_pixels_dev,
                   cudaStream_t s);

@@ -8,6 +8,7 @@ from __future__ import annotations
 
 import ctypes
 
+import numpy as np
 import torch
 
 from . import abi
@@ -30,10 +31,11 @@ def _stream(stream) -> ctypes.c_void_p:
     return ctypes.c_void_p(stream.cuda_stream)
 
 
-def geometry(cfg) -> Geometry:
+def geometry(cfg, n_events: int = 1) -> Geometry:
     """Geometry struct from any object with the config's attribute names."""
     return Geometry(pitch_cm=cfg.pitch_cm, n_sub=cfg.n_sub, tick_us=cfg.tick_us, npx_x=cfg.npx,
-                    npx_y=cfg.npx, nt=cfg.nt, bp=cfg.bp, bt=cfg.bt, kp=cfg.kp, nr=cfg.nr, lt=cfg.lt)
+                    npx_y=cfg.npx, nt=cfg.nt, bp=cfg.bp, bt=cfg.bt, kp=cfg.kp, nr=cfg.nr, lt=cfg.lt,
+                    n_events=n_events)
 
 
 def params(cfg, effq_mode=0, mpcp=1, compensated_gather=0, conv_mode=0) -> Params:
@@ -106,6 +108,24 @@ def tred_set_response(h: Handle, resp: torch.Tensor, stream=None):
 def tred_drift(h: Handle, n: int, x, y, z, t0, ne, out: DepositBuffers, stream=None):
     h.check(h.lib.tred_drift(h.h, n, _ptr(x), _ptr(y), _ptr(z), _ptr(t0), _ptr(ne),
                              ctypes.byref(out.struct), _stream(stream)))
+
+
+def tred_drift_events(h: Handle, n: int, x, y, z, t0, ne, event, out: DepositBuffers, stream=None):
+    h.check(h.lib.tred_drift_events(h.h, n, _ptr(x), _ptr(y), _ptr(z), _ptr(t0), _ptr(ne), _ptr(event),
+                                    ctypes.byref(out.struct), _stream(stream)))
+
+
+def tred_effq_range(h: Handle, n: int, deps: DepositBuffers, block_ids, dep_offsets, dep_index,
+                    n_blocks_dev, slot_base: int, slot_count: int, qeff, stream=None):
+    h.check(h.lib.tred_effq_range(h.h, n, ctypes.byref(deps.struct), _ptr(block_ids), _ptr(dep_offsets),
+                                  _ptr(dep_index), _ptr(n_blocks_dev), slot_base, slot_count, _ptr(qeff),
+                                  _stream(stream)))
+
+
+def tred_convolve_range(h: Handle, block_ids, n_blocks_dev, slot_base: int, slot_count: int, qeff,
+                        out_blocks, stream=None):
+    h.check(h.lib.tred_convolve_range(h.h, _ptr(block_ids), _ptr(n_blocks_dev), slot_base, slot_count,
+                                      _ptr(qeff), _ptr(out_blocks), _stream(stream)))
 
 
 def tred_blockbin(h: Handle, n: int, deps: DepositBuffers, block_ids, block_counts, dep_offsets,
@@ -308,3 +328,100 @@ class TredLoss(torch.autograd.Function):
         gg = (state.gglob * g.to(state.gglob.device).double()).to(torch.float32)
         gp = [gg[k].to(dv) if dv is not None else None for k, dv in enumerate(ctx.pdev)]
         return (None, None, None, gin[:, 0], gin[:, 1], None, gin[:, 2], gin[:, 3], gp[0], gp[1], gp[2])
+
+
+# ----------------------------------------------------------------- batches of events
+class BatchSimulator:
+    """Many events of uneven size in one pass (Sec. III-B-2 hierarchical batching).
+
+    Events are stacked along y (geometry n_events); every kernel runs once per step
+    as a persistent grid over the global active-block list of all events, and the
+    effective charge and convolution run over sub-batches of ``chunk_blocks`` slots
+    so that Q^eff never needs more than one chunk of device memory.  The launch
+    sequence is fixed (the block count stays on the device), so ``capture()`` can
+    record a step in a CUDA graph."""
+
+    def __init__(self, cfg, resp: torch.Tensor, events, max_blocks: int, max_pixels: int,
+                 chunk_blocks: int = 2048, max_hits: int | None = None, mpcp=1, device=None,
+                 n_events: int | None = None, max_deposits: int | None = None):
+        self.cfg = cfg
+        self.device = d = torch.device(device or "cuda")
+        self.n_events = n_events or len(events)
+        cap = max_deposits or int(sum(len(e["x"]) for e in events))
+        self.h = Handle(geometry(cfg, self.n_events), params(cfg, mpcp=mpcp), max(cap, 1), max_blocks,
+                        max_pixels)
+        self.rp = readout_params(cfg)
+        self.chunk = min(chunk_blocks, max_blocks)
+        self.max_blocks = max_blocks
+        self.inputs = {k: torch.zeros(max(cap, 1), dtype=torch.float32, device=d)
+                       for k in ("x", "y", "z", "t0", "ne")}
+        self.inputs["event"] = torch.zeros(max(cap, 1), dtype=torch.int32, device=d)
+        self.load(events)
+        ns, bp, bt, lt = cfg.n_sub, cfg.bp, cfg.bt, cfg.lt
+        self.deps = DepositBuffers(max(cap, 1), d)
+        self.block_ids = torch.zeros(max_blocks, dtype=torch.int32, device=d)
+        self.block_counts = torch.zeros(max_blocks, dtype=torch.int32, device=d)
+        self.dep_offsets = torch.zeros(max_blocks + 1, dtype=torch.int32, device=d)
+        self.dep_index = torch.zeros(8 * max(self.n, 1), dtype=torch.int32, device=d)
+        self.counts = torch.zeros(4, dtype=torch.int32, device=d)
+        self.qeff = torch.empty((self.chunk, ns, ns, bp, bp, bt), dtype=torch.float32, device=d)
+        self.out_blocks = torch.empty((max_blocks, 16, 16, lt), dtype=torch.float32, device=d)
+        self.pixel_ids = torch.zeros(max_pixels, dtype=torch.int32, device=d)
+        self.waveforms = torch.empty((max_pixels, cfg.nt), dtype=torch.float32, device=d)
+        mh = max_hits or 4 * max_pixels
+        self.hit_pixel = torch.zeros(mh, dtype=torch.int32, device=d)
+        self.hit_tick = torch.zeros(mh, dtype=torch.int32, device=d)
+        self.hit_charge = torch.zeros(mh, dtype=torch.float32, device=d)
+        self.resp = resp.to(d, torch.float32).contiguous()
+        tred_set_response(self.h, self.resp)
+        self.graph = None
+
+    def load(self, events):
+        """Copy a batch of events (at most n_events, within the deposit capacity) into the
+        input buffers; event i gets id i."""
+        assert len(events) <= self.n_events
+        n = int(sum(len(e["x"]) for e in events))
+        assert n <= self.inputs["x"].numel()
+        if n:
+            for k in ("x", "y", "z", "t0", "ne"):
+                self.inputs[k][:n].copy_(torch.from_numpy(
+                    np.concatenate([e[k] for e in events]).astype(np.float32)))
+            self.inputs["event"][:n].copy_(torch.from_numpy(
+                np.concatenate([np.full(len(e["x"]), i, np.int32) for i, e in enumerate(events)])))
+        self.n = n
+
+    def step(self, stream=None):
+        h, x, n = self.h, self.inputs, self.n
+        nb_dev, np_dev, nh_dev = self.counts[0:1], self.counts[1:2], self.counts[2:3]
+        tred_drift_events(h, n, x["x"], x["y"], x["z"], x["t0"], x["ne"], x["event"], self.deps, stream)
+        tred_blockbin(h, n, self.deps, self.block_ids, self.block_counts, self.dep_offsets, self.dep_index,
+                      nb_dev, stream)
+        for base in range(0, self.max_blocks, self.chunk):
+            tred_effq_range(h, n, self.deps, self.block_ids, self.dep_offsets, self.dep_index, nb_dev, base,
+                            self.chunk, self.qeff, stream)
+            tred_convolve_range(h, self.block_ids, nb_dev, base, self.chunk, self.qeff, self.out_blocks, stream)
+        tred_gather_pixels(h, self.block_ids, nb_dev, self.out_blocks, self.pixel_ids, self.waveforms, np_dev,
+                           stream)
+        tred_readout(h, self.rp, self.pixel_ids, self.waveforms, np_dev, self.hit_pixel, self.hit_tick,
+                     self.hit_charge, nh_dev, stream)
+
+    def capture(self):
+        """Record one step in a CUDA graph (call after a warm-up step)."""
+        torch.cuda.synchronize()
+        s = torch.cuda.Stream()
+        s.wait_stream(torch.cuda.current_stream())
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g, stream=s):
+            self.step(stream=s)
+        torch.cuda.current_stream().wait_stream(s)
+        self.graph = g
+        return g
+
+    def replay(self):
+        self.graph.replay()
+
+    def status(self, stream=None):
+        return tred_sync_status(self.h, stream)
+
+    def event_of_pixel(self, pixel_ids):
+        return np.asarray(pixel_ids) // (self.cfg.npx * self.cfg.npx)

@@ -1,0 +1,108 @@
+"""Batches of events through one pass of each kernel (event dimension, sub-batched
+effective charge and convolution, CUDA graph), against the oracle per event and
+against the single-event path."""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from parity_util import WAVE_TOL, check_hits, make_sim, pixel_rel_errors, run
+
+pytestmark = pytest.mark.gpu
+
+
+def _tiny_events(k, cfg):
+    return [synth.make_deposits(cfg, seed=cfg.seed + 1000 * i) for i in range(k)]
+
+
+def _batch(cfg, events, resp, chunk):
+    import torch
+    from paper_2602_12052_b300 import autotune
+    sim = autotune.make_batch(cfg, events, torch.from_numpy(resp), chunk_blocks=chunk)
+    sim.step()
+    torch.cuda.synchronize()
+    return sim
+
+
+def _results(sim):
+    import torch
+    torch.cuda.synchronize()
+    nb, npix, nh = (int(v) for v in sim.counts[:3].cpu())
+    return {"block_ids": sim.block_ids[:nb].cpu().numpy(), "block_counts": sim.block_counts[:nb].cpu().numpy(),
+            "pixel_ids": sim.pixel_ids[:npix].cpu().numpy(), "waveforms": sim.waveforms[:npix].cpu().numpy(),
+            "hit_pixel": sim.hit_pixel[:nh].cpu().numpy(), "hit_tick": sim.hit_tick[:nh].cpu().numpy(),
+            "hit_charge": sim.hit_charge[:nh].cpu().numpy()}
+
+
+@pytest.mark.parametrize("chunk", [3, 64])
+def test_batch_matches_oracle_per_event(chunk):
+    cfg = synth.get_config("tiny")
+    resp = synth.make_response(cfg)
+    events = _tiny_events(3, cfg)
+    sim = _batch(cfg, events, resp, chunk)
+    assert sim.status()[0] == 0
+    res = _results(sim)
+    nblk, npx2 = cfg.n_blocks, cfg.npx * cfg.npx
+    for e, dep in enumerate(events):
+        ref = oracle.simulate(cfg, dep, resp)
+        sel_b = (res["block_ids"] // nblk) == e
+        np.testing.assert_array_equal(res["block_ids"][sel_b] - e * nblk, ref["block_ids"])
+        np.testing.assert_array_equal(res["block_counts"][sel_b], ref["block_counts"])
+        sel_p = (res["pixel_ids"] // npx2) == e
+        np.testing.assert_array_equal(res["pixel_ids"][sel_p] - e * npx2, ref["pixel_ids"])
+        err = pixel_rel_errors(res["waveforms"][sel_p], ref["waveforms"])
+        assert err.max() <= WAVE_TOL, (e, err.max())
+        hp, ht, hc, _ = oracle.readout(ref["pixel_ids"], ref["waveforms"], cfg.threshold_e, cfg.clock_ticks,
+                                       cfg.hold_ticks, cfg.reset_ticks)
+        sel_h = (res["hit_pixel"] // npx2) == e
+        check_hits((res["hit_pixel"][sel_h] - e * npx2, res["hit_tick"][sel_h], res["hit_charge"][sel_h]),
+                   (hp, ht, hc), ref["waveforms"], ref["pixel_ids"], cfg.threshold_e, cfg.hold_ticks,
+                   cfg.reset_ticks)
+
+
+def test_batch_graph_replay_matches_eager():
+    import torch
+    cfg = synth.get_config("tiny")
+    resp = synth.make_response(cfg)
+    sim = _batch(cfg, _tiny_events(4, cfg), resp, 8)
+    eager = _results(sim)
+    sim.capture()
+    for _ in range(2):
+        sim.replay()
+        torch.cuda.synchronize()
+        got = _results(sim)
+        for k in ("block_ids", "block_counts", "pixel_ids", "hit_pixel", "hit_tick"):
+            np.testing.assert_array_equal(got[k], eager[k])
+        # effq accumulates with floating-point atomics, so runs agree to rounding
+        assert pixel_rel_errors(got["waveforms"], eager["waveforms"]).max() <= WAVE_TOL
+
+
+def test_batch_of_uneven_events_equals_single_event_runs():
+    """Config-3 style events (uneven deposit counts) batched vs one at a time."""
+    cfg = synth.get_config("module200")
+    resp = synth.make_response(cfg)
+    events = synth.make_events(cfg, 4, 1000, 30000, seed=33)
+    sim = _batch(cfg, events, resp, 256)
+    assert sim.status()[0] == 0
+    res = _results(sim)
+    nblk, npx2 = cfg.n_blocks, cfg.npx * cfg.npx
+    for e, dep in enumerate(events):
+        one = make_sim(cfg, resp, len(dep["x"]), max_blocks=4000, max_pixels=200000)
+        r1 = run(one, dep, keep_qeff=False)
+        sel_b = (res["block_ids"] // nblk) == e
+        np.testing.assert_array_equal(res["block_ids"][sel_b] - e * nblk, r1["block_ids"])
+        sel_p = (res["pixel_ids"] // npx2) == e
+        np.testing.assert_array_equal(res["pixel_ids"][sel_p] - e * npx2, r1["pixel_ids"])
+        assert pixel_rel_errors(res["waveforms"][sel_p], r1["waveforms"]).max() <= WAVE_TOL
+        sel_h = (res["hit_pixel"] // npx2) == e
+        np.testing.assert_array_equal(res["hit_pixel"][sel_h] - e * npx2, r1["hit_pixel"])
+        np.testing.assert_array_equal(res["hit_tick"][sel_h], r1["hit_tick"])
+
+
+@pytest.mark.parametrize("bp,bt,lt", [(8, 128, 512), (4, 256, 512), (8, 320, 1024), (8, 640, 1024)])
+def test_autotuner_shapes_match_oracle(bp, bt, lt):
+    """Every block shape / FFT length the autotuner may pick is parity-checked."""
+    from test_gpu_parity import _full_check
+    cfg = synth.get_config("tiny", nt=1280, bp=bp, bt=bt, lt=lt)
+    dep, resp = synth.make_event(cfg)
+    _full_check(cfg, dep, resp, check_readout=False)
