@@ -51,7 +51,8 @@ def _args():
                     help="deposits of the workload timed through the CPU oracle")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--mode", default="step", choices=["step", "batched", "adjoint", "spill"],
+    ap.add_argument("--mode", default="step",
+                    choices=["step", "batched", "adjoint", "spill", "accuracy", "chunking"],
                     help="step: one event (default); batched: 64 uneven events, autotuned, CUDA graph; "
                          "adjoint: forward + backward; spill: 35 planes in sequence")
     ap.add_argument("--events", type=int, default=64)
@@ -346,13 +347,79 @@ def run_spill(args):
           status=st[:2], clocks=clk.summary())
 
 
+def run_accuracy(args):
+    """The paper's accuracy study (Sec. IV-B): maximum deviation, per pixel, of the
+    charge accumulated in 100 ns windows, for grid-point sampling (GL-1) and the
+    2-point rule, each against the 4-point rule; module-plane event."""
+    import numpy as np
+    import torch
+    import synth
+    from paper_2602_12052_b300 import tred
+    torch.cuda.set_device(0)
+    base = synth.get_config("module200")
+    dep, resp = synth.make_event(base)
+    dev = torch.device("cuda")
+    x = {k: torch.from_numpy(v).to(dev) for k, v in dep.items()}
+    n = len(dep["x"])
+    max_blocks, max_pixels = probe_capacities(base, dep, dev)
+    out = {}
+    for gl in (1, 2, 4):
+        cfg = base.with_(gl_order=gl)
+        sim = tred.Simulator(cfg, torch.from_numpy(resp), max_deposits=n, max_blocks=max_blocks,
+                             max_pixels=max_pixels, device=dev)
+        sim.step(n, x["x"], x["y"], x["z"], x["t0"], x["ne"], readout=False)
+        npix = int(sim.counts[1].item())
+        w = sim.waveforms[:npix].double()
+        ticks_per_window = int(round(0.1 / cfg.tick_us))                # 100 ns
+        q = w[:, : cfg.nt // ticks_per_window * ticks_per_window].reshape(npix, -1, ticks_per_window).sum(-1)
+        out[gl] = (sim.pixel_ids[:npix].cpu().numpy(), q)
+        del sim
+        torch.cuda.empty_cache()
+    assert all(np.array_equal(out[1][0], out[k][0]) for k in (2, 4))
+    res = {}
+    for gl in (1, 2):
+        dev_max = (out[gl][1] - out[4][1]).abs().max(dim=1).values.cpu().numpy()
+        res[f"GL-{gl}"] = {p: float(np.percentile(dev_max, p)) for p in (50, 90, 99, 100)}
+    _line("max deviation of accumulated charge per pixel per 100 ns vs the 4-point rule (electrons)",
+          res["GL-2"][100], "e-", 0.0, args,
+          {"workload": f"module200 event, {n} deposits, {len(out[4][0])} pixels", "noise_scale_e": 500},
+          percentiles=res, higher_is_better=False)
+
+
+def run_chunking(args):
+    """Sub-dimensional chunking (Sec. III-B-2): peak device memory and time of one
+    module-plane step vs the number of active blocks per effective-charge chunk."""
+    import torch
+    import synth
+    from paper_2602_12052_b300 import autotune, tred
+    torch.cuda.set_device(0)
+    cfg = synth.get_config("module1M")
+    dep, resp = synth.make_event(cfg)
+    resp = torch.from_numpy(resp)
+    nb, npix = autotune.probe_blocks(cfg, [dep], resp)
+    rows = []
+    for chunk in (256, 1024, 4096, nb + 8):
+        torch.cuda.empty_cache()
+        free0, total = torch.cuda.mem_get_info()
+        sim = tred.BatchSimulator(cfg, resp, [dep], max_blocks=nb + 8, max_pixels=npix, chunk_blocks=chunk)
+        ms = _timed(sim.step, 2, 1)
+        free1, _ = torch.cuda.mem_get_info()
+        rows.append({"chunk_blocks": chunk, "device_bytes": int(free0 - free1), "ms": ms,
+                     "qeff_bytes": sim.qeff.numel() * 4})
+        del sim
+    _line("device memory of one module-plane step vs effective-charge chunk size", rows[0]["device_bytes"],
+          "bytes", rows[0]["ms"], args, {"workload": f"module1M event, {len(dep['x'])} deposits, {nb} blocks"},
+          rows=rows, higher_is_better=False)
+
+
 def main():
     args = _args()
     if args.impl == "reference":
         run_reference(args)
         return
     if args.mode != "step":
-        {"batched": run_batched, "adjoint": run_adjoint, "spill": run_spill}[args.mode](args)
+        {"batched": run_batched, "adjoint": run_adjoint, "spill": run_spill, "accuracy": run_accuracy,
+         "chunking": run_chunking}[args.mode](args)
         return
     import numpy as np
     import torch

@@ -146,12 +146,23 @@ __global__ void __launch_bounds__(256) k_effq_weights(int n, tred_deposits d, Ef
 
 // Persistent CTAs over active blocks, time-tiled.  One tile holds the block's whole
 // sub-cell plane for EQ_TT consecutive ticks, indexed by sub-cell ([t][gy][gx],
-// (bp n_sub)^2 x 8 floats = 200 KB at 80 x 80 x 8), so each deposit is visited once
+// (bp n_sub)^2 x 8 words = 200 KB at 80 x 80 x 8), so each deposit is visited once
 // per tile it overlaps and all its sub-cells are handled in that visit: lanes over
-// two rows of 16 sub-cells (banks gx and gx + 16: no conflicts), 8 tick updates
-// per lane from the tile's time weights held in registers.  The write pass gathers
-// each (channel, column) segment's 8 ticks into one 32-byte sector of the
-// [jy][jx][py][px][t] layout and zeroes the tile for the next tick range; the
+// two rows of 16 sub-cells (banks gx and gx + 16: no conflicts), 8 tick updates per
+// lane from the tile's time weights held in registers.
+//
+// The tile accumulates in 32-bit fixed point.  Every contribution q e_x e_y e_t is
+// non-negative and at most q m_x m_y m_t, where m_a is the deposit's largest weight
+// on axis a inside this block, so no cell exceeds B = sum over the block's deposits
+// of q m_x m_y m_t, and the scale S = 2^30 / B keeps every sum below 2^31.  B is
+// formed without depending on the order of the block's deposit list (which comes
+// from atomics), integer shared-memory additions are single fire-and-forget
+// reductions (the float ones are compare-and-swap loops) whose sum does not depend
+// on order, so the block's effective charge is bitwise reproducible.  Rounding: at
+// most 0.5 / S per contribution.
+//
+// The write pass converts each (channel, column) segment's 8 ticks back to float
+// (one 32-byte sector of the [jy][jx][py][px][t] layout) and zeroes the tile; the
 // non-empty column masks come from the data written.
 constexpr int EQ_THREADS = 1024;
 constexpr int EQ_TT = 8;
@@ -171,13 +182,14 @@ __global__ void __launch_bounds__(EQ_THREADS, 1) k_effq_blocks(const int32_t *__
     const int cols = c.bp * c.bp;
     const int side = c.bp * c.ns;
     const int plane = side * side;                                            // == nch * cols
-    float *tile = smem_e;                                                     // [8][side][side]
+    unsigned *tile = reinterpret_cast<unsigned *>(smem_e);                    // [8][side][side]
     DepRec *rc = reinterpret_cast<DepRec *>(tile + plane * EQ_TT);            // [EQ_CACHE]
     unsigned long long *mask = reinterpret_cast<unsigned long long *>(rc + EQ_CACHE);  // [nch]
+    float *s_part = reinterpret_cast<float *>(mask + nch);                    // [EQ_THREADS / 32] x 8 bytes
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31, nwarps = EQ_THREADS / 32;
     {
-        const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
-        for (int k = tid; k < plane * (EQ_TT / 4); k += EQ_THREADS) reinterpret_cast<float4 *>(tile)[k] = z4;
+        const uint4 z4 = make_uint4(0u, 0u, 0u, 0u);
+        for (int k = tid; k < plane * (EQ_TT / 4); k += EQ_THREADS) reinterpret_cast<uint4 *>(tile)[k] = z4;
     }
     const int nb = min(n_blocks_dev[0], slot_base + slot_count);
     for (int slot = slot_base + blockIdx.x; slot < nb; slot += gridDim.x) {
@@ -188,6 +200,47 @@ __global__ void __launch_bounds__(EQ_THREADS, 1) k_effq_blocks(const int32_t *__
         const int beg = dep_offsets[slot], end = dep_offsets[slot + 1];
         const int passes = max(1, (end - beg + EQ_CACHE - 1) / EQ_CACHE);
         for (int k = tid; k < nch; k += EQ_THREADS) mask[k] = 0ull;
+        // B: every deposit's largest weight product inside the block (its bound term),
+        // summed order-independently: the terms' maximum M, then an integer sum of the
+        // terms rounded up to multiples of M / 2^20.
+        auto term = [&](int k) -> float {
+            const DepRec r = recs[dep_index[k]];
+            const int xa = max(r.x0, X0), xb = min(r.x1, X0 + side - 1);
+            const int ya = max(r.y0, Y0), yb = min(r.y1, Y0 + side - 1);
+            const int ta = max(r.t0, T0), tb = min(r.t1, T0 + c.bt - 1);
+            if (xa > xb || ya > yb || ta > tb) return 0.f;
+            const float *w = wts + (size_t)r.idx * c.wstride;
+            float mx = 0.f, my = 0.f, mt = 0.f;
+            for (int g = xa; g <= xb; ++g) mx = fmaxf(mx, __ldg(w + (g - r.gx0)));
+            for (int g = ya; g <= yb; ++g) my = fmaxf(my, __ldg(w + c.wx + (g - r.gy0)));
+            for (int g = ta; g <= tb; ++g) mt = fmaxf(mt, __ldg(w + 2 * c.wx + (g - r.gt0)));
+            return fmaxf(r.q, 0.f) * mx * my * mt;
+        };
+        float tmax = 0.f;
+        for (int k = beg + tid; k < end; k += EQ_THREADS) tmax = fmaxf(tmax, term(k));
+#pragma unroll
+        for (int o = 16; o; o >>= 1) tmax = fmaxf(tmax, __shfl_xor_sync(0xffffffffu, tmax, o));
+        if (lane == 0) s_part[warp] = tmax;
+        __syncthreads();
+        float M = 0.f;
+#pragma unroll 8
+        for (int k = 0; k < EQ_THREADS / 32; ++k) M = fmaxf(M, s_part[k]);
+        unsigned long long units = 0ull;
+        if (M > 0.f) {
+            const float to_units = 1048576.0f / M;
+            for (int k = beg + tid; k < end; k += EQ_THREADS) units += (unsigned long long)ceilf(term(k) * to_units) + 1ull;
+        }
+#pragma unroll
+        for (int o = 16; o; o >>= 1) units += __shfl_xor_sync(0xffffffffu, units, o);
+        __syncthreads();                                     // everyone has read M
+        if (lane == 0) reinterpret_cast<unsigned long long *>(s_part)[warp] = units;
+        __syncthreads();
+        unsigned long long usum = 0ull;
+#pragma unroll 8
+        for (int k = 0; k < EQ_THREADS / 32; ++k) usum += reinterpret_cast<const unsigned long long *>(s_part)[k];
+        const float bound = (float)usum * (M * (1.0f / 1048576.0f)) * 1.0001f + 1e-20f;
+        const float scale = 1073741824.0f / bound;          // 2^30 / B
+        const float inv_scale = bound * (1.0f / 1073741824.0f);
         uint32_t nz = 0u;                       // per-lane non-empty flags of its (col, ch) segments
         for (int tt = 0; tt < c.bt; tt += EQ_TT) {
             const int ta = T0 + tt, tb = ta + EQ_TT - 1;   // absolute ticks of the tile
@@ -215,13 +268,14 @@ __global__ void __launch_bounds__(EQ_THREADS, 1) k_effq_blocks(const int32_t *__
                         const int t = ta + e;
                         wt[e] = (t >= r.t0 && t <= r.t1) ? __ldg(w + 2 * c.wx + (t - r.gt0)) : 0.f;
                     }
+                    const float qs = r.q * scale;
                     for (int gy = ya + (lane >> 4); gy <= yb; gy += 2) {
-                        const float ay = r.q * __ldg(wyv + gy);
+                        const float ay = qs * __ldg(wyv + gy);
                         for (int gx = xa + (lane & 15); gx <= xb; gx += 16) {
                             const float a = ay * __ldg(wxv + gx);
-                            float *cell = tile + gy * side + gx;
+                            unsigned *cell = tile + gy * side + gx;
 #pragma unroll
-                            for (int e = 0; e < EQ_TT; ++e) atomicAdd(cell + e * plane, a * wt[e]);
+                            for (int e = 0; e < EQ_TT; ++e) atomicAdd(cell + e * plane, __float2uint_rn(a * wt[e]));
                         }
                     }
                 }
@@ -233,14 +287,15 @@ __global__ void __launch_bounds__(EQ_THREADS, 1) k_effq_blocks(const int32_t *__
                 const int py = col / c.bp, px = col - py * c.bp;
                 for (int ch = lane; ch < nch; ch += 32, ++bit) {
                     const int jy = ch / c.ns, jx = ch - jy * c.ns;
-                    float *cell = tile + (py * c.ns + jy) * side + px * c.ns + jx;
+                    unsigned *cell = tile + (py * c.ns + jy) * side + px * c.ns + jx;
                     float v[EQ_TT];
-                    bool any = false;
+                    unsigned any = 0u;
 #pragma unroll
                     for (int e = 0; e < EQ_TT; ++e) {
-                        v[e] = cell[e * plane];
-                        cell[e * plane] = 0.f;
-                        any |= v[e] != 0.f;
+                        const unsigned u = cell[e * plane];
+                        cell[e * plane] = 0u;
+                        any |= u;
+                        v[e] = (float)u * inv_scale;
                     }
                     if (any) nz |= 1u << bit;
                     float4 *dst = reinterpret_cast<float4 *>(qeff + ((qslot * nch + ch) * cols + col) * c.bt + tt);
@@ -293,7 +348,7 @@ int launch_effq(tred_handle *h, int n, const tred_deposits &deps, const int32_t 
     }
     const int nch = c.ns * c.ns;
     const size_t smem = sizeof(float) * (size_t)nch * c.bp * c.bp * EQ_TT + sizeof(DepRec) * EQ_CACHE +
-                        sizeof(unsigned long long) * nch;
+                        sizeof(unsigned long long) * nch + sizeof(unsigned long long) * (EQ_THREADS / 32);
     static bool attr_set = false;
     if (!attr_set) {
         cudaFuncSetAttribute(k_effq_blocks, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);

@@ -138,8 +138,9 @@ def test_capacity_overflow_sets_status():
     assert res["n_blocks"] == 2
 
 
-def test_repeatable_integer_outputs():
-    """Block list, occupancy and pixel list are identical run to run."""
+def test_repeatable_outputs():
+    """Block list, occupancy and pixel list are identical run to run, and so is the
+    effective charge, bit for bit (fixed-point accumulation in the tile)."""
     cfg = synth.get_config("tiny")
     dep, resp = synth.make_event(cfg)
     sim = make_sim(cfg, resp, len(dep["x"]))
@@ -148,6 +149,7 @@ def test_repeatable_integer_outputs():
     for k in ("block_ids", "block_counts", "pixel_ids", "dep_offsets"):
         np.testing.assert_array_equal(a[k], b[k])
     np.testing.assert_array_equal(np.sort(a["dep_index"]), np.sort(b["dep_index"]))
+    np.testing.assert_array_equal(a["qeff"], b["qeff"])
 
 
 # ------------------------------------------------------------------ full size, sampled
@@ -159,7 +161,7 @@ def _sampled_pixels(res, k=48, seed=0):
     return np.unique(np.concatenate([top, rnd]))
 
 
-@pytest.mark.parametrize("name", ["module200", "module1M"])
+@pytest.mark.parametrize("name", ["module200", "module1M", "spill_plane"])
 def test_module_plane_sampled(name):
     """512 x 512 pixels x 6400 ticks at full size, in the bench's launch
     configuration: bit-exact blocks and pixels, sampled Q^eff blocks, sampled pixel
@@ -167,7 +169,7 @@ def test_module_plane_sampled(name):
     cfg = synth.get_config(name)
     dep, resp = synth.make_event(cfg)
     n = len(dep["x"])
-    sim = make_sim(cfg, resp, n, max_blocks=12000, max_pixels=300000)
+    sim = make_sim(cfg, resp, n, max_blocks=9000, max_pixels=300000)
     res = run(sim, dep, keep_qeff=False)
     assert res["status"][0] == 0, res["status"]
     p = oracle.params(cfg)
@@ -190,3 +192,28 @@ def test_module_plane_sampled(name):
     sel = np.isin(res["hit_pixel"], pix)
     check_hits((res["hit_pixel"][sel], res["hit_tick"][sel], res["hit_charge"][sel]), (hp, ht, hc),
                ref, pix, cfg.threshold_e, cfg.hold_ticks, cfg.reset_ticks)
+
+
+@pytest.mark.parametrize("form", ["fp32", "compensated_gather", "exact_tent_fp64_tails"])
+def test_precision_ladder_module200(form, capsys):
+    """Each precision form of the module-plane event against the FP64 oracle on
+    sampled pixels; the errors are printed (pytest -s) and bounded by the FP32
+    tolerance."""
+    cfg = synth.get_config("module200")
+    dep, resp = synth.make_event(cfg)
+    mode = 1 if form == "exact_tent_fp64_tails" else 0
+    comp = 1 if form == "compensated_gather" else 0
+    sim = make_sim(cfg, resp, len(dep["x"]), max_blocks=3000, max_pixels=150000, effq_mode=mode,
+                   compensated_gather=comp)
+    res = run(sim, dep, keep_qeff=False)
+    p = oracle.params(cfg, effq_mode=mode)
+    d = oracle.drift(p, dep)
+    rows = _sampled_pixels(res, k=64, seed=3)
+    pix = res["pixel_ids"][rows]
+    ref = oracle.pixel_currents(p, d, resp, pix)
+    err = pixel_rel_errors(res["waveforms"][rows], ref)
+    ev = np.linalg.norm(res["waveforms"][rows] - ref) / np.linalg.norm(ref)
+    with capsys.disabled():
+        print(f"\nprecision {form}: max per-pixel rel L2 {err.max():.3e}, median {np.median(err):.3e}, "
+              f"sampled-event rel L2 {ev:.3e}")
+    assert err.max() <= WAVE_TOL
