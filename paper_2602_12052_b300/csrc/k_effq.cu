@@ -144,65 +144,109 @@ __global__ void __launch_bounds__(256) k_effq_weights(int n, tred_deposits d, Ef
     }
 }
 
-// Persistent CTAs over active blocks, time-tiled.  One tile holds the block's whole
-// sub-cell plane for EQ_TT consecutive ticks, indexed by sub-cell ([t][gy][gx],
-// (bp n_sub)^2 x 8 words = 200 KB at 80 x 80 x 8), so each deposit is visited once
-// per tile it overlaps and all its sub-cells are handled in that visit: lanes over
-// two rows of 16 sub-cells (banks gx and gx + 16: no conflicts), 8 tick updates per
-// lane from the tile's time weights held in registers.
+// Effective charge of the active blocks: CTAs take blocks from a queue; per block,
+// 8-tick tiles with the accumulation in registers.
 //
-// The tile accumulates in 32-bit fixed point.  Every contribution q e_x e_y e_t is
-// non-negative and at most q m_x m_y m_t, where m_a is the deposit's largest weight
-// on axis a inside this block, so no cell exceeds B = sum over the block's deposits
-// of q m_x m_y m_t, and the scale S = 2^30 / B keeps every sum below 2^31.  B is
-// formed without depending on the order of the block's deposit list (which comes
-// from atomics), integer shared-memory additions are single fire-and-forget
-// reductions (the float ones are compare-and-swap loops) whose sum does not depend
-// on order, so the block's effective charge is bitwise reproducible.  Rounding: at
-// most 0.5 / S per contribution.
+// The block's sub-cell plane is cut into 8 x 4 patches (gx x gy); a lane owns one
+// sub-cell of a patch with that cell's 8 ticks in registers, and the warps of the
+// CTA take patches one by one.  Per tile the CTA lists, in shared memory, the
+// deposits whose support meets the tile (clipped ranges, scaled charge, the tile's 8
+// time weights, and the clipped x and y weight vectors copied into a pool) and sorts
+// the list into per-patch buckets (count, scan, fill), so a warp walks only the
+// deposits that reach its patch.  No cell is written by two threads: no atomics on
+// data and no shared-memory tile; each lane writes its 8 ticks as one 32-byte
+// sector of the [jy][jx][py][px][t] layout.
 //
-// The write pass converts each (channel, column) segment's 8 ticks back to float
-// (one 32-byte sector of the [jy][jx][py][px][t] layout) and zeroes the tile; the
-// non-empty column masks come from the data written.
-constexpr int EQ_THREADS = 1024;
+// The sums are exact integers.  Every contribution q e_x e_y e_t has magnitude at
+// most q m_x m_y m_t, where m_a is the deposit's largest weight on axis a inside
+// the block; with M the largest such bound and B their sum, the scale
+// S = min(2^22 / M, 2^31 / B) (less a small margin) keeps each scaled contribution
+// below 2^22, where fma(a, w, 1.5 * 2^23) rounds it to the nearest integer in the
+// low mantissa bits, and each cell's sum below 2^31.  Integer sums do not depend on
+// the order of the deposits, so the block's effective charge is bitwise
+// reproducible; the rounding is at most 1 / (2 S) per contribution.
+//
+// A tile whose list would exceed the shared-memory capacities (entries, pool,
+// bucket slots) is processed in passes, each a contiguous run of the block's
+// deposit list chosen by a block-wide scan; the integer partial sums of the cells
+// are kept in a per-CTA global scratch between passes.
 constexpr int EQ_TT = 8;
-constexpr int EQ_CACHE = 256;      // deposit records staged per pass
+constexpr int EQ_WARPS = 10;
+constexpr int EQ_THREADS = EQ_WARPS * 32;
+constexpr int EQ_CTAS_PER_SM = 2;
+constexpr int EQ_LIST = 256;                 // tile-list entries per pass
+constexpr int EQ_POOL = 12288;               // weight-pool floats per pass
+constexpr int EQ_INS = 8192;                 // bucket slots per pass
+constexpr int EQ_PX = 8, EQ_PY = 4;          // patch: 8 gx x 4 gy sub-cells
+constexpr int EQ_MAX_SIDE = 128;             // bp * n_sub
+constexpr int EQ_MAX_PATCH = (EQ_MAX_SIDE / EQ_PX) * (EQ_MAX_SIDE / EQ_PY);
+constexpr float EQ_MAGIC = 12582912.0f;      // 1.5 * 2^23
+constexpr int EQ_MAGIC_BITS = 0x4B400000;
 
-__global__ void __launch_bounds__(EQ_THREADS, 1) k_effq_blocks(const int32_t *__restrict__ block_ids,
-                                                            const int32_t *__restrict__ dep_offsets,
-                                                            const int32_t *__restrict__ dep_index,
-                                                            const int32_t *__restrict__ n_blocks_dev,
-                                                            EffqConst c, const float *__restrict__ wts,
-                                                            const DepRec *__restrict__ recs,
-                                                            float *__restrict__ qeff,
-                                                            uint64_t *__restrict__ colmask, int slot_base,
-                                                            int slot_count) {
-    extern __shared__ float smem_e[];
+struct TileEnt {
+    int y0, y1, x0, x1;          // block-local clipped ranges
+    int qs, wxo, wyo, idx;       // q * S (float bits); pool offsets of the x and y weights; deposit
+    float wt[EQ_TT];             // time weights of the tile's ticks, zero outside the support
+};
+static_assert(sizeof(TileEnt) == 64, "tile list entry");
+
+struct EffqShared {
+    TileEnt list[EQ_LIST];
+    float pool[EQ_POOL];
+    uint16_t bucket[EQ_INS];
+    int boff[EQ_MAX_PATCH + 1];
+    int bfill[EQ_MAX_PATCH];
+    uint32_t nzp[EQ_MAX_PATCH];          // per patch: lanes whose cell is non-zero in some tile
+    int offx[EQ_MAX_SIDE], offy[EQ_MAX_SIDE];   // output offsets of block-local gx and gy
+    unsigned long long mask[128];        // per channel: non-empty (py, px) columns (n_sub^2 <= 128)
+    unsigned long long part[EQ_WARPS * 3];
+    int tot[4];                          // list entries, pool floats, bucket slots, accepted count
+    int slot, next;
+};
+
+__device__ __forceinline__ int fx_round(float a, float w) {
+    return __float_as_int(fmaf(a, w, EQ_MAGIC)) - EQ_MAGIC_BITS;
+}
+
+__global__ void __launch_bounds__(EQ_THREADS, EQ_CTAS_PER_SM) k_effq_blocks(
+    const int32_t *__restrict__ block_ids, const int32_t *__restrict__ dep_offsets,
+    const int32_t *__restrict__ dep_index, const int32_t *__restrict__ n_blocks_dev, EffqConst c,
+    const float *__restrict__ wts, const DepRec *__restrict__ recs, float *__restrict__ qeff,
+    uint64_t *__restrict__ colmask, int32_t *__restrict__ acc_scratch, int32_t *__restrict__ queue,
+    int slot_base, int slot_count) {
+    extern __shared__ __align__(16) unsigned char smem_e[];
+    EffqShared &S = *reinterpret_cast<EffqShared *>(smem_e);
     const int nch = c.ns * c.ns;
     const int cols = c.bp * c.bp;
     const int side = c.bp * c.ns;
-    const int plane = side * side;                                            // == nch * cols
-    unsigned *tile = reinterpret_cast<unsigned *>(smem_e);                    // [8][side][side]
-    DepRec *rc = reinterpret_cast<DepRec *>(tile + plane * EQ_TT);            // [EQ_CACHE]
-    unsigned long long *mask = reinterpret_cast<unsigned long long *>(rc + EQ_CACHE);  // [nch]
-    float *s_part = reinterpret_cast<float *>(mask + nch);                    // [EQ_THREADS / 32] x 8 bytes
-    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31, nwarps = EQ_THREADS / 32;
-    {
-        const uint4 z4 = make_uint4(0u, 0u, 0u, 0u);
-        for (int k = tid; k < plane * (EQ_TT / 4); k += EQ_THREADS) reinterpret_cast<uint4 *>(tile)[k] = z4;
+    const int npx = (side + EQ_PX - 1) / EQ_PX;
+    const int npatch = npx * ((side + EQ_PY - 1) / EQ_PY);
+    const int len_cap = min(c.wx, side);
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int lx = lane & (EQ_PX - 1), ly = lane >> 3;
+    int32_t *scratch = acc_scratch + (size_t)blockIdx.x * side * side * EQ_TT;
+    for (int g = tid; g < side; g += EQ_THREADS) {
+        const int pg = g / c.ns, jg = g - pg * c.ns;
+        S.offx[g] = (jg * cols + pg) * c.bt;                   // jx, px
+        S.offy[g] = (jg * c.ns * cols + pg * c.bp) * c.bt;     // jy, py
     }
     const int nb = min(n_blocks_dev[0], slot_base + slot_count);
-    for (int slot = slot_base + blockIdx.x; slot < nb; slot += gridDim.x) {
+    for (;;) {
+        __syncthreads();
+        if (tid == 0) S.slot = slot_base + atomicAdd(queue, 1);
+        for (int k = tid; k < nch; k += EQ_THREADS) S.mask[k] = 0ull;
+        for (int k = tid; k < npatch; k += EQ_THREADS) S.nzp[k] = 0u;
+        __syncthreads();
+        const int slot = S.slot;
+        if (slot >= nb) break;
         const int blk = block_ids[slot];
         const int bt = blk % c.nbt, bxy = blk / c.nbt, bx = bxy % c.nbx, by = bxy / c.nbx;
         const int X0 = bx * side, Y0 = by * side, T0 = bt * c.bt;
-        const size_t qslot = (size_t)(slot - slot_base);   // row of the caller's qeff buffer
+        float *qblk = qeff + (size_t)(slot - slot_base) * nch * cols * c.bt;   // the caller's buffer row
         const int beg = dep_offsets[slot], end = dep_offsets[slot + 1];
-        const int passes = max(1, (end - beg + EQ_CACHE - 1) / EQ_CACHE);
-        for (int k = tid; k < nch; k += EQ_THREADS) mask[k] = 0ull;
-        // B: every deposit's largest weight product inside the block (its bound term),
-        // summed order-independently: the terms' maximum M, then an integer sum of the
-        // terms rounded up to multiples of M / 2^20.
+        // bound terms: each deposit's largest weight product inside the block, times |q|;
+        // M = their maximum, B = their sum rounded up to multiples of M / 2^20 (an
+        // integer sum, so neither depends on the order of the deposit list)
         auto term = [&](int k) -> float {
             const DepRec r = recs[dep_index[k]];
             const int xa = max(r.x0, X0), xb = min(r.x1, X0 + side - 1);
@@ -211,110 +255,238 @@ __global__ void __launch_bounds__(EQ_THREADS, 1) k_effq_blocks(const int32_t *__
             if (xa > xb || ya > yb || ta > tb) return 0.f;
             const float *w = wts + (size_t)r.idx * c.wstride;
             float mx = 0.f, my = 0.f, mt = 0.f;
-            for (int g = xa; g <= xb; ++g) mx = fmaxf(mx, __ldg(w + (g - r.gx0)));
-            for (int g = ya; g <= yb; ++g) my = fmaxf(my, __ldg(w + c.wx + (g - r.gy0)));
-            for (int g = ta; g <= tb; ++g) mt = fmaxf(mt, __ldg(w + 2 * c.wx + (g - r.gt0)));
-            return fmaxf(r.q, 0.f) * mx * my * mt;
+            for (int g = xa; g <= xb; ++g) mx = fmaxf(mx, fabsf(__ldg(w + (g - r.gx0))));
+            for (int g = ya; g <= yb; ++g) my = fmaxf(my, fabsf(__ldg(w + c.wx + (g - r.gy0))));
+            for (int g = ta; g <= tb; ++g) mt = fmaxf(mt, fabsf(__ldg(w + 2 * c.wx + (g - r.gt0))));
+            return fabsf(r.q) * mx * my * mt;
         };
         float tmax = 0.f;
         for (int k = beg + tid; k < end; k += EQ_THREADS) tmax = fmaxf(tmax, term(k));
 #pragma unroll
         for (int o = 16; o; o >>= 1) tmax = fmaxf(tmax, __shfl_xor_sync(0xffffffffu, tmax, o));
-        if (lane == 0) s_part[warp] = tmax;
+        if (lane == 0) reinterpret_cast<float *>(S.part)[warp] = tmax;
         __syncthreads();
         float M = 0.f;
-#pragma unroll 8
-        for (int k = 0; k < EQ_THREADS / 32; ++k) M = fmaxf(M, s_part[k]);
+#pragma unroll
+        for (int k = 0; k < EQ_WARPS; ++k) M = fmaxf(M, reinterpret_cast<const float *>(S.part)[k]);
         unsigned long long units = 0ull;
         if (M > 0.f) {
             const float to_units = 1048576.0f / M;
-            for (int k = beg + tid; k < end; k += EQ_THREADS) units += (unsigned long long)ceilf(term(k) * to_units) + 1ull;
+            for (int k = beg + tid; k < end; k += EQ_THREADS)
+                units += (unsigned long long)ceilf(term(k) * to_units) + 1ull;
         }
 #pragma unroll
         for (int o = 16; o; o >>= 1) units += __shfl_xor_sync(0xffffffffu, units, o);
         __syncthreads();                                     // everyone has read M
-        if (lane == 0) reinterpret_cast<unsigned long long *>(s_part)[warp] = units;
+        if (lane == 0) S.part[warp] = units;
         __syncthreads();
         unsigned long long usum = 0ull;
-#pragma unroll 8
-        for (int k = 0; k < EQ_THREADS / 32; ++k) usum += reinterpret_cast<const unsigned long long *>(s_part)[k];
-        const float bound = (float)usum * (M * (1.0f / 1048576.0f)) * 1.0001f + 1e-20f;
-        const float scale = 1073741824.0f / bound;          // 2^30 / B
-        const float inv_scale = bound * (1.0f / 1073741824.0f);
-        uint32_t nz = 0u;                       // per-lane non-empty flags of its (col, ch) segments
+#pragma unroll
+        for (int k = 0; k < EQ_WARPS; ++k) usum += S.part[k];
+        float scale = 0.f, inv_scale = 0.f;
+        if (M > 0.f) {
+            const float B = (float)usum * (M * (1.0f / 1048576.0f)) * 1.0001f;
+            scale = fminf(4194304.0f / M, 2147483648.0f / B) * (1.0f - 1.0f / 1024.0f);
+            inv_scale = 1.0f / scale;
+        }
         for (int tt = 0; tt < c.bt; tt += EQ_TT) {
             const int ta = T0 + tt, tb = ta + EQ_TT - 1;   // absolute ticks of the tile
-            for (int pass = 0; pass < passes; ++pass) {
-                const int pb = beg + pass * EQ_CACHE;
-                const int pn = min(EQ_CACHE, end - pb);
-                if (tt == 0 || passes > 1) {
-                    __syncthreads();
-                    for (int k = tid; k < pn; k += EQ_THREADS) rc[k] = recs[dep_index[pb + k]];
-                }
+            int cur = beg;
+            bool first = true;
+            do {   // one pass: a contiguous run [cur, ...) of the block's deposit list
+                __syncthreads();                           // the previous pass is consumed
+                if (tid < 3) S.tot[tid] = 0;
+                for (int k = tid; k < npatch; k += EQ_THREADS) S.bfill[k] = 0;
                 __syncthreads();
-                for (int k = warp; k < pn; k += nwarps) {
-                    const int rt0 = rc[k].t0, rt1 = rc[k].t1;
-                    if (rt1 < ta || rt0 > tb) continue;
-                    const DepRec r = rc[k];
-                    const int xa = max(r.x0, X0) - X0, xb = min(r.x1, X0 + side - 1) - X0;
-                    const int ya = max(r.y0, Y0) - Y0, yb = min(r.y1, Y0 + side - 1) - Y0;
-                    if (xa > xb || ya > yb) continue;
-                    const float *w = wts + (size_t)r.idx * c.wstride;
-                    const float *wxv = w + (X0 - r.gx0);            // indexed by block-local gx
-                    const float *wyv = w + c.wx + (Y0 - r.gy0);     // indexed by block-local gy
-                    float wt[EQ_TT];
-#pragma unroll
-                    for (int e = 0; e < EQ_TT; ++e) {
-                        const int t = ta + e;
-                        wt[e] = (t >= r.t0 && t <= r.t1) ? __ldg(w + 2 * c.wx + (t - r.gt0)) : 0.f;
-                    }
-                    const float qs = r.q * scale;
-                    for (int gy = ya + (lane >> 4); gy <= yb; gy += 2) {
-                        const float ay = qs * __ldg(wyv + gy);
-                        for (int gx = xa + (lane & 15); gx <= xb; gx += 16) {
-                            const float a = ay * __ldg(wxv + gx);
-                            unsigned *cell = tile + gy * side + gx;
-#pragma unroll
-                            for (int e = 0; e < EQ_TT; ++e) atomicAdd(cell + e * plane, __float2uint_rn(a * wt[e]));
+                bool full = false;
+                while (cur < end && !full) {
+                    // (1) evaluate one chunk of the list: overlap, pool floats, bucket slots
+                    const int k = cur + tid;
+                    DepRec r;
+                    int xa = 0, xb = -1, ya = 0, yb = -1, cnt = 0, pl = 0, ins = 0;
+                    if (k < end) {
+                        r = recs[dep_index[k]];
+                        if (!(r.t1 < ta || r.t0 > tb)) {
+                            // clipped ranges, at most len_cap long (the weight capacity bounds
+                            // every accepted support; the cap keeps the indexes in range anyway)
+                            xa = max(r.x0, X0) - X0;
+                            xb = min(min(r.x1, X0 + side - 1) - X0, xa + len_cap - 1);
+                            ya = max(r.y0, Y0) - Y0;
+                            yb = min(min(r.y1, Y0 + side - 1) - Y0, ya + len_cap - 1);
+                            if (xa <= xb && ya <= yb) {
+                                cnt = 1;
+                                pl = (xb - xa + 1) + (yb - ya + 1);
+                                ins = (yb / EQ_PY - ya / EQ_PY + 1) * (xb / EQ_PX - xa / EQ_PX + 1);
+                            }
                         }
                     }
+                    // block-wide inclusive scan of (cnt, pl, ins)
+                    int c1 = cnt, c2 = pl, c3 = ins;
+#pragma unroll
+                    for (int o = 1; o < 32; o <<= 1) {
+                        const int u1 = __shfl_up_sync(0xffffffffu, c1, o);
+                        const int u2 = __shfl_up_sync(0xffffffffu, c2, o);
+                        const int u3 = __shfl_up_sync(0xffffffffu, c3, o);
+                        if (lane >= o) { c1 += u1; c2 += u2; c3 += u3; }
+                    }
+                    int *wp = reinterpret_cast<int *>(S.part);   // [EQ_WARPS][3]
+                    if (lane == 31) { wp[3 * warp] = c1; wp[3 * warp + 1] = c2; wp[3 * warp + 2] = c3; }
+                    __syncthreads();
+                    for (int w2 = 0; w2 < warp; ++w2) { c1 += wp[3 * w2]; c2 += wp[3 * w2 + 1]; c3 += wp[3 * w2 + 2]; }
+                    const int b1 = S.tot[0], b2 = S.tot[1], b3 = S.tot[2];
+                    const bool fits = (b1 + c1 <= EQ_LIST) && (b2 + c2 <= EQ_POOL) && (b3 + c3 <= EQ_INS);
+                    const int acc_n = __syncthreads_count(fits);   // prefix: the totals only grow
+                    if (fits && cnt) {
+                        const int pos = b1 + c1 - 1, po = b2 + c2 - pl;
+                        const size_t base = (size_t)r.idx * c.wstride;
+                        TileEnt en;
+                        en.y0 = ya;
+                        en.y1 = yb;
+                        en.x0 = xa;
+                        en.x1 = xb;
+                        en.qs = __float_as_int(r.q * scale);
+                        en.wxo = po;
+                        en.wyo = po + (xb - xa + 1);
+                        en.idx = r.idx;
+#pragma unroll
+                        for (int e = 0; e < EQ_TT; ++e) {
+                            const int t = ta + e;
+                            en.wt[e] = (t >= r.t0 && t <= r.t1) ? __ldg(wts + base + 2 * c.wx + (t - r.gt0)) : 0.f;
+                        }
+                        int4 *dst = reinterpret_cast<int4 *>(&S.list[pos]);
+                        const int4 *src = reinterpret_cast<const int4 *>(&en);
+#pragma unroll
+                        for (int q = 0; q < 4; ++q) dst[q] = src[q];
+                        for (int qy = ya / EQ_PY; qy <= yb / EQ_PY; ++qy)
+                            for (int qx = xa / EQ_PX; qx <= xb / EQ_PX; ++qx) atomicAdd(&S.bfill[qy * npx + qx], 1);
+                    }
+                    if (tid == acc_n - 1) { S.tot[0] = b1 + c1; S.tot[1] = b2 + c2; S.tot[2] = b3 + c3; }
+                    __syncthreads();
+                    cur += acc_n;
+                    full = acc_n < EQ_THREADS;             // chunk cut short: capacity reached
                 }
-            }
-            __syncthreads();
-            // write the tile (one 32-byte sector per (channel, column) segment), zero it
-            int bit = 0;
-            for (int col = warp; col < cols; col += nwarps) {
-                const int py = col / c.bp, px = col - py * c.bp;
-                for (int ch = lane; ch < nch; ch += 32, ++bit) {
-                    const int jy = ch / c.ns, jx = ch - jy * c.ns;
-                    unsigned *cell = tile + (py * c.ns + jy) * side + px * c.ns + jx;
+                const int ne = S.tot[0];
+                const bool last = cur >= end;
+                // (2) warp 0: bucket offsets; all warps: copy the clipped weight vectors
+                if (warp == 0) {
+                    int carry = 0;
+                    for (int b0 = 0; b0 < npatch; b0 += 32) {
+                        const int k = b0 + lane;
+                        const int v = k < npatch ? S.bfill[k] : 0;
+                        int incl = v;
+#pragma unroll
+                        for (int o = 1; o < 32; o <<= 1) {
+                            const int u = __shfl_up_sync(0xffffffffu, incl, o);
+                            if (lane >= o) incl += u;
+                        }
+                        if (k < npatch) {
+                            S.boff[k] = carry + incl - v;
+                            S.bfill[k] = 0;
+                        }
+                        carry += __shfl_sync(0xffffffffu, incl, 31);
+                    }
+                    if (lane == 0) {
+                        S.boff[npatch] = carry;
+                        S.next = 0;
+                    }
+                }
+                for (int k = warp; k < ne; k += EQ_WARPS) {
+                    const TileEnt &en = S.list[k];
+                    const DepRec r = recs[en.idx];
+                    const float *w = wts + (size_t)en.idx * c.wstride;
+                    const int nx = en.x1 - en.x0 + 1, ny = en.y1 - en.y0 + 1;
+                    for (int q = lane; q < nx; q += 32) S.pool[en.wxo + q] = __ldg(w + (X0 + en.x0 + q - r.gx0));
+                    for (int q = lane; q < ny; q += 32) S.pool[en.wyo + q] = __ldg(w + c.wx + (Y0 + en.y0 + q - r.gy0));
+                }
+                __syncthreads();
+                // (3) bucket fill
+                for (int k = tid; k < ne; k += EQ_THREADS) {
+                    const int4 hy = *reinterpret_cast<const int4 *>(&S.list[k].y0);   // y0 y1 x0 x1
+                    for (int qy = hy.x / EQ_PY; qy <= hy.y / EQ_PY; ++qy)
+                        for (int qx = hy.z / EQ_PX; qx <= hy.w / EQ_PX; ++qx) {
+                            const int b = qy * npx + qx;
+                            S.bucket[S.boff[b] + atomicAdd(&S.bfill[b], 1)] = (uint16_t)k;
+                        }
+                }
+                __syncthreads();
+                // (4) patches, taken one by one by the warps
+                for (;;) {
+                    int pt = 0;
+                    if (lane == 0) pt = atomicAdd(&S.next, 1);
+                    pt = __shfl_sync(0xffffffffu, pt, 0);
+                    if (pt >= npatch) break;
+                    const int qy = pt / npx, qx = pt - qy * npx;
+                    const int gx = qx * EQ_PX + lx, gy = qy * EQ_PY + ly;
+                    const bool own = gx < side && gy < side;
+                    int32_t *sc = scratch + ((size_t)gy * side + gx) * EQ_TT;
+                    int acc[EQ_TT];
+                    if (first || !own) {
+#pragma unroll
+                        for (int e = 0; e < EQ_TT; ++e) acc[e] = 0;
+                    } else {
+                        const int4 u0 = reinterpret_cast<const int4 *>(sc)[0], u1 = reinterpret_cast<const int4 *>(sc)[1];
+                        acc[0] = u0.x; acc[1] = u0.y; acc[2] = u0.z; acc[3] = u0.w;
+                        acc[4] = u1.x; acc[5] = u1.y; acc[6] = u1.z; acc[7] = u1.w;
+                    }
+                    const int kb = S.boff[pt], ke = S.boff[pt + 1];
+                    for (int kk = kb; kk < ke; ++kk) {
+                        const TileEnt &en = S.list[S.bucket[kk]];
+                        const int4 hy = *reinterpret_cast<const int4 *>(&en.y0);     // y0 y1 x0 x1
+                        const int4 hq = *reinterpret_cast<const int4 *>(&en.qs);     // qs wxo wyo
+                        const float4 w0 = *reinterpret_cast<const float4 *>(&en.wt[0]);
+                        const float4 w1 = *reinterpret_cast<const float4 *>(&en.wt[4]);
+                        if (gy >= hy.x && gy <= hy.y && gx >= hy.z && gx <= hy.w) {
+                            const float a = __int_as_float(hq.x) * S.pool[hq.y + gx - hy.z] * S.pool[hq.z + gy - hy.x];
+                            acc[0] += fx_round(a, w0.x);
+                            acc[1] += fx_round(a, w0.y);
+                            acc[2] += fx_round(a, w0.z);
+                            acc[3] += fx_round(a, w0.w);
+                            acc[4] += fx_round(a, w1.x);
+                            acc[5] += fx_round(a, w1.y);
+                            acc[6] += fx_round(a, w1.z);
+                            acc[7] += fx_round(a, w1.w);
+                        }
+                    }
+                    if (!last) {
+                        if (own) {
+                            reinterpret_cast<int4 *>(sc)[0] = make_int4(acc[0], acc[1], acc[2], acc[3]);
+                            reinterpret_cast<int4 *>(sc)[1] = make_int4(acc[4], acc[5], acc[6], acc[7]);
+                        }
+                        continue;
+                    }
+                    int any = 0;
                     float v[EQ_TT];
-                    unsigned any = 0u;
 #pragma unroll
                     for (int e = 0; e < EQ_TT; ++e) {
-                        const unsigned u = cell[e * plane];
-                        cell[e * plane] = 0u;
-                        any |= u;
-                        v[e] = (float)u * inv_scale;
+                        any |= acc[e];
+                        v[e] = (float)acc[e] * inv_scale;
                     }
-                    if (any) nz |= 1u << bit;
-                    float4 *dst = reinterpret_cast<float4 *>(qeff + ((qslot * nch + ch) * cols + col) * c.bt + tt);
-                    dst[0] = make_float4(v[0], v[1], v[2], v[3]);
-                    dst[1] = make_float4(v[4], v[5], v[6], v[7]);
+                    const uint32_t bal = __ballot_sync(0xffffffffu, own && any != 0);
+                    if (lane == 0 && bal) S.nzp[pt] |= bal;       // this warp alone holds patch pt now
+                    if (own) {
+                        float4 *dst = reinterpret_cast<float4 *>(qblk + S.offy[gy] + S.offx[gx] + tt);
+                        dst[0] = make_float4(v[0], v[1], v[2], v[3]);
+                        dst[1] = make_float4(v[4], v[5], v[6], v[7]);
+                    }
                 }
-            }
-            __syncthreads();
-        }
-        {
-            int bit = 0;
-            for (int col = warp; col < cols; col += nwarps)
-                for (int ch = lane; ch < nch; ch += 32, ++bit)
-                    if ((nz >> bit) & 1u) atomicOr(&mask[ch], 1ull << col);
+                first = false;
+            } while (cur < end);
         }
         __syncthreads();
-        for (int k = tid; k < nch; k += EQ_THREADS) colmask[(size_t)slot * nch + k] = mask[k];
+        for (int pt = warp; pt < npatch; pt += EQ_WARPS) {
+            if (!((S.nzp[pt] >> lane) & 1u)) continue;
+            const int qy = pt / npx, qx = pt - qy * npx;
+            const int gx = qx * EQ_PX + lx, gy = qy * EQ_PY + ly;
+            const int py = gy / c.ns, jy = gy - py * c.ns, px = gx / c.ns, jx = gx - px * c.ns;
+            atomicOr(&S.mask[jy * c.ns + jx], 1ull << (py * c.bp + px));
+        }
         __syncthreads();
+        for (int k = tid; k < nch; k += EQ_THREADS) colmask[(size_t)slot * nch + k] = S.mask[k];
     }
+}
+
+size_t effq_scratch_bytes(int side, int sms) {
+    return sizeof(int32_t) * ((size_t)sms * EQ_CTAS_PER_SM * side * side * EQ_TT + 64);
 }
 
 int launch_effq(tred_handle *h, int n, const tred_deposits &deps, const int32_t *block_ids,
@@ -347,19 +519,26 @@ int launch_effq(tred_handle *h, int n, const tred_deposits &deps, const int32_t 
                                                              reinterpret_cast<DepRec *>(h->recs));
     }
     const int nch = c.ns * c.ns;
-    const size_t smem = sizeof(float) * (size_t)nch * c.bp * c.bp * EQ_TT + sizeof(DepRec) * EQ_CACHE +
-                        sizeof(unsigned long long) * nch + sizeof(unsigned long long) * (EQ_THREADS / 32);
+    const int side = c.bp * c.ns;
+    const int len_cap = c.wx < side ? c.wx : side;
+    const int max_ins = ((len_cap + EQ_PY - 2) / EQ_PY + 1) * ((len_cap + EQ_PX - 2) / EQ_PX + 1);
+    if (side > EQ_MAX_SIDE || nch > 128 || 2 * len_cap > EQ_POOL || max_ins > EQ_INS)
+        return set_error(h, TRED_ERR_INVALID_ARG, "effq: bp * n_sub = %d sub-cells (weight length %d) exceeds the tile kernel",
+                         side, c.wx);
+    const size_t smem = sizeof(EffqShared);
     static bool attr_set = false;
     if (!attr_set) {
-        cudaFuncSetAttribute(k_effq_blocks, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+        cudaFuncSetAttribute(k_effq_blocks, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         attr_set = true;
     }
-    if (smem > 227 * 1024)
-        return set_error(h, TRED_ERR_INVALID_ARG, "effq: tile of n_sub^2 bp^2 x 8 ticks exceeds shared memory");
-    const int grid = num_sms(h);
-    k_effq_blocks<<<grid, EQ_THREADS, smem, s>>>(block_ids, dep_offsets, dep_index, n_blocks_dev, c, h->wts,
+    // the block queue counter lives after the per-CTA scratch
+    const int sms = num_sms(h);
+    int32_t *queue = h->effq_acc + (size_t)sms * EQ_CTAS_PER_SM * side * side * EQ_TT;
+    int rc = check_cuda(h, cudaMemsetAsync(queue, 0, sizeof(int32_t), s), "effq queue reset");
+    if (rc) return rc;
+    k_effq_blocks<<<sms * EQ_CTAS_PER_SM, EQ_THREADS, smem, s>>>(block_ids, dep_offsets, dep_index, n_blocks_dev, c, h->wts,
                                                  reinterpret_cast<const DepRec *>(h->recs), qeff, h->colmask,
-                                                 slot_base, slot_count);
+                                                 h->effq_acc, queue, slot_base, slot_count);
     h->launches += 1 + (n > 0 && slot_base == 0 ? 1 : 0);
     return check_cuda(h, cudaGetLastError(), "effq launch");
 }

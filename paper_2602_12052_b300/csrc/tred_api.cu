@@ -174,6 +174,7 @@ int32_t tred_create(const tred_geometry *geom, const tred_params *params, int32_
     alloc((void **)&h->dep_event, sizeof(int32_t) * (size_t)max_deposits, "alloc deposit events");
     alloc((void **)&h->wts, sizeof(float) * (size_t)max_deposits * d.wstride, "alloc weights");
     alloc((void **)&h->recs, 48 * (size_t)max_deposits, "alloc deposit records");
+    alloc((void **)&h->effq_acc, effq_scratch_bytes(geom->bp * ns, num_sms(h)), "alloc effq scratch");
     alloc((void **)&h->blk_count, sizeof(int32_t) * (size_t)d.nblk, "alloc block counts");
     alloc((void **)&h->blk_slot, sizeof(int32_t) * (size_t)d.nblk, "alloc block slots");
     alloc((void **)&h->blk_fill, sizeof(int32_t) * (size_t)max_blocks, "alloc fill");
@@ -234,7 +235,7 @@ int32_t tred_create(const tred_geometry *geom, const tred_params *params, int32_
 
 int32_t tred_destroy(tred_handle *h) {
     if (!h) return TRED_ERR_INVALID_ARG;
-    void *ptrs[] = {h->dep_event, h->wts2, h->pix_row, h->gspec, h->rhat, h->pair_j, h->wts, h->recs, h->blk_count, h->blk_slot, h->blk_fill,
+    void *ptrs[] = {h->dep_event, h->wts2, h->pix_row, h->gspec, h->rhat, h->pair_j, h->wts, h->recs, h->effq_acc, h->blk_count, h->blk_slot, h->blk_fill,
                     h->scan_part, h->colmask, h->yspec, h->pix_flag, h->pix_part, h->hit_cnt,
                     h->hit_tmp, h->hit_tmpc, h->status, h->tw};
     for (void *p : ptrs)

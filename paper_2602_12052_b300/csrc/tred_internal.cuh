@@ -45,6 +45,7 @@ struct tred_handle {
     int32_t *dep_event;    // [max_deposits] event of each deposit (written by drift)
     float *wts;            // [max_deposits][wstride] per-deposit 1-D weights
     void *recs;            // [max_deposits] 48-byte per-deposit records for effq
+    int32_t *effq_acc;     // [SMs][(bp n_sub)^2][8] integer partial sums of multi-pass blocks
     int32_t *blk_count;    // [nblk] occupancy
     int32_t *blk_slot;     // [nblk] slot of an active block or -1
     int32_t *blk_fill;     // [max_blocks] CSR fill cursors
@@ -94,6 +95,7 @@ int launch_drift(tred_handle *h, int n, const float *x, const float *y, const fl
 int launch_blockbin(tred_handle *h, int n, const tred_deposits &deps, int32_t *block_ids,
                     int32_t *block_counts, int32_t *dep_offsets, int32_t *dep_index,
                     int32_t max_pairs, int32_t *n_blocks_dev, cudaStream_t s);
+size_t effq_scratch_bytes(int side, int grid);
 int launch_effq(tred_handle *h, int n, const tred_deposits &deps, const int32_t *block_ids,
                 const int32_t *dep_offsets, const int32_t *dep_index,
                 const int32_t *n_blocks_dev, float *qeff, int slot_base, int slot_count, cudaStream_t s);

@@ -128,6 +128,19 @@ def test_single_deposit_and_off_plane_and_edges():
     assert res["status"][1] == 2           # two off-plane deposits dropped
 
 
+def test_dense_block_multipass():
+    """2500 deposits packed into one block's footprint: the effective-charge kernel
+    takes several passes over the block's deposit list (its list holds 512)."""
+    cfg = synth.get_config("tiny")
+    resp = synth.make_response(cfg)
+    rng = np.random.default_rng(21)
+    n = 2500
+    dep = _dep(rng.uniform(3.6, 6.8, n), rng.uniform(3.6, 6.8, n), rng.uniform(0.5, 1.5, n), t0=2.0,
+               ne=rng.uniform(100.0, 900.0, n))
+    res, ref, _ = _full_check(cfg, dep, resp, check_readout=False)
+    assert res["block_counts"].max() > 1024
+
+
 def test_capacity_overflow_sets_status():
     cfg = synth.get_config("tiny")
     dep, resp = synth.make_event(cfg)
