@@ -174,13 +174,13 @@ __global__ void __launch_bounds__(AS_THREADS, 1)
         __syncthreads();
         // ---- per channel pair: conj(Rhat) Dhat, inverse spatial FFT onto the bp x bp inputs
         for (int p = 0; p < c.npairs; ++p) {
-            const float2 *rp = rhat + ((size_t)k1 * c.npairs + p) * BINS * (LP * LP);
+            const float2 *rp = rhat;   // bin f = k1 + G k2 at rhat_bin(f, p, npairs, lt / 32)
             float2 *gdst = gspec + (((size_t)sl * c.npairs + p) * LT) * 64;
             for (int it = 0; it < BINS / (2 * AS_WARPS); ++it) {
                 const int b = lane >> 4, kx = lane & 15;
                 const int k2 = (BINS / AS_WARPS) * warp + 2 * it + b;
                 const float2 *d = dh + k2 * DH_BIN + kx;
-                const float2 *rsrc = rp + (size_t)k2 * (LP * LP) + kx;
+                const float2 *rsrc = rp + rhat_bin(k1 + G * k2, p, c.npairs, LT / 32) + kx;
                 float2 v[LP];
 #pragma unroll
                 for (int ky = 0; ky < LP; ++ky) v[ky] = cmul(cconj(__ldg(rsrc + ky * LP)), d[ky * DH_ROW]);

@@ -16,9 +16,13 @@
 //                 pre-butterfly over the nonzero n1 = 0..bt/64-1 blocks of the
 //                 input followed by a 64-point FFT across the warp); stage B does
 //                 the 16 x 16 spatial FFT of every bin (8-point in-lane FFTs and a
-//                 per-warp shared transpose) and accumulates Rhat * Z in shared
-//                 memory.  The epilogue inverts the spatial FFT and writes the bins
-//                 of the class to the per-chunk spectrum buffer.
+//                 per-warp shared transpose) and accumulates Rhat * Z in tensor
+//                 memory: each warp owns 64 TMEM columns of its lane quarter, one
+//                 lane per (bin, kx) with the 16 ky values of two bins, read and
+//                 written with tcgen05.ld / tcgen05.st, so the sum over channel pairs
+//                 takes no shared-memory bandwidth.  The epilogue inverts the spatial
+//                 FFT from the registers and writes the class's bins to the
+//                 per-chunk spectrum buffer.
 //   k_conv_itime  one CTA per (block, mirror row pair, half): inverse time FFT of
 //                 16 columns (8 mirror pairs) and the MPCP recombination.
 #include <utility>
@@ -33,8 +37,7 @@ struct ConvConst {
 
 constexpr int SPEC_THREADS = 512;
 constexpr int SPEC_WARPS = SPEC_THREADS / 32;
-constexpr int ACC_ROW = 18;                 // padded kx row (float2) of the accumulator: 16 ky + 2
-constexpr int ACC_BIN = LP * ACC_ROW;       // 288 float2 per bin; layout [k2][kx][ky]
+constexpr int SPEC_TMEM_COLS = 256;         // 4 warps per lane quarter x 64 columns
 constexpr int ZT_ROW = 9;                   // padded px row of the bin-major transpose
 constexpr int ZT_BIN = 8 * ZT_ROW + 1;      // [py][px] for py, px < 8, odd stride
 // Bin order inside the transpose buffer.  Stage A lane l stores bins k2 = a + 2 b
@@ -45,8 +48,10 @@ __device__ __forceinline__ int zt_slot(int k2) { return ((k2 & 1) << 5) | (((k2 
 constexpr int TB_ROW = 9;                   // per-warp transpose rows [kx][py]
 constexpr int TB_BIN = LP * TB_ROW;
 
-constexpr size_t SPEC_SMEM = sizeof(float2) * ((size_t)BINS * ACC_BIN + (size_t)BINS * ZT_BIN +
-                                               (size_t)SPEC_WARPS * 2 * TB_BIN + 32 + 16 + 8 + 64);
+constexpr int EP_ROW = LP + 1;              // epilogue transpose [cy][kx + pad]
+constexpr int EP_BIN = LP * EP_ROW;
+constexpr size_t SPEC_SMEM = sizeof(float2) * ((size_t)BINS * ZT_BIN + (size_t)SPEC_WARPS * 2 * TB_BIN +
+                                               (size_t)SPEC_WARPS * 2 * EP_BIN + 32 + 16 + 8 + 64 + 2);
 
 template <int NB1, int G>
 __global__ void __launch_bounds__(SPEC_THREADS, 1)
@@ -56,28 +61,37 @@ __global__ void __launch_bounds__(SPEC_THREADS, 1)
                 float2 *__restrict__ yspec, int slot_base, int slot_count, int qbase) {
     constexpr int LT = 64 * G;
     extern __shared__ float2 smem[];
-    float2 *acc = smem;                               // [64][16 kx][18]
-    float2 *zt = acc + BINS * ACC_BIN;                // [64][8][9]
+    float2 *zt = smem;                                // [64][8][9]
     float2 *tbuf = zt + BINS * ZT_BIN;                // [warps][2][16][9]
-    float2 *w32 = tbuf + SPEC_WARPS * 2 * TB_BIN;     // W_32
+    float2 *ebuf = tbuf + SPEC_WARPS * 2 * TB_BIN;    // [warps][2][16][17]
+    float2 *w32 = ebuf + SPEC_WARPS * 2 * EP_BIN;     // W_32
     float2 *w16 = w32 + 32;                           // W_16
     float2 *w8 = w16 + 16;                            // W_8
     float2 *w64 = w8 + 8;                             // W_64
+    uint32_t *tslot = reinterpret_cast<uint32_t *>(w64 + 64);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    if (warp == 0) {
+        tmem_alloc(tslot, SPEC_TMEM_COLS);
+        tmem_relinquish();
+    }
     if (tid < 32) w32[tid] = tw[TW_32 + tid];
     if (tid < 16) w16[tid] = tw[TW_16 + tid];
     if (tid < 8) w8[tid] = tw[TW_8 + tid];
     if (tid < 64) w64[tid] = tw[TW_64 + tid];
     for (int k = tid; k < BINS * ZT_BIN; k += SPEC_THREADS) zt[k] = make_float2(0.f, 0.f);
+    tmem_fence_before();
     __syncthreads();
+    tmem_fence_after();
+    // this warp's accumulator columns: lane quarter warp % 4, columns (warp / 4) * 64 + 32 it
+    const uint32_t tacc = *tslot + ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)(64 * (warp >> 2));
 
     const int nb = n_blocks_dev[0];
-    const int nloc = min(slot_count, nb - slot_base);
-    if (nloc <= 0) return;
+    const int nloc = max(0, min(slot_count, nb - slot_base));
     const int cols = c.bp * c.bp;
     const int slab = cols * c.bt;
     const int items = nloc * G;
     float2 *tb = tbuf + warp * 2 * TB_BIN;
+    float2 *eb = ebuf + warp * 2 * EP_BIN;
 
     for (int item = blockIdx.x; item < items; item += gridDim.x) {
         const int sl = item / G, k1 = item % G;
@@ -89,8 +103,13 @@ __global__ void __launch_bounds__(SPEC_THREADS, 1)
         const float2 wl0 = tw[TW_LT + (k1 * lane) % LT];
         const float2 wl1 = tw[TW_LT + (k1 * (lane + 32)) % LT];
         const float2 w64l = w64[lane];
-        for (int k = tid; k < BINS * ACC_BIN; k += SPEC_THREADS) acc[k] = make_float2(0.f, 0.f);
-        __syncthreads();
+        {
+            float z[32];
+#pragma unroll
+            for (int k = 0; k < 32; ++k) z[k] = 0.f;
+            tmem_st32(tacc, z);
+            tmem_st32(tacc + 32, z);
+        }
 
         const float *qblk = qeff + (size_t)(slot - qbase) * c.nch * slab;
         const uint64_t *mrow = colmask + (size_t)slot * c.nch;
@@ -130,7 +149,6 @@ __global__ void __launch_bounds__(SPEC_THREADS, 1)
             }
             __syncthreads();
             // ---------------- stage B: spatial FFT per bin, product with Rhat, accumulate
-            const float2 *rp = rhat + ((size_t)k1 * c.npairs + p) * BINS * (LP * LP);
 #pragma unroll 1
             for (int it = 0; it < BINS / (2 * SPEC_WARPS); ++it) {
                 const int b = lane >> 4;
@@ -139,7 +157,7 @@ __global__ void __launch_bounds__(SPEC_THREADS, 1)
                 // 16 lanes of a bin read one contiguous 128-byte ky row per load
                 const int kx = lane & 15;
                 float2 rr[LP];
-                const float2 *rsrc = rp + (size_t)k2 * (LP * LP) + kx;
+                const float2 *rsrc = rhat + rhat_bin(k1 + G * k2, p, c.npairs, 2 * G) + kx;
 #pragma unroll
                 for (int ky = 0; ky < LP; ++ky) rr[ky] = __ldg(rsrc + ky * LP);
                 // x stage: lane = (b, py, h): 8-point FFT of the (twiddled) row
@@ -171,49 +189,56 @@ __global__ void __launch_bounds__(SPEC_THREADS, 1)
                     }
                     fft_reg_dif_c<8, false>(e);
                     fft_reg_dif_c<8, false>(o);
-                    float4 *ab = reinterpret_cast<float4 *>(acc + k2 * ACC_BIN + kx * ACC_ROW);
+                    float a[32];                               // columns 2 ky + {re, im}
+                    tmem_ld32(tacc + 32 * it, a);
 #pragma unroll
                     for (int k = 0; k < 8; ++k) {
                         const int q = bitrev<8>(k);            // ky pair (2q, 2q + 1)
-                        const float4 a = ab[q];
-                        const float2 a0 = cfma(e[k], rr[2 * q], make_float2(a.x, a.y));
-                        const float2 a1 = cfma(o[k], rr[2 * q + 1], make_float2(a.z, a.w));
-                        ab[q] = make_float4(a0.x, a0.y, a1.x, a1.y);
+                        const float2 a0 = cfma(e[k], rr[2 * q], make_float2(a[4 * q], a[4 * q + 1]));
+                        const float2 a1 = cfma(o[k], rr[2 * q + 1], make_float2(a[4 * q + 2], a[4 * q + 3]));
+                        a[4 * q] = a0.x;
+                        a[4 * q + 1] = a0.y;
+                        a[4 * q + 2] = a1.x;
+                        a[4 * q + 3] = a1.y;
                     }
+                    tmem_st32(tacc + 32 * it, a);
                 }
                 __syncwarp();
             }
             __syncthreads();
         }
-        // ---------------- epilogue: inverse spatial FFT of every bin, in place
+        // ---------------- epilogue: inverse spatial FFT of every bin from the accumulator
 #pragma unroll 1
         for (int it = 0; it < BINS / (2 * SPEC_WARPS); ++it) {
             const int b = lane >> 4, r = lane & 15;
             const int k2 = (BINS / SPEC_WARPS) * warp + 2 * it + b;
-            float2 *ab = acc + k2 * ACC_BIN;
+            float a[32];
+            tmem_ld32(tacc + 32 * it, a);
             float2 v[LP];
 #pragma unroll
-            for (int y = 0; y < LP; ++y) v[y] = ab[r * ACC_ROW + y];        // kx = r: over ky
-            fft_reg_dif_c<LP, true>(v);
+            for (int ky = 0; ky < LP; ++ky) v[ky] = make_float2(a[2 * ky], a[2 * ky + 1]);   // kx = r
+            fft_reg_dif_c<LP, true>(v);                   // over ky: v[k] holds cy = bitrev16(k)
 #pragma unroll
-            for (int k = 0; k < LP; ++k) ab[r * ACC_ROW + bitrev<LP>(k)] = v[k];   // -> [kx][cy]
+            for (int k = 0; k < LP; ++k) eb[b * EP_BIN + bitrev<LP>(k) * EP_ROW + r] = v[k];
             __syncwarp();
 #pragma unroll
-            for (int x = 0; x < LP; ++x) v[x] = ab[x * ACC_ROW + r];        // cy = r: over kx
-            fft_reg_dif_c<LP, true>(v);
-            __syncwarp();
+            for (int x = 0; x < LP; ++x) v[x] = eb[b * EP_BIN + r * EP_ROW + x];   // cy = r over kx
+            fft_reg_dif_c<LP, true>(v);                   // v[k] holds cx = bitrev16(k)
+            float2 o[LP];
 #pragma unroll
-            for (int k = 0; k < LP; ++k) ab[bitrev<LP>(k) * ACC_ROW + r] = v[k];   // -> [cx][cy]
+            for (int k = 0; k < LP; ++k) o[bitrev<LP>(k)] = v[k];
+            float4 *dst = reinterpret_cast<float4 *>(yspec + ((size_t)sl * LT + (k1 + G * k2)) * (LP * LP) + r * LP);
+#pragma unroll
+            for (int x = 0; x < LP; x += 2) dst[x / 2] = make_float4(o[x].x, o[x].y, o[x + 1].x, o[x + 1].y);
             __syncwarp();
         }
-        __syncthreads();
-        // write the class's bins: yspec[sl][f][cy*16+cx], f = k1 + G k2
-        for (int k = tid; k < BINS * LP * LP; k += SPEC_THREADS) {
-            const int k2 = k >> 8, cidx = k & 255;
-            const int cy = cidx >> 4, cx = cidx & 15;
-            yspec[((size_t)sl * LT + (k1 + G * k2)) * (LP * LP) + cidx] = acc[k2 * ACC_BIN + cx * ACC_ROW + cy];
-        }
-        __syncthreads();
+    }
+    // release the accumulator columns once every warp is done with them
+    tmem_fence_before();
+    __syncthreads();
+    if (warp == 0) {
+        tmem_fence_after();
+        tmem_dealloc(*tslot, SPEC_TMEM_COLS);
     }
 }
 

@@ -12,10 +12,10 @@
 //
 //   k_effq_weights  one warp per deposit: the three 1-D weight vectors over the
 //                   support [lo-1, hi+1], stored contiguously per deposit
-//   k_effq_blocks   persistent CTAs over active blocks, 8-tick tiles of all
-//                   channels x columns in shared memory; each deposit is visited once
-//                   per tile it overlaps; tiles written as full 32-byte sectors; plus
-//                   the mask of non-empty (py, px) columns per channel
+//   k_effq_blocks   CTAs take active blocks from a queue; 32-tick tiles of the
+//                   block's sub-cell plane accumulated in registers per 8 x 4 patch
+//                   from per-tile deposit buckets, exact integer sums; plus the mask
+//                   of non-empty (py, px) columns per channel
 #include "tred_internal.cuh"
 
 namespace tred {
@@ -44,10 +44,10 @@ __device__ __forceinline__ float gauss(float d, float inv_sig, float norm) {
     return norm * expf(-0.5f * u * u);
 }
 
-// GL weight of grid point g (offset k = g - (lo - 1)) for a deposit with
-// mean cell + frac and width sig.
-__device__ float weight_gl(int g, int cell, float frac, float sig, int lo, int hi,
-                           const EffqConst &c) {
+// GL weight of grid point g for a deposit with mean cell + frac and width sig, for
+// an order-GL rule (compile-time, so the nodes and weights stay in registers).
+template <int GL>
+__device__ float weight_gl(int g, int cell, float frac, float sig, int lo, int hi, const EffqConst &c) {
     const float inv_sig = 1.0f / sig;
     const float norm = 0.3989422804014327f * inv_sig;   // 1 / (sqrt(2 pi) sig)
     float e = 0.f;
@@ -56,7 +56,8 @@ __device__ float weight_gl(int g, int cell, float frac, float sig, int lo, int h
         const int C = g + dc;
         if (C < lo || C > hi) continue;
         const float base = (float)(C - cell);
-        for (int l = 0; l < c.gl; ++l) {
+#pragma unroll
+        for (int l = 0; l < GL; ++l) {
             const float s = 0.5f * c.xi[l];
             float u;
             if (dc == 0) u = 1.f - fabsf(s);
@@ -100,6 +101,8 @@ __device__ float weight_tent(int g, int cell, float frac, float sig, int lo, int
     return (float)(left + right);
 }
 
+// GL = 0: exact-tent weights; otherwise the order-GL rule.
+template <int GL>
 __global__ void __launch_bounds__(256) k_effq_weights(int n, tred_deposits d, EffqConst c,
                                                       const int32_t *__restrict__ dep_event,
                                                       float *__restrict__ wts, DepRec *__restrict__ recs) {
@@ -138,24 +141,24 @@ __global__ void __launch_bounds__(256) k_effq_weights(int n, tred_deposits d, Ef
         const int len = min(hi[ax] - lo[ax] + 3, cap);
         for (int k = lane; k < len; k += 32) {
             const int g = lo[ax] - 1 + k;
-            wa[k] = c.mode == 1 ? weight_tent(g, cell[ax], frac[ax], sig[ax], lo[ax], hi[ax])
-                                : weight_gl(g, cell[ax], frac[ax], sig[ax], lo[ax], hi[ax], c);
+            wa[k] = GL == 0 ? weight_tent(g, cell[ax], frac[ax], sig[ax], lo[ax], hi[ax])
+                            : weight_gl<GL>(g, cell[ax], frac[ax], sig[ax], lo[ax], hi[ax], c);
         }
     }
 }
 
 // Effective charge of the active blocks: CTAs take blocks from a queue; per block,
-// 8-tick tiles with the accumulation in registers.
+// 32-tick tiles with the accumulation in registers.
 //
 // The block's sub-cell plane is cut into 8 x 4 patches (gx x gy); a lane owns one
-// sub-cell of a patch with that cell's 8 ticks in registers, and the warps of the
+// sub-cell of a patch with that cell's 32 ticks in registers, and the warps of the
 // CTA take patches one by one.  Per tile the CTA lists, in shared memory, the
-// deposits whose support meets the tile (clipped ranges, scaled charge, the tile's 8
+// deposits whose support meets the tile (clipped ranges, scaled charge, the tile's 32
 // time weights, and the clipped x and y weight vectors copied into a pool) and sorts
 // the list into per-patch buckets (count, scan, fill), so a warp walks only the
 // deposits that reach its patch.  No cell is written by two threads: no atomics on
-// data and no shared-memory tile; each lane writes its 8 ticks as one 32-byte
-// sector of the [jy][jx][py][px][t] layout.
+// data and no shared-memory tile; each lane writes its 32 ticks as four 32-byte
+// sectors of the [jy][jx][py][px][t] layout.
 //
 // The sums are exact integers.  Every contribution q e_x e_y e_t has magnitude at
 // most q m_x m_y m_t, where m_a is the deposit's largest weight on axis a inside
@@ -170,8 +173,8 @@ __global__ void __launch_bounds__(256) k_effq_weights(int n, tred_deposits d, Ef
 // bucket slots) is processed in passes, each a contiguous run of the block's
 // deposit list chosen by a block-wide scan; the integer partial sums of the cells
 // are kept in a per-CTA global scratch between passes.
-constexpr int EQ_TT = 8;
-constexpr int EQ_WARPS = 10;
+constexpr int EQ_TT = 32;
+constexpr int EQ_WARPS = 8;
 constexpr int EQ_THREADS = EQ_WARPS * 32;
 constexpr int EQ_CTAS_PER_SM = 2;
 constexpr int EQ_LIST = 256;                 // tile-list entries per pass
@@ -188,7 +191,7 @@ struct TileEnt {
     int qs, wxo, wyo, idx;       // q * S (float bits); pool offsets of the x and y weights; deposit
     float wt[EQ_TT];             // time weights of the tile's ticks, zero outside the support
 };
-static_assert(sizeof(TileEnt) == 64, "tile list entry");
+static_assert(sizeof(TileEnt) == 32 + 4 * EQ_TT, "tile list entry");
 
 struct EffqShared {
     TileEnt list[EQ_LIST];
@@ -356,7 +359,7 @@ __global__ void __launch_bounds__(EQ_THREADS, EQ_CTAS_PER_SM) k_effq_blocks(
                         int4 *dst = reinterpret_cast<int4 *>(&S.list[pos]);
                         const int4 *src = reinterpret_cast<const int4 *>(&en);
 #pragma unroll
-                        for (int q = 0; q < 4; ++q) dst[q] = src[q];
+                        for (int q = 0; q < (int)(sizeof(TileEnt) / 16); ++q) dst[q] = src[q];
                         for (int qy = ya / EQ_PY; qy <= yb / EQ_PY; ++qy)
                             for (int qx = xa / EQ_PX; qx <= xb / EQ_PX; ++qx) atomicAdd(&S.bfill[qy * npx + qx], 1);
                     }
@@ -424,33 +427,34 @@ __global__ void __launch_bounds__(EQ_THREADS, EQ_CTAS_PER_SM) k_effq_blocks(
 #pragma unroll
                         for (int e = 0; e < EQ_TT; ++e) acc[e] = 0;
                     } else {
-                        const int4 u0 = reinterpret_cast<const int4 *>(sc)[0], u1 = reinterpret_cast<const int4 *>(sc)[1];
-                        acc[0] = u0.x; acc[1] = u0.y; acc[2] = u0.z; acc[3] = u0.w;
-                        acc[4] = u1.x; acc[5] = u1.y; acc[6] = u1.z; acc[7] = u1.w;
+#pragma unroll
+                        for (int e4 = 0; e4 < EQ_TT; e4 += 4) {
+                            const int4 u = reinterpret_cast<const int4 *>(sc)[e4 / 4];
+                            acc[e4] = u.x; acc[e4 + 1] = u.y; acc[e4 + 2] = u.z; acc[e4 + 3] = u.w;
+                        }
                     }
                     const int kb = S.boff[pt], ke = S.boff[pt + 1];
                     for (int kk = kb; kk < ke; ++kk) {
                         const TileEnt &en = S.list[S.bucket[kk]];
                         const int4 hy = *reinterpret_cast<const int4 *>(&en.y0);     // y0 y1 x0 x1
                         const int4 hq = *reinterpret_cast<const int4 *>(&en.qs);     // qs wxo wyo
-                        const float4 w0 = *reinterpret_cast<const float4 *>(&en.wt[0]);
-                        const float4 w1 = *reinterpret_cast<const float4 *>(&en.wt[4]);
                         if (gy >= hy.x && gy <= hy.y && gx >= hy.z && gx <= hy.w) {
                             const float a = __int_as_float(hq.x) * S.pool[hq.y + gx - hy.z] * S.pool[hq.z + gy - hy.x];
-                            acc[0] += fx_round(a, w0.x);
-                            acc[1] += fx_round(a, w0.y);
-                            acc[2] += fx_round(a, w0.z);
-                            acc[3] += fx_round(a, w0.w);
-                            acc[4] += fx_round(a, w1.x);
-                            acc[5] += fx_round(a, w1.y);
-                            acc[6] += fx_round(a, w1.z);
-                            acc[7] += fx_round(a, w1.w);
+#pragma unroll
+                            for (int e4 = 0; e4 < EQ_TT; e4 += 4) {
+                                const float4 w = *reinterpret_cast<const float4 *>(&en.wt[e4]);
+                                acc[e4] += fx_round(a, w.x);
+                                acc[e4 + 1] += fx_round(a, w.y);
+                                acc[e4 + 2] += fx_round(a, w.z);
+                                acc[e4 + 3] += fx_round(a, w.w);
+                            }
                         }
                     }
                     if (!last) {
                         if (own) {
-                            reinterpret_cast<int4 *>(sc)[0] = make_int4(acc[0], acc[1], acc[2], acc[3]);
-                            reinterpret_cast<int4 *>(sc)[1] = make_int4(acc[4], acc[5], acc[6], acc[7]);
+#pragma unroll
+                            for (int e4 = 0; e4 < EQ_TT; e4 += 4)
+                                reinterpret_cast<int4 *>(sc)[e4 / 4] = make_int4(acc[e4], acc[e4 + 1], acc[e4 + 2], acc[e4 + 3]);
                         }
                         continue;
                     }
@@ -465,8 +469,8 @@ __global__ void __launch_bounds__(EQ_THREADS, EQ_CTAS_PER_SM) k_effq_blocks(
                     if (lane == 0 && bal) S.nzp[pt] |= bal;       // this warp alone holds patch pt now
                     if (own) {
                         float4 *dst = reinterpret_cast<float4 *>(qblk + S.offy[gy] + S.offx[gx] + tt);
-                        dst[0] = make_float4(v[0], v[1], v[2], v[3]);
-                        dst[1] = make_float4(v[4], v[5], v[6], v[7]);
+#pragma unroll
+                        for (int e4 = 0; e4 < EQ_TT; e4 += 4) dst[e4 / 4] = make_float4(v[e4], v[e4 + 1], v[e4 + 2], v[e4 + 3]);
                     }
                 }
                 first = false;
@@ -515,8 +519,20 @@ int launch_effq(tred_handle *h, int n, const tred_deposits &deps, const int32_t 
     if (n > 0 && slot_base == 0) {   // once per pass: the range starting at slot 0 computes the weights
         const int threads = 256;
         const int64_t blocks = ((int64_t)n * 32 + threads - 1) / threads;
-        k_effq_weights<<<(unsigned)blocks, threads, 0, s>>>(n, deps, c, h->dep_event, h->wts,
-                                                             reinterpret_cast<DepRec *>(h->recs));
+        auto go = [&](auto kern) {
+            kern<<<(unsigned)blocks, threads, 0, s>>>(n, deps, c, h->dep_event, h->wts, reinterpret_cast<DepRec *>(h->recs));
+        };
+        switch (c.mode == 1 ? 0 : c.gl) {
+        case 0: go(k_effq_weights<0>); break;
+        case 1: go(k_effq_weights<1>); break;
+        case 2: go(k_effq_weights<2>); break;
+        case 3: go(k_effq_weights<3>); break;
+        case 4: go(k_effq_weights<4>); break;
+        case 5: go(k_effq_weights<5>); break;
+        case 6: go(k_effq_weights<6>); break;
+        case 7: go(k_effq_weights<7>); break;
+        default: go(k_effq_weights<8>); break;
+        }
     }
     const int nch = c.ns * c.ns;
     const int side = c.bp * c.ns;

@@ -8,9 +8,9 @@
 // (the spatial sign is + because R[j, k] = i[j, -k]; the 1/N of the inverse FFT
 // is folded in).  Evaluated once per response as two direct DFT stages in FP64
 // with exact twiddle arguments, rounded to complex64, and stored as
-//   rhat[k1][pair][k2][ky * 16 + kx]   with f = k1 + G k2,
-// so that the convolution CTA owning time-frequency class k1 streams one
-// contiguous slab per channel pair.
+//   rhat[k1][pair][k2][ky * 16 + kx]   with f = k1 + G2 k2, G2 = lt / 32,
+// so that the convolution CTA owning the 32 bins of class k1 streams one
+// contiguous 64 KB slab per channel pair.
 #include <cmath>
 #include <vector>
 
@@ -46,7 +46,7 @@ __global__ void k_resp_time(const float *__restrict__ resp, const int32_t *__res
 }
 
 // Stage 2: spatial DFT with the + sign, scaling, layout change to the conv order.
-__global__ void k_resp_space(const double2 *__restrict__ T, int npairs, int kp, int lt, int G,
+__global__ void k_resp_space(const double2 *__restrict__ T, int npairs, int kp, int lt, int G2,
                              const double2 *__restrict__ w16, double scale,
                              float2 *__restrict__ rhat) {
     const int R = (kp - 1) / 2;
@@ -71,14 +71,13 @@ __global__ void k_resp_space(const double2 *__restrict__ T, int npairs, int kp, 
                 re += t.x * wr - t.y * wi;
                 im += t.x * wi + t.y * wr;
             }
-        const int k1 = f % G, k2 = f / G;
-        rhat[(((int64_t)k1 * npairs + p) * BINS + k2) * (LP * LP) + ky * LP + kx] =
+        rhat[rhat_bin(f, p, npairs, G2) + ky * LP + kx] =
             make_float2((float)(re * scale), (float)(im * scale));
     }
 }
 
 int launch_response(tred_handle *h, const float *resp, cudaStream_t s) {
-    const int kp = h->g.kp, ns = h->g.n_sub, nr = h->g.nr, lt = h->g.lt, G = h->d.G;
+    const int kp = h->g.kp, ns = h->g.n_sub, nr = h->g.nr, lt = h->g.lt, G2 = lt / 32;
     const int NP = h->d.npairs;
     std::vector<double2> wlt(lt), w16(LP);
     for (int k = 0; k < lt; ++k) {
@@ -100,7 +99,7 @@ int launch_response(tred_handle *h, const float *resp, cudaStream_t s) {
         const int grid = num_sms(h) * 8;
         k_resp_time<<<grid, 256, 0, s>>>(resp, h->pair_j, NP, kp, ns, nr, lt, d_wlt, d_T);
         const double scale = 1.0 / ((double)LP * LP * lt);
-        k_resp_space<<<grid, 256, 0, s>>>(d_T, NP, kp, lt, G, d_w16, scale, h->rhat);
+        k_resp_space<<<grid, 256, 0, s>>>(d_T, NP, kp, lt, G2, d_w16, scale, h->rhat);
         h->launches += 2;
         rc = check_cuda(h, cudaGetLastError(), "response launch");
     }
