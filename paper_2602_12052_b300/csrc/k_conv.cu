@@ -38,6 +38,7 @@ struct ConvConst {
 constexpr int SPEC_THREADS = 512;
 constexpr int SPEC_WARPS = SPEC_THREADS / 32;
 constexpr int SPEC_TMEM_COLS = 256;         // 4 warps per lane quarter x 64 columns
+constexpr int PG = 4;                       // channel pairs per stage A / stage B round
 constexpr int ZT_ROW = 9;                   // padded px row of the bin-major transpose
 constexpr int ZT_BIN = 8 * ZT_ROW + 1;      // [py][px] for py, px < 8, odd stride
 // Bin order inside the transpose buffer.  Stage A lane l stores bins k2 = a + 2 b
@@ -50,8 +51,9 @@ constexpr int TB_BIN = LP * TB_ROW;
 
 constexpr int EP_ROW = LP + 1;              // epilogue transpose [cy][kx + pad]
 constexpr int EP_BIN = LP * EP_ROW;
-constexpr size_t SPEC_SMEM = sizeof(float2) * ((size_t)BINS * ZT_BIN + (size_t)SPEC_WARPS * 2 * TB_BIN +
-                                               (size_t)SPEC_WARPS * 2 * EP_BIN + 32 + 16 + 8 + 64 + 2);
+static_assert(SPEC_WARPS * 2 * EP_BIN <= PG * BINS * ZT_BIN, "the epilogue transpose reuses the stage A buffers");
+constexpr size_t SPEC_SMEM = sizeof(float2) * ((size_t)PG * BINS * ZT_BIN + (size_t)SPEC_WARPS * 2 * TB_BIN +
+                                               32 + 16 + 8 + 64 + 2);
 
 template <int NB1, int G>
 __global__ void __launch_bounds__(SPEC_THREADS, 1)
@@ -61,10 +63,10 @@ __global__ void __launch_bounds__(SPEC_THREADS, 1)
                 float2 *__restrict__ yspec, int slot_base, int slot_count, int qbase) {
     constexpr int LT = 64 * G;
     extern __shared__ float2 smem[];
-    float2 *zt = smem;                                // [64][8][9]
-    float2 *tbuf = zt + BINS * ZT_BIN;                // [warps][2][16][9]
-    float2 *ebuf = tbuf + SPEC_WARPS * 2 * TB_BIN;    // [warps][2][16][17]
-    float2 *w32 = ebuf + SPEC_WARPS * 2 * EP_BIN;     // W_32
+    float2 *zt = smem;                                // [PG][64][8][9]
+    float2 *ebuf = smem;                              // [warps][2][16][17], epilogue only
+    float2 *tbuf = zt + PG * BINS * ZT_BIN;           // [warps][2][16][9]
+    float2 *w32 = tbuf + SPEC_WARPS * 2 * TB_BIN;     // W_32
     float2 *w16 = w32 + 32;                           // W_16
     float2 *w8 = w16 + 16;                            // W_8
     float2 *w64 = w8 + 8;                             // W_64
@@ -78,7 +80,6 @@ __global__ void __launch_bounds__(SPEC_THREADS, 1)
     if (tid < 16) w16[tid] = tw[TW_16 + tid];
     if (tid < 8) w8[tid] = tw[TW_8 + tid];
     if (tid < 64) w64[tid] = tw[TW_64 + tid];
-    for (int k = tid; k < BINS * ZT_BIN; k += SPEC_THREADS) zt[k] = make_float2(0.f, 0.f);
     tmem_fence_before();
     __syncthreads();
     tmem_fence_after();
@@ -96,6 +97,11 @@ __global__ void __launch_bounds__(SPEC_THREADS, 1)
     for (int item = blockIdx.x; item < items; item += gridDim.x) {
         const int sl = item / G, k1 = item % G;
         const int slot = slot_base + sl;
+        // zero the stage A buffers (the previous epilogue used them; rows and columns
+        // beyond bp must read as zero)
+        __syncthreads();
+        for (int k = tid; k < PG * BINS * ZT_BIN; k += SPEC_THREADS) zt[k] = make_float2(0.f, 0.f);
+        __syncthreads();
         // per-lane stage A twiddles for this class
         float2 wg[NB1];
 #pragma unroll
@@ -113,14 +119,17 @@ __global__ void __launch_bounds__(SPEC_THREADS, 1)
 
         const float *qblk = qeff + (size_t)(slot - qbase) * c.nch * slab;
         const uint64_t *mrow = colmask + (size_t)slot * c.nch;
-        for (int p = 0; p < c.npairs; ++p) {
-            const int j1 = pair_j[2 * p], j2 = pair_j[2 * p + 1];
-            uint64_t pm = mrow[j1];
-            if (j2 >= 0) pm |= __brevll(mrow[j2]) >> (64 - cols);
-            // ---------------- stage A: class-restricted time DFT per column
-            for (int col = warp; col < cols; col += SPEC_WARPS) {
+        for (int p0 = 0; p0 < c.npairs; p0 += PG) {
+            const int ng = min(PG, c.npairs - p0);
+            // ---------------- stage A: class-restricted time DFT per (pair, column)
+            for (int task = warp; task < ng * cols; task += SPEC_WARPS) {
+                const int g = task / cols, col = task - g * cols;
+                const int p = p0 + g;
+                const int j1 = pair_j[2 * p], j2 = pair_j[2 * p + 1];
+                uint64_t pm = mrow[j1];
+                if (j2 >= 0) pm |= __brevll(mrow[j2]) >> (64 - cols);
                 const int py = col / c.bp, px = col - py * c.bp;
-                float2 *zdst = zt + py * ZT_ROW + px;
+                float2 *zdst = zt + g * (BINS * ZT_BIN) + py * ZT_ROW + px;
                 const int b5 = bitrev<32>(lane);
                 if (!((pm >> col) & 1ull)) {
                     zdst[zt_slot(2 * b5) * ZT_BIN] = make_float2(0.f, 0.f);
@@ -148,62 +157,66 @@ __global__ void __launch_bounds__(SPEC_THREADS, 1)
                 zdst[zt_slot(2 * b5 + 1) * ZT_BIN] = v1;
             }
             __syncthreads();
-            // ---------------- stage B: spatial FFT per bin, product with Rhat, accumulate
+            // ---------------- stage B: spatial FFT per bin, product with Rhat, sum over the
+            // round's pairs in registers, one accumulator update in tensor memory
 #pragma unroll 1
             for (int it = 0; it < BINS / (2 * SPEC_WARPS); ++it) {
                 const int b = lane >> 4;
                 const int k2 = (BINS / SPEC_WARPS) * warp + 2 * it + b;
-                // prefetch this lane's Rhat column (kx = lane & 15) for the y stage; the
-                // 16 lanes of a bin read one contiguous 128-byte ky row per load
                 const int kx = lane & 15;
-                float2 rr[LP];
-                const float2 *rsrc = rhat + rhat_bin(k1 + G * k2, p, c.npairs, 2 * G) + kx;
+                float a[32];                                   // columns 2 ky + {re, im}
+                tmem_ld32(tacc + 32 * it, a);
+#pragma unroll 1
+                for (int g = 0; g < ng; ++g) {
+                    // this lane's Rhat column (kx = lane & 15); the 16 lanes of a bin read
+                    // one contiguous 128-byte ky row per load
+                    float2 rr[LP];
+                    const float2 *rsrc = rhat + rhat_bin(k1 + G * k2, p0 + g, c.npairs, 2 * G) + kx;
 #pragma unroll
-                for (int ky = 0; ky < LP; ++ky) rr[ky] = __ldg(rsrc + ky * LP);
-                // x stage: lane = (b, py, h): 8-point FFT of the (twiddled) row
-                {
-                    const int py = (lane >> 1) & 7, h = lane & 1;
-                    const float2 *zrow = zt + zt_slot(k2) * ZT_BIN + py * ZT_ROW;
-                    float2 v[8];
+                    for (int ky = 0; ky < LP; ++ky) rr[ky] = __ldg(rsrc + ky * LP);
+                    // x stage: lane = (b, py, h): 8-point FFT of the (twiddled) row
+                    {
+                        const int py = (lane >> 1) & 7, h = lane & 1;
+                        const float2 *zrow = zt + g * (BINS * ZT_BIN) + zt_slot(k2) * ZT_BIN + py * ZT_ROW;
+                        float2 v[8];
 #pragma unroll
-                    for (int x = 0; x < 8; ++x) {
-                        const float2 z = zrow[x];
-                        const float wr = h ? w32c(2 * x) : 1.f, wi = h ? w32s(2 * x) : 0.f;
-                        v[x] = make_float2(z.x * wr - z.y * wi, z.x * wi + z.y * wr);
+                        for (int x = 0; x < 8; ++x) {
+                            const float2 z = zrow[x];
+                            const float wr = h ? w32c(2 * x) : 1.f, wi = h ? w32s(2 * x) : 0.f;
+                            v[x] = make_float2(z.x * wr - z.y * wi, z.x * wi + z.y * wr);
+                        }
+                        fft_reg_dif_c<8, false>(v);
+                        float2 *dst = tb + b * TB_BIN + py;
+#pragma unroll
+                        for (int k = 0; k < 8; ++k) dst[(2 * bitrev<8>(k) + h) * TB_ROW] = v[k];
                     }
-                    fft_reg_dif_c<8, false>(v);
-                    float2 *dst = tb + b * TB_BIN + py;
+                    __syncwarp();
+                    // y stage: lane = (b, kx): 16-point FFT of 8 nonzero inputs
+                    {
+                        const float2 *src = tb + b * TB_BIN + kx * TB_ROW;
+                        float2 e[8], o[8];
 #pragma unroll
-                    for (int k = 0; k < 8; ++k) dst[(2 * bitrev<8>(k) + h) * TB_ROW] = v[k];
+                        for (int y = 0; y < 8; ++y) {
+                            e[y] = src[y];
+                            const float wr = w32c(2 * y), wi = w32s(2 * y);     // W_16^y
+                            o[y] = make_float2(e[y].x * wr - e[y].y * wi, e[y].x * wi + e[y].y * wr);
+                        }
+                        fft_reg_dif_c<8, false>(e);
+                        fft_reg_dif_c<8, false>(o);
+#pragma unroll
+                        for (int k = 0; k < 8; ++k) {
+                            const int q = bitrev<8>(k);            // ky pair (2q, 2q + 1)
+                            const float2 a0 = cfma(e[k], rr[2 * q], make_float2(a[4 * q], a[4 * q + 1]));
+                            const float2 a1 = cfma(o[k], rr[2 * q + 1], make_float2(a[4 * q + 2], a[4 * q + 3]));
+                            a[4 * q] = a0.x;
+                            a[4 * q + 1] = a0.y;
+                            a[4 * q + 2] = a1.x;
+                            a[4 * q + 3] = a1.y;
+                        }
+                    }
+                    __syncwarp();
                 }
-                __syncwarp();
-                // y stage: lane = (b, kx): 16-point FFT of 8 nonzero inputs
-                {
-                    const float2 *src = tb + b * TB_BIN + kx * TB_ROW;
-                    float2 e[8], o[8];
-#pragma unroll
-                    for (int y = 0; y < 8; ++y) {
-                        e[y] = src[y];
-                        const float wr = w32c(2 * y), wi = w32s(2 * y);     // W_16^y
-                        o[y] = make_float2(e[y].x * wr - e[y].y * wi, e[y].x * wi + e[y].y * wr);
-                    }
-                    fft_reg_dif_c<8, false>(e);
-                    fft_reg_dif_c<8, false>(o);
-                    float a[32];                               // columns 2 ky + {re, im}
-                    tmem_ld32(tacc + 32 * it, a);
-#pragma unroll
-                    for (int k = 0; k < 8; ++k) {
-                        const int q = bitrev<8>(k);            // ky pair (2q, 2q + 1)
-                        const float2 a0 = cfma(e[k], rr[2 * q], make_float2(a[4 * q], a[4 * q + 1]));
-                        const float2 a1 = cfma(o[k], rr[2 * q + 1], make_float2(a[4 * q + 2], a[4 * q + 3]));
-                        a[4 * q] = a0.x;
-                        a[4 * q + 1] = a0.y;
-                        a[4 * q + 2] = a1.x;
-                        a[4 * q + 3] = a1.y;
-                    }
-                    tmem_st32(tacc + 32 * it, a);
-                }
-                __syncwarp();
+                tmem_st32(tacc + 32 * it, a);
             }
             __syncthreads();
         }
