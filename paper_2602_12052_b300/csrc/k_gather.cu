@@ -5,7 +5,8 @@
 //   k_px_chunk / k_px_top / k_px_emit
 //                ballot + prefix compaction of the flags into the ascending pixel
 //                list; the flag array then holds each pixel's row (or -1)
-//   k_px_wave    one warp per active pixel, 128 ticks per step (float4 per lane):
+//   k_px_wave    one warp per active pixel, 128 ticks per step (float4 per lane);
+//                the pixel's block slots are read once into shared memory:
 //                sum, in a fixed order (by, bx, bt ascending), the outputs of the
 //                overlapping blocks; deterministic, no atomics.  Optional FP64
 //                accumulation (compensated mode).
@@ -133,16 +134,23 @@ __global__ void __launch_bounds__(1024) k_px_emit(int64_t n, int32_t *__restrict
     }
 }
 
+constexpr int PXW_THREADS = 256;
+constexpr int PXW_WARPS = PXW_THREADS / 32;
+constexpr int PXW_COLS = 16;                // (by, bx) block columns cached per pixel (bp + 2R <= 3 bp)
+constexpr int PXW_MAX_NBT = 64;             // time blocks cached per column
+
 template <bool COMP>
-__global__ void __launch_bounds__(256) k_px_wave(const int32_t *__restrict__ pixel_ids,
-                                                 const int32_t *__restrict__ n_pixels_dev,
-                                                 const int32_t *__restrict__ slot_of,
-                                                 const float *__restrict__ out, GatherConst c,
-                                                 float *__restrict__ wave) {
+__global__ void __launch_bounds__(PXW_THREADS) k_px_wave(const int32_t *__restrict__ pixel_ids,
+                                                         const int32_t *__restrict__ n_pixels_dev,
+                                                         const int32_t *__restrict__ slot_of,
+                                                         const float *__restrict__ out, GatherConst c,
+                                                         float *__restrict__ wave) {
+    __shared__ int s_slot[PXW_WARPS][PXW_COLS][PXW_MAX_NBT];
     const int np = n_pixels_dev[0];
-    const int lane = threadIdx.x & 31;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int nwarps = (gridDim.x * blockDim.x) >> 5;
     const int span = c.bt + c.nr - 1;      // meaningful ticks of a block's output
+    const bool cached = c.nbt <= PXW_MAX_NBT;
     for (int row = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; row < np; row += nwarps) {
         const int pid = pixel_ids[row];
         const int x = pid % c.npx_x, y = pid / c.npx_x;
@@ -150,6 +158,18 @@ __global__ void __launch_bounds__(256) k_px_wave(const int32_t *__restrict__ pix
         const int ev = y / c.npy_e;
         const int by_lo = max(ev * c.nby_e, floordiv(y - c.bp - c.R, c.bp) + 1);
         const int by_hi = min((ev + 1) * c.nby_e - 1, floordiv(y + c.R, c.bp));
+        const int nbxc = bx_hi - bx_lo + 1;
+        const int ncol = (by_hi - by_lo + 1) * nbxc;
+        // this pixel's block slots per (by, bx) column and time block, read once
+        __syncwarp();
+        if (cached && ncol <= PXW_COLS) {
+            for (int k = lane; k < ncol * c.nbt; k += 32) {
+                const int col = k / c.nbt, bt = k - col * c.nbt;
+                const int by = by_lo + col / nbxc, bx = bx_lo + col % nbxc;
+                s_slot[warp][col][bt] = slot_of[((int64_t)by * c.nbx + bx) * c.nbt + bt];
+            }
+        }
+        __syncwarp();
         float *dst = wave + (size_t)row * c.nt;
         for (int T0 = 0; T0 < c.nt; T0 += 128) {
             const int t = T0 + 4 * lane;
@@ -161,7 +181,9 @@ __global__ void __launch_bounds__(256) k_px_wave(const int32_t *__restrict__ pix
             for (int by = by_lo; by <= by_hi; ++by)
                 for (int bx = bx_lo; bx <= bx_hi; ++bx)
                     for (int bt = bt_lo; bt <= bt_hi; ++bt) {
-                        const int slot = slot_of[((int64_t)by * c.nbx + bx) * c.nbt + bt];
+                        const int col = (by - by_lo) * nbxc + (bx - bx_lo);
+                        const int slot = (cached && ncol <= PXW_COLS) ? s_slot[warp][col][bt]
+                                                                      : slot_of[((int64_t)by * c.nbx + bx) * c.nbt + bt];
                         if (slot < 0) continue;
                         const int uy = y - by * c.bp + c.R, ux = x - bx * c.bp + c.R;
                         const int tl = t - bt * c.bt;     // multiple of 4
@@ -217,9 +239,9 @@ int launch_gather(tred_handle *h, const int32_t *block_ids, const int32_t *n_blo
                                     TRED_ST_PIXEL_OVERFLOW, 4);
     k_px_emit<<<(unsigned)h->pix_chunks, 1024, 0, s>>>(npx, h->pix_flag, h->pix_part, h->max_pixels, pixel_ids);
     if (c.comp)
-        k_px_wave<true><<<sms * 8, 256, 0, s>>>(pixel_ids, n_pixels_dev, h->blk_slot, out, c, wave);
+        k_px_wave<true><<<sms * 8, PXW_THREADS, 0, s>>>(pixel_ids, n_pixels_dev, h->blk_slot, out, c, wave);
     else
-        k_px_wave<false><<<sms * 8, 256, 0, s>>>(pixel_ids, n_pixels_dev, h->blk_slot, out, c, wave);
+        k_px_wave<false><<<sms * 8, PXW_THREADS, 0, s>>>(pixel_ids, n_pixels_dev, h->blk_slot, out, c, wave);
     h->launches += 6;
     return check_cuda(h, cudaGetLastError(), "gather launch");
 }

@@ -1,10 +1,13 @@
 // a6. Trigger-reset readout (Sec. II-E, Fig. readout: LArPix trigger-reset scheme).
 //
 // One warp per pixel walks the waveform 128 ticks at a time (4 per lane): lane and
-// warp scans give the running charge inside the step (FP32), the charge carried
-// between steps is kept in FP64.  Clock edges k >= start with C(k) >= threshold are found with a ballot;
-// the charge is sampled at k + hold, the hit (pixel, k + hold, C) is emitted, and
-// integration restarts at k + hold + reset + 1.
+// warp scans give the running charge inside the step, the charge carried between
+// steps is added to it; all in FP32 (the rounding of a running sum over a 6400-tick
+// window is a few 1e-7 of the charge, far inside the 1e-4 threshold band in which
+// the FP64 oracle's hit lists may differ).  Clock edges k >= start with
+// C(k) >= threshold are found with a ballot; the charge is sampled at k + hold, the
+// hit (pixel, k + hold, C) is emitted, and integration restarts at
+// k + hold + reset + 1.
 //
 //   k_ro_count   count hits per pixel; cache the first HIT_TMP hits
 //   (scan)       hit offsets and the total
@@ -28,7 +31,7 @@ template <typename Sink>
 __device__ int walk_pixel(const float *__restrict__ I, const RoConst &c, int lane, Sink sink) {
     int nh = 0;
     int pos = 0;              // first tick of the current step
-    double base = 0.0;        // charge integrated before pos since the last restart
+    float base = 0.f;         // charge integrated before pos since the last restart
     int mode = 0;             // 0: looking for a trigger; 1: waiting for the sample tick
     int ts = 0;
     while (pos < c.nt) {
@@ -46,15 +49,16 @@ __device__ int walk_pixel(const float *__restrict__ I, const RoConst &c, int lan
             if (lane >= o) x += u;
         }
         const float excl = x - v[3];
-        double C[4];
+        float C[4];
 #pragma unroll
-        for (int e = 0; e < 4; ++e) C[e] = base + (double)(excl + v[e]);
+        for (int e = 0; e < 4; ++e) C[e] = base + (excl + v[e]);
         if (mode == 0) {
             int first = 4;
+            int ph = t0 % c.clock;                      // clock phase of tick t0
 #pragma unroll
-            for (int e = 3; e >= 0; --e) {
-                const int t = t0 + e;
-                if (t < c.nt && (t % c.clock) == 0 && C[e] >= (double)c.thr) first = e;
+            for (int e = 0; e < 4; ++e) {
+                if (first == 4 && ph == 0 && t0 + e < c.nt && C[e] >= c.thr) first = e;
+                ph = ph + 1 == c.clock ? 0 : ph + 1;
             }
             const unsigned bal = __ballot_sync(0xffffffffu, first < 4);
             if (bal) {
@@ -69,12 +73,12 @@ __device__ int walk_pixel(const float *__restrict__ I, const RoConst &c, int lan
         if (mode == 1 && ts < pos + 128) {
             const int off = ts - pos;
             const int e = off & 3;
-            const double mine = e == 0 ? C[0] : e == 1 ? C[1] : e == 2 ? C[2] : C[3];
-            const double Cs = __shfl_sync(0xffffffffu, mine, off >> 2);
-            sink(nh, ts, (float)Cs);
+            const float mine = e == 0 ? C[0] : e == 1 ? C[1] : e == 2 ? C[2] : C[3];
+            const float Cs = __shfl_sync(0xffffffffu, mine, off >> 2);
+            sink(nh, ts, Cs);
             ++nh;
             pos = ts + c.reset + 1;
-            base = 0.0;
+            base = 0.f;
             mode = 0;
             continue;
         }
