@@ -40,6 +40,30 @@ SMS, FP32_LANES, SM_MAX_GHZ = 148, 128, 2.032
 FP32_PEAK_TFLOPS = SMS * FP32_LANES * 2 * SM_MAX_GHZ / 1e3
 
 
+def conv_traffic(blocks):
+    """DRAM bytes of one tred_convolve call over `blocks` active blocks: the per-block
+    read + write bytes of an ncu capture (profiles/conv_traffic_module20.txt), scaled by
+    the blocks, or None when the convolution source changed since the capture."""
+    import hashlib
+    path = os.path.join(ROOT, "profiles", "conv_traffic_module20.txt")
+    try:
+        lines = [l.split() for l in open(path) if l.strip() and not l.startswith("#")]
+    except OSError:
+        return None, None
+    kv = {}
+    for parts in lines:
+        if parts[0] == "k_conv.cu" and parts[1] == "sha256":
+            kv["sha"] = parts[2]
+        elif parts[0] == "conv_dram_bytes_per_block":
+            kv["per_block"] = float(parts[1])
+    src = os.path.join(ROOT, "paper_2602_12052_b300", "csrc", "k_conv.cu")
+    cur = hashlib.sha256(open(src, "rb").read()).hexdigest()
+    if kv.get("sha") != cur or "per_block" not in kv:
+        return None, "capture predates the current k_conv.cu"
+    return kv["per_block"] * blocks, ("ncu dram__bytes_read+write of module20 (255 blocks), "
+                                      f"{kv['per_block']:.4g} B per block, scaled to {blocks} blocks")
+
+
 def _args():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -554,7 +578,8 @@ def main():
     achieved = CONV_FLOP_PER_BLOCK * nb / (conv_ms / 1e3) / 1e12
     roofline = {"bound": "alu", "kernel": "tred_convolve (k_conv_spec + k_conv_itime)",
                 "achieved": achieved, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
-                "frac": achieved / FP32_PEAK_TFLOPS, "traffic": None,
+                "frac": achieved / FP32_PEAK_TFLOPS, "traffic": conv_traffic(nb)[0],
+                "traffic_source": conv_traffic(nb)[1],
                 "peak_source": "148 SMs x 128 FP32 lanes x 2 flop x 2.032 GHz (unit counts, max clock)",
                 "flop_per_block": CONV_FLOP_PER_BLOCK, "blocks": nb}
     if clocks.get("sm_mhz"):
