@@ -80,6 +80,9 @@ def _args():
                     help="step: one event (default); batched: 64 uneven events, autotuned, CUDA graph; "
                          "adjoint: forward + backward; spill: 35 planes in sequence")
     ap.add_argument("--events", type=int, default=64)
+    ap.add_argument("--conv-mode", type=int, default=0, choices=[0, 1, 2],
+                    help="0: FP32 FFT convolution (default); 1: time DFT as a tcgen05 GEMM in TF32; "
+                         "2: the same in split TF32 (three products)")
     return ap.parse_args()
 
 
@@ -212,7 +215,7 @@ def run_reference(args):
 def _line(metric, value, unit, ms, args, cfg_extra, **kw):
     line = {"metric": metric, "value": value, "unit": unit, "n_gpus": 1, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f32", "data": "synthetic", "config": cfg_extra}
+            "vs_baseline": None, "dtype": {0: "f32", 1: "tf32", 2: "tf32x3"}[args.conv_mode], "data": "synthetic", "config": cfg_extra}
     line.update(kw)
     print(json.dumps(line), flush=True)
 
@@ -466,7 +469,7 @@ def main():
     max_blocks, max_pixels = probe_capacities(cfg, dep, dev)
     max_hits = 4 * max_pixels
     sim = tred.Simulator(cfg, torch.from_numpy(resp), max_deposits=n, max_blocks=max_blocks,
-                         max_pixels=max_pixels, max_hits=max_hits, device=dev)
+                         max_pixels=max_pixels, max_hits=max_hits, conv_mode=args.conv_mode, device=dev)
     # response spectrum, timed separately (once per response)
     torch.cuda.synchronize()
     t = time.perf_counter()
@@ -584,6 +587,12 @@ def main():
                 "flop_per_block": CONV_FLOP_PER_BLOCK, "blocks": nb}
     if clocks.get("sm_mhz"):
         roofline["frac_at_observed_clock"] = achieved / (FP32_PEAK_TFLOPS * clocks["sm_mhz"] / 2032.0)
+    if args.conv_mode:
+        # the time DFT on the tensor cores: per block 50 pairs x 128 x 512 x bt MACs, one
+        # product (TF32) or three (split TF32); its tensor-pipe share is in profiles/
+        products = 1 if args.conv_mode == 1 else 3
+        roofline["dft_gemm_flop_per_block"] = 2 * 50 * 128 * 512 * cfg.bt * products
+        roofline["traffic"], roofline["traffic_source"] = None, "no capture of this form"
 
     if rank == 0:
         line = {
@@ -593,7 +602,9 @@ def main():
             "config": {"workload": (f"{cfg.name}: one event of {n} point deposits on a "
                                     f"{cfg.npx}x{cfg.npx} pixel plane x {cfg.nt} ticks, GL-{cfg.gl_order}, "
                                     f"{cfg.kp}x{cfg.kp}x{cfg.n_sub}x{cfg.n_sub}x{cfg.nr} response, "
-                                    f"{cfg.bp}x{cfg.bp}x{cfg.bt} blocks, FFT 16x16x{cfg.lt}, MPCP"),
+                                    f"{cfg.bp}x{cfg.bp}x{cfg.bt} blocks, FFT 16x16x{cfg.lt}, MPCP"
+                                    + {0: "", 1: ", time DFT as a TF32 tcgen05 GEMM (tolerance 1e-4)",
+                                       2: ", time DFT as a split-TF32 tcgen05 GEMM"}[args.conv_mode]),
                        "deposits": n, "active_blocks": nb, "active_pixels": npix, "hits": nh,
                        "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
                        "l2": "flushed between timed steps (256 MB write, outside the step events)"},

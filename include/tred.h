@@ -87,7 +87,10 @@ typedef struct {
     float max_drift_cm;      /* largest drift distance the window capacity covers */
     int32_t gl_order;        /* Gauss-Legendre points per axis, 1..8 */
     int32_t effq_mode;       /* 0: Gauss-Legendre (FP32); 1: exact tent, FP64 erf tails */
-    int32_t conv_mode;       /* 0: FP32 shared-memory FFT */
+    int32_t conv_mode;       /* 0: FP32 FFT (shared memory + tensor-memory accumulator);
+                                1: time DFT as a tcgen05 GEMM in TF32 (tolerance 1e-4);
+                                2: the same with split TF32, three products (FP32 grade).
+                                1 and 2 need lt = 512 and bp = 8 (TRED_ERR_INVALID_ARG). */
     int32_t mpcp;            /* 1: mirror-pair complex packing (needs a mirror-
                                 symmetric response); 0: one channel per FFT */
     int32_t compensated_gather; /* 1: accumulate overlapping blocks in FP64 */

@@ -55,12 +55,15 @@ static_assert(SPEC_WARPS * 2 * EP_BIN <= PG * BINS * ZT_BIN, "the epilogue trans
 constexpr size_t SPEC_SMEM = sizeof(float2) * ((size_t)PG * BINS * ZT_BIN + (size_t)SPEC_WARPS * 2 * TB_BIN +
                                                32 + 16 + 8 + 64 + 2);
 
-template <int NB1, int G>
+// ZS: stage A reads the packed time spectra written by the tensor-core DFT
+// (zspec[slot][k1][pair][k2][col], k_dftgemm.cu) instead of computing them.
+template <int NB1, int G, bool ZS>
 __global__ void __launch_bounds__(SPEC_THREADS, 1)
     k_conv_spec(const int32_t *__restrict__ n_blocks_dev, const float *__restrict__ qeff,
                 const uint64_t *__restrict__ colmask, const float2 *__restrict__ rhat,
                 const int32_t *__restrict__ pair_j, const float2 *__restrict__ tw, ConvConst c,
-                float2 *__restrict__ yspec, int slot_base, int slot_count, int qbase) {
+                float2 *__restrict__ yspec, int slot_base, int slot_count, int qbase,
+                const float2 *__restrict__ zspec) {
     constexpr int LT = 64 * G;
     extern __shared__ float2 smem[];
     float2 *zt = smem;                                // [PG][64][8][9]
@@ -121,8 +124,19 @@ __global__ void __launch_bounds__(SPEC_THREADS, 1)
         const uint64_t *mrow = colmask + (size_t)slot * c.nch;
         for (int p0 = 0; p0 < c.npairs; p0 += PG) {
             const int ng = min(PG, c.npairs - p0);
+            if (ZS) {
+                // ---------------- stage A from the tensor-core spectra of the round's pairs
+                const float2 *zsrc = zspec + (((size_t)sl * G + k1) * c.npairs + p0) * BINS * 64;
+                for (int e = tid; e < ng * BINS * cols; e += SPEC_THREADS) {
+                    const int g = e / (BINS * cols), r = e - g * (BINS * cols);
+                    const int k2 = r / cols, col = r - k2 * cols;
+                    const int py = col / c.bp, px = col - py * c.bp;
+                    zt[g * (BINS * ZT_BIN) + zt_slot(k2) * ZT_BIN + py * ZT_ROW + px] =
+                        zsrc[((size_t)g * BINS + k2) * 64 + col];
+                }
+            }
             // ---------------- stage A: class-restricted time DFT per (pair, column)
-            for (int task = warp; task < ng * cols; task += SPEC_WARPS) {
+            for (int task = warp; task < (ZS ? 0 : ng * cols); task += SPEC_WARPS) {
                 const int g = task / cols, col = task - g * cols;
                 const int p = p0 + g;
                 const int j1 = pair_j[2 * p], j2 = pair_j[2 * p + 1];
@@ -352,18 +366,28 @@ static int run_conv(tred_handle *h, const int32_t *n_blocks_dev, const float *qe
     static bool attr = false;
     const size_t itime_smem = sizeof(float2) * (16 * (64 * G + 1) + 64 * G + 32 + 64 * G / 32);
     if (!attr) {
-        cudaFuncSetAttribute(k_conv_spec<NB1, G>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SPEC_SMEM);
+        cudaFuncSetAttribute(k_conv_spec<NB1, G, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SPEC_SMEM);
+        cudaFuncSetAttribute(k_conv_spec<NB1, G, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SPEC_SMEM);
         cudaFuncSetAttribute(k_conv_itime<G>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)itime_smem);
         attr = true;
     }
     const int sms = num_sms(h);
-    const int chunk = h->yspec_blocks;
+    const bool tc = h->p.conv_mode != 0;
+    const int chunk = tc ? h->zspec_blocks : h->yspec_blocks;
     const int end = slot_base + slot_count;
     for (int base = slot_base; base < end; base += chunk) {
         const int cnt = chunk < end - base ? chunk : end - base;
-        k_conv_spec<NB1, G><<<sms, SPEC_THREADS, SPEC_SMEM, s>>>(n_blocks_dev, qeff, h->colmask, h->rhat,
-                                                                 h->pair_j, h->tw, c, h->yspec, base, cnt,
-                                                                 slot_base);
+        if (tc) {
+            int rc = launch_dft_gemm(h, n_blocks_dev, qeff, slot_count, base, cnt, slot_base, s);
+            if (rc) return rc;
+            k_conv_spec<NB1, G, true><<<sms, SPEC_THREADS, SPEC_SMEM, s>>>(n_blocks_dev, qeff, h->colmask, h->rhat,
+                                                                          h->pair_j, h->tw, c, h->yspec, base, cnt,
+                                                                          slot_base, h->zspec);
+        } else {
+            k_conv_spec<NB1, G, false><<<sms, SPEC_THREADS, SPEC_SMEM, s>>>(n_blocks_dev, qeff, h->colmask, h->rhat,
+                                                                           h->pair_j, h->tw, c, h->yspec, base, cnt,
+                                                                           slot_base, nullptr);
+        }
         k_conv_itime<G><<<sms * 2, 256, itime_smem, s>>>(n_blocks_dev, h->yspec, h->tw, c, out, base, cnt);
         h->launches += 2;
     }

@@ -1,0 +1,365 @@
+// a4, tensor-core form: the time DFT of the interlaced convolution (Sec. II-D, Eq.
+// interlaced; Sec. III-A-2, Eq. multch) as a GEMM on the tcgen05 tensor cores.
+//
+// For one active block and one channel pair (j, j') the 128 rows of the A operand are
+// the bp^2 = 64 time columns of impact j followed by the 64 columns of j' (FP32 Q^eff,
+// t fastest, straight from the effective-charge buffer), and the 512 rows of the B
+// operand are a real DFT basis of length lt = 512 over the block's bt ticks:
+//     row 2f:   cos(2 pi f t / lt),  f = 0..255
+//     row 2f+1: -sin(2 pi f t / lt), f = 1..255;  row 1: cos(pi t) (the f = 256 bin)
+// so D = A B^T (128 x 512, FP32 in tensor memory) holds the half spectra of the 128
+// real columns.  The epilogue forms the MPCP-packed spectrum of every bin,
+//     Z[f]       = X_j[c][f] + i X_j'[flip c][f]
+//     Z[lt - f]  = conj(X_j[c][f]) + i conj(X_j'[flip c][f]),
+// and writes it in the order the spatial stage of k_conv_spec reads:
+// zspec[slot][k1][pair][k2][c] with f = k1 + G k2 (G = lt / 64).
+//
+// Precision forms: TF32 (conv_mode 1): both operands rounded to the nearest TF32 (A in
+// shared memory after the copy, the basis on the host), one product, FP32
+// accumulation.  Split TF32 (conv_mode 2): A = A_hi + A_lo and B = B_hi + B_lo, three
+// products A_hi B_hi + A_hi B_lo + A_lo B_hi, FP32 accumulation.
+//
+// Data movement: TMA (cp.async.bulk.tensor, 128-byte swizzle) brings 32-tick chunks of
+// A (two boxes of 64 rows) and B (two boxes of 256 rows) into shared memory, one
+// elected thread issues tcgen05.mma (M = 128, N = 256, K = 8 per instruction, two N
+// halves) and commits to an mbarrier; four warps drain the accumulator with
+// tcgen05.ld.  Every mbarrier wait is bounded (clock64), sets TRED_ST_TIMEOUT when it
+// expires, waits once more (bounded) for the copies or products in flight, frees the
+// tensor memory and returns.
+#include <cudaTypedefs.h>
+
+#include <cmath>
+#include <cstring>
+#include <vector>
+
+#include "tred_internal.cuh"
+
+namespace tred {
+
+constexpr int DG_THREADS = 128;
+constexpr int DG_KC = 32;                       // K chunk: 32 FP32 = one 128-byte row
+constexpr int DG_N = 512;                       // accumulator columns
+constexpr int DG_ROWS = 128;                    // A rows: 64 columns of j, 64 of j'
+constexpr int DG_SROW = 33;                     // epilogue staging row (floats)
+constexpr uint32_t DG_A_BYTES = DG_ROWS * DG_KC * 4;          // 16 KB
+constexpr uint32_t DG_B_BYTES = DG_N * DG_KC * 4;             // 64 KB
+// shared-memory carve (offsets from a 1024-byte aligned base)
+constexpr uint32_t DG_OFF_AHI = 0;
+constexpr uint32_t DG_OFF_ALO = DG_OFF_AHI + DG_A_BYTES;
+constexpr uint32_t DG_OFF_BHI = DG_OFF_ALO + DG_A_BYTES;
+constexpr uint32_t DG_OFF_BLO = DG_OFF_BHI + DG_B_BYTES;
+constexpr uint32_t DG_OFF_STAGE = DG_OFF_BLO + DG_B_BYTES;
+constexpr uint32_t DG_OFF_BAR = DG_OFF_STAGE + DG_ROWS * DG_SROW * 4;
+constexpr size_t DG_SMEM = DG_OFF_BAR + 64 + 1024;             // + alignment slack
+constexpr long long DG_WAIT_CYCLES = 2000000000ll;            // ~1 s at 2 GHz
+
+struct DgConst {
+    int nch, cols, bt, npairs, G, mpcp;
+};
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
+// bounded wait for the phase with parity `phase` to complete; false on timeout
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t phase) {
+    const long long t0 = clock64();
+    for (;;) {
+        uint32_t ok;
+        asm volatile(
+            "{\n\t.reg .pred p;\n\t"
+            "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+            "selp.u32 %0, 1, 0, p;\n\t}"
+            : "=r"(ok)
+            : "r"(bar), "r"(phase)
+            : "memory");
+        if (ok) return true;
+        if (clock64() - t0 > DG_WAIT_CYCLES) return false;
+    }
+}
+__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap *map, int x, int y, uint32_t bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
+            dst),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(bar)
+        : "memory");
+}
+// K-major operand with 128-byte swizzle: rows of 128 B, 8-row atoms 1024 B apart
+__device__ __forceinline__ uint64_t sdesc_sw128(uint32_t addr) {
+    uint64_t d = 0;
+    d |= (uint64_t)((addr & 0x3FFFF) >> 4);        // start address
+    d |= (uint64_t)1 << 16;                        // leading byte offset (unused here)
+    d |= (uint64_t)(1024 >> 4) << 32;              // stride byte offset: next 8-row atom
+    d |= (uint64_t)1 << 46;                        // descriptor version
+    d |= (uint64_t)2 << 61;                        // 128-byte swizzle
+    return d;
+}
+// instruction descriptor: D FP32, A and B TF32, both K-major, N = 256, M = 128
+constexpr uint32_t DG_IDESC = (1u << 4) | (2u << 7) | (2u << 10) | ((256u >> 3) << 17) | ((128u >> 4) << 24);
+
+__device__ __forceinline__ void mma_tf32(uint32_t d, uint64_t a, uint64_t b, uint32_t acc) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}" ::"r"(d),
+        "l"(a), "l"(b), "r"(DG_IDESC), "r"(acc)
+        : "memory");
+}
+__device__ __forceinline__ void mma_commit(uint32_t bar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
+}
+// round to the nearest TF32 (10 explicit mantissa bits), ties away from zero
+__device__ __forceinline__ float tf32_rna(float x) {
+    return __uint_as_float((__float_as_uint(x) + 0x1000u) & 0xFFFFE000u);
+}
+
+template <bool SPLIT>
+__global__ void __launch_bounds__(DG_THREADS, 1)
+    k_dft_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmBhi,
+               const __grid_constant__ CUtensorMap tmBlo, const int32_t *__restrict__ n_blocks_dev,
+               const int32_t *__restrict__ pair_j, DgConst c, float2 *__restrict__ zspec,
+               int32_t *__restrict__ status, int slot_base, int slot_count, int qbase) {
+    extern __shared__ unsigned char dg_raw[];
+    const uint32_t raw = smem_u32(dg_raw);
+    const uint32_t base = (raw + 1023u) & ~1023u;
+    unsigned char *gbase = dg_raw + (base - raw);
+    float *a_hi = reinterpret_cast<float *>(gbase + DG_OFF_AHI);
+    float *a_lo = reinterpret_cast<float *>(gbase + DG_OFF_ALO);
+    float *stage = reinterpret_cast<float *>(gbase + DG_OFF_STAGE);
+    const uint32_t bar_tma = base + DG_OFF_BAR, bar_mma = base + DG_OFF_BAR + 8;
+    uint32_t *tslot = reinterpret_cast<uint32_t *>(gbase + DG_OFF_BAR + 16);
+    const int tid = threadIdx.x, warp = tid >> 5;
+
+    if (warp == 0) {
+        tmem_alloc(tslot, DG_N);
+        tmem_relinquish();
+    }
+    if (tid == 0) {
+        mbar_init(bar_tma, 1);
+        mbar_init(bar_mma, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    tmem_fence_before();
+    __syncthreads();
+    tmem_fence_after();
+    const uint32_t tmem = *tslot;
+
+    const int nb = n_blocks_dev[0];
+    const int nloc = max(0, min(slot_count, nb - slot_base));
+    const int tiles = nloc * c.npairs;
+    const int nkc = c.bt / DG_KC;
+    const uint32_t tx_bytes = DG_A_BYTES + DG_B_BYTES * (SPLIT ? 2u : 1u);
+    uint32_t ph_tma = 0, ph_mma = 0;
+    int bad = 0;        // 1: a copy wait expired, 2: a product wait expired
+
+    for (int tile = blockIdx.x; tile < tiles && !bad; tile += gridDim.x) {
+        const int sl = tile / c.npairs, p = tile - sl * c.npairs;
+        const int slot = slot_base + sl;
+        const int j1 = pair_j[2 * p], j2r = pair_j[2 * p + 1];
+        const int j2 = j2r >= 0 ? j2r : j1;                    // without MPCP the upper rows are unused
+        const int row1 = ((slot - qbase) * c.nch + j1) * c.cols;
+        const int row2 = ((slot - qbase) * c.nch + j2) * c.cols;
+        for (int kc = 0; kc < nkc && !bad; ++kc) {
+            if (tid == 0) {
+                mbar_expect_tx(bar_tma, tx_bytes);
+                tma_load_2d(base + DG_OFF_AHI, &tmA, kc * DG_KC, row1, bar_tma);
+                tma_load_2d(base + DG_OFF_AHI + 64 * 128, &tmA, kc * DG_KC, row2, bar_tma);
+                tma_load_2d(base + DG_OFF_BHI, &tmBhi, kc * DG_KC, 0, bar_tma);
+                tma_load_2d(base + DG_OFF_BHI + 256 * 128, &tmBhi, kc * DG_KC, 256, bar_tma);
+                if (SPLIT) {
+                    tma_load_2d(base + DG_OFF_BLO, &tmBlo, kc * DG_KC, 0, bar_tma);
+                    tma_load_2d(base + DG_OFF_BLO + 256 * 128, &tmBlo, kc * DG_KC, 256, bar_tma);
+                }
+            }
+            int w = mbar_wait(bar_tma, ph_tma) ? 0 : 1;
+            ph_tma ^= 1u;
+            if (__syncthreads_or(w)) {
+                bad = 1;
+                break;
+            }
+            // A to TF32 in place (elementwise, so the swizzled order does not matter)
+            for (int i = tid; i < DG_ROWS * DG_KC; i += DG_THREADS) {
+                const float a = a_hi[i];
+                const float h = tf32_rna(a);
+                a_hi[i] = h;
+                if (SPLIT) a_lo[i] = a - h;
+            }
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            tmem_fence_before();
+            __syncthreads();
+            tmem_fence_after();
+            if (tid == 0) {
+#pragma unroll
+                for (int ks = 0; ks < DG_KC / 8; ++ks) {
+                    const uint32_t acc = (kc > 0 || ks > 0) ? 1u : 0u;
+                    const uint64_t ah = sdesc_sw128(base + DG_OFF_AHI + 32 * ks);
+                    const uint64_t b0 = sdesc_sw128(base + DG_OFF_BHI + 32 * ks);
+                    const uint64_t b1 = sdesc_sw128(base + DG_OFF_BHI + 256 * 128 + 32 * ks);
+                    mma_tf32(tmem, ah, b0, acc);
+                    mma_tf32(tmem + 256, ah, b1, acc);
+                    if (SPLIT) {
+                        const uint64_t al = sdesc_sw128(base + DG_OFF_ALO + 32 * ks);
+                        const uint64_t l0 = sdesc_sw128(base + DG_OFF_BLO + 32 * ks);
+                        const uint64_t l1 = sdesc_sw128(base + DG_OFF_BLO + 256 * 128 + 32 * ks);
+                        mma_tf32(tmem, ah, l0, 1u);
+                        mma_tf32(tmem + 256, ah, l1, 1u);
+                        mma_tf32(tmem, al, b0, 1u);
+                        mma_tf32(tmem + 256, al, b1, 1u);
+                    }
+                }
+                mma_commit(bar_mma);
+            }
+            w = mbar_wait(bar_mma, ph_mma) ? 0 : 2;
+            ph_mma ^= 1u;
+            if (__syncthreads_or(w)) {
+                bad = 2;
+                break;
+            }
+        }
+        if (bad) break;
+        tmem_fence_after();
+        // ---- epilogue: 16 chunks of 32 accumulator columns (16 bins)
+        const bool mp = c.mpcp && j2r >= 0;
+        for (int cc = 0; cc < DG_N / 32; ++cc) {
+            float v[32];
+            tmem_ld32(tmem + ((uint32_t)(32 * warp) << 16) + (uint32_t)(32 * cc), v);
+#pragma unroll
+            for (int k = 0; k < 32; ++k) stage[tid * DG_SROW + k] = v[k];
+            __syncthreads();
+            for (int idx = tid; idx < 16 * 64; idx += DG_THREADS) {
+                const int fb = idx >> 6, cp = idx & 63;
+                const int f = cc * 16 + fb;
+                const float *ra = stage + cp * DG_SROW + 2 * fb;
+                const float *rb = stage + (127 - cp) * DG_SROW + 2 * fb;
+                const float ar = ra[0], ai = ra[1];
+                const float br = mp ? rb[0] : 0.f, bi = mp ? rb[1] : 0.f;
+                float2 *zb = zspec + ((size_t)sl * c.G * c.npairs) * 64 * 64;
+                auto put = [&](int ff, float re, float im) {
+                    const int k1 = ff % c.G, k2 = ff / c.G;
+                    zb[(((size_t)k1 * c.npairs + p) * 64 + k2) * 64 + cp] = make_float2(re, im);
+                };
+                if (f == 0) {
+                    put(0, ar, br);                      // column 0: X[0] (real)
+                    put(256, ai, bi);                    // column 1: X[256] (real)
+                } else {
+                    put(f, ar - bi, ai + br);
+                    put(512 - f, ar + bi, br - ai);
+                }
+            }
+            __syncthreads();
+        }
+        tmem_fence_before();
+        __syncthreads();
+    }
+    if (bad) {
+        if (tid == 0) atomicOr(&status[0], TRED_ST_TIMEOUT);
+        // let the copies or products in flight finish (bounded) before the memory goes
+        if (bad == 1) (void)mbar_wait(bar_tma, ph_tma ^ 1u);
+        if (bad == 2) (void)mbar_wait(bar_mma, ph_mma ^ 1u);
+    }
+    tmem_fence_before();
+    __syncthreads();
+    if (warp == 0) {
+        tmem_fence_after();
+        tmem_dealloc(tmem, DG_N);
+    }
+}
+
+// ---------------------------------------------------------------- host side
+static PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    if (!fn) {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+    }
+    return fn;
+}
+
+// 2-D FP32 tensor [rows][inner], box [box_rows][32], 128-byte swizzle
+static int make_map(tred_handle *h, CUtensorMap *m, const float *ptr, uint64_t inner, uint64_t rows,
+                    uint32_t box_rows) {
+    auto fn = encode_fn();
+    if (!fn) return set_error(h, TRED_ERR_CUDA, "dft-gemm: cuTensorMapEncodeTiled unavailable");
+    const cuuint64_t dims[2] = {inner, rows};
+    const cuuint64_t strides[1] = {inner * sizeof(float)};
+    const cuuint32_t box[2] = {(cuuint32_t)DG_KC, box_rows};
+    const cuuint32_t estr[2] = {1, 1};
+    CUresult r = fn(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float *>(ptr), dims, strides, box, estr,
+                    CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                    CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) return set_error(h, TRED_ERR_CUDA, "dft-gemm: tensor map encode failed (%d)", (int)r);
+    return TRED_OK;
+}
+
+// DFT basis (hi, lo parts) for bt ticks and lt = 512, on the host in FP64
+int dft_basis_build(tred_handle *h) {
+    const int bt = h->g.bt, lt = h->g.lt;
+    std::vector<float> hi((size_t)DG_N * bt), lo((size_t)DG_N * bt);
+    auto tf32 = [](float x) {
+        uint32_t u;
+        memcpy(&u, &x, 4);
+        u = (u + 0x1000u) & 0xFFFFE000u;
+        float y;
+        memcpy(&y, &u, 4);
+        return y;
+    };
+    for (int n = 0; n < DG_N; ++n) {
+        const int f = n / 2;
+        for (int t = 0; t < bt; ++t) {
+            double v;
+            if (n == 1) v = (t & 1) ? -1.0 : 1.0;                                   // f = lt / 2
+            else if (n % 2 == 0) v = std::cos(2.0 * M_PI * (double)(((int64_t)f * t) % lt) / lt);
+            else v = -std::sin(2.0 * M_PI * (double)(((int64_t)f * t) % lt) / lt);
+            const float x = (float)v;
+            const float xh = tf32(x);
+            hi[(size_t)n * bt + t] = xh;
+            lo[(size_t)n * bt + t] = (float)(v - (double)xh);
+        }
+    }
+    int rc = check_cuda(h, cudaMemcpy(h->dft_hi, hi.data(), sizeof(float) * hi.size(), cudaMemcpyHostToDevice),
+                        "copy dft basis");
+    if (!rc)
+        rc = check_cuda(h, cudaMemcpy(h->dft_lo, lo.data(), sizeof(float) * lo.size(), cudaMemcpyHostToDevice),
+                        "copy dft basis");
+    return rc;
+}
+
+size_t dft_basis_bytes(int bt) { return sizeof(float) * (size_t)DG_N * bt; }
+size_t dft_zspec_bytes(int blocks, int npairs, int lt) { return sizeof(float2) * (size_t)blocks * npairs * lt * 64; }
+
+int launch_dft_gemm(tred_handle *h, const int32_t *n_blocks_dev, const float *qeff, int qrows_blocks,
+                    int slot_base, int slot_count, int qbase, cudaStream_t s) {
+    CUtensorMap ta, tbh, tbl;
+    const int nch = h->g.n_sub * h->g.n_sub, cols = h->g.bp * h->g.bp;
+    int rc = make_map(h, &ta, qeff, (uint64_t)h->g.bt, (uint64_t)qrows_blocks * nch * cols, 64);
+    if (!rc) rc = make_map(h, &tbh, h->dft_hi, (uint64_t)h->g.bt, DG_N, 256);
+    if (!rc) rc = make_map(h, &tbl, h->dft_lo, (uint64_t)h->g.bt, DG_N, 256);
+    if (rc) return rc;
+    DgConst c{nch, cols, h->g.bt, h->d.npairs, h->g.lt / 64, h->p.mpcp};
+    const bool split = h->p.conv_mode == 2;
+    static bool attr[2] = {false, false};
+    if (!attr[split]) {
+        cudaFuncSetAttribute(split ? k_dft_gemm<true> : k_dft_gemm<false>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)DG_SMEM);
+        attr[split] = true;
+    }
+    const int grid = num_sms(h);
+    if (split)
+        k_dft_gemm<true><<<grid, DG_THREADS, DG_SMEM, s>>>(ta, tbh, tbl, n_blocks_dev, h->pair_j, c, h->zspec,
+                                                           h->status, slot_base, slot_count, qbase);
+    else
+        k_dft_gemm<false><<<grid, DG_THREADS, DG_SMEM, s>>>(ta, tbh, tbl, n_blocks_dev, h->pair_j, c, h->zspec,
+                                                            h->status, slot_base, slot_count, qbase);
+    h->launches += 1;
+    return check_cuda(h, cudaGetLastError(), "dft-gemm launch");
+}
+
+}  // namespace tred

@@ -98,7 +98,9 @@ static int validate(const tred_geometry *g, const tred_params *p, char *msg, siz
     if (!(p->max_drift_cm >= 0)) return bad("max_drift_cm must be >= 0");
     if (p->gl_order < 1 || p->gl_order > MAX_GL) return bad("gl_order must be 1..8");
     if (p->effq_mode != 0 && p->effq_mode != 1) return bad("effq_mode must be 0 or 1");
-    if (p->conv_mode != 0) return bad("conv_mode must be 0");
+    if (p->conv_mode < 0 || p->conv_mode > 2) return bad("conv_mode must be 0, 1 or 2");
+    if (p->conv_mode != 0 && (g->lt != 512 || g->bp != 8))
+        return bad("the tensor-core convolution (conv_mode 1, 2) needs lt = 512 and bp = 8");
     if (p->mpcp != 0 && p->mpcp != 1) return bad("mpcp must be 0 or 1");
     return TRED_OK;
 }
@@ -175,6 +177,13 @@ int32_t tred_create(const tred_geometry *geom, const tred_params *params, int32_
     alloc((void **)&h->wts, sizeof(float) * (size_t)max_deposits * d.wstride, "alloc weights");
     alloc((void **)&h->recs, 48 * (size_t)max_deposits, "alloc deposit records");
     alloc((void **)&h->effq_acc, effq_scratch_bytes(geom->bp * ns, num_sms(h)), "alloc effq scratch");
+    if (params->conv_mode != 0) {
+        h->zspec_blocks = max_blocks < 256 ? max_blocks : 256;
+        alloc((void **)&h->dft_hi, dft_basis_bytes(geom->bt), "alloc dft basis");
+        alloc((void **)&h->dft_lo, dft_basis_bytes(geom->bt), "alloc dft basis");
+        alloc((void **)&h->zspec, dft_zspec_bytes(h->zspec_blocks, NP, geom->lt), "alloc packed spectra");
+        if (rc == TRED_OK) rc = dft_basis_build(h);
+    }
     alloc((void **)&h->blk_count, sizeof(int32_t) * (size_t)d.nblk, "alloc block counts");
     alloc((void **)&h->blk_slot, sizeof(int32_t) * (size_t)d.nblk, "alloc block slots");
     alloc((void **)&h->blk_fill, sizeof(int32_t) * (size_t)max_blocks, "alloc fill");
@@ -235,7 +244,7 @@ int32_t tred_create(const tred_geometry *geom, const tred_params *params, int32_
 
 int32_t tred_destroy(tred_handle *h) {
     if (!h) return TRED_ERR_INVALID_ARG;
-    void *ptrs[] = {h->dep_event, h->wts2, h->pix_row, h->gspec, h->rhat, h->pair_j, h->wts, h->recs, h->effq_acc, h->blk_count, h->blk_slot, h->blk_fill,
+    void *ptrs[] = {h->dep_event, h->wts2, h->pix_row, h->gspec, h->rhat, h->pair_j, h->wts, h->recs, h->effq_acc, h->dft_hi, h->dft_lo, h->zspec, h->blk_count, h->blk_slot, h->blk_fill,
                     h->scan_part, h->colmask, h->yspec, h->pix_flag, h->pix_part, h->hit_cnt,
                     h->hit_tmp, h->hit_tmpc, h->status, h->tw};
     for (void *p : ptrs)

@@ -50,7 +50,10 @@ struct tred_handle {
     int32_t *dep_event;    // [max_deposits] event of each deposit (written by drift)
     float *wts;            // [max_deposits][wstride] per-deposit 1-D weights
     void *recs;            // [max_deposits] 48-byte per-deposit records for effq
-    int32_t *effq_acc;     // [SMs][(bp n_sub)^2][8] integer partial sums of multi-pass blocks
+    int32_t *effq_acc;     // per-CTA integer partial sums of multi-pass effq tiles + block queue
+    float *dft_hi, *dft_lo;  // tensor-core form: [512][bt] real DFT basis, TF32 part and residual
+    float2 *zspec;         // tensor-core form: [zspec_blocks][G][npairs][64][64] packed spectra
+    int32_t zspec_blocks;
     int32_t *blk_count;    // [nblk] occupancy
     int32_t *blk_slot;     // [nblk] slot of an active block or -1
     int32_t *blk_fill;     // [max_blocks] CSR fill cursors
@@ -101,6 +104,11 @@ int launch_blockbin(tred_handle *h, int n, const tred_deposits &deps, int32_t *b
                     int32_t *block_counts, int32_t *dep_offsets, int32_t *dep_index,
                     int32_t max_pairs, int32_t *n_blocks_dev, cudaStream_t s);
 size_t effq_scratch_bytes(int side, int grid);
+int dft_basis_build(tred_handle *h);
+size_t dft_basis_bytes(int bt);
+size_t dft_zspec_bytes(int blocks, int npairs, int lt);
+int launch_dft_gemm(tred_handle *h, const int32_t *n_blocks_dev, const float *qeff, int qrows_blocks,
+                    int slot_base, int slot_count, int qbase, cudaStream_t s);
 int launch_effq(tred_handle *h, int n, const tred_deposits &deps, const int32_t *block_ids,
                 const int32_t *dep_offsets, const int32_t *dep_index,
                 const int32_t *n_blocks_dev, float *qeff, int slot_base, int slot_count, cudaStream_t s);

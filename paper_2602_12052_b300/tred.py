@@ -210,11 +210,11 @@ class Simulator:
 
     def __init__(self, cfg, resp: torch.Tensor, max_deposits: int, max_blocks: int,
                  max_pixels: int, max_pairs: int | None = None, max_hits: int | None = None,
-                 effq_mode=0, mpcp=1, compensated_gather=0, device=None):
+                 effq_mode=0, mpcp=1, compensated_gather=0, conv_mode=0, device=None):
         self.cfg = cfg
         self.mpcp = mpcp
         self.device = torch.device(device or "cuda")
-        self.h = Handle(geometry(cfg), params(cfg, effq_mode, mpcp, compensated_gather),
+        self.h = Handle(geometry(cfg), params(cfg, effq_mode, mpcp, compensated_gather, conv_mode),
                         max_deposits, max_blocks, max_pixels)
         self.rp = readout_params(cfg)
         d = self.device

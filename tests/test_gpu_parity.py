@@ -22,8 +22,9 @@ def _oracle_all(cfg, dep, resp, effq_mode=0):
     return oracle.simulate(cfg, dep, resp, effq_mode=effq_mode)
 
 
-def _full_check(cfg, dep, resp, effq_mode=0, mpcp=1, comp=0, check_readout=True):
-    sim = make_sim(cfg, resp, len(dep["x"]), effq_mode=effq_mode, mpcp=mpcp, compensated_gather=comp)
+def _full_check(cfg, dep, resp, effq_mode=0, mpcp=1, comp=0, check_readout=True, conv_mode=0, tol=WAVE_TOL):
+    sim = make_sim(cfg, resp, len(dep["x"]), effq_mode=effq_mode, mpcp=mpcp, compensated_gather=comp,
+                   conv_mode=conv_mode)
     res = run(sim, dep)
     ref = _oracle_all(cfg, dep, resp, effq_mode)
     p, d = ref["params"], ref["deps"]
@@ -34,9 +35,9 @@ def _full_check(cfg, dep, resp, effq_mode=0, mpcp=1, comp=0, check_readout=True)
     check_qeff(res["qeff"], oracle.qeff_blocks(p, d, ids))
     np.testing.assert_array_equal(res["pixel_ids"], ref["pixel_ids"])
     err = pixel_rel_errors(res["waveforms"], ref["waveforms"])
-    assert err.max() <= WAVE_TOL, (err.max(), int(err.argmax()))
+    assert err.max() <= tol, (err.max(), int(err.argmax()))
     ev = np.linalg.norm(res["waveforms"] - ref["waveforms"]) / np.linalg.norm(ref["waveforms"])
-    assert ev <= WAVE_TOL
+    assert ev <= tol
     if check_readout:
         hp, ht, hc, _ = oracle.readout(ref["pixel_ids"], ref["waveforms"], cfg.threshold_e,
                                        cfg.clock_ticks, cfg.hold_ticks, cfg.reset_ticks)
@@ -82,6 +83,26 @@ def test_tiny_compensated_gather():
     cfg = synth.get_config("tiny")
     dep, resp = synth.make_event(cfg)
     _full_check(cfg, dep, resp, comp=1, check_readout=False)
+
+
+@pytest.mark.parametrize("conv_mode,tol", [(1, 1e-4), (2, WAVE_TOL)])
+def test_tiny_tensor_core_dft(conv_mode, tol, capsys):
+    """The time DFT as a tcgen05 GEMM: TF32 within the tensor-core bar 1e-4, split TF32
+    (three products) within the FP32 bar."""
+    cfg = synth.get_config("tiny")
+    dep, resp = synth.make_event(cfg)
+    res, ref, err = _full_check(cfg, dep, resp, conv_mode=conv_mode, tol=tol, check_readout=False)
+    with capsys.disabled():
+        print(f"\nconv_mode {conv_mode}: max per-pixel rel L2 {err.max():.3e}, median {np.median(err):.3e}")
+
+
+@pytest.mark.parametrize("conv_mode,tol", [(0, WAVE_TOL), (1, 1e-4), (2, WAVE_TOL)])
+def test_tensor_core_dft_no_mpcp_asymmetric(conv_mode, tol):
+    """Without MPCP (one real channel per impact) and with an x-odd response."""
+    cfg = synth.get_config("tiny")
+    dep = synth.make_deposits(cfg)
+    resp = synth.make_response(cfg, symmetric=False)
+    _full_check(cfg, dep, resp, mpcp=0, conv_mode=conv_mode, tol=tol, check_readout=False)
 
 
 def test_small_blocks_long_fft():
@@ -207,7 +228,8 @@ def test_module_plane_sampled(name):
                ref, pix, cfg.threshold_e, cfg.hold_ticks, cfg.reset_ticks)
 
 
-@pytest.mark.parametrize("form", ["fp32", "compensated_gather", "exact_tent_fp64_tails"])
+@pytest.mark.parametrize("form", ["fp32", "compensated_gather", "exact_tent_fp64_tails", "tf32_dft_gemm",
+                                  "split_tf32_dft_gemm"])
 def test_precision_ladder_module200(form, capsys):
     """Each precision form of the module-plane event against the FP64 oracle on
     sampled pixels; the errors are printed (pytest -s) and bounded by the FP32
@@ -216,8 +238,10 @@ def test_precision_ladder_module200(form, capsys):
     dep, resp = synth.make_event(cfg)
     mode = 1 if form == "exact_tent_fp64_tails" else 0
     comp = 1 if form == "compensated_gather" else 0
+    conv = {"tf32_dft_gemm": 1, "split_tf32_dft_gemm": 2}.get(form, 0)
+    tol = 1e-4 if conv == 1 else WAVE_TOL
     sim = make_sim(cfg, resp, len(dep["x"]), max_blocks=3000, max_pixels=150000, effq_mode=mode,
-                   compensated_gather=comp)
+                   compensated_gather=comp, conv_mode=conv)
     res = run(sim, dep, keep_qeff=False)
     p = oracle.params(cfg, effq_mode=mode)
     d = oracle.drift(p, dep)
@@ -229,4 +253,4 @@ def test_precision_ladder_module200(form, capsys):
     with capsys.disabled():
         print(f"\nprecision {form}: max per-pixel rel L2 {err.max():.3e}, median {np.median(err):.3e}, "
               f"sampled-event rel L2 {ev:.3e}")
-    assert err.max() <= WAVE_TOL
+    assert err.max() <= tol
