@@ -43,14 +43,18 @@ constexpr int DG_ROWS = 128;                    // A rows: 64 columns of j, 64 o
 constexpr int DG_SROW = 33;                     // epilogue staging row (floats)
 constexpr uint32_t DG_A_BYTES = DG_ROWS * DG_KC * 4;          // 16 KB
 constexpr uint32_t DG_B_BYTES = DG_N * DG_KC * 4;             // 64 KB
-// shared-memory carve (offsets from a 1024-byte aligned base)
-constexpr uint32_t DG_OFF_AHI = 0;
-constexpr uint32_t DG_OFF_ALO = DG_OFF_AHI + DG_A_BYTES;
-constexpr uint32_t DG_OFF_BHI = DG_OFF_ALO + DG_A_BYTES;
-constexpr uint32_t DG_OFF_BLO = DG_OFF_BHI + DG_B_BYTES;
-constexpr uint32_t DG_OFF_STAGE = DG_OFF_BLO + DG_B_BYTES;
-constexpr uint32_t DG_OFF_BAR = DG_OFF_STAGE + DG_ROWS * DG_SROW * 4;
-constexpr size_t DG_SMEM = DG_OFF_BAR + 64 + 1024;             // + alignment slack
+// one operand stage: A_hi [A_lo] B_hi [B_lo]; TF32 keeps two stages, split TF32 one
+template <bool SPLIT> struct DgStage {
+    static constexpr int STAGES = SPLIT ? 1 : 2;
+    static constexpr uint32_t OFF_AHI = 0;
+    static constexpr uint32_t OFF_ALO = DG_A_BYTES;
+    static constexpr uint32_t OFF_BHI = SPLIT ? 2 * DG_A_BYTES : DG_A_BYTES;
+    static constexpr uint32_t OFF_BLO = OFF_BHI + DG_B_BYTES;
+    static constexpr uint32_t BYTES = SPLIT ? 2 * (DG_A_BYTES + DG_B_BYTES) : DG_A_BYTES + DG_B_BYTES;
+    static constexpr uint32_t OFF_STAGE = STAGES * BYTES;                  // epilogue staging
+    static constexpr uint32_t OFF_BAR = OFF_STAGE + DG_ROWS * DG_SROW * 4;
+    static constexpr size_t SMEM = OFF_BAR + 64 + 1024;                    // + alignment slack
+};
 constexpr long long DG_WAIT_CYCLES = 2000000000ll;            // ~1 s at 2 GHz
 
 struct DgConst {
@@ -123,15 +127,18 @@ __global__ void __launch_bounds__(DG_THREADS, 1)
                const __grid_constant__ CUtensorMap tmBlo, const int32_t *__restrict__ n_blocks_dev,
                const int32_t *__restrict__ pair_j, DgConst c, float2 *__restrict__ zspec,
                int32_t *__restrict__ status, int slot_base, int slot_count, int qbase) {
+    using L = DgStage<SPLIT>;
+    constexpr int ST = L::STAGES;
     extern __shared__ unsigned char dg_raw[];
     const uint32_t raw = smem_u32(dg_raw);
     const uint32_t base = (raw + 1023u) & ~1023u;
     unsigned char *gbase = dg_raw + (base - raw);
-    float *a_hi = reinterpret_cast<float *>(gbase + DG_OFF_AHI);
-    float *a_lo = reinterpret_cast<float *>(gbase + DG_OFF_ALO);
-    float *stage = reinterpret_cast<float *>(gbase + DG_OFF_STAGE);
-    const uint32_t bar_tma = base + DG_OFF_BAR, bar_mma = base + DG_OFF_BAR + 8;
-    uint32_t *tslot = reinterpret_cast<uint32_t *>(gbase + DG_OFF_BAR + 16);
+    float *stage = reinterpret_cast<float *>(gbase + L::OFF_STAGE);
+    // barriers: full[s] (copies landed), mma[s] (products that read stage s done)
+    const uint32_t bar0 = base + L::OFF_BAR;
+    auto bar_full = [&](int st) { return bar0 + 8u * (uint32_t)st; };
+    auto bar_mma = [&](int st) { return bar0 + 16u + 8u * (uint32_t)st; };
+    uint32_t *tslot = reinterpret_cast<uint32_t *>(gbase + L::OFF_BAR + 32);
     const int tid = threadIdx.x, warp = tid >> 5;
 
     if (warp == 0) {
@@ -139,8 +146,10 @@ __global__ void __launch_bounds__(DG_THREADS, 1)
         tmem_relinquish();
     }
     if (tid == 0) {
-        mbar_init(bar_tma, 1);
-        mbar_init(bar_mma, 1);
+        for (int st = 0; st < ST; ++st) {
+            mbar_init(bar_full(st), 1);
+            mbar_init(bar_mma(st), 1);
+        }
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     tmem_fence_before();
@@ -152,78 +161,104 @@ __global__ void __launch_bounds__(DG_THREADS, 1)
     const int nloc = max(0, min(slot_count, nb - slot_base));
     const int tiles = nloc * c.npairs;
     const int nkc = c.bt / DG_KC;
+    const int my_tiles = tiles > (int)blockIdx.x ? (tiles - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
+    const int Q = my_tiles * nkc;                      // this CTA's chunk stream
     const uint32_t tx_bytes = DG_A_BYTES + DG_B_BYTES * (SPLIT ? 2u : 1u);
-    uint32_t ph_tma = 0, ph_mma = 0;
+    // chunk q uses stage q % ST for the (q / ST)-th time: its copies and its products
+    // complete the phase of parity (q / ST) & 1 of that stage's two barriers
+    auto par = [&](int q) { return (uint32_t)((q / ST) & 1); };
     int bad = 0;        // 1: a copy wait expired, 2: a product wait expired
+    int last_q = -1;    // last chunk whose products were issued
 
-    for (int tile = blockIdx.x; tile < tiles && !bad; tile += gridDim.x) {
+    auto tile_of = [&](int q) { return (int)blockIdx.x + (q / nkc) * (int)gridDim.x; };
+    auto issue = [&](int q) {          // thread 0: copies of chunk q into stage q % ST
+        const int st = q % ST, tile = tile_of(q), kc = q % nkc;
         const int sl = tile / c.npairs, p = tile - sl * c.npairs;
         const int slot = slot_base + sl;
         const int j1 = pair_j[2 * p], j2r = pair_j[2 * p + 1];
-        const int j2 = j2r >= 0 ? j2r : j1;                    // without MPCP the upper rows are unused
+        const int j2 = j2r >= 0 ? j2r : j1;            // without MPCP the upper rows are unused
         const int row1 = ((slot - qbase) * c.nch + j1) * c.cols;
         const int row2 = ((slot - qbase) * c.nch + j2) * c.cols;
-        for (int kc = 0; kc < nkc && !bad; ++kc) {
-            if (tid == 0) {
-                mbar_expect_tx(bar_tma, tx_bytes);
-                tma_load_2d(base + DG_OFF_AHI, &tmA, kc * DG_KC, row1, bar_tma);
-                tma_load_2d(base + DG_OFF_AHI + 64 * 128, &tmA, kc * DG_KC, row2, bar_tma);
-                tma_load_2d(base + DG_OFF_BHI, &tmBhi, kc * DG_KC, 0, bar_tma);
-                tma_load_2d(base + DG_OFF_BHI + 256 * 128, &tmBhi, kc * DG_KC, 256, bar_tma);
-                if (SPLIT) {
-                    tma_load_2d(base + DG_OFF_BLO, &tmBlo, kc * DG_KC, 0, bar_tma);
-                    tma_load_2d(base + DG_OFF_BLO + 256 * 128, &tmBlo, kc * DG_KC, 256, bar_tma);
-                }
-            }
-            int w = mbar_wait(bar_tma, ph_tma) ? 0 : 1;
-            ph_tma ^= 1u;
-            if (__syncthreads_or(w)) {
-                bad = 1;
-                break;
-            }
-            // A to TF32 in place (elementwise, so the swizzled order does not matter)
-            for (int i = tid; i < DG_ROWS * DG_KC; i += DG_THREADS) {
-                const float a = a_hi[i];
-                const float h = tf32_rna(a);
-                a_hi[i] = h;
-                if (SPLIT) a_lo[i] = a - h;
-            }
-            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-            tmem_fence_before();
-            __syncthreads();
-            tmem_fence_after();
-            if (tid == 0) {
+        const uint32_t sb = base + (uint32_t)st * L::BYTES;
+        mbar_expect_tx(bar_full(st), tx_bytes);
+        tma_load_2d(sb + L::OFF_AHI, &tmA, kc * DG_KC, row1, bar_full(st));
+        tma_load_2d(sb + L::OFF_AHI + 64 * 128, &tmA, kc * DG_KC, row2, bar_full(st));
+        tma_load_2d(sb + L::OFF_BHI, &tmBhi, kc * DG_KC, 0, bar_full(st));
+        tma_load_2d(sb + L::OFF_BHI + 256 * 128, &tmBhi, kc * DG_KC, 256, bar_full(st));
+        if (SPLIT) {
+            tma_load_2d(sb + L::OFF_BLO, &tmBlo, kc * DG_KC, 0, bar_full(st));
+            tma_load_2d(sb + L::OFF_BLO + 256 * 128, &tmBlo, kc * DG_KC, 256, bar_full(st));
+        }
+    };
+    if (tid == 0)
+        for (int q = 0; q < ST && q < Q; ++q) issue(q);
+
+    for (int q = 0; q < Q; ++q) {
+        const int st = q % ST, kc = q % nkc;
+        const uint32_t sb = base + (uint32_t)st * L::BYTES;
+        float *a_hi = reinterpret_cast<float *>(gbase + (size_t)st * L::BYTES + L::OFF_AHI);
+        float *a_lo = reinterpret_cast<float *>(gbase + (size_t)st * L::BYTES + L::OFF_ALO);
+        int w = mbar_wait(bar_full(st), par(q)) ? 0 : 1;
+        if (__syncthreads_or(w)) {
+            bad = 1;
+            break;
+        }
+        // A to TF32 in place (elementwise, so the swizzled order does not matter)
+        for (int i = tid; i < DG_ROWS * DG_KC; i += DG_THREADS) {
+            const float a = a_hi[i];
+            const float hsel = tf32_rna(a);
+            a_hi[i] = hsel;
+            if (SPLIT) a_lo[i] = a - hsel;
+        }
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        tmem_fence_before();
+        __syncthreads();
+        tmem_fence_after();
+        if (tid == 0) {
 #pragma unroll
-                for (int ks = 0; ks < DG_KC / 8; ++ks) {
-                    const uint32_t acc = (kc > 0 || ks > 0) ? 1u : 0u;
-                    const uint64_t ah = sdesc_sw128(base + DG_OFF_AHI + 32 * ks);
-                    const uint64_t b0 = sdesc_sw128(base + DG_OFF_BHI + 32 * ks);
-                    const uint64_t b1 = sdesc_sw128(base + DG_OFF_BHI + 256 * 128 + 32 * ks);
-                    mma_tf32(tmem, ah, b0, acc);
-                    mma_tf32(tmem + 256, ah, b1, acc);
-                    if (SPLIT) {
-                        const uint64_t al = sdesc_sw128(base + DG_OFF_ALO + 32 * ks);
-                        const uint64_t l0 = sdesc_sw128(base + DG_OFF_BLO + 32 * ks);
-                        const uint64_t l1 = sdesc_sw128(base + DG_OFF_BLO + 256 * 128 + 32 * ks);
-                        mma_tf32(tmem, ah, l0, 1u);
-                        mma_tf32(tmem + 256, ah, l1, 1u);
-                        mma_tf32(tmem, al, b0, 1u);
-                        mma_tf32(tmem + 256, al, b1, 1u);
-                    }
+            for (int ks = 0; ks < DG_KC / 8; ++ks) {
+                const uint32_t acc = (kc > 0 || ks > 0) ? 1u : 0u;
+                const uint64_t ah = sdesc_sw128(sb + L::OFF_AHI + 32 * ks);
+                const uint64_t b0 = sdesc_sw128(sb + L::OFF_BHI + 32 * ks);
+                const uint64_t b1 = sdesc_sw128(sb + L::OFF_BHI + 256 * 128 + 32 * ks);
+                mma_tf32(tmem, ah, b0, acc);
+                mma_tf32(tmem + 256, ah, b1, acc);
+                if (SPLIT) {
+                    const uint64_t al = sdesc_sw128(sb + L::OFF_ALO + 32 * ks);
+                    const uint64_t l0 = sdesc_sw128(sb + L::OFF_BLO + 32 * ks);
+                    const uint64_t l1 = sdesc_sw128(sb + L::OFF_BLO + 256 * 128 + 32 * ks);
+                    mma_tf32(tmem, ah, l0, 1u);
+                    mma_tf32(tmem + 256, ah, l1, 1u);
+                    mma_tf32(tmem, al, b0, 1u);
+                    mma_tf32(tmem + 256, al, b1, 1u);
                 }
-                mma_commit(bar_mma);
             }
-            w = mbar_wait(bar_mma, ph_mma) ? 0 : 2;
-            ph_mma ^= 1u;
-            if (__syncthreads_or(w)) {
-                bad = 2;
-                break;
+            mma_commit(bar_mma(st));
+            // refill the stage of chunk q + 1 once the products that last read it
+            // (those of chunk q + 1 - ST) are done
+            const int qn = q + 1;
+            if (qn >= ST && qn < Q) {
+                w = mbar_wait(bar_mma(qn % ST), par(qn - ST)) ? 0 : 2;
+                if (!w) issue(qn);
             }
         }
-        if (bad) break;
+        last_q = q;
+        if (__syncthreads_or(w)) {
+            bad = 2;
+            break;
+        }
+        if (kc != nkc - 1) continue;
+        // ---- last chunk of a tile: wait for its products, then the epilogue
+        w = mbar_wait(bar_mma(st), par(q)) ? 0 : 2;
+        if (__syncthreads_or(w)) {
+            bad = 2;
+            break;
+        }
         tmem_fence_after();
-        // ---- epilogue: 16 chunks of 32 accumulator columns (16 bins)
-        const bool mp = c.mpcp && j2r >= 0;
+        const int tile = tile_of(q);
+        const int sl = tile / c.npairs, p = tile - sl * c.npairs;
+        const bool mp = c.mpcp && pair_j[2 * p + 1] >= 0;
+        float2 *zb = zspec + ((size_t)sl * c.G * c.npairs) * 64 * 64;
         for (int cc = 0; cc < DG_N / 32; ++cc) {
             float v[32];
             tmem_ld32(tmem + ((uint32_t)(32 * warp) << 16) + (uint32_t)(32 * cc), v);
@@ -237,7 +272,6 @@ __global__ void __launch_bounds__(DG_THREADS, 1)
                 const float *rb = stage + (127 - cp) * DG_SROW + 2 * fb;
                 const float ar = ra[0], ai = ra[1];
                 const float br = mp ? rb[0] : 0.f, bi = mp ? rb[1] : 0.f;
-                float2 *zb = zspec + ((size_t)sl * c.G * c.npairs) * 64 * 64;
                 auto put = [&](int ff, float re, float im) {
                     const int k1 = ff % c.G, k2 = ff / c.G;
                     zb[(((size_t)k1 * c.npairs + p) * 64 + k2) * 64 + cp] = make_float2(re, im);
@@ -257,9 +291,9 @@ __global__ void __launch_bounds__(DG_THREADS, 1)
     }
     if (bad) {
         if (tid == 0) atomicOr(&status[0], TRED_ST_TIMEOUT);
-        // let the copies or products in flight finish (bounded) before the memory goes
-        if (bad == 1) (void)mbar_wait(bar_tma, ph_tma ^ 1u);
-        if (bad == 2) (void)mbar_wait(bar_mma, ph_mma ^ 1u);
+        // let the copies and products in flight finish (bounded) before the memory goes
+        if (last_q >= 0) (void)mbar_wait(bar_mma(last_q % ST), par(last_q));
+        for (int q = last_q + 1; q < Q && q <= last_q + ST; ++q) (void)mbar_wait(bar_full(q % ST), par(q));
     }
     tmem_fence_before();
     __syncthreads();
@@ -346,18 +380,19 @@ int launch_dft_gemm(tred_handle *h, const int32_t *n_blocks_dev, const float *qe
     DgConst c{nch, cols, h->g.bt, h->d.npairs, h->g.lt / 64, h->p.mpcp};
     const bool split = h->p.conv_mode == 2;
     static bool attr[2] = {false, false};
+    const size_t smem = split ? DgStage<true>::SMEM : DgStage<false>::SMEM;
     if (!attr[split]) {
         cudaFuncSetAttribute(split ? k_dft_gemm<true> : k_dft_gemm<false>,
-                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)DG_SMEM);
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         attr[split] = true;
     }
     const int grid = num_sms(h);
     if (split)
-        k_dft_gemm<true><<<grid, DG_THREADS, DG_SMEM, s>>>(ta, tbh, tbl, n_blocks_dev, h->pair_j, c, h->zspec,
-                                                           h->status, slot_base, slot_count, qbase);
+        k_dft_gemm<true><<<grid, DG_THREADS, smem, s>>>(ta, tbh, tbl, n_blocks_dev, h->pair_j, c, h->zspec,
+                                                        h->status, slot_base, slot_count, qbase);
     else
-        k_dft_gemm<false><<<grid, DG_THREADS, DG_SMEM, s>>>(ta, tbh, tbl, n_blocks_dev, h->pair_j, c, h->zspec,
-                                                            h->status, slot_base, slot_count, qbase);
+        k_dft_gemm<false><<<grid, DG_THREADS, smem, s>>>(ta, tbh, tbl, n_blocks_dev, h->pair_j, c, h->zspec,
+                                                         h->status, slot_base, slot_count, qbase);
     h->launches += 1;
     return check_cuda(h, cudaGetLastError(), "dft-gemm launch");
 }
