@@ -276,6 +276,9 @@ def run_batched(args):
     for e in events:
         one.load([e])
         per_event.append(_timed(one.step, 1, 1))
+        st = one.status()
+        if st[0] != 0:
+            raise RuntimeError(f"device status {st} on a single event of {len(e['x'])} deposits")
     ms_single = sum(per_event)
     _line("events/s and depos/s, 64 uneven events batched in one CUDA graph vs one at a time",
           ntot / (ms_graph / 1e3), "depos/s", ms_graph, args,

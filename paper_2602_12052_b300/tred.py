@@ -362,7 +362,9 @@ class BatchSimulator:
         self.block_ids = torch.zeros(max_blocks, dtype=torch.int32, device=d)
         self.block_counts = torch.zeros(max_blocks, dtype=torch.int32, device=d)
         self.dep_offsets = torch.zeros(max_blocks + 1, dtype=torch.int32, device=d)
-        self.dep_index = torch.zeros(8 * max(self.n, 1), dtype=torch.int32, device=d)
+        # a support is shorter than a block on every axis, so a deposit meets at most
+        # 2 x 2 x 2 blocks: 8 (deposit, block) pairs per deposit of the capacity
+        self.dep_index = torch.zeros(8 * max(cap, 1), dtype=torch.int32, device=d)
         self.counts = torch.zeros(4, dtype=torch.int32, device=d)
         self.qeff = torch.empty((self.chunk, ns, ns, bp, bp, bt), dtype=torch.float32, device=d)
         self.out_blocks = torch.empty((max_blocks, 16, 16, lt), dtype=torch.float32, device=d)
