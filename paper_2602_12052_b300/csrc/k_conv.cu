@@ -53,7 +53,8 @@ constexpr int EP_ROW = LP + 1;              // epilogue transpose [cy][kx + pad]
 constexpr int EP_BIN = LP * EP_ROW;
 static_assert(SPEC_WARPS * 2 * EP_BIN <= PG * BINS * ZT_BIN, "the epilogue transpose reuses the stage A buffers");
 constexpr size_t SPEC_SMEM = sizeof(float2) * ((size_t)PG * BINS * ZT_BIN + (size_t)SPEC_WARPS * 2 * TB_BIN +
-                                               32 + 16 + 8 + 64 + 2);
+                                               32 + 16 + 8 + 64 + 2) +
+                             sizeof(int) * (PG * 64 + 4);      // stage A task list and counters
 
 // ZS: stage A reads the packed time spectra written by the tensor-core DFT
 // (zspec[slot][k1][pair][k2][col], k_dftgemm.cu) instead of computing them.
@@ -74,7 +75,10 @@ __global__ void __launch_bounds__(SPEC_THREADS, 1)
     float2 *w8 = w16 + 16;                            // W_8
     float2 *w64 = w8 + 8;                             // W_64
     uint32_t *tslot = reinterpret_cast<uint32_t *>(w64 + 64);
+    int *s_task = reinterpret_cast<int *>(tslot + 4);         // [PG * 64] non-empty (pair, column)
+    int *s_ntask = s_task + PG * 64;                          // [2] counters, one per round parity
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    if (tid < 2) s_ntask[tid] = 0;
     if (warp == 0) {
         tmem_alloc(tslot, SPEC_TMEM_COLS);
         tmem_relinquish();
@@ -104,6 +108,7 @@ __global__ void __launch_bounds__(SPEC_THREADS, 1)
         // beyond bp must read as zero)
         __syncthreads();
         for (int k = tid; k < PG * BINS * ZT_BIN; k += SPEC_THREADS) zt[k] = make_float2(0.f, 0.f);
+        if (tid < 2) s_ntask[tid] = 0;                  // round counters start at zero per item
         __syncthreads();
         // per-lane stage A twiddles for this class
         float2 wg[NB1];
@@ -135,40 +140,70 @@ __global__ void __launch_bounds__(SPEC_THREADS, 1)
                         zsrc[((size_t)g * BINS + k2) * 64 + col];
                 }
             }
-            // ---------------- stage A: class-restricted time DFT per (pair, column)
-            for (int task = warp; task < (ZS ? 0 : ng * cols); task += SPEC_WARPS) {
-                const int g = task / cols, col = task - g * cols;
-                const int p = p0 + g;
-                const int j1 = pair_j[2 * p], j2 = pair_j[2 * p + 1];
-                uint64_t pm = mrow[j1];
-                if (j2 >= 0) pm |= __brevll(mrow[j2]) >> (64 - cols);
-                const int py = col / c.bp, px = col - py * c.bp;
-                float2 *zdst = zt + g * (BINS * ZT_BIN) + py * ZT_ROW + px;
+            // ---------------- stage A: class-restricted time DFT of the non-empty columns.
+            // The round's buffers are zeroed and the non-empty (pair, column) tasks listed,
+            // so that the warps share the few columns that carry charge evenly and each
+            // warp issues the loads of two columns before computing either.
+            if (!ZS) {
+                const int par = (p0 / PG) & 1;
+                float4 *z4 = reinterpret_cast<float4 *>(zt);
+                for (int k = tid; k < ng * BINS * ZT_BIN / 2; k += SPEC_THREADS) z4[k] = make_float4(0.f, 0.f, 0.f, 0.f);
+                if (tid == 0) s_ntask[par ^ 1] = 0;
+                for (int task = tid; task < ng * cols; task += SPEC_THREADS) {
+                    const int g = task / cols, col = task - g * cols;
+                    const int p = p0 + g;
+                    const int j1 = pair_j[2 * p], j2 = pair_j[2 * p + 1];
+                    uint64_t pm = mrow[j1];
+                    if (j2 >= 0) pm |= __brevll(mrow[j2]) >> (64 - cols);
+                    if ((pm >> col) & 1ull) s_task[atomicAdd(&s_ntask[par], 1)] = task;
+                }
+                __syncthreads();
+                const int ntask = s_ntask[par];
                 const int b5 = bitrev<32>(lane);
-                if (!((pm >> col) & 1ull)) {
-                    zdst[zt_slot(2 * b5) * ZT_BIN] = make_float2(0.f, 0.f);
-                    zdst[zt_slot(2 * b5 + 1) * ZT_BIN] = make_float2(0.f, 0.f);
-                    continue;
-                }
-                const float *q1 = qblk + (size_t)j1 * slab + (size_t)col * c.bt;
-                const float *q2 = j2 >= 0 ? qblk + (size_t)j2 * slab + (size_t)(cols - 1 - col) * c.bt : nullptr;
-                float2 y0 = make_float2(0.f, 0.f), y1 = make_float2(0.f, 0.f);
+                for (int t0 = warp; t0 < ntask; t0 += 2 * SPEC_WARPS) {
+                    const int nt = t0 + SPEC_WARPS < ntask ? 2 : 1;
+                    float2 za[2][NB1], zb[2][NB1];
+                    int tk[2];
 #pragma unroll
-                for (int n1 = 0; n1 < NB1; ++n1) {
-                    const int t0 = lane + 64 * n1, t1 = t0 + 32;
-                    const float2 z0 = make_float2(__ldg(q1 + t0), q2 ? __ldg(q2 + t0) : 0.f);
-                    const float2 z1 = make_float2(__ldg(q1 + t1), q2 ? __ldg(q2 + t1) : 0.f);
-                    y0 = cfma(z0, wg[n1], y0);
-                    y1 = cfma(z1, wg[n1], y1);
+                    for (int u = 0; u < 2; ++u) {
+                        if (u >= nt) break;
+                        const int task = s_task[t0 + u * SPEC_WARPS];
+                        tk[u] = task;
+                        const int g = task / cols, col = task - g * cols;
+                        const int p = p0 + g;
+                        const int j1 = pair_j[2 * p], j2 = pair_j[2 * p + 1];
+                        const float *q1 = qblk + (size_t)j1 * slab + (size_t)col * c.bt;
+                        const float *q2 = j2 >= 0 ? qblk + (size_t)j2 * slab + (size_t)(cols - 1 - col) * c.bt : nullptr;
+#pragma unroll
+                        for (int n1 = 0; n1 < NB1; ++n1) {
+                            const int ta = lane + 64 * n1, tb = ta + 32;
+                            za[u][n1] = make_float2(__ldg(q1 + ta), q2 ? __ldg(q2 + ta) : 0.f);
+                            zb[u][n1] = make_float2(__ldg(q1 + tb), q2 ? __ldg(q2 + tb) : 0.f);
+                        }
+                    }
+#pragma unroll
+                    for (int u = 0; u < 2; ++u) {
+                        if (u >= nt) break;
+                        const int task = tk[u];
+                        const int g = task / cols, col = task - g * cols;
+                        const int py = col / c.bp, px = col - py * c.bp;
+                        float2 *zdst = zt + g * (BINS * ZT_BIN) + py * ZT_ROW + px;
+                        float2 y0 = make_float2(0.f, 0.f), y1 = make_float2(0.f, 0.f);
+#pragma unroll
+                        for (int n1 = 0; n1 < NB1; ++n1) {
+                            y0 = cfma(za[u][n1], wg[n1], y0);
+                            y1 = cfma(zb[u][n1], wg[n1], y1);
+                        }
+                        y0 = cmul(y0, wl0);
+                        y1 = cmul(y1, wl1);
+                        float2 v0 = cadd(y0, y1);
+                        float2 v1 = cmul(csub(y0, y1), w64l);
+                        v0 = fft32_lanes<false>(v0, w32, lane);
+                        v1 = fft32_lanes<false>(v1, w32, lane);
+                        zdst[zt_slot(2 * b5) * ZT_BIN] = v0;          // bin k2 = a + 2 b
+                        zdst[zt_slot(2 * b5 + 1) * ZT_BIN] = v1;
+                    }
                 }
-                y0 = cmul(y0, wl0);
-                y1 = cmul(y1, wl1);
-                float2 v0 = cadd(y0, y1);
-                float2 v1 = cmul(csub(y0, y1), w64l);
-                v0 = fft32_lanes<false>(v0, w32, lane);
-                v1 = fft32_lanes<false>(v1, w32, lane);
-                zdst[zt_slot(2 * b5) * ZT_BIN] = v0;          // bin k2 = a + 2 b
-                zdst[zt_slot(2 * b5 + 1) * ZT_BIN] = v1;
             }
             __syncthreads();
             // ---------------- stage B: spatial FFT per bin, product with Rhat, sum over the
