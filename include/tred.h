@@ -94,6 +94,11 @@ typedef struct {
     int32_t mpcp;            /* 1: mirror-pair complex packing (needs a mirror-
                                 symmetric response); 0: one channel per FFT */
     int32_t compensated_gather; /* 1: accumulate overlapping blocks in FP64 */
+    int32_t effq_skip_empty;    /* 1: tred_effq writes only the sub-cell columns that some
+                                   deposit's support covers; the other columns of the qeff
+                                   buffer are left as they were (conv_mode 0 reads only the
+                                   columns whose non-empty mask bit is set).  0: every column
+                                   is written (required by conv_mode 1, 2). */
 } tred_params;
 
 /* Trigger-reset readout (Sec. II-E). */

@@ -153,9 +153,11 @@ __global__ void __launch_bounds__(SPEC_THREADS, 1)
                     const int g = task / cols, col = task - g * cols;
                     const int p = p0 + g;
                     const int j1 = pair_j[2 * p], j2 = pair_j[2 * p + 1];
-                    uint64_t pm = mrow[j1];
-                    if (j2 >= 0) pm |= __brevll(mrow[j2]) >> (64 - cols);
-                    if ((pm >> col) & 1ull) s_task[atomicAdd(&s_ntask[par], 1)] = task;
+                    // each half of the packed column is read only where its own mask bit is
+                    // set (a column that no support covers may not have been written)
+                    const int h1 = (int)((mrow[j1] >> col) & 1ull);
+                    const int h2 = j2 >= 0 ? (int)((mrow[j2] >> (cols - 1 - col)) & 1ull) : 0;
+                    if (h1 | h2) s_task[atomicAdd(&s_ntask[par], 1)] = task | (h1 << 20) | (h2 << 21);
                 }
                 __syncthreads();
                 const int ntask = s_ntask[par];
@@ -167,18 +169,19 @@ __global__ void __launch_bounds__(SPEC_THREADS, 1)
 #pragma unroll
                     for (int u = 0; u < 2; ++u) {
                         if (u >= nt) break;
-                        const int task = s_task[t0 + u * SPEC_WARPS];
+                        const int te = s_task[t0 + u * SPEC_WARPS];
+                        const int task = te & 0xFFFFF;
                         tk[u] = task;
                         const int g = task / cols, col = task - g * cols;
                         const int p = p0 + g;
                         const int j1 = pair_j[2 * p], j2 = pair_j[2 * p + 1];
-                        const float *q1 = qblk + (size_t)j1 * slab + (size_t)col * c.bt;
-                        const float *q2 = j2 >= 0 ? qblk + (size_t)j2 * slab + (size_t)(cols - 1 - col) * c.bt : nullptr;
+                        const float *q1 = (te >> 20) & 1 ? qblk + (size_t)j1 * slab + (size_t)col * c.bt : nullptr;
+                        const float *q2 = (te >> 21) & 1 ? qblk + (size_t)j2 * slab + (size_t)(cols - 1 - col) * c.bt : nullptr;
 #pragma unroll
                         for (int n1 = 0; n1 < NB1; ++n1) {
                             const int ta = lane + 64 * n1, tb = ta + 32;
-                            za[u][n1] = make_float2(__ldg(q1 + ta), q2 ? __ldg(q2 + ta) : 0.f);
-                            zb[u][n1] = make_float2(__ldg(q1 + tb), q2 ? __ldg(q2 + tb) : 0.f);
+                            za[u][n1] = make_float2(q1 ? __ldg(q1 + ta) : 0.f, q2 ? __ldg(q2 + ta) : 0.f);
+                            zb[u][n1] = make_float2(q1 ? __ldg(q1 + tb) : 0.f, q2 ? __ldg(q2 + tb) : 0.f);
                         }
                     }
 #pragma unroll

@@ -35,6 +35,7 @@ struct EffqConst {
     int ns, bp, bt, ngx, ngy, nt, nbx, nbt, wx, wt, wstride, gl, mode;
     int ngy_e;                     // sub-cells of one event along y
     int cols_log2;                 // log2(bp * bp)
+    int skip_empty;                // write only the columns some deposit's support covers
     float xi[MAX_GL], wl[MAX_GL];
 };
 
@@ -202,6 +203,7 @@ struct EffqShared {
     uint32_t nzp[EQ_MAX_PATCH];          // per patch: lanes whose cell is non-zero in some tile
     int offx[EQ_MAX_SIDE], offy[EQ_MAX_SIDE];   // output offsets of block-local gx and gy
     unsigned long long mask[128];        // per channel: non-empty (py, px) columns (n_sub^2 <= 128)
+    uint32_t cov[EQ_MAX_SIDE * EQ_MAX_SIDE / 32];   // sub-cell columns covered by a support
     unsigned long long part[EQ_WARPS * 3];
     int tot[4];                          // list entries, pool floats, bucket slots, accepted count
     int slot, next;
@@ -291,6 +293,26 @@ __global__ void __launch_bounds__(EQ_THREADS, EQ_CTAS_PER_SM) k_effq_blocks(
             const float B = (float)usum * (M * (1.0f / 1048576.0f)) * 1.0001f;
             scale = fminf(4194304.0f / M, 2147483648.0f / B) * (1.0f - 1.0f / 1024.0f);
             inv_scale = 1.0f / scale;
+        }
+        if (c.skip_empty) {
+            // columns (gy, gx) covered by some deposit's clipped support: the others stay
+            // zero in every tile and are not written
+            for (int k = tid; k < (side * side + 31) / 32; k += EQ_THREADS) S.cov[k] = 0u;
+            __syncthreads();
+            for (int k = beg + tid; k < end; k += EQ_THREADS) {
+                const DepRec r = recs[dep_index[k]];
+                const int xa = max(r.x0, X0) - X0, xb = min(r.x1, X0 + side - 1) - X0;
+                const int ya = max(r.y0, Y0) - Y0, yb = min(r.y1, Y0 + side - 1) - Y0;
+                for (int gy = ya; gy <= yb; ++gy) {
+                    const int b0 = gy * side + xa, b1 = gy * side + xb;
+                    for (int wd = b0 >> 5; wd <= (b1 >> 5); ++wd) {
+                        const int lo = max(b0, wd << 5) & 31, hi = min(b1, (wd << 5) + 31) & 31;
+                        const uint32_t m = (hi == 31 ? 0xffffffffu : ((1u << (hi + 1)) - 1u)) & ~((1u << lo) - 1u);
+                        atomicOr(&S.cov[wd], m);
+                    }
+                }
+            }
+            __syncthreads();
         }
         for (int tt = 0; tt < c.bt; tt += EQ_TT) {
             const int ta = T0 + tt, tb = ta + EQ_TT - 1;   // absolute ticks of the tile
@@ -467,7 +489,8 @@ __global__ void __launch_bounds__(EQ_THREADS, EQ_CTAS_PER_SM) k_effq_blocks(
                     }
                     const uint32_t bal = __ballot_sync(0xffffffffu, own && any != 0);
                     if (lane == 0 && bal) S.nzp[pt] |= bal;       // this warp alone holds patch pt now
-                    if (own) {
+                    const int cb = gy * side + gx;
+                    if (own && (!c.skip_empty || ((S.cov[cb >> 5] >> (cb & 31)) & 1u))) {
                         float4 *dst = reinterpret_cast<float4 *>(qblk + S.offy[gy] + S.offx[gx] + tt);
 #pragma unroll
                         for (int e4 = 0; e4 < EQ_TT; e4 += 4) dst[e4 / 4] = make_float4(v[e4], v[e4 + 1], v[e4 + 2], v[e4 + 3]);
@@ -512,6 +535,7 @@ int launch_effq(tred_handle *h, int n, const tred_deposits &deps, const int32_t 
     c.gl = h->p.gl_order;
     c.mode = h->p.effq_mode;
     c.cols_log2 = h->g.bp == 8 ? 6 : 4;
+    c.skip_empty = h->p.effq_skip_empty;
     for (int l = 0; l < MAX_GL; ++l) {
         c.xi[l] = l < c.gl ? h->gl_xi[l] : 0.f;
         c.wl[l] = l < c.gl ? h->gl_wi[l] : 0.f;

@@ -102,6 +102,8 @@ static int validate(const tred_geometry *g, const tred_params *p, char *msg, siz
     if (p->conv_mode != 0 && (g->lt != 512 || g->bp != 8))
         return bad("the tensor-core convolution (conv_mode 1, 2) needs lt = 512 and bp = 8");
     if (p->mpcp != 0 && p->mpcp != 1) return bad("mpcp must be 0 or 1");
+    if (p->effq_skip_empty != 0 && p->effq_skip_empty != 1) return bad("effq_skip_empty must be 0 or 1");
+    if (p->effq_skip_empty && p->conv_mode != 0) return bad("the tensor-core convolution reads every column: effq_skip_empty must be 0");
     return TRED_OK;
 }
 
