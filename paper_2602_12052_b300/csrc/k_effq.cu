@@ -179,11 +179,12 @@ constexpr int EQ_WARPS = 8;
 constexpr int EQ_THREADS = EQ_WARPS * 32;
 constexpr int EQ_CTAS_PER_SM = 2;
 constexpr int EQ_LIST = 256;                 // tile-list entries per pass
-constexpr int EQ_POOL = 12288;               // weight-pool floats per pass
-constexpr int EQ_INS = 8192;                 // bucket slots per pass
+constexpr int EQ_POOL = 8192;                // weight-pool floats per pass
+constexpr int EQ_INS = 4096;                 // bucket slots per pass
 constexpr int EQ_PX = 8, EQ_PY = 4;          // patch: 8 gx x 4 gy sub-cells
 constexpr int EQ_MAX_SIDE = 128;             // bp * n_sub
 constexpr int EQ_MAX_PATCH = (EQ_MAX_SIDE / EQ_PX) * (EQ_MAX_SIDE / EQ_PY);
+constexpr int EQ_TERMS = 1024;               // bound terms kept in shared memory
 constexpr float EQ_MAGIC = 12582912.0f;      // 1.5 * 2^23
 constexpr int EQ_MAGIC_BITS = 0x4B400000;
 
@@ -204,10 +205,15 @@ struct EffqShared {
     int offx[EQ_MAX_SIDE], offy[EQ_MAX_SIDE];   // output offsets of block-local gx and gy
     unsigned long long mask[128];        // per channel: non-empty (py, px) columns (n_sub^2 <= 128)
     uint32_t cov[EQ_MAX_SIDE * EQ_MAX_SIDE / 32];   // sub-cell columns covered by a support
+    uint8_t pcov[EQ_MAX_PATCH];                       // patch has a covered column
+    float term[EQ_TERMS];                             // bound terms of the block's first deposits
     unsigned long long part[EQ_WARPS * 3];
     int tot[4];                          // list entries, pool floats, bucket slots, accepted count
     int slot, next;
 };
+
+// two CTAs per SM: 228 KB of shared memory per SM, 1 KB reserved per CTA
+static_assert(2 * (sizeof(EffqShared) + 1024) <= 233472, "effq shared memory must leave room for two CTAs per SM");
 
 __device__ __forceinline__ int fx_round(float a, float w) {
     return __float_as_int(fmaf(a, w, EQ_MAGIC)) - EQ_MAGIC_BITS;
@@ -266,7 +272,11 @@ __global__ void __launch_bounds__(EQ_THREADS, EQ_CTAS_PER_SM) k_effq_blocks(
             return fabsf(r.q) * mx * my * mt;
         };
         float tmax = 0.f;
-        for (int k = beg + tid; k < end; k += EQ_THREADS) tmax = fmaxf(tmax, term(k));
+        for (int k = beg + tid; k < end; k += EQ_THREADS) {
+            const float tv = term(k);
+            if (k - beg < EQ_TERMS) S.term[k - beg] = tv;
+            tmax = fmaxf(tmax, tv);
+        }
 #pragma unroll
         for (int o = 16; o; o >>= 1) tmax = fmaxf(tmax, __shfl_xor_sync(0xffffffffu, tmax, o));
         if (lane == 0) reinterpret_cast<float *>(S.part)[warp] = tmax;
@@ -278,7 +288,7 @@ __global__ void __launch_bounds__(EQ_THREADS, EQ_CTAS_PER_SM) k_effq_blocks(
         if (M > 0.f) {
             const float to_units = 1048576.0f / M;
             for (int k = beg + tid; k < end; k += EQ_THREADS)
-                units += (unsigned long long)ceilf(term(k) * to_units) + 1ull;
+                units += (unsigned long long)ceilf((k - beg < EQ_TERMS ? S.term[k - beg] : term(k)) * to_units) + 1ull;
         }
 #pragma unroll
         for (int o = 16; o; o >>= 1) units += __shfl_xor_sync(0xffffffffu, units, o);
@@ -311,6 +321,22 @@ __global__ void __launch_bounds__(EQ_THREADS, EQ_CTAS_PER_SM) k_effq_blocks(
                         atomicOr(&S.cov[wd], m);
                     }
                 }
+            }
+            __syncthreads();
+            for (int pt = tid; pt < npatch; pt += EQ_THREADS) {
+                const int qy = pt / npx, qx = pt - qy * npx;
+                int any = 0;
+                for (int r = 0; r < EQ_PY; ++r) {
+                    const int gy = qy * EQ_PY + r;
+                    for (int cx = 0; cx < EQ_PX && gy < side; ++cx) {
+                        const int gx = qx * EQ_PX + cx;
+                        if (gx < side) {
+                            const int cb = gy * side + gx;
+                            any |= (S.cov[cb >> 5] >> (cb & 31)) & 1u;
+                        }
+                    }
+                }
+                S.pcov[pt] = (uint8_t)any;
             }
             __syncthreads();
         }
@@ -456,6 +482,18 @@ __global__ void __launch_bounds__(EQ_THREADS, EQ_CTAS_PER_SM) k_effq_blocks(
                         }
                     }
                     const int kb = S.boff[pt], ke = S.boff[pt + 1];
+                    if (kb == ke && first && last) {
+                        // no deposit reaches the patch in this tile: zeros where written at all
+                        const int cb = gy * side + gx;
+                        if (c.skip_empty && !S.pcov[pt]) continue;
+                        if (own && (!c.skip_empty || ((S.cov[cb >> 5] >> (cb & 31)) & 1u))) {
+                            float4 *dst = reinterpret_cast<float4 *>(qblk + S.offy[gy] + S.offx[gx] + tt);
+                            const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+                            for (int e4 = 0; e4 < EQ_TT; e4 += 4) dst[e4 / 4] = z4;
+                        }
+                        continue;
+                    }
                     for (int kk = kb; kk < ke; ++kk) {
                         const TileEnt &en = S.list[S.bucket[kk]];
                         const int4 hy = *reinterpret_cast<const int4 *>(&en.y0);     // y0 y1 x0 x1
