@@ -76,7 +76,7 @@ def _args():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--mode", default="step",
-                    choices=["step", "batched", "adjoint", "spill", "accuracy", "chunking"],
+                    choices=["step", "batched", "adjoint", "spill", "accuracy", "chunking", "lines"],
                     help="step: one event (default); batched: 64 uneven events, autotuned, CUDA graph; "
                          "adjoint: forward + backward; spill: 35 planes in sequence")
     ap.add_argument("--events", type=int, default=64)
@@ -294,6 +294,66 @@ def run_batched(args):
           speedup_vs_per_event=ms_single / ms_graph, clocks=clocks)
 
 
+def run_lines(args):
+    """Line-shape track segments (Sec. II-C, Eq. qline): a 200-track module plane in
+    3 mm segments through segment transport, binning, the segments' effective charge,
+    convolution, gather and readout; segments/s with per-stage times."""
+    import torch
+    import synth
+    from paper_2602_12052_b300 import tred
+    torch.cuda.set_device(0)
+    cfg = synth.get_config("module_lines")
+    seg = synth.make_segments(cfg, synth.SEG_CM["module_lines"])
+    resp = torch.from_numpy(synth.make_response(cfg))
+    n = len(seg["x0"])
+    sim = tred.LineSimulator(cfg, resp, max_segments=n, max_blocks=6000, max_pixels=300000)
+    x = {k: torch.from_numpy(v).cuda() for k, v in seg.items()}
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+
+    def stages(ev):
+        h = sim.h
+        ev[0].record()
+        tred.tred_drift_lines(h, n, x["x0"], x["y0"], x["z0"], x["x1"], x["y1"], x["z1"], x["t0"], x["ne"],
+                              sim.deps, sim.half)
+        tred.tred_blockbin(h, n, sim.deps, sim.block_ids, sim.block_counts, sim.dep_offsets, sim.dep_index,
+                           sim.n_blocks_dev)
+        ev[1].record()
+        tred.tred_effq_lines(h, n, sim.deps, sim.half, sim.block_ids, sim.dep_offsets, sim.dep_index,
+                             sim.n_blocks_dev, sim.qeff)
+        ev[2].record()
+        tred.tred_convolve(h, sim.block_ids, sim.n_blocks_dev, sim.qeff, sim.out_blocks)
+        ev[3].record()
+        tred.tred_gather_pixels(h, sim.block_ids, sim.n_blocks_dev, sim.out_blocks, sim.pixel_ids, sim.waveforms,
+                                sim.n_pixels_dev)
+        tred.tred_readout(h, sim.rp, sim.pixel_ids, sim.waveforms, sim.n_pixels_dev, sim.hit_pixel, sim.hit_tick,
+                          sim.hit_charge, sim.n_hits_dev)
+        ev[4].record()
+    for _ in range(args.warmup):
+        stages([torch.cuda.Event(enable_timing=True) for _ in range(5)])
+    torch.cuda.synchronize()
+    st = sim.status()
+    if st[0] != 0:
+        raise RuntimeError(f"device status {st}")
+    rows = []
+    with ClockSampler(0) as clk:
+        for _ in range(args.steps):
+            flush.zero_()
+            ev = [torch.cuda.Event(enable_timing=True) for _ in range(5)]
+            stages(ev)
+            torch.cuda.synchronize()
+            rows.append([ev[i].elapsed_time(ev[i + 1]) for i in range(4)])
+    m = [statistics.mean(r[i] for r in rows) for i in range(4)]
+    ms = sum(m)
+    nb, npix, nh = (int(v) for v in sim.counts[:3].cpu())
+    _line("line segments/s to pixel currents (Eq. qline effective charge)", n / (ms / 1e3), "segments/s", ms, args,
+          {"workload": f"module_lines: {n} segments of 3 mm from 200 tracks, 512x512 px x 6400 ticks, GL-2, "
+                       "9x9x10x10x200 response, 8x8x256 blocks",
+           "active_blocks": nb, "active_pixels": npix, "hits": nh,
+           "l2": "flushed between timed steps"},
+          stages_ms={"drift+blockbin": m[0], "effq_lines": m[1], "convolve": m[2], "gather+readout": m[3]},
+          clocks=clk.summary())
+
+
 def run_adjoint(args):
     """Config 4: forward + backward (adjoint) deposits/s and peak device memory."""
     import torch
@@ -449,7 +509,7 @@ def main():
         return
     if args.mode != "step":
         {"batched": run_batched, "adjoint": run_adjoint, "spill": run_spill, "accuracy": run_accuracy,
-         "chunking": run_chunking}[args.mode](args)
+         "chunking": run_chunking, "lines": run_lines}[args.mode](args)
         return
     import numpy as np
     import torch

@@ -176,6 +176,34 @@ int32_t tred_drift_events(tred_handle *h, int32_t n, const float *x, const float
                           const float *z, const float *t0, const float *ne, const int32_t *event,
                           const tred_deposits *out, void *stream);
 
+/* Line-shape track segments (Sec. II-C, Eq. qline; short segments).  Transport of
+ * both endpoints (x0, y0, z0) and (x1, y1, z1) with one start time t0 and n_e
+ * electrons per segment: cell/frac = the midpoint split as in tred_drift, sigma per
+ * axis at the midpoint's drift time, q with attachment at the midpoint, window per
+ * axis [floor(min endpoint - nsigma sigma), ceil(max endpoint + nsigma sigma)] (the
+ * same binary64 sequence as tred_drift, so the oracle's windows agree bit for bit).
+ * half[3 * n] (device, caller-owned): (p1 - p0) / 2 per axis in grid units, axis
+ * major (x block, then y, then t).  A segment with an endpoint off the plane or
+ * beyond max_drift_cm is dropped as in tred_drift.  Single event (event 0).  The
+ * blockbin pair capacity assumes a segment's window is shorter than a block on every
+ * axis (at most 2 blocks per axis). */
+int32_t tred_drift_lines(tred_handle *h, int32_t n, const float *x0, const float *y0,
+                         const float *z0, const float *x1, const float *y1, const float *z1,
+                         const float *t0, const float *ne, const tred_deposits *out, float *half,
+                         void *stream);
+
+/* Effective charge of line segments (Eq. eff_q with the node charge
+ * Q rho(node) w_l w_m w_n / 8, rho the diffused line density of Eq. qline with the
+ * factor 1/2 in the exponent; segments shorter than 0.1 sigma on every axis use the
+ * point Gaussian at the midpoint).  Same block list, CSR, qeff layout and column
+ * masks as tred_effq; every column of every active block is written.  Needs
+ * effq_mode 0, gl_order <= 4, (bp n_sub)^2 <= 8192 and bt a multiple of 16.  FP32
+ * sums in the order of each block's segment list. */
+int32_t tred_effq_lines(tred_handle *h, int32_t n, const tred_deposits *deps, const float *half,
+                        const int32_t *block_ids, const int32_t *dep_offsets,
+                        const int32_t *dep_index, const int32_t *n_blocks_dev, float *qeff,
+                        void *stream);
+
 /* a2. Block-sparse binning (Sec. III-B-1).  A block is active iff the clipped
  * support box of some deposit intersects it; its count is the number of such
  * deposits.  Output (device): block_ids[nb] ascending, block_counts[nb],

@@ -97,6 +97,13 @@ def _setup(L):
     L.orc_adjoint.argtypes = [_P, ctypes.c_int, _P, _P, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                               _P, _P, _P]
     L.orc_param_grads.argtypes = [_P, ctypes.c_int, _P, _P, _P, _P, _P, _P]
+    L.orc_drift_lines.argtypes = [_P, ctypes.c_int, _P, _P, _P, _P, _P, _P, _P, _P, _P]
+    L.orc_drift_lines.restype = None
+    L.orc_line_density.argtypes = [_P, _P, _P, ctypes.c_double, _P]
+    L.orc_line_density.restype = ctypes.c_double
+    L.orc_qeff_line_blocks.argtypes = [_P, ctypes.c_int, _P, ctypes.c_double, ctypes.c_int, _P, _P]
+    L.orc_currents_from_qeff.argtypes = [_P, ctypes.c_int, _P, _P, _P, ctypes.c_int, ctypes.c_int,
+                                         ctypes.c_int, _P, _P]
 
 
 def _ptr(a: np.ndarray):
@@ -285,3 +292,65 @@ def currents_frozen(p: Params, dep: dict, frozen: np.ndarray, resp, pixel_ids):
     d["lo"] = frozen["lo"]
     d["hi"] = frozen["hi"]
     return pixel_currents(p, d, resp, pixel_ids)
+
+
+# ----------------------------------------------------------------- line segments
+LINE_DTYPE = np.dtype([("d", DEP_DTYPE), ("p0", "<f8", 3), ("p1", "<f8", 3)], align=True)
+SHORT_FRAC = 0.1          # segments shorter than this many sigma on every axis are points
+
+
+def drift_lines(p: Params, seg: dict) -> np.ndarray:
+    """Transport of line segments (Sec. II-A, II-C): both endpoints in grid units, one
+    width per axis at the midpoint's drift time, window over both endpoints."""
+    n = len(seg["x0"])
+    out = np.zeros(n, dtype=LINE_DTYPE)
+    f = {k: np.ascontiguousarray(seg[k], dtype=np.float32) for k in ("x0", "y0", "z0", "x1", "y1", "z1", "t0", "ne")}
+    lib().orc_drift_lines(ctypes.byref(p), n, _ptr(f["x0"]), _ptr(f["y0"]), _ptr(f["z0"]), _ptr(f["x1"]),
+                          _ptr(f["y1"]), _ptr(f["z1"]), _ptr(f["t0"]), _ptr(f["ne"]), _ptr(out))
+    return out
+
+
+def line_density(p0, p1, sig, x, frac: float = SHORT_FRAC) -> float:
+    """Normalised Eq. qline (grid units) at x; the point Gaussian for short segments."""
+    a = [np.ascontiguousarray(v, dtype=np.float64) for v in (p0, p1, sig, x)]
+    return lib().orc_line_density(_ptr(a[0]), _ptr(a[1]), _ptr(a[2]), float(frac), _ptr(a[3]))
+
+
+def line_windows(lines: np.ndarray) -> np.ndarray:
+    """The per-segment window records (DEP_DTYPE) that drive the block functions."""
+    return np.ascontiguousarray(lines["d"])
+
+
+def qeff_line_blocks(p: Params, lines: np.ndarray, blocks, frac: float = SHORT_FRAC) -> np.ndarray:
+    """Effective charge of the listed blocks from line segments, [nb][ns][ns][bp][bp][bt]."""
+    blocks = np.ascontiguousarray(blocks, dtype=np.int32)
+    q = np.zeros((len(blocks), p.n_sub, p.n_sub, p.bp, p.bp, p.bt))
+    lib().orc_qeff_line_blocks(ctypes.byref(p), len(lines), _ptr(lines), float(frac), len(blocks),
+                               _ptr(blocks), _ptr(q))
+    return q
+
+
+def currents_from_qeff(p: Params, blocks, qeff: np.ndarray, resp: np.ndarray, pixel_ids) -> np.ndarray:
+    """Eq. interlaced from block-stored effective charge on the listed pixels."""
+    blocks = np.ascontiguousarray(blocks, dtype=np.int32)
+    qeff = np.ascontiguousarray(qeff, dtype=np.float64)
+    resp = np.ascontiguousarray(resp, dtype=np.float32)
+    kp, nr = resp.shape[0], resp.shape[-1]
+    pixel_ids = np.ascontiguousarray(pixel_ids, dtype=np.int32)
+    w = np.zeros((len(pixel_ids), p.nt))
+    lib().orc_currents_from_qeff(ctypes.byref(p), len(blocks), _ptr(blocks), _ptr(qeff), _ptr(resp), kp, nr,
+                                 len(pixel_ids), _ptr(pixel_ids), _ptr(w))
+    return w
+
+
+def simulate_lines(cfg, seg: dict, resp: np.ndarray, pixels=None, frac: float = SHORT_FRAC):
+    """The path for line segments: transport, blocks, effective charge, currents."""
+    p = params(cfg)
+    L = drift_lines(p, seg)
+    w = line_windows(L)
+    ids, counts = active_blocks(p, w)
+    q = qeff_line_blocks(p, L, ids, frac)
+    pix = active_pixels(p, ids, resp.shape[0]) if pixels is None else np.asarray(pixels, np.int32)
+    wave = currents_from_qeff(p, ids, q, resp, pix)
+    return {"params": p, "lines": L, "block_ids": ids, "block_counts": counts, "qeff": q,
+            "pixel_ids": pix, "waveforms": wave}

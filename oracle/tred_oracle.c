@@ -749,3 +749,239 @@ void orc_param_grads(const orc_params *p, int n, const float *z, const float *ne
     glob[2] = gtau;
     (void)ne;
 }
+
+/* ========================================================================= */
+/* Line-shape track segments (Sec. II-C, "Calculation of Q for a line-shape      */
+/* track segment", Eq. qline; "short track segments").                         */
+/* ========================================================================= */
+
+/* Drifted segment: both endpoints in grid units; one width per axis, taken at the
+ * midpoint's drift time (the paper gives one sigma per segment); the window spans
+ * both endpoints +- nsigma sigma; attachment at the midpoint's drift time. */
+typedef struct {
+    orc_dep d;          /* mu = midpoint, sig, q, lo/hi window, valid */
+    double p0[3], p1[3];
+} orc_line;
+
+void orc_drift_lines(const orc_params *p, int n, const float *x0, const float *y0,
+                     const float *z0, const float *x1, const float *y1, const float *z1,
+                     const float *t0, const float *ne, orc_line *out)
+{
+    const double v = (double)p->v_cm_per_us;
+    const double tick = (double)p->tick_us;
+    const double h = (double)p->pitch_cm / (double)p->n_sub;
+    const double width_x = (double)p->npx_x * (double)p->pitch_cm;
+    const double width_y = (double)p->npx_y * (double)p->pitch_cm;
+    const double DT = (double)p->DT_cm2_per_s, DL = (double)p->DL_cm2_per_s;
+    const double s0 = (double)p->sigma0_cells_xy, s0t = (double)p->sigma0_ticks;
+    const double ns = (double)p->nsigma;
+    const double tau = (double)p->lifetime_us;
+    for (int i = 0; i < n; ++i) {
+        orc_line *L = &out[i];
+        orc_dep *d = &L->d;
+        const double xa = x0[i], ya = y0[i], za = z0[i], xb = x1[i], yb = y1[i], zb = z1[i];
+        const double t0d = t0[i], ned = ne[i];
+        int ok = isfinite(xa) && isfinite(ya) && isfinite(za) && isfinite(xb) && isfinite(yb)
+                 && isfinite(zb) && isfinite(t0d) && isfinite(ned) && za >= 0.0 && zb >= 0.0
+                 && ned >= 0.0 && xa >= 0.0 && xa < width_x && ya >= 0.0 && ya < width_y
+                 && xb >= 0.0 && xb < width_x && yb >= 0.0 && yb < width_y;
+        memset(L, 0, sizeof(*L));
+        if (!ok) {
+            for (int a = 0; a < 3; ++a) { d->lo[a] = 0; d->hi[a] = -1; }
+            d->valid = 0;
+            continue;
+        }
+        d->valid = 1;
+        const double tda = za / v, tdb = zb / v;
+        L->p0[0] = xa / h - 0.5;
+        L->p0[1] = ya / h - 0.5;
+        L->p0[2] = (t0d + tda) / tick;
+        L->p1[0] = xb / h - 0.5;
+        L->p1[1] = yb / h - 0.5;
+        L->p1[2] = (t0d + tdb) / tick;
+        double zm = za + zb;
+        zm = zm * 0.5;
+        const double td = zm / v;               /* midpoint drift time */
+        double a = DT * 2.0;
+        a = a * 1e-6;
+        a = a * td;
+        double b = h * h;
+        a = a / b;
+        double c = s0 * s0;
+        const double sxy = sqrt(a + c);
+        a = DL * 2.0;
+        a = a * 1e-6;
+        a = a * td;
+        b = v * tick;
+        b = b * b;
+        a = a / b;
+        c = s0t * s0t;
+        const double st = sqrt(a + c);
+        d->sig[0] = sxy;
+        d->sig[1] = sxy;
+        d->sig[2] = st;
+        d->q = ned * exp(-td / tau);
+        for (int ax = 0; ax < 3; ++ax) {
+            d->mu[ax] = 0.5 * (L->p0[ax] + L->p1[ax]);
+            const double K = ns * d->sig[ax];
+            const double mn = L->p0[ax] < L->p1[ax] ? L->p0[ax] : L->p1[ax];
+            const double mx = L->p0[ax] < L->p1[ax] ? L->p1[ax] : L->p0[ax];
+            d->lo[ax] = (int32_t)floor(mn - K);
+            d->hi[ax] = (int32_t)ceil(mx + K);
+        }
+    }
+}
+
+/* Normalised charge density of a uniform line from p0 to p1 diffused by an
+ * axis-aligned Gaussian (Eq. qline divided by Q), in grid units, written with
+ *     Delta^2 = S alpha,  A1 = -S beta,  A2 = S (alpha - beta),  B = S (alpha gamma - beta^2),
+ *     S = sx^2 sy^2 sz^2, alpha = sum d_i^2 / s_i^2, beta = sum a_i d_i / s_i^2,
+ *     gamma = sum a_i^2 / s_i^2, d = p1 - p0, a = x - p0,
+ * so that rho = exp(-B / (2 Delta^2)) (erf(A2 / (sqrt2 Delta sx sy sz))
+ *                - erf(A1 / (sqrt2 Delta sx sy sz))) / (4 pi Delta).
+ * The exponent carries the factor 1/2 that the isotropic limit exp(-d_perp^2 / 2 s^2)
+ * requires.  Segments shorter than frac * sigma on every axis use the point
+ * Gaussian at the midpoint (the short-segment limit). */
+double orc_line_density(const double *p0, const double *p1, const double *sig, double frac,
+                        const double *x)
+{
+    int shortseg = 1;
+    for (int i = 0; i < 3; ++i) shortseg &= fabs(p1[i] - p0[i]) < frac * sig[i];
+    if (shortseg) {
+        double r = 1.0;
+        for (int i = 0; i < 3; ++i) {
+            const double m = 0.5 * (p0[i] + p1[i]);
+            const double u = (x[i] - m) / sig[i];
+            r *= exp(-0.5 * u * u) / (sqrt(2.0 * M_PI) * sig[i]);
+        }
+        return r;
+    }
+    const double S = sig[0] * sig[0] * sig[1] * sig[1] * sig[2] * sig[2];
+    double alpha = 0.0, beta = 0.0, gamma = 0.0;
+    for (int i = 0; i < 3; ++i) {
+        const double di = p1[i] - p0[i], ai = x[i] - p0[i], w = 1.0 / (sig[i] * sig[i]);
+        alpha += di * di * w;
+        beta += ai * di * w;
+        gamma += ai * ai * w;
+    }
+    const double Delta = sqrt(S * alpha);
+    const double B = S * (alpha * gamma - beta * beta);
+    const double A1 = -S * beta, A2 = S * (alpha - beta);
+    const double den = sqrt(2.0) * Delta * sig[0] * sig[1] * sig[2];
+    return exp(-B / (2.0 * Delta * Delta)) * (erf(A2 / den) - erf(A1 / den)) / (4.0 * M_PI * Delta);
+}
+
+/* Effective charge of the listed blocks from line segments (Eq. eff_q with the node
+ * charge Q_{lmn,C} = Q rho(node) w_l w_m w_n / 8): every quadrature node of every cell
+ * of the window is scattered to the grid points of Eq. trilinear (its cell centre
+ * with 1 - |s| and the adjacent centre on its side with |s|, per axis).  The
+ * support of the result is the window +- 1, as for points.  Layout as
+ * orc_qeff_blocks. */
+void orc_qeff_line_blocks(const orc_params *p, int n, const orc_line *L, double frac, int nb,
+                          const int32_t *blocks, double *qeff)
+{
+    const int ns = p->n_sub, bp = p->bp, btk = p->bt, nl = p->gl_order;
+    const int nbx = p->npx_x / p->bp, nbt = p->nt / p->bt;
+    const size_t per_block = (size_t)ns * ns * bp * bp * btk;
+    double xi[64], wl[64];
+    orc_gl_rule(nl, xi, wl);
+    memset(qeff, 0, sizeof(double) * per_block * nb);
+#pragma omp parallel for schedule(dynamic)
+    for (int b = 0; b < nb; ++b) {
+        int blk = blocks[b];
+        int bt = blk % nbt, bxy = blk / nbt, bx = bxy % nbx, by = bxy / nbx;
+        int X0 = bx * bp * ns, Y0 = by * bp * ns, T0 = bt * btk;
+        double *Q = qeff + per_block * b;
+        for (int i = 0; i < n; ++i) {
+            const orc_dep *d = &L[i].d;
+            int ga[3], gb[3];
+            int ok = 1;
+            for (int ax = 0; ax < 3; ++ax) ok &= support(p, d, ax, &ga[ax], &gb[ax]);
+            if (!ok) continue;
+            if (gb[0] < X0 || ga[0] > X0 + bp * ns - 1 || gb[1] < Y0 || ga[1] > Y0 + bp * ns - 1
+                || gb[2] < T0 || ga[2] > T0 + btk - 1)
+                continue;
+            for (int cz = d->lo[2]; cz <= d->hi[2]; ++cz)
+                for (int cy = d->lo[1]; cy <= d->hi[1]; ++cy)
+                    for (int cx = d->lo[0]; cx <= d->hi[0]; ++cx)
+                        for (int ln = 0; ln < nl; ++ln)
+                            for (int lm = 0; lm < nl; ++lm)
+                                for (int ll = 0; ll < nl; ++ll) {
+                                    const double s[3] = {0.5 * xi[ll], 0.5 * xi[lm], 0.5 * xi[ln]};
+                                    const double node[3] = {cx + s[0], cy + s[1], cz + s[2]};
+                                    const double qn = d->q * 0.125 * wl[ll] * wl[lm] * wl[ln]
+                                                      * orc_line_density(L[i].p0, L[i].p1, d->sig, frac, node);
+                                    /* targets per axis: (grid point, coefficient) */
+                                    int tg[3][2];
+                                    double tc[3][2];
+                                    int nt3[3];
+                                    const int cc[3] = {cx, cy, cz};
+                                    for (int ax = 0; ax < 3; ++ax) {
+                                        if (s[ax] == 0.0) {
+                                            tg[ax][0] = cc[ax]; tc[ax][0] = 1.0; nt3[ax] = 1;
+                                        } else {
+                                            tg[ax][0] = cc[ax]; tc[ax][0] = 1.0 - fabs(s[ax]);
+                                            tg[ax][1] = cc[ax] + (s[ax] > 0 ? 1 : -1); tc[ax][1] = fabs(s[ax]);
+                                            nt3[ax] = 2;
+                                        }
+                                    }
+                                    for (int kz = 0; kz < nt3[2]; ++kz) {
+                                        const int gt = tg[2][kz];
+                                        if (gt < T0 || gt >= T0 + btk || gt < ga[2] || gt > gb[2]) continue;
+                                        for (int ky = 0; ky < nt3[1]; ++ky) {
+                                            const int gy = tg[1][ky];
+                                            if (gy < Y0 || gy >= Y0 + bp * ns || gy < ga[1] || gy > gb[1]) continue;
+                                            for (int kx = 0; kx < nt3[0]; ++kx) {
+                                                const int gx = tg[0][kx];
+                                                if (gx < X0 || gx >= X0 + bp * ns || gx < ga[0] || gx > gb[0]) continue;
+                                                const int jy = gy % ns, py = gy / ns - by * bp;
+                                                const int jx = gx % ns, px = gx / ns - bx * bp;
+                                                Q[((((size_t)jy * ns + jx) * bp + py) * bp + px) * btk + (gt - T0)] +=
+                                                    qn * tc[0][kx] * tc[1][ky] * tc[2][kz];
+                                            }
+                                        }
+                                    }
+                                }
+        }
+    }
+}
+
+/* Induced current on listed pixels from block-stored effective charge (Eq.
+ * interlaced written out): I[P, t] = sum_j sum_K sum_tau Qeff[j, P + K, t - tau]
+ * i[j, K, tau], summing over the listed blocks (which must cover the support).
+ * qeff layout [block][jy][jx][py][px][t]; resp [Ky][Kx][jy][jx][tau]. */
+void orc_currents_from_qeff(const orc_params *p, int nb, const int32_t *blocks, const double *qeff,
+                            const float *resp, int kp, int nr, int npix, const int32_t *pixel_ids,
+                            double *wave)
+{
+    const int ns = p->n_sub, bp = p->bp, btk = p->bt, R = (kp - 1) / 2, nt = p->nt;
+    const int nbx = p->npx_x / p->bp, nbt = p->nt / p->bt;
+    const size_t per_block = (size_t)ns * ns * bp * bp * btk;
+#pragma omp parallel for schedule(dynamic)
+    for (int ip = 0; ip < npix; ++ip) {
+        double *I = wave + (size_t)ip * nt;
+        memset(I, 0, sizeof(double) * nt);
+        const int P = pixel_ids[ip], Px = P % p->npx_x, Py = P / p->npx_x;
+        for (int b = 0; b < nb; ++b) {
+            const int blk = blocks[b];
+            const int bt = blk % nbt, bxy = blk / nbt, bx = bxy % nbx, by = bxy / nbx;
+            const double *Q = qeff + per_block * b;
+            for (int py = 0; py < bp; ++py)
+                for (int px = 0; px < bp; ++px) {
+                    const int Ky = by * bp + py - Py, Kx = bx * bp + px - Px;
+                    if (Ky < -R || Ky > R || Kx < -R || Kx > R) continue;
+                    for (int jy = 0; jy < ns; ++jy)
+                        for (int jx = 0; jx < ns; ++jx) {
+                            const double *col = Q + ((((size_t)jy * ns + jx) * bp + py) * bp + px) * btk;
+                            const float *ir = resp + ((((size_t)(Ky + R) * kp + (Kx + R)) * ns + jy) * ns + jx) * nr;
+                            for (int tl = 0; tl < btk; ++tl) {
+                                const double q = col[tl];
+                                if (q == 0.0) continue;
+                                const int ts = bt * btk + tl;
+                                for (int tau = 0; tau < nr && ts + tau < nt; ++tau) I[ts + tau] += q * (double)ir[tau];
+                            }
+                        }
+                }
+        }
+    }
+}

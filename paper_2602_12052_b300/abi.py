@@ -33,7 +33,7 @@ EXPORTS = [
     "tred_set_response", "tred_drift", "tred_blockbin", "tred_effq", "tred_convolve",
     "tred_gather_pixels", "tred_readout", "tred_launch_count", "tred_blockbin_noalloc",
     "tred_set_transport", "tred_residual", "tred_adjoint", "tred_param_grads",
-    "tred_drift_events", "tred_effq_range", "tred_convolve_range",
+    "tred_drift_events", "tred_effq_range", "tred_convolve_range", "tred_drift_lines", "tred_effq_lines",
 ]
 
 
@@ -100,6 +100,8 @@ def load(path: str | None = None) -> ctypes.CDLL:
     lib.tred_effq_range.argtypes = [_P, _I, ctypes.POINTER(Deposits), _P, _P, _P, _P, _I, _I, _P, _P]
     lib.tred_convolve_range.argtypes = [_P, _P, _P, _I, _I, _P, _P, _P]
     lib.tred_set_transport.argtypes = [_P, ctypes.POINTER(Params)]
+    lib.tred_drift_lines.argtypes = [_P, _I, _P, _P, _P, _P, _P, _P, _P, _P, ctypes.POINTER(Deposits), _P, _P]
+    lib.tred_effq_lines.argtypes = [_P, _I, ctypes.POINTER(Deposits), _P, _P, _P, _P, _P, _P, _P]
     lib.tred_residual.argtypes = [_P, _P, _P, _P, _P, _I, _P, _P, _P, _P]
     lib.tred_adjoint.argtypes = [_P, _I, ctypes.POINTER(Deposits), _P, _P, _P, _P, _P, _P, _P, _P, _P, _P]
     lib.tred_param_grads.argtypes = [_P, _I, _P, ctypes.POINTER(Deposits), _P, _P, _P, _P]

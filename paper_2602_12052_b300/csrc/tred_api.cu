@@ -366,6 +366,31 @@ int32_t tred_drift(tred_handle *h, int32_t n, const float *x, const float *y, co
     return launch_drift(h, n, x, y, z, t0, ne, nullptr, *out, (cudaStream_t)stream);
 }
 
+int32_t tred_drift_lines(tred_handle *h, int32_t n, const float *x0, const float *y0, const float *z0,
+                         const float *x1, const float *y1, const float *z1, const float *t0, const float *ne,
+                         const tred_deposits *out, float *half, void *stream) {
+    if (!h) return TRED_ERR_INVALID_ARG;
+    if (n < 0 || n > h->max_deposits)
+        return set_error(h, TRED_ERR_CAPACITY, "tred_drift_lines: n=%d outside [0, max_deposits=%d]", n, h->max_deposits);
+    if (n > 0 && (!x0 || !y0 || !z0 || !x1 || !y1 || !z1 || !t0 || !ne || !half || !deps_ok(out)))
+        return set_error(h, TRED_ERR_INVALID_ARG, "tred_drift_lines: null pointer");
+    if (h->d.n_events > 1) return set_error(h, TRED_ERR_INVALID_ARG, "tred_drift_lines: single-event handles only");
+    if (n == 0) return TRED_OK;
+    return launch_drift_lines(h, n, x0, y0, z0, x1, y1, z1, t0, ne, *out, half, (cudaStream_t)stream);
+}
+
+int32_t tred_effq_lines(tred_handle *h, int32_t n, const tred_deposits *deps, const float *half,
+                        const int32_t *block_ids, const int32_t *dep_offsets, const int32_t *dep_index,
+                        const int32_t *n_blocks_dev, float *qeff, void *stream) {
+    if (!h) return TRED_ERR_INVALID_ARG;
+    if (n < 0 || n > h->max_deposits)
+        return set_error(h, TRED_ERR_CAPACITY, "tred_effq_lines: n=%d outside [0, max_deposits]", n);
+    if ((n > 0 && (!deps_ok(deps) || !half)) || !block_ids || !dep_offsets || !dep_index || !n_blocks_dev || !qeff)
+        return set_error(h, TRED_ERR_INVALID_ARG, "tred_effq_lines: null pointer");
+    return launch_effq_lines(h, n, n > 0 ? *deps : tred_deposits{}, half, block_ids, dep_offsets, dep_index,
+                             n_blocks_dev, qeff, (cudaStream_t)stream);
+}
+
 int32_t tred_drift_events(tred_handle *h, int32_t n, const float *x, const float *y, const float *z,
                           const float *t0, const float *ne, const int32_t *event, const tred_deposits *out,
                           void *stream) {

@@ -105,6 +105,12 @@ int launch_blockbin(tred_handle *h, int n, const tred_deposits &deps, int32_t *b
                     int32_t max_pairs, int32_t *n_blocks_dev, cudaStream_t s);
 size_t effq_scratch_bytes(int side, int grid);
 int dft_basis_build(tred_handle *h);
+int launch_drift_lines(tred_handle *h, int n, const float *x0, const float *y0, const float *z0, const float *x1,
+                       const float *y1, const float *z1, const float *t0, const float *ne, const tred_deposits &out,
+                       float *half, cudaStream_t s);
+int launch_effq_lines(tred_handle *h, int n, const tred_deposits &deps, const float *half, const int32_t *block_ids,
+                      const int32_t *dep_offsets, const int32_t *dep_index, const int32_t *n_blocks_dev, float *qeff,
+                      cudaStream_t s);
 size_t dft_basis_bytes(int bt);
 size_t dft_zspec_bytes(int blocks, int npairs, int lt);
 int launch_dft_gemm(tred_handle *h, const int32_t *n_blocks_dev, const float *qeff, int qrows_blocks,

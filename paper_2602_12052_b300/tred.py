@@ -115,6 +115,18 @@ def tred_drift_events(h: Handle, n: int, x, y, z, t0, ne, event, out: DepositBuf
                                     ctypes.byref(out.struct), _stream(stream)))
 
 
+def tred_drift_lines(h: Handle, n: int, x0, y0, z0, x1, y1, z1, t0, ne, out: DepositBuffers, half, stream=None):
+    h.check(h.lib.tred_drift_lines(h.h, n, _ptr(x0), _ptr(y0), _ptr(z0), _ptr(x1), _ptr(y1), _ptr(z1), _ptr(t0),
+                                   _ptr(ne), ctypes.byref(out.struct), _ptr(half), _stream(stream)))
+
+
+def tred_effq_lines(h: Handle, n: int, deps: DepositBuffers, half, block_ids, dep_offsets, dep_index,
+                    n_blocks_dev, qeff, stream=None):
+    h.check(h.lib.tred_effq_lines(h.h, n, ctypes.byref(deps.struct), _ptr(half), _ptr(block_ids),
+                                  _ptr(dep_offsets), _ptr(dep_index), _ptr(n_blocks_dev), _ptr(qeff),
+                                  _stream(stream)))
+
+
 def tred_effq_range(h: Handle, n: int, deps: DepositBuffers, block_ids, dep_offsets, dep_index,
                     n_blocks_dev, slot_base: int, slot_count: int, qeff, stream=None):
     h.check(h.lib.tred_effq_range(h.h, n, ctypes.byref(deps.struct), _ptr(block_ids), _ptr(dep_offsets),
@@ -281,6 +293,30 @@ class Simulator:
 
 
 # ----------------------------------------------------------------- differentiation
+class LineSimulator(Simulator):
+    """The hot path for line-shape track segments (Sec. II-C, Eq. qline): segment
+    transport, the same binning, the segments' effective charge, then the same
+    convolution, gather and readout."""
+
+    def __init__(self, cfg, resp: torch.Tensor, max_segments: int, max_blocks: int, max_pixels: int, **kw):
+        super().__init__(cfg, resp, max_deposits=max_segments, max_blocks=max_blocks, max_pixels=max_pixels, **kw)
+        self.half = torch.zeros(3 * max(max_segments, 1), dtype=torch.float32, device=self.device)
+
+    def step_lines(self, n, x0, y0, z0, x1, y1, z1, t0, ne, stream=None, readout=True):
+        """Enqueue one pass for n segments already on the device."""
+        tred_drift_lines(self.h, n, x0, y0, z0, x1, y1, z1, t0, ne, self.deps, self.half[:3 * max(n, 1)], stream)
+        tred_blockbin(self.h, n, self.deps, self.block_ids, self.block_counts, self.dep_offsets,
+                      self.dep_index, self.n_blocks_dev, stream)
+        tred_effq_lines(self.h, n, self.deps, self.half[:3 * max(n, 1)], self.block_ids, self.dep_offsets,
+                        self.dep_index, self.n_blocks_dev, self.qeff, stream)
+        tred_convolve(self.h, self.block_ids, self.n_blocks_dev, self.qeff, self.out_blocks, stream)
+        tred_gather_pixels(self.h, self.block_ids, self.n_blocks_dev, self.out_blocks,
+                           self.pixel_ids, self.waveforms, self.n_pixels_dev, stream)
+        if readout:
+            tred_readout(self.h, self.rp, self.pixel_ids, self.waveforms, self.n_pixels_dev,
+                         self.hit_pixel, self.hit_tick, self.hit_charge, self.n_hits_dev, stream)
+
+
 class DiffState:
     """Buffers of the backward pass bound to a Simulator."""
 

@@ -97,11 +97,20 @@ CONFIGS = {
         track_len_cm=(1.0, 100.0), z_range_cm=(0.0, 50.0), ne_mean=60.0, seed=1020),
     # Spill-scale plane: GL-3, 13 x 13 pixel x 400 tick response, 4 x 4 pixel blocks
     # (so the padded spatial extent stays 16), FFT length 1024 along time.
+    # Line segments (Sec. II-C, Eq. qline): the tiny track and a 200-track module plane
+    # cut into 0.25 cm and 0.3 cm segments (make_segments).
+    "tiny_lines": Config(name="tiny_lines"),
+    "module_lines": Config(
+        name="module_lines", npx=512, nt=6400, kind="tracks", n_tracks=200,
+        track_len_cm=(1.0, 100.0), z_range_cm=(0.0, 50.0), ne_mean=60.0, seed=1002),
     "spill_plane": Config(
         name="spill_plane", npx=512, nt=6400, kind="tracks", n_tracks=0,
         min_deposits=290_000, track_len_cm=(1.0, 100.0), z_range_cm=(0.0, 50.0),
         ne_mean=60.0, seed=1005, gl_order=3, kp=13, nr=400, bp=4, bt=256, lt=1024),
 }
+
+
+SEG_CM = {"tiny_lines": 0.25, "module_lines": 0.3}
 
 
 def get_config(name: str, **overrides) -> Config:
@@ -185,6 +194,56 @@ def make_deposits(cfg: Config, seed: int | None = None) -> dict:
         "z": p[:, 2].astype(np.float32), "t0": t0.astype(np.float32),
         "ne": ne.astype(np.float32),
     }
+
+
+def make_segments(cfg: Config, seg_cm: float, seed: int | None = None) -> dict:
+    """Line-segment deposits {x0, y0, z0, x1, y1, z1, t0, ne}: the tracks of
+    ``make_deposits`` cut into consecutive segments of ``seg_cm`` (the last piece of a
+    track may be shorter), n_e ~ Poisson(ne_mean * length / step_cm).  Segments with
+    an endpoint outside the volume are dropped."""
+    rng = np.random.default_rng((cfg.seed if seed is None else seed) + 7777)
+    width = cfg.npx * cfg.pitch_cm
+    a_all, b_all, t_all = [], [], []
+
+    def cut(start, d, L):
+        k = np.arange(int(math.ceil(L / seg_cm)))
+        s0 = k * seg_cm
+        s1 = np.minimum((k + 1) * seg_cm, L)
+        return start[None, :] + s0[:, None] * d[None, :], start[None, :] + s1[:, None] * d[None, :]
+
+    def inside(p):
+        return ((p[:, 0] >= 0.0) & (p[:, 0] < width) & (p[:, 1] >= 0.0) & (p[:, 1] < width)
+                & (p[:, 2] >= cfg.z_range_cm[0]) & (p[:, 2] <= cfg.z_range_cm[1]))
+    if cfg.kind == "single_track":
+        margin = 4 * cfg.pitch_cm
+        L = cfg.track_len_cm[0]
+        while True:
+            start = np.array([rng.uniform(0.0, width), rng.uniform(0.0, width), rng.uniform(*cfg.z_range_cm)])
+            d = _isotropic(rng, 1)[0]
+            end = start + L * d
+            lo, hi = np.minimum(start, end), np.maximum(start, end)
+            if (lo[0] >= margin and hi[0] <= width - margin and lo[1] >= margin and hi[1] <= width - margin
+                    and lo[2] >= cfg.z_range_cm[0] and hi[2] <= cfg.z_range_cm[1]):
+                break
+        a, b = cut(start, d, L)
+        t0 = 32.0 * cfg.tick_us - float(min(a[:, 2].min(), b[:, 2].min())) / cfg.v_cm_per_us
+        a_all.append(a); b_all.append(b); t_all.append(np.full(len(a), t0))
+    else:
+        for _ in range(cfg.n_tracks):
+            L = math.exp(rng.uniform(math.log(cfg.track_len_cm[0]), math.log(cfg.track_len_cm[1])))
+            start = np.array([rng.uniform(0.0, width), rng.uniform(0.0, width), rng.uniform(*cfg.z_range_cm)])
+            d = _isotropic(rng, 1)[0]
+            a, b = cut(start, d, L)
+            keep = inside(a) & inside(b)
+            a_all.append(a[keep]); b_all.append(b[keep]); t_all.append(np.zeros(int(keep.sum())))
+    a = np.concatenate(a_all) if a_all else np.zeros((0, 3))
+    b = np.concatenate(b_all) if b_all else np.zeros((0, 3))
+    t0 = np.concatenate(t_all) if t_all else np.zeros(0)
+    length = np.linalg.norm(b - a, axis=1)
+    ne = rng.poisson(cfg.ne_mean * length / cfg.step_cm).astype(np.float32)
+    f = lambda v: np.ascontiguousarray(v, dtype=np.float32)
+    return {"x0": f(a[:, 0]), "y0": f(a[:, 1]), "z0": f(a[:, 2]), "x1": f(b[:, 0]), "y1": f(b[:, 1]),
+            "z1": f(b[:, 2]), "t0": f(t0), "ne": ne}
 
 
 def make_event(cfg: Config, seed: int | None = None):
