@@ -351,7 +351,20 @@ def run_lines(args):
            "active_blocks": nb, "active_pixels": npix, "hits": nh,
            "l2": "flushed between timed steps"},
           stages_ms={"drift+blockbin": m[0], "effq_lines": m[1], "convolve": m[2], "gather+readout": m[3]},
-          clocks=clk.summary())
+          clocks=clk.summary(), cpu_baseline=None if args.no_cpu_baseline else _lines_cpu(cfg, seg, resp.numpy()))
+
+
+def _lines_cpu(cfg, seg, resp, k=400):
+    """The FP64 oracle on the first k segments of the workload (every pixel they
+    reach), on the host cores."""
+    import oracle
+    sub = {kk: v[:k] for kk, v in seg.items()}
+    t = time.perf_counter()
+    r = oracle.simulate_lines(cfg, sub, resp)
+    dt = time.perf_counter() - t
+    return {"value": k / dt, "unit": "segments/s", "cores": oracle.num_threads(), "kind": "oracle",
+            "sample": f"first {k} segments of module_lines, full path to pixel currents "
+                      f"({len(r['block_ids'])} blocks, {len(r['pixel_ids'])} pixels), {dt:.1f} s"}
 
 
 def run_adjoint(args):
