@@ -38,7 +38,7 @@ struct ConvConst {
 constexpr int SPEC_THREADS = 512;
 constexpr int SPEC_WARPS = SPEC_THREADS / 32;
 constexpr int SPEC_TMEM_COLS = 256;         // 4 warps per lane quarter x 64 columns
-constexpr int PG = 4;                       // channel pairs per stage A / stage B round
+constexpr int PG = 5;                       // channel pairs per stage A / stage B round
 constexpr int ZT_ROW = 9;                   // padded px row of the bin-major transpose
 constexpr int ZT_BIN = 8 * ZT_ROW + 1;      // [py][px] for py, px < 8, odd stride
 // Bin order inside the transpose buffer.  Stage A lane l stores bins k2 = a + 2 b
