@@ -23,8 +23,10 @@
 //                 takes no shared-memory bandwidth.  The epilogue inverts the spatial
 //                 FFT from the registers and writes the class's bins to the
 //                 per-chunk spectrum buffer.
-//   k_conv_itime  one CTA per (block, mirror row pair, half): inverse time FFT of
-//                 16 columns (8 mirror pairs) and the MPCP recombination.
+//   k_conv_itime  persistent CTAs over (block, mirror row pair, part) items of 16
+//                 columns (8 mirror pairs; 8 columns at lt = 1024), one warp per
+//                 column: inverse time FFT and the MPCP recombination, the next
+//                 item's spectra streamed in by cp.async meanwhile.
 #include <utility>
 
 #include "tred_internal.cuh"
@@ -307,102 +309,145 @@ __global__ void __launch_bounds__(SPEC_THREADS, 1)
     }
 }
 
-// Inverse time FFT of 8 mirror column pairs + MPCP recombination.
+// 8-byte asynchronous copy global -> shared (through L1), committed per item
+__device__ __forceinline__ void cp_async8(void *smem, const void *gmem) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"((uint32_t)__cvta_generic_to_shared(smem)),
+                 "l"(gmem)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+    asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
+
+// Inverse time FFT + MPCP recombination.  An item is NC columns of one block: NC / 2
+// columns (a, cx) of a row a and their mirrors (m(a), m(cx)), m(c) = (bp - 1 - c) mod 16.
+// Persistent CTAs, one warp per column: the next item's spectra stream into the
+// other half of a double buffer (cp.async) while the current item is transformed;
+// mirror partners exchange their imaginary parts through shared memory.
 template <int G>
-__global__ void __launch_bounds__(256) k_conv_itime(const int32_t *__restrict__ n_blocks_dev,
-                                                    const float2 *__restrict__ yspec,
-                                                    const float2 *__restrict__ tw, ConvConst c,
-                                                    float *__restrict__ out, int slot_base,
-                                                    int slot_count) {
+__host__ __device__ constexpr int itime_cols() { return G == 8 ? 16 : 8; }
+template <int G>
+constexpr size_t itime_smem_bytes() {
+    return sizeof(float2) * (2 * itime_cols<G>() * (64 * G + 1) + 64 * G + 32) +
+           sizeof(float) * itime_cols<G>() * (2 * G) * 33;
+}
+
+template <int G>
+__global__ void __launch_bounds__(32 * itime_cols<G>(), 1)
+    k_conv_itime(const int32_t *__restrict__ n_blocks_dev, const float2 *__restrict__ yspec,
+                 const float2 *__restrict__ tw, ConvConst c, float *__restrict__ out, int slot_base,
+                 int slot_count) {
     constexpr int LT = 64 * G;
     constexpr int NPL = LT / 32;          // values per lane
+    constexpr int NC = itime_cols<G>();   // columns per item
+    constexpr int HC = NC / 2;
+    constexpr int PARTS = LP / HC;        // items per mirror row pair
+    constexpr int NT = 32 * NC;
     constexpr int SROW = LT + 1;
+    constexpr int IROW = 33;              // imaginary-part exchange: [column][bitrev(k)][lane group]
     extern __shared__ float2 sm[];
-    float2 *S = sm;                       // [16][LT + 1]
-    float2 *wlt = S + 16 * SROW;          // W_LT
+    float2 *S = sm;                                                   // [2][NC][SROW]
+    float2 *wlt = S + 2 * NC * SROW;                                  // W_LT
     float2 *w32 = wlt + LT;
-    float2 *wn = w32 + 32;                // W_NPL
+    float *Ib = reinterpret_cast<float *>(w32 + 32);                  // [NC][NPL][IROW]
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    for (int k = tid; k < LT; k += blockDim.x) wlt[k] = tw[TW_LT + k];
+    for (int k = tid; k < LT; k += NT) wlt[k] = tw[TW_LT + k];
     if (tid < 32) w32[tid] = tw[TW_32 + tid];
-    if (tid < NPL) wn[tid] = tw[TW_LT + tid * 32];        // W_NPL^m = W_LT^{32 m}
     const int nb = n_blocks_dev[0];
     const int nloc = min(slot_count, nb - slot_base);
     if (nloc <= 0) return;
-    const int items = nloc * 16;
-    for (int item = blockIdx.x; item < items; item += gridDim.x) {
-        const int sl = item >> 4, rp = (item >> 1) & 7, half = item & 1;
-        // mirror map on cyclic indices: m(c) = (bp - 1 - c) mod 16; row pairs {a, m(a)}
-        int a = -1, cnt = 0;
+    const int items = nloc * 8 * PARTS;
+    // the rows of mirror row pair rp: the rp-th row a with a < m(a), and bro = m(a)
+    auto rows_of = [&](int rp, int &a, int &bro) {
+        a = -1;
+        int cnt = 0;
         for (int r = 0; r < LP; ++r) {
             const int m = (c.bp - 1 - r + 2 * LP) % LP;
             if (r < m) {
-                if (cnt == rp) { a = r; break; }
+                if (cnt == rp) {
+                    a = r;
+                    break;
+                }
                 ++cnt;
             }
         }
-        const int bro = (c.bp - 1 - a + 2 * LP) % LP;
-        __syncthreads();
-        // load 16 columns: q < 8 -> (a, cx = 8 half + q); q >= 8 -> (bro, m(8 half + q - 8))
-        for (int k = tid; k < 16 * LT; k += blockDim.x) {
-            const int q = k & 15, f = k >> 4;
-            const int cx0 = 8 * half + (q & 7);
-            const int cy = q < 8 ? a : bro;
-            const int cx = q < 8 ? cx0 : (c.bp - 1 - cx0 + 2 * LP) % LP;
-            S[q * SROW + f] = yspec[((size_t)sl * LT + f) * (LP * LP) + cy * LP + cx];
+        bro = (c.bp - 1 - a + 2 * LP) % LP;
+    };
+    auto column = [&](int q, int part, int a, int bro, int &cy, int &cx) {
+        const int cx0 = HC * part + (q % HC);
+        cy = q < HC ? a : bro;
+        cx = q < HC ? cx0 : (c.bp - 1 - cx0 + 2 * LP) % LP;
+    };
+    // thread tid copies column q = tid % NC at frequencies f = tid / NC + 32 j
+    auto issue = [&](int it, int bsel) {
+        const int sl = it / (8 * PARTS), rp = (it / PARTS) % 8, part = it % PARTS;
+        int a, bro, cy, cx;
+        rows_of(rp, a, bro);
+        const int q = tid % NC;
+        column(q, part, a, bro, cy, cx);
+        const float2 *src = yspec + (size_t)sl * LT * (LP * LP) + cy * LP + cx;
+        float2 *dst = S + (bsel * NC + q) * SROW;
+#pragma unroll 4
+        for (int f = tid / NC; f < LT; f += NT / NC) cp_async8(dst + f, src + (size_t)f * (LP * LP));
+        cp_async_commit();
+    };
+    int it = blockIdx.x;
+    if (it < items) issue(it, 0);
+    for (int i = 0; it < items; ++i, it += gridDim.x) {
+        const int cur = i & 1;
+        if (it + (int)gridDim.x < items)
+            issue(it + gridDim.x, cur ^ 1);       // that buffer's last readers passed the previous barrier
+        else
+            cp_async_commit();                    // empty group: keeps the wait count uniform
+        cp_async_wait<1>();
+        __syncthreads();                          // this item's columns (and W tables) are in place
+        const int sl = it / (8 * PARTS), rp = (it / PARTS) % 8, part = it % PARTS;
+        int a, bro, cy, cx;
+        rows_of(rp, a, bro);
+        const int q = warp;
+        column(q, part, a, bro, cy, cx);
+        float2 v[NPL];
+        {
+            const float2 *src = S + (cur * NC + q) * SROW;
+#pragma unroll
+            for (int m = 0; m < NPL; ++m) v[m] = src[lane + 32 * m];
         }
-        __syncthreads();
-        if (warp < 8) {
-            const int q = warp;                       // pair (q, q + 8)
-            const int cx1 = 8 * half + q;
-            const int cx2 = (c.bp - 1 - cx1 + 2 * LP) % LP;
-            float2 x1[NPL], x2[NPL];
-            for (int which = 0; which < 2; ++which) {
-                const float2 *src = S + (which ? q + 8 : q) * SROW;
-                float2 v[NPL];
+        fft_reg_dif_c<NPL, true>(v);              // v[k] = u[bitrev(k)]
 #pragma unroll
-                for (int m = 0; m < NPL; ++m) v[m] = src[lane + 32 * m];
-                fft_reg_dif_c<NPL, true>(v);          // v[k] = u[bitrev(k)]
-#pragma unroll
-                for (int k = 0; k < NPL; ++k) {
-                    const int aa = bitrev<NPL>(k);
-                    float2 w = wlt[(lane * aa) % LT];
-                    w.y = -w.y;
-                    v[k] = fft32_lanes<true>(cmul(v[k], w), w32, lane);
-                }
-#pragma unroll
-                for (int k = 0; k < NPL; ++k) {
-                    if (which) x2[k] = v[k];
-                    else x1[k] = v[k];
-                }
-            }
-            // lane holds t = NPL * bitrev5(lane) + bitrev(k) in register k
-            const int uy1 = (a + c.R) % LP, ux1 = (cx1 + c.R) % LP;
-            const int uy2 = (bro + c.R) % LP, ux2 = (cx2 + c.R) % LP;
-            const int slot = slot_base + sl;
-            float *o1 = out + (((size_t)slot * LP + uy1) * LP + ux1) * LT + NPL * bitrev<32>(lane);
-            float *o2 = out + (((size_t)slot * LP + uy2) * LP + ux2) * LT + NPL * bitrev<32>(lane);
-            float r1[NPL], r2[NPL];
-#pragma unroll
-            for (int k = 0; k < NPL; ++k) {
-                const int t = bitrev<NPL>(k);
-                r1[t] = c.mpcp ? x1[k].x + x2[k].y : x1[k].x;
-                r2[t] = c.mpcp ? x2[k].x + x1[k].y : x2[k].x;
-            }
-#pragma unroll
-            for (int k = 0; k < NPL; k += 4) {
-                *reinterpret_cast<float4 *>(o1 + k) = make_float4(r1[k], r1[k + 1], r1[k + 2], r1[k + 3]);
-                *reinterpret_cast<float4 *>(o2 + k) = make_float4(r2[k], r2[k + 1], r2[k + 2], r2[k + 3]);
-            }
+        for (int k = 0; k < NPL; ++k) {
+            const int aa = bitrev<NPL>(k);
+            float2 w = wlt[(lane * aa) % LT];
+            w.y = -w.y;
+            v[k] = fft32_lanes<true>(cmul(v[k], w), w32, lane);
         }
+        // lane holds t = NPL * bitrev5(lane) + bitrev(k) in register k
+        const int b5 = bitrev<32>(lane);
+        float *ib = Ib + q * NPL * IROW;
+#pragma unroll
+        for (int k = 0; k < NPL; ++k) ib[bitrev<NPL>(k) * IROW + b5] = v[k].y;
+        __syncthreads();
+        const float *pib = Ib + (q < HC ? q + HC : q - HC) * NPL * IROW;   // mirror partner
+        const int uy = (cy + c.R) % LP, ux = (cx + c.R) % LP;
+        float *o = out + (((size_t)(slot_base + sl) * LP + uy) * LP + ux) * LT + NPL * b5;
+        float r[NPL];
+#pragma unroll
+        for (int k = 0; k < NPL; ++k) {
+            const int t = bitrev<NPL>(k);
+            r[t] = c.mpcp ? v[k].x + pib[t * IROW + b5] : v[k].x;
+        }
+#pragma unroll
+        for (int k = 0; k < NPL; k += 4) *reinterpret_cast<float4 *>(o + k) = make_float4(r[k], r[k + 1], r[k + 2], r[k + 3]);
     }
+    cp_async_wait<0>();
 }
 
 template <int NB1, int G>
 static int run_conv(tred_handle *h, const int32_t *n_blocks_dev, const float *qeff, float *out,
                     const ConvConst &c, int slot_base, int slot_count, cudaStream_t s) {
     static bool attr = false;
-    const size_t itime_smem = sizeof(float2) * (16 * (64 * G + 1) + 64 * G + 32 + 64 * G / 32);
+    const size_t itime_smem = itime_smem_bytes<G>();
     if (!attr) {
         cudaFuncSetAttribute(k_conv_spec<NB1, G, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SPEC_SMEM);
         cudaFuncSetAttribute(k_conv_spec<NB1, G, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SPEC_SMEM);
@@ -426,7 +471,8 @@ static int run_conv(tred_handle *h, const int32_t *n_blocks_dev, const float *qe
                                                                            h->pair_j, h->tw, c, h->yspec, base, cnt,
                                                                            slot_base, nullptr);
         }
-        k_conv_itime<G><<<sms * 2, 256, itime_smem, s>>>(n_blocks_dev, h->yspec, h->tw, c, out, base, cnt);
+        k_conv_itime<G><<<sms, 32 * itime_cols<G>(), itime_smem, s>>>(n_blocks_dev, h->yspec, h->tw, c, out, base,
+                                                                       cnt);
         h->launches += 2;
     }
     return check_cuda(h, cudaGetLastError(), "convolve launch");

@@ -5,11 +5,13 @@
 //   k_px_chunk / k_px_top / k_px_emit
 //                ballot + prefix compaction of the flags into the ascending pixel
 //                list; the flag array then holds each pixel's row (or -1)
-//   k_px_wave    one warp per active pixel, 128 ticks per step (float4 per lane);
-//                the pixel's block slots are read once into shared memory:
-//                sum, in a fixed order (by, bx, bt ascending), the outputs of the
-//                overlapping blocks; deterministic, no atomics.  Optional FP64
-//                accumulation (compensated mode).
+//   k_px_wave    one warp per active pixel: the pixel's contributing blocks are
+//                listed once in shared memory, then the window is swept 512 ticks
+//                per step (4 float4 per lane): sum, in a fixed order (by, bx, bt
+//                ascending), the outputs of the overlapping blocks; deterministic,
+//                no atomics.  Optional FP64 accumulation (compensated mode).
+#include <type_traits>
+
 #include "tred_internal.cuh"
 
 namespace tred {
@@ -136,21 +138,62 @@ __global__ void __launch_bounds__(1024) k_px_emit(int64_t n, int32_t *__restrict
 
 constexpr int PXW_THREADS = 256;
 constexpr int PXW_WARPS = PXW_THREADS / 32;
-constexpr int PXW_COLS = 16;                // (by, bx) block columns cached per pixel (bp + 2R <= 3 bp)
-constexpr int PXW_MAX_NBT = 64;             // time blocks cached per column
+constexpr int PXW_MAXE = 128;               // contributing (block column, time block) entries per pixel
+constexpr int PXW_CHUNK = 512;              // ticks per step of a warp (4 float4 per lane)
 
+// The output column of entry (slot, uy, ux) and its time block's first tick.
+struct PxEntry {
+    long long off;
+    int t0;
+};
+
+// Sum, for ticks t = T0 + 128 i + 4 lane + (0..3), i < 4, the listed entries' outputs in
+// list order (entries whose range [t0, t0 + span) misses the chunk add nothing).
+template <typename Acc>
+__device__ __forceinline__ void px_accumulate(const float *__restrict__ out, long long off, int t0e, int T0,
+                                              int lane, int span, Acc (&acc)[4][4]) {
+    const float *src = out + off;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const int tl = T0 + 128 * i + 4 * lane - t0e;     // multiple of 4
+        float4 v;
+        if (tl >= 0 && tl + 3 < span) {
+            v = *reinterpret_cast<const float4 *>(src + tl);
+        } else if (tl + 3 < 0 || tl >= span) {
+            continue;
+        } else {
+            v.x = (tl >= 0 && tl < span) ? src[tl] : 0.f;
+            v.y = (tl + 1 >= 0 && tl + 1 < span) ? src[tl + 1] : 0.f;
+            v.z = (tl + 2 >= 0 && tl + 2 < span) ? src[tl + 2] : 0.f;
+            v.w = (tl + 3 >= 0 && tl + 3 < span) ? src[tl + 3] : 0.f;
+        }
+        acc[i][0] += v.x;
+        acc[i][1] += v.y;
+        acc[i][2] += v.z;
+        acc[i][3] += v.w;
+    }
+}
+
+// One warp per active pixel.  The pixel's contributing entries -- every active block
+// whose output footprint covers it, in (by, bx, bt) order -- are listed once in shared
+// memory; then the warp sweeps the window 512 ticks per step, summing per tick, in
+// list order, the entries that overlap the step (a fixed order: deterministic, no
+// atomics), and writes every tick of the row (zeros where no block contributes).
+// Optional FP64 accumulation (compensated mode).  A pixel with more than PXW_MAXE
+// entries reads the block map per step instead, in the same order.
 template <bool COMP>
 __global__ void __launch_bounds__(PXW_THREADS) k_px_wave(const int32_t *__restrict__ pixel_ids,
                                                          const int32_t *__restrict__ n_pixels_dev,
                                                          const int32_t *__restrict__ slot_of,
                                                          const float *__restrict__ out, GatherConst c,
                                                          float *__restrict__ wave) {
-    __shared__ int s_slot[PXW_WARPS][PXW_COLS][PXW_MAX_NBT];
+    using Acc = typename std::conditional<COMP, double, float>::type;
+    __shared__ PxEntry s_e[PXW_WARPS][PXW_MAXE];
     const int np = n_pixels_dev[0];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int nwarps = (gridDim.x * blockDim.x) >> 5;
     const int span = c.bt + c.nr - 1;      // meaningful ticks of a block's output
-    const bool cached = c.nbt <= PXW_MAX_NBT;
+    PxEntry *E = s_e[warp];
     for (int row = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; row < np; row += nwarps) {
         const int pid = pixel_ids[row];
         const int x = pid % c.npx_x, y = pid / c.npx_x;
@@ -158,56 +201,57 @@ __global__ void __launch_bounds__(PXW_THREADS) k_px_wave(const int32_t *__restri
         const int ev = y / c.npy_e;
         const int by_lo = max(ev * c.nby_e, floordiv(y - c.bp - c.R, c.bp) + 1);
         const int by_hi = min((ev + 1) * c.nby_e - 1, floordiv(y + c.R, c.bp));
-        const int nbxc = bx_hi - bx_lo + 1;
-        const int ncol = (by_hi - by_lo + 1) * nbxc;
-        // this pixel's block slots per (by, bx) column and time block, read once
+        // list the entries (ballot compaction over time blocks, columns in order)
         __syncwarp();
-        if (cached && ncol <= PXW_COLS) {
-            for (int k = lane; k < ncol * c.nbt; k += 32) {
-                const int col = k / c.nbt, bt = k - col * c.nbt;
-                const int by = by_lo + col / nbxc, bx = bx_lo + col % nbxc;
-                s_slot[warp][col][bt] = slot_of[((int64_t)by * c.nbx + bx) * c.nbt + bt];
+        int ne = 0;
+        for (int by = by_lo; by <= by_hi; ++by)
+            for (int bx = bx_lo; bx <= bx_hi; ++bx) {
+                const int uy = y - by * c.bp + c.R, ux = x - bx * c.bp + c.R;
+                for (int b0 = 0; b0 < c.nbt; b0 += 32) {
+                    const int bt = b0 + lane;
+                    const int slot = bt < c.nbt ? slot_of[((int64_t)by * c.nbx + bx) * c.nbt + bt] : -1;
+                    const unsigned bal = __ballot_sync(0xffffffffu, slot >= 0);
+                    if (slot >= 0) {
+                        const int idx = ne + __popc(bal & ((1u << lane) - 1u));
+                        if (idx < PXW_MAXE) E[idx] = {(((long long)slot * LP + uy) * LP + ux) * c.lt, bt * c.bt};
+                    }
+                    ne += __popc(bal);
+                }
             }
-        }
         __syncwarp();
         float *dst = wave + (size_t)row * c.nt;
-        for (int T0 = 0; T0 < c.nt; T0 += 128) {
-            const int t = T0 + 4 * lane;
-            double ad[4] = {0, 0, 0, 0};
-            float af[4] = {0, 0, 0, 0};
-            // blocks whose output range [bt*BT, bt*BT + span) meets [T0, T0 + 128)
-            const int bt_lo = max(0, floordiv(T0 - span, c.bt) + 1);
-            const int bt_hi = min(c.nbt - 1, floordiv(T0 + 127, c.bt));
-            for (int by = by_lo; by <= by_hi; ++by)
-                for (int bx = bx_lo; bx <= bx_hi; ++bx)
-                    for (int bt = bt_lo; bt <= bt_hi; ++bt) {
-                        const int col = (by - by_lo) * nbxc + (bx - bx_lo);
-                        const int slot = (cached && ncol <= PXW_COLS) ? s_slot[warp][col][bt]
-                                                                      : slot_of[((int64_t)by * c.nbx + bx) * c.nbt + bt];
-                        if (slot < 0) continue;
+        for (int T0 = 0; T0 < c.nt; T0 += PXW_CHUNK) {
+            Acc acc[4][4];
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+#pragma unroll
+                for (int e = 0; e < 4; ++e) acc[i][e] = 0;
+            if (ne <= PXW_MAXE) {
+                for (int k = 0; k < ne; ++k) {
+                    const PxEntry en = E[k];
+                    if (en.t0 >= T0 + PXW_CHUNK || en.t0 + span <= T0) continue;
+                    px_accumulate(out, en.off, en.t0, T0, lane, span, acc);
+                }
+            } else {
+                const int bt_lo = max(0, floordiv(T0 - span, c.bt) + 1);
+                const int bt_hi = min(c.nbt - 1, floordiv(T0 + PXW_CHUNK - 1, c.bt));
+                for (int by = by_lo; by <= by_hi; ++by)
+                    for (int bx = bx_lo; bx <= bx_hi; ++bx) {
                         const int uy = y - by * c.bp + c.R, ux = x - bx * c.bp + c.R;
-                        const int tl = t - bt * c.bt;     // multiple of 4
-                        if (tl + 3 < 0 || tl >= span) continue;
-                        const float *src = out + (((size_t)slot * LP + uy) * LP + ux) * c.lt;
-                        float4 v;
-                        if (tl >= 0 && tl + 3 < span) {
-                            v = *reinterpret_cast<const float4 *>(src + tl);
-                        } else {
-                            v.x = (tl >= 0 && tl < span) ? src[tl] : 0.f;
-                            v.y = (tl + 1 >= 0 && tl + 1 < span) ? src[tl + 1] : 0.f;
-                            v.z = (tl + 2 >= 0 && tl + 2 < span) ? src[tl + 2] : 0.f;
-                            v.w = (tl + 3 >= 0 && tl + 3 < span) ? src[tl + 3] : 0.f;
-                        }
-                        if (COMP) {
-                            ad[0] += v.x; ad[1] += v.y; ad[2] += v.z; ad[3] += v.w;
-                        } else {
-                            af[0] += v.x; af[1] += v.y; af[2] += v.z; af[3] += v.w;
+                        for (int bt = bt_lo; bt <= bt_hi; ++bt) {
+                            const int slot = slot_of[((int64_t)by * c.nbx + bx) * c.nbt + bt];
+                            if (slot < 0) continue;
+                            px_accumulate(out, (((long long)slot * LP + uy) * LP + ux) * c.lt, bt * c.bt, T0, lane,
+                                          span, acc);
                         }
                     }
-            if (t < c.nt) {
-                float4 o = COMP ? make_float4((float)ad[0], (float)ad[1], (float)ad[2], (float)ad[3])
-                                : make_float4(af[0], af[1], af[2], af[3]);
-                *reinterpret_cast<float4 *>(dst + t) = o;
+            }
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                const int t = T0 + 128 * i + 4 * lane;
+                if (t < c.nt)
+                    *reinterpret_cast<float4 *>(dst + t) =
+                        make_float4((float)acc[i][0], (float)acc[i][1], (float)acc[i][2], (float)acc[i][3]);
             }
         }
     }

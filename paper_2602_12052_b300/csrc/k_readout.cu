@@ -1,8 +1,9 @@
 // a6. Trigger-reset readout (Sec. II-E, Fig. readout: LArPix trigger-reset scheme).
 //
-// One warp per pixel walks the waveform 128 ticks at a time (4 per lane): lane and
-// warp scans give the running charge inside the step, the charge carried between
-// steps is added to it; all in FP32 (the rounding of a running sum over a 6400-tick
+// One warp per pixel walks the waveform 512 ticks at a time (the loads of a step in
+// flight together), scanning it 128 ticks (4 per lane) at a time: lane and warp scans
+// give the running charge inside the sub-step, the charge carried between sub-steps
+// is added to it; all in FP32 (the rounding of a running sum over a 6400-tick
 // window is a few 1e-7 of the charge, far inside the 1e-4 threshold band in which
 // the FP64 oracle's hit lists may differ).  Clock edges k >= start with
 // C(k) >= threshold are found with a ballot; the charge is sampled at k + hold, the
@@ -25,65 +26,85 @@ struct RoConst {
     float thr;
 };
 
-// Walk one pixel 128 ticks per step (4 consecutive ticks per lane); for each hit
-// call sink(index, tick, charge).  Returns the hit count.
+// Walk one pixel 512 ticks per step: the step's loads are issued together (4 ticks per
+// lane in each of 4 sub-steps of 128 ticks), then the sub-steps are scanned in tick
+// order.  For each hit call sink(index, tick, charge).  Returns the hit count.
 template <typename Sink>
 __device__ int walk_pixel(const float *__restrict__ I, const RoConst &c, int lane, Sink sink) {
     int nh = 0;
     int pos = 0;              // first tick of the current step
-    float base = 0.f;         // charge integrated before pos since the last restart
+    float base = 0.f;         // charge integrated before the sub-step since the last restart
     int mode = 0;             // 0: looking for a trigger; 1: waiting for the sample tick
     int ts = 0;
     while (pos < c.nt) {
-        const int t0 = pos + 4 * lane;
-        float v[4];
+        float v[4][4];
 #pragma unroll
-        for (int e = 0; e < 4; ++e) v[e] = (t0 + e < c.nt) ? __ldg(I + t0 + e) : 0.f;
-        v[1] += v[0];
-        v[2] += v[1];
-        v[3] += v[2];
-        float x = v[3];
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const float u = __shfl_up_sync(0xffffffffu, x, o);
-            if (lane >= o) x += u;
-        }
-        const float excl = x - v[3];
-        float C[4];
-#pragma unroll
-        for (int e = 0; e < 4; ++e) C[e] = base + (excl + v[e]);
-        if (mode == 0) {
-            int first = 4;
-            int ph = t0 % c.clock;                      // clock phase of tick t0
+        for (int i = 0; i < 4; ++i)
 #pragma unroll
             for (int e = 0; e < 4; ++e) {
-                if (first == 4 && ph == 0 && t0 + e < c.nt && C[e] >= c.thr) first = e;
-                ph = ph + 1 == c.clock ? 0 : ph + 1;
+                const int t = pos + 128 * i + 4 * lane + e;
+                v[i][e] = t < c.nt ? __ldg(I + t) : 0.f;
             }
-            const unsigned bal = __ballot_sync(0xffffffffu, first < 4);
-            if (bal) {
-                const int src = __ffs(bal) - 1;
-                const int fe = __shfl_sync(0xffffffffu, first, src);
-                const int k = pos + 4 * src + fe;
-                ts = k + c.hold;
-                if (ts >= c.nt) break;                  // sample falls outside the window
-                mode = 1;
+        bool restart = false;
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            const int spos = pos + 128 * i;
+            if (spos >= c.nt) break;
+            const int t0 = spos + 4 * lane;
+            // an all-zero sub-step leaves the running charge at `base`: with no trigger
+            // possible (idle and base below threshold) or the sample tick beyond it,
+            // nothing changes, so it is skipped (the scan below would give C = base)
+            const bool nz = (v[i][0] != 0.f) | (v[i][1] != 0.f) | (v[i][2] != 0.f) | (v[i][3] != 0.f);
+            if (!__any_sync(0xffffffffu, nz) && ((mode == 0 && !(base >= c.thr)) || (mode == 1 && ts >= spos + 128)))
+                continue;
+            float w[4] = {v[i][0], v[i][1], v[i][2], v[i][3]};
+            w[1] += w[0];
+            w[2] += w[1];
+            w[3] += w[2];
+            float x = w[3];
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const float u = __shfl_up_sync(0xffffffffu, x, o);
+                if (lane >= o) x += u;
             }
+            const float excl = x - w[3];
+            float C[4];
+#pragma unroll
+            for (int e = 0; e < 4; ++e) C[e] = base + (excl + w[e]);
+            if (mode == 0) {
+                int first = 4;
+                int ph = t0 % c.clock;                      // clock phase of tick t0
+#pragma unroll
+                for (int e = 0; e < 4; ++e) {
+                    if (first == 4 && ph == 0 && t0 + e < c.nt && C[e] >= c.thr) first = e;
+                    ph = ph + 1 == c.clock ? 0 : ph + 1;
+                }
+                const unsigned bal = __ballot_sync(0xffffffffu, first < 4);
+                if (bal) {
+                    const int src = __ffs(bal) - 1;
+                    const int fe = __shfl_sync(0xffffffffu, first, src);
+                    const int k = spos + 4 * src + fe;
+                    ts = k + c.hold;
+                    if (ts >= c.nt) return nh;              // sample falls outside the window
+                    mode = 1;
+                }
+            }
+            if (mode == 1 && ts < spos + 128) {
+                const int off = ts - spos;
+                const int e = off & 3;
+                const float mine = e == 0 ? C[0] : e == 1 ? C[1] : e == 2 ? C[2] : C[3];
+                const float Cs = __shfl_sync(0xffffffffu, mine, off >> 2);
+                sink(nh, ts, Cs);
+                ++nh;
+                pos = ts + c.reset + 1;
+                base = 0.f;
+                mode = 0;
+                restart = true;
+                break;
+            }
+            base = __shfl_sync(0xffffffffu, C[3], 31);
         }
-        if (mode == 1 && ts < pos + 128) {
-            const int off = ts - pos;
-            const int e = off & 3;
-            const float mine = e == 0 ? C[0] : e == 1 ? C[1] : e == 2 ? C[2] : C[3];
-            const float Cs = __shfl_sync(0xffffffffu, mine, off >> 2);
-            sink(nh, ts, Cs);
-            ++nh;
-            pos = ts + c.reset + 1;
-            base = 0.f;
-            mode = 0;
-            continue;
-        }
-        base = __shfl_sync(0xffffffffu, C[3], 31);
-        pos += 128;
+        if (!restart) pos += 512;
     }
     return nh;
 }
