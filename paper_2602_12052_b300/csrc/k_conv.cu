@@ -43,13 +43,22 @@ constexpr int SPEC_TMEM_COLS = 256;         // 4 warps per lane quarter x 64 col
 constexpr int PG = 5;                       // channel pairs per stage A / stage B round
 constexpr int ZT_ROW = 9;                   // padded px row of the bin-major transpose
 constexpr int ZT_BIN = 8 * ZT_ROW + 1;      // [py][px] for py, px < 8, odd stride
-// Bin order inside the transpose buffer.  Stage A lane l stores bins k2 = a + 2 b
+// Bin order inside the stage A buffer.  Stage A lane l stores bins k2 = a + 2 b
 // with b = bitrev5(l): the 16 lanes of a half warp hold the even b, the other 16
-// the odd ones.  k2 = 4 c + 2 d + a goes to slot 32 a + 16 d + c so that each half
-// warp's 16 stores land on 16 distinct 8-byte bank pairs (odd bin stride).
-__device__ __forceinline__ int zt_slot(int k2) { return ((k2 & 1) << 5) | (((k2 >> 1) & 1) << 4) | (k2 >> 2); }
-constexpr int TB_ROW = 9;                   // per-warp transpose rows [kx][py]
-constexpr int TB_BIN = LP * TB_ROW;
+// the odd ones.  k2 = 4 c + 2 d + a goes to slot 32 a + 16 d + (c ^ 8 a): each half
+// warp's 16 stores land on 16 distinct 8-byte bank pairs (odd bin stride), and the
+// row stage's two bins k2, k2 + 1 (k2 even) sit 8 bank pairs apart, so its 16
+// distinct row addresses per warp are conflict-free too.
+__device__ __forceinline__ int zt_slot(int k2) {
+    const int a = k2 & 1;
+    return (a << 5) | (((k2 >> 1) & 1) << 4) | ((k2 >> 2) ^ (a << 3));
+}
+// Per-warp transpose of the row-stage outputs: (kx = 2 r + h, py) at 17 r + 8 h + py, so
+// that the row stage's stores (lanes py, h at fixed r) and the column stage's loads
+// (lanes kx at fixed py) both fall on 16 distinct 8-byte bank pairs per half warp
+// with compile-time offsets; the bins of a warp are 136 entries apart.
+constexpr int TB_R = 17;
+constexpr int TB_BIN = 8 * TB_R;
 
 constexpr int EP_ROW = LP + 1;              // epilogue transpose [cy][kx + pad]
 constexpr int EP_BIN = LP * EP_ROW;
@@ -236,24 +245,29 @@ __global__ void __launch_bounds__(SPEC_THREADS, 1)
 #pragma unroll
                         for (int x = 0; x < 8; ++x) {
                             const float2 z = zrow[x];
-                            const float wr = h ? w32c(2 * x) : 1.f, wi = h ? w32s(2 * x) : 0.f;
-                            v[x] = make_float2(z.x * wr - z.y * wi, z.x * wi + z.y * wr);
+                            if (x == 0) {
+                                v[x] = z;                                  // W_16^0
+                            } else if (x == 4) {
+                                v[x] = h ? make_float2(z.y, -z.x) : z;     // W_16^4 = -i
+                            } else {
+                                const float wr = h ? w32c(2 * x) : 1.f, wi = h ? w32s(2 * x) : 0.f;
+                                v[x] = make_float2(z.x * wr - z.y * wi, z.x * wi + z.y * wr);
+                            }
                         }
                         fft_reg_dif_c<8, false>(v);
-                        float2 *dst = tb + b * TB_BIN + py;
+                        float2 *dst = tb + b * TB_BIN + 8 * h + py;
 #pragma unroll
-                        for (int k = 0; k < 8; ++k) dst[(2 * bitrev<8>(k) + h) * TB_ROW] = v[k];
+                        for (int k = 0; k < 8; ++k) dst[TB_R * bitrev<8>(k)] = v[k];   // kx = 2 bitrev3(k) + h
                     }
                     __syncwarp();
                     // y stage: lane = (b, kx): 16-point FFT of 8 nonzero inputs
                     {
-                        const float2 *src = tb + b * TB_BIN + kx * TB_ROW;
+                        const float2 *src = tb + b * TB_BIN + TB_R * (kx >> 1) + 8 * (kx & 1);
                         float2 e[8], o[8];
 #pragma unroll
                         for (int y = 0; y < 8; ++y) {
                             e[y] = src[y];
-                            const float wr = w32c(2 * y), wi = w32s(2 * y);     // W_16^y
-                            o[y] = make_float2(e[y].x * wr - e[y].y * wi, e[y].x * wi + e[y].y * wr);
+                            o[y] = mul_w16(e[y], y);                       // e W_16^y
                         }
                         fft_reg_dif_c<8, false>(e);
                         fft_reg_dif_c<8, false>(o);

@@ -264,6 +264,15 @@ __device__ __forceinline__ float2 fft32_lanes(float2 v, const float2 *__restrict
     return v;
 }
 
+// x * W_16^m (forward), m a compile-time constant after unrolling: the rotations by
+// 0 and -i are exact swaps, the others one complex product
+__device__ __forceinline__ float2 mul_w16(float2 x, int m) {
+    if (m == 0) return x;
+    if (m == 4) return make_float2(x.y, -x.x);
+    const float wr = w32c(2 * m), wi = w32s(2 * m);
+    return make_float2(x.x * wr - x.y * wi, x.x * wi + x.y * wr);
+}
+
 // ---------------------------------------------------------------- tensor memory (TMEM)
 // Allocation by one full warp; the address (lane << 16 | column) lands in shared memory.
 __device__ __forceinline__ void tmem_alloc(uint32_t *smem_dst, uint32_t ncols) {
