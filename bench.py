@@ -80,6 +80,10 @@ def _args():
                     help="step: one event (default); batched: 64 uneven events, autotuned, CUDA graph; "
                          "adjoint: forward + backward; spill: 35 planes in sequence")
     ap.add_argument("--events", type=int, default=64)
+    ap.add_argument("--readout-mode", type=int, default=0, choices=[0, 1, 2],
+                    help="0: trigger-reset (default); 1: successive digitisations without resets "
+                         "(--n-samples per trigger); 2: fixed-charge integration")
+    ap.add_argument("--n-samples", type=int, default=3, help="digitisations per trigger in readout mode 1")
     ap.add_argument("--conv-mode", type=int, default=0, choices=[0, 1, 2],
                     help="0: FP32 FFT convolution (default); 1: time DFT as a tcgen05 GEMM in TF32; "
                          "2: the same in split TF32 (three products)")
@@ -538,6 +542,8 @@ def main():
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     lib_build.build()
     cfg = synth.get_config(args.config)
+    if args.readout_mode:
+        cfg = cfg.with_(readout_mode=args.readout_mode, n_samples=args.n_samples if args.readout_mode == 1 else 1)
     dep = synth.make_deposits(cfg, seed=cfg.seed + 7919 * rank)
     resp = synth.make_response(cfg)
     n = len(dep["x"])
@@ -682,7 +688,9 @@ def main():
                                     f"{cfg.bp}x{cfg.bp}x{cfg.bt} blocks, FFT 16x16x{cfg.lt}, MPCP"
                                     + {0: ", effective charge written for covered columns only",
                                        1: ", time DFT as a TF32 tcgen05 GEMM (tolerance 1e-4)",
-                                       2: ", time DFT as a split-TF32 tcgen05 GEMM"}[args.conv_mode]),
+                                       2: ", time DFT as a split-TF32 tcgen05 GEMM"}[args.conv_mode]
+                                    + {0: "", 1: f", readout: {cfg.n_samples} successive digitisations per trigger",
+                                       2: ", readout: fixed-charge quanta"}[args.readout_mode]),
                        "deposits": n, "active_blocks": nb, "active_pixels": npix, "hits": nh,
                        "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
                        "l2": "flushed between timed steps (256 MB write, outside the step events)"},

@@ -101,12 +101,18 @@ typedef struct {
                                    is written (required by conv_mode 1, 2). */
 } tred_params;
 
-/* Trigger-reset readout (Sec. II-E). */
+/* Pixel readout (Sec. II-E): the trigger-reset scheme and the two variants the
+ * section names.  A zero-initialised mode / n_samples selects trigger-reset. */
 typedef struct {
-    float threshold_e;       /* trigger threshold on the integrated charge */
+    float threshold_e;       /* trigger threshold on the integrated charge; in mode 2 the
+                                charge quantum */
     int32_t clock_ticks;     /* clock period: triggers are tested at multiples of it */
-    int32_t hold_ticks;      /* charge is sampled hold_ticks after the trigger edge */
-    int32_t reset_ticks;     /* dead time after the sample */
+    int32_t hold_ticks;      /* charge is sampled hold_ticks after the trigger edge (mode 1:
+                                spacing of the successive samples) */
+    int32_t reset_ticks;     /* dead time after the (last) sample */
+    int32_t mode;            /* 0 trigger-reset, 1 successive digitisations without
+                                intervening resets, 2 fixed-charge integration */
+    int32_t n_samples;       /* mode 1: digitisations per trigger (>= 1; 1 is mode 0) */
 } tred_readout_params;
 
 /* Drifted deposits, structure of arrays, caller-owned device arrays of length
@@ -262,10 +268,21 @@ int32_t tred_gather_pixels(tred_handle *h, const int32_t *block_ids,
                            int32_t *pixel_ids, float *waveforms, int32_t *n_pixels_dev,
                            void *stream);
 
-/* a6. Trigger-reset readout (Sec. II-E, Fig. readout).  C = running sum of the current
- * since the end of the last reset; at clock edges k >= start, if C(k) >= threshold
- * a hit (pixel, k + hold, C(k + hold)) is emitted when k + hold < nt and C restarts
- * at k + hold + reset + 1.  Hits sorted by (pixel, tick); n_hits_dev[0] = count. */
+/* a6. Pixel readout (Sec. II-E, Fig. readout), per pixel over its waveform row.
+ * mode 0, trigger-reset: C = running sum of the current since the end of the last
+ *   reset; at clock edges k >= start, if C(k) >= threshold a hit (pixel, k + hold,
+ *   C(k + hold)) is emitted when k + hold < nt and C restarts at k + hold + reset + 1.
+ * mode 1, successive digitisations: a trigger at edge k gives n_samples hits
+ *   (pixel, k + m hold, C(k + m hold)), m = 1..n_samples, with C not reset between
+ *   them; C restarts at k + n_samples hold + reset + 1.  A sample at or beyond nt
+ *   ends the pixel.
+ * mode 2, fixed-charge integration: C = running sum from tick 0, never reset; at
+ *   each clock edge k with C(k) >= threshold a hit (pixel, k, threshold) is emitted
+ *   and the quantum is taken from C (no charge is lost).
+ * All in FP32 running sums.  Hits sorted by (pixel, tick); n_hits_dev[0] = count
+ * (capped at max_hits: TRED_ST_HIT_OVERFLOW in the status word beyond it).
+ * TRED_ERR_INVALID_ARG for a null pointer, clock_ticks < 1, hold_ticks or
+ * reset_ticks < 0, an unknown mode, or mode 1 with n_samples < 1 or hold_ticks < 1. */
 int32_t tred_readout(tred_handle *h, const tred_readout_params *rp,
                      const int32_t *pixel_ids, const float *waveforms,
                      const int32_t *n_pixels_dev, int32_t *hit_pixel, int32_t *hit_tick,

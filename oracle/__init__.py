@@ -88,8 +88,8 @@ def _setup(L):
     L.orc_active_pixels.argtypes = [_P, ctypes.c_int, _P, ctypes.c_int, _P]
     L.orc_active_pixels.restype = ctypes.c_int
     L.orc_readout.argtypes = [ctypes.c_int, ctypes.c_int, _P, _P, ctypes.c_double,
-                              ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_double,
-                              _P, _P, _P, ctypes.c_long, _P]
+                              ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                              ctypes.c_double, _P, _P, _P, ctypes.c_long, _P]
     L.orc_readout.restype = ctypes.c_long
     L.orc_num_threads.restype = ctypes.c_int
     L.orc_weights_gl_grad.argtypes = [ctypes.c_int, _P, _P, ctypes.c_double, ctypes.c_double,
@@ -222,21 +222,28 @@ def active_pixels(p: Params, blocks, kp: int) -> np.ndarray:
 
 
 def readout(pixel_ids, wave: np.ndarray, threshold: float, clock: int, hold: int,
-            reset: int, tol: float | None = None):
-    """Trigger-reset readout (Sec. II-E).  Returns (pixel, tick, charge) arrays sorted
-    by (pixel, tick) and, per pixel, the first edge whose charge is within ``tol``
-    (default 1e-4 * threshold) of the threshold, or -1."""
+            reset: int, tol: float | None = None, mode: int = 0, n_samples: int = 1):
+    """Pixel readout (Sec. II-E): mode 0 trigger-reset, mode 1 ``n_samples`` successive
+    digitisations per trigger without intervening resets, mode 2 fixed-charge
+    integration (quanta of ``threshold``).  Returns (pixel, tick, charge) arrays sorted
+    by (pixel, tick) and, per pixel, the first tested edge whose charge is within
+    ``tol`` (default 1e-4 * threshold) of the threshold, or -1."""
     pixel_ids = np.ascontiguousarray(pixel_ids, dtype=np.int32)
     wave = np.ascontiguousarray(wave, dtype=np.float64)
     npix, nt = wave.shape
     tol = 1e-4 * threshold if tol is None else tol
-    cap = max(1, npix * (nt // max(1, hold + reset + 1) + 1))
+    if mode == 2:
+        cap = max(1, npix * (nt // max(1, clock) + 1))
+    else:
+        cap = max(1, npix * n_samples * (nt // max(1, hold + reset + 1) + 1))
     hp = np.zeros(cap, np.int32)
     ht = np.zeros(cap, np.int32)
     hc = np.zeros(cap, np.float64)
     amb = np.zeros(npix, np.int32)
     m = lib().orc_readout(npix, nt, _ptr(pixel_ids), _ptr(wave), float(threshold), clock,
-                          hold, reset, float(tol), _ptr(hp), _ptr(ht), _ptr(hc), cap, _ptr(amb))
+                          hold, reset, int(mode), int(n_samples), float(tol), _ptr(hp), _ptr(ht),
+                          _ptr(hc), cap, _ptr(amb))
+    assert m <= cap
     return hp[:m].copy(), ht[:m].copy(), hc[:m].copy(), amb
 
 

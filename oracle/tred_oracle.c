@@ -480,29 +480,59 @@ int orc_active_pixels(const orc_params *p, int nb, const int32_t *blocks, int kp
 }
 
 /* ------------------------------------------------------------------------- */
-/* Trigger-reset readout (Sec. II-E, Fig. readout).  Per pixel, the charge C is the   */
-/* running sum of the current since the end of the last reset.  At each clock   */
-/* edge k (k a multiple of clock) with k >= start: if C(k) >= threshold the     */
-/* channel triggers; the charge is sampled at k + hold and a hit               */
-/* (pixel, k + hold, C(k + hold)) is emitted if k + hold < nt; then C restarts  */
-/* at k + hold + reset + 1.  Also reports, per pixel, the first edge whose C    */
+/* Pixel readout (Sec. II-E), three schemes.  Per pixel the charge C is the running  */
+/* sum of the current.  Also reports, per pixel, the first tested edge whose C  */
 /* lies within tol of the threshold (-1 if none): hit lists may legitimately    */
-/* differ from that edge on.                                                    */
-/* Returns the number of hits (written up to cap).                              */
+/* differ from that edge on.  Returns the number of hits (written up to cap).   */
+/*                                                                              */
+/* mode 0, trigger-reset (Fig. readout): C counts from the end of the last      */
+/*   reset.  At each clock edge k (k a multiple of clock) with k >= start: if    */
+/*   C(k) >= threshold the channel triggers; the charge is sampled at k + hold   */
+/*   and a hit (pixel, k + hold, C(k + hold)) is emitted if k + hold < nt; then  */
+/*   C restarts at k + hold + reset + 1.                                        */
+/* mode 1, successive digitisations without intervening resets: a trigger at   */
+/*   edge k is followed by nsamp samples at k + m hold, m = 1..nsamp, each a hit */
+/*   (pixel, k + m hold, C(k + m hold)) with C not reset between them; after    */
+/*   the last, C restarts at k + nsamp hold + reset + 1.  A sample tick at or    */
+/*   beyond nt ends the pixel.  nsamp = 1 is mode 0.                            */
+/* mode 2, fixed-charge integration: C counts from tick 0 and is never reset;   */
+/*   at each clock edge k with C(k) >= threshold a hit (pixel, k, threshold) is  */
+/*   emitted and one quantum (the threshold) is taken from C, so no charge is    */
+/*   lost: hits x threshold + C(nt - 1) is the total charge.                    */
 /* ------------------------------------------------------------------------- */
 long orc_readout(int npix, int nt, const int32_t *pixel_ids, const double *wave,
-                 double thr, int clock, int hold, int reset, double tol,
+                 double thr, int clock, int hold, int reset, int mode, int nsamp, double tol,
                  int32_t *hit_pixel, int32_t *hit_tick, double *hit_charge, long cap,
                  int32_t *first_ambiguous)
 {
     long m = 0;
+#define ORC_EMIT(P, T, Q)                                                         \
+    do {                                                                          \
+        if (m < cap) { hit_pixel[m] = (P); hit_tick[m] = (T); hit_charge[m] = (Q); } \
+        ++m;                                                                      \
+    } while (0)
     for (int ip = 0; ip < npix; ++ip) {
         const double *I = wave + (size_t)ip * nt;
         first_ambiguous[ip] = -1;
+        if (mode == 2) {
+            double C = 0.0;
+            int t = 0;
+            for (int k = 0; k < nt; k += clock) {
+                while (t <= k) C += I[t++];
+                if (first_ambiguous[ip] < 0 && fabs(C - thr) <= tol) first_ambiguous[ip] = k;
+                if (C >= thr) {
+                    ORC_EMIT(pixel_ids[ip], k, thr);
+                    C -= thr;
+                }
+            }
+            continue;
+        }
+        const int ns = mode == 1 ? nsamp : 1;
         int start = 0;
         double C = 0.0;
         int t = 0;           /* next tick to add into C */
-        while (1) {
+        int done = 0;
+        while (!done) {
             int k = ((start + clock - 1) / clock) * clock;   /* first edge >= start */
             int fired = 0;
             for (; k < nt; k += clock) {
@@ -511,21 +541,21 @@ long orc_readout(int npix, int nt, const int32_t *pixel_ids, const double *wave,
                 if (C >= thr) { fired = 1; break; }
             }
             if (!fired) break;
-            int ts = k + hold;
-            if (ts >= nt) break;
-            while (t <= ts) C += I[t++];
-            if (m < cap) {
-                hit_pixel[m] = pixel_ids[ip];
-                hit_tick[m] = ts;
-                hit_charge[m] = C;
+            int ts = k;
+            for (int s = 1; s <= ns; ++s) {
+                ts = k + s * hold;
+                if (ts >= nt) { done = 1; break; }
+                while (t <= ts) C += I[t++];
+                ORC_EMIT(pixel_ids[ip], ts, C);
             }
-            ++m;
+            if (done) break;
             start = ts + reset + 1;
             C = 0.0;
             t = start;
             if (start >= nt) break;
         }
     }
+#undef ORC_EMIT
     return m;
 }
 

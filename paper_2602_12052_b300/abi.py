@@ -56,7 +56,8 @@ class Params(ctypes.Structure):
 
 class ReadoutParams(ctypes.Structure):
     _fields_ = [("threshold_e", ctypes.c_float), ("clock_ticks", ctypes.c_int32),
-                ("hold_ticks", ctypes.c_int32), ("reset_ticks", ctypes.c_int32)]
+                ("hold_ticks", ctypes.c_int32), ("reset_ticks", ctypes.c_int32),
+                ("mode", ctypes.c_int32), ("n_samples", ctypes.c_int32)]
 
 
 DEPOSIT_FIELDS = ["cell_x", "cell_y", "cell_t", "frac_x", "frac_y", "frac_t", "sigma_x", "sigma_y",

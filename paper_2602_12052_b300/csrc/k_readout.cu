@@ -1,4 +1,6 @@
-// a6. Trigger-reset readout (Sec. II-E, Fig. readout: LArPix trigger-reset scheme).
+// a6. Pixel readout (Sec. II-E, Fig. readout: LArPix trigger-reset scheme, and the
+// two variants the section names: successive digitisations without intervening
+// resets, and fixed-charge integration).
 //
 // One warp per pixel walks the waveform 512 ticks at a time (the loads of a step in
 // flight together), scanning it 128 ticks (4 per lane) at a time: lane and warp scans
@@ -8,7 +10,10 @@
 // the FP64 oracle's hit lists may differ).  Clock edges k >= start with
 // C(k) >= threshold are found with a ballot; the charge is sampled at k + hold, the
 // hit (pixel, k + hold, C) is emitted, and integration restarts at
-// k + hold + reset + 1.
+// k + hold + reset + 1.  Successive digitisations take n_samples samples hold apart
+// before that restart; fixed-charge integration never restarts and, sub-step by
+// sub-step, emits one quantum at every edge whose charge less the quanta already
+// taken reaches the threshold.
 //
 //   k_ro_count   count hits per pixel; cache the first HIT_TMP hits
 //   (scan)       hit offsets and the total
@@ -22,20 +27,22 @@ int launch_scan_small(tred_handle *h, int64_t n, int32_t *part, int32_t cap, int
                       int flag, int word, cudaStream_t s);
 
 struct RoConst {
-    int nt, clock, hold, reset;
+    int nt, clock, hold, reset, nsamp;
     float thr;
 };
 
 // Walk one pixel 512 ticks per step: the step's loads are issued together (4 ticks per
 // lane in each of 4 sub-steps of 128 ticks), then the sub-steps are scanned in tick
 // order.  For each hit call sink(index, tick, charge).  Returns the hit count.
-template <typename Sink>
+// RM: readout mode (0 trigger-reset, 1 successive digitisations, 2 fixed charge).
+template <int RM, typename Sink>
 __device__ int walk_pixel(const float *__restrict__ I, const RoConst &c, int lane, Sink sink) {
     int nh = 0;
     int pos = 0;              // first tick of the current step
-    float base = 0.f;         // charge integrated before the sub-step since the last restart
-    int mode = 0;             // 0: looking for a trigger; 1: waiting for the sample tick
-    int ts = 0;
+    float base = 0.f;         // charge integrated before the sub-step (since the last restart)
+    int state = 0;            // 0: looking for a trigger; 1: waiting for the sample tick
+    int ts = 0;               // next sample tick
+    int left = 0;             // samples still to take after ts (mode 1)
     while (pos < c.nt) {
         float v[4][4];
 #pragma unroll
@@ -55,7 +62,7 @@ __device__ int walk_pixel(const float *__restrict__ I, const RoConst &c, int lan
             // possible (idle and base below threshold) or the sample tick beyond it,
             // nothing changes, so it is skipped (the scan below would give C = base)
             const bool nz = (v[i][0] != 0.f) | (v[i][1] != 0.f) | (v[i][2] != 0.f) | (v[i][3] != 0.f);
-            if (!__any_sync(0xffffffffu, nz) && ((mode == 0 && !(base >= c.thr)) || (mode == 1 && ts >= spos + 128)))
+            if (!__any_sync(0xffffffffu, nz) && ((state == 0 && !(base >= c.thr)) || (state == 1 && ts >= spos + 128)))
                 continue;
             float w[4] = {v[i][0], v[i][1], v[i][2], v[i][3]};
             w[1] += w[0];
@@ -71,7 +78,32 @@ __device__ int walk_pixel(const float *__restrict__ I, const RoConst &c, int lan
             float C[4];
 #pragma unroll
             for (int e = 0; e < 4; ++e) C[e] = base + (excl + w[e]);
-            if (mode == 0) {
+            if (RM == 2) {
+                // fixed charge: every edge with C >= threshold gives one quantum, taken
+                // from C; the edges are visited in order, quanta already taken subtracted
+                float sub = 0.f;
+                int from = spos;
+                for (;;) {
+                    int first = 4;
+                    int ph = t0 % c.clock;
+#pragma unroll
+                    for (int e = 0; e < 4; ++e) {
+                        if (first == 4 && ph == 0 && t0 + e < c.nt && t0 + e >= from && C[e] - sub >= c.thr) first = e;
+                        ph = ph + 1 == c.clock ? 0 : ph + 1;
+                    }
+                    const unsigned bal = __ballot_sync(0xffffffffu, first < 4);
+                    if (!bal) break;
+                    const int src = __ffs(bal) - 1;
+                    const int k = spos + 4 * src + __shfl_sync(0xffffffffu, first, src);
+                    sink(nh, k, c.thr);
+                    ++nh;
+                    sub += c.thr;
+                    from = k + 1;
+                }
+                base = __shfl_sync(0xffffffffu, C[3], 31) - sub;
+                continue;
+            }
+            if (state == 0) {
                 int first = 4;
                 int ph = t0 % c.clock;                      // clock phase of tick t0
 #pragma unroll
@@ -86,22 +118,30 @@ __device__ int walk_pixel(const float *__restrict__ I, const RoConst &c, int lan
                     const int k = spos + 4 * src + fe;
                     ts = k + c.hold;
                     if (ts >= c.nt) return nh;              // sample falls outside the window
-                    mode = 1;
+                    left = RM == 1 ? c.nsamp - 1 : 0;
+                    state = 1;
                 }
             }
-            if (mode == 1 && ts < spos + 128) {
+            // the samples that fall in this sub-step (several in mode 1 when hold < 128)
+            while (state == 1 && ts < spos + 128) {
                 const int off = ts - spos;
                 const int e = off & 3;
                 const float mine = e == 0 ? C[0] : e == 1 ? C[1] : e == 2 ? C[2] : C[3];
                 const float Cs = __shfl_sync(0xffffffffu, mine, off >> 2);
                 sink(nh, ts, Cs);
                 ++nh;
+                if (left > 0) {                             // next digitisation, no reset
+                    --left;
+                    ts += c.hold;
+                    if (ts >= c.nt) return nh;
+                    continue;
+                }
                 pos = ts + c.reset + 1;
                 base = 0.f;
-                mode = 0;
+                state = 0;
                 restart = true;
-                break;
             }
+            if (restart) break;
             base = __shfl_sync(0xffffffffu, C[3], 31);
         }
         if (!restart) pos += 512;
@@ -109,6 +149,7 @@ __device__ int walk_pixel(const float *__restrict__ I, const RoConst &c, int lan
     return nh;
 }
 
+template <int RM>
 __global__ void __launch_bounds__(256) k_ro_count(const float *__restrict__ wave,
                                                   const int32_t *__restrict__ n_pixels_dev, RoConst c,
                                                   int32_t *__restrict__ cnt, int32_t *__restrict__ tmp_t,
@@ -118,7 +159,7 @@ __global__ void __launch_bounds__(256) k_ro_count(const float *__restrict__ wave
     const int nwarps = (gridDim.x * blockDim.x) >> 5;
     for (int row = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; row < np; row += nwarps) {
         const float *I = wave + (size_t)row * c.nt;
-        const int nh = walk_pixel(I, c, lane, [&](int k, int t, float q) {
+        const int nh = walk_pixel<RM>(I, c, lane, [&](int k, int t, float q) {
             if (lane == 0 && k < HIT_TMP) {
                 tmp_t[(size_t)row * HIT_TMP + k] = t;
                 tmp_c[(size_t)row * HIT_TMP + k] = q;
@@ -128,6 +169,7 @@ __global__ void __launch_bounds__(256) k_ro_count(const float *__restrict__ wave
     }
 }
 
+template <int RM>
 __global__ void __launch_bounds__(256) k_ro_emit(const float *__restrict__ wave,
                                                  const int32_t *__restrict__ pixel_ids,
                                                  const int32_t *__restrict__ n_pixels_dev, RoConst c,
@@ -149,7 +191,7 @@ __global__ void __launch_bounds__(256) k_ro_emit(const float *__restrict__ wave,
                 hc[o + lane] = tmp_c[(size_t)row * HIT_TMP + lane];
             }
         } else {
-            walk_pixel(wave + (size_t)row * c.nt, c, lane, [&](int k, int t, float q) {
+            walk_pixel<RM>(wave + (size_t)row * c.nt, c, lane, [&](int k, int t, float q) {
                 if (lane == 0 && o + k < max_hits) {
                     hp[o + k] = pid;
                     ht[o + k] = t;
@@ -164,16 +206,24 @@ int launch_readout(tred_handle *h, const tred_readout_params &rp, const int32_t 
                    const float *wave, const int32_t *n_pixels_dev, int32_t *hit_pixel,
                    int32_t *hit_tick, float *hit_charge, int32_t *n_hits_dev, int32_t max_hits,
                    cudaStream_t s) {
-    RoConst c{h->g.nt, rp.clock_ticks, rp.hold_ticks, rp.reset_ticks, rp.threshold_e};
+    RoConst c{h->g.nt, rp.clock_ticks, rp.hold_ticks, rp.reset_ticks, rp.mode == 1 ? rp.n_samples : 1, rp.threshold_e};
     const int sms = num_sms(h);
     int rc = check_cuda(h, cudaMemsetAsync(h->hit_cnt, 0, sizeof(int32_t) * ((size_t)h->max_pixels + 1), s),
                         "clear hit counts");
     if (rc) return rc;
-    k_ro_count<<<sms * 8, 256, 0, s>>>(wave, n_pixels_dev, c, h->hit_cnt, h->hit_tmp, h->hit_tmpc);
+    auto count = [&](auto kern) { kern<<<sms * 8, 256, 0, s>>>(wave, n_pixels_dev, c, h->hit_cnt, h->hit_tmp, h->hit_tmpc); };
+    if (rp.mode == 2) count(k_ro_count<2>);
+    else if (rp.mode == 1) count(k_ro_count<1>);
+    else count(k_ro_count<0>);
     rc = launch_scan_small(h, h->max_pixels, h->hit_cnt, max_hits, n_hits_dev, TRED_ST_HIT_OVERFLOW, 5, s);
     if (rc) return rc;
-    k_ro_emit<<<sms * 8, 256, 0, s>>>(wave, pixel_ids, n_pixels_dev, c, h->hit_cnt, h->hit_tmp, h->hit_tmpc,
-                                      max_hits, hit_pixel, hit_tick, hit_charge);
+    auto emit = [&](auto kern) {
+        kern<<<sms * 8, 256, 0, s>>>(wave, pixel_ids, n_pixels_dev, c, h->hit_cnt, h->hit_tmp, h->hit_tmpc, max_hits,
+                                     hit_pixel, hit_tick, hit_charge);
+    };
+    if (rp.mode == 2) emit(k_ro_emit<2>);
+    else if (rp.mode == 1) emit(k_ro_emit<1>);
+    else emit(k_ro_emit<0>);
     h->launches += 2;
     return check_cuda(h, cudaGetLastError(), "readout launch");
 }

@@ -482,7 +482,8 @@ int32_t tred_readout(tred_handle *h, const tred_readout_params *rp, const int32_
     if (!rp || !pixel_ids || !waveforms || !n_pixels_dev || !n_hits_dev || max_hits < 0 ||
         (max_hits > 0 && (!hit_pixel || !hit_tick || !hit_charge)))
         return set_error(h, TRED_ERR_INVALID_ARG, "tred_readout: null pointer");
-    if (rp->clock_ticks < 1 || rp->hold_ticks < 0 || rp->reset_ticks < 0)
+    if (rp->clock_ticks < 1 || rp->hold_ticks < 0 || rp->reset_ticks < 0 || rp->mode < 0 || rp->mode > 2 ||
+        (rp->mode == 1 && (rp->n_samples < 1 || rp->hold_ticks < 1)))
         return set_error(h, TRED_ERR_INVALID_ARG, "tred_readout: bad readout parameters");
     return launch_readout(h, *rp, pixel_ids, waveforms, n_pixels_dev, hit_pixel, hit_tick, hit_charge,
                           n_hits_dev, max_hits, (cudaStream_t)stream);

@@ -49,7 +49,8 @@ def params(cfg, effq_mode=0, mpcp=1, compensated_gather=0, conv_mode=0, effq_ski
 
 def readout_params(cfg) -> ReadoutParams:
     return ReadoutParams(threshold_e=cfg.threshold_e, clock_ticks=cfg.clock_ticks,
-                         hold_ticks=cfg.hold_ticks, reset_ticks=cfg.reset_ticks)
+                         hold_ticks=cfg.hold_ticks, reset_ticks=cfg.reset_ticks,
+                         mode=getattr(cfg, "readout_mode", 0), n_samples=getattr(cfg, "n_samples", 1))
 
 
 class DepositBuffers:

@@ -64,11 +64,13 @@ class Config:
     step_cm: float = 0.01
     seed: int = 1001
     response_seed: int = 7
-    # readout (trigger-reset)
+    # readout: 0 trigger-reset, 1 successive digitisations, 2 fixed-charge quanta
     threshold_e: float = 5000.0
     clock_ticks: int = 2
     hold_ticks: int = 32
     reset_ticks: int = 2
+    readout_mode: int = 0
+    n_samples: int = 1
 
     @property
     def n_blocks(self) -> int:

@@ -12,7 +12,7 @@ import pytest
 
 import oracle
 import synth
-from parity_util import (WAVE_TOL, check_blocks, check_csr_sets, check_drift, check_hits,
+from parity_util import (WAVE_TOL, check_hits_near_threshold, check_blocks, check_csr_sets, check_drift, check_hits,
                          check_qeff, make_sim, pixel_rel_errors, run)
 
 pytestmark = pytest.mark.gpu
@@ -276,3 +276,22 @@ def test_precision_ladder_module200(form, capsys):
         print(f"\nprecision {form}: max per-pixel rel L2 {err.max():.3e}, median {np.median(err):.3e}, "
               f"sampled-event rel L2 {ev:.3e}")
     assert err.max() <= tol
+
+
+@pytest.mark.parametrize("mode,n_samples", [(1, 3), (2, 1)])
+def test_readout_variants_tiny(mode, n_samples):
+    """Successive digitisations (no reset between the 3 samples of a trigger) and
+    fixed-charge quanta (Sec. II-E) on the full tiny event: the GPU hit lists equal
+    the FP64 oracle's, except from an edge whose charge is within 1e-4 of threshold."""
+    cfg = synth.get_config("tiny", readout_mode=mode, n_samples=n_samples)
+    dep, resp = synth.make_event(cfg)
+    res, ref, _ = _full_check(cfg, dep, resp, check_readout=False)
+    assert res["status"][0] == 0, res["status"]
+    hp, ht, hc, amb = oracle.readout(ref["pixel_ids"], ref["waveforms"], cfg.threshold_e, cfg.clock_ticks,
+                                     cfg.hold_ticks, cfg.reset_ticks, mode=mode, n_samples=n_samples)
+    assert len(hp) > 0
+    check_hits_near_threshold((res["hit_pixel"], res["hit_tick"], res["hit_charge"]), (hp, ht, hc), amb,
+                              ref["pixel_ids"], cfg.threshold_e)
+    if mode == 2:
+        assert np.all(res["hit_charge"] == np.float32(cfg.threshold_e))
+

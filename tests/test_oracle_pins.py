@@ -366,3 +366,68 @@ def test_readout_below_threshold_and_bipolar():
     assert list(hp) == [1]
     # C(k)=300(k-19) >= 5000 at k=36 (5100); sample at 68: 6000 - 2000 = 4000
     assert ht[0] == 68 and abs(hc[0] - 4000.0) < 1e-9
+
+
+# --------------------------------------------------------------- readout variants
+def test_readout_variants_hand_computed():
+    """Successive digitisations (3 per trigger) and fixed-charge quanta on the
+    hand-worked step waveform (tests/golden/readout_modes.txt, Sec. II-E)."""
+    ref = np.loadtxt(os.path.join(GOLDEN, "readout_modes.txt"))
+    wave = np.zeros((1, 400))
+    wave[0, 10:] = 100.0
+    for mode, ns in ((1, 3), (2, 1)):
+        hp, ht, hc, amb = oracle.readout(np.array([7], np.int32), wave, 5000.0, 2, 32, 2, mode=mode, n_samples=ns)
+        r = ref[ref[:, 0] == mode]
+        assert list(hp) == [7] * len(r)
+        np.testing.assert_array_equal(ht, r[:, 1].astype(int))
+        np.testing.assert_allclose(hc, r[:, 2], rtol=0, atol=1e-9)
+    # fixed charge: hits x quantum + what is left on the front end = all the charge
+    assert 7 * 5000.0 + 4000.0 == wave.sum()
+
+
+def test_readout_single_digitisation_is_trigger_reset():
+    rng = np.random.default_rng(5)
+    wave = rng.normal(0.0, 60.0, (6, 900)) + np.where(rng.random((6, 900)) < 0.05, 900.0, 0.0)
+    pix = np.arange(6, dtype=np.int32)
+    a = oracle.readout(pix, wave, 5000.0, 2, 32, 2, mode=0)
+    b = oracle.readout(pix, wave, 5000.0, 2, 32, 2, mode=1, n_samples=1)
+    for x, y in zip(a, b):
+        np.testing.assert_array_equal(x, y)
+
+
+def test_readout_fixed_charge_cumulative_thresholds():
+    """For non-negative currents below one quantum per clock period, the k-th quantum
+    is recorded at the first clock edge whose cumulative charge reaches k quanta."""
+    rng = np.random.default_rng(6)
+    clock, thr, nt = 4, 5000.0, 2000
+    wave = rng.uniform(0.0, thr / clock * 0.9, (5, nt)) * (rng.random((5, nt)) < 0.3)
+    hp, ht, hc, _ = oracle.readout(np.arange(5, dtype=np.int32), wave, thr, clock, 32, 2, mode=2)
+    edges = np.arange(0, nt, clock)
+    for p in range(5):
+        Q = np.cumsum(wave[p])[edges]
+        n = int(np.floor(Q[-1] / thr))
+        want = edges[np.searchsorted(Q, thr * np.arange(1, n + 1), side="left")]
+        np.testing.assert_array_equal(ht[hp == p], want)
+        assert np.all(hc[hp == p] == thr)
+
+
+def test_readout_successive_digitisations_follow_the_running_sum():
+    """Each trigger gives n samples hold apart with the integrator not reset between
+    them: sample m minus sample 1 is the charge collected in between; the first group
+    is the trigger-reset hit."""
+    rng = np.random.default_rng(7)
+    nt, hold, ns = 1500, 24, 4
+    wave = np.where(rng.random((4, nt)) < 0.08, rng.uniform(0, 900, (4, nt)), 0.0)
+    pix = np.arange(4, dtype=np.int32)
+    hp, ht, hc, _ = oracle.readout(pix, wave, 5000.0, 2, hold, 3, mode=1, n_samples=ns)
+    h0p, h0t, h0c, _ = oracle.readout(pix, wave, 5000.0, 2, hold, 3, mode=0)
+    for p in range(4):
+        t, q = ht[hp == p], hc[hp == p]
+        assert len(t) > ns
+        full = len(t) - len(t) % ns
+        g = t[:full].reshape(-1, ns)
+        assert np.all(np.diff(g, axis=1) == hold)
+        cq = q[:full].reshape(-1, ns)
+        cs = np.cumsum(wave[p])
+        np.testing.assert_allclose(cq[:, 1:] - cq[:, :1], cs[g[:, 1:]] - cs[g[:, :1]], rtol=0, atol=1e-6)
+        assert t[0] == h0t[h0p == p][0] and abs(q[0] - h0c[h0p == p][0]) < 1e-9
