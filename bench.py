@@ -310,7 +310,7 @@ def run_lines(args):
     seg = synth.make_segments(cfg, synth.SEG_CM["module_lines"])
     resp = torch.from_numpy(synth.make_response(cfg))
     n = len(seg["x0"])
-    sim = tred.LineSimulator(cfg, resp, max_segments=n, max_blocks=6000, max_pixels=300000)
+    sim = tred.LineSimulator(cfg, resp, max_segments=n, max_blocks=6000, max_pixels=300000, effq_skip_empty=1)
     x = {k: torch.from_numpy(v).cuda() for k, v in seg.items()}
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
 

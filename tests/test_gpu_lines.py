@@ -11,14 +11,14 @@ from parity_util import (WAVE_TOL, check_blocks, check_drift, check_hits, check_
 pytestmark = pytest.mark.gpu
 
 
-def _run(cfg, seg, resp, max_blocks=None, max_pixels=None):
+def _run(cfg, seg, resp, max_blocks=None, max_pixels=None, skip_empty=0):
     import torch
     from paper_2602_12052_b300 import build, tred
     build.build()
     n = len(seg["x0"])
     sim = tred.LineSimulator(cfg, torch.from_numpy(np.ascontiguousarray(resp)), max_segments=max(n, 1),
                              max_blocks=max_blocks or min(cfg.n_blocks, 20000),
-                             max_pixels=max_pixels or min(cfg.npx * cfg.npx, 400000))
+                             max_pixels=max_pixels or min(cfg.npx * cfg.npx, 400000), effq_skip_empty=skip_empty)
     t = {k: torch.from_numpy(np.ascontiguousarray(v)).cuda() for k, v in seg.items()}
     sim.step_lines(n, t["x0"], t["y0"], t["z0"], t["x1"], t["y1"], t["z1"], t["t0"], t["ne"])
     res = sim.results()
@@ -122,3 +122,23 @@ def test_module_plane_segments_sampled():
     ref = oracle.currents_from_qeff(p, sel, oracle.qeff_line_blocks(p, L, sel), resp, pix)
     err = pixel_rel_errors(res["waveforms"][rows], ref)
     assert err.max() <= WAVE_TOL, (err.max(), int(pix[err.argmax()]))
+
+
+def test_tiny_track_segments_covered_columns_only():
+    """The same tiny track with the effective charge written only for the sub-cell
+    columns some segment's support covers (the bench's setting): pixel waveforms
+    within tolerance of the oracle, and the same pixels and hits as the dense run."""
+    cfg = synth.get_config("tiny_lines")
+    seg = synth.make_segments(cfg, synth.SEG_CM["tiny_lines"])
+    resp = synth.make_response(cfg)
+    _, dense = _run(cfg, seg, resp)
+    sim, res = _run(cfg, seg, resp, skip_empty=1)
+    assert res["status"][0] == 0, res["status"]
+    ref = oracle.simulate_lines(cfg, seg, resp)
+    np.testing.assert_array_equal(res["pixel_ids"], ref["pixel_ids"])
+    err = pixel_rel_errors(res["waveforms"], ref["waveforms"])
+    assert err.max() <= WAVE_TOL, (err.max(), int(err.argmax()))
+    np.testing.assert_array_equal(res["pixel_ids"], dense["pixel_ids"])
+    np.testing.assert_array_equal(res["hit_pixel"], dense["hit_pixel"])
+    np.testing.assert_array_equal(res["hit_tick"], dense["hit_tick"])
+
