@@ -81,10 +81,14 @@ struct AdjConst {
 
 constexpr int AS_THREADS = 512;
 constexpr int AS_WARPS = AS_THREADS / 32;
-constexpr int DH_ROW = 17;                  // [k2][ky][kx] rows padded
-constexpr int DH_BIN = LP * DH_ROW;
-constexpr int AT_ROW = 17;                  // per-warp transpose [2][8 cy][16 kx + 1]
+constexpr int DH_ROW = 17;                  // [slot][ky][kx] rows padded
+constexpr int DH_BIN = LP * DH_ROW + 1;     // odd bin stride
+constexpr int AT_ROW = 18;                  // per-warp transpose [2][8 cy][16 kx + 2]
 constexpr int AT_BIN = 8 * AT_ROW;
+// Bin slot in the spectrum buffer: bin k2 = 4 c + 2 d + a at slot 32 a + 16 d + c.  Stage
+// A's lane l holds bins 2 b + {0, 1}, b = bitrev5(l), so each half warp's 16 stores land
+// on 16 distinct slots modulo 16, i.e. distinct bank pairs with the odd bin stride.
+__device__ __forceinline__ int dh_slot(int k2) { return ((k2 & 1) << 5) | (((k2 >> 1) & 1) << 4) | (k2 >> 2); }
 constexpr size_t ADJ_SPEC_SMEM = sizeof(float2) * ((size_t)BINS * DH_BIN + (size_t)AS_WARPS * 2 * AT_BIN);
 
 template <int G>
@@ -147,15 +151,15 @@ __global__ void __launch_bounds__(AS_THREADS, 1)
             v0 = fft32_lanes<false>(v0, tw + TW_32, lane);
             v1 = fft32_lanes<false>(v1, tw + TW_32, lane);
             const int b5 = bitrev<32>(lane);
-            dh[(2 * b5) * DH_BIN + cy * DH_ROW + cx] = v0;
-            dh[(2 * b5 + 1) * DH_BIN + cy * DH_ROW + cx] = v1;
+            dh[dh_slot(2 * b5) * DH_BIN + cy * DH_ROW + cx] = v0;
+            dh[dh_slot(2 * b5 + 1) * DH_BIN + cy * DH_ROW + cx] = v1;
         }
         __syncthreads();
         // ---- forward 16 x 16 spatial FFT of every bin, in place -> [k2][ky][kx]
         for (int it = 0; it < BINS / (2 * AS_WARPS); ++it) {
             const int b = lane >> 4, r = lane & 15;
             const int k2 = (BINS / AS_WARPS) * warp + 2 * it + b;
-            float2 *d = dh + k2 * DH_BIN;
+            float2 *d = dh + dh_slot(k2) * DH_BIN;
             float2 v[LP];
 #pragma unroll
             for (int x = 0; x < LP; ++x) v[x] = d[r * DH_ROW + x];          // row cy = r over cx
@@ -179,7 +183,7 @@ __global__ void __launch_bounds__(AS_THREADS, 1)
             for (int it = 0; it < BINS / (2 * AS_WARPS); ++it) {
                 const int b = lane >> 4, kx = lane & 15;
                 const int k2 = (BINS / AS_WARPS) * warp + 2 * it + b;
-                const float2 *d = dh + k2 * DH_BIN + kx;
+                const float2 *d = dh + dh_slot(k2) * DH_BIN + kx;
                 const float2 *rsrc = rp + rhat_bin(k1 + G * k2, p, c.npairs, LT / 32) + kx;
                 float2 v[LP];
 #pragma unroll
@@ -227,47 +231,86 @@ __global__ void __launch_bounds__(AS_THREADS, 1)
     }
 }
 
-// Inverse time FFT per (block, pair, 8 input columns); writes dL/dQeff.
+// 8-byte asynchronous copy global -> shared (through L1), committed per item
+__device__ __forceinline__ void acp_async8(void *smem, const void *gmem) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"((uint32_t)__cvta_generic_to_shared(smem)),
+                 "l"(gmem)
+                 : "memory");
+}
+__device__ __forceinline__ void acp_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void acp_wait() {
+    asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
+
 template <int G>
-__global__ void __launch_bounds__(256) k_adj_itime(const int32_t *__restrict__ n_blocks_dev,
-                                                   const float2 *__restrict__ gspec,
-                                                   const int32_t *__restrict__ pair_j,
-                                                   const float2 *__restrict__ tw, AdjConst c,
-                                                   float *__restrict__ gq, int slot_base, int slot_count) {
+__host__ __device__ constexpr int adj_itime_cols() { return G == 8 ? 16 : 8; }
+template <int G>
+constexpr size_t adj_itime_smem() {
+    return sizeof(float2) * (2 * adj_itime_cols<G>() * (64 * G + 1) + 64 * G + 32);
+}
+
+// Inverse time FFT of the packed adjoint spectra; writes dL/dQeff of both impacts of
+// each pair.  Persistent CTAs over (block, pair, group of NC input columns) items, one
+// warp per column; the next item's spectra stream into the other half of a double
+// buffer (cp.async) while the current item is transformed, and each lane writes its
+// 16 (or 32) consecutive ticks as float4 stores.
+template <int G>
+__global__ void __launch_bounds__(32 * adj_itime_cols<G>(), 1)
+    k_adj_itime(const int32_t *__restrict__ n_blocks_dev, const float2 *__restrict__ gspec,
+                const int32_t *__restrict__ pair_j, const float2 *__restrict__ tw, AdjConst c,
+                float *__restrict__ gq, int slot_base, int slot_count) {
     constexpr int LT = 64 * G;
     constexpr int NPL = LT / 32;
+    constexpr int NC = adj_itime_cols<G>();
+    constexpr int NT = 32 * NC;
     constexpr int SROW = LT + 1;
     extern __shared__ float2 sm_t[];
-    float2 *S = sm_t;                      // [8][LT + 1]
-    float2 *wlt = S + 8 * SROW;
+    float2 *S = sm_t;                      // [2][NC][LT + 1]
+    float2 *wlt = S + 2 * NC * SROW;
     float2 *w32 = wlt + LT;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    for (int k = tid; k < LT; k += blockDim.x) wlt[k] = tw[TW_LT + k];
+    for (int k = tid; k < LT; k += NT) wlt[k] = tw[TW_LT + k];
     if (tid < 32) w32[tid] = tw[TW_32 + tid];
     const int nb = n_blocks_dev[0];
     const int nloc = min(slot_count, nb - slot_base);
     if (nloc <= 0) return;
     const int cols = c.bp * c.bp;
-    const int groups = (cols + 7) / 8;
+    const int groups = (cols + NC - 1) / NC;
     const int items = nloc * c.npairs * groups;
-    for (int item = blockIdx.x; item < items; item += gridDim.x) {
+    // thread tid copies column q = tid % NC of the item at frequencies f = tid / NC + 32 j
+    auto issue = [&](int item, int bsel) {
         const int grp = item % groups;
         const int p = (item / groups) % c.npairs;
         const int sl = item / (groups * c.npairs);
-        __syncthreads();
-        const float2 *src = gspec + (((size_t)sl * c.npairs + p) * LT) * 64;
-        for (int k = tid; k < 8 * LT; k += blockDim.x) {
-            const int q = k & 7, f = k >> 3;
-            const int col = grp * 8 + q;
+        const int q = tid % NC, col = grp * NC + q;
+        if (col < cols) {
             const int py = col / c.bp, px = col % c.bp;
-            S[q * SROW + f] = col < cols ? src[(size_t)f * 64 + py * 8 + px] : make_float2(0.f, 0.f);
+            const float2 *src = gspec + ((size_t)sl * c.npairs + p) * LT * 64 + py * 8 + px;
+            float2 *dst = S + (bsel * NC + q) * SROW;
+#pragma unroll 4
+            for (int f = tid / NC; f < LT; f += NT / NC) acp_async8(dst + f, src + (size_t)f * 64);
         }
-        __syncthreads();
-        const int col = grp * 8 + warp;
+        acp_commit();
+    };
+    int item = blockIdx.x;
+    if (item < items) issue(item, 0);
+    for (int i = 0; item < items; ++i, item += gridDim.x) {
+        const int cur = i & 1;
+        if (item + (int)gridDim.x < items)
+            issue(item + gridDim.x, cur ^ 1);   // that buffer's last readers passed the previous barrier
+        else
+            acp_commit();                       // empty group: keeps the wait count uniform
+        acp_wait<1>();
+        __syncthreads();                        // this item's columns (and the W tables) are in place
+        const int grp = item % groups;
+        const int p = (item / groups) % c.npairs;
+        const int sl = item / (groups * c.npairs);
+        const int col = grp * NC + warp;
         if (col < cols) {
             float2 v[NPL];
 #pragma unroll
-            for (int m = 0; m < NPL; ++m) v[m] = S[warp * SROW + lane + 32 * m];
+            for (int m = 0; m < NPL; ++m) v[m] = S[(cur * NC + warp) * SROW + lane + 32 * m];
             fft_reg_dif_c<NPL, true>(v);
 #pragma unroll
             for (int k = 0; k < NPL; ++k) {
@@ -276,22 +319,30 @@ __global__ void __launch_bounds__(256) k_adj_itime(const int32_t *__restrict__ n
                 w.y = -w.y;
                 v[k] = fft32_lanes<true>(cmul(v[k], w), w32, lane);
             }
-            // lane holds t = NPL * bitrev5(lane) + bitrev(k)
-            const int slot = slot_base + sl;
-            const int j1 = pair_j[2 * p], j2 = pair_j[2 * p + 1];
+            // lane holds t = NPL * bitrev5(lane) + bitrev(k); bt is a multiple of NPL, so a
+            // lane's NPL consecutive ticks are all inside [0, bt) or all beyond it
             const int tbase = NPL * bitrev<32>(lane);
-            float *o1 = gq + (((size_t)slot * c.nch + j1) * cols + col) * c.bt;
-            float *o2 = j2 >= 0 ? gq + (((size_t)slot * c.nch + j2) * cols + (cols - 1 - col)) * c.bt : nullptr;
+            if (tbase < c.bt) {
+                const int slot = slot_base + sl;
+                const int j1 = pair_j[2 * p], j2 = pair_j[2 * p + 1];
+                float *o1 = gq + (((size_t)slot * c.nch + j1) * cols + col) * c.bt + tbase;
 #pragma unroll
-            for (int k = 0; k < NPL; ++k) {
-                const int t = tbase + bitrev<NPL>(k);
-                if (t < c.bt) {
-                    o1[t] = v[k].x;
-                    if (o2) o2[t] = v[k].y;
+                for (int k = 0; k < NPL; k += 4)        // tick k + e sits in register bitrev(k + e)
+                    *reinterpret_cast<float4 *>(o1 + k) =
+                        make_float4(v[bitrev<NPL>(k)].x, v[bitrev<NPL>(k + 1)].x, v[bitrev<NPL>(k + 2)].x,
+                                    v[bitrev<NPL>(k + 3)].x);
+                if (j2 >= 0) {
+                    float *o2 = gq + (((size_t)slot * c.nch + j2) * cols + (cols - 1 - col)) * c.bt + tbase;
+#pragma unroll
+                    for (int k = 0; k < NPL; k += 4)
+                        *reinterpret_cast<float4 *>(o2 + k) =
+                            make_float4(v[bitrev<NPL>(k)].y, v[bitrev<NPL>(k + 1)].y, v[bitrev<NPL>(k + 2)].y,
+                                        v[bitrev<NPL>(k + 3)].y);
                 }
             }
         }
     }
+    acp_wait<0>();
 }
 
 // ------------------------------------------------------------------ chain rule
@@ -487,7 +538,7 @@ template <int G>
 static int run_adjoint_conv(tred_handle *h, const int32_t *block_ids, const int32_t *n_blocks_dev,
                             const float *resid, float *gq, const AdjConst &c, cudaStream_t s) {
     static bool attr = false;
-    const size_t itime_smem = sizeof(float2) * (8 * (64 * G + 1) + 64 * G + 32);
+    const size_t itime_smem = adj_itime_smem<G>();
     if (!attr) {
         cudaFuncSetAttribute(k_adj_spec<G>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ADJ_SPEC_SMEM);
         cudaFuncSetAttribute(k_adj_itime<G>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)itime_smem);
@@ -498,8 +549,8 @@ static int run_adjoint_conv(tred_handle *h, const int32_t *block_ids, const int3
     for (int base = 0; base < h->max_blocks; base += chunk) {
         k_adj_spec<G><<<sms, AS_THREADS, ADJ_SPEC_SMEM, s>>>(n_blocks_dev, block_ids, resid, h->pix_row, h->tw,
                                                              h->rhat, c, h->gspec, base, chunk);
-        k_adj_itime<G><<<sms * 2, 256, itime_smem, s>>>(n_blocks_dev, h->gspec, h->pair_j, h->tw, c, gq, base,
-                                                        chunk);
+        k_adj_itime<G><<<sms, 32 * adj_itime_cols<G>(), itime_smem, s>>>(n_blocks_dev, h->gspec, h->pair_j, h->tw, c,
+                                                                         gq, base, chunk);
         h->launches += 2;
     }
     return check_cuda(h, cudaGetLastError(), "adjoint convolution launch");
