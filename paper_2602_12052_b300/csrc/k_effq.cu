@@ -206,6 +206,8 @@ struct EffqShared {
     unsigned long long mask[128];        // per channel: non-empty (py, px) columns (n_sub^2 <= 128)
     uint32_t cov[EQ_MAX_SIDE * EQ_MAX_SIDE / 32];   // sub-cell columns covered by a support
     uint8_t pcov[EQ_MAX_PATCH];                       // patch has a covered column
+    uint16_t alist[EQ_MAX_PATCH];                     // the patches written at all, in order
+    int nactive;
     float term[EQ_TERMS];                             // bound terms of the block's first deposits
     unsigned long long part[EQ_WARPS * 3];
     int tot[4];                          // list entries, pool floats, bucket slots, accepted count
@@ -340,6 +342,20 @@ __global__ void __launch_bounds__(EQ_THREADS, EQ_CTAS_PER_SM) k_effq_blocks(
             }
             __syncthreads();
         }
+        // the patches written at all (every patch, or those with a covered column): the
+        // warps of each tile take only these
+        if (warp == 0) {
+            int na = 0;
+            for (int b0 = 0; b0 < npatch; b0 += 32) {
+                const int pt = b0 + lane;
+                const bool act = pt < npatch && (!c.skip_empty || S.pcov[pt]);
+                const unsigned bal = __ballot_sync(0xffffffffu, act);
+                if (act) S.alist[na + __popc(bal & ((1u << lane) - 1u))] = (uint16_t)pt;
+                na += __popc(bal);
+            }
+            if (lane == 0) S.nactive = na;
+        }
+        __syncthreads();
         for (int tt = 0; tt < c.bt; tt += EQ_TT) {
             const int ta = T0 + tt, tb = ta + EQ_TT - 1;   // absolute ticks of the tile
             int cur = beg;
@@ -460,12 +476,14 @@ __global__ void __launch_bounds__(EQ_THREADS, EQ_CTAS_PER_SM) k_effq_blocks(
                         }
                 }
                 __syncthreads();
-                // (4) patches, taken one by one by the warps
+                // (4) patches, taken one by one by the warps from the list of written patches
+                const int nact = S.nactive;
                 for (;;) {
-                    int pt = 0;
-                    if (lane == 0) pt = atomicAdd(&S.next, 1);
-                    pt = __shfl_sync(0xffffffffu, pt, 0);
-                    if (pt >= npatch) break;
+                    int pi = 0;
+                    if (lane == 0) pi = atomicAdd(&S.next, 1);
+                    pi = __shfl_sync(0xffffffffu, pi, 0);
+                    if (pi >= nact) break;
+                    const int pt = S.alist[pi];
                     const int qy = pt / npx, qx = pt - qy * npx;
                     const int gx = qx * EQ_PX + lx, gy = qy * EQ_PY + ly;
                     const bool own = gx < side && gy < side;
