@@ -43,15 +43,22 @@ __device__ int walk_pixel(const float *__restrict__ I, const RoConst &c, int lan
     int state = 0;            // 0: looking for a trigger; 1: waiting for the sample tick
     int ts = 0;               // next sample tick
     int left = 0;             // samples still to take after ts (mode 1)
-    while (pos < c.nt) {
-        float v[4][4];
+    auto load = [&](float (&v)[4][4], int p) {
 #pragma unroll
         for (int i = 0; i < 4; ++i)
 #pragma unroll
             for (int e = 0; e < 4; ++e) {
-                const int t = pos + 128 * i + 4 * lane + e;
+                const int t = p + 128 * i + 4 * lane + e;
                 v[i][e] = t < c.nt ? __ldg(I + t) : 0.f;
             }
+    };
+    float v[4][4];
+    load(v, pos);
+    while (pos < c.nt) {
+        // the next step's loads are in flight while this step is scanned (a restart after a
+        // hit reloads from the new position)
+        float vn[4][4];
+        load(vn, pos + 512);
         bool restart = false;
 #pragma unroll
         for (int i = 0; i < 4; ++i) {
@@ -144,13 +151,21 @@ __device__ int walk_pixel(const float *__restrict__ I, const RoConst &c, int lan
             if (restart) break;
             base = __shfl_sync(0xffffffffu, C[3], 31);
         }
-        if (!restart) pos += 512;
+        if (!restart) {
+            pos += 512;
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+#pragma unroll
+                for (int e = 0; e < 4; ++e) v[i][e] = vn[i][e];
+        } else if (pos < c.nt) {
+            load(v, pos);
+        }
     }
     return nh;
 }
 
 template <int RM>
-__global__ void __launch_bounds__(256) k_ro_count(const float *__restrict__ wave,
+__global__ void __launch_bounds__(256, 2) k_ro_count(const float *__restrict__ wave,
                                                   const int32_t *__restrict__ n_pixels_dev, RoConst c,
                                                   int32_t *__restrict__ cnt, int32_t *__restrict__ tmp_t,
                                                   float *__restrict__ tmp_c) {
@@ -170,7 +185,7 @@ __global__ void __launch_bounds__(256) k_ro_count(const float *__restrict__ wave
 }
 
 template <int RM>
-__global__ void __launch_bounds__(256) k_ro_emit(const float *__restrict__ wave,
+__global__ void __launch_bounds__(256, 2) k_ro_emit(const float *__restrict__ wave,
                                                  const int32_t *__restrict__ pixel_ids,
                                                  const int32_t *__restrict__ n_pixels_dev, RoConst c,
                                                  const int32_t *__restrict__ off,
