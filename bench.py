@@ -90,6 +90,26 @@ def _args():
     return ap.parse_args()
 
 
+def replica_seed(cfg, rank: int) -> int:
+    """Seed of rank `rank`'s independent event (replicas: every rank simulates its own)."""
+    return cfg.seed + 7919 * rank
+
+
+def aggregate_replicas(n_local: float, ms_local: float, world: int, device=None):
+    """Whole-job totals of independent replicas: the units all ranks processed and the
+    slowest rank's time (max over ranks).  The only collectives of the multi-GPU path;
+    nothing on the data path."""
+    if world <= 1:
+        return float(n_local), float(ms_local)
+    import torch
+    import torch.distributed as dist
+    n_t = torch.tensor([float(n_local)], dtype=torch.float64, device=device)
+    m_t = torch.tensor([float(ms_local)], dtype=torch.float64, device=device)
+    dist.all_reduce(n_t, op=dist.ReduceOp.SUM)
+    dist.all_reduce(m_t, op=dist.ReduceOp.MAX)
+    return float(n_t.item()), float(m_t.item())
+
+
 def _dist():
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -544,7 +564,7 @@ def main():
     cfg = synth.get_config(args.config)
     if args.readout_mode:
         cfg = cfg.with_(readout_mode=args.readout_mode, n_samples=args.n_samples if args.readout_mode == 1 else 1)
-    dep = synth.make_deposits(cfg, seed=cfg.seed + 7919 * rank)
+    dep = synth.make_deposits(cfg, seed=replica_seed(cfg, rank))
     resp = synth.make_response(cfg)
     n = len(dep["x"])
     dev = torch.device("cuda", local)
@@ -619,11 +639,8 @@ def main():
     stage_ms = {nm: statistics.mean(evs[k][i].elapsed_time(evs[k][i + 1]) for k in range(args.steps))
                 for i, nm in enumerate(stage_names)}
     ms = statistics.mean(step_ms)
-    if world > 1:
-        t_ = torch.tensor([ms], device=dev)
-        torch.distributed.all_reduce(t_, op=torch.distributed.ReduceOp.MAX)
-        ms = float(t_.item())
-    value = n * world / (ms / 1e3)
+    n_job, ms = aggregate_replicas(n, ms, world, dev)
+    value = n_job / (ms / 1e3)
 
     # end to end through the public API: pinned host inputs -> device, step,
     # counts + hit list -> pinned host, every step inside the timed region
@@ -653,11 +670,8 @@ def main():
             if k >= args.warmup:
                 e_ms.append(a.elapsed_time(b))
         em = statistics.mean(e_ms)
-        if world > 1:
-            t_ = torch.tensor([em], device=dev)
-            torch.distributed.all_reduce(t_, op=torch.distributed.ReduceOp.MAX)
-            em = float(t_.item())
-        e2e = {"value": n * world / (em / 1e3), "unit": "depos/s", "h2d_bytes_per_step": h2d,
+        n_e2e, em = aggregate_replicas(n, em, world, dev)
+        e2e = {"value": n_e2e / (em / 1e3), "unit": "depos/s", "h2d_bytes_per_step": h2d,
                "d2h_bytes_per_step": d2h, "ms_per_step": em}
 
     conv_ms = stage_ms["convolve"]
@@ -692,6 +706,7 @@ def main():
                                     + {0: "", 1: f", readout: {cfg.n_samples} successive digitisations per trigger",
                                        2: ", readout: fixed-charge quanta"}[args.readout_mode]),
                        "deposits": n, "active_blocks": nb, "active_pixels": npix, "hits": nh,
+                       **({"deposits_all_ranks": int(n_job)} if world > 1 else {}),
                        "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
                        "l2": "flushed between timed steps (256 MB write, outside the step events)"},
             "stages_ms": stage_ms, "set_response_ms": set_response_ms,
