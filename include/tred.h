@@ -152,6 +152,16 @@ int32_t tred_reset_status(tred_handle *h, void *stream);
  * access; diagnostics for benchmarks). */
 int32_t tred_launch_count(const tred_handle *h, int64_t *count);
 
+/* Failure-detection self-test of the bounded device waits (the paper has no
+ * counterpart; this is the library's own fault path).  Enqueues one thread that
+ * waits, for limit_cycles SM clock cycles (1 .. 2e9; about 1 s per 2e9 at the
+ * maximum clock), on an mbarrier phase that nothing completes, exactly as the
+ * tensor-core convolution waits on its copies; when the limit passes it sets
+ * TRED_ST_TIMEOUT in the status word and returns, leaving the context usable.
+ * Read it with tred_sync_status; clear it with tred_reset_status.
+ * TRED_ERR_INVALID_ARG for a limit outside the range. */
+int32_t tred_wait_selftest(tred_handle *h, int64_t limit_cycles, void *stream);
+
 /* a0. Response spectrum (Sec. III-A-2: the spectra of the per-impact responses are computed once; Eq. interlaced,
  * R[j, k] = i[j, -k]).  resp_dev: [kp][kp][n_sub][n_sub][nr] float32, index
  * [Ky + R][Kx + R][jy][jx][tau] = current on the central electrode from unit charge

@@ -69,8 +69,9 @@ __device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
 __device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
     asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
 }
-// bounded wait for the phase with parity `phase` to complete; false on timeout
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t phase) {
+// bounded wait for the phase with parity `phase` to complete; false once `limit` cycles
+// have passed without it
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t phase, long long limit = DG_WAIT_CYCLES) {
     const long long t0 = clock64();
     for (;;) {
         uint32_t ok;
@@ -82,8 +83,26 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t phase) {
             : "r"(bar), "r"(phase)
             : "memory");
         if (ok) return true;
-        if (clock64() - t0 > DG_WAIT_CYCLES) return false;
+        if (clock64() - t0 > limit) return false;
     }
+}
+
+// Bounded-wait self-test: one thread initialises an mbarrier that expects one arrival
+// which never comes, waits on it for `limit` cycles and reports the expiry in the status
+// word exactly as the tensor-core convolution's waits do (TRED_ST_TIMEOUT).  Nothing is
+// left in flight: the barrier is plain shared memory, released when the CTA exits.
+__global__ void k_wait_selftest(long long limit, int32_t *__restrict__ status) {
+    __shared__ __align__(8) uint64_t bar;
+    if (threadIdx.x != 0) return;
+    const uint32_t b = smem_u32(&bar);
+    mbar_init(b, 1);
+    if (!mbar_wait(b, 0, limit)) atomicOr(&status[0], TRED_ST_TIMEOUT);
+}
+
+int launch_wait_selftest(tred_handle *h, long long limit, cudaStream_t s) {
+    k_wait_selftest<<<1, 32, 0, s>>>(limit, h->status);
+    h->launches += 1;
+    return check_cuda(h, cudaGetLastError(), "wait self-test launch");
 }
 __device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap *map, int x, int y, uint32_t bar) {
     asm volatile(

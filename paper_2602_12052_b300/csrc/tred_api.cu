@@ -489,4 +489,11 @@ int32_t tred_readout(tred_handle *h, const tred_readout_params *rp, const int32_
                           n_hits_dev, max_hits, (cudaStream_t)stream);
 }
 
+int32_t tred_wait_selftest(tred_handle *h, int64_t limit_cycles, void *stream) {
+    if (!h) return TRED_ERR_INVALID_ARG;
+    if (limit_cycles < 1 || limit_cycles > 2000000000ll)
+        return set_error(h, TRED_ERR_INVALID_ARG, "tred_wait_selftest: limit must be in [1, 2e9] cycles");
+    return launch_wait_selftest(h, (long long)limit_cycles, (cudaStream_t)stream);
+}
+
 }  // extern "C"

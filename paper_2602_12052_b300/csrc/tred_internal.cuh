@@ -119,6 +119,7 @@ int launch_effq(tred_handle *h, int n, const tred_deposits &deps, const int32_t 
                 const int32_t *dep_offsets, const int32_t *dep_index,
                 const int32_t *n_blocks_dev, float *qeff, int slot_base, int slot_count, cudaStream_t s);
 int launch_response(tred_handle *h, const float *resp, cudaStream_t s);
+int launch_wait_selftest(tred_handle *h, long long limit, cudaStream_t s);
 int launch_convolve(tred_handle *h, const int32_t *block_ids, const int32_t *n_blocks_dev,
                     const float *qeff, float *out, int slot_base, int slot_count, cudaStream_t s);
 int launch_gather(tred_handle *h, const int32_t *block_ids, const int32_t *n_blocks_dev,

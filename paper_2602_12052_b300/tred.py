@@ -174,6 +174,10 @@ def tred_readout(h: Handle, rp: ReadoutParams, pixel_ids, waveforms, n_pixels_de
                                _stream(stream)))
 
 
+def tred_wait_selftest(h: Handle, limit_cycles: int, stream=None):
+    h.check(h.lib.tred_wait_selftest(h.h, int(limit_cycles), _stream(stream)))
+
+
 def tred_sync_status(h: Handle, stream=None):
     buf = (ctypes.c_int32 * abi.TRED_STATUS_WORDS)()
     h.check(h.lib.tred_sync_status(h.h, _stream(stream), ctypes.cast(buf, ctypes.c_void_p)))

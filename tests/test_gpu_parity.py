@@ -192,6 +192,29 @@ def test_capacity_overflow_sets_status():
     assert res["n_blocks"] == 2
 
 
+def test_bounded_wait_expires_into_the_status_word():
+    """A device wait on an mbarrier phase that nothing completes gives up after its
+    limit, sets TRED_ST_TIMEOUT and leaves the context usable: after clearing the status
+    the same handle runs the tiny event to the oracle's currents."""
+    import torch
+    from paper_2602_12052_b300 import abi, tred
+    cfg = synth.get_config("tiny")
+    dep, resp = synth.make_event(cfg)
+    sim = make_sim(cfg, resp, len(dep["x"]))
+    tred.tred_wait_selftest(sim.h, 2_000_000)            # about 1 ms at the maximum clock
+    torch.cuda.synchronize()
+    st = tred.tred_sync_status(sim.h)
+    assert st[0] & abi.TRED_ST_TIMEOUT, st
+    with pytest.raises(abi.TredError):
+        tred.tred_wait_selftest(sim.h, 0)                # limit outside the range
+    tred.tred_reset_status(sim.h)
+    res = run(sim, dep, keep_qeff=False)
+    assert res["status"][0] == 0, res["status"]
+    ref = _oracle_all(cfg, dep, resp, 0)
+    np.testing.assert_array_equal(res["pixel_ids"], ref["pixel_ids"])
+    assert pixel_rel_errors(res["waveforms"], ref["waveforms"]).max() <= WAVE_TOL
+
+
 def test_repeatable_outputs():
     """Block list, occupancy and pixel list are identical run to run, and so is the
     effective charge, bit for bit (fixed-point accumulation in the tile)."""
