@@ -197,6 +197,7 @@ static_assert(sizeof(TileEnt) == 32 + 4 * EQ_TT, "tile list entry");
 
 struct EffqShared {
     TileEnt list[EQ_LIST];
+    int2 wsrc[EQ_LIST];                  // per entry: offsets of its clipped x and y weights in wts
     float pool[EQ_POOL];
     uint16_t bucket[EQ_INS];
     int boff[EQ_MAX_PATCH + 1];
@@ -415,6 +416,7 @@ __global__ void __launch_bounds__(EQ_THREADS, EQ_CTAS_PER_SM) k_effq_blocks(
                         en.wxo = po;
                         en.wyo = po + (xb - xa + 1);
                         en.idx = r.idx;
+                        S.wsrc[pos] = make_int2((int)(base + (X0 + xa - r.gx0)), (int)(base + c.wx + (Y0 + ya - r.gy0)));
 #pragma unroll
                         for (int e = 0; e < EQ_TT; ++e) {
                             const int t = ta + e;
@@ -457,13 +459,34 @@ __global__ void __launch_bounds__(EQ_THREADS, EQ_CTAS_PER_SM) k_effq_blocks(
                         S.next = 0;
                     }
                 }
-                for (int k = warp; k < ne; k += EQ_WARPS) {
-                    const TileEnt &en = S.list[k];
-                    const DepRec r = recs[en.idx];
-                    const float *w = wts + (size_t)en.idx * c.wstride;
-                    const int nx = en.x1 - en.x0 + 1, ny = en.y1 - en.y0 + 1;
-                    for (int q = lane; q < nx; q += 32) S.pool[en.wxo + q] = __ldg(w + (X0 + en.x0 + q - r.gx0));
-                    for (int q = lane; q < ny; q += 32) S.pool[en.wyo + q] = __ldg(w + c.wx + (Y0 + en.y0 + q - r.gy0));
+                // the clipped x and y weight vectors of the entries, two entries' loads in
+                // flight per warp (their source offsets were kept when the entries were made)
+                for (int k0 = warp; k0 < ne; k0 += 2 * EQ_WARPS) {
+                    float vx[2], vy[2];
+                    int ox[2], oy[2], nxs[2], nys[2];
+#pragma unroll
+                    for (int u = 0; u < 2; ++u) {
+                        const int k = k0 + u * EQ_WARPS;
+                        nxs[u] = nys[u] = 0;
+                        vx[u] = vy[u] = 0.f;
+                        if (k < ne) {
+                            const int4 hy = *reinterpret_cast<const int4 *>(&S.list[k].y0);   // y0 y1 x0 x1
+                            const int2 src = S.wsrc[k];
+                            nxs[u] = hy.w - hy.z + 1;
+                            nys[u] = hy.y - hy.x + 1;
+                            ox[u] = S.list[k].wxo;
+                            oy[u] = S.list[k].wyo;
+                            if (lane < nxs[u]) vx[u] = __ldg(wts + (size_t)(unsigned)src.x + lane);
+                            if (lane < nys[u]) vy[u] = __ldg(wts + (size_t)(unsigned)src.y + lane);
+                            for (int q = lane + 32; q < nxs[u]; q += 32) S.pool[ox[u] + q] = __ldg(wts + (size_t)(unsigned)src.x + q);
+                            for (int q = lane + 32; q < nys[u]; q += 32) S.pool[oy[u] + q] = __ldg(wts + (size_t)(unsigned)src.y + q);
+                        }
+                    }
+#pragma unroll
+                    for (int u = 0; u < 2; ++u) {
+                        if (lane < nxs[u]) S.pool[ox[u] + lane] = vx[u];
+                        if (lane < nys[u]) S.pool[oy[u] + lane] = vy[u];
+                    }
                 }
                 __syncthreads();
                 // (3) bucket fill
@@ -618,6 +641,9 @@ int launch_effq(tred_handle *h, int n, const tred_deposits &deps, const int32_t 
     const int side = c.bp * c.ns;
     const int len_cap = c.wx < side ? c.wx : side;
     const int max_ins = ((len_cap + EQ_PY - 2) / EQ_PY + 1) * ((len_cap + EQ_PX - 2) / EQ_PX + 1);
+    if ((size_t)h->max_deposits * (size_t)c.wstride >= ((size_t)1 << 32))
+        return set_error(h, TRED_ERR_INVALID_ARG, "effq: %d deposits x %d weights exceed 32-bit offsets",
+                         h->max_deposits, c.wstride);
     if (side > EQ_MAX_SIDE || nch > 128 || 2 * len_cap > EQ_POOL || max_ins > EQ_INS)
         return set_error(h, TRED_ERR_INVALID_ARG, "effq: bp * n_sub = %d sub-cells (weight length %d) exceeds the tile kernel",
                          side, c.wx);
