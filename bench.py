@@ -347,10 +347,9 @@ def run_lines(args):
         ev[2].record()
         tred.tred_convolve(h, sim.block_ids, sim.n_blocks_dev, sim.qeff, sim.out_blocks)
         ev[3].record()
-        tred.tred_gather_pixels(h, sim.block_ids, sim.n_blocks_dev, sim.out_blocks, sim.pixel_ids, sim.waveforms,
-                                sim.n_pixels_dev)
-        tred.tred_readout(h, sim.rp, sim.pixel_ids, sim.waveforms, sim.n_pixels_dev, sim.hit_pixel, sim.hit_tick,
-                          sim.hit_charge, sim.n_hits_dev)
+        tred.tred_gather_readout(h, sim.block_ids, sim.n_blocks_dev, sim.out_blocks, sim.pixel_ids, sim.waveforms,
+                                 sim.n_pixels_dev, sim.rp, sim.hit_pixel, sim.hit_tick, sim.hit_charge,
+                                 sim.n_hits_dev)
         ev[4].record()
     for _ in range(args.warmup):
         stages([torch.cuda.Event(enable_timing=True) for _ in range(5)])
@@ -584,11 +583,11 @@ def main():
     stream = torch.cuda.current_stream()
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)   # > L2 (126 MB)
 
-    stage_names = ["drift", "blockbin", "effq", "convolve", "gather", "readout"]
+    stage_names = ["drift", "blockbin", "effq", "convolve", "gather+readout"]
 
     def step(events=None):
         h = sim.h
-        ev = events or [None] * 7
+        ev = events or [None] * 6
 
         def rec(i):
             if ev[i] is not None:
@@ -604,12 +603,12 @@ def main():
         rec(3)
         tred.tred_convolve(h, sim.block_ids, sim.n_blocks_dev, sim.qeff, sim.out_blocks)
         rec(4)
-        tred.tred_gather_pixels(h, sim.block_ids, sim.n_blocks_dev, sim.out_blocks, sim.pixel_ids,
-                                sim.waveforms, sim.n_pixels_dev)
+        # a5 + a6: the electrode gather and the readout in one call (the readout skips the
+        # pixels whose positive current cannot reach the threshold)
+        tred.tred_gather_readout(h, sim.block_ids, sim.n_blocks_dev, sim.out_blocks, sim.pixel_ids,
+                                 sim.waveforms, sim.n_pixels_dev, sim.rp, sim.hit_pixel, sim.hit_tick,
+                                 sim.hit_charge, sim.n_hits_dev)
         rec(5)
-        tred.tred_readout(h, sim.rp, sim.pixel_ids, sim.waveforms, sim.n_pixels_dev, sim.hit_pixel,
-                          sim.hit_tick, sim.hit_charge, sim.n_hits_dev)
-        rec(6)
 
     tred.tred_reset_status(sim.h)
     for _ in range(args.warmup):
@@ -623,7 +622,7 @@ def main():
     if world > 1:
         torch.distributed.barrier()
     torch.cuda.synchronize()
-    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(7)] for _ in range(args.steps)]
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(6)] for _ in range(args.steps)]
     launches0 = tred.tred_launch_count(sim.h)
     with ClockSampler(local) as clk:
         time.sleep(0.3)
@@ -635,7 +634,7 @@ def main():
     clocks = clk.summary()
     if world > 1:
         torch.distributed.barrier()
-    step_ms = [evs[k][0].elapsed_time(evs[k][6]) for k in range(args.steps)]
+    step_ms = [evs[k][0].elapsed_time(evs[k][5]) for k in range(args.steps)]
     stage_ms = {nm: statistics.mean(evs[k][i].elapsed_time(evs[k][i + 1]) for k in range(args.steps))
                 for i, nm in enumerate(stage_names)}
     ms = statistics.mean(step_ms)

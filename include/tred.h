@@ -299,6 +299,18 @@ int32_t tred_readout(tred_handle *h, const tred_readout_params *rp,
                      float *hit_charge, int32_t *n_hits_dev, int32_t max_hits,
                      void *stream);
 
+/* a5 + a6 in one call: the outputs of tred_gather_pixels followed by tred_readout on
+ * its waveforms (same arguments, same results).  While the waveforms are written, the
+ * gather records per pixel the sum of the positive current, which bounds the charge
+ * any readout scheme integrates on the pixel; the readout then skips, without reading
+ * them, the pixels whose bound stays below (1 - 1e-4) x threshold (they cannot reach
+ * the threshold; the margin is far above the FP32 rounding of the sums). */
+int32_t tred_gather_readout(tred_handle *h, const int32_t *block_ids, const int32_t *n_blocks_dev,
+                            const float *out_blocks, int32_t *pixel_ids, float *waveforms,
+                            int32_t *n_pixels_dev, const tred_readout_params *rp, int32_t *hit_pixel,
+                            int32_t *hit_tick, float *hit_charge, int32_t *n_hits_dev, int32_t max_hits,
+                            void *stream);
+
 /* ---- Differentiable simulation (Sec. V-C).  Loss L = 1/2 sum (I - I*)^2 over
  * pixels and ticks; gradients through the whole path with the raster windows held
  * fixed (they are piecewise constant) and the quadrature recomputed, not stored.

@@ -34,7 +34,7 @@ EXPORTS = [
     "tred_gather_pixels", "tred_readout", "tred_launch_count", "tred_blockbin_noalloc",
     "tred_set_transport", "tred_residual", "tred_adjoint", "tred_param_grads",
     "tred_drift_events", "tred_effq_range", "tred_convolve_range", "tred_drift_lines", "tred_effq_lines",
-    "tred_wait_selftest",
+    "tred_wait_selftest", "tred_gather_readout",
 ]
 
 
@@ -92,6 +92,8 @@ def load(path: str | None = None) -> ctypes.CDLL:
     lib.tred_reset_status.argtypes = [_P, _P]
     lib.tred_launch_count.argtypes = [_P, ctypes.POINTER(ctypes.c_int64)]
     lib.tred_wait_selftest.argtypes = [_P, ctypes.c_int64, _P]
+    lib.tred_gather_readout.argtypes = [_P, _P, _P, _P, _P, _P, _P, ctypes.POINTER(ReadoutParams), _P, _P, _P, _P,
+                                        _I, _P]
     lib.tred_set_response.argtypes = [_P, _P, _P]
     lib.tred_drift.argtypes = [_P, _I, _P, _P, _P, _P, _P, ctypes.POINTER(Deposits), _P]
     lib.tred_blockbin.argtypes = [_P, _I, ctypes.POINTER(Deposits), _P, _P, _P, _P, _I, _P, _P]

@@ -180,13 +180,15 @@ __device__ __forceinline__ void px_accumulate(const float *__restrict__ out, lon
 // list order, the entries that overlap the step (a fixed order: deterministic, no
 // atomics), and writes every tick of the row (zeros where no block contributes).
 // Optional FP64 accumulation (compensated mode).  A pixel with more than PXW_MAXE
-// entries reads the block map per step instead, in the same order.
+// entries reads the block map per step instead, in the same order.  With `possum` given,
+// also records per row the sum of the positive current (FP32), a bound on the charge
+// any readout scheme can integrate on the pixel.
 template <bool COMP>
 __global__ void __launch_bounds__(PXW_THREADS) k_px_wave(const int32_t *__restrict__ pixel_ids,
                                                          const int32_t *__restrict__ n_pixels_dev,
                                                          const int32_t *__restrict__ slot_of,
                                                          const float *__restrict__ out, GatherConst c,
-                                                         float *__restrict__ wave) {
+                                                         float *__restrict__ wave, float *__restrict__ possum) {
     using Acc = typename std::conditional<COMP, double, float>::type;
     __shared__ PxEntry s_e[PXW_WARPS][PXW_MAXE];
     const int np = n_pixels_dev[0];
@@ -220,6 +222,7 @@ __global__ void __launch_bounds__(PXW_THREADS) k_px_wave(const int32_t *__restri
             }
         __syncwarp();
         float *dst = wave + (size_t)row * c.nt;
+        float pos = 0.f;
         for (int T0 = 0; T0 < c.nt; T0 += PXW_CHUNK) {
             Acc acc[4][4];
 #pragma unroll
@@ -249,10 +252,17 @@ __global__ void __launch_bounds__(PXW_THREADS) k_px_wave(const int32_t *__restri
 #pragma unroll
             for (int i = 0; i < 4; ++i) {
                 const int t = T0 + 128 * i + 4 * lane;
-                if (t < c.nt)
-                    *reinterpret_cast<float4 *>(dst + t) =
-                        make_float4((float)acc[i][0], (float)acc[i][1], (float)acc[i][2], (float)acc[i][3]);
+                if (t < c.nt) {
+                    const float4 o = make_float4((float)acc[i][0], (float)acc[i][1], (float)acc[i][2], (float)acc[i][3]);
+                    *reinterpret_cast<float4 *>(dst + t) = o;
+                    pos += fmaxf(o.x, 0.f) + fmaxf(o.y, 0.f) + fmaxf(o.z, 0.f) + fmaxf(o.w, 0.f);
+                }
             }
+        }
+        if (possum) {
+#pragma unroll
+            for (int o = 16; o; o >>= 1) pos += __shfl_xor_sync(0xffffffffu, pos, o);
+            if (lane == 0) possum[row] = pos;
         }
     }
 }
@@ -267,7 +277,7 @@ __global__ void k_slot_map(const int32_t *__restrict__ block_ids, const int32_t 
 
 int launch_gather(tred_handle *h, const int32_t *block_ids, const int32_t *n_blocks_dev,
                   const float *out, int32_t *pixel_ids, float *wave, int32_t *n_pixels_dev,
-                  cudaStream_t s) {
+                  cudaStream_t s, float *possum) {
     GatherConst c{h->g.npx_x, h->d.npy, h->g.nt, h->g.bp, h->g.bt, h->g.nr, h->g.lt, h->d.R,
                   h->d.nbx, h->d.nby, h->d.nbt, h->p.compensated_gather, h->d.npy_e, h->d.nby_e};
     const int64_t npx = (int64_t)h->g.npx_x * h->d.npy;
@@ -283,9 +293,9 @@ int launch_gather(tred_handle *h, const int32_t *block_ids, const int32_t *n_blo
                                     TRED_ST_PIXEL_OVERFLOW, 4);
     k_px_emit<<<(unsigned)h->pix_chunks, 1024, 0, s>>>(npx, h->pix_flag, h->pix_part, h->max_pixels, pixel_ids);
     if (c.comp)
-        k_px_wave<true><<<sms * 8, PXW_THREADS, 0, s>>>(pixel_ids, n_pixels_dev, h->blk_slot, out, c, wave);
+        k_px_wave<true><<<sms * 8, PXW_THREADS, 0, s>>>(pixel_ids, n_pixels_dev, h->blk_slot, out, c, wave, possum);
     else
-        k_px_wave<false><<<sms * 8, PXW_THREADS, 0, s>>>(pixel_ids, n_pixels_dev, h->blk_slot, out, c, wave);
+        k_px_wave<false><<<sms * 8, PXW_THREADS, 0, s>>>(pixel_ids, n_pixels_dev, h->blk_slot, out, c, wave, possum);
     h->launches += 6;
     return check_cuda(h, cudaGetLastError(), "gather launch");
 }

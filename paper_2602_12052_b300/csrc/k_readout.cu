@@ -164,15 +164,23 @@ __device__ int walk_pixel(const float *__restrict__ I, const RoConst &c, int lan
     return nh;
 }
 
+// With `possum` given (the gather's per-row sum of the positive current), a row whose
+// sum stays below `cut` (the threshold less a margin far above FP32 rounding) cannot reach
+// the threshold in any scheme: its hit count is zero without reading the waveform.
 template <int RM>
 __global__ void __launch_bounds__(256, 2) k_ro_count(const float *__restrict__ wave,
                                                   const int32_t *__restrict__ n_pixels_dev, RoConst c,
                                                   int32_t *__restrict__ cnt, int32_t *__restrict__ tmp_t,
-                                                  float *__restrict__ tmp_c) {
+                                                  float *__restrict__ tmp_c, const float *__restrict__ possum,
+                                                  float cut) {
     const int np = n_pixels_dev[0];
     const int lane = threadIdx.x & 31;
     const int nwarps = (gridDim.x * blockDim.x) >> 5;
     for (int row = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; row < np; row += nwarps) {
+        if (possum && possum[row] < cut) {
+            if (lane == 0) cnt[row] = 0;
+            continue;
+        }
         const float *I = wave + (size_t)row * c.nt;
         const int nh = walk_pixel<RM>(I, c, lane, [&](int k, int t, float q) {
             if (lane == 0 && k < HIT_TMP) {
@@ -220,13 +228,16 @@ __global__ void __launch_bounds__(256, 2) k_ro_emit(const float *__restrict__ wa
 int launch_readout(tred_handle *h, const tred_readout_params &rp, const int32_t *pixel_ids,
                    const float *wave, const int32_t *n_pixels_dev, int32_t *hit_pixel,
                    int32_t *hit_tick, float *hit_charge, int32_t *n_hits_dev, int32_t max_hits,
-                   cudaStream_t s) {
+                   cudaStream_t s, const float *possum) {
+    const float cut = rp.threshold_e > 0.f ? rp.threshold_e * (1.0f - 1e-4f) : -3.0e38f;
     RoConst c{h->g.nt, rp.clock_ticks, rp.hold_ticks, rp.reset_ticks, rp.mode == 1 ? rp.n_samples : 1, rp.threshold_e};
     const int sms = num_sms(h);
     int rc = check_cuda(h, cudaMemsetAsync(h->hit_cnt, 0, sizeof(int32_t) * ((size_t)h->max_pixels + 1), s),
                         "clear hit counts");
     if (rc) return rc;
-    auto count = [&](auto kern) { kern<<<sms * 8, 256, 0, s>>>(wave, n_pixels_dev, c, h->hit_cnt, h->hit_tmp, h->hit_tmpc); };
+    auto count = [&](auto kern) {
+        kern<<<sms * 8, 256, 0, s>>>(wave, n_pixels_dev, c, h->hit_cnt, h->hit_tmp, h->hit_tmpc, possum, cut);
+    };
     if (rp.mode == 2) count(k_ro_count<2>);
     else if (rp.mode == 1) count(k_ro_count<1>);
     else count(k_ro_count<0>);

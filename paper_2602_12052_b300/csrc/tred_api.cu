@@ -197,6 +197,7 @@ int32_t tred_create(const tred_geometry *geom, const tred_params *params, int32_
     alloc((void **)&h->pix_flag, sizeof(int32_t) * (size_t)geom->npx_x * d.npy, "alloc pixel flags");
     h->pix_chunks = ((int64_t)geom->npx_x * d.npy + 1023) / 1024;
     alloc((void **)&h->pix_part, sizeof(int32_t) * (size_t)(h->pix_chunks + 8), "alloc pixel scan");
+    alloc((void **)&h->px_possum, sizeof(float) * ((size_t)max_pixels + 8), "alloc pixel bounds");
     alloc((void **)&h->hit_cnt, sizeof(int32_t) * ((size_t)max_pixels + 8), "alloc hit counts");
     alloc((void **)&h->hit_tmp, sizeof(int32_t) * (size_t)max_pixels * HIT_TMP, "alloc hit cache");
     alloc((void **)&h->hit_tmpc, sizeof(float) * (size_t)max_pixels * HIT_TMP, "alloc hit cache");
@@ -247,7 +248,7 @@ int32_t tred_create(const tred_geometry *geom, const tred_params *params, int32_
 int32_t tred_destroy(tred_handle *h) {
     if (!h) return TRED_ERR_INVALID_ARG;
     void *ptrs[] = {h->dep_event, h->wts2, h->pix_row, h->gspec, h->rhat, h->pair_j, h->wts, h->recs, h->effq_acc, h->dft_hi, h->dft_lo, h->zspec, h->blk_count, h->blk_slot, h->blk_fill,
-                    h->scan_part, h->colmask, h->yspec, h->pix_flag, h->pix_part, h->hit_cnt,
+                    h->scan_part, h->colmask, h->yspec, h->pix_flag, h->pix_part, h->px_possum, h->hit_cnt,
                     h->hit_tmp, h->hit_tmpc, h->status, h->tw};
     for (void *p : ptrs)
         if (p) cudaFree(p);
@@ -487,6 +488,25 @@ int32_t tred_readout(tred_handle *h, const tred_readout_params *rp, const int32_
         return set_error(h, TRED_ERR_INVALID_ARG, "tred_readout: bad readout parameters");
     return launch_readout(h, *rp, pixel_ids, waveforms, n_pixels_dev, hit_pixel, hit_tick, hit_charge,
                           n_hits_dev, max_hits, (cudaStream_t)stream);
+}
+
+int32_t tred_gather_readout(tred_handle *h, const int32_t *block_ids, const int32_t *n_blocks_dev,
+                            const float *out_blocks, int32_t *pixel_ids, float *waveforms, int32_t *n_pixels_dev,
+                            const tred_readout_params *rp, int32_t *hit_pixel, int32_t *hit_tick, float *hit_charge,
+                            int32_t *n_hits_dev, int32_t max_hits, void *stream) {
+    if (!h) return TRED_ERR_INVALID_ARG;
+    if (!block_ids || !n_blocks_dev || !out_blocks || !pixel_ids || !waveforms || !n_pixels_dev || !rp ||
+        !n_hits_dev || max_hits < 0 || (max_hits > 0 && (!hit_pixel || !hit_tick || !hit_charge)))
+        return set_error(h, TRED_ERR_INVALID_ARG, "tred_gather_readout: null pointer");
+    if (rp->clock_ticks < 1 || rp->hold_ticks < 0 || rp->reset_ticks < 0 || rp->mode < 0 || rp->mode > 2 ||
+        (rp->mode == 1 && (rp->n_samples < 1 || rp->hold_ticks < 1)))
+        return set_error(h, TRED_ERR_INVALID_ARG, "tred_gather_readout: bad readout parameters");
+    const cudaStream_t s = (cudaStream_t)stream;
+    const int rc = launch_gather(h, block_ids, n_blocks_dev, out_blocks, pixel_ids, waveforms, n_pixels_dev, s,
+                                 h->px_possum);
+    if (rc) return rc;
+    return launch_readout(h, *rp, pixel_ids, waveforms, n_pixels_dev, hit_pixel, hit_tick, hit_charge, n_hits_dev,
+                          max_hits, s, h->px_possum);
 }
 
 int32_t tred_wait_selftest(tred_handle *h, int64_t limit_cycles, void *stream) {

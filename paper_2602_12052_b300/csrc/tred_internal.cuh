@@ -64,6 +64,7 @@ struct tred_handle {
     int32_t yspec_blocks;
     int32_t *pix_flag;     // [npx_x * npx_y] active pixel flags, then row index
     int32_t *pix_part;     // pixel scan partials
+    float *px_possum;      // [max_pixels] sum of the positive current per pixel row (fused readout)
     int64_t pix_chunks;
     int32_t *hit_cnt;      // [max_pixels + 1] hits per pixel then offsets
     int32_t *hit_tmp;      // [max_pixels][HIT_TMP] cached hits (tick)
@@ -124,11 +125,11 @@ int launch_convolve(tred_handle *h, const int32_t *block_ids, const int32_t *n_b
                     const float *qeff, float *out, int slot_base, int slot_count, cudaStream_t s);
 int launch_gather(tred_handle *h, const int32_t *block_ids, const int32_t *n_blocks_dev,
                   const float *out, int32_t *pixel_ids, float *wave, int32_t *n_pixels_dev,
-                  cudaStream_t s);
+                  cudaStream_t s, float *possum = nullptr);
 int launch_readout(tred_handle *h, const tred_readout_params &rp, const int32_t *pixel_ids,
                    const float *wave, const int32_t *n_pixels_dev, int32_t *hit_pixel,
                    int32_t *hit_tick, float *hit_charge, int32_t *n_hits_dev,
-                   int32_t max_hits, cudaStream_t s);
+                   int32_t max_hits, cudaStream_t s, const float *possum = nullptr);
 
 int launch_residual(tred_handle *h, const int32_t *pix, const int32_t *n_pix_dev, const float *wave,
                     const int32_t *tpix, int n_target, const float *twave, float *resid, double *loss,

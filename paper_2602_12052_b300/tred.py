@@ -166,6 +166,14 @@ def tred_gather_pixels(h: Handle, block_ids, n_blocks_dev, out_blocks, pixel_ids
                                      _stream(stream)))
 
 
+def tred_gather_readout(h: Handle, block_ids, n_blocks_dev, out_blocks, pixel_ids, waveforms, n_pixels_dev,
+                        rp: ReadoutParams, hit_pixel, hit_tick, hit_charge, n_hits_dev, stream=None):
+    h.check(h.lib.tred_gather_readout(h.h, _ptr(block_ids), _ptr(n_blocks_dev), _ptr(out_blocks), _ptr(pixel_ids),
+                                      _ptr(waveforms), _ptr(n_pixels_dev), ctypes.byref(rp), _ptr(hit_pixel),
+                                      _ptr(hit_tick), _ptr(hit_charge), _ptr(n_hits_dev), hit_pixel.numel(),
+                                      _stream(stream)))
+
+
 def tred_readout(h: Handle, rp: ReadoutParams, pixel_ids, waveforms, n_pixels_dev, hit_pixel,
                  hit_tick, hit_charge, n_hits_dev, stream=None):
     h.check(h.lib.tred_readout(h.h, ctypes.byref(rp), _ptr(pixel_ids), _ptr(waveforms),
@@ -273,11 +281,13 @@ class Simulator:
         tred_effq(self.h, n, self.deps, self.block_ids, self.dep_offsets, self.dep_index,
                   self.n_blocks_dev, self.qeff, stream)
         tred_convolve(self.h, self.block_ids, self.n_blocks_dev, self.qeff, self.out_blocks, stream)
-        tred_gather_pixels(self.h, self.block_ids, self.n_blocks_dev, self.out_blocks,
-                           self.pixel_ids, self.waveforms, self.n_pixels_dev, stream)
-        if readout:
-            tred_readout(self.h, self.rp, self.pixel_ids, self.waveforms, self.n_pixels_dev,
-                         self.hit_pixel, self.hit_tick, self.hit_charge, self.n_hits_dev, stream)
+        if readout:      # gather and readout in one call (readout skips pixels that cannot trigger)
+            tred_gather_readout(self.h, self.block_ids, self.n_blocks_dev, self.out_blocks, self.pixel_ids,
+                                self.waveforms, self.n_pixels_dev, self.rp, self.hit_pixel, self.hit_tick,
+                                self.hit_charge, self.n_hits_dev, stream)
+        else:
+            tred_gather_pixels(self.h, self.block_ids, self.n_blocks_dev, self.out_blocks,
+                               self.pixel_ids, self.waveforms, self.n_pixels_dev, stream)
 
     def status(self, stream=None):
         return tred_sync_status(self.h, stream)
@@ -315,11 +325,13 @@ class LineSimulator(Simulator):
         tred_effq_lines(self.h, n, self.deps, self.half[:3 * max(n, 1)], self.block_ids, self.dep_offsets,
                         self.dep_index, self.n_blocks_dev, self.qeff, stream)
         tred_convolve(self.h, self.block_ids, self.n_blocks_dev, self.qeff, self.out_blocks, stream)
-        tred_gather_pixels(self.h, self.block_ids, self.n_blocks_dev, self.out_blocks,
-                           self.pixel_ids, self.waveforms, self.n_pixels_dev, stream)
-        if readout:
-            tred_readout(self.h, self.rp, self.pixel_ids, self.waveforms, self.n_pixels_dev,
-                         self.hit_pixel, self.hit_tick, self.hit_charge, self.n_hits_dev, stream)
+        if readout:      # gather and readout in one call (readout skips pixels that cannot trigger)
+            tred_gather_readout(self.h, self.block_ids, self.n_blocks_dev, self.out_blocks, self.pixel_ids,
+                                self.waveforms, self.n_pixels_dev, self.rp, self.hit_pixel, self.hit_tick,
+                                self.hit_charge, self.n_hits_dev, stream)
+        else:
+            tred_gather_pixels(self.h, self.block_ids, self.n_blocks_dev, self.out_blocks,
+                               self.pixel_ids, self.waveforms, self.n_pixels_dev, stream)
 
 
 class DiffState:
@@ -443,10 +455,8 @@ class BatchSimulator:
             tred_effq_range(h, n, self.deps, self.block_ids, self.dep_offsets, self.dep_index, nb_dev, base,
                             self.chunk, self.qeff, stream)
             tred_convolve_range(h, self.block_ids, nb_dev, base, self.chunk, self.qeff, self.out_blocks, stream)
-        tred_gather_pixels(h, self.block_ids, nb_dev, self.out_blocks, self.pixel_ids, self.waveforms, np_dev,
-                           stream)
-        tred_readout(h, self.rp, self.pixel_ids, self.waveforms, np_dev, self.hit_pixel, self.hit_tick,
-                     self.hit_charge, nh_dev, stream)
+        tred_gather_readout(h, self.block_ids, nb_dev, self.out_blocks, self.pixel_ids, self.waveforms, np_dev,
+                            self.rp, self.hit_pixel, self.hit_tick, self.hit_charge, nh_dev, stream)
 
     def capture(self):
         """Record one step in a CUDA graph (call after a warm-up step)."""

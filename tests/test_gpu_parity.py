@@ -215,6 +215,28 @@ def test_bounded_wait_expires_into_the_status_word():
     assert pixel_rel_errors(res["waveforms"], ref["waveforms"]).max() <= WAVE_TOL
 
 
+@pytest.mark.parametrize("mode,n_samples", [(0, 1), (1, 3), (2, 1)])
+def test_fused_gather_readout_equals_separate_calls(mode, n_samples):
+    """tred_gather_readout (the readout skipping pixels whose positive current cannot
+    reach the threshold) gives exactly the hits of tred_readout over every pixel."""
+    import torch
+    from paper_2602_12052_b300 import tred
+    cfg = synth.get_config("module20", readout_mode=mode, n_samples=n_samples)
+    dep, resp = synth.make_event(cfg)
+    sim = make_sim(cfg, resp, len(dep["x"]), max_blocks=1000, max_pixels=40000)
+    fused = run(sim, dep, keep_qeff=False)
+    assert fused["status"][0] == 0 and fused["n_hits"] > 0
+    hp, ht, hc = (torch.zeros_like(t) for t in (sim.hit_pixel, sim.hit_tick, sim.hit_charge))
+    nh = torch.zeros(1, dtype=torch.int32, device=sim.hit_pixel.device)
+    tred.tred_readout(sim.h, sim.rp, sim.pixel_ids, sim.waveforms, sim.n_pixels_dev, hp, ht, hc, nh)
+    torch.cuda.synchronize()
+    n = int(nh.item())
+    assert n == fused["n_hits"]
+    np.testing.assert_array_equal(hp[:n].cpu().numpy(), fused["hit_pixel"])
+    np.testing.assert_array_equal(ht[:n].cpu().numpy(), fused["hit_tick"])
+    np.testing.assert_array_equal(hc[:n].cpu().numpy(), fused["hit_charge"])
+
+
 def test_repeatable_outputs():
     """Block list, occupancy and pixel list are identical run to run, and so is the
     effective charge, bit for bit (fixed-point accumulation in the tile)."""
