@@ -55,37 +55,11 @@ template <bool SPLIT> struct DgStage {
     static constexpr uint32_t OFF_BAR = OFF_STAGE + DG_ROWS * DG_SROW * 4;
     static constexpr size_t SMEM = OFF_BAR + 64 + 1024;                    // + alignment slack
 };
-constexpr long long DG_WAIT_CYCLES = 2000000000ll;            // ~1 s at 2 GHz
 
 struct DgConst {
     int nch, cols, bt, npairs, G, mpcp;
 };
 
-__device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
-
-__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
-}
-__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
-}
-// bounded wait for the phase with parity `phase` to complete; false once `limit` cycles
-// have passed without it
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t phase, long long limit = DG_WAIT_CYCLES) {
-    const long long t0 = clock64();
-    for (;;) {
-        uint32_t ok;
-        asm volatile(
-            "{\n\t.reg .pred p;\n\t"
-            "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-            "selp.u32 %0, 1, 0, p;\n\t}"
-            : "=r"(ok)
-            : "r"(bar), "r"(phase)
-            : "memory");
-        if (ok) return true;
-        if (clock64() - t0 > limit) return false;
-    }
-}
 
 // Bounded-wait self-test: one thread initialises an mbarrier that expects one arrival
 // which never comes, waits on it for `limit` cycles and reports the expiry in the status

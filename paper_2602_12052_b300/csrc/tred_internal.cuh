@@ -277,6 +277,35 @@ __device__ __forceinline__ float2 mul_w16(float2 x, int m) {
 
 // ---------------------------------------------------------------- tensor memory (TMEM)
 // Allocation by one full warp; the address (lane << 16 | column) lands in shared memory.
+// ---------------------------------------------------------------- mbarriers
+constexpr long long WAIT_CYCLES = 2000000000ll;   // bound of every mbarrier wait (~1 s at 2 GHz)
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
+// bounded wait for the phase with parity `phase` to complete; false once `limit` cycles
+// have passed without it
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t phase, long long limit = WAIT_CYCLES) {
+    const long long t0 = clock64();
+    for (;;) {
+        uint32_t ok;
+        asm volatile(
+            "{\n\t.reg .pred p;\n\t"
+            "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+            "selp.u32 %0, 1, 0, p;\n\t}"
+            : "=r"(ok)
+            : "r"(bar), "r"(phase)
+            : "memory");
+        if (ok) return true;
+        if (clock64() - t0 > limit) return false;
+    }
+}
+
 __device__ __forceinline__ void tmem_alloc(uint32_t *smem_dst, uint32_t ncols) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
                      (uint32_t)__cvta_generic_to_shared(smem_dst)),
