@@ -9,6 +9,9 @@
 //   k_bb_top     one CTA: exclusive scan of the chunk totals; writes nb
 //   k_bb_emit    per chunk: ballot + warp/CTA prefix -> slot of each active block
 //   k_bb_fill    one thread per deposit: CSR fill through per-slot cursors
+//   k_bb_sort    one CTA per active block: the block's deposit ids in ascending order
+//                (the fill leaves them in arrival order), so that every later sum
+//                over a block's deposits runs in one fixed order
 #include "tred_internal.cuh"
 
 namespace tred {
@@ -224,6 +227,88 @@ __global__ void __launch_bounds__(256) k_bb_fill(int n, tred_deposits d, BinGeom
             }
 }
 
+// Ascending sort of each block's deposit ids: a bitonic network whose comparators all
+// point the same way (the first step of each merge pairs mirrored positions), so the
+// list can stand for its power-of-two padding with +infinity that never moves: a
+// comparator whose upper element lies past the end is simply skipped.  A warp sorts a
+// list of up to BB_SORT_WARP ids in its part of shared memory; the CTA then sorts its
+// longer lists together, in shared memory up to BB_SORT_CTA ids, else in place in global
+// memory (the CTA alone owns the list and synchronises between steps).
+constexpr int BB_SORT_THREADS = 256;
+constexpr int BB_SORT_WARP = 1024;
+constexpr int BB_SORT_CTA = (BB_SORT_THREADS / 32) * BB_SORT_WARP;
+
+// threads t = 0 .. nt - 1 of the calling group sort key[0 .. n); sync() separates the steps
+template <typename Sync>
+__device__ void bitonic_ascending(int32_t *key, int n, int t, int nt, Sync sync) {
+    int P = 1;
+    while (P < n) P <<= 1;
+    for (int k = 2; k <= P; k <<= 1) {
+        for (int j = k >> 1, lj = __ffs(k) - 2; j >= 1; j >>= 1, --lj) {   // j = 2^lj
+            for (int i = t; i < P / 2; i += nt) {
+                const int lo = ((i >> lj) << (lj + 1)) | (i & (j - 1));
+                const int hi = j == (k >> 1) ? (lo ^ (k - 1)) : lo + j;   // mirror pair on a merge's first step
+                if (hi < n) {
+                    const int32_t a = key[lo], b = key[hi];
+                    if (b < a) {
+                        key[lo] = b;
+                        key[hi] = a;
+                    }
+                }
+            }
+            sync();
+        }
+    }
+}
+
+__global__ void __launch_bounds__(BB_SORT_THREADS) k_bb_sort(const int32_t *__restrict__ n_blocks_dev,
+                                                            const int32_t *__restrict__ dep_offsets,
+                                                            int32_t *__restrict__ dep_index, int32_t max_pairs,
+                                                            int32_t max_blocks) {
+    __shared__ int32_t key[BB_SORT_CTA];
+    __shared__ int big[BB_SORT_THREADS / 32 * 8];
+    __shared__ int nbig;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int nb = min(n_blocks_dev[0], max_blocks);
+    const int per = gridDim.x * (BB_SORT_THREADS / 32);
+    for (int base = blockIdx.x * (BB_SORT_THREADS / 32); base < nb; base += per) {
+        if (threadIdx.x == 0) nbig = 0;
+        __syncthreads();
+        // one list per warp
+        const int slot = base + warp;
+        if (slot < nb) {
+            const int beg = min(dep_offsets[slot], max_pairs), end = min(dep_offsets[slot + 1], max_pairs);
+            const int n = end - beg;
+            if (n > BB_SORT_WARP) {
+                if (lane == 0) big[atomicAdd(&nbig, 1)] = slot;
+            } else if (n > 1) {
+                int32_t *kw = key + warp * BB_SORT_WARP;
+                for (int i = lane; i < n; i += 32) kw[i] = dep_index[beg + i];
+                __syncwarp();
+                bitonic_ascending(kw, n, lane, 32, [] { __syncwarp(); });
+                for (int i = lane; i < n; i += 32) dep_index[beg + i] = kw[i];
+            }
+        }
+        __syncthreads();
+        // the longer lists, one at a time by the whole CTA
+        for (int q = 0; q < nbig; ++q) {
+            const int sl = big[q];
+            const int beg = min(dep_offsets[sl], max_pairs), end = min(dep_offsets[sl + 1], max_pairs);
+            const int n = end - beg;
+            auto bar = [] { __syncthreads(); };
+            if (n <= BB_SORT_CTA) {
+                for (int i = threadIdx.x; i < n; i += BB_SORT_THREADS) key[i] = dep_index[beg + i];
+                __syncthreads();
+                bitonic_ascending(key, n, threadIdx.x, BB_SORT_THREADS, bar);
+                for (int i = threadIdx.x; i < n; i += BB_SORT_THREADS) dep_index[beg + i] = key[i];
+                __syncthreads();
+            } else {
+                bitonic_ascending(dep_index + beg, n, threadIdx.x, BB_SORT_THREADS, bar);
+            }
+        }
+    }
+}
+
 // Zero-block case: dep_offsets[0] = 0 must still hold.
 __global__ void k_bb_offsets0(int32_t *dep_offsets, const int32_t *n_blocks_dev) {
     if (n_blocks_dev[0] == 0) dep_offsets[0] = 0;
@@ -246,7 +331,10 @@ int launch_blockbin(tred_handle *h, int n, const tred_deposits &deps, int32_t *b
     if (n > 0)
         k_bb_fill<<<(n + 255) / 256, 256, 0, s>>>(n, deps, g, h->blk_slot, dep_offsets, h->blk_fill,
                                                   dep_index, max_pairs);
-    h->launches += 4 + (n > 0 ? 2 : 0);
+    if (n > 0)
+        k_bb_sort<<<num_sms(h) * 4, BB_SORT_THREADS, 0, s>>>(n_blocks_dev, dep_offsets, dep_index, max_pairs,
+                                                            h->max_blocks);
+    h->launches += 4 + (n > 0 ? 3 : 0);
     return check_cuda(h, cudaGetLastError(), "blockbin launch");
 }
 
@@ -332,5 +420,11 @@ extern "C" int32_t tred_blockbin_noalloc(const tred_geometry *geom, int32_t n, c
     if (n > 0)
         k_bb_fill<<<(n + 255) / 256, 256, 0, s>>>(n, *deps, bg, slot_of, dep_offsets, fill, dep_index,
                                                   max_pairs);
+    if (n > 0) {
+        int dev = 0, sms = 0;
+        if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+            return TRED_ERR_CUDA;
+        k_bb_sort<<<sms * 4, BB_SORT_THREADS, 0, s>>>(n_blocks_dev, dep_offsets, dep_index, max_pairs, max_blocks);
+    }
     return cudaGetLastError() == cudaSuccess ? TRED_OK : TRED_ERR_CUDA;
 }

@@ -14,8 +14,8 @@
 //                   support [lo-1, hi+1], stored contiguously per deposit
 //   k_effq_blocks   CTAs take active blocks from a queue; 32-tick tiles of the
 //                   block's sub-cell plane accumulated in registers per 8 x 4 patch
-//                   from per-tile deposit buckets, exact integer sums; plus the mask
-//                   of non-empty (py, px) columns per channel
+//                   from the tile's deposit list, in the list's fixed order; plus the
+//                   mask of non-empty (py, px) columns per channel
 #include "tred_internal.cuh"
 
 namespace tred {
@@ -153,44 +153,37 @@ __global__ void __launch_bounds__(256) k_effq_weights(int n, tred_deposits d, Ef
 //
 // The block's sub-cell plane is cut into 8 x 4 patches (gx x gy); a lane owns one
 // sub-cell of a patch with that cell's 32 ticks in registers, and the warps of the
-// CTA take patches one by one.  Per tile the CTA lists, in shared memory, the
-// deposits whose support meets the tile (clipped ranges, scaled charge, the tile's 32
-// time weights, and the clipped x and y weight vectors copied into a pool) and sorts
-// the list into per-patch buckets (count, scan, fill), so a warp walks only the
-// deposits that reach its patch.  No cell is written by two threads: no atomics on
-// data and no shared-memory tile; each lane writes its 32 ticks as four 32-byte
-// sectors of the [jy][jx][py][px][t] layout.
+// CTA take patches one by one.  Per tile the CTA lists, in shared memory, the deposits
+// whose support meets the tile (clipped ranges, charge, the tile's 32 time weights,
+// and the clipped x and y weight vectors copied into a pool).  A warp walks the list
+// 32 entries at a time, keeps (ballot) the ones that reach its patch and adds
+// q e_x e_y e_t of each to its cells with one FP32 FMA per tick (a zero factor outside
+// the entry's support).  No cell is written by two threads: no atomics and no
+// shared-memory tile; each lane writes its 32 ticks as four 32-byte sectors of the
+// [jy][jx][py][px][t] layout.
 //
-// The sums are exact integers.  Every contribution q e_x e_y e_t has magnitude at
-// most q m_x m_y m_t, where m_a is the deposit's largest weight on axis a inside
-// the block; with M the largest such bound and B their sum, the scale
-// S = min(2^22 / M, 2^31 / B) (less a small margin) keeps each scaled contribution
-// below 2^22, where fma(a, w, 1.5 * 2^23) rounds it to the nearest integer in the
-// low mantissa bits, and each cell's sum below 2^31.  Integer sums do not depend on
-// the order of the deposits, so the block's effective charge is bitwise
-// reproducible; the rounding is at most 1 / (2 S) per contribution.
+// The order of every sum is fixed: the deposits of a block come sorted by index
+// (tred_blockbin), the tile list keeps that order and each patch takes its deposits
+// in list order, so Q^eff is bitwise reproducible.
 //
-// A tile whose list would exceed the shared-memory capacities (entries, pool,
-// bucket slots) is processed in passes, each a contiguous run of the block's
-// deposit list chosen by a block-wide scan; the integer partial sums of the cells
-// are kept in a per-CTA global scratch between passes.
+// A tile whose list would exceed the shared-memory capacities (entries, pool) is
+// processed in passes, each a contiguous run of the block's deposit list chosen by a
+// block-wide scan; the partial sums of the cells are kept in a per-CTA global scratch
+// between passes.
 constexpr int EQ_TT = 32;
 constexpr int EQ_WARPS = 8;
 constexpr int EQ_THREADS = EQ_WARPS * 32;
 constexpr int EQ_CTAS_PER_SM = 2;
 constexpr int EQ_LIST = 256;                 // tile-list entries per pass
 constexpr int EQ_POOL = 8192;                // weight-pool floats per pass
-constexpr int EQ_INS = 4096;                 // bucket slots per pass
 constexpr int EQ_PX = 8, EQ_PY = 4;          // patch: 8 gx x 4 gy sub-cells
 constexpr int EQ_MAX_SIDE = 128;             // bp * n_sub
 constexpr int EQ_MAX_PATCH = (EQ_MAX_SIDE / EQ_PX) * (EQ_MAX_SIDE / EQ_PY);
-constexpr int EQ_TERMS = 1024;               // bound terms kept in shared memory
-constexpr float EQ_MAGIC = 12582912.0f;      // 1.5 * 2^23
-constexpr int EQ_MAGIC_BITS = 0x4B400000;
 
 struct TileEnt {
     int y0, y1, x0, x1;          // block-local clipped ranges
-    int qs, wxo, wyo, idx;       // q * S (float bits); pool offsets of the x and y weights; deposit
+    int q, wxo, wyo, wmax;       // charge (float bits); pool offsets of the x and y weights; largest
+                                 // time weight of the tile (float bits)
     float wt[EQ_TT];             // time weights of the tile's ticks, zero outside the support
 };
 static_assert(sizeof(TileEnt) == 32 + 4 * EQ_TT, "tile list entry");
@@ -199,28 +192,22 @@ struct EffqShared {
     TileEnt list[EQ_LIST];
     int2 wsrc[EQ_LIST];                  // per entry: offsets of its clipped x and y weights in wts
     float pool[EQ_POOL];
-    uint16_t bucket[EQ_INS];
-    int boff[EQ_MAX_PATCH + 1];
-    int bfill[EQ_MAX_PATCH];
-    uint32_t nzp[EQ_MAX_PATCH];          // per patch: lanes whose cell is non-zero in some tile
+    int wl[EQ_WARPS][32];                // per warp: the list entries of its patch in one 32-entry chunk
+    uint32_t nzp[EQ_MAX_PATCH];          // per patch: cells that are non-zero in some tile
     int offx[EQ_MAX_SIDE], offy[EQ_MAX_SIDE];   // output offsets of block-local gx and gy
     unsigned long long mask[128];        // per channel: non-empty (py, px) columns (n_sub^2 <= 128)
     uint32_t cov[EQ_MAX_SIDE * EQ_MAX_SIDE / 32];   // sub-cell columns covered by a support
     uint8_t pcov[EQ_MAX_PATCH];                       // patch has a covered column
     uint16_t alist[EQ_MAX_PATCH];                     // the patches written at all, in order
     int nactive;
-    float term[EQ_TERMS];                             // bound terms of the block's first deposits
     unsigned long long part[EQ_WARPS * 3];
-    int tot[4];                          // list entries, pool floats, bucket slots, accepted count
+    int tot[4];                          // list entries, pool floats
     int slot, next;
+    float flush;                         // contributions below this are left out
 };
 
 // two CTAs per SM: 228 KB of shared memory per SM, 1 KB reserved per CTA
 static_assert(2 * (sizeof(EffqShared) + 1024) <= 233472, "effq shared memory must leave room for two CTAs per SM");
-
-__device__ __forceinline__ int fx_round(float a, float w) {
-    return __float_as_int(fmaf(a, w, EQ_MAGIC)) - EQ_MAGIC_BITS;
-}
 
 __global__ void __launch_bounds__(EQ_THREADS, EQ_CTAS_PER_SM) k_effq_blocks(
     const int32_t *__restrict__ block_ids, const int32_t *__restrict__ dep_offsets,
@@ -237,8 +224,8 @@ __global__ void __launch_bounds__(EQ_THREADS, EQ_CTAS_PER_SM) k_effq_blocks(
     const int npatch = npx * ((side + EQ_PY - 1) / EQ_PY);
     const int len_cap = min(c.wx, side);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int lx = lane & (EQ_PX - 1), ly = lane >> 3;
-    int32_t *scratch = acc_scratch + (size_t)blockIdx.x * side * side * EQ_TT;
+    const int lx = lane & (EQ_PX - 1), ly = lane >> 3;   // the lane's cell of a patch
+    float *scratch = reinterpret_cast<float *>(acc_scratch) + (size_t)blockIdx.x * side * side * EQ_TT;
     for (int g = tid; g < side; g += EQ_THREADS) {
         const int pg = g / c.ns, jg = g - pg * c.ns;
         S.offx[g] = (jg * cols + pg) * c.bt;                   // jx, px
@@ -258,54 +245,34 @@ __global__ void __launch_bounds__(EQ_THREADS, EQ_CTAS_PER_SM) k_effq_blocks(
         const int X0 = bx * side, Y0 = by * side, T0 = bt * c.bt;
         float *qblk = qeff + (size_t)(slot - slot_base) * nch * cols * c.bt;   // the caller's buffer row
         const int beg = dep_offsets[slot], end = dep_offsets[slot + 1];
-        // bound terms: each deposit's largest weight product inside the block, times |q|;
-        // M = their maximum, B = their sum rounded up to multiples of M / 2^20 (an
-        // integer sum, so neither depends on the order of the deposit list)
-        auto term = [&](int k) -> float {
-            const DepRec r = recs[dep_index[k]];
-            const int xa = max(r.x0, X0), xb = min(r.x1, X0 + side - 1);
-            const int ya = max(r.y0, Y0), yb = min(r.y1, Y0 + side - 1);
-            const int ta = max(r.t0, T0), tb = min(r.t1, T0 + c.bt - 1);
-            if (xa > xb || ya > yb || ta > tb) return 0.f;
-            const float *w = wts + (size_t)r.idx * c.wstride;
-            float mx = 0.f, my = 0.f, mt = 0.f;
-            for (int g = xa; g <= xb; ++g) mx = fmaxf(mx, fabsf(__ldg(w + (g - r.gx0))));
-            for (int g = ya; g <= yb; ++g) my = fmaxf(my, fabsf(__ldg(w + c.wx + (g - r.gy0))));
-            for (int g = ta; g <= tb; ++g) mt = fmaxf(mt, fabsf(__ldg(w + 2 * c.wx + (g - r.gt0))));
-            return fabsf(r.q) * mx * my * mt;
-        };
-        float tmax = 0.f;
-        for (int k = beg + tid; k < end; k += EQ_THREADS) {
-            const float tv = term(k);
-            if (k - beg < EQ_TERMS) S.term[k - beg] = tv;
-            tmax = fmaxf(tmax, tv);
-        }
+        // flush level: 2^-23 of the largest single contribution inside the block (|q| times
+        // each axis' largest weight within the block); a deposit's contribution to a cell
+        // that stays below it over a whole tile is under the FP32 resolution of the block's
+        // sums and is left out, so that columns holding only such tails stay empty for the
+        // convolution
+        {
+            float pm = 0.f;
+            for (int k = beg + tid; k < end; k += EQ_THREADS) {
+                const DepRec r = recs[dep_index[k]];
+                const int xa = max(r.x0, X0), xb = min(r.x1, X0 + side - 1);
+                const int ya = max(r.y0, Y0), yb = min(r.y1, Y0 + side - 1);
+                const int ta = max(r.t0, T0), tb = min(r.t1, T0 + c.bt - 1);
+                if (xa > xb || ya > yb || ta > tb) continue;
+                const float *w = wts + (size_t)r.idx * c.wstride;
+                float mx = 0.f, my = 0.f, mt = 0.f;
+                for (int g = xa; g <= xb; ++g) mx = fmaxf(mx, fabsf(__ldg(w + (g - r.gx0))));
+                for (int g = ya; g <= yb; ++g) my = fmaxf(my, fabsf(__ldg(w + c.wx + (g - r.gy0))));
+                for (int g = ta; g <= tb; ++g) mt = fmaxf(mt, fabsf(__ldg(w + 2 * c.wx + (g - r.gt0))));
+                pm = fmaxf(pm, fabsf(r.q) * mx * my * mt);
+            }
 #pragma unroll
-        for (int o = 16; o; o >>= 1) tmax = fmaxf(tmax, __shfl_xor_sync(0xffffffffu, tmax, o));
-        if (lane == 0) reinterpret_cast<float *>(S.part)[warp] = tmax;
-        __syncthreads();
-        float M = 0.f;
+            for (int o = 16; o; o >>= 1) pm = fmaxf(pm, __shfl_xor_sync(0xffffffffu, pm, o));
+            float *pw = reinterpret_cast<float *>(S.part);
+            if (lane == 0) pw[warp] = pm;
+            __syncthreads();
 #pragma unroll
-        for (int k = 0; k < EQ_WARPS; ++k) M = fmaxf(M, reinterpret_cast<const float *>(S.part)[k]);
-        unsigned long long units = 0ull;
-        if (M > 0.f) {
-            const float to_units = 1048576.0f / M;
-            for (int k = beg + tid; k < end; k += EQ_THREADS)
-                units += (unsigned long long)ceilf((k - beg < EQ_TERMS ? S.term[k - beg] : term(k)) * to_units) + 1ull;
-        }
-#pragma unroll
-        for (int o = 16; o; o >>= 1) units += __shfl_xor_sync(0xffffffffu, units, o);
-        __syncthreads();                                     // everyone has read M
-        if (lane == 0) S.part[warp] = units;
-        __syncthreads();
-        unsigned long long usum = 0ull;
-#pragma unroll
-        for (int k = 0; k < EQ_WARPS; ++k) usum += S.part[k];
-        float scale = 0.f, inv_scale = 0.f;
-        if (M > 0.f) {
-            const float B = (float)usum * (M * (1.0f / 1048576.0f)) * 1.0001f;
-            scale = fminf(4194304.0f / M, 2147483648.0f / B) * (1.0f - 1.0f / 1024.0f);
-            inv_scale = 1.0f / scale;
+            for (int k = 0; k < EQ_WARPS; ++k) pm = fmaxf(pm, pw[k]);
+            if (tid == 0) S.flush = pm * 1.1920928955078125e-7f;   // 2^-23 (read after later barriers)
         }
         if (c.skip_empty) {
             // columns (gy, gx) covered by some deposit's clipped support: the others stay
@@ -363,15 +330,15 @@ __global__ void __launch_bounds__(EQ_THREADS, EQ_CTAS_PER_SM) k_effq_blocks(
             bool first = true;
             do {   // one pass: a contiguous run [cur, ...) of the block's deposit list
                 __syncthreads();                           // the previous pass is consumed
-                if (tid < 3) S.tot[tid] = 0;
-                for (int k = tid; k < npatch; k += EQ_THREADS) S.bfill[k] = 0;
+                if (tid < 2) S.tot[tid] = 0;
+                if (tid == 0) S.next = 0;
                 __syncthreads();
                 bool full = false;
                 while (cur < end && !full) {
-                    // (1) evaluate one chunk of the list: overlap, pool floats, bucket slots
+                    // (1) evaluate one chunk of the list: overlap and pool floats
                     const int k = cur + tid;
                     DepRec r;
-                    int xa = 0, xb = -1, ya = 0, yb = -1, cnt = 0, pl = 0, ins = 0;
+                    int xa = 0, xb = -1, ya = 0, yb = -1, cnt = 0, pl = 0;
                     if (k < end) {
                         r = recs[dep_index[k]];
                         if (!(r.t1 < ta || r.t0 > tb)) {
@@ -384,25 +351,23 @@ __global__ void __launch_bounds__(EQ_THREADS, EQ_CTAS_PER_SM) k_effq_blocks(
                             if (xa <= xb && ya <= yb) {
                                 cnt = 1;
                                 pl = (xb - xa + 1) + (yb - ya + 1);
-                                ins = (yb / EQ_PY - ya / EQ_PY + 1) * (xb / EQ_PX - xa / EQ_PX + 1);
                             }
                         }
                     }
-                    // block-wide inclusive scan of (cnt, pl, ins)
-                    int c1 = cnt, c2 = pl, c3 = ins;
+                    // block-wide inclusive scan of (cnt, pl)
+                    int c1 = cnt, c2 = pl;
 #pragma unroll
                     for (int o = 1; o < 32; o <<= 1) {
                         const int u1 = __shfl_up_sync(0xffffffffu, c1, o);
                         const int u2 = __shfl_up_sync(0xffffffffu, c2, o);
-                        const int u3 = __shfl_up_sync(0xffffffffu, c3, o);
-                        if (lane >= o) { c1 += u1; c2 += u2; c3 += u3; }
+                        if (lane >= o) { c1 += u1; c2 += u2; }
                     }
-                    int *wp = reinterpret_cast<int *>(S.part);   // [EQ_WARPS][3]
-                    if (lane == 31) { wp[3 * warp] = c1; wp[3 * warp + 1] = c2; wp[3 * warp + 2] = c3; }
+                    int *wp = reinterpret_cast<int *>(S.part);   // [EQ_WARPS][2]
+                    if (lane == 31) { wp[2 * warp] = c1; wp[2 * warp + 1] = c2; }
                     __syncthreads();
-                    for (int w2 = 0; w2 < warp; ++w2) { c1 += wp[3 * w2]; c2 += wp[3 * w2 + 1]; c3 += wp[3 * w2 + 2]; }
-                    const int b1 = S.tot[0], b2 = S.tot[1], b3 = S.tot[2];
-                    const bool fits = (b1 + c1 <= EQ_LIST) && (b2 + c2 <= EQ_POOL) && (b3 + c3 <= EQ_INS);
+                    for (int w2 = 0; w2 < warp; ++w2) { c1 += wp[2 * w2]; c2 += wp[2 * w2 + 1]; }
+                    const int b1 = S.tot[0], b2 = S.tot[1];
+                    const bool fits = (b1 + c1 <= EQ_LIST) && (b2 + c2 <= EQ_POOL);
                     const int acc_n = __syncthreads_count(fits);   // prefix: the totals only grow
                     if (fits && cnt) {
                         const int pos = b1 + c1 - 1, po = b2 + c2 - pl;
@@ -412,54 +377,31 @@ __global__ void __launch_bounds__(EQ_THREADS, EQ_CTAS_PER_SM) k_effq_blocks(
                         en.y1 = yb;
                         en.x0 = xa;
                         en.x1 = xb;
-                        en.qs = __float_as_int(r.q * scale);
+                        en.q = __float_as_int(r.q);
                         en.wxo = po;
                         en.wyo = po + (xb - xa + 1);
-                        en.idx = r.idx;
                         S.wsrc[pos] = make_int2((int)(base + (X0 + xa - r.gx0)), (int)(base + c.wx + (Y0 + ya - r.gy0)));
+                        float wm = 0.f;
 #pragma unroll
                         for (int e = 0; e < EQ_TT; ++e) {
                             const int t = ta + e;
                             en.wt[e] = (t >= r.t0 && t <= r.t1) ? __ldg(wts + base + 2 * c.wx + (t - r.gt0)) : 0.f;
+                            wm = fmaxf(wm, fabsf(en.wt[e]));
                         }
+                        en.wmax = __float_as_int(wm);
                         int4 *dst = reinterpret_cast<int4 *>(&S.list[pos]);
                         const int4 *src = reinterpret_cast<const int4 *>(&en);
 #pragma unroll
                         for (int q = 0; q < (int)(sizeof(TileEnt) / 16); ++q) dst[q] = src[q];
-                        for (int qy = ya / EQ_PY; qy <= yb / EQ_PY; ++qy)
-                            for (int qx = xa / EQ_PX; qx <= xb / EQ_PX; ++qx) atomicAdd(&S.bfill[qy * npx + qx], 1);
                     }
-                    if (tid == acc_n - 1) { S.tot[0] = b1 + c1; S.tot[1] = b2 + c2; S.tot[2] = b3 + c3; }
+                    if (tid == acc_n - 1) { S.tot[0] = b1 + c1; S.tot[1] = b2 + c2; }
                     __syncthreads();
                     cur += acc_n;
                     full = acc_n < EQ_THREADS;             // chunk cut short: capacity reached
                 }
                 const int ne = S.tot[0];
                 const bool last = cur >= end;
-                // (2) warp 0: bucket offsets; all warps: copy the clipped weight vectors
-                if (warp == 0) {
-                    int carry = 0;
-                    for (int b0 = 0; b0 < npatch; b0 += 32) {
-                        const int k = b0 + lane;
-                        const int v = k < npatch ? S.bfill[k] : 0;
-                        int incl = v;
-#pragma unroll
-                        for (int o = 1; o < 32; o <<= 1) {
-                            const int u = __shfl_up_sync(0xffffffffu, incl, o);
-                            if (lane >= o) incl += u;
-                        }
-                        if (k < npatch) {
-                            S.boff[k] = carry + incl - v;
-                            S.bfill[k] = 0;
-                        }
-                        carry += __shfl_sync(0xffffffffu, incl, 31);
-                    }
-                    if (lane == 0) {
-                        S.boff[npatch] = carry;
-                        S.next = 0;
-                    }
-                }
-                // the clipped x and y weight vectors of the entries, two entries' loads in
+                // (2) the clipped x and y weight vectors of the entries, two entries' loads in
                 // flight per warp (their source offsets were kept when the entries were made)
                 for (int k0 = warp; k0 < ne; k0 += 2 * EQ_WARPS) {
                     float vx[2], vy[2];
@@ -489,18 +431,10 @@ __global__ void __launch_bounds__(EQ_THREADS, EQ_CTAS_PER_SM) k_effq_blocks(
                     }
                 }
                 __syncthreads();
-                // (3) bucket fill
-                for (int k = tid; k < ne; k += EQ_THREADS) {
-                    const int4 hy = *reinterpret_cast<const int4 *>(&S.list[k].y0);   // y0 y1 x0 x1
-                    for (int qy = hy.x / EQ_PY; qy <= hy.y / EQ_PY; ++qy)
-                        for (int qx = hy.z / EQ_PX; qx <= hy.w / EQ_PX; ++qx) {
-                            const int b = qy * npx + qx;
-                            S.bucket[S.boff[b] + atomicAdd(&S.bfill[b], 1)] = (uint16_t)k;
-                        }
-                }
-                __syncthreads();
-                // (4) patches, taken one by one by the warps from the list of written patches
+                // (3) patches, taken one by one by the warps from the list of written patches
                 const int nact = S.nactive;
+                const float flush = S.flush;
+                int *wl = S.wl[warp];
                 for (;;) {
                     int pi = 0;
                     if (lane == 0) pi = atomicAdd(&S.next, 1);
@@ -508,71 +442,74 @@ __global__ void __launch_bounds__(EQ_THREADS, EQ_CTAS_PER_SM) k_effq_blocks(
                     if (pi >= nact) break;
                     const int pt = S.alist[pi];
                     const int qy = pt / npx, qx = pt - qy * npx;
-                    const int gx = qx * EQ_PX + lx, gy = qy * EQ_PY + ly;
+                    const int px0 = qx * EQ_PX, py0 = qy * EQ_PY;
+                    const int gx = px0 + lx, gy = py0 + ly;
                     const bool own = gx < side && gy < side;
-                    int32_t *sc = scratch + ((size_t)gy * side + gx) * EQ_TT;
-                    int acc[EQ_TT];
+                    float *sc = scratch + ((size_t)gy * side + gx) * EQ_TT;
+                    float acc[EQ_TT];
                     if (first || !own) {
 #pragma unroll
-                        for (int e = 0; e < EQ_TT; ++e) acc[e] = 0;
+                        for (int e = 0; e < EQ_TT; ++e) acc[e] = 0.f;
                     } else {
 #pragma unroll
                         for (int e4 = 0; e4 < EQ_TT; e4 += 4) {
-                            const int4 u = reinterpret_cast<const int4 *>(sc)[e4 / 4];
+                            const float4 u = reinterpret_cast<const float4 *>(sc)[e4 / 4];
                             acc[e4] = u.x; acc[e4 + 1] = u.y; acc[e4 + 2] = u.z; acc[e4 + 3] = u.w;
                         }
                     }
-                    const int kb = S.boff[pt], ke = S.boff[pt + 1];
-                    if (kb == ke && first && last) {
-                        // no deposit reaches the patch in this tile: zeros where written at all
-                        const int cb = gy * side + gx;
-                        if (c.skip_empty && !S.pcov[pt]) continue;
-                        if (own && (!c.skip_empty || ((S.cov[cb >> 5] >> (cb & 31)) & 1u))) {
-                            float4 *dst = reinterpret_cast<float4 *>(qblk + S.offy[gy] + S.offx[gx] + tt);
-                            const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
-#pragma unroll
-                            for (int e4 = 0; e4 < EQ_TT; e4 += 4) dst[e4 / 4] = z4;
+                    // the tile list in order, 32 entries at a time: the ones that reach the
+                    // patch, then each of them added to the lane's cell (zero outside its support)
+                    for (int c0 = 0; c0 < ne; c0 += 32) {
+                        const int k = c0 + lane;
+                        bool ov = false;
+                        if (k < ne) {
+                            const int4 hy = *reinterpret_cast<const int4 *>(&S.list[k].y0);   // y0 y1 x0 x1
+                            ov = hy.z <= px0 + EQ_PX - 1 && hy.w >= px0 && hy.x <= py0 + EQ_PY - 1 && hy.y >= py0;
                         }
-                        continue;
-                    }
-                    for (int kk = kb; kk < ke; ++kk) {
-                        const TileEnt &en = S.list[S.bucket[kk]];
-                        const int4 hy = *reinterpret_cast<const int4 *>(&en.y0);     // y0 y1 x0 x1
-                        const int4 hq = *reinterpret_cast<const int4 *>(&en.qs);     // qs wxo wyo
-                        if (gy >= hy.x && gy <= hy.y && gx >= hy.z && gx <= hy.w) {
-                            const float a = __int_as_float(hq.x) * S.pool[hq.y + gx - hy.z] * S.pool[hq.z + gy - hy.x];
+                        const unsigned bal = __ballot_sync(0xffffffffu, ov);
+                        if (!bal) continue;
+                        if (ov) wl[__popc(bal & ((1u << lane) - 1u))] = k;
+                        __syncwarp();
+                        const int cnt = __popc(bal);
+                        for (int s = 0; s < cnt; ++s) {
+                            const TileEnt &en = S.list[wl[s]];
+                            const int4 hy = *reinterpret_cast<const int4 *>(&en.y0);   // y0 y1 x0 x1
+                            const int4 hq = *reinterpret_cast<const int4 *>(&en.q);    // q wxo wyo wmax
+                            const bool in = gx >= hy.z && gx <= hy.w && gy >= hy.x && gy <= hy.y;
+                            const float wx = S.pool[in ? hq.y + gx - hy.z : 0], wy = S.pool[in ? hq.z + gy - hy.x : 0];
+                            const float a0 = __int_as_float(hq.x) * wx * wy;
+                            // a contribution that stays below the flush level at every tick of the
+                            // tile is under the FP32 resolution of the block's sums: left out
+                            const float a = (in && fabsf(a0) * __int_as_float(hq.w) >= flush) ? a0 : 0.f;
 #pragma unroll
                             for (int e4 = 0; e4 < EQ_TT; e4 += 4) {
                                 const float4 w = *reinterpret_cast<const float4 *>(&en.wt[e4]);
-                                acc[e4] += fx_round(a, w.x);
-                                acc[e4 + 1] += fx_round(a, w.y);
-                                acc[e4 + 2] += fx_round(a, w.z);
-                                acc[e4 + 3] += fx_round(a, w.w);
+                                acc[e4] = fmaf(a, w.x, acc[e4]);
+                                acc[e4 + 1] = fmaf(a, w.y, acc[e4 + 1]);
+                                acc[e4 + 2] = fmaf(a, w.z, acc[e4 + 2]);
+                                acc[e4 + 3] = fmaf(a, w.w, acc[e4 + 3]);
                             }
                         }
+                        __syncwarp();                          // wl is rewritten by the next chunk
                     }
                     if (!last) {
                         if (own) {
 #pragma unroll
                             for (int e4 = 0; e4 < EQ_TT; e4 += 4)
-                                reinterpret_cast<int4 *>(sc)[e4 / 4] = make_int4(acc[e4], acc[e4 + 1], acc[e4 + 2], acc[e4 + 3]);
+                                reinterpret_cast<float4 *>(sc)[e4 / 4] = make_float4(acc[e4], acc[e4 + 1], acc[e4 + 2], acc[e4 + 3]);
                         }
                         continue;
                     }
-                    int any = 0;
-                    float v[EQ_TT];
+                    bool any = false;
 #pragma unroll
-                    for (int e = 0; e < EQ_TT; ++e) {
-                        any |= acc[e];
-                        v[e] = (float)acc[e] * inv_scale;
-                    }
-                    const uint32_t bal = __ballot_sync(0xffffffffu, own && any != 0);
+                    for (int e = 0; e < EQ_TT; ++e) any |= acc[e] != 0.f;
+                    const uint32_t bal = __ballot_sync(0xffffffffu, own && any);
                     if (lane == 0 && bal) S.nzp[pt] |= bal;       // this warp alone holds patch pt now
                     const int cb = gy * side + gx;
                     if (own && (!c.skip_empty || ((S.cov[cb >> 5] >> (cb & 31)) & 1u))) {
                         float4 *dst = reinterpret_cast<float4 *>(qblk + S.offy[gy] + S.offx[gx] + tt);
 #pragma unroll
-                        for (int e4 = 0; e4 < EQ_TT; e4 += 4) dst[e4 / 4] = make_float4(v[e4], v[e4 + 1], v[e4 + 2], v[e4 + 3]);
+                        for (int e4 = 0; e4 < EQ_TT; e4 += 4) dst[e4 / 4] = make_float4(acc[e4], acc[e4 + 1], acc[e4 + 2], acc[e4 + 3]);
                     }
                 }
                 first = false;
@@ -640,11 +577,10 @@ int launch_effq(tred_handle *h, int n, const tred_deposits &deps, const int32_t 
     const int nch = c.ns * c.ns;
     const int side = c.bp * c.ns;
     const int len_cap = c.wx < side ? c.wx : side;
-    const int max_ins = ((len_cap + EQ_PY - 2) / EQ_PY + 1) * ((len_cap + EQ_PX - 2) / EQ_PX + 1);
     if ((size_t)h->max_deposits * (size_t)c.wstride >= ((size_t)1 << 32))
         return set_error(h, TRED_ERR_INVALID_ARG, "effq: %d deposits x %d weights exceed 32-bit offsets",
                          h->max_deposits, c.wstride);
-    if (side > EQ_MAX_SIDE || nch > 128 || 2 * len_cap > EQ_POOL || max_ins > EQ_INS)
+    if (side > EQ_MAX_SIDE || nch > 128 || 2 * len_cap > EQ_POOL)
         return set_error(h, TRED_ERR_INVALID_ARG, "effq: bp * n_sub = %d sub-cells (weight length %d) exceeds the tile kernel",
                          side, c.wx);
     const size_t smem = sizeof(EffqShared);

@@ -308,4 +308,56 @@ int launch_scan_small(tred_handle *h, int64_t n, int32_t *part, int32_t cap, int
     return check_cuda(h, cudaGetLastError(), "scan launch");
 }
 
+// Exclusive scan of a long array in three passes: the sum of every 1024-entry chunk (one
+// CTA each), the single-CTA scan of those sums (total, cap and overflow flag as
+// k_scan_small), then each chunk's own scan plus its offset.
+__device__ __forceinline__ int block_incl_scan1024(int v, int *s) {
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    int x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int t = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += t;
+    }
+    if (lane == 31) s[warp] = x;
+    __syncthreads();
+    if (warp == 0) {
+        int w = s[lane];
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int t = __shfl_up_sync(0xffffffffu, w, o);
+            if (lane >= o) w += t;
+        }
+        s[lane] = w;
+    }
+    __syncthreads();
+    return x + (warp ? s[warp - 1] : 0);
+}
+__global__ void __launch_bounds__(1024) k_chunk_sum(int64_t n, const int32_t *__restrict__ part,
+                                                    int32_t *__restrict__ sums) {
+    __shared__ int s[32];
+    const int64_t i = (int64_t)blockIdx.x * 1024 + threadIdx.x;
+    const int x = block_incl_scan1024(i < n ? part[i] : 0, s);
+    if (threadIdx.x == 1023) sums[blockIdx.x] = x;
+}
+__global__ void __launch_bounds__(1024) k_chunk_apply(int64_t n, int32_t *__restrict__ part,
+                                                      const int32_t *__restrict__ sums, int nchunks) {
+    __shared__ int s[32];
+    const int64_t i = (int64_t)blockIdx.x * 1024 + threadIdx.x;
+    const int v = i < n ? part[i] : 0;
+    const int x = block_incl_scan1024(v, s);
+    if (i < n) part[i] = sums[blockIdx.x] + x - v;
+    if (blockIdx.x == 0 && threadIdx.x == 0) part[n] = sums[nchunks];
+}
+int launch_scan_large(tred_handle *h, int64_t n, int32_t *part, int32_t *sums, int32_t cap, int32_t *count_dev,
+                      int flag, int word, cudaStream_t s) {
+    const int nchunks = (int)((n + 1023) / 1024);
+    if (nchunks < 1) return launch_scan_small(h, n, part, cap, count_dev, flag, word, s);
+    k_chunk_sum<<<nchunks, 1024, 0, s>>>(n, part, sums);
+    k_scan_small<<<1, 1024, 0, s>>>(nchunks, sums, cap, count_dev, h->status, flag, word);
+    k_chunk_apply<<<nchunks, 1024, 0, s>>>(n, part, sums, nchunks);
+    h->launches += 3;
+    return check_cuda(h, cudaGetLastError(), "scan launch");
+}
+
 }  // namespace tred

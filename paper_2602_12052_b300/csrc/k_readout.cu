@@ -23,7 +23,7 @@
 
 namespace tred {
 
-int launch_scan_small(tred_handle *h, int64_t n, int32_t *part, int32_t cap, int32_t *count_dev,
+int launch_scan_large(tred_handle *h, int64_t n, int32_t *part, int32_t *sums, int32_t cap, int32_t *count_dev,
                       int flag, int word, cudaStream_t s);
 
 struct RoConst {
@@ -241,7 +241,9 @@ int launch_readout(tred_handle *h, const tred_readout_params &rp, const int32_t 
     if (rp.mode == 2) count(k_ro_count<2>);
     else if (rp.mode == 1) count(k_ro_count<1>);
     else count(k_ro_count<0>);
-    rc = launch_scan_small(h, h->max_pixels, h->hit_cnt, max_hits, n_hits_dev, TRED_ST_HIT_OVERFLOW, 5, s);
+    // chunk sums after the counts and their total (max_pixels + 8 words)
+    rc = launch_scan_large(h, h->max_pixels, h->hit_cnt, h->hit_cnt + (size_t)h->max_pixels + 8, max_hits, n_hits_dev,
+                           TRED_ST_HIT_OVERFLOW, 5, s);
     if (rc) return rc;
     auto emit = [&](auto kern) {
         kern<<<sms * 8, 256, 0, s>>>(wave, pixel_ids, n_pixels_dev, c, h->hit_cnt, h->hit_tmp, h->hit_tmpc, max_hits,

@@ -198,7 +198,8 @@ int32_t tred_create(const tred_geometry *geom, const tred_params *params, int32_
     h->pix_chunks = ((int64_t)geom->npx_x * d.npy + 1023) / 1024;
     alloc((void **)&h->pix_part, sizeof(int32_t) * (size_t)(h->pix_chunks + 8), "alloc pixel scan");
     alloc((void **)&h->px_possum, sizeof(float) * ((size_t)max_pixels + 8), "alloc pixel bounds");
-    alloc((void **)&h->hit_cnt, sizeof(int32_t) * ((size_t)max_pixels + 8), "alloc hit counts");
+    alloc((void **)&h->hit_cnt, sizeof(int32_t) * ((size_t)max_pixels + 8 + (size_t)max_pixels / 1024 + 8),
+          "alloc hit counts");   // counts and their scan, then the scan's chunk sums
     alloc((void **)&h->hit_tmp, sizeof(int32_t) * (size_t)max_pixels * HIT_TMP, "alloc hit cache");
     alloc((void **)&h->hit_tmpc, sizeof(float) * (size_t)max_pixels * HIT_TMP, "alloc hit cache");
     alloc((void **)&h->status, sizeof(int32_t) * TRED_STATUS_WORDS, "alloc status");

@@ -66,7 +66,7 @@ struct tred_handle {
     int32_t *pix_part;     // pixel scan partials
     float *px_possum;      // [max_pixels] sum of the positive current per pixel row (fused readout)
     int64_t pix_chunks;
-    int32_t *hit_cnt;      // [max_pixels + 1] hits per pixel then offsets
+    int32_t *hit_cnt;      // [max_pixels + 1] hits per pixel then offsets; from max_pixels + 8 the scan's chunk sums
     int32_t *hit_tmp;      // [max_pixels][HIT_TMP] cached hits (tick)
     float *hit_tmpc;       // [max_pixels][HIT_TMP] cached hits (charge)
     int32_t *status;       // [TRED_STATUS_WORDS]

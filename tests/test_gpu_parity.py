@@ -238,17 +238,32 @@ def test_fused_gather_readout_equals_separate_calls(mode, n_samples):
 
 
 def test_repeatable_outputs():
-    """Block list, occupancy and pixel list are identical run to run, and so is the
-    effective charge, bit for bit (fixed-point accumulation in the tile)."""
+    """Block list, occupancy, deposit lists and pixel list are identical run to run,
+    and so are the effective charge and the currents, bit for bit (each block's
+    deposits are sorted and every sum runs in one fixed order)."""
     cfg = synth.get_config("tiny")
     dep, resp = synth.make_event(cfg)
     sim = make_sim(cfg, resp, len(dep["x"]))
     a = run(sim, dep)
     b = run(sim, dep)
-    for k in ("block_ids", "block_counts", "pixel_ids", "dep_offsets"):
+    for k in ("block_ids", "block_counts", "pixel_ids", "dep_offsets", "dep_index", "qeff", "waveforms"):
         np.testing.assert_array_equal(a[k], b[k])
-    np.testing.assert_array_equal(np.sort(a["dep_index"]), np.sort(b["dep_index"]))
-    np.testing.assert_array_equal(a["qeff"], b["qeff"])
+
+
+def test_block_deposit_lists_ascending_like_oracle():
+    """Each block's deposit list is the oracle's, in ascending deposit order (Sec. III-B-1),
+    on the tiny event and on a module plane with blocks of a few hundred deposits."""
+    for name, n_tracks in (("tiny", None), ("module200", 40)):
+        cfg = synth.get_config(name) if n_tracks is None else synth.get_config(name, n_tracks=n_tracks)
+        dep, resp = synth.make_event(cfg)
+        sim = make_sim(cfg, resp, len(dep["x"]), max_blocks=min(cfg.n_blocks, 4000), max_pixels=200000)
+        res = run(sim, dep, readout=False, keep_qeff=False, keep_waves=False)
+        p = oracle.params(cfg)
+        d = oracle.drift(p, dep)
+        off, idx = res["dep_offsets"], res["dep_index"]
+        assert len(res["block_ids"]) > 0
+        for s, blk in enumerate(res["block_ids"]):
+            np.testing.assert_array_equal(idx[off[s]:off[s + 1]], oracle.block_deposits(p, d, int(blk)))
 
 
 # ------------------------------------------------------------------ full size, sampled
