@@ -223,9 +223,9 @@ int32_t tred_effq_lines(tred_handle *h, int32_t n, const tred_deposits *deps, co
 /* a2. Block-sparse binning (Sec. III-B-1).  A block is active iff the clipped
  * support box of some deposit intersects it; its count is the number of such
  * deposits.  Output (device): block_ids[nb] ascending, block_counts[nb],
- * dep_offsets[nb + 1] (CSR), dep_index[pairs] (deposit ids of each block, in no
- * particular order within a block), n_blocks_dev[0] = nb.  Capacities: max_blocks
- * (tred_create) and max_pairs. */
+ * dep_offsets[nb + 1] (CSR), dep_index[pairs] (deposit ids of each block, ascending
+ * within a block), n_blocks_dev[0] = nb.  Capacities: max_blocks (tred_create) and
+ * max_pairs. */
 int32_t tred_blockbin(tred_handle *h, int32_t n, const tred_deposits *deps,
                       int32_t *block_ids, int32_t *block_counts, int32_t *dep_offsets,
                       int32_t *dep_index, int32_t max_pairs, int32_t *n_blocks_dev,
@@ -235,7 +235,11 @@ int32_t tred_blockbin(tred_handle *h, int32_t n, const tred_deposits *deps,
  * per axis e[g] = sum_C sum_l (w_l / 2) phi(C + xi_l / 2) u_l(g - C) (Gauss-Legendre)
  * or the exact tent integral (effq_mode 1); Qeff = q e_x e_y e_t summed over the
  * block's deposits.  qeff_dev: [max_blocks][n_sub][n_sub][bp][bp][bt] float32,
- * index [slot][jy][jx][py][px][t], grid point gx = (bx bp + px) n_sub + jx. */
+ * index [slot][jy][jx][py][px][t], grid point gx = (bx bp + px) n_sub + jx.  Each
+ * cell is summed in FP32 over the block's deposits in the order of dep_index (ascending
+ * as tred_blockbin writes it), so the result is bitwise reproducible; a deposit's
+ * contribution to a cell that stays below 2^-23 of the block's largest single
+ * contribution over a 32-tick tile is left out. */
 int32_t tred_effq(tred_handle *h, int32_t n, const tred_deposits *deps,
                   const int32_t *block_ids, const int32_t *dep_offsets,
                   const int32_t *dep_index, const int32_t *n_blocks_dev, float *qeff,
