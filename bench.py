@@ -80,6 +80,10 @@ def _args():
                     help="step: one event (default); batched: 64 uneven events, autotuned, CUDA graph; "
                          "adjoint: forward + backward; spill: 35 planes in sequence")
     ap.add_argument("--events", type=int, default=64)
+    ap.add_argument("--graph", action="store_true",
+                    help="step mode: time the step replayed from a CUDA graph (the launch sequence is "
+                         "fixed and every count stays on the device); the per-stage times come from "
+                         "the eager steps")
     ap.add_argument("--readout-mode", type=int, default=0, choices=[0, 1, 2],
                     help="0: trigger-reset (default); 1: successive digitisations without resets "
                          "(--n-samples per trigger); 2: fixed-charge integration")
@@ -638,6 +642,33 @@ def main():
     stage_ms = {nm: statistics.mean(evs[k][i].elapsed_time(evs[k][i + 1]) for k in range(args.steps))
                 for i, nm in enumerate(stage_names)}
     ms = statistics.mean(step_ms)
+
+    # the same step recorded once in a CUDA graph and replayed: no host launch overhead
+    graph = None
+    if args.graph:
+        side = torch.cuda.Stream()
+        side.wait_stream(stream)
+        graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(graph, stream=side):
+            step()
+        stream.wait_stream(side)
+        for _ in range(args.warmup):
+            graph.replay()
+        torch.cuda.synchronize()
+        g_ms = []
+        for k in range(args.steps):
+            flush.zero_()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            graph.replay()
+            b.record(stream)
+            b.synchronize()
+            g_ms.append(a.elapsed_time(b))
+        status = tred.tred_sync_status(sim.h)
+        if status[0] != 0:
+            raise RuntimeError(f"device status after the graph replays: {status}")
+        eager_ms, ms = ms, statistics.mean(g_ms)
+
     n_job, ms = aggregate_replicas(n, ms, world, dev)
     value = n_job / (ms / 1e3)
 
@@ -659,7 +690,10 @@ def main():
             a.record(stream)
             for kk in x:
                 x[kk].copy_(host[kk], non_blocking=True)
-            step()
+            if graph is not None:
+                graph.replay()
+            else:
+                step()
             h_counts.copy_(sim.counts, non_blocking=True)
             h_hp.copy_(sim.hit_pixel, non_blocking=True)
             h_ht.copy_(sim.hit_tick, non_blocking=True)
@@ -707,6 +741,7 @@ def main():
                        "deposits": n, "active_blocks": nb, "active_pixels": npix, "hits": nh,
                        **({"deposits_all_ranks": int(n_job)} if world > 1 else {}),
                        "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
+                       **({"launch": f"CUDA graph replay (eager step {eager_ms:.3f} ms)"} if graph is not None else {}),
                        "l2": "flushed between timed steps (256 MB write, outside the step events)"},
             "stages_ms": stage_ms, "set_response_ms": set_response_ms,
             "gpu_launches": launches, "clocks": clocks, "roofline": roofline, "e2e": e2e,
