@@ -314,7 +314,9 @@ int32_t tred_adjoint(tred_handle *h, int32_t n, const tred_deposits *deps, const
         !pixel_ids || !n_pixels_dev || !resid || !dqeff)
         return set_error(h, TRED_ERR_INVALID_ARG, "tred_adjoint: null pointer");
     if (!h->wts2) {   // first call: adjoint scratch
-        h->adj_chunk = h->max_blocks < 32 ? h->max_blocks : 32;
+        // blocks per backward sub-batch: 256 keep every SM busy over ~14 waves of (block,
+        // class) items (32 left the second of two waves three quarters full), 3.4 GB of spectra
+        h->adj_chunk = h->max_blocks < 256 ? h->max_blocks : 256;
         const size_t b1 = sizeof(float) * 3 * (size_t)h->max_deposits * h->d.wstride;
         const size_t b2 = sizeof(int32_t) * (size_t)h->g.npx_x * h->d.npy;
         const size_t b3 = sizeof(float2) * (size_t)h->adj_chunk * h->d.npairs * h->g.lt * 64;
