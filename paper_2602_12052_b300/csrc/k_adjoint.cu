@@ -13,7 +13,8 @@
 //                   impact at the flipped column (Eq. multch read backwards)
 //   k_adj_weights   per deposit: the 1-D weights and their derivatives in mu, sigma
 //   k_adj_chain     per (block, deposit): sums of dL/dQeff against the separable
-//                   weights and derivatives -> dL/d(q, mu, sigma) (windows fixed)
+//                   weights and derivatives -> dL/d(q, mu, sigma) (windows fixed), the
+//                   lanes along time so that the gradient loads cover whole sectors
 //   k_adj_params    chain rule through the transport step to dL/d(x, y, t0, ne) and
 //                   the global dL/d(DL, DT, tau)
 #include "tred_internal.cuh"
@@ -409,21 +410,34 @@ __global__ void __launch_bounds__(256) k_adj_weights(int n, tred_deposits d, Cha
     }
 }
 
-// One warp per (block, deposit) pair of the CSR: lanes over the deposit's (gy, gx)
-// columns inside the block, each summing along time.
-__global__ void __launch_bounds__(256) k_adj_chain(const int32_t *__restrict__ block_ids,
+// One warp per (block, deposit) pair of the CSR.  The lanes run along time (W
+// consecutive ticks, W the window's length rounded up to a power of two, at most 32)
+// and over 32 / W columns at once, so each load of dL/dQeff covers whole sectors; per
+// pixel-row gy the sums over the row's columns are kept apart and multiplied by the
+// row's y factors once:
+//   s = sum_gy fy(gy) sum_gx fx(gx) sum_t dL/dQeff(gx, gy, t) ft(t)
+// for the seven combinations of value and derivative factors.
+constexpr int CH_MAX_SIDE = 128;   // bp * n_sub
+__global__ void __launch_bounds__(256, 2) k_adj_chain(const int32_t *__restrict__ block_ids,
                                                    const int32_t *__restrict__ dep_offsets,
                                                    const int32_t *__restrict__ dep_index,
                                                    const int32_t *__restrict__ n_blocks_dev, tred_deposits d,
                                                    ChainConst c, const float *__restrict__ wts2,
                                                    const int32_t *__restrict__ dep_event,
                                                    const float *__restrict__ gq, float *__restrict__ grad7) {
+    __shared__ int offx[CH_MAX_SIDE], offy[CH_MAX_SIDE];   // offsets of block-local gx and gy in a slot
+    const int side = c.bp * c.ns, cols = c.bp * c.bp;
+    for (int g = threadIdx.x; g < side; g += blockDim.x) {
+        const int pg = g / c.ns, jg = g - pg * c.ns;
+        offx[g] = (jg * cols + pg) * c.bt;                   // jx, px
+        offy[g] = (jg * c.ns * cols + pg * c.bp) * c.bt;     // jy, py
+    }
+    __syncthreads();
     const int nb = n_blocks_dev[0];
     if (nb <= 0) return;
     const int total = dep_offsets[nb];
     const int lane = threadIdx.x & 31;
     const int nwarps = (gridDim.x * blockDim.x) >> 5;
-    const int side = c.bp * c.ns, cols = c.bp * c.bp;
     for (int k = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; k < total; k += nwarps) {
         // slot of CSR entry k: binary search in dep_offsets
         int lo = 0, hi = nb - 1;
@@ -446,31 +460,47 @@ __global__ void __launch_bounds__(256) k_adj_chain(const int32_t *__restrict__ b
         if (xa > xb || ya > yb || ta > tb) continue;
         const float *w = wts2 + (size_t)i * 3 * c.wstride;
         const float *ex = w, *ey = w + c.wx, *et = w + 2 * c.wx;
-        const int nx = xb - xa + 1, ncol = nx * (yb - ya + 1);
+        const float *gblk = gq + (size_t)slot * c.nch * cols * c.bt - T0;
+        const int ntw = tb - ta + 1, ncol = (xb - xa + 1) * (yb - ya + 1);
+        // W = 2^lw lanes along time: the width with the fewest lane passes over the
+        // window, ceil(ntw / W) time chunks times ceil(ncol W / 32) column groups
+        int lw = 2, best = 1 << 30;
+        for (int l = 2; l <= 5; ++l) {
+            const int passes = ((ntw + (1 << l) - 1) >> l) * (((ncol << l) + 31) >> 5);
+            if (passes < best) best = passes, lw = l;
+        }
+        const int W = 1 << lw, tl = lane & (W - 1), cl = lane >> lw, cpg = 32 >> lw;
         float s[7] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-        for (int cc = lane; cc < ncol; cc += 32) {
-            const int gy = ya + cc / nx, gx = xa + cc % nx;
-            const int lgy = gy - Y0, lgx = gx - X0;
-            const int jy = lgy % c.ns, py = lgy / c.ns, jx = lgx % c.ns, px = lgx / c.ns;
-            const float *g = gq + (((size_t)slot * c.nch + jy * c.ns + jx) * cols + py * c.bp + px) * c.bt - T0;
-            float t0 = 0.f, t1 = 0.f, t2 = 0.f;
-            for (int t = ta; t <= tb; ++t) {
-                const float gv = g[t];
-                const int gi = t - (lot - 1);
-                t0 = fmaf(gv, et[gi], t0);
-                t1 = fmaf(gv, et[c.wstride + gi], t1);
-                t2 = fmaf(gv, et[2 * c.wstride + gi], t2);
+        for (int t0 = ta; t0 <= tb; t0 += W) {
+            const int t = t0 + tl;
+            const bool tok = t <= tb;
+            const int gi = t - (lot - 1);
+            const float e0 = tok ? et[gi] : 0.f, e1 = tok ? et[c.wstride + gi] : 0.f, e2 = tok ? et[2 * c.wstride + gi] : 0.f;
+            for (int gy = ya; gy <= yb; ++gy) {
+                const float *grow = gblk + offy[gy - Y0] + t;
+                float r0 = 0.f, r1 = 0.f, r2 = 0.f, rb = 0.f, rc = 0.f;
+#pragma unroll 4
+                for (int gx = xa + cl; gx <= xb; gx += cpg) {
+                    const float gv = tok ? grow[offx[gx - X0]] : 0.f;
+                    const float A = gv * e0, B = gv * e1, C = gv * e2;
+                    const int ix = gx - (lox - 1);
+                    const float vx = ex[ix], dmx = ex[c.wstride + ix], dsx = ex[2 * c.wstride + ix];
+                    r0 = fmaf(vx, A, r0);
+                    r1 = fmaf(dmx, A, r1);
+                    r2 = fmaf(dsx, A, r2);
+                    rb = fmaf(vx, B, rb);
+                    rc = fmaf(vx, C, rc);
+                }
+                const int iy = gy - (loy - 1);
+                const float vy = ey[iy], dmy = ey[c.wstride + iy], dsy = ey[2 * c.wstride + iy];
+                s[0] = fmaf(vy, r0, s[0]);
+                s[1] = fmaf(vy, r1, s[1]);
+                s[2] = fmaf(dmy, r0, s[2]);
+                s[3] = fmaf(vy, rb, s[3]);
+                s[4] = fmaf(vy, r2, s[4]);
+                s[5] = fmaf(dsy, r0, s[5]);
+                s[6] = fmaf(vy, rc, s[6]);
             }
-            const int ix = gx - (lox - 1), iy = gy - (loy - 1);
-            const float vx = ex[ix], dmx = ex[c.wstride + ix], dsx = ex[2 * c.wstride + ix];
-            const float vy = ey[iy], dmy = ey[c.wstride + iy], dsy = ey[2 * c.wstride + iy];
-            s[0] = fmaf(vx * vy, t0, s[0]);
-            s[1] = fmaf(dmx * vy, t0, s[1]);
-            s[2] = fmaf(vx * dmy, t0, s[2]);
-            s[3] = fmaf(vx * vy, t1, s[3]);
-            s[4] = fmaf(dsx * vy, t0, s[4]);
-            s[5] = fmaf(vx * dsy, t0, s[5]);
-            s[6] = fmaf(vx * vy, t2, s[6]);
         }
 #pragma unroll
         for (int q = 0; q < 7; ++q)
