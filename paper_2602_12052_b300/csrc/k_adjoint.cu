@@ -49,17 +49,34 @@ __global__ void __launch_bounds__(256) k_resid(const int32_t *__restrict__ pix, 
             const float *a = wave + (size_t)row * nt;
             const float *b = tr >= 0 ? twave + (size_t)tr * nt : nullptr;
             float *o = resid + (size_t)row * nt;
-            for (int t = lane; t < nt; t += 32) {
-                const float v = a[t] - (b ? b[t] : 0.f);
-                o[t] = v;
-                acc += 0.5 * (double)v * v;
+            // squares summed in FP32 eight at a time, the partial sums in FP64
+            for (int t0 = lane; t0 < nt; t0 += 32 * 8) {
+                float part = 0.f;
+#pragma unroll
+                for (int u = 0; u < 8; ++u) {
+                    const int t = t0 + 32 * u;
+                    if (t < nt) {
+                        const float v = a[t] - (b ? b[t] : 0.f);
+                        o[t] = v;
+                        part = fmaf(v, v, part);
+                    }
+                }
+                acc += 0.5 * (double)part;
             }
         } else {
             // target pixels the current pass does not reach: constant part of L
             const int tr = row - np;
             if (find_sorted(pix, np, tpix[tr]) >= 0) continue;
             const float *b = twave + (size_t)tr * nt;
-            for (int t = lane; t < nt; t += 32) acc += 0.5 * (double)b[t] * b[t];
+            for (int t0 = lane; t0 < nt; t0 += 32 * 8) {
+                float part = 0.f;
+#pragma unroll
+                for (int u = 0; u < 8; ++u) {
+                    const int t = t0 + 32 * u;
+                    if (t < nt) part = fmaf(b[t], b[t], part);
+                }
+                acc += 0.5 * (double)part;
+            }
         }
     }
 #pragma unroll
