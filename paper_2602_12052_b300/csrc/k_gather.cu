@@ -147,6 +147,37 @@ struct PxEntry {
     int t0;
 };
 
+// The output of an entry at ticks t = T0 + 128 i + 4 lane + (0..3), i < 4 (zero outside its
+// range [t0, t0 + span)).
+__device__ __forceinline__ void px_load(const float *__restrict__ out, long long off, int t0e, int T0, int lane,
+                                        int span, float4 (&v)[4]) {
+    const float *src = out + off;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const int tl = T0 + 128 * i + 4 * lane - t0e;     // multiple of 4
+        if (tl >= 0 && tl + 3 < span) {
+            v[i] = *reinterpret_cast<const float4 *>(src + tl);
+        } else if (tl + 3 < 0 || tl >= span) {
+            v[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+        } else {
+            v[i].x = (tl >= 0 && tl < span) ? src[tl] : 0.f;
+            v[i].y = (tl + 1 >= 0 && tl + 1 < span) ? src[tl + 1] : 0.f;
+            v[i].z = (tl + 2 >= 0 && tl + 2 < span) ? src[tl + 2] : 0.f;
+            v[i].w = (tl + 3 >= 0 && tl + 3 < span) ? src[tl + 3] : 0.f;
+        }
+    }
+}
+template <typename Acc>
+__device__ __forceinline__ void px_add(Acc (&acc)[4][4], const float4 (&v)[4]) {
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        acc[i][0] += v[i].x;
+        acc[i][1] += v[i].y;
+        acc[i][2] += v[i].z;
+        acc[i][3] += v[i].w;
+    }
+}
+
 // Sum, for ticks t = T0 + 128 i + 4 lane + (0..3), i < 4, the listed entries' outputs in
 // list order (entries whose range [t0, t0 + span) misses the chunk add nothing).
 template <typename Acc>
@@ -230,10 +261,24 @@ __global__ void __launch_bounds__(PXW_THREADS) k_px_wave(const int32_t *__restri
 #pragma unroll
                 for (int e = 0; e < 4; ++e) acc[i][e] = 0;
             if (ne <= PXW_MAXE) {
-                for (int k = 0; k < ne; ++k) {
-                    const PxEntry en = E[k];
-                    if (en.t0 >= T0 + PXW_CHUNK || en.t0 + span <= T0) continue;
-                    px_accumulate(out, en.off, en.t0, T0, lane, span, acc);
+                // the entries that overlap the step, two at a time with all eight loads in
+                // flight before either is added (still in list order)
+                int k = 0;
+                for (;;) {
+                    while (k < ne && (E[k].t0 >= T0 + PXW_CHUNK || E[k].t0 + span <= T0)) ++k;
+                    if (k >= ne) break;
+                    const PxEntry ea = E[k++];
+                    while (k < ne && (E[k].t0 >= T0 + PXW_CHUNK || E[k].t0 + span <= T0)) ++k;
+                    float4 va[4], vb[4];
+                    px_load(out, ea.off, ea.t0, T0, lane, span, va);
+                    if (k < ne) {
+                        const PxEntry eb = E[k++];
+                        px_load(out, eb.off, eb.t0, T0, lane, span, vb);
+                        px_add(acc, va);
+                        px_add(acc, vb);
+                    } else {
+                        px_add(acc, va);
+                    }
                 }
             } else {
                 const int bt_lo = max(0, floordiv(T0 - span, c.bt) + 1);
