@@ -182,6 +182,25 @@ def test_dense_block_multipass():
     assert res["block_counts"].max() > 1024
 
 
+def test_very_dense_block_sorted_in_global_memory():
+    """9000 deposits packed into one block: the block's deposit list is longer than the
+    binning's shared-memory sort holds (8192), so it is sorted in place in global memory;
+    the list must still be the oracle's, ascending, and the currents the oracle's."""
+    cfg = synth.get_config("tiny")
+    resp = synth.make_response(cfg)
+    rng = np.random.default_rng(22)
+    n = 9000
+    dep = _dep(rng.uniform(4.0, 6.4, n), rng.uniform(4.0, 6.4, n), rng.uniform(0.8, 1.2, n), t0=2.0,
+               ne=rng.uniform(100.0, 900.0, n))
+    res, ref, _ = _full_check(cfg, dep, resp, check_readout=False)
+    assert res["block_counts"].max() > 8192
+    p = oracle.params(cfg)
+    d = oracle.drift(p, dep)
+    off, idx = res["dep_offsets"], res["dep_index"]
+    for s_, blk in enumerate(res["block_ids"]):
+        np.testing.assert_array_equal(idx[off[s_]:off[s_ + 1]], oracle.block_deposits(p, d, int(blk)))
+
+
 def test_capacity_overflow_sets_status():
     cfg = synth.get_config("tiny")
     dep, resp = synth.make_event(cfg)
