@@ -192,7 +192,10 @@ int32_t tred_create(const tred_geometry *geom, const tred_params *params, int32_
     h->nchunks = (d.nblk + 1023) / 1024;
     alloc((void **)&h->scan_part, sizeof(int32_t) * (size_t)(2 * h->nchunks + 8), "alloc scan");
     alloc((void **)&h->colmask, sizeof(uint64_t) * (size_t)max_blocks * ns * ns, "alloc masks");
-    h->yspec_blocks = max_blocks < 1024 ? max_blocks : 1024;
+    // blocks per convolution launch pair: 8192 (8.6 GB of spectra at lt = 512) puts a
+    // module plane in one launch, so the spectral kernel's last partial wave of
+    // (block, class) items comes once per call rather than once per 1024 blocks
+    h->yspec_blocks = max_blocks < 8192 ? max_blocks : 8192;
     alloc((void **)&h->yspec, sizeof(float2) * (size_t)h->yspec_blocks * geom->lt * LP * LP, "alloc yspec");
     alloc((void **)&h->pix_flag, sizeof(int32_t) * (size_t)geom->npx_x * d.npy, "alloc pixel flags");
     h->pix_chunks = ((int64_t)geom->npx_x * d.npy + 1023) / 1024;
