@@ -10,7 +10,8 @@
 // Without MPCP each impact is its own (real) channel and out[u] = Re C[...].
 //
 // Work split (B300: 148 SMs, 227 KB shared memory per CTA):
-//   k_conv_spec   one CTA (512 threads) per (block, time-frequency class k1):
+//   k_conv_spec   one CTA (512 threads) per (block, time-frequency class k1), the
+//                 persistent CTAs taking the items from a queue:
 //                 the class owns the 64 bins f = k1 + G k2.  Stage A computes, per
 //                 column, the time DFT restricted to the class (an in-lane
 //                 pre-butterfly over the nonzero n1 = 0..bt/64-1 blocks of the
@@ -75,7 +76,7 @@ __global__ void __launch_bounds__(SPEC_THREADS, 1)
                 const uint64_t *__restrict__ colmask, const float2 *__restrict__ rhat,
                 const int32_t *__restrict__ pair_j, const float2 *__restrict__ tw, ConvConst c,
                 float2 *__restrict__ yspec, int slot_base, int slot_count, int qbase,
-                const float2 *__restrict__ zspec) {
+                const float2 *__restrict__ zspec, int32_t *__restrict__ queue) {
     constexpr int LT = 64 * G;
     extern __shared__ float2 smem[];
     float2 *zt = smem;                                // [PG][64][8][9]
@@ -112,7 +113,13 @@ __global__ void __launch_bounds__(SPEC_THREADS, 1)
     float2 *tb = tbuf + warp * 2 * TB_BIN;
     float2 *eb = ebuf + warp * 2 * EP_BIN;
 
-    for (int item = blockIdx.x; item < items; item += gridDim.x) {
+    // items are taken from a queue (their stage A cost varies with the block's non-empty columns)
+    for (;;) {
+        __syncthreads();
+        if (tid == 0) s_ntask[2] = atomicAdd(queue, 1);
+        __syncthreads();
+        const int item = s_ntask[2];
+        if (item >= items) break;
         const int sl = item / G, k1 = item % G;
         const int slot = slot_base + sl;
         // zero the stage A buffers (the previous epilogue used them; rows and columns
@@ -470,6 +477,8 @@ static int run_conv(tred_handle *h, const int32_t *n_blocks_dev, const float *qe
     }
     const int sms = num_sms(h);
     const bool tc = h->p.conv_mode != 0;
+    // the item queue counter: a word after the effective charge's per-CTA scratch
+    int32_t *queue = h->effq_acc + (effq_scratch_bytes(h->g.bp * h->g.n_sub, sms) / sizeof(int32_t) - 48);
     const int chunk = tc ? h->zspec_blocks : h->yspec_blocks;
     const int end = slot_base + slot_count;
     for (int base = slot_base; base < end; base += chunk) {
@@ -477,13 +486,17 @@ static int run_conv(tred_handle *h, const int32_t *n_blocks_dev, const float *qe
         if (tc) {
             int rc = launch_dft_gemm(h, n_blocks_dev, qeff, slot_count, base, cnt, slot_base, s);
             if (rc) return rc;
+            rc = check_cuda(h, cudaMemsetAsync(queue, 0, sizeof(int32_t), s), "convolution queue reset");
+            if (rc) return rc;
             k_conv_spec<NB1, G, true><<<sms, SPEC_THREADS, SPEC_SMEM, s>>>(n_blocks_dev, qeff, h->colmask, h->rhat,
                                                                           h->pair_j, h->tw, c, h->yspec, base, cnt,
-                                                                          slot_base, h->zspec);
+                                                                          slot_base, h->zspec, queue);
         } else {
+            int rc = check_cuda(h, cudaMemsetAsync(queue, 0, sizeof(int32_t), s), "convolution queue reset");
+            if (rc) return rc;
             k_conv_spec<NB1, G, false><<<sms, SPEC_THREADS, SPEC_SMEM, s>>>(n_blocks_dev, qeff, h->colmask, h->rhat,
                                                                            h->pair_j, h->tw, c, h->yspec, base, cnt,
-                                                                           slot_base, nullptr);
+                                                                           slot_base, nullptr, queue);
         }
         k_conv_itime<G><<<sms, 32 * itime_cols<G>(), itime_smem, s>>>(n_blocks_dev, h->yspec, h->tw, c, out, base,
                                                                        cnt);
