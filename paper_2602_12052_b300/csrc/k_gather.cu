@@ -219,7 +219,8 @@ __global__ void __launch_bounds__(PXW_THREADS) k_px_wave(const int32_t *__restri
                                                          const int32_t *__restrict__ n_pixels_dev,
                                                          const int32_t *__restrict__ slot_of,
                                                          const float *__restrict__ out, GatherConst c,
-                                                         float *__restrict__ wave, float *__restrict__ possum) {
+                                                         float *__restrict__ wave, float *__restrict__ possum,
+                                                         int32_t *__restrict__ queue) {
     using Acc = typename std::conditional<COMP, double, float>::type;
     __shared__ PxEntry s_e[PXW_WARPS][PXW_MAXE];
     const int np = n_pixels_dev[0];
@@ -227,7 +228,12 @@ __global__ void __launch_bounds__(PXW_THREADS) k_px_wave(const int32_t *__restri
     const int nwarps = (gridDim.x * blockDim.x) >> 5;
     const int span = c.bt + c.nr - 1;      // meaningful ticks of a block's output
     PxEntry *E = s_e[warp];
-    for (int row = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; row < np; row += nwarps) {
+    (void)nwarps;
+    for (;;) {   // rows from a queue: their cost varies with the number of contributing blocks
+        int row = 0;
+        if (lane == 0) row = atomicAdd(queue, 1);
+        row = __shfl_sync(0xffffffffu, row, 0);
+        if (row >= np) break;
         const int pid = pixel_ids[row];
         const int x = pid % c.npx_x, y = pid / c.npx_x;
         const int bx_lo = max(0, floordiv(x - c.bp - c.R, c.bp) + 1), bx_hi = min(c.nbx - 1, floordiv(x + c.R, c.bp));
@@ -337,10 +343,15 @@ int launch_gather(tred_handle *h, const int32_t *block_ids, const int32_t *n_blo
     k_scan_small<<<1, 1024, 0, s>>>(h->pix_chunks, h->pix_part, h->max_pixels, n_pixels_dev, h->status,
                                     TRED_ST_PIXEL_OVERFLOW, 4);
     k_px_emit<<<(unsigned)h->pix_chunks, 1024, 0, s>>>(npx, h->pix_flag, h->pix_part, h->max_pixels, pixel_ids);
+    int32_t *queue = h->pix_part + h->pix_chunks + 4;   // past the scan's total
+    rc = check_cuda(h, cudaMemsetAsync(queue, 0, sizeof(int32_t), s), "gather queue reset");
+    if (rc) return rc;
     if (c.comp)
-        k_px_wave<true><<<sms * 8, PXW_THREADS, 0, s>>>(pixel_ids, n_pixels_dev, h->blk_slot, out, c, wave, possum);
+        k_px_wave<true><<<sms * 8, PXW_THREADS, 0, s>>>(pixel_ids, n_pixels_dev, h->blk_slot, out, c, wave, possum,
+                                                        queue);
     else
-        k_px_wave<false><<<sms * 8, PXW_THREADS, 0, s>>>(pixel_ids, n_pixels_dev, h->blk_slot, out, c, wave, possum);
+        k_px_wave<false><<<sms * 8, PXW_THREADS, 0, s>>>(pixel_ids, n_pixels_dev, h->blk_slot, out, c, wave, possum,
+                                                         queue);
     h->launches += 6;
     return check_cuda(h, cudaGetLastError(), "gather launch");
 }
