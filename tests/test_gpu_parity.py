@@ -269,6 +269,37 @@ def test_repeatable_outputs():
         np.testing.assert_array_equal(a[k], b[k])
 
 
+def test_step_replayed_from_a_cuda_graph_equals_eager():
+    """The single-event step recorded once in a CUDA graph (device-side counts keep its
+    launch sequence fixed) and replayed gives the eager step's outputs bit for bit."""
+    import torch
+    cfg = synth.get_config("tiny")
+    dep, resp = synth.make_event(cfg)
+    sim = make_sim(cfg, resp, len(dep["x"]))
+    eager = run(sim, dep)
+    n = len(dep["x"])
+    x = {k: torch.from_numpy(np.ascontiguousarray(v)).cuda() for k, v in dep.items()}
+    torch.cuda.synchronize()
+    side = torch.cuda.Stream()
+    side.wait_stream(torch.cuda.current_stream())
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=side):
+        sim.step(n, x["x"], x["y"], x["z"], x["t0"], x["ne"])
+    torch.cuda.current_stream().wait_stream(side)
+    for _ in range(2):
+        sim.qeff.zero_()
+        sim.waveforms.zero_()
+        g.replay()
+        torch.cuda.synchronize()
+        res = sim.results()
+        assert sim.status()[0] == 0
+        for k in ("block_ids", "block_counts", "pixel_ids", "hit_pixel", "hit_tick", "hit_charge"):
+            np.testing.assert_array_equal(res[k], eager[k])
+        nb, npix = res["n_blocks"], res["n_pixels"]
+        np.testing.assert_array_equal(sim.qeff[:nb].cpu().numpy(), eager["qeff"])
+        np.testing.assert_array_equal(sim.waveforms[:npix].cpu().numpy(), eager["waveforms"])
+
+
 def test_block_deposit_lists_ascending_like_oracle():
     """Each block's deposit list is the oracle's, in ascending deposit order (Sec. III-B-1),
     on the tiny event and on a module plane with blocks of a few hundred deposits."""
