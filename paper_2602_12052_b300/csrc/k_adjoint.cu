@@ -114,9 +114,10 @@ __global__ void __launch_bounds__(AS_THREADS, 1)
     k_adj_spec(const int32_t *__restrict__ n_blocks_dev, const int32_t *__restrict__ block_ids,
                const float *__restrict__ resid, const int32_t *__restrict__ row_of,
                const float2 *__restrict__ tw, const float2 *__restrict__ rhat, AdjConst c,
-               float2 *__restrict__ gspec, int slot_base, int slot_count) {
+               float2 *__restrict__ gspec, int slot_base, int slot_count, int32_t *__restrict__ queue) {
     constexpr int LT = 64 * G;
     extern __shared__ float2 sm_a[];
+    __shared__ int s_item;
     float2 *dh = sm_a;                                  // [64][16][17]
     float2 *tbuf = dh + BINS * DH_BIN;                  // [warps][2][8][17]
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -125,7 +126,12 @@ __global__ void __launch_bounds__(AS_THREADS, 1)
     if (nloc <= 0) return;
     const int span = c.bt + c.nr - 1;
     float2 *tb = tbuf + warp * 2 * AT_BIN;
-    for (int item = blockIdx.x; item < nloc * G; item += gridDim.x) {
+    for (;;) {   // (block, class) items from a queue
+        __syncthreads();
+        if (tid == 0) s_item = atomicAdd(queue, 1);
+        __syncthreads();
+        const int item = s_item;
+        if (item >= nloc * G) break;
         const int sl = item / G, k1 = item % G;
         const int slot = slot_base + sl;
         const int blk = block_ids[slot];
@@ -593,9 +599,13 @@ static int run_adjoint_conv(tred_handle *h, const int32_t *block_ids, const int3
     }
     const int sms = num_sms(h);
     const int chunk = h->adj_chunk;
+    // the item queue counter: a word after the effective charge's per-CTA scratch
+    int32_t *queue = h->effq_acc + (effq_scratch_bytes(h->g.bp * h->g.n_sub, sms) / sizeof(int32_t) - 16);
     for (int base = 0; base < h->max_blocks; base += chunk) {
+        int rc = check_cuda(h, cudaMemsetAsync(queue, 0, sizeof(int32_t), s), "adjoint queue reset");
+        if (rc) return rc;
         k_adj_spec<G><<<sms, AS_THREADS, ADJ_SPEC_SMEM, s>>>(n_blocks_dev, block_ids, resid, h->pix_row, h->tw,
-                                                             h->rhat, c, h->gspec, base, chunk);
+                                                             h->rhat, c, h->gspec, base, chunk, queue);
         k_adj_itime<G><<<sms, 32 * adj_itime_cols<G>(), itime_smem, s>>>(n_blocks_dev, h->gspec, h->pair_j, h->tw, c,
                                                                          gq, base, chunk);
         h->launches += 2;

@@ -6,9 +6,20 @@
 #include <cstring>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "tred_internal.cuh"
 
 namespace tred {
+
+// An NVTX range over one ABI call (named after it), so that a profiler's timeline shows
+// the path's steps around their kernels; a push and a pop when no tool is attached.
+struct CallRange {
+    explicit CallRange(const char *name) { nvtxRangePushA(name); }
+    ~CallRange() { nvtxRangePop(); }
+    CallRange(const CallRange &) = delete;
+    CallRange &operator=(const CallRange &) = delete;
+};
 
 int set_error(tred_handle *h, int code, const char *fmt, ...) {
     if (h) {
@@ -297,6 +308,7 @@ int32_t tred_set_transport(tred_handle *h, const tred_params *params) {
 int32_t tred_residual(tred_handle *h, const int32_t *pixel_ids, const int32_t *n_pixels_dev, const float *waveforms,
                       const int32_t *target_ids, int32_t n_target, const float *target_waves, float *resid,
                       double *loss_dev, void *stream) {
+    tred::CallRange range_("tred_residual");
     if (!h) return TRED_ERR_INVALID_ARG;
     if (!pixel_ids || !n_pixels_dev || !waveforms || !resid || !loss_dev || n_target < 0 ||
         (n_target > 0 && (!target_ids || !target_waves)))
@@ -309,6 +321,7 @@ int32_t tred_adjoint(tred_handle *h, int32_t n, const tred_deposits *deps, const
                      const int32_t *dep_offsets, const int32_t *dep_index, const int32_t *n_blocks_dev,
                      const int32_t *pixel_ids, const int32_t *n_pixels_dev, const float *resid, float *dqeff,
                      float *grad7, void *stream) {
+    tred::CallRange range_("tred_adjoint");
     if (!h) return TRED_ERR_INVALID_ARG;
     if (!h->response_ready) return set_error(h, TRED_ERR_NOT_READY, "tred_adjoint: call tred_set_response first");
     if (h->p.effq_mode != 0) return set_error(h, TRED_ERR_INVALID_ARG, "tred_adjoint: Gauss-Legendre mode only");
@@ -334,6 +347,7 @@ int32_t tred_adjoint(tred_handle *h, int32_t n, const tred_deposits *deps, const
 
 int32_t tred_param_grads(tred_handle *h, int32_t n, const float *z, const tred_deposits *deps, const float *grad7,
                          float *grad_inputs, double *grad_global, void *stream) {
+    tred::CallRange range_("tred_param_grads");
     if (!h) return TRED_ERR_INVALID_ARG;
     if (n < 0 || n > h->max_deposits || (n > 0 && (!z || !deps_ok(deps) || !grad7 || !grad_inputs)) || !grad_global)
         return set_error(h, TRED_ERR_INVALID_ARG, "tred_param_grads: bad arguments");
@@ -354,6 +368,7 @@ int32_t tred_reset_status(tred_handle *h, void *stream) {
 }
 
 int32_t tred_set_response(tred_handle *h, const float *resp_dev, void *stream) {
+    tred::CallRange range_("tred_set_response");
     if (!h) return TRED_ERR_INVALID_ARG;
     if (!resp_dev) return set_error(h, TRED_ERR_INVALID_ARG, "tred_set_response: null response");
     int rc = launch_response(h, resp_dev, (cudaStream_t)stream);
@@ -364,6 +379,7 @@ int32_t tred_set_response(tred_handle *h, const float *resp_dev, void *stream) {
 
 int32_t tred_drift(tred_handle *h, int32_t n, const float *x, const float *y, const float *z,
                    const float *t0, const float *ne, const tred_deposits *out, void *stream) {
+    tred::CallRange range_("tred_drift");
     if (!h) return TRED_ERR_INVALID_ARG;
     if (n < 0 || n > h->max_deposits)
         return set_error(h, TRED_ERR_CAPACITY, "tred_drift: n=%d outside [0, max_deposits=%d]", n, h->max_deposits);
@@ -376,6 +392,7 @@ int32_t tred_drift(tred_handle *h, int32_t n, const float *x, const float *y, co
 int32_t tred_drift_lines(tred_handle *h, int32_t n, const float *x0, const float *y0, const float *z0,
                          const float *x1, const float *y1, const float *z1, const float *t0, const float *ne,
                          const tred_deposits *out, float *half, void *stream) {
+    tred::CallRange range_("tred_drift_lines");
     if (!h) return TRED_ERR_INVALID_ARG;
     if (n < 0 || n > h->max_deposits)
         return set_error(h, TRED_ERR_CAPACITY, "tred_drift_lines: n=%d outside [0, max_deposits=%d]", n, h->max_deposits);
@@ -389,6 +406,7 @@ int32_t tred_drift_lines(tred_handle *h, int32_t n, const float *x0, const float
 int32_t tred_effq_lines(tred_handle *h, int32_t n, const tred_deposits *deps, const float *half,
                         const int32_t *block_ids, const int32_t *dep_offsets, const int32_t *dep_index,
                         const int32_t *n_blocks_dev, float *qeff, void *stream) {
+    tred::CallRange range_("tred_effq_lines");
     if (!h) return TRED_ERR_INVALID_ARG;
     if (n < 0 || n > h->max_deposits)
         return set_error(h, TRED_ERR_CAPACITY, "tred_effq_lines: n=%d outside [0, max_deposits]", n);
@@ -401,6 +419,7 @@ int32_t tred_effq_lines(tred_handle *h, int32_t n, const tred_deposits *deps, co
 int32_t tred_drift_events(tred_handle *h, int32_t n, const float *x, const float *y, const float *z,
                           const float *t0, const float *ne, const int32_t *event, const tred_deposits *out,
                           void *stream) {
+    tred::CallRange range_("tred_drift_events");
     if (!h) return TRED_ERR_INVALID_ARG;
     if (n < 0 || n > h->max_deposits)
         return set_error(h, TRED_ERR_CAPACITY, "tred_drift_events: n=%d outside [0, max_deposits=%d]", n,
@@ -414,6 +433,7 @@ int32_t tred_drift_events(tred_handle *h, int32_t n, const float *x, const float
 int32_t tred_blockbin(tred_handle *h, int32_t n, const tred_deposits *deps, int32_t *block_ids,
                       int32_t *block_counts, int32_t *dep_offsets, int32_t *dep_index,
                       int32_t max_pairs, int32_t *n_blocks_dev, void *stream) {
+    tred::CallRange range_("tred_blockbin");
     if (!h) return TRED_ERR_INVALID_ARG;
     if (n < 0 || n > h->max_deposits)
         return set_error(h, TRED_ERR_CAPACITY, "tred_blockbin: n=%d outside [0, max_deposits]", n);
@@ -427,6 +447,7 @@ int32_t tred_blockbin(tred_handle *h, int32_t n, const tred_deposits *deps, int3
 int32_t tred_effq(tred_handle *h, int32_t n, const tred_deposits *deps, const int32_t *block_ids,
                   const int32_t *dep_offsets, const int32_t *dep_index, const int32_t *n_blocks_dev,
                   float *qeff, void *stream) {
+    tred::CallRange range_("tred_effq");
     if (!h) return TRED_ERR_INVALID_ARG;
     if (n < 0 || n > h->max_deposits)
         return set_error(h, TRED_ERR_CAPACITY, "tred_effq: n=%d outside [0, max_deposits]", n);
@@ -439,6 +460,7 @@ int32_t tred_effq(tred_handle *h, int32_t n, const tred_deposits *deps, const in
 int32_t tred_effq_range(tred_handle *h, int32_t n, const tred_deposits *deps, const int32_t *block_ids,
                         const int32_t *dep_offsets, const int32_t *dep_index, const int32_t *n_blocks_dev,
                         int32_t slot_base, int32_t slot_count, float *qeff, void *stream) {
+    tred::CallRange range_("tred_effq_range");
     if (!h) return TRED_ERR_INVALID_ARG;
     if (n < 0 || n > h->max_deposits)
         return set_error(h, TRED_ERR_CAPACITY, "tred_effq_range: n=%d outside [0, max_deposits]", n);
@@ -451,6 +473,7 @@ int32_t tred_effq_range(tred_handle *h, int32_t n, const tred_deposits *deps, co
 
 int32_t tred_convolve(tred_handle *h, const int32_t *block_ids, const int32_t *n_blocks_dev,
                       const float *qeff, float *out_blocks, void *stream) {
+    tred::CallRange range_("tred_convolve");
     if (!h) return TRED_ERR_INVALID_ARG;
     if (!h->response_ready)
         return set_error(h, TRED_ERR_NOT_READY, "tred_convolve: call tred_set_response first");
@@ -462,6 +485,7 @@ int32_t tred_convolve(tred_handle *h, const int32_t *block_ids, const int32_t *n
 int32_t tred_convolve_range(tred_handle *h, const int32_t *block_ids, const int32_t *n_blocks_dev,
                             int32_t slot_base, int32_t slot_count, const float *qeff, float *out_blocks,
                             void *stream) {
+    tred::CallRange range_("tred_convolve_range");
     if (!h) return TRED_ERR_INVALID_ARG;
     if (!h->response_ready)
         return set_error(h, TRED_ERR_NOT_READY, "tred_convolve_range: call tred_set_response first");
@@ -474,6 +498,7 @@ int32_t tred_convolve_range(tred_handle *h, const int32_t *block_ids, const int3
 int32_t tred_gather_pixels(tred_handle *h, const int32_t *block_ids, const int32_t *n_blocks_dev,
                            const float *out_blocks, int32_t *pixel_ids, float *waveforms,
                            int32_t *n_pixels_dev, void *stream) {
+    tred::CallRange range_("tred_gather_pixels");
     if (!h) return TRED_ERR_INVALID_ARG;
     if (!block_ids || !n_blocks_dev || !out_blocks || !pixel_ids || !waveforms || !n_pixels_dev)
         return set_error(h, TRED_ERR_INVALID_ARG, "tred_gather_pixels: null pointer");
@@ -485,6 +510,7 @@ int32_t tred_readout(tred_handle *h, const tred_readout_params *rp, const int32_
                      const float *waveforms, const int32_t *n_pixels_dev, int32_t *hit_pixel,
                      int32_t *hit_tick, float *hit_charge, int32_t *n_hits_dev, int32_t max_hits,
                      void *stream) {
+    tred::CallRange range_("tred_readout");
     if (!h) return TRED_ERR_INVALID_ARG;
     if (!rp || !pixel_ids || !waveforms || !n_pixels_dev || !n_hits_dev || max_hits < 0 ||
         (max_hits > 0 && (!hit_pixel || !hit_tick || !hit_charge)))
@@ -500,6 +526,7 @@ int32_t tred_gather_readout(tred_handle *h, const int32_t *block_ids, const int3
                             const float *out_blocks, int32_t *pixel_ids, float *waveforms, int32_t *n_pixels_dev,
                             const tred_readout_params *rp, int32_t *hit_pixel, int32_t *hit_tick, float *hit_charge,
                             int32_t *n_hits_dev, int32_t max_hits, void *stream) {
+    tred::CallRange range_("tred_gather_readout");
     if (!h) return TRED_ERR_INVALID_ARG;
     if (!block_ids || !n_blocks_dev || !out_blocks || !pixel_ids || !waveforms || !n_pixels_dev || !rp ||
         !n_hits_dev || max_hits < 0 || (max_hits > 0 && (!hit_pixel || !hit_tick || !hit_charge)))
