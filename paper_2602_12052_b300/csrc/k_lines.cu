@@ -169,7 +169,7 @@ __device__ __forceinline__ float line_rho(const LineRec &s, float ax, float ay, 
     const float lam = bet * s.inva;
     const float ex = ax - lam * 2.f * s.hv[0], ey = ay - lam * 2.f * s.hv[1], et = at - lam * 2.f * s.hv[2];
     const float gp = ex * ex * s.isg2[0] + ey * ey * s.isg2[1] + et * et * s.isg2[2];
-    return s.pref * expf(-0.5f * gp) * (erff((s.alpha - bet) * s.rs2a) + erff(bet * s.rs2a));
+    return s.pref * __expf(-0.5f * gp) * (erff((s.alpha - bet) * s.rs2a) + erff(bet * s.rs2a));
 }
 
 // offset of the node (cell C, rule point l) on axis ax from the segment's reference point
