@@ -232,14 +232,24 @@ __global__ void __launch_bounds__(EQ_THREADS, EQ_CTAS_PER_SM) k_effq_blocks(
         S.offy[g] = (jg * c.ns * cols + pg * c.bp) * c.bt;     // jy, py
     }
     const int nb = min(n_blocks_dev[0], slot_base + slot_count);
+    const int nloc = max(0, nb - slot_base);
+    // An item is a run of tg of the block's 32-tick tiles: the whole block while there are
+    // enough blocks to keep every CTA busy, fewer tiles when a small event has few blocks,
+    // so that its blocks spread over more CTAs (every CTA derives the same tg from nb)
+    const int ntiles = c.bt / EQ_TT;
+    int tg = ntiles;
+    while (tg > 1 && (long long)nloc * ((ntiles + tg - 1) / tg) < 2ll * gridDim.x) tg = (tg + 1) / 2;
+    const int groups = (ntiles + tg - 1) / tg;
     for (;;) {
         __syncthreads();
-        if (tid == 0) S.slot = slot_base + atomicAdd(queue, 1);
+        if (tid == 0) S.slot = atomicAdd(queue, 1);   // item index
         for (int k = tid; k < nch; k += EQ_THREADS) S.mask[k] = 0ull;
         for (int k = tid; k < npatch; k += EQ_THREADS) S.nzp[k] = 0u;
         __syncthreads();
-        const int slot = S.slot;
-        if (slot >= nb) break;
+        const int item = S.slot;
+        if (item >= nloc * groups) break;
+        const int slot = slot_base + item / groups, grp = item - (item / groups) * groups;
+        const int tt_beg = grp * tg * EQ_TT, tt_end = min(c.bt, (grp + 1) * tg * EQ_TT);
         const int blk = block_ids[slot];
         const int bt = blk % c.nbt, bxy = blk / c.nbt, bx = bxy % c.nbx, by = bxy / c.nbx;
         const int X0 = bx * side, Y0 = by * side, T0 = bt * c.bt;
@@ -324,7 +334,7 @@ __global__ void __launch_bounds__(EQ_THREADS, EQ_CTAS_PER_SM) k_effq_blocks(
             if (lane == 0) S.nactive = na;
         }
         __syncthreads();
-        for (int tt = 0; tt < c.bt; tt += EQ_TT) {
+        for (int tt = tt_beg; tt < tt_end; tt += EQ_TT) {
             const int ta = T0 + tt, tb = ta + EQ_TT - 1;   // absolute ticks of the tile
             int cur = beg;
             bool first = true;
@@ -524,7 +534,9 @@ __global__ void __launch_bounds__(EQ_THREADS, EQ_CTAS_PER_SM) k_effq_blocks(
             atomicOr(&S.mask[jy * c.ns + jx], 1ull << (py * c.bp + px));
         }
         __syncthreads();
-        for (int k = tid; k < nch; k += EQ_THREADS) colmask[(size_t)slot * nch + k] = S.mask[k];
+        // the block's items each add their columns (the launch cleared the masks)
+        for (int k = tid; k < nch; k += EQ_THREADS)
+            if (S.mask[k]) atomicOr(reinterpret_cast<unsigned long long *>(&colmask[(size_t)slot * nch + k]), S.mask[k]);
     }
 }
 
@@ -594,6 +606,16 @@ int launch_effq(tred_handle *h, int n, const tred_deposits &deps, const int32_t 
     int32_t *queue = h->effq_acc + (size_t)sms * EQ_CTAS_PER_SM * side * side * EQ_TT;
     int rc = check_cuda(h, cudaMemsetAsync(queue, 0, sizeof(int32_t), s), "effq queue reset");
     if (rc) return rc;
+    {
+        // the non-empty column masks of the slots this call covers are OR-ed by its items
+        const int hi = slot_count < h->max_blocks - slot_base ? slot_base + slot_count : h->max_blocks;
+        if (hi > slot_base) {
+            rc = check_cuda(h, cudaMemsetAsync(h->colmask + (size_t)slot_base * nch, 0,
+                                               sizeof(uint64_t) * (size_t)(hi - slot_base) * nch, s),
+                            "effq mask reset");
+            if (rc) return rc;
+        }
+    }
     k_effq_blocks<<<sms * EQ_CTAS_PER_SM, EQ_THREADS, smem, s>>>(block_ids, dep_offsets, dep_index, n_blocks_dev, c, h->wts,
                                                  reinterpret_cast<const DepRec *>(h->recs), qeff, h->colmask,
                                                  h->effq_acc, queue, slot_base, slot_count);
