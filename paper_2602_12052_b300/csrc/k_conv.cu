@@ -68,6 +68,15 @@ constexpr size_t SPEC_SMEM = sizeof(float2) * ((size_t)PG * BINS * ZT_BIN + (siz
                                                32 + 16 + 8 + 64 + 2) +
                              sizeof(int) * (PG * 64 + 4);      // stage A task list and counters
 
+// Rounds of channel pairs per (block, class) item: all of them, or half when the event has
+// so few blocks that its items would leave most CTAs idle (then each half of the rounds is
+// its own item, writing its partial spectra to a plane of its own, nloc planes further on,
+// which the inverse time transform adds; two halves at most, and only while the spectrum
+// buffer holds both planes).  Both kernels derive it from the same device-side count.
+__host__ __device__ inline int conv_round_groups(int nloc, int G, int grid, int chunk) {
+    return (nloc > 0 && 2 * nloc * G <= grid && 2 * nloc <= chunk) ? 2 : 1;
+}
+
 // ZS: stage A reads the packed time spectra written by the tensor-core DFT
 // (zspec[slot][k1][pair][k2][col], k_dftgemm.cu) instead of computing them.
 template <int NB1, int G, bool ZS>
@@ -109,7 +118,9 @@ __global__ void __launch_bounds__(SPEC_THREADS, 1)
     const int nloc = max(0, min(slot_count, nb - slot_base));
     const int cols = c.bp * c.bp;
     const int slab = cols * c.bt;
-    const int items = nloc * G;
+    const int ngrp = conv_round_groups(nloc, G, gridDim.x, slot_count);
+    const int nrounds = (c.npairs + PG - 1) / PG;
+    const int items = nloc * G * ngrp;
     float2 *tb = tbuf + warp * 2 * TB_BIN;
     float2 *eb = ebuf + warp * 2 * EP_BIN;
 
@@ -120,8 +131,9 @@ __global__ void __launch_bounds__(SPEC_THREADS, 1)
         __syncthreads();
         const int item = s_ntask[2];
         if (item >= items) break;
-        const int sl = item / G, k1 = item % G;
+        const int grp = item % ngrp, sl = item / ngrp / G, k1 = (item / ngrp) % G;
         const int slot = slot_base + sl;
+        const int p_beg = PG * (grp * nrounds / ngrp), p_end = min(c.npairs, PG * ((grp + 1) * nrounds / ngrp));
         // zero the stage A buffers (the previous epilogue used them; rows and columns
         // beyond bp must read as zero)
         __syncthreads();
@@ -145,8 +157,8 @@ __global__ void __launch_bounds__(SPEC_THREADS, 1)
 
         const float *qblk = qeff + (size_t)(slot - qbase) * c.nch * slab;
         const uint64_t *mrow = colmask + (size_t)slot * c.nch;
-        for (int p0 = 0; p0 < c.npairs; p0 += PG) {
-            const int ng = min(PG, c.npairs - p0);
+        for (int p0 = p_beg; p0 < p_end; p0 += PG) {
+            const int ng = min(PG, p_end - p0);
             if (ZS) {
                 // ---------------- stage A from the tensor-core spectra of the round's pairs
                 const float2 *zsrc = zspec + (((size_t)sl * G + k1) * c.npairs + p0) * BINS * 64;
@@ -315,7 +327,7 @@ __global__ void __launch_bounds__(SPEC_THREADS, 1)
             float2 o[LP];
 #pragma unroll
             for (int k = 0; k < LP; ++k) o[bitrev<LP>(k)] = v[k];
-            float4 *dst = reinterpret_cast<float4 *>(yspec + ((size_t)sl * LT + (k1 + G * k2)) * (LP * LP) + r * LP);
+            float4 *dst = reinterpret_cast<float4 *>(yspec + ((size_t)(grp * nloc + sl) * LT + (k1 + G * k2)) * (LP * LP) + r * LP);
 #pragma unroll
             for (int x = 0; x < LP; x += 2) dst[x / 2] = make_float4(o[x].x, o[x].y, o[x + 1].x, o[x + 1].y);
             __syncwarp();
@@ -380,6 +392,8 @@ __global__ void __launch_bounds__(32 * itime_cols<G>(), 1)
     const int nloc = min(slot_count, nb - slot_base);
     if (nloc <= 0) return;
     const int items = nloc * 8 * PARTS;
+    // the spectral kernel's grid is one CTA per SM, as this one's
+    const int ngrp = conv_round_groups(nloc, G, gridDim.x, slot_count);
     // the rows of mirror row pair rp: the rp-th row a with a < m(a), and bro = m(a)
     auto rows_of = [&](int rp, int &a, int &bro) {
         a = -1;
@@ -434,6 +448,11 @@ __global__ void __launch_bounds__(32 * itime_cols<G>(), 1)
             const float2 *src = S + (cur * NC + q) * SROW;
 #pragma unroll
             for (int m = 0; m < NPL; ++m) v[m] = src[lane + 32 * m];
+            if (ngrp == 2) {   // the second half of the rounds' spectra, from its own plane
+                const float2 *g2 = yspec + (size_t)(nloc + sl) * LT * (LP * LP) + cy * LP + cx;
+#pragma unroll
+                for (int m = 0; m < NPL; ++m) v[m] = cadd(v[m], __ldg(g2 + (size_t)(lane + 32 * m) * (LP * LP)));
+            }
         }
         fft_reg_dif_c<NPL, true>(v);              // v[k] = u[bitrev(k)]
 #pragma unroll
