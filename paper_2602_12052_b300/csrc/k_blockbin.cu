@@ -332,8 +332,10 @@ int launch_blockbin(tred_handle *h, int n, const tred_deposits &deps, int32_t *b
         k_bb_fill<<<(n + 255) / 256, 256, 0, s>>>(n, deps, g, h->blk_slot, dep_offsets, h->blk_fill,
                                                   dep_index, max_pairs);
     if (n > 0)
-        k_bb_sort<<<num_sms(h) * 4, BB_SORT_THREADS, 0, s>>>(n_blocks_dev, dep_offsets, dep_index, max_pairs,
-                                                            h->max_blocks);
+        // eight lists per CTA: no more CTAs than the block capacity can use
+        k_bb_sort<<<min(num_sms(h) * 4, (h->max_blocks + 7) / 8), BB_SORT_THREADS, 0, s>>>(n_blocks_dev, dep_offsets,
+                                                                                      dep_index, max_pairs,
+                                                                                      h->max_blocks);
     h->launches += 4 + (n > 0 ? 3 : 0);
     return check_cuda(h, cudaGetLastError(), "blockbin launch");
 }
@@ -424,7 +426,8 @@ extern "C" int32_t tred_blockbin_noalloc(const tred_geometry *geom, int32_t n, c
         int dev = 0, sms = 0;
         if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
             return TRED_ERR_CUDA;
-        k_bb_sort<<<sms * 4, BB_SORT_THREADS, 0, s>>>(n_blocks_dev, dep_offsets, dep_index, max_pairs, max_blocks);
+        k_bb_sort<<<min(sms * 4, (max_blocks + 7) / 8), BB_SORT_THREADS, 0, s>>>(n_blocks_dev, dep_offsets, dep_index,
+                                                                                max_pairs, max_blocks);
     }
     return cudaGetLastError() == cudaSuccess ? TRED_OK : TRED_ERR_CUDA;
 }

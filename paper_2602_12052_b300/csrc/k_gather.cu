@@ -344,13 +344,14 @@ int launch_gather(tred_handle *h, const int32_t *block_ids, const int32_t *n_blo
                                     TRED_ST_PIXEL_OVERFLOW, 4);
     k_px_emit<<<(unsigned)h->pix_chunks, 1024, 0, s>>>(npx, h->pix_flag, h->pix_part, h->max_pixels, pixel_ids);
     int32_t *queue = h->pix_part + h->pix_chunks + 4;   // past the scan's total
+    const int pxw_grid = min(sms * 8, (h->max_pixels + PXW_WARPS - 1) / PXW_WARPS);   // a warp per pixel
     rc = check_cuda(h, cudaMemsetAsync(queue, 0, sizeof(int32_t), s), "gather queue reset");
     if (rc) return rc;
     if (c.comp)
-        k_px_wave<true><<<sms * 8, PXW_THREADS, 0, s>>>(pixel_ids, n_pixels_dev, h->blk_slot, out, c, wave, possum,
+        k_px_wave<true><<<pxw_grid, PXW_THREADS, 0, s>>>(pixel_ids, n_pixels_dev, h->blk_slot, out, c, wave, possum,
                                                         queue);
     else
-        k_px_wave<false><<<sms * 8, PXW_THREADS, 0, s>>>(pixel_ids, n_pixels_dev, h->blk_slot, out, c, wave, possum,
+        k_px_wave<false><<<pxw_grid, PXW_THREADS, 0, s>>>(pixel_ids, n_pixels_dev, h->blk_slot, out, c, wave, possum,
                                                          queue);
     h->launches += 6;
     return check_cuda(h, cudaGetLastError(), "gather launch");

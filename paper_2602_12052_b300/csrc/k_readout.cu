@@ -232,11 +232,12 @@ int launch_readout(tred_handle *h, const tred_readout_params &rp, const int32_t 
     const float cut = rp.threshold_e > 0.f ? rp.threshold_e * (1.0f - 1e-4f) : -3.0e38f;
     RoConst c{h->g.nt, rp.clock_ticks, rp.hold_ticks, rp.reset_ticks, rp.mode == 1 ? rp.n_samples : 1, rp.threshold_e};
     const int sms = num_sms(h);
+    const int ro_grid = min(sms * 8, (h->max_pixels + 7) / 8);   // a warp per pixel, 8 per CTA
     int rc = check_cuda(h, cudaMemsetAsync(h->hit_cnt, 0, sizeof(int32_t) * ((size_t)h->max_pixels + 1), s),
                         "clear hit counts");
     if (rc) return rc;
     auto count = [&](auto kern) {
-        kern<<<sms * 8, 256, 0, s>>>(wave, n_pixels_dev, c, h->hit_cnt, h->hit_tmp, h->hit_tmpc, possum, cut);
+        kern<<<ro_grid, 256, 0, s>>>(wave, n_pixels_dev, c, h->hit_cnt, h->hit_tmp, h->hit_tmpc, possum, cut);
     };
     if (rp.mode == 2) count(k_ro_count<2>);
     else if (rp.mode == 1) count(k_ro_count<1>);
@@ -246,7 +247,7 @@ int launch_readout(tred_handle *h, const tred_readout_params &rp, const int32_t 
                            TRED_ST_HIT_OVERFLOW, 5, s);
     if (rc) return rc;
     auto emit = [&](auto kern) {
-        kern<<<sms * 8, 256, 0, s>>>(wave, pixel_ids, n_pixels_dev, c, h->hit_cnt, h->hit_tmp, h->hit_tmpc, max_hits,
+        kern<<<ro_grid, 256, 0, s>>>(wave, pixel_ids, n_pixels_dev, c, h->hit_cnt, h->hit_tmp, h->hit_tmpc, max_hits,
                                      hit_pixel, hit_tick, hit_charge);
     };
     if (rp.mode == 2) emit(k_ro_emit<2>);
