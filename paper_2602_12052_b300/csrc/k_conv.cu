@@ -79,7 +79,9 @@ __host__ __device__ inline int conv_round_groups(int nloc, int G, int grid, int 
 
 // ZS: stage A reads the packed time spectra written by the tensor-core DFT
 // (zspec[slot][k1][pair][k2][col], k_dftgemm.cu) instead of computing them.
-template <int NB1, int G, bool ZS>
+// HZ: blocks of at most 4 x 4 pixels, so the rows and columns 4..7 of every packed input
+// are zero: both spatial stages skip them (half-zero first butterfly stage).
+template <int NB1, int G, bool ZS, bool HZ>
 __global__ void __launch_bounds__(SPEC_THREADS, 1)
     k_conv_spec(const int32_t *__restrict__ n_blocks_dev, const float *__restrict__ qeff,
                 const uint64_t *__restrict__ colmask, const float2 *__restrict__ rhat,
@@ -263,6 +265,10 @@ __global__ void __launch_bounds__(SPEC_THREADS, 1)
                         float2 v[8];
 #pragma unroll
                         for (int x = 0; x < 8; ++x) {
+                            if (HZ && x >= 4) {
+                                v[x] = make_float2(0.f, 0.f);              // not read
+                                continue;
+                            }
                             const float2 z = zrow[x];
                             if (x == 0) {
                                 v[x] = z;                                  // W_16^0
@@ -273,7 +279,7 @@ __global__ void __launch_bounds__(SPEC_THREADS, 1)
                                 v[x] = make_float2(z.x * wr - z.y * wi, z.x * wi + z.y * wr);
                             }
                         }
-                        fft_reg_dif_c<8, false>(v);
+                        fft_reg_dif_c<8, false, HZ>(v);
                         float2 *dst = tb + b * TB_BIN + 8 * h + py;
 #pragma unroll
                         for (int k = 0; k < 8; ++k) dst[TB_R * bitrev<8>(k)] = v[k];   // kx = 2 bitrev3(k) + h
@@ -285,11 +291,15 @@ __global__ void __launch_bounds__(SPEC_THREADS, 1)
                         float2 e[8], o[8];
 #pragma unroll
                         for (int y = 0; y < 8; ++y) {
+                            if (HZ && y >= 4) {
+                                e[y] = o[y] = make_float2(0.f, 0.f);      // not read
+                                continue;
+                            }
                             e[y] = src[y];
                             o[y] = mul_w16(e[y], y);                       // e W_16^y
                         }
-                        fft_reg_dif_c<8, false>(e);
-                        fft_reg_dif_c<8, false>(o);
+                        fft_reg_dif_c<8, false, HZ>(e);
+                        fft_reg_dif_c<8, false, HZ>(o);
 #pragma unroll
                         for (int k = 0; k < 8; ++k) {
                             const int q = bitrev<8>(k);            // ky pair (2q, 2q + 1)
@@ -483,14 +493,14 @@ __global__ void __launch_bounds__(32 * itime_cols<G>(), 1)
     cp_async_wait<0>();
 }
 
-template <int NB1, int G>
-static int run_conv(tred_handle *h, const int32_t *n_blocks_dev, const float *qeff, float *out,
+template <int NB1, int G, bool HZ>
+static int run_conv_bp(tred_handle *h, const int32_t *n_blocks_dev, const float *qeff, float *out,
                     const ConvConst &c, int slot_base, int slot_count, cudaStream_t s) {
     static bool attr = false;
     const size_t itime_smem = itime_smem_bytes<G>();
     if (!attr) {
-        cudaFuncSetAttribute(k_conv_spec<NB1, G, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SPEC_SMEM);
-        cudaFuncSetAttribute(k_conv_spec<NB1, G, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SPEC_SMEM);
+        cudaFuncSetAttribute(k_conv_spec<NB1, G, false, HZ>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SPEC_SMEM);
+        cudaFuncSetAttribute(k_conv_spec<NB1, G, true, HZ>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SPEC_SMEM);
         cudaFuncSetAttribute(k_conv_itime<G>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)itime_smem);
         attr = true;
     }
@@ -507,13 +517,13 @@ static int run_conv(tred_handle *h, const int32_t *n_blocks_dev, const float *qe
             if (rc) return rc;
             rc = check_cuda(h, cudaMemsetAsync(queue, 0, sizeof(int32_t), s), "convolution queue reset");
             if (rc) return rc;
-            k_conv_spec<NB1, G, true><<<sms, SPEC_THREADS, SPEC_SMEM, s>>>(n_blocks_dev, qeff, h->colmask, h->rhat,
+            k_conv_spec<NB1, G, true, HZ><<<sms, SPEC_THREADS, SPEC_SMEM, s>>>(n_blocks_dev, qeff, h->colmask, h->rhat,
                                                                           h->pair_j, h->tw, c, h->yspec, base, cnt,
                                                                           slot_base, h->zspec, queue);
         } else {
             int rc = check_cuda(h, cudaMemsetAsync(queue, 0, sizeof(int32_t), s), "convolution queue reset");
             if (rc) return rc;
-            k_conv_spec<NB1, G, false><<<sms, SPEC_THREADS, SPEC_SMEM, s>>>(n_blocks_dev, qeff, h->colmask, h->rhat,
+            k_conv_spec<NB1, G, false, HZ><<<sms, SPEC_THREADS, SPEC_SMEM, s>>>(n_blocks_dev, qeff, h->colmask, h->rhat,
                                                                            h->pair_j, h->tw, c, h->yspec, base, cnt,
                                                                            slot_base, nullptr, queue);
         }
@@ -522,6 +532,13 @@ static int run_conv(tred_handle *h, const int32_t *n_blocks_dev, const float *qe
         h->launches += 2;
     }
     return check_cuda(h, cudaGetLastError(), "convolve launch");
+}
+
+template <int NB1, int G>
+static int run_conv(tred_handle *h, const int32_t *n_blocks_dev, const float *qeff, float *out,
+                    const ConvConst &c, int slot_base, int slot_count, cudaStream_t s) {
+    return c.bp <= 4 ? run_conv_bp<NB1, G, true>(h, n_blocks_dev, qeff, out, c, slot_base, slot_count, s)
+                     : run_conv_bp<NB1, G, false>(h, n_blocks_dev, qeff, out, c, slot_base, slot_count, s);
 }
 
 int launch_convolve(tred_handle *h, const int32_t *block_ids, const int32_t *n_blocks_dev,

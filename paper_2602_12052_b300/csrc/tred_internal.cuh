@@ -206,7 +206,9 @@ __host__ __device__ constexpr float w32s(int m) {
 }
 
 // Radix-2 DIF FFT in registers, N <= 32, twiddles as constants.  Output v[k] = X[bitrev(k)].
-template <int N, bool INV>
+// HZ: the upper half of the input is zero (v[N/2 ..] are not read), so the first stage's
+// butterflies reduce to a copy and a twiddled copy.
+template <int N, bool INV, bool HZ = false>
 __device__ __forceinline__ void fft_reg_dif_c(float2 (&v)[N]) {
     static_assert(N >= 2 && N <= 32 && (N & (N - 1)) == 0, "N must be a power of two <= 32");
 #pragma unroll
@@ -215,9 +217,15 @@ __device__ __forceinline__ void fft_reg_dif_c(float2 (&v)[N]) {
         for (int start = 0; start < N; start += 2 * span) {
 #pragma unroll
             for (int i = 0; i < span; ++i) {
-                float2 a = v[start + i], b = v[start + i + span];
-                v[start + i] = cadd(a, b);
-                float2 d = csub(a, b);
+                float2 a = v[start + i];
+                float2 d;
+                if (HZ && span == N / 2) {
+                    d = a;
+                } else {
+                    const float2 b = v[start + i + span];
+                    v[start + i] = cadd(a, b);
+                    d = csub(a, b);
+                }
                 const int m = i * (N / (2 * span));        // exponent on W_N
                 const int m32 = m * (32 / N);               // same angle on W_32
                 if (m == 0) {
