@@ -438,7 +438,7 @@ def run_adjoint(args):
 
 def run_spill(args):
     """Config 5: ~1e7 deposits over 35 module planes, processed one plane after the
-    other on one GPU; GL-3, 13x13x10x10x400 response, 4x4x256 blocks, FFT 16x16x1024."""
+    other on one GPU; GL-3, 13x13x10x10x400 response, 4x4x256 blocks, FFT 16x16x768."""
     import torch
     import synth
     from paper_2602_12052_b300 import autotune, tred
@@ -470,7 +470,7 @@ def run_spill(args):
     dense = 35 * cfg.npx * cfg.npx * cfg.nt * 4
     _line("depos/s over 35 module planes in sequence (spill scale)", ntot / (ms / 1e3), "depos/s", ms, args,
           {"workload": f"35 planes x 512x512 px x 6400 ticks, {ntot} deposits, GL-3, 13x13x10x10x400 response, "
-                       "4x4x256 blocks, FFT 16x16x1024"},
+                       "4x4x256 blocks, FFT 16x16x768"},
           memory={"device_bytes_in_use": int(total - free1),
                   "dense_pixel_current_estimate_bytes": dense,
                   "dense_subpixel_qeff_estimate_bytes": dense * cfg.n_sub ** 2},

@@ -370,7 +370,7 @@ __device__ __forceinline__ void cp_async_wait() {
 // other half of a double buffer (cp.async) while the current item is transformed;
 // mirror partners exchange their imaginary parts through shared memory.
 template <int G>
-__host__ __device__ constexpr int itime_cols() { return G == 8 ? 16 : 8; }
+__host__ __device__ constexpr int itime_cols() { return 64 * G <= 512 ? 16 : 8; }
 template <int G>
 constexpr size_t itime_smem_bytes() {
     return sizeof(float2) * (2 * itime_cols<G>() * (64 * G + 1) + 64 * G + 32) +
@@ -464,19 +464,19 @@ __global__ void __launch_bounds__(32 * itime_cols<G>(), 1)
                 for (int m = 0; m < NPL; ++m) v[m] = cadd(v[m], __ldg(g2 + (size_t)(lane + 32 * m) * (LP * LP)));
             }
         }
-        fft_reg_dif_c<NPL, true>(v);              // v[k] = u[bitrev(k)]
+        fft_reg_any<NPL, true>(v);                // v[k] = u[fft_perm(k)]
 #pragma unroll
         for (int k = 0; k < NPL; ++k) {
-            const int aa = bitrev<NPL>(k);
+            const int aa = fft_perm<NPL>(k);
             float2 w = wlt[(lane * aa) % LT];
             w.y = -w.y;
             v[k] = fft32_lanes<true>(cmul(v[k], w), w32, lane);
         }
-        // lane holds t = NPL * bitrev5(lane) + bitrev(k) in register k
+        // lane holds t = NPL * bitrev5(lane) + fft_perm(k) in register k
         const int b5 = bitrev<32>(lane);
         float *ib = Ib + q * NPL * IROW;
 #pragma unroll
-        for (int k = 0; k < NPL; ++k) ib[bitrev<NPL>(k) * IROW + b5] = v[k].y;
+        for (int k = 0; k < NPL; ++k) ib[fft_perm<NPL>(k) * IROW + b5] = v[k].y;
         __syncthreads();
         const float *pib = Ib + (q < HC ? q + HC : q - HC) * NPL * IROW;   // mirror partner
         const int uy = (cy + c.R) % LP, ux = (cx + c.R) % LP;
@@ -484,7 +484,7 @@ __global__ void __launch_bounds__(32 * itime_cols<G>(), 1)
         float r[NPL];
 #pragma unroll
         for (int k = 0; k < NPL; ++k) {
-            const int t = bitrev<NPL>(k);
+            const int t = fft_perm<NPL>(k);
             r[t] = c.mpcp ? v[k].x + pib[t * IROW + b5] : v[k].x;
         }
 #pragma unroll
@@ -500,7 +500,8 @@ static int run_conv_bp(tred_handle *h, const int32_t *n_blocks_dev, const float 
     const size_t itime_smem = itime_smem_bytes<G>();
     if (!attr) {
         cudaFuncSetAttribute(k_conv_spec<NB1, G, false, HZ>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SPEC_SMEM);
-        cudaFuncSetAttribute(k_conv_spec<NB1, G, true, HZ>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SPEC_SMEM);
+        if constexpr (G == 8)   // the tensor-core time DFT: lt = 512 only
+            cudaFuncSetAttribute(k_conv_spec<NB1, G, true, HZ>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SPEC_SMEM);
         cudaFuncSetAttribute(k_conv_itime<G>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)itime_smem);
         attr = true;
     }
@@ -513,13 +514,17 @@ static int run_conv_bp(tred_handle *h, const int32_t *n_blocks_dev, const float 
     for (int base = slot_base; base < end; base += chunk) {
         const int cnt = chunk < end - base ? chunk : end - base;
         if (tc) {
-            int rc = launch_dft_gemm(h, n_blocks_dev, qeff, slot_count, base, cnt, slot_base, s);
-            if (rc) return rc;
-            rc = check_cuda(h, cudaMemsetAsync(queue, 0, sizeof(int32_t), s), "convolution queue reset");
-            if (rc) return rc;
-            k_conv_spec<NB1, G, true, HZ><<<sms, SPEC_THREADS, SPEC_SMEM, s>>>(n_blocks_dev, qeff, h->colmask, h->rhat,
-                                                                          h->pair_j, h->tw, c, h->yspec, base, cnt,
-                                                                          slot_base, h->zspec, queue);
+            if constexpr (G == 8) {   // the tensor-core time DFT: lt = 512 only
+                int rc = launch_dft_gemm(h, n_blocks_dev, qeff, slot_count, base, cnt, slot_base, s);
+                if (rc) return rc;
+                rc = check_cuda(h, cudaMemsetAsync(queue, 0, sizeof(int32_t), s), "convolution queue reset");
+                if (rc) return rc;
+                k_conv_spec<NB1, G, true, HZ><<<sms, SPEC_THREADS, SPEC_SMEM, s>>>(
+                    n_blocks_dev, qeff, h->colmask, h->rhat, h->pair_j, h->tw, c, h->yspec, base, cnt, slot_base,
+                    h->zspec, queue);
+            } else {
+                return set_error(h, TRED_ERR_INVALID_ARG, "convolve: the tensor-core time DFT needs lt = 512");
+            }
         } else {
             int rc = check_cuda(h, cudaMemsetAsync(queue, 0, sizeof(int32_t), s), "convolution queue reset");
             if (rc) return rc;
@@ -564,6 +569,21 @@ int launch_convolve(tred_handle *h, const int32_t *block_ids, const int32_t *n_b
             case 5: return run_conv<5, 8>(h, n_blocks_dev, qeff, out, c, slot_base, slot_count, s);
             case 6: return run_conv<6, 8>(h, n_blocks_dev, qeff, out, c, slot_base, slot_count, s);
             case 7: return run_conv<7, 8>(h, n_blocks_dev, qeff, out, c, slot_base, slot_count, s);
+            default: break;
+        }
+    } else if (c.G == 6) {   // lt = 384 = 3 x 128: the inverse time transform is mixed radix
+        switch (nb1) {
+            case 1: return run_conv<1, 6>(h, n_blocks_dev, qeff, out, c, slot_base, slot_count, s);
+            case 2: return run_conv<2, 6>(h, n_blocks_dev, qeff, out, c, slot_base, slot_count, s);
+            default: break;
+        }
+    } else if (c.G == 12) {   // lt = 768 = 3 x 256
+        switch (nb1) {
+            case 1: return run_conv<1, 12>(h, n_blocks_dev, qeff, out, c, slot_base, slot_count, s);
+            case 2: return run_conv<2, 12>(h, n_blocks_dev, qeff, out, c, slot_base, slot_count, s);
+            case 4: return run_conv<4, 12>(h, n_blocks_dev, qeff, out, c, slot_base, slot_count, s);
+            case 5: return run_conv<5, 12>(h, n_blocks_dev, qeff, out, c, slot_base, slot_count, s);
+            case 8: return run_conv<8, 12>(h, n_blocks_dev, qeff, out, c, slot_base, slot_count, s);
             default: break;
         }
     } else if (c.G == 16) {

@@ -91,7 +91,7 @@ static int validate(const tred_geometry *g, const tred_params *p, char *msg, siz
     if ((int64_t)g->n_sub * g->n_sub * g->bp * g->bp > 6400) return bad("n_sub^2 bp^2 must be <= 6400");
     if (g->bp != 4 && g->bp != 8) return bad("bp must be 4 or 8 (padded extent 16)");
     if (g->kp < 1 || g->kp % 2 == 0 || g->bp + g->kp - 1 > LP) return bad("kp odd with bp + kp - 1 <= 16");
-    if (g->lt != 512 && g->lt != 1024) return bad("lt must be 512 or 1024");
+    if (g->lt != 384 && g->lt != 512 && g->lt != 768 && g->lt != 1024) return bad("lt must be 384, 512, 768 or 1024");
     if (g->bt < 64 || g->bt % 64 || g->bt + g->nr - 1 > g->lt) return bad("bt multiple of 64 with bt + nr - 1 <= lt");
     if (g->bt / 64 > g->lt / 64) return bad("bt too large for lt");
     if (g->nr < 1) return bad("nr must be >= 1");

@@ -251,6 +251,69 @@ __host__ __device__ constexpr int bitrev(int x) {
     return r;
 }
 
+// exp(-2 pi i m / 24) as compile-time constants (cos and -sin rounded to binary32), for the
+// in-register transforms of 12 and 24 points
+__host__ __device__ constexpr float w24c(int m) {
+    constexpr float c[24] = {1.000000000e+00f, 9.659258263e-01f, 8.660254038e-01f, 7.071067812e-01f, 5.000000000e-01f, 2.588190451e-01f, 0.0f, -2.588190451e-01f, -5.000000000e-01f, -7.071067812e-01f, -8.660254038e-01f, -9.659258263e-01f, -1.000000000e+00f, -9.659258263e-01f, -8.660254038e-01f, -7.071067812e-01f, -5.000000000e-01f, -2.588190451e-01f, 0.0f, 2.588190451e-01f, 5.000000000e-01f, 7.071067812e-01f, 8.660254038e-01f, 9.659258263e-01f};
+    return c[((m % 24) + 24) % 24];
+}
+__host__ __device__ constexpr float w24s(int m) {
+    constexpr float s[24] = {0.0f, -2.588190451e-01f, -5.000000000e-01f, -7.071067812e-01f, -8.660254038e-01f, -9.659258263e-01f, -1.000000000e+00f, -9.659258263e-01f, -8.660254038e-01f, -7.071067812e-01f, -5.000000000e-01f, -2.588190451e-01f, 0.0f, 2.588190451e-01f, 5.000000000e-01f, 7.071067812e-01f, 8.660254038e-01f, 9.659258263e-01f, 1.000000000e+00f, 9.659258263e-01f, 8.660254038e-01f, 7.071067812e-01f, 5.000000000e-01f, 2.588190451e-01f};
+    return s[((m % 24) + 24) % 24];
+}
+
+// In-register DFT of N = 3 M points (M = 4 or 8; N = 12 or 24), mixed radix: a radix-3
+// butterfly over n = n2 + M n1 for each n2, the twiddles W_N^(n2 k1), then an M-point
+// radix-2 DIF transform of each of the three rows k1.  Output register k1 M + j holds
+// X[3 bitrev_M(j) + k1] (fft_perm gives that index).  INV: conjugate twiddles.
+template <int N, bool INV>
+__device__ __forceinline__ void fft_reg_mixed3(float2 (&v)[N]) {
+    static_assert(N == 12 || N == 24, "N = 12 or 24");
+    constexpr int M = N / 3;
+    constexpr float C3 = 8.660254038e-01f;                  // sin(2 pi / 3)
+#pragma unroll
+    for (int n2 = 0; n2 < M; ++n2) {
+        const float2 x0 = v[n2], x1 = v[n2 + M], x2 = v[n2 + 2 * M];
+        const float2 sm = make_float2(x1.x + x2.x, x1.y + x2.y), df = make_float2(x1.x - x2.x, x1.y - x2.y);
+        const float2 y0 = make_float2(x0.x + sm.x, x0.y + sm.y);
+        const float2 t = make_float2(x0.x - 0.5f * sm.x, x0.y - 0.5f * sm.y);
+        const float2 id = make_float2(-C3 * df.y, C3 * df.x);   // i sin(2 pi / 3) (x1 - x2)
+        const float2 y1 = INV ? make_float2(t.x + id.x, t.y + id.y) : make_float2(t.x - id.x, t.y - id.y);
+        const float2 y2 = INV ? make_float2(t.x - id.x, t.y - id.y) : make_float2(t.x + id.x, t.y + id.y);
+        v[n2] = y0;
+        const int m1 = n2 * (24 / N), m2 = 2 * n2 * (24 / N);     // W_N^(n2) and W_N^(2 n2) on W_24
+        const float c1 = w24c(m1), s1 = INV ? -w24s(m1) : w24s(m1);
+        const float c2 = w24c(m2), s2 = INV ? -w24s(m2) : w24s(m2);
+        v[n2 + M] = n2 == 0 ? y1 : make_float2(y1.x * c1 - y1.y * s1, y1.x * s1 + y1.y * c1);
+        v[n2 + 2 * M] = n2 == 0 ? y2 : make_float2(y2.x * c2 - y2.y * s2, y2.x * s2 + y2.y * c2);
+    }
+#pragma unroll
+    for (int k1 = 0; k1 < 3; ++k1) {
+        float2 r[M];
+#pragma unroll
+        for (int j = 0; j < M; ++j) r[j] = v[k1 * M + j];
+        fft_reg_dif_c<M, INV>(r);
+#pragma unroll
+        for (int j = 0; j < M; ++j) v[k1 * M + j] = r[j];
+    }
+}
+
+// Output index held in register k by fft_reg_any<N>: bit reversal for powers of two,
+// 3 bitrev_M(k mod M) + k div M for N = 3 M.
+template <int N>
+__host__ __device__ constexpr int fft_perm(int k) {
+    if constexpr ((N & (N - 1)) == 0) {
+        return bitrev<N>(k);
+    } else {
+        return 3 * bitrev<N / 3>(k % (N / 3)) + k / (N / 3);
+    }
+}
+template <int N, bool INV>
+__device__ __forceinline__ void fft_reg_any(float2 (&v)[N]) {
+    if constexpr ((N & (N - 1)) == 0) fft_reg_dif_c<N, INV>(v);
+    else fft_reg_mixed3<N, INV>(v);
+}
+
 // Cross-lane 32-point DIF FFT (one value per lane, natural order in lane index);
 // afterwards lane l holds X[bitrev5(l)].  w32: lane-independent table
 // W32[m] = exp(-2 pi i m / 32) (shared or global memory).

@@ -98,7 +98,8 @@ CONFIGS = {
         name="module20", npx=512, nt=6400, kind="tracks", n_tracks=20,
         track_len_cm=(1.0, 100.0), z_range_cm=(0.0, 50.0), ne_mean=60.0, seed=1020),
     # Spill-scale plane: GL-3, 13 x 13 pixel x 400 tick response, 4 x 4 pixel blocks
-    # (so the padded spatial extent stays 16), FFT length 1024 along time.
+    # (so the padded spatial extent stays 16), FFT length 768 = 3 x 256 along time (the
+    # smallest 2^a 3^b at or above bt + nr - 1 = 655).
     # Line segments (Sec. II-C, Eq. qline): the tiny track and a 200-track module plane
     # cut into 0.25 cm and 0.3 cm segments (make_segments).
     "tiny_lines": Config(name="tiny_lines"),
@@ -108,7 +109,7 @@ CONFIGS = {
     "spill_plane": Config(
         name="spill_plane", npx=512, nt=6400, kind="tracks", n_tracks=0,
         min_deposits=290_000, track_len_cm=(1.0, 100.0), z_range_cm=(0.0, 50.0),
-        ne_mean=60.0, seed=1005, gl_order=3, kp=13, nr=400, bp=4, bt=256, lt=1024),
+        ne_mean=60.0, seed=1005, gl_order=3, kp=13, nr=400, bp=4, bt=256, lt=768),
 }
 
 

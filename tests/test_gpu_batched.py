@@ -99,10 +99,11 @@ def test_batch_of_uneven_events_equals_single_event_runs():
         np.testing.assert_array_equal(res["hit_tick"][sel_h], r1["hit_tick"])
 
 
-@pytest.mark.parametrize("bp,bt,lt", [(8, 128, 512), (4, 256, 512), (8, 320, 1024), (8, 640, 1024)])
+@pytest.mark.parametrize("bp,bt,lt", [(8, 128, 384), (8, 128, 512), (4, 256, 512), (8, 320, 768), (8, 320, 1024),
+                                      (8, 512, 768), (8, 640, 1024)])
 def test_autotuner_shapes_match_oracle(bp, bt, lt):
     """Every block shape / FFT length the autotuner may pick is parity-checked."""
     from test_gpu_parity import _full_check
-    cfg = synth.get_config("tiny", nt=1280, bp=bp, bt=bt, lt=lt)
+    cfg = synth.get_config("tiny", nt=1280 if 1280 % bt == 0 else 1536, bp=bp, bt=bt, lt=lt)
     dep, resp = synth.make_event(cfg)
     _full_check(cfg, dep, resp, check_readout=False)

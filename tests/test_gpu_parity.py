@@ -132,6 +132,16 @@ def test_small_blocks_long_fft():
     _full_check(cfg, dep, resp, check_readout=False)
 
 
+@pytest.mark.parametrize("bt,lt,bp,kp,nr,gl", [(128, 384, 8, 9, 200, 2), (256, 768, 8, 9, 200, 2),
+                                              (256, 768, 4, 13, 400, 3)])
+def test_mixed_radix_fft_lengths(bt, lt, bp, kp, nr, gl):
+    """FFT lengths 384 = 3 x 128 and 768 = 3 x 256 (the smallest 2^a 3^b at or above
+    bt + nr - 1 for these shapes): the inverse time transform runs a radix-3 stage."""
+    cfg = synth.get_config("tiny", bt=bt, lt=lt, bp=bp, kp=kp, nr=nr, gl_order=gl)
+    dep, resp = synth.make_event(cfg)
+    _full_check(cfg, dep, resp, check_readout=False)
+
+
 def test_short_blocks():
     """bt = 128 (two 64-tick input blocks per FFT column)."""
     cfg = synth.get_config("tiny", bt=128)
