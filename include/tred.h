@@ -68,7 +68,7 @@ typedef struct {
     int32_t nt;          /* readout window in ticks (multiple of bt) */
     int32_t bp, bt;      /* block shape: bp x bp pixels x bt ticks */
     int32_t kp, nr;      /* field response: kp x kp pixels (odd), nr ticks */
-    int32_t lt;          /* FFT length along time: 512 or 1024, >= bt + nr - 1 */
+    int32_t lt;          /* FFT length along time: 384, 512, 768 or 1024, >= bt + nr - 1 */
     int32_t n_events;    /* independent events stacked along y (0 or 1: a single event).
                             Event e occupies pixel rows [e npx_y, (e + 1) npx_y); no support,
                             footprint or gather crosses an event boundary, so a batch of
