@@ -27,7 +27,10 @@
 //   k_conv_itime  persistent CTAs over (block, mirror row pair, part) items of 16
 //                 columns (8 mirror pairs; 8 columns at lt = 1024), one warp per
 //                 column: inverse time FFT and the MPCP recombination, the next
-//                 item's spectra streamed in by cp.async meanwhile.
+//                 item's spectra streamed in by cp.async meanwhile.  At lt = 512,
+//                 k_conv_itime512 takes the same items with one warp per mirror pair
+//                 and no cross-lane butterflies (a shared transpose between a 16-point
+//                 and a 32-point in-lane stage).
 #include <utility>
 
 #include "tred_internal.cuh"
@@ -493,6 +496,135 @@ __global__ void __launch_bounds__(32 * itime_cols<G>(), 1)
     cp_async_wait<0>();
 }
 
+// Inverse time FFT + MPCP recombination at lt = 512, two columns per warp: a column and
+// its mirror partner.  The same (block, mirror row pair, part) items of 16 columns as
+// k_conv_itime, 8 warps (items of 8 columns over two CTAs per SM read 32-byte runs and
+// ran slower).  With n = l + 32 m (lane l, register m) the transform is a
+// 16-point in-lane DFT over m, the twiddles W_512^(l k1), a per-warp shared transpose,
+// then one 32-point in-lane DFT over l per lane (lane = (column, k1)), giving
+// t = k1 + 16 k2.  No cross-lane butterflies: the only shuffle fetches the partner
+// column's imaginary parts from lane ^ 16, and each half warp stores a 64-byte run.
+constexpr int IT5_WARPS = 8;   // warps per CTA (16-column items: 64-byte runs per row); one CTA per SM
+constexpr size_t itime512_smem_bytes() {
+    return sizeof(float2) * (2 * 2 * IT5_WARPS * 513 + 512 + IT5_WARPS * 2 * 512);
+}
+
+__global__ void __launch_bounds__(32 * IT5_WARPS, 8 / IT5_WARPS)
+    k_conv_itime512(const int32_t *__restrict__ n_blocks_dev, const float2 *__restrict__ yspec,
+                    const float2 *__restrict__ tw, ConvConst c, float *__restrict__ out, int slot_base,
+                    int slot_count, int spec_grid) {
+    constexpr int LT = 512;
+    constexpr int HC = IT5_WARPS, NC = 2 * HC, PARTS = LP / HC, NT = 32 * IT5_WARPS, SROW = LT + 1;
+    extern __shared__ float2 sm[];
+    float2 *S = sm;                          // [2][NC][SROW] spectra, double buffered
+    float2 *twl = S + 2 * NC * SROW;         // [k1][l] = conj(W_512^(l k1))
+    float2 *T = twl + 512;                   // per warp [2 columns][k1][l ^ k1]
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    for (int i = tid; i < 512; i += NT) {
+        float2 w = tw[TW_LT + (i & 31) * (i >> 5)];
+        w.y = -w.y;
+        twl[i] = w;
+    }
+    const int nb = n_blocks_dev[0];
+    const int nloc = min(slot_count, nb - slot_base);
+    if (nloc <= 0) return;
+    const int items = nloc * 8 * PARTS;
+    const int ngrp = conv_round_groups(nloc, 8, spec_grid, slot_count);   // as the spectral kernel split
+    // the rows of mirror row pair rp: the rp-th row a with a < m(a), and bro = m(a)
+    auto rows_of = [&](int rp, int &a, int &bro) {
+        a = -1;
+        int cnt = 0;
+        for (int r = 0; r < LP; ++r) {
+            const int m = (c.bp - 1 - r + 2 * LP) % LP;
+            if (r < m) {
+                if (cnt == rp) {
+                    a = r;
+                    break;
+                }
+                ++cnt;
+            }
+        }
+        bro = (c.bp - 1 - a + 2 * LP) % LP;
+    };
+    auto column = [&](int q, int part, int a, int bro, int &cy, int &cx) {
+        const int cx0 = HC * part + (q % HC);
+        cy = q < HC ? a : bro;
+        cx = q < HC ? cx0 : (c.bp - 1 - cx0 + 2 * LP) % LP;
+    };
+    // thread tid copies column q = tid % NC at frequencies f = tid / NC + (NT / NC) j
+    auto issue = [&](int it, int bsel) {
+        const int sl = it / (8 * PARTS), rp = (it / PARTS) % 8, part = it % PARTS;
+        int a, bro, cy, cx;
+        rows_of(rp, a, bro);
+        const int q = tid % NC;
+        column(q, part, a, bro, cy, cx);
+        const float2 *src = yspec + (size_t)sl * LT * (LP * LP) + cy * LP + cx;
+        float2 *dst = S + (bsel * NC + q) * SROW;
+#pragma unroll 4
+        for (int f = tid / NC; f < LT; f += NT / NC) cp_async8(dst + f, src + (size_t)f * (LP * LP));
+        cp_async_commit();
+    };
+    float2 *Ta = T + warp * 2 * 512;
+    int it = blockIdx.x;
+    if (it < items) issue(it, 0);
+    for (int i = 0; it < items; ++i, it += gridDim.x) {
+        const int cur = i & 1;
+        cp_async_wait<0>();
+        __syncthreads();                     // this item's columns are in place, the other buffer is free
+        if (it + (int)gridDim.x < items) issue(it + gridDim.x, cur ^ 1);
+        const int sl = it / (8 * PARTS), rp = (it / PARTS) % 8, part = it % PARTS;
+        int a, bro, cya, cxa, cyb, cxb;
+        rows_of(rp, a, bro);
+        column(warp, part, a, bro, cya, cxa);          // column A
+        column(warp + HC, part, a, bro, cyb, cxb);     // its mirror partner B
+        {
+            float2 va[16], vb[16];
+            const float2 *sa = S + (cur * NC + warp) * SROW, *sb = S + (cur * NC + warp + HC) * SROW;
+#pragma unroll
+            for (int m = 0; m < 16; ++m) {
+                va[m] = sa[lane + 32 * m];
+                vb[m] = sb[lane + 32 * m];
+            }
+            if (ngrp == 2) {   // the second half of the rounds' spectra, from its own plane
+                const float2 *ga = yspec + (size_t)(nloc + sl) * LT * (LP * LP) + cya * LP + cxa;
+                const float2 *gb = yspec + (size_t)(nloc + sl) * LT * (LP * LP) + cyb * LP + cxb;
+#pragma unroll
+                for (int m = 0; m < 16; ++m) {
+                    va[m] = cadd(va[m], __ldg(ga + (size_t)(lane + 32 * m) * (LP * LP)));
+                    vb[m] = cadd(vb[m], __ldg(gb + (size_t)(lane + 32 * m) * (LP * LP)));
+                }
+            }
+            fft_reg_dif_c<16, true>(va);             // va[k] = sum over m at k1 = bitrev4(k)
+            fft_reg_dif_c<16, true>(vb);
+#pragma unroll
+            for (int k = 0; k < 16; ++k) {
+                const int k1 = bitrev<16>(k);
+                const float2 w = twl[k1 * 32 + lane];
+                Ta[k1 * 32 + (lane ^ k1)] = cmul(va[k], w);
+                Ta[512 + k1 * 32 + (lane ^ k1)] = cmul(vb[k], w);
+            }
+        }
+        __syncwarp();
+        const int hcol = lane >> 4, k1 = lane & 15;
+        float2 y[32];
+        {
+            const float2 *tr = Ta + hcol * 512 + k1 * 32;
+#pragma unroll
+            for (int l = 0; l < 32; ++l) y[l] = tr[l ^ k1];
+        }
+        fft_reg_dif_c<32, true>(y);                  // y[k] = x at t = k1 + 16 bitrev5(k)
+        const int cy = hcol ? cyb : cya, cx = hcol ? cxb : cxa;
+        const int uy = (cy + c.R) % LP, ux = (cx + c.R) % LP;
+        float *o = out + (((size_t)(slot_base + sl) * LP + uy) * LP + ux) * LT + k1;
+#pragma unroll
+        for (int k = 0; k < 32; ++k) {
+            const float im = __shfl_xor_sync(0xffffffffu, y[k].y, 16);   // the partner column, same t
+            o[16 * bitrev<32>(k)] = c.mpcp ? y[k].x + im : y[k].x;
+        }
+    }
+    cp_async_wait<0>();
+}
+
 template <int NB1, int G, bool HZ>
 static int run_conv_bp(tred_handle *h, const int32_t *n_blocks_dev, const float *qeff, float *out,
                     const ConvConst &c, int slot_base, int slot_count, cudaStream_t s) {
@@ -503,6 +635,12 @@ static int run_conv_bp(tred_handle *h, const int32_t *n_blocks_dev, const float 
         if constexpr (G == 8)   // the tensor-core time DFT: lt = 512 only
             cudaFuncSetAttribute(k_conv_spec<NB1, G, true, HZ>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SPEC_SMEM);
         cudaFuncSetAttribute(k_conv_itime<G>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)itime_smem);
+        if constexpr (G == 8)
+        {
+            cudaFuncSetAttribute(k_conv_itime512, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)itime512_smem_bytes());
+            cudaFuncSetAttribute(k_conv_itime512, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+        }
         attr = true;
     }
     const int sms = num_sms(h);
@@ -532,8 +670,12 @@ static int run_conv_bp(tred_handle *h, const int32_t *n_blocks_dev, const float 
                                                                            h->pair_j, h->tw, c, h->yspec, base, cnt,
                                                                            slot_base, nullptr, queue);
         }
-        k_conv_itime<G><<<sms, 32 * itime_cols<G>(), itime_smem, s>>>(n_blocks_dev, h->yspec, h->tw, c, out, base,
-                                                                       cnt);
+        if constexpr (G == 8)
+            k_conv_itime512<<<sms * (8 / IT5_WARPS), 32 * IT5_WARPS, itime512_smem_bytes(), s>>>(
+                n_blocks_dev, h->yspec, h->tw, c, out, base, cnt, sms);
+        else
+            k_conv_itime<G><<<sms, 32 * itime_cols<G>(), itime_smem, s>>>(n_blocks_dev, h->yspec, h->tw, c, out,
+                                                                           base, cnt);
         h->launches += 2;
     }
     return check_cuda(h, cudaGetLastError(), "convolve launch");
