@@ -10,7 +10,9 @@
 //                   restricted to the block's bp x bp input pixels
 //   k_adj_itime     inverse time FFT per (block, pair, input column): real part ->
 //                   dL/dQeff of the first impact, imaginary part -> of the mirror
-//                   impact at the flipped column (Eq. multch read backwards)
+//                   impact at the flipped column (Eq. multch read backwards); at
+//                   lt = 512 k_adj_itime512, two columns per warp and a shared transpose
+//                   between in-lane stages instead of cross-lane butterflies
 //   k_adj_weights   per deposit: the 1-D weights and their derivatives in mu, sigma
 //   k_adj_chain     per (block, deposit): sums of dL/dQeff against the separable
 //                   weights and derivatives -> dL/d(q, mu, sigma) (windows fixed), the
@@ -369,6 +371,110 @@ __global__ void __launch_bounds__(32 * adj_itime_cols<G>(), 1)
     acp_wait<0>();
 }
 
+// The same transform at lt = 512 with two columns per warp (columns w and w + 8 of the
+// item): a 16-point in-lane DFT over m (n = l + 32 m), the twiddles W_512^(l k1), a
+// per-warp shared transpose and one 32-point in-lane DFT per lane (lane = (column, k1)),
+// so t = k1 + 16 k2 with no cross-lane butterflies; each half warp stores 64-byte runs.
+constexpr int AIT5_THREADS = 256;
+constexpr size_t adj_itime512_smem() {
+    return sizeof(float2) * (2 * 16 * 513 + 512 + (AIT5_THREADS / 32) * 2 * 512);
+}
+
+__global__ void __launch_bounds__(AIT5_THREADS, 1)
+    k_adj_itime512(const int32_t *__restrict__ n_blocks_dev, const float2 *__restrict__ gspec,
+                   const int32_t *__restrict__ pair_j, const float2 *__restrict__ tw, AdjConst c,
+                   float *__restrict__ gq, int slot_base, int slot_count) {
+    constexpr int LT = 512, NC = 16, HC = 8, NT = AIT5_THREADS, SROW = LT + 1;
+    extern __shared__ float2 sm_t[];
+    float2 *S = sm_t;                      // [2][NC][LT + 1]
+    float2 *twl = S + 2 * NC * SROW;       // [k1][l] = conj(W_512^(l k1))
+    float2 *T = twl + 512;                 // per warp [2 columns][k1][l ^ k1]
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    for (int i = tid; i < 512; i += NT) {
+        float2 w = tw[TW_LT + (i & 31) * (i >> 5)];
+        w.y = -w.y;
+        twl[i] = w;
+    }
+    const int nb = n_blocks_dev[0];
+    const int nloc = min(slot_count, nb - slot_base);
+    if (nloc <= 0) return;
+    const int cols = c.bp * c.bp;
+    const int groups = (cols + NC - 1) / NC;
+    const int items = nloc * c.npairs * groups;
+    // thread tid copies column q = tid % NC of the item at frequencies f = tid / NC + 16 j
+    auto issue = [&](int item, int bsel) {
+        const int grp = item % groups;
+        const int p = (item / groups) % c.npairs;
+        const int sl = item / (groups * c.npairs);
+        const int q = tid % NC, col = grp * NC + q;
+        if (col < cols) {
+            const int py = col / c.bp, px = col % c.bp;
+            const float2 *src = gspec + ((size_t)sl * c.npairs + p) * LT * 64 + py * 8 + px;
+            float2 *dst = S + (bsel * NC + q) * SROW;
+#pragma unroll 4
+            for (int f = tid / NC; f < LT; f += NT / NC) acp_async8(dst + f, src + (size_t)f * 64);
+        }
+        acp_commit();
+    };
+    float2 *Ta = T + warp * 2 * 512;
+    int item = blockIdx.x;
+    if (item < items) issue(item, 0);
+    for (int i = 0; item < items; ++i, item += gridDim.x) {
+        const int cur = i & 1;
+        acp_wait<0>();
+        __syncthreads();                        // this item's columns are in place, the other buffer is free
+        if (item + (int)gridDim.x < items) issue(item + gridDim.x, cur ^ 1);
+        const int grp = item % groups;
+        const int p = (item / groups) % c.npairs;
+        const int sl = item / (groups * c.npairs);
+        const int cola = grp * NC + warp;
+        if (cola >= cols) continue;             // warp-uniform; then column b is out of range too
+        {
+            float2 va[16], vb[16];
+            const float2 *sa = S + (cur * NC + warp) * SROW, *sb = S + (cur * NC + warp + HC) * SROW;
+#pragma unroll
+            for (int m = 0; m < 16; ++m) {
+                va[m] = sa[lane + 32 * m];
+                vb[m] = sb[lane + 32 * m];
+            }
+            fft_reg_dif_c<16, true>(va);
+            fft_reg_dif_c<16, true>(vb);
+#pragma unroll
+            for (int k = 0; k < 16; ++k) {
+                const int k1 = bitrev<16>(k);
+                const float2 w = twl[k1 * 32 + lane];
+                Ta[k1 * 32 + (lane ^ k1)] = cmul(va[k], w);
+                Ta[512 + k1 * 32 + (lane ^ k1)] = cmul(vb[k], w);
+            }
+        }
+        __syncwarp();
+        const int hcol = lane >> 4, k1 = lane & 15;
+        float2 y[32];
+        {
+            const float2 *tr = Ta + hcol * 512 + k1 * 32;
+#pragma unroll
+            for (int l = 0; l < 32; ++l) y[l] = tr[l ^ k1];
+        }
+        fft_reg_dif_c<32, true>(y);             // y[k] = x at t = k1 + 16 bitrev5(k)
+        const int col = cola + hcol * HC;
+        if (col < cols) {
+            const int slot = slot_base + sl;
+            const int j1 = pair_j[2 * p], j2 = pair_j[2 * p + 1];
+            float *o1 = gq + (((size_t)slot * c.nch + j1) * cols + col) * c.bt + k1;
+            float *o2 = gq + (((size_t)slot * c.nch + (j2 >= 0 ? j2 : j1)) * cols + (cols - 1 - col)) * c.bt + k1;
+#pragma unroll
+            for (int k = 0; k < 32; ++k) {
+                const int t = k1 + 16 * bitrev<32>(k);
+                if (t < c.bt) {
+                    o1[16 * bitrev<32>(k)] = y[k].x;
+                    if (j2 >= 0) o2[16 * bitrev<32>(k)] = y[k].y;
+                }
+            }
+        }
+    }
+    acp_wait<0>();
+}
+
 // ------------------------------------------------------------------ chain rule
 struct ChainConst {
     int ns, bp, bt, ngx, ngy, nt, nbx, nbt, wx, wt, wstride, nch, gl;
@@ -595,6 +701,9 @@ static int run_adjoint_conv(tred_handle *h, const int32_t *block_ids, const int3
     if (!attr) {
         cudaFuncSetAttribute(k_adj_spec<G>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ADJ_SPEC_SMEM);
         cudaFuncSetAttribute(k_adj_itime<G>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)itime_smem);
+        if constexpr (G == 8)
+            cudaFuncSetAttribute(k_adj_itime512, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)adj_itime512_smem());
         attr = true;
     }
     const int sms = num_sms(h);
@@ -606,8 +715,12 @@ static int run_adjoint_conv(tred_handle *h, const int32_t *block_ids, const int3
         if (rc) return rc;
         k_adj_spec<G><<<sms, AS_THREADS, ADJ_SPEC_SMEM, s>>>(n_blocks_dev, block_ids, resid, h->pix_row, h->tw,
                                                              h->rhat, c, h->gspec, base, chunk, queue);
-        k_adj_itime<G><<<sms, 32 * adj_itime_cols<G>(), itime_smem, s>>>(n_blocks_dev, h->gspec, h->pair_j, h->tw, c,
-                                                                         gq, base, chunk);
+        if constexpr (G == 8)
+            k_adj_itime512<<<sms, AIT5_THREADS, adj_itime512_smem(), s>>>(n_blocks_dev, h->gspec, h->pair_j, h->tw,
+                                                                          c, gq, base, chunk);
+        else
+            k_adj_itime<G><<<sms, 32 * adj_itime_cols<G>(), itime_smem, s>>>(n_blocks_dev, h->gspec, h->pair_j,
+                                                                             h->tw, c, gq, base, chunk);
         h->launches += 2;
     }
     return check_cuda(h, cudaGetLastError(), "adjoint convolution launch");
