@@ -709,7 +709,7 @@ def main():
 
     conv_ms = stage_ms["convolve"]
     achieved = CONV_FLOP_PER_BLOCK * nb / (conv_ms / 1e3) / 1e12
-    roofline = {"bound": "alu", "kernel": "tred_convolve (k_conv_spec + k_conv_itime512)",
+    roofline = {"bound": "alu", "kernel": "tred_convolve (k_conv_spec + k_conv_itime_mp)",
                 "achieved": achieved, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
                 "frac": achieved / FP32_PEAK_TFLOPS, "traffic": conv_traffic(nb)[0],
                 "traffic_source": conv_traffic(nb)[1],

@@ -27,8 +27,8 @@
 //   k_conv_itime  persistent CTAs over (block, mirror row pair, part) items of 16
 //                 columns (8 mirror pairs; 8 columns at lt = 1024), one warp per
 //                 column: inverse time FFT and the MPCP recombination, the next
-//                 item's spectra streamed in by cp.async meanwhile.  At lt = 512,
-//                 k_conv_itime512 takes the same items with one warp per mirror pair
+//                 item's spectra streamed in by cp.async meanwhile.  At lt = 512 and
+//                 384, k_conv_itime_mp takes the same items with one warp per mirror pair
 //                 and no cross-lane butterflies (a shared transpose between a 16-point
 //                 and a 32-point in-lane stage).
 #include <utility>
@@ -496,31 +496,35 @@ __global__ void __launch_bounds__(32 * itime_cols<G>(), 1)
     cp_async_wait<0>();
 }
 
-// Inverse time FFT + MPCP recombination at lt = 512, two columns per warp: a column and
-// its mirror partner.  The same (block, mirror row pair, part) items of 16 columns as
-// k_conv_itime, 8 warps (items of 8 columns over two CTAs per SM read 32-byte runs and
-// ran slower).  With n = l + 32 m (lane l, register m) the transform is a
-// 16-point in-lane DFT over m, the twiddles W_512^(l k1), a per-warp shared transpose,
-// then one 32-point in-lane DFT over l per lane (lane = (column, k1)), giving
-// t = k1 + 16 k2.  No cross-lane butterflies: the only shuffle fetches the partner
-// column's imaginary parts from lane ^ 16, and each half warp stores a 64-byte run.
+// Inverse time FFT + MPCP recombination at lt = 64 G = 32 NPL (NPL = 16 or 12: lt = 512
+// or 384), two columns per warp: a column and its mirror partner.  The same (block,
+// mirror row pair, part) items of 16 columns as k_conv_itime, 8 warps (items of 8 columns
+// over two CTAs per SM read 32-byte runs and ran slower).  With n = l + 32 m (lane l,
+// register m) the transform is an NPL-point in-lane DFT over m, the twiddles
+// W_lt^(l k1), a per-warp shared transpose, then one 32-point in-lane DFT over l per
+// lane (lane = (column, k1); at NPL = 12 lanes k1 = 12..15 idle), giving t = k1 + NPL k2.
+// No cross-lane butterflies: the only shuffle fetches the partner column's imaginary
+// parts from lane ^ 16, and each half warp stores a run of NPL consecutive ticks.
 constexpr int IT5_WARPS = 8;   // warps per CTA (16-column items: 64-byte runs per row); one CTA per SM
-constexpr size_t itime512_smem_bytes() {
-    return sizeof(float2) * (2 * 2 * IT5_WARPS * 513 + 512 + IT5_WARPS * 2 * 512);
+template <int G>
+constexpr size_t itime_mp_smem_bytes() {
+    return sizeof(float2) * (2 * 2 * IT5_WARPS * (64 * G + 1) + 2 * G * 32 + IT5_WARPS * 2 * (2 * G) * 32);
 }
 
-__global__ void __launch_bounds__(32 * IT5_WARPS, 8 / IT5_WARPS)
-    k_conv_itime512(const int32_t *__restrict__ n_blocks_dev, const float2 *__restrict__ yspec,
+template <int G>
+__global__ void __launch_bounds__(32 * IT5_WARPS, 1)
+    k_conv_itime_mp(const int32_t *__restrict__ n_blocks_dev, const float2 *__restrict__ yspec,
                     const float2 *__restrict__ tw, ConvConst c, float *__restrict__ out, int slot_base,
-                    int slot_count, int spec_grid) {
-    constexpr int LT = 512;
+                    int slot_count) {
+    constexpr int LT = 64 * G, NPL = 2 * G;
+    static_assert(NPL == 16 || NPL == 12, "lt = 512 or 384");
     constexpr int HC = IT5_WARPS, NC = 2 * HC, PARTS = LP / HC, NT = 32 * IT5_WARPS, SROW = LT + 1;
     extern __shared__ float2 sm[];
     float2 *S = sm;                          // [2][NC][SROW] spectra, double buffered
-    float2 *twl = S + 2 * NC * SROW;         // [k1][l] = conj(W_512^(l k1))
-    float2 *T = twl + 512;                   // per warp [2 columns][k1][l ^ k1]
+    float2 *twl = S + 2 * NC * SROW;         // [k1][l] = conj(W_lt^(l k1))
+    float2 *T = twl + NPL * 32;              // per warp [2 columns][k1][l ^ k1]
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    for (int i = tid; i < 512; i += NT) {
+    for (int i = tid; i < NPL * 32; i += NT) {
         float2 w = tw[TW_LT + (i & 31) * (i >> 5)];
         w.y = -w.y;
         twl[i] = w;
@@ -529,7 +533,7 @@ __global__ void __launch_bounds__(32 * IT5_WARPS, 8 / IT5_WARPS)
     const int nloc = min(slot_count, nb - slot_base);
     if (nloc <= 0) return;
     const int items = nloc * 8 * PARTS;
-    const int ngrp = conv_round_groups(nloc, 8, spec_grid, slot_count);   // as the spectral kernel split
+    const int ngrp = conv_round_groups(nloc, G, gridDim.x, slot_count);   // as the spectral kernel split
     // the rows of mirror row pair rp: the rp-th row a with a < m(a), and bro = m(a)
     auto rows_of = [&](int rp, int &a, int &bro) {
         a = -1;
@@ -564,7 +568,7 @@ __global__ void __launch_bounds__(32 * IT5_WARPS, 8 / IT5_WARPS)
         for (int f = tid / NC; f < LT; f += NT / NC) cp_async8(dst + f, src + (size_t)f * (LP * LP));
         cp_async_commit();
     };
-    float2 *Ta = T + warp * 2 * 512;
+    float2 *Ta = T + warp * 2 * NPL * 32;
     int it = blockIdx.x;
     if (it < items) issue(it, 0);
     for (int i = 0; it < items; ++i, it += gridDim.x) {
@@ -578,10 +582,10 @@ __global__ void __launch_bounds__(32 * IT5_WARPS, 8 / IT5_WARPS)
         column(warp, part, a, bro, cya, cxa);          // column A
         column(warp + HC, part, a, bro, cyb, cxb);     // its mirror partner B
         {
-            float2 va[16], vb[16];
+            float2 va[NPL], vb[NPL];
             const float2 *sa = S + (cur * NC + warp) * SROW, *sb = S + (cur * NC + warp + HC) * SROW;
 #pragma unroll
-            for (int m = 0; m < 16; ++m) {
+            for (int m = 0; m < NPL; ++m) {
                 va[m] = sa[lane + 32 * m];
                 vb[m] = sb[lane + 32 * m];
             }
@@ -589,37 +593,38 @@ __global__ void __launch_bounds__(32 * IT5_WARPS, 8 / IT5_WARPS)
                 const float2 *ga = yspec + (size_t)(nloc + sl) * LT * (LP * LP) + cya * LP + cxa;
                 const float2 *gb = yspec + (size_t)(nloc + sl) * LT * (LP * LP) + cyb * LP + cxb;
 #pragma unroll
-                for (int m = 0; m < 16; ++m) {
+                for (int m = 0; m < NPL; ++m) {
                     va[m] = cadd(va[m], __ldg(ga + (size_t)(lane + 32 * m) * (LP * LP)));
                     vb[m] = cadd(vb[m], __ldg(gb + (size_t)(lane + 32 * m) * (LP * LP)));
                 }
             }
-            fft_reg_dif_c<16, true>(va);             // va[k] = sum over m at k1 = bitrev4(k)
-            fft_reg_dif_c<16, true>(vb);
+            fft_reg_any<NPL, true>(va);              // va[k] = sum over m at k1 = fft_perm(k)
+            fft_reg_any<NPL, true>(vb);
 #pragma unroll
-            for (int k = 0; k < 16; ++k) {
-                const int k1 = bitrev<16>(k);
+            for (int k = 0; k < NPL; ++k) {
+                const int k1 = fft_perm<NPL>(k);
                 const float2 w = twl[k1 * 32 + lane];
                 Ta[k1 * 32 + (lane ^ k1)] = cmul(va[k], w);
-                Ta[512 + k1 * 32 + (lane ^ k1)] = cmul(vb[k], w);
+                Ta[NPL * 32 + k1 * 32 + (lane ^ k1)] = cmul(vb[k], w);
             }
         }
         __syncwarp();
         const int hcol = lane >> 4, k1 = lane & 15;
+        const int kr = k1 < NPL ? k1 : NPL - 1;       // idle lanes re-read a valid row
         float2 y[32];
         {
-            const float2 *tr = Ta + hcol * 512 + k1 * 32;
+            const float2 *tr = Ta + hcol * NPL * 32 + kr * 32;
 #pragma unroll
-            for (int l = 0; l < 32; ++l) y[l] = tr[l ^ k1];
+            for (int l = 0; l < 32; ++l) y[l] = tr[l ^ kr];
         }
-        fft_reg_dif_c<32, true>(y);                  // y[k] = x at t = k1 + 16 bitrev5(k)
+        fft_reg_dif_c<32, true>(y);                  // y[k] = x at t = k1 + NPL bitrev5(k)
         const int cy = hcol ? cyb : cya, cx = hcol ? cxb : cxa;
         const int uy = (cy + c.R) % LP, ux = (cx + c.R) % LP;
         float *o = out + (((size_t)(slot_base + sl) * LP + uy) * LP + ux) * LT + k1;
 #pragma unroll
         for (int k = 0; k < 32; ++k) {
             const float im = __shfl_xor_sync(0xffffffffu, y[k].y, 16);   // the partner column, same t
-            o[16 * bitrev<32>(k)] = c.mpcp ? y[k].x + im : y[k].x;
+            if (k1 < NPL) o[NPL * bitrev<32>(k)] = c.mpcp ? y[k].x + im : y[k].x;
         }
     }
     cp_async_wait<0>();
@@ -635,11 +640,10 @@ static int run_conv_bp(tred_handle *h, const int32_t *n_blocks_dev, const float 
         if constexpr (G == 8)   // the tensor-core time DFT: lt = 512 only
             cudaFuncSetAttribute(k_conv_spec<NB1, G, true, HZ>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SPEC_SMEM);
         cudaFuncSetAttribute(k_conv_itime<G>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)itime_smem);
-        if constexpr (G == 8)
-        {
-            cudaFuncSetAttribute(k_conv_itime512, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)itime512_smem_bytes());
-            cudaFuncSetAttribute(k_conv_itime512, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+        if constexpr (G == 8 || G == 6) {
+            cudaFuncSetAttribute(k_conv_itime_mp<G>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)itime_mp_smem_bytes<G>());
+            cudaFuncSetAttribute(k_conv_itime_mp<G>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
         }
         attr = true;
     }
@@ -670,9 +674,9 @@ static int run_conv_bp(tred_handle *h, const int32_t *n_blocks_dev, const float 
                                                                            h->pair_j, h->tw, c, h->yspec, base, cnt,
                                                                            slot_base, nullptr, queue);
         }
-        if constexpr (G == 8)
-            k_conv_itime512<<<sms * (8 / IT5_WARPS), 32 * IT5_WARPS, itime512_smem_bytes(), s>>>(
-                n_blocks_dev, h->yspec, h->tw, c, out, base, cnt, sms);
+        if constexpr (G == 8 || G == 6)
+            k_conv_itime_mp<G><<<sms, 32 * IT5_WARPS, itime_mp_smem_bytes<G>(), s>>>(n_blocks_dev, h->yspec, h->tw,
+                                                                                  c, out, base, cnt);
         else
             k_conv_itime<G><<<sms, 32 * itime_cols<G>(), itime_smem, s>>>(n_blocks_dev, h->yspec, h->tw, c, out,
                                                                            base, cnt);
