@@ -76,6 +76,16 @@ def test_tiny_no_mpcp_asymmetric_response():
     _full_check(cfg, dep, resp, mpcp=0, check_readout=False)
 
 
+@pytest.mark.parametrize("bt,lt", [(128, 384), (256, 768)])
+def test_no_mpcp_asymmetric_mixed_radix(bt, lt):
+    """The unpacked path at the mixed-radix FFT lengths: every inverse time transform
+    form (two columns per warp at 384, one per warp at 768) with no mirror recombination."""
+    cfg = synth.get_config("tiny", bt=bt, lt=lt)
+    dep = synth.make_deposits(cfg)
+    resp = synth.make_response(cfg, symmetric=False)
+    _full_check(cfg, dep, resp, mpcp=0, check_readout=False)
+
+
 def test_tiny_exact_tent_fp64_tails():
     cfg = synth.get_config("tiny")
     dep, resp = synth.make_event(cfg)
