@@ -9,8 +9,8 @@ import synth
 pytestmark = pytest.mark.gpu
 
 
-def _event(n=None, start=0):
-    cfg = synth.get_config("tiny")
+def _event(n=None, start=0, **shape):
+    cfg = synth.get_config("tiny", **shape)
     dep, resp = synth.make_event(cfg)
     if n is not None:
         dep = {k: v[start:start + n].copy() for k, v in dep.items()}
@@ -66,9 +66,13 @@ def _oracle_backward(cfg, dep, resp, tid, twave):
     return loss, g7, gin, gglob
 
 
-@pytest.mark.parametrize("n,start", [(120, 200), (500, 0)])
-def test_adjoint_matches_oracle_gradient(n, start):
-    cfg, dep, resp = _event(n, start)
+@pytest.mark.parametrize("n,start,shape", [(120, 200, {}), (500, 0, {}),
+                                           (300, 100, {"bp": 4, "bt": 128, "lt": 512})])
+def test_adjoint_matches_oracle_gradient(n, start, shape):
+    """Gradients of the loss against the oracle's adjoint; the last case has 16 input
+    columns per block (one item of the inverse time transform, every warp's second
+    column inside it) and 128-tick blocks (the transform keeps t < 128 of 512)."""
+    cfg, dep, resp = _event(n, start, **shape)
     tid, twave = _target(cfg, dep, resp)
     loss, g7, gin, gglob = _gpu_backward(cfg, dep, resp, tid, twave)
     rloss, rg7, rgin, rgglob = _oracle_backward(cfg, dep, resp, tid, twave)
@@ -100,7 +104,7 @@ def test_autograd_function_matches_oracle():
                                x["x"], x["y"], x["z"], x["t0"], x["ne"], DL, DT, tau)
     loss.backward()
     rloss, rg7, rgin, rgglob = _oracle_backward(cfg, dep, resp, tid, twave)
-    assert abs(float(loss) - rloss) <= 1e-5 * rloss
+    assert abs(float(loss.detach()) - rloss) <= 1e-5 * rloss
     for k, name in enumerate(["x", "y", "t0", "ne"]):
         g = x[name].grad.cpu().numpy().astype(np.float64)
         assert np.abs(g - rgin[:, k]).max() <= 1e-4 * np.abs(rgin[:, k]).max(), name
