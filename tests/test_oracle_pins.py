@@ -188,6 +188,16 @@ def test_drift_closed_form():
     assert abs(d["q"][0] - 600.0 * math.exp(-td / 2200.0)) < 1e-9
     assert d["lo"][0, 0] == math.floor(d["mu"][0, 0] - 4 * d["sig"][0, 0])
     assert d["hi"][0, 2] == math.ceil(d["mu"][0, 2] + 4 * d["sig"][0, 2])
+    # worked by hand for deposit 0 (62.5 us of drift): transverse spread
+    # sqrt(2 * 8.8 cm^2/s * 62.5 us) = 0.3317 mm = 0.7538 sub-cells of 0.44 mm, 0.9045 with
+    # the 0.5-cell floor added in quadrature; longitudinal sqrt(2 * 4 cm^2/s * 62.5 us) =
+    # 0.2236 mm = 2.795 ticks at 1.6 mm/us and 50 ns, 2.839 with the floor; charge after
+    # attachment 600 exp(-62.5 / 2200) = 583.19 electrons; x = 1 cm is 22.727 sub-cell
+    # widths, grid coordinate 22.227 (grid points at sub-cell centres), y = 2 cm 44.955
+    assert abs(d["sig"][0, 0] - 0.9045) < 1e-4 and abs(d["sig"][0, 1] - 0.9045) < 1e-4
+    assert abs(d["sig"][0, 2] - 2.8395) < 1e-4
+    assert abs(d["q"][0] - 583.19) < 1e-2
+    assert abs(d["mu"][0, 0] - 22.227) < 1e-3 and abs(d["mu"][0, 1] - 44.955) < 1e-3
     # zero drift: widths at the floor
     assert abs(d["sig"][1, 0] - 0.5) < 1e-15 and abs(d["sig"][1, 2] - 0.5) < 1e-15
     assert d["q"][3] == 0.0
@@ -431,3 +441,61 @@ def test_readout_successive_digitisations_follow_the_running_sum():
         cs = np.cumsum(wave[p])
         np.testing.assert_allclose(cq[:, 1:] - cq[:, :1], cs[g[:, 1:]] - cs[g[:, :1]], rtol=0, atol=1e-6)
         assert t[0] == h0t[h0p == p][0] and abs(q[0] - h0c[h0p == p][0]) < 1e-9
+
+
+# --------------------------------------------------------------- active pixel set
+def _footprint_brute_force(cfg, blocks):
+    """Pixels of each block's output footprint written out per pixel: block bx covers
+    pixels [bx bp, bx bp + bp - 1]; the response reaches R pixels further each way, so
+    the footprint is [bx bp - R, bx bp + bp - 1 + R] per axis, clipped to the plane."""
+    R = (cfg.kp - 1) // 2
+    nbx, nbt = cfg.npx // cfg.bp, cfg.nt // cfg.bt
+    out = set()
+    for blk in blocks:
+        bxy = int(blk) // nbt
+        bx, by = bxy % nbx, bxy // nbx
+        for py in range(cfg.npx):
+            for px in range(cfg.npx):
+                if (by * cfg.bp - R <= py <= by * cfg.bp + cfg.bp - 1 + R
+                        and bx * cfg.bp - R <= px <= bx * cfg.bp + cfg.bp - 1 + R):
+                    out.add(py * cfg.npx + px)
+    return np.array(sorted(out), np.int32)
+
+
+def test_active_pixels_cover_every_pixel_with_current():
+    """The electrode set the gather accumulates on (Fig. flowchart: unique electrodes)
+    is every pixel some active block's output reaches.  Pinned two ways on the 32 x 32
+    plane with an x-odd response: it equals a per-pixel brute-force footprint of the
+    active blocks (including blocks on the plane's edges, where it is clipped), and every
+    pixel whose current (computed on the whole plane) is nonzero belongs to it.  The
+    nonzero set needs the full R-pixel halo (a footprint one pixel narrower misses
+    pixels with current), so a footprint too small or too large fails."""
+    cfg = synth.get_config("tiny")
+    resp = synth.make_response(cfg, symmetric=False)
+    w = cfg.npx * cfg.pitch_cm
+    rng = np.random.default_rng(17)
+    # deposits in corner, edge and interior blocks, some on block boundaries; two sit in
+    # the last pixel column / row of a block, clear of its neighbours, so that their
+    # current reaches R pixels past the block into a footprint no other block covers
+    a = cfg.pitch_cm
+    xs = [0.05, w - 0.05, 0.05, w - 0.05, 8 * a, 8 * a - 0.01, 0.5 * w, 7.5 * a, 20.5 * a]
+    ys = [0.05, 0.05, w - 0.05, w - 0.05, 8 * a, 24 * a - 0.01, 0.5 * w, 12.5 * a, 23.5 * a]
+    n = len(xs)
+    dep = {"x": np.asarray(xs, np.float32), "y": np.asarray(ys, np.float32),
+           "z": rng.uniform(0.5, 6.0, n).astype(np.float32), "t0": np.full(n, 2.0, np.float32),
+           "ne": np.full(n, 2000.0, np.float32)}
+    p = oracle.params(cfg)
+    d = oracle.drift(p, dep)
+    assert np.all(d["valid"] == 1)
+    ids, _ = oracle.active_blocks(p, d)
+    act = oracle.active_pixels(p, ids, cfg.kp)
+    np.testing.assert_array_equal(act, _footprint_brute_force(cfg, ids))
+    nbx, nbt = cfg.npx // cfg.bp, cfg.nt // cfg.bt
+    bxy = ids // nbt
+    assert {0, nbx - 1} <= set((bxy % nbx).tolist()) and {0, nbx - 1} <= set((bxy // nbx).tolist())
+    wave = oracle.pixel_currents(p, d, resp, _all_pixels(cfg))
+    live = np.nonzero(np.any(wave != 0.0, axis=1))[0].astype(np.int32)
+    assert len(live) > 0
+    assert np.all(np.isin(live, act)), np.setdiff1d(live, act)[:10]
+    narrow = _footprint_brute_force(synth.get_config("tiny", kp=cfg.kp - 2), ids)
+    assert not np.all(np.isin(live, narrow))
