@@ -374,12 +374,19 @@ int32_t tred_param_grads(tred_handle *h, int32_t n, const float *z, const tred_d
  *  - status_dev: caller-owned device int32[TRED_STATUS_WORDS]; words 0 (bits), 2 and
  *    3 are written as by tred_blockbin; the caller clears it when it wants to.
  *  - The first call on a device looks up the array's device address on the current
- *    device (cudaGetSymbolAddress); make that first call before any stream capture.
+ *    device (cudaGetSymbolAddress) and caches it.  With CUDA's lazy module loading
+ *    (the default) that first call may also load the library's device code, which
+ *    reserves the array and synchronises: make one warm-up call on each device before
+ *    the region that must not allocate, and before any stream capture.
+ *  - cudaDeviceReset unloads the array and leaves the cached address stale: do not
+ *    call this entry point on a device after resetting it in the same process.
  *  - Every call reuses the same array and the array keeps the last call's contents
  *    (the counts are cleared at the start of each call).  Calls whose work overlaps
  *    on the GPU (several streams, or several host threads) race on it and give wrong
  *    results: serialise them on one stream.
- *  - Arguments otherwise as tred_blockbin; geometry as in tred_create. */
+ *  - Arguments otherwise as tred_blockbin.  The geometry gets tred_create's checks
+ *    (and n_events must be 0 or 1); a failed check, a null array in *deps (when
+ *    n > 0) or a null output gives TRED_ERR_INVALID_ARG with nothing enqueued. */
 #define TRED_NOALLOC_MAX_GRID_BLOCKS (1 << 19)
 int32_t tred_blockbin_noalloc(const tred_geometry *geom, int32_t n, const tred_deposits *deps,
                               int32_t *block_ids, int32_t *block_counts, int32_t *dep_offsets,

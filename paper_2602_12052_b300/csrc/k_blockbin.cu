@@ -345,8 +345,9 @@ int launch_blockbin(tred_handle *h, int n, const tred_deposits &deps, int32_t *b
 // ---------------------------------------------------------------------------
 // tred_blockbin_noalloc: the same binning for callers that may not allocate
 // device memory themselves (see include/tred.h).  Its scratch lives in this
-// file-scope array, allocated when the library is loaded onto a device and held
-// until the process exits.
+// file-scope array, reserved when the library's device code is loaded onto a
+// device (with CUDA's lazy module loading, possibly during the first call) and
+// held until the process exits.
 // ---------------------------------------------------------------------------
 namespace tred {
 
@@ -358,7 +359,8 @@ constexpr int64_t NOALLOC_WORDS = 3 * NOALLOC_MAX_GRID_BLOCKS + 2 * NOALLOC_MAX_
 static __device__ __align__(256) int32_t g_noalloc_scratch[NOALLOC_WORDS];
 
 // Device address of g_noalloc_scratch per device, looked up on the first call made
-// with that device current.
+// with that device current.  A cudaDeviceReset unloads the module and makes the cached
+// address stale: the header tells callers not to use this entry point after a reset.
 static int32_t *g_noalloc_ptr[64];
 
 static int noalloc_scratch(int32_t **out) {
@@ -385,13 +387,15 @@ extern "C" int32_t tred_blockbin_noalloc(const tred_geometry *geom, int32_t n, c
                                          int32_t *n_blocks_dev, int32_t *status_dev, void *stream) {
     using namespace tred;
     if (!geom || n < 0 || !block_ids || !block_counts || !dep_offsets || !n_blocks_dev || !status_dev ||
-        max_blocks < 1 || max_pairs < 0 || (max_pairs > 0 && !dep_index) || (n > 0 && !deps))
+        max_blocks < 1 || max_pairs < 0 || (max_pairs > 0 && !dep_index) || (n > 0 && !deps_ok(deps)))
         return TRED_ERR_INVALID_ARG;
     const tred_geometry &g = *geom;
-    if (g.n_events > 1) return TRED_ERR_INVALID_ARG;   // single event only
-    if (g.n_sub < 1 || g.bp < 1 || g.bt < 1 || g.npx_x < g.bp || g.npx_y < g.bp || g.npx_x % g.bp ||
-        g.npx_y % g.bp || g.nt < g.bt || g.nt % g.bt)
+    char msg[256];
+    if (validate_geometry(&g, msg, sizeof msg) != TRED_OK) {   // the checks of tred_create
+        fprintf(stderr, "tred_blockbin_noalloc: %s\n", msg);
         return TRED_ERR_INVALID_ARG;
+    }
+    if (g.n_events > 1) return TRED_ERR_INVALID_ARG;   // single event only
     const int64_t nbx = g.npx_x / g.bp, nby = g.npx_y / g.bp, nbt = g.nt / g.bt;
     const int64_t nblk = nbx * nby * nbt;
     if (nblk > NOALLOC_MAX_GRID_BLOCKS || max_blocks > NOALLOC_MAX_GRID_BLOCKS) {

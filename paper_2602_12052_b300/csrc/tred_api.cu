@@ -84,8 +84,19 @@ extern "C" {
 
 const char *tred_last_error(const tred_handle *h) { return h ? h->err : "null handle"; }
 
-static int validate(const tred_geometry *g, const tred_params *p, char *msg, size_t len) {
+}  // extern "C"
+
+namespace tred {
+
+bool deps_ok(const tred_deposits *d) {
+    return d && d->cell_x && d->cell_y && d->cell_t && d->frac_x && d->frac_y && d->frac_t &&
+           d->sigma_x && d->sigma_y && d->sigma_t && d->lo_x && d->lo_y && d->lo_t && d->hi_x &&
+           d->hi_y && d->hi_t && d->q;
+}
+
+int validate_geometry(const tred_geometry *g, char *msg, size_t len) {
     auto bad = [&](const char *m) { snprintf(msg, len, "%s", m); return TRED_ERR_INVALID_ARG; };
+    if (!g) return bad("null geometry");
     if (!(g->pitch_cm > 0 && g->tick_us > 0)) return bad("pitch and tick must be > 0");
     if (g->n_sub < 2 || g->n_sub % 2 || g->n_sub > 32) return bad("n_sub must be even, 2..32");
     if ((int64_t)g->n_sub * g->n_sub * g->bp * g->bp > 6400) return bad("n_sub^2 bp^2 must be <= 6400");
@@ -102,6 +113,16 @@ static int validate(const tred_geometry *g, const tred_params *p, char *msg, siz
     if ((int64_t)g->npx_x * g->n_sub > (1 << 28) ||
         (int64_t)g->npx_y * g->n_sub * (g->n_events > 1 ? g->n_events : 1) > (1 << 28))
         return bad("plane too large");
+    return TRED_OK;
+}
+
+}  // namespace tred
+
+extern "C" {
+
+static int validate(const tred_geometry *g, const tred_params *p, char *msg, size_t len) {
+    auto bad = [&](const char *m) { snprintf(msg, len, "%s", m); return TRED_ERR_INVALID_ARG; };
+    if (validate_geometry(g, msg, len) != TRED_OK) return TRED_ERR_INVALID_ARG;
     if (!(p->v_cm_per_us > 0 && p->lifetime_us > 0 && p->DL_cm2_per_s >= 0 && p->DT_cm2_per_s >= 0))
         return bad("bad transport constants");
     if (!(p->sigma0_cells_xy > 0 && p->sigma0_ticks > 0)) return bad("sigma floors must be > 0");
@@ -278,12 +299,6 @@ int32_t tred_sync_status(tred_handle *h, void *stream, int32_t *host_status) {
                                            cudaMemcpyDeviceToHost, s), "read status");
     if (rc) return rc;
     return check_cuda(h, cudaStreamSynchronize(s), "sync status");
-}
-
-static bool deps_ok(const tred_deposits *d) {
-    return d && d->cell_x && d->cell_y && d->cell_t && d->frac_x && d->frac_y && d->frac_t &&
-           d->sigma_x && d->sigma_y && d->sigma_t && d->lo_x && d->lo_y && d->lo_t && d->hi_x &&
-           d->hi_y && d->hi_t && d->q;
 }
 
 int32_t tred_set_transport(tred_handle *h, const tred_params *params) {

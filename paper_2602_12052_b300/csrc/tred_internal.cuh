@@ -95,6 +95,11 @@ constexpr int TW_LT = 128;          // lt entries (<= 1024)
 constexpr int TW_TOTAL = 128 + 1024;
 
 int set_error(tred_handle *h, int code, const char *fmt, ...);
+// argument checks shared by the handle path and the allocation-free binning: every
+// device array of a deposit set present; the geometry accepted by tred_create (a
+// message in msg otherwise)
+bool deps_ok(const tred_deposits *d);
+int validate_geometry(const tred_geometry *g, char *msg, size_t len);
 int check_cuda(tred_handle *h, cudaError_t e, const char *what);
 
 // kernel launchers (each .cu file)

@@ -55,3 +55,34 @@ def test_create_rejects_bad_geometry_without_gpu(lib):
     h = ctypes.c_void_p()
     rc = abi.load().tred_create(ctypes.byref(g), ctypes.byref(p), 10, 10, 10, ctypes.byref(h))
     assert rc == abi.TRED_ERR_INVALID_ARG and not h.value
+
+
+def test_noalloc_blockbin_rejects_bad_arguments_without_gpu(lib):
+    """The allocation-free binning checks its arguments as the handle path does, before
+    any device call: a deposit set with one null array, a negative event count, a
+    geometry tred_create rejects and a missing output all give TRED_ERR_INVALID_ARG."""
+    from paper_2602_12052_b300 import abi
+    L = abi.load()
+
+    def geom(**kw):
+        base = dict(pitch_cm=0.44, n_sub=10, tick_us=0.05, npx_x=32, npx_y=32, nt=1024, bp=8, bt=256,
+                    kp=9, nr=200, lt=512, n_events=0)
+        base.update(kw)
+        return abi.Geometry(**base)
+
+    fake = ctypes.c_void_p(256)                       # never dereferenced: the checks come first
+    full = abi.Deposits(**{f: 256 for f in abi.DEPOSIT_FIELDS})
+    one_null = abi.Deposits(**{f: (None if f == "hi_x" else 256) for f in abi.DEPOSIT_FIELDS})
+
+    def call(g, n, deps, out=fake):
+        return L.tred_blockbin_noalloc(ctypes.byref(g), n, ctypes.byref(deps) if deps is not None else None,
+                                       out, fake, fake, fake, 64, 512, fake, fake, None)
+
+    assert call(geom(), 10, one_null) == abi.TRED_ERR_INVALID_ARG
+    assert call(geom(), 10, None) == abi.TRED_ERR_INVALID_ARG
+    assert call(geom(n_events=-1), 10, full) == abi.TRED_ERR_INVALID_ARG
+    assert call(geom(n_events=2), 10, full) == abi.TRED_ERR_INVALID_ARG
+    assert call(geom(n_sub=1 << 20), 10, full) == abi.TRED_ERR_INVALID_ARG     # n_sub * npx overflow
+    assert call(geom(bp=6), 10, full) == abi.TRED_ERR_INVALID_ARG
+    assert call(geom(), 10, full, out=None) == abi.TRED_ERR_INVALID_ARG
+    assert call(geom(), -1, full) == abi.TRED_ERR_INVALID_ARG

@@ -16,18 +16,19 @@ import synth
 pytestmark = pytest.mark.gpu
 
 
-def _bin_both(cfg, dep):
+def _bin_both(cfg, dep, mb=None):
     import torch
     from paper_2602_12052_b300 import abi, build, tred
     build.build()
     lib = abi.load()
     dev = torch.device("cuda")
     n = len(dep["x"])
-    h = tred.Handle(tred.geometry(cfg), tred.params(cfg), max(n, 1), min(cfg.n_blocks, 20000), 1)
+    mb = mb or min(cfg.n_blocks, 20000)
+    h = tred.Handle(tred.geometry(cfg), tred.params(cfg), max(n, 1), mb, 1)
     deps = tred.DepositBuffers(max(n, 1), dev)
     x = {k: torch.from_numpy(v).to(dev) for k, v in dep.items()}
-    tred.tred_drift(h, n, x["x"], x["y"], x["z"], x["t0"], x["ne"], deps)
-    mb = min(cfg.n_blocks, 20000)
+    if n:
+        tred.tred_drift(h, n, x["x"], x["y"], x["z"], x["t0"], x["ne"], deps)
     mp = 8 * max(n, 1)
 
     def bufs():
@@ -61,9 +62,10 @@ def _same(ref, o):
         np.testing.assert_array_equal(a[:nb].cpu().numpy(), b[:nb].cpu().numpy())
     off = ref[2][:nb + 1].cpu().numpy()
     np.testing.assert_array_equal(off, o[2][:nb + 1].cpu().numpy())
+    # CSR: the same deposit ids in the same (ascending per block) order, which fixes the
+    # order of the effective charge's sums downstream
     ri, oi = ref[3].cpu().numpy(), o[3].cpu().numpy()
-    for b in range(nb):                      # CSR: same deposit set per block
-        np.testing.assert_array_equal(np.sort(ri[off[b]:off[b + 1]]), np.sort(oi[off[b]:off[b + 1]]))
+    np.testing.assert_array_equal(ri[:off[nb]], oi[:off[nb]])
     return nb
 
 
@@ -76,6 +78,32 @@ def test_noalloc_blockbin_matches_handle_path(name):
         nb = _same(ref, o)
         assert nb > 0
         assert status[0] == ref_status[0] == 0
+        assert status[2] == ref_status[2] and status[3] == ref_status[3]
+
+
+def test_noalloc_blockbin_empty_event():
+    """No deposits: no blocks, an empty CSR and a clear status, call after call."""
+    cfg = synth.get_config("tiny")
+    dep = {k: np.zeros(0, np.float32) for k in ("x", "y", "z", "t0", "ne")}
+    ref, ref_status, outs = _bin_both(cfg, dep)
+    for o, status in outs:
+        assert _same(ref, o) == 0
+        assert int(o[2][0].item()) == 0
+        assert status[0] == ref_status[0] == 0 and status[2] == 0 and status[3] == 0
+
+
+def test_noalloc_blockbin_block_overflow_matches_handle_path():
+    """max_blocks below the event's active block count: both paths set the block-overflow
+    bit, keep the first max_blocks blocks in order and clamp the CSR the same way."""
+    from paper_2602_12052_b300 import abi
+    cfg = synth.get_config("tiny")
+    dep = synth.make_deposits(cfg)
+    ref, ref_status, outs = _bin_both(cfg, dep, mb=3)
+    assert ref_status[2] > 3                 # more active blocks than kept
+    for o, status in outs:
+        assert _same(ref, o) == 3
+        assert status[0] & abi.TRED_ST_BLOCK_OVERFLOW
+        assert status[0] == ref_status[0]
         assert status[2] == ref_status[2] and status[3] == ref_status[3]
 
 
