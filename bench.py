@@ -31,37 +31,99 @@ if ROOT not in sys.path:
 METRIC = "depos/s to pixel currents at <=1e-5 rel L2 vs FP64 oracle; % of HBM/TC roofline"
 WORKLOAD = "module1M"
 # Algorithmic FLOPs of one block's convolution: 50 packed forward 3-D FFTs of
-# N = 16*16*512 points at 5 N log2 N, 50 spectrum products at 8 N, one inverse FFT.
-_N = 16 * 16 * 512
-CONV_FLOP_PER_BLOCK = 50 * 5 * _N * 17 + 50 * 8 * _N + 5 * _N * 17
+# N = 16*16*lt points at 5 N log2 N, 50 spectrum products at 8 N, one inverse FFT.
+def conv_flop_per_block(lt=512, npairs=50, lp=16):
+    import math
+    n = lp * lp * lt
+    return npairs * 5 * n * math.log2(n) + npairs * 8 * n + 5 * n * math.log2(n)
+
+
+CONV_FLOP_PER_BLOCK = conv_flop_per_block()
 # FP32 ALU peak from unit counts and the maximum clock: 148 SMs x 128 FP32 lanes x
-# 2 flop (FMA) x 2.032 GHz.
+# 2 flop (FMA) x 2.032 GHz.  The measured one (an FMA loop over every SM, tred_fp32_peak)
+# is reported beside it.
 SMS, FP32_LANES, SM_MAX_GHZ = 148, 128, 2.032
 FP32_PEAK_TFLOPS = SMS * FP32_LANES * 2 * SM_MAX_GHZ / 1e3
+
+
+def _profile_figures():
+    """Per-block figures of the committed ncu capture of the convolution on module20
+    (profiles/conv_traffic_module20.txt) with the source hashes they were taken at."""
+    path = os.path.join(ROOT, "profiles", "conv_traffic_module20.txt")
+    kv = {}
+    try:
+        for line in open(path):
+            parts = line.split()
+            if not parts or parts[0].startswith("#"):
+                continue
+            if len(parts) >= 3 and parts[1] == "sha256":
+                kv[parts[0]] = parts[2]
+            elif len(parts) >= 2:
+                kv[parts[0]] = float(parts[1])
+    except OSError:
+        pass
+    return kv
+
+
+CONV_SOURCES = ("k_conv.cu", "conv_item.cuh", "tred_internal.cuh")
+
+
+def _source_sha(names=CONV_SOURCES):
+    """sha256 over the convolution's source files (the kernels and the headers they use)."""
+    import hashlib
+    h = hashlib.sha256()
+    for name in names:
+        h.update(open(os.path.join(ROOT, "paper_2602_12052_b300", "csrc", name), "rb").read())
+    return h.hexdigest()
 
 
 def conv_traffic(blocks):
     """DRAM bytes of one tred_convolve call over `blocks` active blocks: the per-block
     read + write bytes of an ncu capture (profiles/conv_traffic_module20.txt), scaled by
     the blocks, or None when the convolution source changed since the capture."""
-    import hashlib
-    path = os.path.join(ROOT, "profiles", "conv_traffic_module20.txt")
-    try:
-        lines = [l.split() for l in open(path) if l.strip() and not l.startswith("#")]
-    except OSError:
-        return None, None
-    kv = {}
-    for parts in lines:
-        if parts[0] == "k_conv.cu" and parts[1] == "sha256":
-            kv["sha"] = parts[2]
-        elif parts[0] == "conv_dram_bytes_per_block":
-            kv["per_block"] = float(parts[1])
-    src = os.path.join(ROOT, "paper_2602_12052_b300", "csrc", "k_conv.cu")
-    cur = hashlib.sha256(open(src, "rb").read()).hexdigest()
-    if kv.get("sha") != cur or "per_block" not in kv:
-        return None, "capture predates the current k_conv.cu"
-    return kv["per_block"] * blocks, ("ncu dram__bytes_read+write of module20 (255 blocks), "
-                                      f"{kv['per_block']:.4g} B per block, scaled to {blocks} blocks")
+    kv = _profile_figures()
+    if kv.get("conv_sources") != _source_sha() or "conv_dram_bytes_per_block" not in kv:
+        return None, "capture predates the current convolution sources"
+    per = kv["conv_dram_bytes_per_block"]
+    return per * blocks, ("ncu dram__bytes_read+write of module20 (255 blocks), "
+                          f"{per:.4g} B per block, scaled to {blocks} blocks")
+
+
+def conv_counters():
+    """Executed FP32 FLOPs per block (2 FFMA + FADD + FMUL thread instructions) and the
+    FMA-pipe share of the spectral kernel, from the same capture, or {} when stale."""
+    kv = _profile_figures()
+    if kv.get("conv_sources") != _source_sha():
+        return {}
+    out = {}
+    for k in ("conv_executed_flop_per_block", "conv_spec_fma_pipe_pct", "conv_spec_issue_active_pct"):
+        if k in kv:
+            out[k] = kv[k]
+    return out
+
+
+def measured_fp32_peak():
+    """FP32 FMA TFLOP/s and SM count measured on this device (tred_fp32_peak)."""
+    from paper_2602_12052_b300 import tred
+    tf, sms = tred.tred_fp32_peak(iters=32768)
+    return tf, sms
+
+
+def alu_roofline(kernel, flop_per_block, blocks, ms, clocks, peak_meas=None):
+    """The FP32-ALU roofline object of a convolution-dominated form: algorithmic FLOPs
+    (unpruned 5 N log2 N count) per launch over its CUDA-event time, against the
+    unit-count peak and the measured FMA-loop peak."""
+    achieved = flop_per_block * blocks / (ms / 1e3) / 1e12
+    r = {"bound": "alu", "kernel": kernel, "achieved": achieved, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
+         "frac": achieved / FP32_PEAK_TFLOPS, "traffic": None,
+         "peak_source": "148 SMs x 128 FP32 lanes x 2 flop x 2.032 GHz (unit counts, max clock)",
+         "flop_per_block": flop_per_block, "blocks": blocks, "ms": ms}
+    if peak_meas:
+        r["peak_measured"] = peak_meas
+        r["frac_vs_measured"] = achieved / peak_meas
+    if clocks and clocks.get("sm_mhz"):
+        r["frac_at_observed_clock"] = achieved / (FP32_PEAK_TFLOPS * clocks["sm_mhz"] / 2032.0)
+    return r
 
 
 def _args():
@@ -88,6 +150,9 @@ def _args():
                     help="0: trigger-reset (default); 1: successive digitisations without resets "
                          "(--n-samples per trigger); 2: fixed-charge integration")
     ap.add_argument("--n-samples", type=int, default=3, help="digitisations per trigger in readout mode 1")
+    ap.add_argument("--fused", type=int, default=0, choices=[0, 1],
+                    help="step mode: 1 = the effective charge and the convolution as one persistent launch "
+                         "over the active-block queue (tred_effq_convolve)")
     ap.add_argument("--conv-mode", type=int, default=0, choices=[0, 1, 2],
                     help="0: FP32 FFT convolution (default); 1: time DFT as a tcgen05 GEMM in TF32; "
                          "2: the same in split TF32 (three products)")
@@ -291,7 +356,14 @@ def run_batched(args):
     with ClockSampler(0) as clk:
         ms_graph = _timed(sim.replay, args.steps, 1)
     clocks = clk.summary()
-    launches_per_step = None
+    # the convolution's own time, from an eager step with events around its launches
+    cev = []
+    sim.step(conv_events=cev)
+    torch.cuda.synchronize()
+    conv_ms = sum(a.elapsed_time(b) for a, b in cev)
+    peak_meas, sms = measured_fp32_peak()
+    roof = alu_roofline("tred_convolve_range (k_conv_spec + inverse time transform), all chunks of one step",
+                        conv_flop_per_block(cfg.lt), nb, conv_ms, clocks, peak_meas)
     del sim
     torch.cuda.empty_cache()
     # one event at a time through the same kernels (no graph, one launch sequence each)
@@ -319,7 +391,7 @@ def run_batched(args):
           events_per_s=args.events / (ms_graph / 1e3),
           per_event={"ms_total": ms_single, "depos_per_s": ntot / (ms_single / 1e3),
                      "events_per_s": args.events / (ms_single / 1e3)},
-          speedup_vs_per_event=ms_single / ms_graph, clocks=clocks)
+          speedup_vs_per_event=ms_single / ms_graph, clocks=clocks, roofline=roof)
 
 
 def run_lines(args):
@@ -372,13 +444,18 @@ def run_lines(args):
     m = [statistics.mean(r[i] for r in rows) for i in range(4)]
     ms = sum(m)
     nb, npix, nh = (int(v) for v in sim.counts[:3].cpu())
+    clocks = clk.summary()
+    peak_meas, _ = measured_fp32_peak()
+    roof = alu_roofline("tred_convolve (k_conv_spec + k_conv_itime_mp)", conv_flop_per_block(cfg.lt), nb, m[2],
+                        clocks, peak_meas)
     _line("line segments/s to pixel currents (Eq. qline effective charge)", n / (ms / 1e3), "segments/s", ms, args,
           {"workload": f"module_lines: {n} segments of 3 mm from 200 tracks, 512x512 px x 6400 ticks, GL-2, "
                        "9x9x10x10x200 response, 8x8x256 blocks",
            "active_blocks": nb, "active_pixels": npix, "hits": nh,
            "l2": "flushed between timed steps"},
           stages_ms={"drift+blockbin": m[0], "effq_lines": m[1], "convolve": m[2], "gather+readout": m[3]},
-          clocks=clk.summary(), cpu_baseline=None if args.no_cpu_baseline else _lines_cpu(cfg, seg, resp.numpy()))
+          clocks=clocks, roofline=roof,
+          cpu_baseline=None if args.no_cpu_baseline else _lines_cpu(cfg, seg, resp.numpy()))
 
 
 def _lines_cpu(cfg, seg, resp, k=400):
@@ -423,8 +500,21 @@ def run_adjoint(args):
 
     with ClockSampler(0) as clk:
         ms = _timed(fwd_bwd, args.steps, args.warmup)
+        # the backward's dominant call alone: tred_adjoint (correlation with the response,
+        # inverse transforms, chain rule) after one forward
+        loss = tred.TredLoss.apply(st, tid, twave, x["x"], x["y"], x["z"], x["t0"], x["ne"], *p)
+
+        def adj():
+            tred.tred_adjoint(sim.h, n, sim.deps, sim.block_ids, sim.dep_offsets, sim.dep_index, sim.n_blocks_dev,
+                              sim.pixel_ids, sim.n_pixels_dev, st.resid, sim.qeff, st.grad7)
+        adj_ms = _timed(adj, args.steps, 1)
+    clocks = clk.summary()
     free1, _ = torch.cuda.mem_get_info()
     nb = int(sim.counts[0].item())
+    peak_meas, _ = measured_fp32_peak()
+    roof = alu_roofline("tred_adjoint (k_adj_spec + k_adj_itime512 + k_adj_chain); the backward correlation "
+                        "counted as one convolution's FLOPs", conv_flop_per_block(cfg.lt), nb, adj_ms, clocks,
+                        peak_meas)
     stored_gb = nb * cfg.n_sub ** 2 * cfg.bp ** 2 * cfg.bt * 4 * (1 + 2 * cfg.gl_order ** 3) / 1e9
     _line("forward+backward depos/s (gradients of an L2 loss w.r.t. deposit x/y/t0/ne, DL, DT, lifetime)",
           n / (ms / 1e3), "depos/s", ms, args,
@@ -433,7 +523,7 @@ def run_adjoint(args):
           memory={"device_bytes_in_use": int(total - free1), "before_handle": int(total - free0),
                   "note": "quadrature recomputed in the backward; dL/dQeff reuses the forward's Q^eff buffer",
                   "stored_quadrature_estimate_gb": stored_gb},
-          clocks=clk.summary())
+          clocks=clocks, roofline=roof, adjoint_call_ms=adj_ms)
 
 
 def run_spill(args):
@@ -465,8 +555,25 @@ def run_spill(args):
 
     with ClockSampler(0) as clk:
         ms = _timed(all_planes, max(1, args.steps // 2), 1)
+        # the convolution's own time over all planes (events around its launches) and the
+        # planes' active blocks, from one more pass
+        cev, nbs = [], 0
+        for pl in dev_planes:
+            nn = pl["x"].numel()
+            for k in ("x", "y", "z", "t0", "ne"):
+                one.inputs[k][:nn].copy_(pl[k])
+            one.n = nn
+            one.step(conv_events=cev)
+            nbs += int(one.counts[0].item())
+        torch.cuda.synchronize()
+        conv_ms = sum(a.elapsed_time(b) for a, b in cev)
+    clocks = clk.summary()
     free1, _ = torch.cuda.mem_get_info()
     st = one.status()
+    peak_meas, _ = measured_fp32_peak()
+    npairs = cfg.n_sub * cfg.n_sub // 2
+    roof = alu_roofline("tred_convolve_range over the 35 planes (k_conv_spec + k_conv_itime)",
+                        conv_flop_per_block(cfg.lt, npairs), nbs, conv_ms, clocks, peak_meas)
     dense = 35 * cfg.npx * cfg.npx * cfg.nt * 4
     _line("depos/s over 35 module planes in sequence (spill scale)", ntot / (ms / 1e3), "depos/s", ms, args,
           {"workload": f"35 planes x 512x512 px x 6400 ticks, {ntot} deposits, GL-3, 13x13x10x10x400 response, "
@@ -474,7 +581,7 @@ def run_spill(args):
           memory={"device_bytes_in_use": int(total - free1),
                   "dense_pixel_current_estimate_bytes": dense,
                   "dense_subpixel_qeff_estimate_bytes": dense * cfg.n_sub ** 2},
-          status=st[:2], clocks=clk.summary())
+          status=st[:2], clocks=clocks, roofline=roof)
 
 
 def run_accuracy(args):
@@ -493,6 +600,7 @@ def run_accuracy(args):
     n = len(dep["x"])
     max_blocks, max_pixels = probe_capacities(base, dep, dev)
     out = {}
+    clk = ClockSampler(0).__enter__()
     for gl in (1, 2, 4):
         cfg = base.with_(gl_order=gl)
         sim = tred.Simulator(cfg, torch.from_numpy(resp), max_deposits=n, max_blocks=max_blocks,
@@ -505,6 +613,7 @@ def run_accuracy(args):
         out[gl] = (sim.pixel_ids[:npix].cpu().numpy(), q)
         del sim
         torch.cuda.empty_cache()
+    clk.__exit__(None, None, None)
     assert all(np.array_equal(out[1][0], out[k][0]) for k in (2, 4))
     res = {}
     for gl in (1, 2):
@@ -513,7 +622,7 @@ def run_accuracy(args):
     _line("max deviation of accumulated charge per pixel per 100 ns vs the 4-point rule (electrons)",
           res["GL-2"][100], "e-", 0.0, args,
           {"workload": f"module200 event, {n} deposits, {len(out[4][0])} pixels", "noise_scale_e": 500},
-          percentiles=res, higher_is_better=False)
+          percentiles=res, higher_is_better=False, clocks=clk.summary())
 
 
 def run_chunking(args):
@@ -528,6 +637,7 @@ def run_chunking(args):
     resp = torch.from_numpy(resp)
     nb, npix = autotune.probe_blocks(cfg, [dep], resp)
     rows = []
+    clk = ClockSampler(0).__enter__()
     for chunk in (256, 1024, 4096, nb + 8):
         torch.cuda.empty_cache()
         free0, total = torch.cuda.mem_get_info()
@@ -537,9 +647,10 @@ def run_chunking(args):
         rows.append({"chunk_blocks": chunk, "device_bytes": int(free0 - free1), "ms": ms,
                      "qeff_bytes": sim.qeff.numel() * 4})
         del sim
+    clk.__exit__(None, None, None)
     _line("device memory of one module-plane step vs effective-charge chunk size", rows[0]["device_bytes"],
           "bytes", rows[0]["ms"], args, {"workload": f"module1M event, {len(dep['x'])} deposits, {nb} blocks"},
-          rows=rows, higher_is_better=False)
+          rows=rows, higher_is_better=False, clocks=clk.summary())
 
 
 def main():
@@ -573,9 +684,10 @@ def main():
     dev = torch.device("cuda", local)
     max_blocks, max_pixels = probe_capacities(cfg, dep, dev)
     max_hits = 4 * max_pixels
+    fused = bool(args.fused) and args.conv_mode == 0
     sim = tred.Simulator(cfg, torch.from_numpy(resp), max_deposits=n, max_blocks=max_blocks,
                          max_pixels=max_pixels, max_hits=max_hits, conv_mode=args.conv_mode,
-                         effq_skip_empty=1 if args.conv_mode == 0 else 0, device=dev)
+                         effq_skip_empty=1 if args.conv_mode == 0 else 0, device=dev, fused=fused)
     # response spectrum, timed separately (once per response)
     torch.cuda.synchronize()
     t = time.perf_counter()
@@ -588,6 +700,8 @@ def main():
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)   # > L2 (126 MB)
 
     stage_names = ["drift", "blockbin", "effq", "convolve", "gather+readout"]
+    if fused:
+        stage_names = ["drift", "blockbin", "effq_weights", "effq+convolve", "gather+readout"]
 
     def step(events=None):
         h = sim.h
@@ -602,10 +716,15 @@ def main():
         tred.tred_blockbin(h, n, sim.deps, sim.block_ids, sim.block_counts, sim.dep_offsets,
                            sim.dep_index, sim.n_blocks_dev)
         rec(2)
-        tred.tred_effq(h, n, sim.deps, sim.block_ids, sim.dep_offsets, sim.dep_index,
-                       sim.n_blocks_dev, sim.qeff)
-        rec(3)
-        tred.tred_convolve(h, sim.block_ids, sim.n_blocks_dev, sim.qeff, sim.out_blocks)
+        if fused:   # one persistent launch (its per-deposit weights kernel first, inside the call)
+            rec(3)
+            tred.tred_effq_convolve(h, n, sim.deps, sim.block_ids, sim.dep_offsets, sim.dep_index,
+                                    sim.n_blocks_dev, sim.qeff, sim.out_blocks)
+        else:
+            tred.tred_effq(h, n, sim.deps, sim.block_ids, sim.dep_offsets, sim.dep_index,
+                           sim.n_blocks_dev, sim.qeff)
+            rec(3)
+            tred.tred_convolve(h, sim.block_ids, sim.n_blocks_dev, sim.qeff, sim.out_blocks)
         rec(4)
         # a5 + a6: the electrode gather and the readout in one call (the readout skips the
         # pixels whose positive current cannot reach the threshold)
@@ -671,6 +790,7 @@ def main():
 
     n_job, ms = aggregate_replicas(n, ms, world, dev)
     value = n_job / (ms / 1e3)
+    peak_meas, sms = measured_fp32_peak()
 
     # end to end through the public API: pinned host inputs -> device, step,
     # counts + hit list -> pinned host, every step inside the timed region
@@ -705,18 +825,28 @@ def main():
         em = statistics.mean(e_ms)
         n_e2e, em = aggregate_replicas(n, em, world, dev)
         e2e = {"value": n_e2e / (em / 1e3), "unit": "depos/s", "h2d_bytes_per_step": h2d,
-               "d2h_bytes_per_step": d2h, "ms_per_step": em}
+               "d2h_bytes_per_step": d2h, "ms_per_step": em,
+               "h2d_what": "the event's deposits (x, y, z, t0, n_e float32)",
+               "d2h_what": ("the device counts and the capacity-sized hit lists (pixel, tick, charge); "
+                            "the pixel waveforms stay in device memory")}
 
-    conv_ms = stage_ms["convolve"]
-    achieved = CONV_FLOP_PER_BLOCK * nb / (conv_ms / 1e3) / 1e12
-    roofline = {"bound": "alu", "kernel": "tred_convolve (k_conv_spec + k_conv_itime_mp)",
-                "achieved": achieved, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
-                "frac": achieved / FP32_PEAK_TFLOPS, "traffic": conv_traffic(nb)[0],
-                "traffic_source": conv_traffic(nb)[1],
-                "peak_source": "148 SMs x 128 FP32 lanes x 2 flop x 2.032 GHz (unit counts, max clock)",
-                "flop_per_block": CONV_FLOP_PER_BLOCK, "blocks": nb}
-    if clocks.get("sm_mhz"):
-        roofline["frac_at_observed_clock"] = achieved / (FP32_PEAK_TFLOPS * clocks["sm_mhz"] / 2032.0)
+    conv_ms = stage_ms["effq+convolve" if fused else "convolve"]
+    flop_blk = conv_flop_per_block(cfg.lt)
+    roofline = alu_roofline("tred_effq_convolve (k_block_pipeline: effective charge + convolution, one "
+                            "persistent launch)" if fused else "tred_convolve (k_conv_spec + k_conv_itime_mp)",
+                            flop_blk, nb, conv_ms, clocks, peak_meas)
+    roofline["traffic"], roofline["traffic_source"] = conv_traffic(nb) if not fused else (None, "no capture")
+    roofline["sms"] = sms
+    cc = conv_counters() if not fused else {}
+    if "conv_executed_flop_per_block" in cc:
+        ex = cc["conv_executed_flop_per_block"]
+        roofline["executed_flop_per_block"] = ex
+        roofline["frac_executed_vs_measured"] = ex * nb / (conv_ms / 1e3) / 1e12 / peak_meas
+        roofline["executed_source"] = ("ncu 2*FFMA + FADD + FMUL thread instructions of the convolution's "
+                                       "kernels on module20, per block")
+    if "conv_spec_fma_pipe_pct" in cc:
+        roofline["ncu_fma_pipe_pct"] = cc["conv_spec_fma_pipe_pct"]
+        roofline["ncu_issue_active_pct"] = cc.get("conv_spec_issue_active_pct")
     if args.conv_mode:
         # the time DFT on the tensor cores: per block 50 pairs x 128 x 512 x bt MACs, one
         # product (TF32) or three (split TF32); its tensor-pipe share is in profiles/
@@ -737,7 +867,9 @@ def main():
                                        1: ", time DFT as a TF32 tcgen05 GEMM (tolerance 1e-4)",
                                        2: ", time DFT as a split-TF32 tcgen05 GEMM"}[args.conv_mode]
                                     + {0: "", 1: f", readout: {cfg.n_samples} successive digitisations per trigger",
-                                       2: ", readout: fixed-charge quanta"}[args.readout_mode]),
+                                       2: ", readout: fixed-charge quanta"}[args.readout_mode]
+                                    + (", effective charge and convolution in one persistent launch over the "
+                                       "active-block queue (Q^eff in per-CTA ring rows)" if fused else "")),
                        "deposits": n, "active_blocks": nb, "active_pixels": npix, "hits": nh,
                        **({"deposits_all_ranks": int(n_job)} if world > 1 else {}),
                        "parallelism": f"replicas x{world}" if world > 1 else "single GPU",

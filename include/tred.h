@@ -162,6 +162,17 @@ int32_t tred_launch_count(const tred_handle *h, int64_t *count);
  * TRED_ERR_INVALID_ARG for a limit outside the range. */
 int32_t tred_wait_selftest(tred_handle *h, int64_t limit_cycles, void *stream);
 
+/* Measured FP32 FMA throughput of the current device (the paper has no counterpart:
+ * the convolution is bound by the FP32 ALU, and this gives its roofline denominator).
+ * Runs 8 CTAs of 256 threads per SM, each thread 8 independent FMA chains of
+ * 16 * iters FMAs, once to warm up and once timed with CUDA events on `stream`
+ * (synchronises it).  sink: caller-owned device float[sink_len] with sink_len >=
+ * SMs * 2048 (TRED_ERR_CAPACITY otherwise), written with the chains' results.
+ * *tflops = 2 * FMAs / time in TFLOP/s; *sms_out (if not null) = SM count.
+ * TRED_ERR_INVALID_ARG for null outputs or iters < 1. */
+int32_t tred_fp32_peak(float *sink, int64_t sink_len, int32_t iters, void *stream, double *tflops,
+                       int32_t *sms_out);
+
 /* a0. Response spectrum (Sec. III-A-2: the spectra of the per-impact responses are computed once; Eq. interlaced,
  * R[j, k] = i[j, -k]).  resp_dev: [kp][kp][n_sub][n_sub][nr] float32, index
  * [Ky + R][Kx + R][jy][jx][tau] = current on the central electrode from unit charge
@@ -272,6 +283,26 @@ int32_t tred_convolve(tred_handle *h, const int32_t *block_ids,
 int32_t tred_convolve_range(tred_handle *h, const int32_t *block_ids, const int32_t *n_blocks_dev,
                             int32_t slot_base, int32_t slot_count, const float *qeff,
                             float *out_blocks, void *stream);
+
+/* a3 + a4 in one persistent launch over the active-block queue (Sec. III-B-2: the
+ * blocks of many events batched through the effective charge and the convolution).
+ * One CTA per SM takes blocks from one device queue holding every active block (all
+ * events of an n_events handle) and runs, per block: the effective charge (as
+ * tred_effq computes it: Eq. eff_q, each cell's sum in the block's deposit order) into
+ * its CTA's row of qeff_ring, then the convolution of every time-frequency class and
+ * the inverse time transform (as tred_convolve) into out_blocks[slot].
+ *  - qeff_ring: caller-owned device float32 [ring_rows][n_sub][n_sub][bp][bp][bt], the
+ *    staging rows of the resident CTAs; ring_rows must be at least min(SMs,
+ *    max_blocks, 8192) (TRED_ERR_CAPACITY otherwise).  Its contents afterwards are
+ *    unspecified (each row holds the last block its CTA took).
+ *  - out_blocks as tred_convolve: [max_blocks][16][16][lt], rows 0..n_blocks-1 written.
+ *  - n, deps, block_ids, dep_offsets, dep_index, n_blocks_dev as tred_effq (the
+ *    per-deposit weights are computed here too).
+ *  - conv_mode 0 and lt = 384 or 512 only (TRED_ERR_INVALID_ARG otherwise); effq_skip_empty
+ *    as the handle sets it.  Graph-capturable (counts stay on the device). */
+int32_t tred_effq_convolve(tred_handle *h, int32_t n, const tred_deposits *deps, const int32_t *block_ids,
+                           const int32_t *dep_offsets, const int32_t *dep_index, const int32_t *n_blocks_dev,
+                           float *qeff_ring, int32_t ring_rows, float *out_blocks, void *stream);
 
 /* a5. Electrode gather (Fig. flowchart: binning and accumulation onto the unique electrodes): every
  * in-plane pixel of an active block's output footprint is active; its waveform

@@ -34,7 +34,7 @@ EXPORTS = [
     "tred_gather_pixels", "tred_readout", "tred_launch_count", "tred_blockbin_noalloc",
     "tred_set_transport", "tred_residual", "tred_adjoint", "tred_param_grads",
     "tred_drift_events", "tred_effq_range", "tred_convolve_range", "tred_drift_lines", "tred_effq_lines",
-    "tred_wait_selftest", "tred_gather_readout",
+    "tred_wait_selftest", "tred_gather_readout", "tred_fp32_peak", "tred_effq_convolve",
 ]
 
 
@@ -110,6 +110,8 @@ def load(path: str | None = None) -> ctypes.CDLL:
     lib.tred_residual.argtypes = [_P, _P, _P, _P, _P, _I, _P, _P, _P, _P]
     lib.tred_adjoint.argtypes = [_P, _I, ctypes.POINTER(Deposits), _P, _P, _P, _P, _P, _P, _P, _P, _P, _P]
     lib.tred_param_grads.argtypes = [_P, _I, _P, ctypes.POINTER(Deposits), _P, _P, _P, _P]
+    lib.tred_effq_convolve.argtypes = [_P, _I, ctypes.POINTER(Deposits), _P, _P, _P, _P, _P, _I, _P, _P]
+    lib.tred_fp32_peak.argtypes = [_P, ctypes.c_int64, _I, _P, _P, _P]
     lib.tred_blockbin_noalloc.argtypes = [ctypes.POINTER(Geometry), _I, ctypes.POINTER(Deposits), _P, _P, _P,
                                           _P, _I, _I, _P, _P, _P]
     for name in EXPORTS:

@@ -67,14 +67,20 @@ def count_pixels(cfg, n_events, block_ids):
     return int(flags.sum())
 
 
-def make_batch(cfg, events, resp, chunk_blocks=2048, device=None):
+def make_batch(cfg, events, resp, chunk_blocks=2048, device=None, persistent=None):
+    """A BatchSimulator sized to the batch; persistent (default: whenever the FFT length
+    allows it, lt = 384 or 512) runs the effective charge and the convolution as one
+    persistent launch over the batch's active-block queue."""
     nb, npix = probe_blocks(cfg, events, resp, device)
+    if persistent is None:
+        persistent = cfg.lt in (384, 512)
     return tred.BatchSimulator(cfg, resp, events, max_blocks=nb + 8, max_pixels=npix,
-                               chunk_blocks=chunk_blocks, device=device)
+                               chunk_blocks=chunk_blocks, device=device, persistent=persistent)
 
 
 def autotune(cfg, events, resp, candidates=CANDIDATES, sample=8, device=None):
-    """Return ((bp, bt, lt), {shape: ms per deposit}) measured on the first `sample` events."""
+    """Return ((bp, bt, lt), {shape: ms per deposit}) measured on the first `sample` events
+    (each shape in the form make_batch gives it: persistent at lt = 384 and 512)."""
     evs = events[:sample]
     n = sum(len(e["x"]) for e in evs)
     timings = {}

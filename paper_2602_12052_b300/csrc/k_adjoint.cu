@@ -210,10 +210,15 @@ __global__ void __launch_bounds__(AS_THREADS, 1)
                 const int b = lane >> 4, kx = lane & 15;
                 const int k2 = (BINS / AS_WARPS) * warp + 2 * it + b;
                 const float2 *d = dh + dh_slot(k2) * DH_BIN + kx;
-                const float2 *rsrc = rp + rhat_bin(k1 + G * k2, p, c.npairs, LT / 32) + kx;
+                const float4 *rsrc = reinterpret_cast<const float4 *>(rp + rhat_bin(k1 + G * k2, p, c.npairs, LT / 32) +
+                                                                      rhat_kk(0, kx));
                 float2 v[LP];
 #pragma unroll
-                for (int ky = 0; ky < LP; ++ky) v[ky] = cmul(cconj(__ldg(rsrc + ky * LP)), d[ky * DH_ROW]);
+                for (int q = 0; q < LP / 2; ++q) {
+                    const float4 r = __ldg(rsrc + q * LP);   // ky = 2q, 2q + 1
+                    v[2 * q] = cmul(cconj(make_float2(r.x, r.y)), d[2 * q * DH_ROW]);
+                    v[2 * q + 1] = cmul(cconj(make_float2(r.z, r.w)), d[(2 * q + 1) * DH_ROW]);
+                }
                 fft_reg_dif_c<LP, true>(v);                 // over ky -> cy (bit-reversed)
                 float2 *t = tb + b * AT_BIN;
 #pragma unroll

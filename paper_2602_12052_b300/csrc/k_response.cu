@@ -8,7 +8,7 @@
 // (the spatial sign is + because R[j, k] = i[j, -k]; the 1/N of the inverse FFT
 // is folded in).  Evaluated once per response as two direct DFT stages in FP64
 // with exact twiddle arguments, rounded to complex64, and stored as
-//   rhat[k1][pair][k2][ky * 16 + kx]   with f = k1 + G2 k2, G2 = lt / 32,
+//   rhat[k1][pair][k2][rhat_kk(ky, kx)]   with f = k1 + G2 k2, G2 = lt / 32,
 // so that the convolution CTA owning the 32 bins of class k1 streams one
 // contiguous 64 KB slab per channel pair.
 #include <cmath>
@@ -71,7 +71,7 @@ __global__ void k_resp_space(const double2 *__restrict__ T, int npairs, int kp, 
                 re += t.x * wr - t.y * wi;
                 im += t.x * wi + t.y * wr;
             }
-        rhat[rhat_bin(f, p, npairs, G2) + ky * LP + kx] =
+        rhat[rhat_bin(f, p, npairs, G2) + rhat_kk(ky, kx)] =
             make_float2((float)(re * scale), (float)(im * scale));
     }
 }

@@ -486,6 +486,22 @@ int32_t tred_effq_range(tred_handle *h, int32_t n, const tred_deposits *deps, co
                        qeff, slot_base, slot_count, (cudaStream_t)stream);
 }
 
+int32_t tred_effq_convolve(tred_handle *h, int32_t n, const tred_deposits *deps, const int32_t *block_ids,
+                           const int32_t *dep_offsets, const int32_t *dep_index, const int32_t *n_blocks_dev,
+                           float *qeff_ring, int32_t ring_rows, float *out_blocks, void *stream) {
+    tred::CallRange range_("tred_effq_convolve");
+    if (!h) return TRED_ERR_INVALID_ARG;
+    if (!h->response_ready)
+        return set_error(h, TRED_ERR_NOT_READY, "tred_effq_convolve: call tred_set_response first");
+    if (n < 0 || n > h->max_deposits)
+        return set_error(h, TRED_ERR_CAPACITY, "tred_effq_convolve: n=%d outside [0, max_deposits]", n);
+    if ((n > 0 && !deps_ok(deps)) || !block_ids || !dep_offsets || !dep_index || !n_blocks_dev || !qeff_ring ||
+        ring_rows < 1 || !out_blocks)
+        return set_error(h, TRED_ERR_INVALID_ARG, "tred_effq_convolve: bad arguments");
+    return launch_pipeline(h, n, n > 0 ? *deps : tred_deposits{}, block_ids, dep_offsets, dep_index, n_blocks_dev,
+                           qeff_ring, ring_rows, out_blocks, (cudaStream_t)stream);
+}
+
 int32_t tred_convolve(tred_handle *h, const int32_t *block_ids, const int32_t *n_blocks_dev,
                       const float *qeff, float *out_blocks, void *stream) {
     tred::CallRange range_("tred_convolve");

@@ -14,10 +14,15 @@ namespace tred {
 constexpr int LP = 16;               // padded spatial FFT extent (pixels per axis)
 constexpr int BINS = 64;             // time-frequency bins of one adjoint spectral CTA
 constexpr int CBINS = 32;            // bins of one convolution class: f = k1 + G2 k2, G2 = lt / 32
-// offset of bin f of channel pair p in the response spectrum rhat[f mod G2][p][f div G2][ky * 16 + kx]
+// offset of bin f of channel pair p in the response spectrum rhat[f mod G2][p][f div G2][16 x 16]
+// (the plane's order: rhat_kk)
 __host__ __device__ inline size_t rhat_bin(int f, int p, int npairs, int G2) {
     return (((size_t)(f % G2) * npairs + p) * CBINS + f / G2) * (size_t)(LP * LP);
 }
+// position of (ky, kx) inside one bin's 16 x 16 plane of the response spectrum: the ky
+// pairs (2q, 2q + 1) of one kx are adjacent, so that a lane holding one kx reads two ky
+// values per 16-byte load and the 16 lanes of a bin read 256 contiguous bytes per load
+__host__ __device__ constexpr int rhat_kk(int ky, int kx) { return (ky >> 1) * (2 * LP) + 2 * kx + (ky & 1); }
 constexpr int MAX_GL = 8;
 
 struct Derived {
@@ -125,6 +130,9 @@ int launch_effq(tred_handle *h, int n, const tred_deposits &deps, const int32_t 
                 const int32_t *dep_offsets, const int32_t *dep_index,
                 const int32_t *n_blocks_dev, float *qeff, int slot_base, int slot_count, cudaStream_t s);
 int launch_response(tred_handle *h, const float *resp, cudaStream_t s);
+int launch_pipeline(tred_handle *h, int n, const tred_deposits &deps, const int32_t *block_ids,
+                    const int32_t *dep_offsets, const int32_t *dep_index, const int32_t *n_blocks_dev, float *qring,
+                    int ring_rows, float *out, cudaStream_t s);
 int launch_wait_selftest(tred_handle *h, long long limit, cudaStream_t s);
 int launch_convolve(tred_handle *h, const int32_t *block_ids, const int32_t *n_blocks_dev,
                     const float *qeff, float *out, int slot_base, int slot_count, cudaStream_t s);

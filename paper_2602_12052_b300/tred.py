@@ -154,6 +154,13 @@ def tred_effq(h: Handle, n: int, deps: DepositBuffers, block_ids, dep_offsets, d
                             _ptr(dep_index), _ptr(n_blocks_dev), _ptr(qeff), _stream(stream)))
 
 
+def tred_effq_convolve(h: Handle, n: int, deps: DepositBuffers, block_ids, dep_offsets, dep_index, n_blocks_dev,
+                       qeff_ring, out_blocks, stream=None):
+    h.check(h.lib.tred_effq_convolve(h.h, n, ctypes.byref(deps.struct), _ptr(block_ids), _ptr(dep_offsets),
+                                     _ptr(dep_index), _ptr(n_blocks_dev), _ptr(qeff_ring), qeff_ring.shape[0],
+                                     _ptr(out_blocks), _stream(stream)))
+
+
 def tred_convolve(h: Handle, block_ids, n_blocks_dev, qeff, out_blocks, stream=None):
     h.check(h.lib.tred_convolve(h.h, _ptr(block_ids), _ptr(n_blocks_dev), _ptr(qeff),
                                 _ptr(out_blocks), _stream(stream)))
@@ -224,6 +231,20 @@ def tred_param_grads(h: Handle, n: int, z, deps: DepositBuffers, grad7, grad_inp
                                    _ptr(grad_inputs), _ptr(grad_global), _stream(stream)))
 
 
+def tred_fp32_peak(iters: int = 4096, stream=None):
+    """Measured FP32 FMA throughput of the current device in TFLOP/s and its SM count
+    (the convolution's roofline denominator)."""
+    lib = abi.load()
+    props = torch.cuda.get_device_properties(torch.cuda.current_device())
+    sink = torch.empty(props.multi_processor_count * 2048, dtype=torch.float32, device="cuda")
+    tf = ctypes.c_double()
+    sms = ctypes.c_int32()
+    rc = lib.tred_fp32_peak(_ptr(sink), sink.numel(), int(iters), _stream(stream), ctypes.byref(tf), ctypes.byref(sms))
+    if rc != abi.TRED_OK:
+        raise abi.TredError(rc, "tred_fp32_peak")
+    return float(tf.value), int(sms.value)
+
+
 def tred_reset_status(h: Handle, stream=None):
     h.check(h.lib.tred_reset_status(h.h, _stream(stream)))
 
@@ -235,9 +256,11 @@ class Simulator:
 
     def __init__(self, cfg, resp: torch.Tensor, max_deposits: int, max_blocks: int,
                  max_pixels: int, max_pairs: int | None = None, max_hits: int | None = None,
-                 effq_mode=0, mpcp=1, compensated_gather=0, conv_mode=0, effq_skip_empty=0, device=None):
+                 effq_mode=0, mpcp=1, compensated_gather=0, conv_mode=0, effq_skip_empty=0, device=None,
+                 fused=False):
         self.cfg = cfg
         self.mpcp = mpcp
+        self.fused = bool(fused)
         self.device = torch.device(device or "cuda")
         self.h = Handle(geometry(cfg), params(cfg, effq_mode, mpcp, compensated_gather, conv_mode, effq_skip_empty),
                         max_deposits, max_blocks, max_pixels)
@@ -250,7 +273,11 @@ class Simulator:
         self.dep_offsets = torch.zeros(max_blocks + 1, dtype=torch.int32, device=d)
         self.dep_index = torch.zeros(max_pairs or 8 * max_deposits, dtype=torch.int32, device=d)
         self.counts = torch.zeros(4, dtype=torch.int32, device=d)    # nb, npix, nhits, spare
-        self.qeff = torch.empty((max_blocks, ns, ns, bp, bp, bt), dtype=torch.float32, device=d)
+        # fused: the effective charge and the convolution in one persistent launch
+        # (tred_effq_convolve), Q^eff staged in one ring row per resident CTA
+        qrows = min(torch.cuda.get_device_properties(d).multi_processor_count, max_blocks, 8192) if self.fused \
+            else max_blocks
+        self.qeff = torch.empty((qrows, ns, ns, bp, bp, bt), dtype=torch.float32, device=d)
         self.out_blocks = torch.empty((max_blocks, 16, 16, lt), dtype=torch.float32, device=d)
         self.pixel_ids = torch.zeros(max_pixels, dtype=torch.int32, device=d)
         self.waveforms = torch.empty((max_pixels, cfg.nt), dtype=torch.float32, device=d)
@@ -278,9 +305,13 @@ class Simulator:
         tred_drift(self.h, n, x, y, z, t0, ne, self.deps, stream)
         tred_blockbin(self.h, n, self.deps, self.block_ids, self.block_counts, self.dep_offsets,
                       self.dep_index, self.n_blocks_dev, stream)
-        tred_effq(self.h, n, self.deps, self.block_ids, self.dep_offsets, self.dep_index,
-                  self.n_blocks_dev, self.qeff, stream)
-        tred_convolve(self.h, self.block_ids, self.n_blocks_dev, self.qeff, self.out_blocks, stream)
+        if self.fused:
+            tred_effq_convolve(self.h, n, self.deps, self.block_ids, self.dep_offsets, self.dep_index,
+                               self.n_blocks_dev, self.qeff, self.out_blocks, stream)
+        else:
+            tred_effq(self.h, n, self.deps, self.block_ids, self.dep_offsets, self.dep_index,
+                      self.n_blocks_dev, self.qeff, stream)
+            tred_convolve(self.h, self.block_ids, self.n_blocks_dev, self.qeff, self.out_blocks, stream)
         if readout:      # gather and readout in one call (readout skips pixels that cannot trigger)
             tred_gather_readout(self.h, self.block_ids, self.n_blocks_dev, self.out_blocks, self.pixel_ids,
                                 self.waveforms, self.n_pixels_dev, self.rp, self.hit_pixel, self.hit_tick,
@@ -338,6 +369,8 @@ class DiffState:
     """Buffers of the backward pass bound to a Simulator."""
 
     def __init__(self, sim: "Simulator"):
+        if sim.fused:
+            raise ValueError("the adjoint needs a Simulator with fused=False (dL/dQeff uses the full Q^eff buffer)")
         d = sim.device
         self.sim = sim
         self.resid = torch.zeros((sim.h.max_pixels, sim.cfg.nt), dtype=torch.float32, device=d)
@@ -388,23 +421,33 @@ class BatchSimulator:
     """Many events of uneven size in one pass (Sec. III-B-2 hierarchical batching).
 
     Events are stacked along y (geometry n_events); every kernel runs once per step
-    as a persistent grid over the global active-block list of all events, and the
-    effective charge and convolution run over sub-batches of ``chunk_blocks`` slots
+    as a persistent grid over the global active-block list of all events.  With
+    ``persistent`` (lt = 384 or 512) the effective charge and the convolution are one
+    persistent launch over that list (tred_effq_convolve), Q^eff staged in one ring row
+    per resident CTA; otherwise they run over sub-batches of ``chunk_blocks`` slots
     so that Q^eff never needs more than one chunk of device memory.  The launch
     sequence is fixed (the block count stays on the device), so ``capture()`` can
     record a step in a CUDA graph."""
 
     def __init__(self, cfg, resp: torch.Tensor, events, max_blocks: int, max_pixels: int,
                  chunk_blocks: int = 2048, max_hits: int | None = None, mpcp=1, device=None,
-                 n_events: int | None = None, max_deposits: int | None = None):
+                 n_events: int | None = None, max_deposits: int | None = None, persistent: bool = False,
+                 effq_skip_empty: int = 0):
         self.cfg = cfg
         self.device = d = torch.device(device or "cuda")
         self.n_events = n_events or len(events)
         cap = max_deposits or int(sum(len(e["x"]) for e in events))
-        self.h = Handle(geometry(cfg, self.n_events), params(cfg, mpcp=mpcp), max(cap, 1), max_blocks,
-                        max_pixels)
+        self.persistent = bool(persistent)
+        skip = 1 if self.persistent else effq_skip_empty
+        self.h = Handle(geometry(cfg, self.n_events), params(cfg, mpcp=mpcp, effq_skip_empty=skip), max(cap, 1),
+                        max_blocks, max_pixels)
         self.rp = readout_params(cfg)
-        self.chunk = min(chunk_blocks, max_blocks)
+        if self.persistent:
+            # one Q^eff ring row per resident CTA of the persistent launch
+            sms = torch.cuda.get_device_properties(d).multi_processor_count
+            self.chunk = min(sms, max_blocks, 8192)
+        else:
+            self.chunk = min(chunk_blocks, max_blocks)
         self.max_blocks = max_blocks
         self.inputs = {k: torch.zeros(max(cap, 1), dtype=torch.float32, device=d)
                        for k in ("x", "y", "z", "t0", "ne")}
@@ -445,16 +488,35 @@ class BatchSimulator:
                 np.concatenate([np.full(len(e["x"]), i, np.int32) for i, e in enumerate(events)])))
         self.n = n
 
-    def step(self, stream=None):
+    def step(self, stream=None, conv_events=None):
+        """Enqueue one step.  conv_events: a list that receives a (start, end) pair of
+        recorded CUDA events around every convolution launch (timing only)."""
         h, x, n = self.h, self.inputs, self.n
         nb_dev, np_dev, nh_dev = self.counts[0:1], self.counts[1:2], self.counts[2:3]
         tred_drift_events(h, n, x["x"], x["y"], x["z"], x["t0"], x["ne"], x["event"], self.deps, stream)
         tred_blockbin(h, n, self.deps, self.block_ids, self.block_counts, self.dep_offsets, self.dep_index,
                       nb_dev, stream)
-        for base in range(0, self.max_blocks, self.chunk):
+        if self.persistent:
+            ev = None
+            if conv_events is not None:
+                ev = (torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+                ev[0].record()
+            tred_effq_convolve(h, n, self.deps, self.block_ids, self.dep_offsets, self.dep_index, nb_dev, self.qeff,
+                               self.out_blocks, stream)
+            if ev is not None:
+                ev[1].record()
+                conv_events.append(ev)
+        for base in range(0, self.max_blocks if not self.persistent else 0, self.chunk):
             tred_effq_range(h, n, self.deps, self.block_ids, self.dep_offsets, self.dep_index, nb_dev, base,
                             self.chunk, self.qeff, stream)
+            ev = None
+            if conv_events is not None:
+                ev = (torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+                ev[0].record()
             tred_convolve_range(h, self.block_ids, nb_dev, base, self.chunk, self.qeff, self.out_blocks, stream)
+            if ev is not None:
+                ev[1].record()
+                conv_events.append(ev)
         tred_gather_readout(h, self.block_ids, nb_dev, self.out_blocks, self.pixel_ids, self.waveforms, np_dev,
                             self.rp, self.hit_pixel, self.hit_tick, self.hit_charge, nh_dev, stream)
 

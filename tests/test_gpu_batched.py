@@ -15,13 +15,24 @@ def _tiny_events(k, cfg):
     return [synth.make_deposits(cfg, seed=cfg.seed + 1000 * i) for i in range(k)]
 
 
-def _batch(cfg, events, resp, chunk):
+def _batch(cfg, events, resp, chunk, persistent=False):
     import torch
     from paper_2602_12052_b300 import autotune
-    sim = autotune.make_batch(cfg, events, torch.from_numpy(resp), chunk_blocks=chunk)
+    sim = autotune.make_batch(cfg, events, torch.from_numpy(resp), chunk_blocks=chunk, persistent=persistent)
     sim.step()
     torch.cuda.synchronize()
     return sim
+
+
+def _uneven_tiny_events(cfg, k=8):
+    """k events of the 32 x 32 pixel plane with uneven deposit counts (from one deposit
+    to the whole 5 cm track, one of them empty), each from its own seeded track."""
+    sizes = [500, 1, 37, 0, 260, 5, 499, 120, 333, 64][:k]
+    out = []
+    for i, m in enumerate(sizes):
+        dep = synth.make_deposits(cfg, seed=cfg.seed + 1000 * i)
+        out.append({kk: v[:m].copy() for kk, v in dep.items()})
+    return out
 
 
 def _results(sim):
@@ -34,12 +45,16 @@ def _results(sim):
             "hit_charge": sim.hit_charge[:nh].cpu().numpy()}
 
 
-@pytest.mark.parametrize("chunk", [3, 64])
-def test_batch_matches_oracle_per_event(chunk):
+@pytest.mark.parametrize("chunk,persistent", [(3, False), (64, False), (0, True)])
+def test_batch_matches_oracle_per_event(chunk, persistent):
+    """Eight events of uneven size (one empty, one with a single deposit) through the
+    batched path, against the oracle run on each event alone: sub-batches of 3 or 64
+    slots, or the one persistent launch over the batch's active-block queue."""
     cfg = synth.get_config("tiny")
     resp = synth.make_response(cfg)
-    events = _tiny_events(3, cfg)
-    sim = _batch(cfg, events, resp, chunk)
+    events = _uneven_tiny_events(cfg)
+    sim = _batch(cfg, events, resp, chunk or 64, persistent)
+    assert sim.persistent == persistent
     assert sim.status()[0] == 0
     res = _results(sim)
     nblk, npx2 = cfg.n_blocks, cfg.npx * cfg.npx
@@ -50,6 +65,9 @@ def test_batch_matches_oracle_per_event(chunk):
         np.testing.assert_array_equal(res["block_counts"][sel_b], ref["block_counts"])
         sel_p = (res["pixel_ids"] // npx2) == e
         np.testing.assert_array_equal(res["pixel_ids"][sel_p] - e * npx2, ref["pixel_ids"])
+        if len(dep["x"]) == 0:
+            assert not sel_b.any() and not sel_p.any()
+            continue
         err = pixel_rel_errors(res["waveforms"][sel_p], ref["waveforms"])
         assert err.max() <= WAVE_TOL, (e, err.max())
         hp, ht, hc, _ = oracle.readout(ref["pixel_ids"], ref["waveforms"], cfg.threshold_e, cfg.clock_ticks,
@@ -60,29 +78,34 @@ def test_batch_matches_oracle_per_event(chunk):
                    cfg.reset_ticks)
 
 
-def test_batch_graph_replay_matches_eager():
+@pytest.mark.parametrize("persistent", [False, True])
+def test_batch_graph_replay_matches_eager(persistent):
+    """The batched step recorded in a CUDA graph and replayed gives the eager step's
+    outputs bit for bit: every sum of the effective charge and the convolution runs in
+    a fixed order (sorted deposit lists, no atomics on data), whichever CTA takes a block."""
     import torch
     cfg = synth.get_config("tiny")
     resp = synth.make_response(cfg)
-    sim = _batch(cfg, _tiny_events(4, cfg), resp, 8)
+    sim = _batch(cfg, _tiny_events(4, cfg), resp, 8, persistent)
     eager = _results(sim)
     sim.capture()
     for _ in range(2):
+        sim.waveforms.zero_()
+        sim.out_blocks.zero_()
         sim.replay()
         torch.cuda.synchronize()
         got = _results(sim)
-        for k in ("block_ids", "block_counts", "pixel_ids", "hit_pixel", "hit_tick"):
+        for k in ("block_ids", "block_counts", "pixel_ids", "hit_pixel", "hit_tick", "hit_charge", "waveforms"):
             np.testing.assert_array_equal(got[k], eager[k])
-        # effq accumulates with floating-point atomics, so runs agree to rounding
-        assert pixel_rel_errors(got["waveforms"], eager["waveforms"]).max() <= WAVE_TOL
 
 
-def test_batch_of_uneven_events_equals_single_event_runs():
+@pytest.mark.parametrize("persistent", [False, True])
+def test_batch_of_uneven_events_equals_single_event_runs(persistent):
     """Config-3 style events (uneven deposit counts) batched vs one at a time."""
     cfg = synth.get_config("module200")
     resp = synth.make_response(cfg)
     events = synth.make_events(cfg, 4, 1000, 30000, seed=33)
-    sim = _batch(cfg, events, resp, 256)
+    sim = _batch(cfg, events, resp, 256, persistent)
     assert sim.status()[0] == 0
     res = _results(sim)
     nblk, npx2 = cfg.n_blocks, cfg.npx * cfg.npx
@@ -107,3 +130,24 @@ def test_autotuner_shapes_match_oracle(bp, bt, lt):
     cfg = synth.get_config("tiny", nt=1280 if 1280 % bt == 0 else 1536, bp=bp, bt=bt, lt=lt)
     dep, resp = synth.make_event(cfg)
     _full_check(cfg, dep, resp, check_readout=False)
+
+
+@pytest.mark.parametrize("bp,bt,lt", [(8, 128, 384), (8, 128, 512), (4, 256, 512), (8, 256, 512)])
+def test_persistent_shapes_match_oracle(bp, bt, lt):
+    """Every block shape the autotuner runs in the persistent form (lt = 384 or 512;
+    4-pixel blocks with their half-zero spatial stages), two uneven events against the
+    oracle per event."""
+    cfg = synth.get_config("tiny", nt=1280, bp=bp, bt=bt, lt=lt)
+    resp = synth.make_response(cfg)
+    events = _uneven_tiny_events(cfg, 3)[::2]          # 500 and 37 deposits
+    sim = _batch(cfg, events, resp, 64, True)
+    assert sim.status()[0] == 0
+    res = _results(sim)
+    nblk, npx2 = cfg.n_blocks, cfg.npx * cfg.npx
+    for e, dep in enumerate(events):
+        ref = oracle.simulate(cfg, dep, resp)
+        sel_b = (res["block_ids"] // nblk) == e
+        np.testing.assert_array_equal(res["block_ids"][sel_b] - e * nblk, ref["block_ids"])
+        sel_p = (res["pixel_ids"] // npx2) == e
+        np.testing.assert_array_equal(res["pixel_ids"][sel_p] - e * npx2, ref["pixel_ids"])
+        assert pixel_rel_errors(res["waveforms"][sel_p], ref["waveforms"]).max() <= WAVE_TOL
