@@ -89,8 +89,10 @@ typedef struct {
     int32_t effq_mode;       /* 0: Gauss-Legendre (FP32); 1: exact tent, FP64 erf tails */
     int32_t conv_mode;       /* 0: FP32 FFT (shared memory + tensor-memory accumulator);
                                 1: time DFT as a tcgen05 GEMM in TF32 (tolerance 1e-4);
-                                2: the same with split TF32, three products (FP32 grade).
-                                1 and 2 need lt = 512 and bp = 8 (TRED_ERR_INVALID_ARG). */
+                                2: the same with split TF32, three products (FP32 grade);
+                                3: the same with split BF16, three products (BF16 hi + lo
+                                parts of both operands; tolerance 1e-4).
+                                1, 2 and 3 need lt = 512 and bp = 8 (TRED_ERR_INVALID_ARG). */
     int32_t mpcp;            /* 1: mirror-pair complex packing (needs a mirror-
                                 symmetric response); 0: one channel per FFT */
     int32_t compensated_gather; /* 1: accumulate overlapping blocks in FP64 */
@@ -98,7 +100,7 @@ typedef struct {
                                    deposit's support covers; the other columns of the qeff
                                    buffer are left as they were (conv_mode 0 reads only the
                                    columns whose non-empty mask bit is set).  0: every column
-                                   is written (required by conv_mode 1, 2). */
+                                   is written (required by conv_mode 1, 2, 3). */
 } tred_params;
 
 /* Pixel readout (Sec. II-E): the trigger-reset scheme and the two variants the

@@ -79,10 +79,11 @@ struct SpecSmem {
 };
 
 // Loads of the effective charge: through the read-only path when another kernel wrote
-// it; through L2 (coherent) when the same persistent kernel wrote it just before.
+// it; as ordinary cached loads (coherent with this SM's own stores, never the read-only
+// path) when the same persistent CTA wrote it just before.
 template <bool FUSED>
 __device__ __forceinline__ float ldq(const float *p) {
-    if constexpr (FUSED) return __ldcg(p);
+    if constexpr (FUSED) return __ldca(p);
     else return __ldg(p);
 }
 

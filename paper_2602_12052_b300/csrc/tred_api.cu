@@ -130,9 +130,9 @@ static int validate(const tred_geometry *g, const tred_params *p, char *msg, siz
     if (!(p->max_drift_cm >= 0)) return bad("max_drift_cm must be >= 0");
     if (p->gl_order < 1 || p->gl_order > MAX_GL) return bad("gl_order must be 1..8");
     if (p->effq_mode != 0 && p->effq_mode != 1) return bad("effq_mode must be 0 or 1");
-    if (p->conv_mode < 0 || p->conv_mode > 2) return bad("conv_mode must be 0, 1 or 2");
+    if (p->conv_mode < 0 || p->conv_mode > 3) return bad("conv_mode must be 0, 1, 2 or 3");
     if (p->conv_mode != 0 && (g->lt != 512 || g->bp != 8))
-        return bad("the tensor-core convolution (conv_mode 1, 2) needs lt = 512 and bp = 8");
+        return bad("the tensor-core convolution (conv_mode 1, 2, 3) needs lt = 512 and bp = 8");
     if (p->mpcp != 0 && p->mpcp != 1) return bad("mpcp must be 0 or 1");
     if (p->effq_skip_empty != 0 && p->effq_skip_empty != 1) return bad("effq_skip_empty must be 0 or 1");
     if (p->effq_skip_empty && p->conv_mode != 0) return bad("the tensor-core convolution reads every column: effq_skip_empty must be 0");

@@ -98,10 +98,10 @@ def test_tiny_compensated_gather():
     _full_check(cfg, dep, resp, comp=1, check_readout=False)
 
 
-@pytest.mark.parametrize("conv_mode,tol", [(1, 1e-4), (2, WAVE_TOL)])
+@pytest.mark.parametrize("conv_mode,tol", [(1, 1e-4), (2, WAVE_TOL), (3, 1e-4)])
 def test_tiny_tensor_core_dft(conv_mode, tol, capsys):
     """The time DFT as a tcgen05 GEMM: TF32 within the tensor-core bar 1e-4, split TF32
-    (three products) within the FP32 bar."""
+    (three products) within the FP32 bar, split BF16 (three products) within 1e-4."""
     cfg = synth.get_config("tiny")
     dep, resp = synth.make_event(cfg)
     res, ref, err = _full_check(cfg, dep, resp, conv_mode=conv_mode, tol=tol, check_readout=False)
@@ -109,7 +109,7 @@ def test_tiny_tensor_core_dft(conv_mode, tol, capsys):
         print(f"\nconv_mode {conv_mode}: max per-pixel rel L2 {err.max():.3e}, median {np.median(err):.3e}")
 
 
-@pytest.mark.parametrize("conv_mode,tol", [(0, WAVE_TOL), (1, 1e-4), (2, WAVE_TOL)])
+@pytest.mark.parametrize("conv_mode,tol", [(0, WAVE_TOL), (1, 1e-4), (2, WAVE_TOL), (3, 1e-4)])
 def test_tensor_core_dft_no_mpcp_asymmetric(conv_mode, tol):
     """Without MPCP (one real channel per impact) and with an x-odd response."""
     cfg = synth.get_config("tiny")
@@ -466,7 +466,7 @@ def test_module_plane_sampled(name, skip, fused, capsys):
 
 
 @pytest.mark.parametrize("form", ["fp32", "compensated_gather", "exact_tent_fp64_tails", "tf32_dft_gemm",
-                                  "split_tf32_dft_gemm"])
+                                  "split_tf32_dft_gemm", "split_bf16_dft_gemm"])
 def test_precision_ladder_module200(form, capsys):
     """Each precision form of the module-plane event against the FP64 oracle on
     sampled pixels; the errors are printed (pytest -s) and bounded by the FP32
@@ -475,8 +475,8 @@ def test_precision_ladder_module200(form, capsys):
     dep, resp = synth.make_event(cfg)
     mode = 1 if form == "exact_tent_fp64_tails" else 0
     comp = 1 if form == "compensated_gather" else 0
-    conv = {"tf32_dft_gemm": 1, "split_tf32_dft_gemm": 2}.get(form, 0)
-    tol = 1e-4 if conv == 1 else WAVE_TOL
+    conv = {"tf32_dft_gemm": 1, "split_tf32_dft_gemm": 2, "split_bf16_dft_gemm": 3}.get(form, 0)
+    tol = 1e-4 if conv in (1, 3) else WAVE_TOL
     sim = make_sim(cfg, resp, len(dep["x"]), max_blocks=3000, max_pixels=150000, effq_mode=mode,
                    compensated_gather=comp, conv_mode=conv)
     res = run(sim, dep, keep_qeff=False)
