@@ -574,6 +574,9 @@ def run_spill(args):
     npairs = cfg.n_sub * cfg.n_sub // 2
     roof = alu_roofline("tred_convolve_range over the 35 planes (k_conv_spec + k_conv_itime)",
                         conv_flop_per_block(cfg.lt, npairs), nbs, conv_ms, clocks, peak_meas)
+    roof["note"] = ("4 x 4-pixel blocks: each 16 x 16 spatial plane holds a 4 x 4 input, whose zero rows and "
+                    "columns the kernel's half-zero stages skip; the unpruned 5 N log2 N count credits that "
+                    "padding, so the fraction can exceed 1 (it is a count, not executed FLOPs)")
     dense = 35 * cfg.npx * cfg.npx * cfg.nt * 4
     _line("depos/s over 35 module planes in sequence (spill scale)", ntot / (ms / 1e3), "depos/s", ms, args,
           {"workload": f"35 planes x 512x512 px x 6400 ticks, {ntot} deposits, GL-3, 13x13x10x10x400 response, "

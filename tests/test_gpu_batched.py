@@ -101,7 +101,8 @@ def test_batch_graph_replay_matches_eager(persistent):
 
 @pytest.mark.parametrize("persistent", [False, True])
 def test_batch_of_uneven_events_equals_single_event_runs(persistent):
-    """Config-3 style events (uneven deposit counts) batched vs one at a time."""
+    """Config-3 style events (uneven deposit counts) batched vs one at a time, and each
+    event's brightest and random pixels against the oracle directly."""
     cfg = synth.get_config("module200")
     resp = synth.make_response(cfg)
     events = synth.make_events(cfg, 4, 1000, 30000, seed=33)
@@ -109,6 +110,15 @@ def test_batch_of_uneven_events_equals_single_event_runs(persistent):
     assert sim.status()[0] == 0
     res = _results(sim)
     nblk, npx2 = cfg.n_blocks, cfg.npx * cfg.npx
+    p = oracle.params(cfg)
+    rng = np.random.default_rng(9)
+    for e, dep in enumerate(events):
+        sel_p = (res["pixel_ids"] // npx2) == e
+        pix_e, wav_e = res["pixel_ids"][sel_p] - e * npx2, res["waveforms"][sel_p]
+        nrm = np.linalg.norm(wav_e, axis=1)
+        rows = np.unique(np.concatenate([np.argsort(nrm)[-8:], rng.choice(len(nrm), 8, replace=False)]))
+        ref = oracle.pixel_currents(p, oracle.drift(p, dep), resp, pix_e[rows])
+        assert pixel_rel_errors(wav_e[rows], ref).max() <= WAVE_TOL, e
     for e, dep in enumerate(events):
         one = make_sim(cfg, resp, len(dep["x"]), max_blocks=4000, max_pixels=200000)
         r1 = run(one, dep, keep_qeff=False)
