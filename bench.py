@@ -138,7 +138,7 @@ def _args():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--mode", default="step",
-                    choices=["step", "batched", "adjoint", "spill", "accuracy", "chunking", "lines"],
+                    choices=["step", "batched", "adjoint", "spill", "accuracy", "chunking", "lines", "binsize"],
                     help="step: one event (default); batched: 64 uneven events, autotuned, CUDA graph; "
                          "adjoint: forward + backward; spill: 35 planes in sequence")
     ap.add_argument("--events", type=int, default=64)
@@ -656,6 +656,53 @@ def run_chunking(args):
           rows=rows, higher_is_better=False, clocks=clk.summary())
 
 
+def run_binsize(args):
+    """The paper's bin-size study (Sec. IV-B): the block-sparse binning's time and the
+    whole step's time on the module-plane event for time-bin (block) lengths of 64 to 640
+    ticks, each with the smallest supported FFT length at or above bt + nr - 1."""
+    import torch
+    import synth
+    from paper_2602_12052_b300 import tred
+    torch.cuda.set_device(0)
+    base = synth.get_config("module1M")
+    dep, resp = synth.make_event(base)
+    n = len(dep["x"])
+    dev = torch.device("cuda")
+    x = {k: torch.from_numpy(v).to(dev) for k, v in dep.items()}
+    rows = []
+    clk = ClockSampler(0).__enter__()
+    for bt, lt in ((64, 384), (128, 384), (256, 512), (320, 768), (640, 1024)):
+        cfg = base.with_(bt=bt, lt=lt)
+        max_blocks, max_pixels = probe_capacities(cfg, dep, dev)
+        sim = tred.Simulator(cfg, torch.from_numpy(resp), max_deposits=n, max_blocks=max_blocks,
+                             max_pixels=max_pixels, effq_skip_empty=1, device=dev)
+
+        def binning():
+            tred.tred_drift(sim.h, n, x["x"], x["y"], x["z"], x["t0"], x["ne"], sim.deps)
+            tred.tred_blockbin(sim.h, n, sim.deps, sim.block_ids, sim.block_counts, sim.dep_offsets,
+                               sim.dep_index, sim.n_blocks_dev)
+
+        def step():
+            sim.step(n, x["x"], x["y"], x["z"], x["t0"], x["ne"])
+
+        bin_ms = _timed(binning, args.steps, args.warmup)
+        step_ms = _timed(step, args.steps, args.warmup)
+        st = sim.status()
+        if st[0] != 0:
+            raise RuntimeError(f"device status {st} at bt={bt}")
+        nb = int(sim.counts[0].item())
+        rows.append({"bt": bt, "lt": lt, "active_blocks": nb, "binning_ms": bin_ms, "step_ms": step_ms,
+                     "depos_per_s": n / (step_ms / 1e3)})
+        del sim
+        torch.cuda.empty_cache()
+    clk.__exit__(None, None, None)
+    best = min(rows, key=lambda r: r["step_ms"])
+    _line("depos/s vs time-bin (block) length, module-plane event (bin-size study)", best["depos_per_s"],
+          "depos/s", best["step_ms"], args,
+          {"workload": f"module1M event, {n} deposits, 8x8-pixel blocks, bt = 64 ... 640 ticks"},
+          rows=rows, clocks=clk.summary())
+
+
 def main():
     args = _args()
     if args.impl == "reference":
@@ -663,7 +710,7 @@ def main():
         return
     if args.mode != "step":
         {"batched": run_batched, "adjoint": run_adjoint, "spill": run_spill, "accuracy": run_accuracy,
-         "chunking": run_chunking, "lines": run_lines}[args.mode](args)
+         "chunking": run_chunking, "lines": run_lines, "binsize": run_binsize}[args.mode](args)
         return
     import numpy as np
     import torch

@@ -14,8 +14,8 @@ import torch
 from . import tred
 
 # (bp, bt, lt): pixels per block side, ticks per block, FFT length along time
-CANDIDATES = [(8, 128, 384), (8, 128, 512), (8, 256, 512), (4, 256, 512), (8, 320, 768), (8, 320, 1024),
-              (8, 512, 768), (8, 640, 1024)]
+CANDIDATES = [(8, 64, 384), (8, 128, 384), (8, 128, 512), (8, 256, 512), (4, 256, 512), (8, 320, 768),
+              (8, 320, 1024), (8, 512, 768), (8, 640, 1024)]
 
 
 def valid(cfg, bp, bt, lt) -> bool:

@@ -132,8 +132,8 @@ def test_batch_of_uneven_events_equals_single_event_runs(persistent):
         np.testing.assert_array_equal(res["hit_tick"][sel_h], r1["hit_tick"])
 
 
-@pytest.mark.parametrize("bp,bt,lt", [(8, 128, 384), (8, 128, 512), (4, 256, 512), (8, 320, 768), (8, 320, 1024),
-                                      (8, 512, 768), (8, 640, 1024)])
+@pytest.mark.parametrize("bp,bt,lt", [(8, 64, 384), (8, 128, 384), (8, 128, 512), (4, 256, 512), (8, 320, 768),
+                                      (8, 320, 1024), (8, 512, 768), (8, 640, 1024)])
 def test_autotuner_shapes_match_oracle(bp, bt, lt):
     """Every block shape / FFT length the autotuner may pick is parity-checked."""
     from test_gpu_parity import _full_check
@@ -142,7 +142,7 @@ def test_autotuner_shapes_match_oracle(bp, bt, lt):
     _full_check(cfg, dep, resp, check_readout=False)
 
 
-@pytest.mark.parametrize("bp,bt,lt", [(8, 128, 384), (8, 128, 512), (4, 256, 512), (8, 256, 512)])
+@pytest.mark.parametrize("bp,bt,lt", [(8, 64, 384), (8, 128, 384), (8, 128, 512), (4, 256, 512), (8, 256, 512)])
 def test_persistent_shapes_match_oracle(bp, bt, lt):
     """Every block shape the autotuner runs in the persistent form (lt = 384 or 512;
     4-pixel blocks with their half-zero spatial stages), two uneven events against the
