@@ -86,3 +86,13 @@ def test_noalloc_blockbin_rejects_bad_arguments_without_gpu(lib):
     assert call(geom(bp=6), 10, full) == abi.TRED_ERR_INVALID_ARG
     assert call(geom(), 10, full, out=None) == abi.TRED_ERR_INVALID_ARG
     assert call(geom(), -1, full) == abi.TRED_ERR_INVALID_ARG
+
+
+def test_fp32_peak_rejects_bad_arguments_without_gpu(lib):
+    """The FMA-peak measurement checks its arguments before any device call."""
+    from paper_2602_12052_b300 import abi
+    L = abi.load()
+    tf = ctypes.c_double()
+    assert L.tred_fp32_peak(None, 1 << 20, 16, None, ctypes.byref(tf), None) == abi.TRED_ERR_INVALID_ARG
+    assert L.tred_fp32_peak(ctypes.c_void_p(256), 1 << 20, 0, None, ctypes.byref(tf), None) == abi.TRED_ERR_INVALID_ARG
+    assert L.tred_fp32_peak(ctypes.c_void_p(256), 1 << 20, 16, None, None, None) == abi.TRED_ERR_INVALID_ARG

@@ -525,3 +525,14 @@ def test_fused_effq_convolve_tiny_full_parity(skip):
     # a second event through the same ring rows
     dense = {k: v[::-1].copy() for k, v in synth.make_deposits(cfg, seed=cfg.seed + 77).items()}
     _full_check(cfg, dense, resp, skip_empty=1, sim=sim, check_readout=False)
+
+
+def test_fp32_peak_measurement_is_plausible():
+    """The measured FMA throughput (the convolution's roofline denominator) lies between
+    half and 1.05 times the device's unit-count peak (SMs x 128 lanes x 2 flop x clock)."""
+    import torch
+    from paper_2602_12052_b300 import tred
+    tf, sms = tred.tred_fp32_peak(iters=4096)
+    assert sms == torch.cuda.get_device_properties(0).multi_processor_count
+    unit = sms * 128 * 2 * 2.032 / 1e3           # TFLOP/s at the B300's 2032 MHz maximum clock
+    assert 0.5 * unit <= tf <= 1.05 * unit, (tf, unit)
