@@ -138,7 +138,7 @@ def _args():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--mode", default="step",
-                    choices=["step", "batched", "adjoint", "spill", "accuracy", "chunking", "lines", "binsize"],
+                    choices=["step", "batched", "adjoint", "spill", "accuracy", "chunking", "lines", "binsize", "sizes"],
                     help="step: one event (default); batched: 64 uneven events, autotuned, CUDA graph; "
                          "adjoint: forward + backward; spill: 35 planes in sequence")
     ap.add_argument("--events", type=int, default=64)
@@ -703,6 +703,54 @@ def run_binsize(args):
           rows=rows, clocks=clk.summary())
 
 
+def run_sizes(args):
+    """Runtime against input size (the paper's runtime-per-batch study, Sec. IV-B): one
+    module-plane event of 10^3 .. 10^6 deposits at a time through the standard step, the
+    step recorded in a CUDA graph and replayed (latency floor for small events, then the
+    linear regime once the GPU is full)."""
+    import torch
+    import synth
+    from paper_2602_12052_b300 import tred
+    torch.cuda.set_device(0)
+    base = synth.get_config("module200")
+    resp = synth.make_response(base)
+    dev = torch.device("cuda")
+    rows = []
+    clk = ClockSampler(0).__enter__()
+    for n_target in (1000, 3000, 10000, 30000, 100000, 300000, 1000000):
+        cfg = base.with_(n_tracks=0, min_deposits=n_target)
+        dep = synth.make_deposits(cfg, seed=base.seed + n_target)
+        dep = {k: v[:n_target] for k, v in dep.items()}
+        n = len(dep["x"])
+        max_blocks, max_pixels = probe_capacities(cfg, dep, dev)
+        sim = tred.Simulator(cfg, torch.from_numpy(resp), max_deposits=n, max_blocks=max_blocks,
+                             max_pixels=max_pixels, effq_skip_empty=1, device=dev)
+        x = {k: torch.from_numpy(v).to(dev) for k, v in dep.items()}
+        sim.step(n, x["x"], x["y"], x["z"], x["t0"], x["ne"])
+        torch.cuda.synchronize()
+        side = torch.cuda.Stream()
+        side.wait_stream(torch.cuda.current_stream())
+        graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(graph, stream=side):
+            sim.step(n, x["x"], x["y"], x["z"], x["t0"], x["ne"])
+        torch.cuda.current_stream().wait_stream(side)
+        ms = _timed(graph.replay, args.steps, args.warmup)
+        st = sim.status()
+        if st[0] != 0:
+            raise RuntimeError(f"device status {st} at {n} deposits")
+        nb = int(sim.counts[0].item())
+        rows.append({"deposits": n, "active_blocks": nb, "ms": ms, "depos_per_s": n / (ms / 1e3),
+                     "us_per_block": 1e3 * ms / max(nb, 1)})
+        del sim, graph
+        torch.cuda.empty_cache()
+    clk.__exit__(None, None, None)
+    big = rows[-1]
+    _line("step time vs event size, module plane, CUDA graph replay (runtime vs input size)", big["depos_per_s"],
+          "depos/s", big["ms"], args,
+          {"workload": "one module-plane event (512x512 px x 6400 ticks) of 1e3 .. 1e6 deposits, 8x8x256 blocks"},
+          rows=rows, clocks=clk.summary())
+
+
 def main():
     args = _args()
     if args.impl == "reference":
@@ -710,7 +758,8 @@ def main():
         return
     if args.mode != "step":
         {"batched": run_batched, "adjoint": run_adjoint, "spill": run_spill, "accuracy": run_accuracy,
-         "chunking": run_chunking, "lines": run_lines, "binsize": run_binsize}[args.mode](args)
+         "chunking": run_chunking, "lines": run_lines, "binsize": run_binsize,
+         "sizes": run_sizes}[args.mode](args)
         return
     import numpy as np
     import torch
