@@ -153,7 +153,7 @@ def _args():
     ap.add_argument("--fused", type=int, default=0, choices=[0, 1],
                     help="step mode: 1 = the effective charge and the convolution as one persistent launch "
                          "over the active-block queue (tred_effq_convolve)")
-    ap.add_argument("--conv-mode", type=int, default=0, choices=[0, 1, 2, 3],
+    ap.add_argument("--conv-mode", type=int, default=0, choices=[0, 1, 2, 3, 4],
                     help="0: FP32 FFT convolution (default); 1: time DFT as a tcgen05 GEMM in TF32; "
                          "2: the same in split TF32 (three products); 3: the same in split BF16 (three products)")
     return ap.parse_args()
@@ -308,7 +308,7 @@ def run_reference(args):
 def _line(metric, value, unit, ms, args, cfg_extra, **kw):
     line = {"metric": metric, "value": value, "unit": unit, "n_gpus": 1, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": {0: "f32", 1: "tf32", 2: "tf32x3", 3: "bf16x3"}[args.conv_mode], "data": "synthetic", "config": cfg_extra}
+            "vs_baseline": None, "dtype": {0: "f32", 1: "tf32", 2: "tf32x3", 3: "bf16x3", 4: "f32+bf16x3"}[args.conv_mode], "data": "synthetic", "config": cfg_extra}
     line.update(kw)
     print(json.dumps(line), flush=True)
 
@@ -786,7 +786,7 @@ def main():
     fused = bool(args.fused) and args.conv_mode == 0
     sim = tred.Simulator(cfg, torch.from_numpy(resp), max_deposits=n, max_blocks=max_blocks,
                          max_pixels=max_pixels, max_hits=max_hits, conv_mode=args.conv_mode,
-                         effq_skip_empty=1 if args.conv_mode == 0 else 0, device=dev, fused=fused)
+                         effq_skip_empty=1 if args.conv_mode in (0, 4) else 0, device=dev, fused=fused)
     # response spectrum, timed separately (once per response)
     torch.cuda.synchronize()
     t = time.perf_counter()
@@ -946,7 +946,7 @@ def main():
     if "conv_spec_fma_pipe_pct" in cc:
         roofline["ncu_fma_pipe_pct"] = cc["conv_spec_fma_pipe_pct"]
         roofline["ncu_issue_active_pct"] = cc.get("conv_spec_issue_active_pct")
-    if args.conv_mode:
+    if args.conv_mode in (1, 2, 3):
         # the time DFT on the tensor cores: per block 50 pairs x 128 x 512 x bt MACs, one
         # product (TF32) or three (split TF32); its tensor-pipe share is in profiles/
         products = 1 if args.conv_mode == 1 else 3   # TF32; split TF32 or split BF16
@@ -957,7 +957,7 @@ def main():
         line = {
             "metric": METRIC, "value": value, "unit": "depos/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": {0: "f32", 1: "tf32", 2: "tf32x3", 3: "bf16x3"}[args.conv_mode],
+            "vs_baseline": None, "dtype": {0: "f32", 1: "tf32", 2: "tf32x3", 3: "bf16x3", 4: "f32+bf16x3"}[args.conv_mode],
             "data": "synthetic",
             "config": {"workload": (f"{cfg.name}: one event of {n} point deposits on a "
                                     f"{cfg.npx}x{cfg.npx} pixel plane x {cfg.nt} ticks, GL-{cfg.gl_order}, "
@@ -966,7 +966,8 @@ def main():
                                     + {0: ", effective charge written for covered columns only",
                                        1: ", time DFT as a TF32 tcgen05 GEMM (tolerance 1e-4)",
                                        2: ", time DFT as a split-TF32 tcgen05 GEMM",
-                                       3: ", time DFT as a split-BF16 tcgen05 GEMM (tolerance 1e-4)"}[args.conv_mode]
+                                       3: ", time DFT as a split-BF16 tcgen05 GEMM (tolerance 1e-4)",
+                                       4: ", time DFT by FFT, impacts x taps per bin as a split-BF16 tcgen05 GEMM"}[args.conv_mode]
                                     + {0: "", 1: f", readout: {cfg.n_samples} successive digitisations per trigger",
                                        2: ", readout: fixed-charge quanta"}[args.readout_mode]
                                     + (", effective charge and convolution in one persistent launch over the "

@@ -92,7 +92,13 @@ typedef struct {
                                 2: the same with split TF32, three products (FP32 grade);
                                 3: the same with split BF16, three products (BF16 hi + lo
                                 parts of both operands; tolerance 1e-4).
-                                1, 2 and 3 need lt = 512 and bp = 8 (TRED_ERR_INVALID_ARG). */
+                                1, 2 and 3 need lt = 512 and bp = 8 (TRED_ERR_INVALID_ARG).
+                                4: time DFT by FFT, then per time-frequency bin the sum over
+                                impacts and response taps of the block pixels that hold
+                                charge as a split-BF16 tcgen05 GEMM (three products, FP32
+                                accumulation); needs lt = 384 or 512 and kp <= 9
+                                (TRED_ERR_INVALID_ARG); reads only the columns whose
+                                non-empty mask bit is set, so effq_skip_empty may be 1. */
     int32_t mpcp;            /* 1: mirror-pair complex packing (needs a mirror-
                                 symmetric response); 0: one channel per FFT */
     int32_t compensated_gather; /* 1: accumulate overlapping blocks in FP64 */
@@ -100,7 +106,12 @@ typedef struct {
                                    deposit's support covers; the other columns of the qeff
                                    buffer are left as they were (conv_mode 0 reads only the
                                    columns whose non-empty mask bit is set).  0: every column
-                                   is written (required by conv_mode 1, 2, 3). */
+                                   is written (required by conv_mode 1, 2, 3; conv_mode 4
+                                   reads only the non-empty columns, as conv_mode 0). */
+    int32_t conv_rows_cap;      /* conv_mode 4: non-empty (block, pixel) rows per launch pair
+                                   of its forward DFT and GEMM, a multiple of 128 (device
+                                   memory 4 (lt/2 + 1) 2 n_sub^2 bytes per row); 0: 131072.
+                                   Larger row sets run as several launch pairs. */
 } tred_params;
 
 /* Pixel readout (Sec. II-E): the trigger-reset scheme and the two variants the

@@ -52,7 +52,8 @@ class Params(ctypes.Structure):
                 ("nsigma", ctypes.c_float), ("max_drift_cm", ctypes.c_float),
                 ("gl_order", ctypes.c_int32), ("effq_mode", ctypes.c_int32),
                 ("conv_mode", ctypes.c_int32), ("mpcp", ctypes.c_int32),
-                ("compensated_gather", ctypes.c_int32), ("effq_skip_empty", ctypes.c_int32)]
+                ("compensated_gather", ctypes.c_int32), ("effq_skip_empty", ctypes.c_int32),
+                ("conv_rows_cap", ctypes.c_int32)]
 
 
 class ReadoutParams(ctypes.Structure):

@@ -378,6 +378,7 @@ static int run_conv(tred_handle *h, const int32_t *n_blocks_dev, const float *qe
 int launch_convolve(tred_handle *h, const int32_t *block_ids, const int32_t *n_blocks_dev,
                     const float *qeff, float *out, int slot_base, int slot_count, cudaStream_t s) {
     (void)block_ids;
+    if (h->p.conv_mode == 4) return launch_direct(h, n_blocks_dev, qeff, out, slot_base, slot_count, slot_base, s);
     ConvConst c;
     c.ns = h->g.n_sub;
     c.bp = h->g.bp;

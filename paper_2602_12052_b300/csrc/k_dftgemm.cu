@@ -531,6 +531,8 @@ static PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
     return fn;
 }
 
+void *tensor_map_encoder() { return reinterpret_cast<void *>(encode_fn()); }
+
 // 2-D FP32 tensor [rows][inner], box [box_rows][32], 128-byte swizzle
 static int make_map(tred_handle *h, CUtensorMap *m, const float *ptr, uint64_t inner, uint64_t rows,
                     uint32_t box_rows) {

@@ -1,0 +1,838 @@
+// a4, tensor-core form with the spatial sum taken directly per time frequency (Sec.
+// II-D, Eq. interlaced; Sec. III-A-2: the time axis by DFT, the pixel plane and the
+// impacts by a GEMM on the tcgen05 tensor cores).
+//
+// The interlaced convolution of one active block,
+//     I[P, t] = sum_j sum_K sum_tau Qeff[j, P + K, t - tau] i[j, K, tau],
+// becomes after a length-lt DFT over time, for every bin f = 0 .. lt/2 (the data are
+// real, so the other half of the spectrum is the conjugate),
+//     Ihat[P, f] = sum_{p'} Z[p', p' - P, f],   Z[p', K, f] = sum_j Qhat[j, p', f] R[j, K, f]
+// with Qhat the DFT of the block's column (impact j, pixel p') and R the DFT of the
+// response column (j, K).  For each bin, Z is a complex matrix product over the impacts:
+// rows = the block's pixels that hold charge (on a module plane about 10 of the 64),
+// columns = the kp^2 response taps.  Batched over every non-empty (block, pixel) row of
+// the pass, each bin is one GEMM with M = rows, K = 2 nch (real and imaginary parts of
+// the nch impacts), N = 2 kp^2 (real and imaginary parts of the taps), run as three
+// split-BF16 products (A_hi B_hi + A_hi B_lo + A_lo B_hi, FP32 accumulation in tensor
+// memory).  The real form of the complex product is laid out with the impacts in pairs,
+//     k = 4 q + c,  c = 0: Re Qhat[2q], 1: Re Qhat[2q + 1], 2: Im Qhat[2q], 3: Im Qhat[2q + 1]
+//     B[n][k]          (n < kp^2, Re Z of tap n):  Re R, Re R, -Im R, -Im R
+//     B[kp^2 + n][k]   (Im Z of tap n):            Im R, Im R,  Re R,  Re R
+// so that the forward kernel writes 64 consecutive k of one bin from 16 impact pairs.
+//
+// Kernels of one pass over at most dx_blocks slots:
+//  k_dx_pixmask / k_dx_rows  non-empty pixels of each slot (from the effective charge's
+//                            column masks) and the row list, in slot then pixel order;
+//  k_dx_fwd                  per row, the real DFT of its nch columns (two real columns
+//                            per complex FFT in registers, split by Hermitian symmetry),
+//                            transposed in shared memory and written as BF16 hi and lo
+//                            parts [bin][row][k];
+//  k_dx_gemm                 per (bin, 128-row tile): TMA (64-byte swizzle) of the two
+//                            operands' parts, tcgen05.mma kind::f16 (M = 128, N = npad,
+//                            K = 16) into one of two tensor-memory accumulators, and an
+//                            epilogue that sums each block's rows into its 16 x 16 output
+//                            spectrum Ihat[slot][f][P] in a fixed row order;
+//  k_dx_inv                  per block, the inverse real DFT of the 256 output pixels
+//                            (two per complex FFT) into out_blocks[slot][uy][ux][t].
+// A block whose rows cross a 128-row tile boundary gets its two tiles' parts by two
+// floating-point additions onto zero (the fixed summation order holds: a + b = b + a).
+// Every mbarrier wait is bounded; an expired wait sets TRED_ST_TIMEOUT, and the CTA
+// lets its copies and products in flight finish (bounded) before it frees the tensor
+// memory and returns.
+#include <cudaTypedefs.h>
+
+#include <cmath>
+#include <cstring>
+#include <vector>
+
+#include "tred_internal.cuh"
+
+namespace tred {
+
+constexpr int DX_M = 128;                // rows of one GEMM tile
+constexpr int DX_KC = 32;                // K chunk: 32 BF16 = one 64-byte row (64-byte swizzle)
+constexpr int DX_STAGES = 3;             // operand stages
+constexpr int DX_ROWS_MAX = 131072;      // rows per forward + GEMM launch pair
+constexpr int DX_BLOCKS_MAX = 8192;      // slots per pass
+constexpr int DX_FWD_THREADS = 512;
+constexpr int DX_INV_THREADS = 512;
+constexpr int DX_GEMM_THREADS = 192;     // warp 0 copies, warp 1 products, warps 2..5 epilogue
+constexpr uint32_t DX_A_BYTES = DX_M * DX_KC * 2;   // 8 KB per part
+
+struct DxConst {
+    int nch, kq, ntap, npad, kp, R, bp, bp2, bt, lt, nbins, rows_cap;
+};
+
+__host__ __device__ constexpr int dx_round16(int x) { return (x + 15) & ~15; }
+__host__ __device__ constexpr uint32_t dx_b_bytes(int npad) { return (uint32_t)npad * DX_KC * 2; }
+__host__ __device__ constexpr uint32_t dx_stage_bytes(int npad) {
+    return (2 * DX_A_BYTES + 2 * dx_b_bytes(npad) + 1023u) & ~1023u;
+}
+// odd column stride of the forward kernel's transposition buffer (bins per column)
+__host__ __device__ constexpr int dx_tstride(int nbins) { return nbins | 1; }
+size_t dx_fwd_smem(int kq, int nbins) { return sizeof(float) * (size_t)kq * dx_tstride(nbins); }
+static size_t dx_gemm_smem(int npad, int ntap) {
+    return 1024 + DX_STAGES * (size_t)dx_stage_bytes(npad) + sizeof(float) * DX_M * (2 * ntap + 1) +
+           sizeof(int32_t) * DX_M + 128;
+}
+
+// nearest BF16 (ties to even) of a finite binary32 value, as its 16 bits, and its value
+__host__ __device__ __forceinline__ uint32_t dx_bf16_bits(float x) {
+#ifdef __CUDA_ARCH__
+    const uint32_t u = __float_as_uint(x);
+#else
+    uint32_t u;
+    memcpy(&u, &x, 4);
+#endif
+    return (u + 0x7FFFu + ((u >> 16) & 1u)) >> 16;
+}
+__host__ __device__ __forceinline__ float dx_bf16_value(uint32_t b) {
+#ifdef __CUDA_ARCH__
+    return __uint_as_float(b << 16);
+#else
+    const uint32_t u = b << 16;
+    float x;
+    memcpy(&x, &u, 4);
+    return x;
+#endif
+}
+
+// ---------------------------------------------------------------- response operand
+// R[j][n][f] = (1 / lt) sum_tau i[Ky][Kx][jy][jx][tau] exp(-2 pi i tau f / lt) in FP64
+// (n = Ky kp + Kx, j = jy ns + jx; the 1/lt of the inverse DFT folded in).
+__global__ void k_dx_resp_time(const float *__restrict__ resp, int nch, int ntap, int nr, int lt, int nbins,
+                               const double2 *__restrict__ wlt, double2 *__restrict__ Rt) {
+    const int64_t total = (int64_t)nch * ntap * nbins;
+    const double scale = 1.0 / (double)lt;
+    for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < total;
+         idx += (int64_t)gridDim.x * blockDim.x) {
+        const int f = (int)(idx % nbins);
+        const int64_t r = idx / nbins;
+        const int n = (int)(r % ntap);
+        const int j = (int)(r / ntap);
+        // resp layout [Ky][Kx][jy][jx][tau] = [n][j][tau]
+        const float *ir = resp + ((int64_t)n * nch + j) * nr;
+        double re = 0.0, im = 0.0;
+        for (int tau = 0; tau < nr; ++tau) {
+            const double v = (double)ir[tau];
+            const double2 w = wlt[((int64_t)tau * f) % lt];
+            re = fma(v, w.x, re);
+            im = fma(v, w.y, im);
+        }
+        Rt[idx] = make_double2(re * scale, im * scale);
+    }
+}
+
+// the GEMM's B operand in the paired real form, split into BF16 hi and lo parts
+__global__ void k_dx_resp_pack(const double2 *__restrict__ Rt, DxConst c, uint16_t *__restrict__ bhi,
+                               uint16_t *__restrict__ blo) {
+    const int64_t total = (int64_t)c.nbins * c.npad * c.kq;
+    for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < total;
+         idx += (int64_t)gridDim.x * blockDim.x) {
+        const int k = (int)(idx % c.kq);
+        const int64_t r = idx / c.kq;
+        const int row = (int)(r % c.npad);
+        const int f = (int)(r / c.npad);
+        const int q = k >> 2, cc = k & 3;
+        const int j = 2 * q + (cc & 1);
+        const bool imq = (cc >> 1) != 0;   // the column holds Im Qhat[j]
+        double v = 0.0;
+        if (row < 2 * c.ntap && j < c.nch) {
+            const int n = row < c.ntap ? row : row - c.ntap;
+            const double2 R = Rt[((int64_t)j * c.ntap + n) * c.nbins + f];
+            if (row < c.ntap) v = imq ? -R.y : R.x;    // Re Z = Re Q Re R - Im Q Im R
+            else v = imq ? R.x : R.y;                  // Im Z = Re Q Im R + Im Q Re R
+        }
+        const float x = (float)v;
+        const uint32_t h = dx_bf16_bits(x);
+        const uint32_t l = dx_bf16_bits((float)(v - (double)dx_bf16_value(h)));
+        bhi[idx] = (uint16_t)h;
+        blo[idx] = (uint16_t)l;
+    }
+}
+
+static DxConst dx_const_of(const tred_handle *h) {
+    DxConst c;
+    c.nch = h->g.n_sub * h->g.n_sub;
+    c.kq = 2 * c.nch;
+    c.kp = h->g.kp;
+    c.ntap = c.kp * c.kp;
+    c.npad = dx_round16(2 * c.ntap);
+    c.R = h->d.R;
+    c.bp = h->g.bp;
+    c.bp2 = c.bp * c.bp;
+    c.bt = h->g.bt;
+    c.lt = h->g.lt;
+    c.nbins = c.lt / 2 + 1;
+    c.rows_cap = h->dx_rows_cap;
+    return c;
+}
+
+int launch_direct_response(tred_handle *h, const float *resp, cudaStream_t s) {
+    const DxConst c = dx_const_of(h);
+    std::vector<double2> wlt(c.lt);
+    for (int k = 0; k < c.lt; ++k) {
+        const double a = 2.0 * M_PI * (double)k / (double)c.lt;
+        wlt[k] = make_double2(std::cos(a), -std::sin(a));
+    }
+    double2 *d_wlt = nullptr, *d_R = nullptr;
+    int rc = check_cuda(h, cudaMalloc(&d_wlt, sizeof(double2) * c.lt), "alloc direct-form twiddles");
+    if (!rc) rc = check_cuda(h, cudaMalloc(&d_R, sizeof(double2) * (size_t)c.nch * c.ntap * c.nbins), "alloc direct-form stage");
+    if (!rc) rc = check_cuda(h, cudaMemcpyAsync(d_wlt, wlt.data(), sizeof(double2) * c.lt, cudaMemcpyHostToDevice, s), "copy");
+    if (!rc) {
+        const int grid = num_sms(h) * 8;
+        k_dx_resp_time<<<grid, 256, 0, s>>>(resp, c.nch, c.ntap, h->g.nr, c.lt, c.nbins, d_wlt, d_R);
+        k_dx_resp_pack<<<grid, 256, 0, s>>>(d_R, c, h->dx_bhi, h->dx_blo);
+        h->launches += 2;
+        rc = check_cuda(h, cudaGetLastError(), "direct-form response launch");
+    }
+    cudaError_t e = cudaStreamSynchronize(s);   // set-up path, once per response
+    if (!rc) rc = check_cuda(h, e, "direct-form response sync");
+    cudaFree(d_wlt);
+    cudaFree(d_R);
+    return rc;
+}
+
+// ---------------------------------------------------------------- rows
+// One warp per slot of the pass: the OR of its nch column masks = its non-empty pixels.
+__global__ void k_dx_pixmask(const int32_t *__restrict__ n_blocks_dev, const uint64_t *__restrict__ colmask, int nch,
+                             int bp2, int slot_base, int slot_count, uint64_t *__restrict__ pmask) {
+    const int nb = n_blocks_dev[0];
+    const int cnt = max(0, min(slot_count, nb - slot_base));
+    const int lane = threadIdx.x & 31;
+    const uint64_t keep = bp2 >= 64 ? ~0ull : ((1ull << bp2) - 1ull);
+    for (int s = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; s < cnt; s += (gridDim.x * blockDim.x) >> 5) {
+        const uint64_t *m = colmask + (size_t)(slot_base + s) * nch;
+        uint64_t v = 0;
+        for (int j = lane; j < nch; j += 32) v |= m[j];
+#pragma unroll
+        for (int o = 16; o >= 1; o >>= 1) v |= __shfl_xor_sync(0xffffffffu, v, o);
+        if (lane == 0) pmask[s] = v & keep;
+    }
+}
+
+// One CTA: exclusive scan of the slots' pixel counts (rowstart), the row records in slot
+// then pixel order, meta = {slots of the pass, rows of the pass}.
+constexpr int DX_ROWS_THREADS = 1024;
+__global__ void __launch_bounds__(DX_ROWS_THREADS) k_dx_rows(const int32_t *__restrict__ n_blocks_dev,
+                                                              const uint64_t *__restrict__ pmask, int slot_base,
+                                                              int slot_count, int32_t *__restrict__ rows,
+                                                              int32_t *__restrict__ rowstart,
+                                                              int32_t *__restrict__ meta) {
+    __shared__ int wsum[32];
+    __shared__ int carry_s;
+    const int nb = n_blocks_dev[0];
+    const int cnt = max(0, min(slot_count, nb - slot_base));
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    if (tid == 0) carry_s = 0;
+    __syncthreads();
+    for (int base = 0; base < cnt; base += DX_ROWS_THREADS) {
+        const int s = base + tid;
+        const uint64_t m = s < cnt ? pmask[s] : 0ull;
+        const int n = __popcll(m);
+        int x = n;   // inclusive warp scan
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, x, o);
+            if (lane >= o) x += y;
+        }
+        if (lane == 31) wsum[warp] = x;
+        __syncthreads();
+        if (warp == 0) {
+            int w = wsum[lane];
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int y = __shfl_up_sync(0xffffffffu, w, o);
+                if (lane >= o) w += y;
+            }
+            wsum[lane] = w;   // inclusive over warps
+        }
+        __syncthreads();
+        const int carry = carry_s;
+        const int start = carry + (warp ? wsum[warp - 1] : 0) + x - n;
+        if (s < cnt) {
+            rowstart[s] = start;
+            uint64_t mm = m;
+            int r = start;
+            while (mm) {
+                const int p = __ffsll((long long)mm) - 1;
+                rows[r++] = (s << 6) | p;
+                mm &= mm - 1ull;
+            }
+        }
+        __syncthreads();
+        if (tid == 0) carry_s = carry + wsum[31];
+        __syncthreads();
+    }
+    if (tid == 0) {
+        rowstart[cnt] = carry_s;
+        meta[0] = cnt;
+        meta[1] = carry_s;
+    }
+}
+
+// ---------------------------------------------------------------- forward time DFT
+// index k with fft_perm<N>(k) == v (compile time)
+template <int N>
+__host__ __device__ constexpr int dx_perm_inv(int v) {
+    for (int k = 0; k < N; ++k)
+        if (fft_perm<N>(k) == v) return k;
+    return 0;
+}
+
+// Zero the output spectra of the slots whose rows cross a 128-row tile boundary: the
+// GEMM epilogue adds their two parts onto zero.
+__device__ __forceinline__ void dx_zero_straddling(const int32_t *__restrict__ rowstart, int cnt, int nbins,
+                                                   float2 *__restrict__ ybuf) {
+    for (int s = blockIdx.x; s < cnt; s += gridDim.x) {
+        const int rs = rowstart[s], re = rowstart[s + 1];
+        if (re <= rs || (rs >> 7) == ((re - 1) >> 7)) continue;
+        float4 *y = reinterpret_cast<float4 *>(ybuf + (size_t)s * nbins * (LP * LP));
+        const int n4 = nbins * (LP * LP) / 2;
+        for (int i = threadIdx.x; i < n4; i += blockDim.x) y[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+}
+
+// One CTA per row at a time (persistent over the rows [row0, row0 + rows_cap) of the
+// pass).  Warp w transforms the impact pairs q = w, w + 16, ...: the two real columns
+// as one complex sequence, z[t] = Q[2q][t] + i Q[2q+1][t] (t < bt, zero to lt), by a
+// 32-point DFT across the lanes for each of the NPL samples a lane holds (lane l holds
+// t = NPL l + m), the twiddles W_lt^(m k1), and an NPL-point DFT in registers, so lane
+// l holds bin f = k1 + 32 fft_perm(k) in register k with k1 = bitrev5(l); then
+//     Qhat[2q][f] = (Z[f] + conj Z[lt - f]) / 2,   Qhat[2q+1][f] = (Z[f] - conj Z[lt - f]) / 2i
+// (the partner bin sits in lane bitrev5(32 - k1)), written column-major into T[k][f].
+// A pair whose two columns are empty in the block's masks is written as zeros without a
+// transform.  Then the CTA writes bin by bin the row's kq values as BF16 hi and lo parts.
+template <int G>
+__global__ void __launch_bounds__(DX_FWD_THREADS, 1)
+    k_dx_fwd(const float *__restrict__ qeff, const uint64_t *__restrict__ colmask, const int32_t *__restrict__ rows,
+             const int32_t *__restrict__ rowstart, const int32_t *__restrict__ meta, const float2 *__restrict__ tw,
+             DxConst c, int slot_base, int qbase, int row0, int zero_straddling, uint16_t *__restrict__ qhi,
+             uint16_t *__restrict__ qlo, float2 *__restrict__ ybuf) {
+    constexpr int LT = 64 * G;
+    constexpr int NPL = LT / 32;
+    constexpr int NW = DX_FWD_THREADS / 32;
+    extern __shared__ float T[];   // [kq][ST]
+    const int ST = dx_tstride(c.nbins);
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int cnt = meta[0], nrows = meta[1];
+    if (zero_straddling) dx_zero_straddling(rowstart, cnt, c.nbins, ybuf);
+    const int nloc = min(c.rows_cap, nrows - row0);
+    const float2 *wlt = tw + TW_LT;
+    const float2 *w32 = tw + TW_32;
+    const int k1 = bitrev<32>(lane);
+    const int src = k1 == 0 ? 0 : bitrev<32>(32 - k1);
+    const int npq = c.kq >> 2;
+    for (int rl = blockIdx.x; rl < nloc; rl += gridDim.x) {
+        const int rec = rows[row0 + rl];
+        const int s = rec >> 6, p = rec & 63;
+        const uint64_t *mk = colmask + (size_t)(slot_base + s) * c.nch;
+        const float *qs = qeff + (size_t)(slot_base + s - qbase) * c.nch * c.bp2 * c.bt + (size_t)p * c.bt;
+        for (int q = warp; q < npq; q += NW) {
+            const int ja = 2 * q, jb = 2 * q + 1;
+            const bool nza = (mk[ja] >> p) & 1ull;
+            const bool nzb = (mk[jb] >> p) & 1ull;
+            float *Tq = T + (size_t)(4 * q) * ST;
+            if (!(nza || nzb)) {
+                for (int f = lane; f < c.nbins; f += 32) {
+                    Tq[f] = 0.f;
+                    Tq[ST + f] = 0.f;
+                    Tq[2 * ST + f] = 0.f;
+                    Tq[3 * ST + f] = 0.f;
+                }
+                continue;
+            }
+            const float *ca = qs + (size_t)ja * c.bp2 * c.bt;
+            const float *cb = qs + (size_t)jb * c.bp2 * c.bt;
+            float2 v[NPL];
+#pragma unroll
+            for (int e = 0; e < NPL / 4; ++e) {
+                const int t0 = NPL * lane + 4 * e;
+                float4 a = make_float4(0.f, 0.f, 0.f, 0.f), b = a;
+                if (t0 < c.bt) {
+                    if (nza) a = __ldg(reinterpret_cast<const float4 *>(ca + t0));
+                    if (nzb) b = __ldg(reinterpret_cast<const float4 *>(cb + t0));
+                }
+                v[4 * e + 0] = make_float2(a.x, b.x);
+                v[4 * e + 1] = make_float2(a.y, b.y);
+                v[4 * e + 2] = make_float2(a.z, b.z);
+                v[4 * e + 3] = make_float2(a.w, b.w);
+            }
+#pragma unroll
+            for (int m = 0; m < NPL; ++m) v[m] = fft32_lanes<false>(v[m], w32, lane);
+#pragma unroll
+            for (int m = 1; m < NPL; ++m) v[m] = cmul(v[m], __ldg(wlt + (m * k1) % LT));
+            fft_reg_any<NPL, false>(v);
+#pragma unroll
+            for (int k = 0; k < NPL; ++k) {
+                const int P = fft_perm<NPL>(k);
+                const int f = k1 + 32 * P;
+                // partner Z[lt - f]: lane src, register with perm NPL - 1 - P (k1 > 0) or
+                // (NPL - P) mod NPL (k1 = 0)
+                const int ka = dx_perm_inv<NPL>(NPL - 1 - P);
+                const int kb = dx_perm_inv<NPL>((NPL - P) % NPL);
+                float2 za, zb;
+                za.x = __shfl_sync(0xffffffffu, v[ka].x, src);
+                za.y = __shfl_sync(0xffffffffu, v[ka].y, src);
+                zb.x = __shfl_sync(0xffffffffu, v[kb].x, src);
+                zb.y = __shfl_sync(0xffffffffu, v[kb].y, src);
+                const float2 zc = k1 == 0 ? zb : za;
+                const float2 z = v[k];
+                if (f < c.nbins) {
+                    Tq[f] = 0.5f * (z.x + zc.x);               // Re Qhat[2q]
+                    Tq[2 * ST + f] = 0.5f * (z.y - zc.y);      // Im Qhat[2q]
+                    Tq[ST + f] = 0.5f * (z.y + zc.y);          // Re Qhat[2q + 1]
+                    Tq[3 * ST + f] = 0.5f * (zc.x - z.x);      // Im Qhat[2q + 1]
+                }
+            }
+        }
+        __syncthreads();
+        // bin by bin: lane pairs k = 2 lane + 64 i, BF16 hi and lo parts packed in pairs
+        for (int f = warp; f < c.nbins; f += NW) {
+            const size_t o = ((size_t)f * c.rows_cap + rl) * c.kq;
+            for (int k = 2 * lane; k < c.kq; k += 64) {
+                const float x0 = T[(size_t)k * ST + f], x1 = T[(size_t)(k + 1) * ST + f];
+                const uint32_t h0 = dx_bf16_bits(x0), h1 = dx_bf16_bits(x1);
+                const uint32_t l0 = dx_bf16_bits(x0 - dx_bf16_value(h0)), l1 = dx_bf16_bits(x1 - dx_bf16_value(h1));
+                *reinterpret_cast<uint32_t *>(qhi + o + k) = h0 | (h1 << 16);
+                *reinterpret_cast<uint32_t *>(qlo + o + k) = l0 | (l1 << 16);
+            }
+        }
+        __syncthreads();
+    }
+}
+
+// ---------------------------------------------------------------- GEMM per bin
+__device__ __forceinline__ void dx_tma_2d(uint32_t dst, const CUtensorMap *map, int x, int y, uint32_t bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
+            dst),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(bar)
+        : "memory");
+}
+// K-major operand with the 64-byte swizzle: rows of 64 B, 8-row atoms 512 B apart
+__device__ __forceinline__ uint64_t dx_sdesc_sw64(uint32_t addr) {
+    uint64_t d = 0;
+    d |= (uint64_t)((addr & 0x3FFFF) >> 4);        // start address
+    d |= (uint64_t)1 << 16;                        // leading byte offset (unused for swizzled K-major)
+    d |= (uint64_t)(512 >> 4) << 32;               // stride byte offset: next 8-row atom
+    d |= (uint64_t)1 << 46;                        // descriptor version
+    d |= (uint64_t)4 << 61;                        // 64-byte swizzle
+    return d;
+}
+__device__ __forceinline__ void dx_mma_bf16(uint32_t d, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d),
+        "l"(a), "l"(b), "r"(idesc), "r"(acc)
+        : "memory");
+}
+__device__ __forceinline__ void dx_commit(uint32_t bar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
+}
+__device__ __forceinline__ void dx_arrive(uint32_t bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+__device__ __forceinline__ void dx_epi_sync() { asm volatile("barrier.sync 1, 128;" ::: "memory"); }
+// OR of a flag over the 128 epilogue threads (named barrier 1 with a reduction)
+__device__ __forceinline__ int dx_epi_any(int flag) {
+    uint32_t r;
+    asm volatile(
+        "{\n\t.reg .pred p, q;\n\t"
+        "setp.ne.b32 p, %1, 0;\n\t"
+        "barrier.red.or.pred q, 1, 128, p;\n\t"
+        "selp.u32 %0, 1, 0, q;\n\t}"
+        : "=r"(r)
+        : "r"(flag)
+        : "memory");
+    return (int)r;
+}
+
+// Items (bin f, tile t) in bin-major order, strided over the persistent CTAs, so that the
+// CTAs running at one time share the bin's B operand in L2.  Warp 0 (one lane) issues
+// the copies of each item's K chunks into DX_STAGES stages; warp 1 (one lane) issues the
+// products into accumulator (item index & 1) of tensor memory and commits; warps 2..5
+// drain the accumulator into shared memory (row r = TMEM lane r), release it, and sum
+// each block's rows into Ihat[slot][f][P]:
+//     Ihat[P] = sum over the block's rows r (pixel p') of Z_r[K],  K = p' + R - (P - P0)
+// with P - P0 = (uy, ux) the block-local output pixel, rows in ascending order.
+__global__ void __launch_bounds__(DX_GEMM_THREADS, 1)
+    k_dx_gemm(const __grid_constant__ CUtensorMap tmAh, const __grid_constant__ CUtensorMap tmAl,
+              const __grid_constant__ CUtensorMap tmBh, const __grid_constant__ CUtensorMap tmBl,
+              const int32_t *__restrict__ rows, const int32_t *__restrict__ rowstart, const int32_t *__restrict__ meta,
+              DxConst c, int row0, float2 *__restrict__ ybuf, int32_t *__restrict__ status) {
+    extern __shared__ unsigned char dx_raw[];
+    const uint32_t raw = smem_u32(dx_raw);
+    const uint32_t base = (raw + 1023u) & ~1023u;
+    unsigned char *gbase = dx_raw + (base - raw);
+    const uint32_t SB = dx_stage_bytes(c.npad);
+    const uint32_t BB = dx_b_bytes(c.npad);
+    const int SZ = 2 * c.ntap + 1;
+    float *Zs = reinterpret_cast<float *>(gbase + DX_STAGES * SB);
+    int32_t *rowrec = reinterpret_cast<int32_t *>(Zs + DX_M * SZ);
+    const uint32_t bar0 = (smem_u32(rowrec + DX_M) + 7u) & ~7u;
+    auto bar_full = [&](int st) { return bar0 + 8u * (uint32_t)st; };
+    auto bar_empty = [&](int st) { return bar0 + 8u * (uint32_t)(DX_STAGES + st); };
+    auto bar_accf = [&](int ab) { return bar0 + 8u * (uint32_t)(2 * DX_STAGES + ab); };
+    auto bar_acce = [&](int ab) { return bar0 + 8u * (uint32_t)(2 * DX_STAGES + 2 + ab); };
+    const uint32_t bar_done = bar0 + 8u * (uint32_t)(2 * DX_STAGES + 4);
+    unsigned char *gb = gbase + (bar_done + 8u - base);
+    uint32_t *tslot = reinterpret_cast<uint32_t *>(gb);
+    volatile int *abort_flag = reinterpret_cast<volatile int *>(gb + 4);
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+
+    if (warp == 0) {
+        tmem_alloc(tslot, 512);
+        tmem_relinquish();
+    }
+    if (tid == 0) {
+        for (int st = 0; st < DX_STAGES; ++st) {
+            mbar_init(bar_full(st), 1);
+            mbar_init(bar_empty(st), 1);
+        }
+        for (int ab = 0; ab < 2; ++ab) {
+            mbar_init(bar_accf(ab), 1);
+            mbar_init(bar_acce(ab), 4);
+        }
+        mbar_init(bar_done, 1);
+        *abort_flag = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    tmem_fence_before();
+    __syncthreads();
+    tmem_fence_after();
+    const uint32_t tmem = *tslot;
+
+    const int nrows = meta[1];
+    const int nloc = min(c.rows_cap, nrows - row0);
+    const int ntiles = nloc > 0 ? (nloc + DX_M - 1) / DX_M : 0;
+    const int nitems = ntiles * c.nbins;
+    const int nkc = (c.kq + DX_KC - 1) / DX_KC;
+    const uint32_t tx_bytes = 2 * DX_A_BYTES + 2 * BB;
+    const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(c.npad >> 3) << 17) | ((128u >> 4) << 24);
+
+    if (warp == 0) {
+        // ------------------------------------------------ copies
+        if (lane == 0) {
+            int g = 0;
+            bool ok = true;
+            for (int it = blockIdx.x; it < nitems && ok; it += gridDim.x) {
+                const int f = it / ntiles, t = it - f * ntiles;
+                for (int kc = 0; kc < nkc; ++kc, ++g) {
+                    const int st = g % DX_STAGES;
+                    if (g >= DX_STAGES && !mbar_wait(bar_empty(st), (uint32_t)((g / DX_STAGES - 1) & 1))) {
+                        ok = false;
+                        break;
+                    }
+                    if (*abort_flag) {
+                        ok = false;
+                        break;
+                    }
+                    const uint32_t sb = base + (uint32_t)st * SB;
+                    mbar_expect_tx(bar_full(st), tx_bytes);
+                    const int ya = f * c.rows_cap + t * DX_M;
+                    dx_tma_2d(sb, &tmAh, kc * DX_KC, ya, bar_full(st));
+                    dx_tma_2d(sb + DX_A_BYTES, &tmAl, kc * DX_KC, ya, bar_full(st));
+                    dx_tma_2d(sb + 2 * DX_A_BYTES, &tmBh, kc * DX_KC, f * c.npad, bar_full(st));
+                    dx_tma_2d(sb + 2 * DX_A_BYTES + BB, &tmBl, kc * DX_KC, f * c.npad, bar_full(st));
+                }
+            }
+            if (!ok) {
+                atomicOr(&status[0], TRED_ST_TIMEOUT);
+                *abort_flag = 1;
+            }
+            // the last copies into each stage have landed before the CTA ends
+            for (int q = max(0, g - DX_STAGES); q < g; ++q)
+                (void)mbar_wait(bar_full(q % DX_STAGES), (uint32_t)((q / DX_STAGES) & 1));
+        }
+    } else if (warp == 1) {
+        // ------------------------------------------------ products
+        if (lane == 0) {
+            int g = 0, i = 0;
+            bool ok = true;
+            for (int it = blockIdx.x; it < nitems && ok; it += gridDim.x, ++i) {
+                const int ab = i & 1;
+                if (i >= 2 && !mbar_wait(bar_acce(ab), (uint32_t)(((i >> 1) - 1) & 1))) {
+                    ok = false;
+                    break;
+                }
+                tmem_fence_after();
+                const uint32_t d = tmem + (uint32_t)(ab * 256);
+                for (int kc = 0; kc < nkc; ++kc, ++g) {
+                    const int st = g % DX_STAGES;
+                    if (!mbar_wait(bar_full(st), (uint32_t)((g / DX_STAGES) & 1)) || *abort_flag) {
+                        ok = false;
+                        break;
+                    }
+                    tmem_fence_after();
+                    const uint32_t sb = base + (uint32_t)st * SB;
+#pragma unroll
+                    for (int ks = 0; ks < DX_KC / 16; ++ks) {
+                        if (kc * DX_KC + ks * 16 >= c.kq) break;
+                        const uint32_t acc = (kc > 0 || ks > 0) ? 1u : 0u;
+                        const uint64_t ah = dx_sdesc_sw64(sb + 32 * ks);
+                        const uint64_t al = dx_sdesc_sw64(sb + DX_A_BYTES + 32 * ks);
+                        const uint64_t bh = dx_sdesc_sw64(sb + 2 * DX_A_BYTES + 32 * ks);
+                        const uint64_t bl = dx_sdesc_sw64(sb + 2 * DX_A_BYTES + BB + 32 * ks);
+                        dx_mma_bf16(d, ah, bh, idesc, acc);
+                        dx_mma_bf16(d, ah, bl, idesc, 1u);
+                        dx_mma_bf16(d, al, bh, idesc, 1u);
+                    }
+                    dx_commit(bar_empty(st));
+                }
+                if (!ok) break;
+                dx_commit(bar_accf(ab));
+            }
+            if (!ok) {
+                atomicOr(&status[0], TRED_ST_TIMEOUT);
+                *abort_flag = 1;
+            }
+            // every product issued has completed before the tensor memory goes
+            dx_commit(bar_done);
+            (void)mbar_wait(bar_done, 0);
+        }
+    } else {
+        // ------------------------------------------------ epilogue (warps 2..5)
+        const int te = tid - 64;
+        const int quarter = warp & 3;
+        const int R2 = 2 * c.R;
+        int i = 0;
+        for (int it = blockIdx.x; it < nitems; it += gridDim.x, ++i) {
+            const int f = it / ntiles, t = it - f * ntiles;
+            const int ab = i & 1;
+            const int nv = min(DX_M, nloc - t * DX_M);
+            const int t0g = row0 + t * DX_M;
+            rowrec[te] = te < nv ? rows[t0g + te] : 0;
+            int bad = mbar_wait(bar_accf(ab), (uint32_t)((i >> 1) & 1)) ? 0 : 1;
+            bad |= *abort_flag;
+            if (dx_epi_any(bad)) {   // the four epilogue warps leave together
+                if (te == 0) {
+                    atomicOr(&status[0], TRED_ST_TIMEOUT);
+                    *abort_flag = 1;
+                }
+                break;
+            }
+            tmem_fence_after();
+            const int r = 32 * quarter + lane;
+            for (int cc = 0; cc < (2 * c.ntap + 31) / 32; ++cc) {
+                float v[32];
+                tmem_ld32(tmem + ((uint32_t)(32 * quarter) << 16) + (uint32_t)(ab * 256 + 32 * cc), v);
+#pragma unroll
+                for (int e = 0; e < 32; ++e)
+                    if (32 * cc + e < 2 * c.ntap) Zs[r * SZ + 32 * cc + e] = v[e];
+            }
+            tmem_fence_before();
+            __syncwarp();
+            if (lane == 0) dx_arrive(bar_acce(ab));
+            dx_epi_sync();
+            const int s_first = rowrec[0] >> 6, s_last = rowrec[nv - 1] >> 6;
+            for (int s = s_first; s <= s_last; ++s) {
+                const int rs = rowstart[s], re = rowstart[s + 1];
+                const int ra = max(rs - t0g, 0), rb = min(re - t0g, nv);
+                if (ra >= rb) continue;
+                const bool split = (rs >> 7) != ((re - 1) >> 7);
+                float2 *yb = ybuf + ((size_t)s * c.nbins + f) * (LP * LP);
+                for (int u = te; u < LP * LP; u += 128) {
+                    const int uy = u >> 4, ux = u & 15;
+                    float ar = 0.f, ai = 0.f;
+                    for (int rr = ra; rr < rb; ++rr) {
+                        const int pp = rowrec[rr] & 63;
+                        const int py = pp / c.bp, px = pp - py * c.bp;
+                        const int Ky = py + R2 - uy, Kx = px + R2 - ux;
+                        if ((unsigned)Ky < (unsigned)c.kp && (unsigned)Kx < (unsigned)c.kp) {
+                            const int n = Ky * c.kp + Kx;
+                            ar += Zs[rr * SZ + n];
+                            ai += Zs[rr * SZ + c.ntap + n];
+                        }
+                    }
+                    if (split) {
+                        atomicAdd(&yb[u].x, ar);
+                        atomicAdd(&yb[u].y, ai);
+                    } else {
+                        yb[u] = make_float2(ar, ai);
+                    }
+                }
+            }
+            dx_epi_sync();
+        }
+    }
+    tmem_fence_before();
+    __syncthreads();
+    if (warp == 0) {
+        tmem_fence_after();
+        tmem_dealloc(tmem, 512);
+    }
+}
+
+// ---------------------------------------------------------------- inverse time DFT
+// Per block (persistent over the slots of the pass), 32 output pixels at a time: their
+// lt/2 + 1 bins staged in shared memory [f][32], then warp w inverts pixels a = w and
+// b = w + 16 of the group as one complex sequence Z[f] = Ihat_a[f] + i Ihat_b[f] (the
+// bins above lt/2 from the conjugate symmetry of real signals): an NPL-point inverse DFT
+// over the samples a lane holds (bins l + 32 m), the twiddles, a 32-point inverse DFT
+// across the lanes; lane l then holds t = NPL bitrev5(l) + fft_perm(k) in register k,
+// Re z[t] = I_a[t] and Im z[t] = I_b[t].  A slot with no rows is written as zeros.
+template <int G>
+__global__ void __launch_bounds__(DX_INV_THREADS, 1)
+    k_dx_inv(const float2 *__restrict__ ybuf, const int32_t *__restrict__ rowstart, const int32_t *__restrict__ meta,
+             const float2 *__restrict__ tw, DxConst c, int slot_base, float *__restrict__ out) {
+    constexpr int LT = 64 * G;
+    constexpr int NPL = LT / 32;
+    constexpr int NB = LT / 2 + 1;
+    constexpr int YS = 33;   // staging row (float2)
+    extern __shared__ float2 Ys[];   // [NB][YS]
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int cnt = meta[0];
+    const float2 *wlt = tw + TW_LT;
+    const float2 *w32 = tw + TW_32;
+    const int b5 = bitrev<32>(lane);
+    for (int s = blockIdx.x; s < cnt; s += gridDim.x) {
+        float *ob = out + (size_t)(slot_base + s) * (LP * LP) * LT;
+        if (rowstart[s + 1] == rowstart[s]) {
+            float4 *o4 = reinterpret_cast<float4 *>(ob);
+            for (int i = tid; i < (LP * LP) * LT / 4; i += DX_INV_THREADS) o4[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+            continue;
+        }
+        const float2 *yb = ybuf + (size_t)s * NB * (LP * LP);
+        for (int ug = 0; ug < (LP * LP) / 32; ++ug) {
+            __syncthreads();   // the previous group's reads are done
+            for (int i = tid; i < NB * 32; i += DX_INV_THREADS) {
+                const int f = i >> 5, ul = i & 31;
+                Ys[f * YS + ul] = yb[(size_t)f * (LP * LP) + 32 * ug + ul];
+            }
+            __syncthreads();
+            const int ua = warp, ub = warp + 16;
+            float2 v[NPL];
+#pragma unroll
+            for (int m = 0; m < NPL; ++m) {
+                const int f = lane + 32 * m;
+                float2 A, B;
+                if (f < NB) {
+                    A = Ys[f * YS + ua];
+                    B = Ys[f * YS + ub];
+                } else {
+                    A = cconj(Ys[(LT - f) * YS + ua]);
+                    B = cconj(Ys[(LT - f) * YS + ub]);
+                }
+                v[m] = make_float2(A.x - B.y, A.y + B.x);
+            }
+            fft_reg_any<NPL, true>(v);   // v[k] = u[fft_perm(k)]
+#pragma unroll
+            for (int k = 0; k < NPL; ++k) {
+                const int aa = fft_perm<NPL>(k);
+                float2 w = __ldg(wlt + (lane * aa) % LT);
+                w.y = -w.y;
+                v[k] = fft32_lanes<true>(cmul(v[k], w), w32, lane);
+            }
+            float ra[NPL], rb[NPL];
+#pragma unroll
+            for (int k = 0; k < NPL; ++k) {
+                const int t = fft_perm<NPL>(k);
+                ra[t] = v[k].x;
+                rb[t] = v[k].y;
+            }
+            float *oa = ob + (size_t)(32 * ug + ua) * LT + NPL * b5;
+            float *obb = ob + (size_t)(32 * ug + ub) * LT + NPL * b5;
+#pragma unroll
+            for (int k = 0; k < NPL; k += 4) {
+                *reinterpret_cast<float4 *>(oa + k) = make_float4(ra[k], ra[k + 1], ra[k + 2], ra[k + 3]);
+                *reinterpret_cast<float4 *>(obb + k) = make_float4(rb[k], rb[k + 1], rb[k + 2], rb[k + 3]);
+            }
+        }
+        __syncthreads();
+    }
+}
+
+// ---------------------------------------------------------------- host side
+// 2-D BF16 tensor [rows][inner], box [box_rows][32] (64 bytes), 64-byte swizzle; columns
+// past inner read as zero
+static int dx_make_map(tred_handle *h, CUtensorMap *m, const void *ptr, uint64_t inner, uint64_t rows,
+                       uint32_t box_rows) {
+    auto fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(tensor_map_encoder());
+    if (!fn) return set_error(h, TRED_ERR_CUDA, "direct form: cuTensorMapEncodeTiled unavailable");
+    const cuuint64_t dims[2] = {inner, rows};
+    const cuuint64_t strides[1] = {inner * 2};
+    const cuuint32_t box[2] = {(cuuint32_t)DX_KC, box_rows};
+    const cuuint32_t estr[2] = {1, 1};
+    CUresult r = fn(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void *>(ptr), dims, strides, box, estr,
+                    CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                    CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) return set_error(h, TRED_ERR_CUDA, "direct form: tensor map encode failed (%d)", (int)r);
+    return TRED_OK;
+}
+
+template <int G>
+static int run_direct(tred_handle *h, const DxConst &c, const int32_t *n_blocks_dev, const float *qeff, float *out,
+                      int slot_base, int slot_count, int qbase, cudaStream_t s) {
+    const size_t fwd_smem = dx_fwd_smem(c.kq, c.nbins);
+    const size_t gemm_smem = dx_gemm_smem(c.npad, c.ntap);
+    const size_t inv_smem = sizeof(float2) * (size_t)(32 * G + 1) * 33;
+    // the largest dynamic shared memory asked for so far (shapes differ between handles)
+    static size_t set_fwd = 0, set_inv = 0;
+    static size_t set_gemm = 0;
+    if (fwd_smem > set_fwd) {
+        cudaFuncSetAttribute(k_dx_fwd<G>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fwd_smem);
+        set_fwd = fwd_smem;
+    }
+    if (gemm_smem > set_gemm) {
+        cudaFuncSetAttribute(k_dx_gemm, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)gemm_smem);
+        set_gemm = gemm_smem;
+    }
+    if (inv_smem > set_inv) {
+        cudaFuncSetAttribute(k_dx_inv<G>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)inv_smem);
+        set_inv = inv_smem;
+    }
+    CUtensorMap tah, tal, tbh, tbl;
+    int rc = dx_make_map(h, &tah, h->dx_qhi, (uint64_t)c.kq, (uint64_t)c.nbins * c.rows_cap, DX_M);
+    if (!rc) rc = dx_make_map(h, &tal, h->dx_qlo, (uint64_t)c.kq, (uint64_t)c.nbins * c.rows_cap, DX_M);
+    if (!rc) rc = dx_make_map(h, &tbh, h->dx_bhi, (uint64_t)c.kq, (uint64_t)c.nbins * c.npad, (uint32_t)c.npad);
+    if (!rc) rc = dx_make_map(h, &tbl, h->dx_blo, (uint64_t)c.kq, (uint64_t)c.nbins * c.npad, (uint32_t)c.npad);
+    if (rc) return rc;
+    const int sms = num_sms(h);
+    const int end = slot_base + slot_count;
+    for (int base = slot_base; base < end; base += h->dx_blocks) {
+        const int cnt = h->dx_blocks < end - base ? h->dx_blocks : end - base;
+        k_dx_pixmask<<<sms * 4, 256, 0, s>>>(n_blocks_dev, h->colmask, c.nch, c.bp2, base, cnt, h->dx_pmask);
+        k_dx_rows<<<1, DX_ROWS_THREADS, 0, s>>>(n_blocks_dev, h->dx_pmask, base, cnt, h->dx_rows, h->dx_rowstart,
+                                                h->dx_meta);
+        h->launches += 2;
+        const int64_t max_rows = (int64_t)cnt * c.bp2;
+        const int nrc = (int)((max_rows + c.rows_cap - 1) / c.rows_cap);
+        for (int k = 0; k < nrc; ++k) {
+            const int row0 = k * c.rows_cap;
+            k_dx_fwd<G><<<sms, DX_FWD_THREADS, fwd_smem, s>>>(qeff, h->colmask, h->dx_rows, h->dx_rowstart, h->dx_meta,
+                                                             h->tw, c, base, qbase, row0, k == 0 ? 1 : 0, h->dx_qhi,
+                                                             h->dx_qlo, h->dx_y);
+            k_dx_gemm<<<sms, DX_GEMM_THREADS, gemm_smem, s>>>(tah, tal, tbh, tbl, h->dx_rows, h->dx_rowstart,
+                                                              h->dx_meta, c, row0, h->dx_y, h->status);
+            h->launches += 2;
+        }
+        k_dx_inv<G><<<sms, DX_INV_THREADS, inv_smem, s>>>(h->dx_y, h->dx_rowstart, h->dx_meta, h->tw, c, base, out);
+        h->launches += 1;
+    }
+    return check_cuda(h, cudaGetLastError(), "direct-form launch");
+}
+
+int launch_direct(tred_handle *h, const int32_t *n_blocks_dev, const float *qeff, float *out, int slot_base,
+                  int slot_count, int qbase, cudaStream_t s) {
+    const DxConst c = dx_const_of(h);
+    if (c.lt == 512) return run_direct<8>(h, c, n_blocks_dev, qeff, out, slot_base, slot_count, qbase, s);
+    if (c.lt == 384) return run_direct<6>(h, c, n_blocks_dev, qeff, out, slot_base, slot_count, qbase, s);
+    return set_error(h, TRED_ERR_INVALID_ARG, "direct form: lt must be 384 or 512");
+}
+
+// sizes of the direct form's buffers (tred_create)
+size_t dx_bytes_b(int nbins, int npad, int kq) { return 2 * (size_t)nbins * npad * kq; }
+size_t dx_bytes_q(int nbins, int rows_cap, int kq) { return 2 * (size_t)nbins * rows_cap * kq; }
+int dx_rows_cap_of(int dx_blocks, int bp2, int cap_param) {
+    const int64_t want = (int64_t)dx_blocks * bp2;
+    const int64_t lim = cap_param > 0 ? cap_param : DX_ROWS_MAX;
+    const int64_t cap = want < lim ? want : lim;
+    return (int)((cap + DX_M - 1) / DX_M * DX_M);
+}
+int dx_blocks_of(int max_blocks) { return max_blocks < DX_BLOCKS_MAX ? max_blocks : DX_BLOCKS_MAX; }
+// the forward kernel's transposition buffer must fit in one CTA's shared memory
+bool dx_shape_ok(int kq, int lt) { return dx_fwd_smem(kq, lt / 2 + 1) <= 227 * 1024; }
+
+}  // namespace tred

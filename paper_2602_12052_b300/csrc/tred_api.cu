@@ -130,12 +130,16 @@ static int validate(const tred_geometry *g, const tred_params *p, char *msg, siz
     if (!(p->max_drift_cm >= 0)) return bad("max_drift_cm must be >= 0");
     if (p->gl_order < 1 || p->gl_order > MAX_GL) return bad("gl_order must be 1..8");
     if (p->effq_mode != 0 && p->effq_mode != 1) return bad("effq_mode must be 0 or 1");
-    if (p->conv_mode < 0 || p->conv_mode > 3) return bad("conv_mode must be 0, 1, 2 or 3");
-    if (p->conv_mode != 0 && (g->lt != 512 || g->bp != 8))
+    if (p->conv_mode < 0 || p->conv_mode > 4) return bad("conv_mode must be 0, 1, 2, 3 or 4");
+    if (p->conv_mode >= 1 && p->conv_mode <= 3 && (g->lt != 512 || g->bp != 8))
         return bad("the tensor-core convolution (conv_mode 1, 2, 3) needs lt = 512 and bp = 8");
+    if (p->conv_mode == 4 && ((g->lt != 384 && g->lt != 512) || g->kp > 9 || !dx_shape_ok(2 * g->n_sub * g->n_sub, g->lt)))
+        return bad("the direct spatial form (conv_mode 4) needs lt = 384 or 512, kp <= 9 and n_sub <= 10");
     if (p->mpcp != 0 && p->mpcp != 1) return bad("mpcp must be 0 or 1");
     if (p->effq_skip_empty != 0 && p->effq_skip_empty != 1) return bad("effq_skip_empty must be 0 or 1");
-    if (p->effq_skip_empty && p->conv_mode != 0) return bad("the tensor-core convolution reads every column: effq_skip_empty must be 0");
+    if (p->conv_rows_cap < 0 || p->conv_rows_cap % 128) return bad("conv_rows_cap must be a non-negative multiple of 128");
+    if (p->effq_skip_empty && p->conv_mode >= 1 && p->conv_mode <= 3)
+        return bad("the tensor-core time DFT reads every column: effq_skip_empty must be 0");
     return TRED_OK;
 }
 
@@ -211,7 +215,7 @@ int32_t tred_create(const tred_geometry *geom, const tred_params *params, int32_
     alloc((void **)&h->wts, sizeof(float) * (size_t)max_deposits * d.wstride, "alloc weights");
     alloc((void **)&h->recs, 48 * (size_t)max_deposits, "alloc deposit records");
     alloc((void **)&h->effq_acc, effq_scratch_bytes(geom->bp * ns, num_sms(h)), "alloc effq scratch");
-    if (params->conv_mode != 0) {
+    if (params->conv_mode >= 1 && params->conv_mode <= 3) {
         h->zspec_blocks = max_blocks < 256 ? max_blocks : 256;
         alloc((void **)&h->dft_hi, dft_basis_bytes(geom->bt), "alloc dft basis");
         alloc((void **)&h->dft_lo, dft_basis_bytes(geom->bt), "alloc dft basis");
@@ -227,8 +231,24 @@ int32_t tred_create(const tred_geometry *geom, const tred_params *params, int32_
     // blocks per convolution launch pair: 8192 (8.6 GB of spectra at lt = 512) puts a
     // module plane in one launch, so the spectral kernel's last partial wave of
     // (block, class) items comes once per call rather than once per 1024 blocks
-    h->yspec_blocks = max_blocks < 8192 ? max_blocks : 8192;
-    alloc((void **)&h->yspec, sizeof(float2) * (size_t)h->yspec_blocks * geom->lt * LP * LP, "alloc yspec");
+    if (params->conv_mode == 4) {
+        const int kq = 2 * ns * ns, npad = (2 * geom->kp * geom->kp + 15) & ~15, nbins = geom->lt / 2 + 1;
+        const int bp2 = geom->bp * geom->bp;
+        h->dx_blocks = dx_blocks_of(max_blocks);
+        h->dx_rows_cap = dx_rows_cap_of(h->dx_blocks, bp2, params->conv_rows_cap);
+        alloc((void **)&h->dx_bhi, dx_bytes_b(nbins, npad, kq), "alloc direct-form response");
+        alloc((void **)&h->dx_blo, dx_bytes_b(nbins, npad, kq), "alloc direct-form response");
+        alloc((void **)&h->dx_qhi, dx_bytes_q(nbins, h->dx_rows_cap, kq), "alloc direct-form spectra");
+        alloc((void **)&h->dx_qlo, dx_bytes_q(nbins, h->dx_rows_cap, kq), "alloc direct-form spectra");
+        alloc((void **)&h->dx_y, sizeof(float2) * (size_t)h->dx_blocks * nbins * LP * LP, "alloc direct-form output");
+        alloc((void **)&h->dx_rows, sizeof(int32_t) * (size_t)h->dx_blocks * bp2, "alloc direct-form rows");
+        alloc((void **)&h->dx_rowstart, sizeof(int32_t) * ((size_t)h->dx_blocks + 2), "alloc direct-form rows");
+        alloc((void **)&h->dx_meta, sizeof(int32_t) * 4, "alloc direct-form rows");
+        alloc((void **)&h->dx_pmask, sizeof(uint64_t) * (size_t)h->dx_blocks, "alloc direct-form masks");
+    } else {
+        h->yspec_blocks = max_blocks < 8192 ? max_blocks : 8192;
+        alloc((void **)&h->yspec, sizeof(float2) * (size_t)h->yspec_blocks * geom->lt * LP * LP, "alloc yspec");
+    }
     alloc((void **)&h->pix_flag, sizeof(int32_t) * (size_t)geom->npx_x * d.npy, "alloc pixel flags");
     h->pix_chunks = ((int64_t)geom->npx_x * d.npy + 1023) / 1024;
     alloc((void **)&h->pix_part, sizeof(int32_t) * (size_t)(h->pix_chunks + 8), "alloc pixel scan");
@@ -285,7 +305,8 @@ int32_t tred_destroy(tred_handle *h) {
     if (!h) return TRED_ERR_INVALID_ARG;
     void *ptrs[] = {h->dep_event, h->wts2, h->pix_row, h->gspec, h->rhat, h->pair_j, h->wts, h->recs, h->effq_acc, h->dft_hi, h->dft_lo, h->zspec, h->blk_count, h->blk_slot, h->blk_fill,
                     h->scan_part, h->colmask, h->yspec, h->pix_flag, h->pix_part, h->px_possum, h->hit_cnt,
-                    h->hit_tmp, h->hit_tmpc, h->status, h->tw};
+                    h->hit_tmp, h->hit_tmpc, h->status, h->tw, h->dx_bhi, h->dx_blo, h->dx_qhi, h->dx_qlo,
+                    h->dx_y, h->dx_rows, h->dx_rowstart, h->dx_meta, h->dx_pmask};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     free(h);
@@ -387,6 +408,7 @@ int32_t tred_set_response(tred_handle *h, const float *resp_dev, void *stream) {
     if (!h) return TRED_ERR_INVALID_ARG;
     if (!resp_dev) return set_error(h, TRED_ERR_INVALID_ARG, "tred_set_response: null response");
     int rc = launch_response(h, resp_dev, (cudaStream_t)stream);
+    if (rc == TRED_OK && h->p.conv_mode == 4) rc = launch_direct_response(h, resp_dev, (cudaStream_t)stream);
     if (rc == TRED_OK) h->response_ready = true;
     return rc;
 }

@@ -59,6 +59,16 @@ struct tred_handle {
     float *dft_hi, *dft_lo;  // tensor-core form: [512][bt] real DFT basis, TF32 part and residual
     float2 *zspec;         // tensor-core form: [zspec_blocks][G][npairs][64][64] packed spectra
     int32_t zspec_blocks;
+    // direct spatial form (conv_mode 4): per time frequency, the sum over impacts and
+    // response taps as a split-BF16 tensor-core GEMM over the non-empty block pixels
+    uint16_t *dx_bhi, *dx_blo;  // [nbins][npad][kq] response operand (BF16 hi and lo parts)
+    uint16_t *dx_qhi, *dx_qlo;  // [nbins][dx_rows_cap][kq] charge spectra of the rows
+    float2 *dx_y;               // [dx_blocks][nbins][16 * 16] block output spectra
+    int32_t *dx_rows;           // [dx_blocks * bp^2] row records: local slot << 6 | pixel
+    int32_t *dx_rowstart;       // [dx_blocks + 1] first row of each slot, then the row count
+    int32_t *dx_meta;           // [4]: slots of the pass, rows of the pass
+    uint64_t *dx_pmask;         // [dx_blocks] non-empty pixels of each slot
+    int32_t dx_blocks, dx_rows_cap;
     int32_t *blk_count;    // [nblk] occupancy
     int32_t *blk_slot;     // [nblk] slot of an active block or -1
     int32_t *blk_fill;     // [max_blocks] CSR fill cursors
@@ -134,6 +144,18 @@ int launch_pipeline(tred_handle *h, int n, const tred_deposits &deps, const int3
                     const int32_t *dep_offsets, const int32_t *dep_index, const int32_t *n_blocks_dev, float *qring,
                     int ring_rows, float *out, cudaStream_t s);
 int launch_wait_selftest(tred_handle *h, long long limit, cudaStream_t s);
+// direct spatial form (conv_mode 4): the response operand (once per response) and the
+// convolution of slots [slot_base, slot_base + slot_count) with qeff rows from qbase
+int launch_direct_response(tred_handle *h, const float *resp, cudaStream_t s);
+int launch_direct(tred_handle *h, const int32_t *n_blocks_dev, const float *qeff, float *out, int slot_base,
+                  int slot_count, int qbase, cudaStream_t s);
+size_t dx_bytes_b(int nbins, int npad, int kq);
+size_t dx_bytes_q(int nbins, int rows_cap, int kq);
+int dx_rows_cap_of(int dx_blocks, int bp2, int cap_param);
+int dx_blocks_of(int max_blocks);
+bool dx_shape_ok(int kq, int lt);
+// the driver entry point cuTensorMapEncodeTiled (nullptr when unavailable)
+void *tensor_map_encoder();
 int launch_convolve(tred_handle *h, const int32_t *block_ids, const int32_t *n_blocks_dev,
                     const float *qeff, float *out, int slot_base, int slot_count, cudaStream_t s);
 int launch_gather(tred_handle *h, const int32_t *block_ids, const int32_t *n_blocks_dev,

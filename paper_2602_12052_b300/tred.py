@@ -38,13 +38,14 @@ def geometry(cfg, n_events: int = 1) -> Geometry:
                     n_events=n_events)
 
 
-def params(cfg, effq_mode=0, mpcp=1, compensated_gather=0, conv_mode=0, effq_skip_empty=0) -> Params:
+def params(cfg, effq_mode=0, mpcp=1, compensated_gather=0, conv_mode=0, effq_skip_empty=0, conv_rows_cap=0) -> Params:
     return Params(v_cm_per_us=cfg.v_cm_per_us, DL_cm2_per_s=cfg.DL_cm2_per_s,
                   DT_cm2_per_s=cfg.DT_cm2_per_s, lifetime_us=cfg.lifetime_us,
                   sigma0_cells_xy=cfg.sigma0_cells_xy, sigma0_ticks=cfg.sigma0_ticks,
                   nsigma=cfg.nsigma, max_drift_cm=cfg.max_drift_cm, gl_order=cfg.gl_order,
                   effq_mode=effq_mode, conv_mode=conv_mode, mpcp=mpcp,
-                  compensated_gather=compensated_gather, effq_skip_empty=effq_skip_empty)
+                  compensated_gather=compensated_gather, effq_skip_empty=effq_skip_empty,
+                  conv_rows_cap=conv_rows_cap)
 
 
 def readout_params(cfg) -> ReadoutParams:
@@ -257,12 +258,13 @@ class Simulator:
     def __init__(self, cfg, resp: torch.Tensor, max_deposits: int, max_blocks: int,
                  max_pixels: int, max_pairs: int | None = None, max_hits: int | None = None,
                  effq_mode=0, mpcp=1, compensated_gather=0, conv_mode=0, effq_skip_empty=0, device=None,
-                 fused=False):
+                 fused=False, conv_rows_cap=0):
         self.cfg = cfg
         self.mpcp = mpcp
         self.fused = bool(fused)
         self.device = torch.device(device or "cuda")
-        self.h = Handle(geometry(cfg), params(cfg, effq_mode, mpcp, compensated_gather, conv_mode, effq_skip_empty),
+        self.h = Handle(geometry(cfg), params(cfg, effq_mode, mpcp, compensated_gather, conv_mode, effq_skip_empty,
+                                              conv_rows_cap),
                         max_deposits, max_blocks, max_pixels)
         self.rp = readout_params(cfg)
         d = self.device
