@@ -54,13 +54,14 @@ constexpr int DX_KC = 32;                // K chunk: 32 BF16 = one 64-byte row (
 constexpr int DX_STAGES = 3;             // operand stages
 constexpr int DX_ROWS_MAX = 131072;      // rows per forward + GEMM launch pair
 constexpr int DX_BLOCKS_MAX = 8192;      // slots per pass
-constexpr int DX_FWD_THREADS = 512;
-constexpr int DX_INV_THREADS = 512;
-constexpr int DX_GEMM_THREADS = 192;     // warp 0 copies, warp 1 products, warps 2..5 epilogue
+constexpr int DX_FWD_THREADS = 256;
+constexpr int DX_INV_THREADS = 256;
+constexpr int DX_GEMM_THREADS = 320;     // warp 0 copies, warp 1 products, warps 2..9 epilogue
 constexpr uint32_t DX_A_BYTES = DX_M * DX_KC * 2;   // 8 KB per part
+constexpr int DX_TAPS_PER_LANE = 3;   // kp <= 9: at most 81 taps
 
 struct DxConst {
-    int nch, kq, ntap, npad, kp, R, bp, bp2, bt, lt, nbins, rows_cap;
+    int nch, kq, ntap, npad, kp, R, bp, bpl, bp2, bt, lt, nbins, rows_cap;
 };
 
 __host__ __device__ constexpr int dx_round16(int x) { return (x + 15) & ~15; }
@@ -68,12 +69,18 @@ __host__ __device__ constexpr uint32_t dx_b_bytes(int npad) { return (uint32_t)n
 __host__ __device__ constexpr uint32_t dx_stage_bytes(int npad) {
     return (2 * DX_A_BYTES + 2 * dx_b_bytes(npad) + 1023u) & ~1023u;
 }
-// odd column stride of the forward kernel's transposition buffer (bins per column)
-__host__ __device__ constexpr int dx_tstride(int nbins) { return nbins | 1; }
-size_t dx_fwd_smem(int kq, int nbins) { return sizeof(float) * (size_t)kq * dx_tstride(nbins); }
+// column stride of the forward kernel's transposition buffer: at least nbins + 3 (room
+// for the columns' skew of up to 3) and 1 mod 8, so that the lanes reading columns
+// 4 k4 .. 4 k4 + 3 of one bin (k4 = lane) hit distinct banks; the buffer holds half a
+// row's kq columns
+__host__ __device__ constexpr int dx_tstride(int nbins) { return ((nbins + 10) & ~7) + 1; }
+size_t dx_fwd_smem(int kq, int nbins) { return sizeof(float) * (size_t)(kq / 2) * dx_tstride(nbins); }
+// epilogue staging row (floats): a multiple of 4 (16-byte stores) with an odd number of
+// 16-byte chunks (the 32 lanes' rows start in distinct bank groups)
+__host__ __device__ constexpr int dx_zstride(int ntap) { return ((2 * ntap + 3) / 4 | 1) * 4; }
 static size_t dx_gemm_smem(int npad, int ntap) {
-    return 1024 + DX_STAGES * (size_t)dx_stage_bytes(npad) + sizeof(float) * DX_M * (2 * ntap + 1) +
-           sizeof(int32_t) * DX_M + 128;
+    return 1024 + DX_STAGES * (size_t)dx_stage_bytes(npad) + sizeof(float) * DX_M * dx_zstride(ntap) +
+           sizeof(float2) * 8 * LP * LP + sizeof(int32_t) * (3 * DX_M + 2 + 5) + 128;
 }
 
 // nearest BF16 (ties to even) of a finite binary32 value, as its 16 bits, and its value
@@ -160,6 +167,7 @@ static DxConst dx_const_of(const tred_handle *h) {
     c.npad = dx_round16(2 * c.ntap);
     c.R = h->d.R;
     c.bp = h->g.bp;
+    c.bpl = c.bp == 8 ? 3 : 2;   // bp is 4 or 8
     c.bp2 = c.bp * c.bp;
     c.bt = h->g.bt;
     c.lt = h->g.lt;
@@ -293,18 +301,32 @@ __device__ __forceinline__ void dx_zero_straddling(const int32_t *__restrict__ r
     }
 }
 
-// One CTA per row at a time (persistent over the rows [row0, row0 + rows_cap) of the
-// pass).  Warp w transforms the impact pairs q = w, w + 16, ...: the two real columns
-// as one complex sequence, z[t] = Q[2q][t] + i Q[2q+1][t] (t < bt, zero to lt), by a
-// 32-point DFT across the lanes for each of the NPL samples a lane holds (lane l holds
-// t = NPL l + m), the twiddles W_lt^(m k1), and an NPL-point DFT in registers, so lane
-// l holds bin f = k1 + 32 fft_perm(k) in register k with k1 = bitrev5(l); then
-//     Qhat[2q][f] = (Z[f] + conj Z[lt - f]) / 2,   Qhat[2q+1][f] = (Z[f] - conj Z[lt - f]) / 2i
-// (the partner bin sits in lane bitrev5(32 - k1)), written column-major into T[k][f].
-// A pair whose two columns are empty in the block's masks is written as zeros without a
-// transform.  Then the CTA writes bin by bin the row's kq values as BF16 hi and lo parts.
+// Items (row, half): the CTA transforms the impact pairs of one half of a row (two CTAs
+// per SM).  Warp w takes the half's pairs q = w, w + 8, ...: the two real columns as one
+// complex sequence z[t] = Q[2q][t] + i Q[2q+1][t] (t < bt, zero to lt), N = lt = 32 NPL:
+//   pass 1  lane l holds z[l + 32 n1], n1 < NPL: an NPL-point DFT in registers, the
+//           twiddles W_N^(l f1);
+//   transpose through the pair's own columns of T (S[f1][n2 ^ f1]);
+//   pass 2  lanes 2 d + e (d = f1 < NPL) hold the 16 samples n2 = 2 a + e of the 32-point
+//           DFT over n2: a 16-point DFT in registers, the twiddles W_32^(e g), and one
+//           radix-2 step across the lane pair, so that lane 2 d + e holds bin
+//           f = d + NPL (g + 16 e) in register k (g = bitrev16(k));
+// then Z[f] (f <= N/2) and Z[N - f] land in the pair's four columns and one pass over the
+// bins forms
+//     Qhat[2q][f] = (Z[f] + conj Z[N - f]) / 2,   Qhat[2q+1][f] = (Z[f] - conj Z[N - f]) / 2i
+// in place, T[k][f] with k = 4 q + (Re 2q, Re 2q+1, Im 2q, Im 2q+1).  A pair whose two
+// columns are empty in the block's masks is written as zeros without a transform.  Then
+// the CTA writes bin by bin the half's kq/2 values as BF16 hi and lo parts.
+__device__ __forceinline__ int dx_tcol(int k, int ST) { return k * ST + ((k >> 5) & 3); }
+
+template <int N, bool HZ>
+__device__ __forceinline__ void dx_fft_fwd(float2 (&v)[N]) {
+    if constexpr ((N & (N - 1)) == 0) fft_reg_dif_c<N, false, HZ>(v);
+    else fft_reg_mixed3<N, false>(v);
+}
+
 template <int G>
-__global__ void __launch_bounds__(DX_FWD_THREADS, 1)
+__global__ void __launch_bounds__(DX_FWD_THREADS, 2)
     k_dx_fwd(const float *__restrict__ qeff, const uint64_t *__restrict__ colmask, const int32_t *__restrict__ rows,
              const int32_t *__restrict__ rowstart, const int32_t *__restrict__ meta, const float2 *__restrict__ tw,
              DxConst c, int slot_base, int qbase, int row0, int zero_straddling, uint16_t *__restrict__ qhi,
@@ -312,33 +334,36 @@ __global__ void __launch_bounds__(DX_FWD_THREADS, 1)
     constexpr int LT = 64 * G;
     constexpr int NPL = LT / 32;
     constexpr int NW = DX_FWD_THREADS / 32;
-    extern __shared__ float T[];   // [kq][ST]
+    static_assert(NPL <= 16, "pass 2 holds 16 samples per lane");
+    extern __shared__ float T[];   // [kq / 2] columns of ST bins, column k at dx_tcol(k)
     const int ST = dx_tstride(c.nbins);
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int cnt = meta[0], nrows = meta[1];
     if (zero_straddling) dx_zero_straddling(rowstart, cnt, c.nbins, ybuf);
     const int nloc = min(c.rows_cap, nrows - row0);
     const float2 *wlt = tw + TW_LT;
-    const float2 *w32 = tw + TW_32;
-    const int k1 = bitrev<32>(lane);
-    const int src = k1 == 0 ? 0 : bitrev<32>(32 - k1);
-    const int npq = c.kq >> 2;
-    for (int rl = blockIdx.x; rl < nloc; rl += gridDim.x) {
+    const int kh = c.kq >> 1, nph = kh >> 2;
+    const int d = lane >> 1, e = lane & 1;
+    const bool hz = 2 * c.bt <= LT;
+    for (int item = blockIdx.x; item < 2 * nloc; item += gridDim.x) {
+        const int rl = item >> 1, hh = item & 1;
         const int rec = rows[row0 + rl];
         const int s = rec >> 6, p = rec & 63;
         const uint64_t *mk = colmask + (size_t)(slot_base + s) * c.nch;
         const float *qs = qeff + (size_t)(slot_base + s - qbase) * c.nch * c.bp2 * c.bt + (size_t)p * c.bt;
-        for (int q = warp; q < npq; q += NW) {
+        for (int ql = warp; ql < nph; ql += NW) {
+            const int q = hh * nph + ql;
             const int ja = 2 * q, jb = 2 * q + 1;
             const bool nza = (mk[ja] >> p) & 1ull;
             const bool nzb = (mk[jb] >> p) & 1ull;
-            float *Tq = T + (size_t)(4 * q) * ST;
+            float *T0 = T + dx_tcol(4 * ql, ST);   // the pair's four columns, contiguous
+            float *T1 = T0 + ST, *T2 = T0 + 2 * ST, *T3 = T0 + 3 * ST;
             if (!(nza || nzb)) {
                 for (int f = lane; f < c.nbins; f += 32) {
-                    Tq[f] = 0.f;
-                    Tq[ST + f] = 0.f;
-                    Tq[2 * ST + f] = 0.f;
-                    Tq[3 * ST + f] = 0.f;
+                    T0[f] = 0.f;
+                    T1[f] = 0.f;
+                    T2[f] = 0.f;
+                    T3[f] = 0.f;
                 }
                 continue;
             }
@@ -346,56 +371,81 @@ __global__ void __launch_bounds__(DX_FWD_THREADS, 1)
             const float *cb = qs + (size_t)jb * c.bp2 * c.bt;
             float2 v[NPL];
 #pragma unroll
-            for (int e = 0; e < NPL / 4; ++e) {
-                const int t0 = NPL * lane + 4 * e;
-                float4 a = make_float4(0.f, 0.f, 0.f, 0.f), b = a;
-                if (t0 < c.bt) {
-                    if (nza) a = __ldg(reinterpret_cast<const float4 *>(ca + t0));
-                    if (nzb) b = __ldg(reinterpret_cast<const float4 *>(cb + t0));
-                }
-                v[4 * e + 0] = make_float2(a.x, b.x);
-                v[4 * e + 1] = make_float2(a.y, b.y);
-                v[4 * e + 2] = make_float2(a.z, b.z);
-                v[4 * e + 3] = make_float2(a.w, b.w);
+            for (int n1 = 0; n1 < NPL; ++n1) {
+                const int t = lane + 32 * n1;
+                const bool in = t < c.bt;
+                v[n1] = make_float2(nza && in ? __ldg(ca + t) : 0.f, nzb && in ? __ldg(cb + t) : 0.f);
             }
-#pragma unroll
-            for (int m = 0; m < NPL; ++m) v[m] = fft32_lanes<false>(v[m], w32, lane);
-#pragma unroll
-            for (int m = 1; m < NPL; ++m) v[m] = cmul(v[m], __ldg(wlt + (m * k1) % LT));
-            fft_reg_any<NPL, false>(v);
+            if (hz) dx_fft_fwd<NPL, true>(v);
+            else dx_fft_fwd<NPL, false>(v);
+            // the pair's region starts at an odd float where the column skew is odd: the
+            // scratch (NPL x 32 complex, 8-byte aligned) starts one float later there
+            float2 *S = reinterpret_cast<float2 *>(T0 + (dx_tcol(4 * ql, ST) & 1));
+            __syncwarp();
 #pragma unroll
             for (int k = 0; k < NPL; ++k) {
-                const int P = fft_perm<NPL>(k);
-                const int f = k1 + 32 * P;
-                // partner Z[lt - f]: lane src, register with perm NPL - 1 - P (k1 > 0) or
-                // (NPL - P) mod NPL (k1 = 0)
-                const int ka = dx_perm_inv<NPL>(NPL - 1 - P);
-                const int kb = dx_perm_inv<NPL>((NPL - P) % NPL);
-                float2 za, zb;
-                za.x = __shfl_sync(0xffffffffu, v[ka].x, src);
-                za.y = __shfl_sync(0xffffffffu, v[ka].y, src);
-                zb.x = __shfl_sync(0xffffffffu, v[kb].x, src);
-                zb.y = __shfl_sync(0xffffffffu, v[kb].y, src);
-                const float2 zc = k1 == 0 ? zb : za;
-                const float2 z = v[k];
-                if (f < c.nbins) {
-                    Tq[f] = 0.5f * (z.x + zc.x);               // Re Qhat[2q]
-                    Tq[2 * ST + f] = 0.5f * (z.y - zc.y);      // Im Qhat[2q]
-                    Tq[ST + f] = 0.5f * (z.y + zc.y);          // Re Qhat[2q + 1]
-                    Tq[3 * ST + f] = 0.5f * (zc.x - z.x);      // Im Qhat[2q + 1]
+                const int f1 = fft_perm<NPL>(k);
+                const float2 x = f1 ? cmul(v[k], __ldg(wlt + (lane * f1) % LT)) : v[k];
+                S[f1 * 32 + (lane ^ f1)] = x;
+            }
+            __syncwarp();
+            float2 w[16];
+#pragma unroll
+            for (int a = 0; a < 16; ++a)
+                w[a] = d < NPL ? S[d * 32 + ((2 * a + e) ^ d)] : make_float2(0.f, 0.f);
+            __syncwarp();
+            fft_reg_dif_c<16, false>(w);   // w[k] = E_e[bitrev16(k)]
+#pragma unroll
+            for (int k = 1; k < 16; ++k) {
+                const int g = bitrev<16>(k);
+                if (e) w[k] = cmul(w[k], make_float2(w32c(g), w32s(g)));
+            }
+#pragma unroll
+            for (int k = 0; k < 16; ++k) {
+                float2 o;
+                o.x = __shfl_xor_sync(0xffffffffu, w[k].x, 1);
+                o.y = __shfl_xor_sync(0xffffffffu, w[k].y, 1);
+                w[k] = e ? csub(o, w[k]) : cadd(w[k], o);
+            }
+            if (d < NPL) {
+#pragma unroll
+                for (int k = 0; k < 16; ++k) {
+                    const int f = d + NPL * (bitrev<16>(k) + 16 * e);
+                    if (2 * f <= LT) {
+                        T0[f] = w[k].x;
+                        T1[f] = w[k].y;
+                    } else {
+                        T2[LT - f] = w[k].x;
+                        T3[LT - f] = w[k].y;
+                    }
                 }
+            }
+            __syncwarp();
+            for (int f = lane; f < c.nbins; f += 32) {
+                const float zr = T0[f], zi = T1[f];
+                const bool self = f == 0 || 2 * f == LT;
+                const float cr = self ? zr : T2[f], ci = self ? zi : T3[f];
+                T0[f] = 0.5f * (zr + cr);   // Re Qhat[2q]
+                T1[f] = 0.5f * (zi + ci);   // Re Qhat[2q + 1]
+                T2[f] = 0.5f * (zi - ci);   // Im Qhat[2q]
+                T3[f] = 0.5f * (cr - zr);   // Im Qhat[2q + 1]
             }
         }
         __syncthreads();
-        // bin by bin: lane pairs k = 2 lane + 64 i, BF16 hi and lo parts packed in pairs
+        // bin by bin: lane k4 writes k = 4 k4 .. 4 k4 + 3 of the half, BF16 hi and lo parts
         for (int f = warp; f < c.nbins; f += NW) {
-            const size_t o = ((size_t)f * c.rows_cap + rl) * c.kq;
-            for (int k = 2 * lane; k < c.kq; k += 64) {
-                const float x0 = T[(size_t)k * ST + f], x1 = T[(size_t)(k + 1) * ST + f];
-                const uint32_t h0 = dx_bf16_bits(x0), h1 = dx_bf16_bits(x1);
-                const uint32_t l0 = dx_bf16_bits(x0 - dx_bf16_value(h0)), l1 = dx_bf16_bits(x1 - dx_bf16_value(h1));
-                *reinterpret_cast<uint32_t *>(qhi + o + k) = h0 | (h1 << 16);
-                *reinterpret_cast<uint32_t *>(qlo + o + k) = l0 | (l1 << 16);
+            const size_t o = ((size_t)f * c.rows_cap + rl) * c.kq + (size_t)hh * kh;
+            for (int k4 = lane; k4 < (kh >> 2); k4 += 32) {
+                const float *tc = T + dx_tcol(4 * k4, ST) + f;
+                uint32_t hb[4], lb[4];
+#pragma unroll
+                for (int i = 0; i < 4; ++i) {
+                    const float x = tc[i * ST];
+                    hb[i] = dx_bf16_bits(x);
+                    lb[i] = dx_bf16_bits(x - dx_bf16_value(hb[i]));
+                }
+                *reinterpret_cast<uint2 *>(qhi + o + 4 * k4) = make_uint2(hb[0] | (hb[1] << 16), hb[2] | (hb[3] << 16));
+                *reinterpret_cast<uint2 *>(qlo + o + 4 * k4) = make_uint2(lb[0] | (lb[1] << 16), lb[2] | (lb[3] << 16));
             }
         }
         __syncthreads();
@@ -434,14 +484,14 @@ __device__ __forceinline__ void dx_commit(uint32_t bar) {
 __device__ __forceinline__ void dx_arrive(uint32_t bar) {
     asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
 }
-__device__ __forceinline__ void dx_epi_sync() { asm volatile("barrier.sync 1, 128;" ::: "memory"); }
-// OR of a flag over the 128 epilogue threads (named barrier 1 with a reduction)
+__device__ __forceinline__ void dx_epi_sync() { asm volatile("barrier.sync 1, 256;" ::: "memory"); }
+// OR of a flag over the 256 epilogue threads (named barrier 1 with a reduction)
 __device__ __forceinline__ int dx_epi_any(int flag) {
     uint32_t r;
     asm volatile(
         "{\n\t.reg .pred p, q;\n\t"
         "setp.ne.b32 p, %1, 0;\n\t"
-        "barrier.red.or.pred q, 1, 128, p;\n\t"
+        "barrier.red.or.pred q, 1, 256, p;\n\t"
         "selp.u32 %0, 1, 0, q;\n\t}"
         : "=r"(r)
         : "r"(flag)
@@ -452,11 +502,12 @@ __device__ __forceinline__ int dx_epi_any(int flag) {
 // Items (bin f, tile t) in bin-major order, strided over the persistent CTAs, so that the
 // CTAs running at one time share the bin's B operand in L2.  Warp 0 (one lane) issues
 // the copies of each item's K chunks into DX_STAGES stages; warp 1 (one lane) issues the
-// products into accumulator (item index & 1) of tensor memory and commits; warps 2..5
+// products into accumulator (item index & 1) of tensor memory and commits; warps 2..9
 // drain the accumulator into shared memory (row r = TMEM lane r), release it, and sum
-// each block's rows into Ihat[slot][f][P]:
-//     Ihat[P] = sum over the block's rows r (pixel p') of Z_r[K],  K = p' + R - (P - P0)
-// with P - P0 = (uy, ux) the block-local output pixel, rows in ascending order.
+// each block's rows into Ihat[slot][f][u]:
+//     Ihat[u] = sum over the block's rows r (pixel p') of Z_r[K],  K = p' + 2R - u
+// (u = (uy, ux) the block-local output pixel, tap index K per axis in [0, kp)), rows in
+// ascending order.
 __global__ void __launch_bounds__(DX_GEMM_THREADS, 1)
     k_dx_gemm(const __grid_constant__ CUtensorMap tmAh, const __grid_constant__ CUtensorMap tmAl,
               const __grid_constant__ CUtensorMap tmBh, const __grid_constant__ CUtensorMap tmBl,
@@ -468,10 +519,14 @@ __global__ void __launch_bounds__(DX_GEMM_THREADS, 1)
     unsigned char *gbase = dx_raw + (base - raw);
     const uint32_t SB = dx_stage_bytes(c.npad);
     const uint32_t BB = dx_b_bytes(c.npad);
-    const int SZ = 2 * c.ntap + 1;
+    const int SZ = dx_zstride(c.ntap);
     float *Zs = reinterpret_cast<float *>(gbase + DX_STAGES * SB);
-    int32_t *rowrec = reinterpret_cast<int32_t *>(Zs + DX_M * SZ);
-    const uint32_t bar0 = (smem_u32(rowrec + DX_M) + 7u) & ~7u;
+    float2 *yacc_all = reinterpret_cast<float2 *>(Zs + DX_M * SZ);      // [8][16 * 16] block outputs
+    int32_t *rowrec = reinterpret_cast<int32_t *>(yacc_all + 8 * LP * LP);   // [DX_M + 2]
+    int32_t *seg_slot = rowrec + DX_M + 2;                               // [DX_M]
+    int32_t *seg_base = seg_slot + DX_M;                                 // [DX_M]
+    int32_t *seg_cnt = seg_base + DX_M;                                  // [5]
+    const uint32_t bar0 = (smem_u32(seg_cnt + 5) + 7u) & ~7u;
     auto bar_full = [&](int st) { return bar0 + 8u * (uint32_t)st; };
     auto bar_empty = [&](int st) { return bar0 + 8u * (uint32_t)(DX_STAGES + st); };
     auto bar_accf = [&](int ab) { return bar0 + 8u * (uint32_t)(2 * DX_STAGES + ab); };
@@ -493,7 +548,7 @@ __global__ void __launch_bounds__(DX_GEMM_THREADS, 1)
         }
         for (int ab = 0; ab < 2; ++ab) {
             mbar_init(bar_accf(ab), 1);
-            mbar_init(bar_acce(ab), 4);
+            mbar_init(bar_acce(ab), 8);
         }
         mbar_init(bar_done, 1);
         *abort_flag = 0;
@@ -593,20 +648,40 @@ __global__ void __launch_bounds__(DX_GEMM_THREADS, 1)
             (void)mbar_wait(bar_done, 0);
         }
     } else {
-        // ------------------------------------------------ epilogue (warps 2..5)
+        // ------------------------------------------------ epilogue (warps 2..9)
+        // warp w drains lane quarter w & 3 of the accumulator, columns half (w - 2) >> 2;
+        // the first four warps list the tile's block segments (consecutive rows of one
+        // slot: slot, first row, row count); then warp e takes segments e, e + 8, ... and
+        // adds its rows in ascending order into the block's 16 x 16 output in its own
+        // shared-memory accumulator: row r at pixel p' adds Z_r[K] at u = p' + 2R - K, one
+        // lane per tap (the taps of a row reach distinct outputs)
         const int te = tid - 64;
-        const int quarter = warp & 3;
+        const int ew = te >> 5;   // epilogue warp 0..7
+        const int quarter = warp & 3, half = (warp - 2) >> 2;
         const int R2 = 2 * c.R;
+        const int ncc = (2 * c.ntap + 31) / 32, hcc = (ncc + 1) / 2;
+        float2 *yacc = yacc_all + ew * (LP * LP);
+        // this lane's taps n = lane + 32 j and their output offsets (2R - K per axis)
+        int tap_off[DX_TAPS_PER_LANE];
+#pragma unroll
+        for (int j = 0; j < DX_TAPS_PER_LANE; ++j) {
+            const int n = lane + 32 * j;
+            tap_off[j] = n < c.ntap ? (R2 - n / c.kp) * LP + (R2 - n % c.kp) : -1;
+        }
         int i = 0;
         for (int it = blockIdx.x; it < nitems; it += gridDim.x, ++i) {
             const int f = it / ntiles, t = it - f * ntiles;
             const int ab = i & 1;
             const int nv = min(DX_M, nloc - t * DX_M);
             const int t0g = row0 + t * DX_M;
-            rowrec[te] = te < nv ? rows[t0g + te] : 0;
+            if (te < DX_M) rowrec[te] = te < nv ? rows[t0g + te] : -1;
+            // the slots of the rows just before and after the tile (a block with rows
+            // there is split across tiles)
+            if (te == DX_M) rowrec[DX_M] = t0g > 0 ? (rows[t0g - 1] >> 6) : -1;
+            if (te == DX_M + 1) rowrec[DX_M + 1] = t0g + nv < nrows ? (rows[t0g + nv] >> 6) : -1;
             int bad = mbar_wait(bar_accf(ab), (uint32_t)((i >> 1) & 1)) ? 0 : 1;
             bad |= *abort_flag;
-            if (dx_epi_any(bad)) {   // the four epilogue warps leave together
+            if (dx_epi_any(bad)) {   // the eight epilogue warps leave together (and rowrec is complete)
                 if (te == 0) {
                     atomicOr(&status[0], TRED_ST_TIMEOUT);
                     *abort_flag = 1;
@@ -615,44 +690,75 @@ __global__ void __launch_bounds__(DX_GEMM_THREADS, 1)
             }
             tmem_fence_after();
             const int r = 32 * quarter + lane;
-            for (int cc = 0; cc < (2 * c.ntap + 31) / 32; ++cc) {
+            for (int cc = half * hcc; cc < min(ncc, (half + 1) * hcc); ++cc) {
                 float v[32];
                 tmem_ld32(tmem + ((uint32_t)(32 * quarter) << 16) + (uint32_t)(ab * 256 + 32 * cc), v);
 #pragma unroll
-                for (int e = 0; e < 32; ++e)
-                    if (32 * cc + e < 2 * c.ntap) Zs[r * SZ + 32 * cc + e] = v[e];
+                for (int e4 = 0; e4 < 8; ++e4)
+                    if (32 * cc + 4 * e4 < 2 * c.ntap)
+                        *reinterpret_cast<float4 *>(Zs + r * SZ + 32 * cc + 4 * e4) =
+                            make_float4(v[4 * e4], v[4 * e4 + 1], v[4 * e4 + 2], v[4 * e4 + 3]);
             }
             tmem_fence_before();
             __syncwarp();
             if (lane == 0) dx_arrive(bar_acce(ab));
+            // segment starts: ballots of the first four epilogue warps (rows 0..127)
+            unsigned sbal = 0u;
+            int start = 0, rec = -1;
+            if (te < DX_M) {
+                rec = rowrec[te];
+                start = te < nv && (te == 0 || (rowrec[te - 1] >> 6) != (rec >> 6));
+                sbal = __ballot_sync(0xffffffffu, start);
+                if (lane == 0) seg_cnt[te >> 5] = __popc(sbal);
+            }
             dx_epi_sync();
-            const int s_first = rowrec[0] >> 6, s_last = rowrec[nv - 1] >> 6;
-            for (int s = s_first; s <= s_last; ++s) {
-                const int rs = rowstart[s], re = rowstart[s + 1];
-                const int ra = max(rs - t0g, 0), rb = min(re - t0g, nv);
-                if (ra >= rb) continue;
-                const bool split = (rs >> 7) != ((re - 1) >> 7);
-                float2 *yb = ybuf + ((size_t)s * c.nbins + f) * (LP * LP);
-                for (int u = te; u < LP * LP; u += 128) {
-                    const int uy = u >> 4, ux = u & 15;
-                    float ar = 0.f, ai = 0.f;
-                    for (int rr = ra; rr < rb; ++rr) {
-                        const int pp = rowrec[rr] & 63;
-                        const int py = pp / c.bp, px = pp - py * c.bp;
-                        const int Ky = py + R2 - uy, Kx = px + R2 - ux;
-                        if ((unsigned)Ky < (unsigned)c.kp && (unsigned)Kx < (unsigned)c.kp) {
-                            const int n = Ky * c.kp + Kx;
-                            ar += Zs[rr * SZ + n];
-                            ai += Zs[rr * SZ + c.ntap + n];
-                        }
+            if (start) {
+                int si = -1;
+                for (int w = 0; w < (te >> 5); ++w) si += seg_cnt[w];
+                si += __popc(sbal & (0xffffffffu >> (31 - lane)));
+                seg_slot[si] = rec >> 6;
+                seg_base[si] = te;
+            }
+            if (te == 0) seg_cnt[4] = seg_cnt[0] + seg_cnt[1] + seg_cnt[2] + seg_cnt[3];
+            dx_epi_sync();
+            const int nseg = seg_cnt[4];
+            const int slot_before = rowrec[DX_M], slot_after = rowrec[DX_M + 1];
+            for (int si = ew; si < nseg; si += 8) {
+                const int sl = seg_slot[si], base = seg_base[si];
+                const int end = si + 1 < nseg ? seg_base[si + 1] : nv;
+#pragma unroll
+                for (int j = 0; j < (LP * LP) / 32; ++j) yacc[lane + 32 * j] = make_float2(0.f, 0.f);
+                __syncwarp();
+                for (int rr = base; rr < end; ++rr) {
+                    const int pp = rowrec[rr] & 63;
+                    const int pu = (pp >> c.bpl) * LP + (pp & (c.bp - 1));
+                    const float *zr = Zs + rr * SZ;
+#pragma unroll
+                    for (int j = 0; j < DX_TAPS_PER_LANE; ++j) {
+                        if (tap_off[j] < 0) continue;
+                        const int n = lane + 32 * j;
+                        float2 *y = yacc + pu + tap_off[j];
+                        float2 a = *y;
+                        a.x += zr[n];
+                        a.y += zr[c.ntap + n];
+                        *y = a;
                     }
+                    __syncwarp();
+                }
+                const bool split = (si == 0 && sl == slot_before) || (si == nseg - 1 && sl == slot_after);
+                float2 *yb = ybuf + ((size_t)sl * c.nbins + f) * (LP * LP);
+#pragma unroll
+                for (int j = 0; j < (LP * LP) / 32; ++j) {
+                    const int u = lane + 32 * j;
+                    const float2 a = yacc[u];
                     if (split) {
-                        atomicAdd(&yb[u].x, ar);
-                        atomicAdd(&yb[u].y, ai);
+                        atomicAdd(&yb[u].x, a.x);
+                        atomicAdd(&yb[u].y, a.y);
                     } else {
-                        yb[u] = make_float2(ar, ai);
+                        yb[u] = a;
                     }
                 }
+                __syncwarp();
             }
             dx_epi_sync();
         }
@@ -666,15 +772,15 @@ __global__ void __launch_bounds__(DX_GEMM_THREADS, 1)
 }
 
 // ---------------------------------------------------------------- inverse time DFT
-// Per block (persistent over the slots of the pass), 32 output pixels at a time: their
-// lt/2 + 1 bins staged in shared memory [f][32], then warp w inverts pixels a = w and
-// b = w + 16 of the group as one complex sequence Z[f] = Ihat_a[f] + i Ihat_b[f] (the
+// Per block (persistent over the slots of the pass, two CTAs per SM), 32 output pixels
+// at a time: their lt/2 + 1 bins staged in shared memory [f][32], then warp w inverts
+// pixels a = j and b = j + 16 of the group (j = w, w + 8) as one complex sequence Z[f] = Ihat_a[f] + i Ihat_b[f] (the
 // bins above lt/2 from the conjugate symmetry of real signals): an NPL-point inverse DFT
 // over the samples a lane holds (bins l + 32 m), the twiddles, a 32-point inverse DFT
 // across the lanes; lane l then holds t = NPL bitrev5(l) + fft_perm(k) in register k,
 // Re z[t] = I_a[t] and Im z[t] = I_b[t].  A slot with no rows is written as zeros.
 template <int G>
-__global__ void __launch_bounds__(DX_INV_THREADS, 1)
+__global__ void __launch_bounds__(DX_INV_THREADS, 2)
     k_dx_inv(const float2 *__restrict__ ybuf, const int32_t *__restrict__ rowstart, const int32_t *__restrict__ meta,
              const float2 *__restrict__ tw, DxConst c, int slot_base, float *__restrict__ out) {
     constexpr int LT = 64 * G;
@@ -702,44 +808,46 @@ __global__ void __launch_bounds__(DX_INV_THREADS, 1)
                 Ys[f * YS + ul] = yb[(size_t)f * (LP * LP) + 32 * ug + ul];
             }
             __syncthreads();
-            const int ua = warp, ub = warp + 16;
-            float2 v[NPL];
+            for (int j = warp; j < 16; j += DX_INV_THREADS / 32) {
+                const int ua = j, ub = j + 16;
+                float2 v[NPL];
 #pragma unroll
-            for (int m = 0; m < NPL; ++m) {
-                const int f = lane + 32 * m;
-                float2 A, B;
-                if (f < NB) {
-                    A = Ys[f * YS + ua];
-                    B = Ys[f * YS + ub];
-                } else {
-                    A = cconj(Ys[(LT - f) * YS + ua]);
-                    B = cconj(Ys[(LT - f) * YS + ub]);
+                for (int m = 0; m < NPL; ++m) {
+                    const int f = lane + 32 * m;
+                    float2 A, B;
+                    if (f < NB) {
+                        A = Ys[f * YS + ua];
+                        B = Ys[f * YS + ub];
+                    } else {
+                        A = cconj(Ys[(LT - f) * YS + ua]);
+                        B = cconj(Ys[(LT - f) * YS + ub]);
+                    }
+                    v[m] = make_float2(A.x - B.y, A.y + B.x);
                 }
-                v[m] = make_float2(A.x - B.y, A.y + B.x);
-            }
-            fft_reg_any<NPL, true>(v);   // v[k] = u[fft_perm(k)]
+                fft_reg_any<NPL, true>(v);   // v[k] = u[fft_perm(k)]
 #pragma unroll
-            for (int k = 0; k < NPL; ++k) {
-                const int aa = fft_perm<NPL>(k);
-                float2 w = __ldg(wlt + (lane * aa) % LT);
-                w.y = -w.y;
-                v[k] = fft32_lanes<true>(cmul(v[k], w), w32, lane);
-            }
-            float ra[NPL], rb[NPL];
+                for (int k = 0; k < NPL; ++k) {
+                    const int aa = fft_perm<NPL>(k);
+                    float2 w = __ldg(wlt + (lane * aa) % LT);
+                    w.y = -w.y;
+                    v[k] = fft32_lanes<true>(cmul(v[k], w), w32, lane);
+                }
+                float ra[NPL], rb[NPL];
 #pragma unroll
-            for (int k = 0; k < NPL; ++k) {
-                const int t = fft_perm<NPL>(k);
-                ra[t] = v[k].x;
-                rb[t] = v[k].y;
-            }
-            float *oa = ob + (size_t)(32 * ug + ua) * LT + NPL * b5;
-            float *obb = ob + (size_t)(32 * ug + ub) * LT + NPL * b5;
+                for (int k = 0; k < NPL; ++k) {
+                    const int t = fft_perm<NPL>(k);
+                    ra[t] = v[k].x;
+                    rb[t] = v[k].y;
+                }
+                float *oa = ob + (size_t)(32 * ug + ua) * LT + NPL * b5;
+                float *obb = ob + (size_t)(32 * ug + ub) * LT + NPL * b5;
 #pragma unroll
-            for (int k = 0; k < NPL; k += 4) {
-                *reinterpret_cast<float4 *>(oa + k) = make_float4(ra[k], ra[k + 1], ra[k + 2], ra[k + 3]);
-                *reinterpret_cast<float4 *>(obb + k) = make_float4(rb[k], rb[k + 1], rb[k + 2], rb[k + 3]);
+                for (int k = 0; k < NPL; k += 4) {
+                    *reinterpret_cast<float4 *>(oa + k) = make_float4(ra[k], ra[k + 1], ra[k + 2], ra[k + 3]);
+                    *reinterpret_cast<float4 *>(obb + k) = make_float4(rb[k], rb[k + 1], rb[k + 2], rb[k + 3]);
+                }
             }
-        }
+            }
         __syncthreads();
     }
 }
@@ -773,6 +881,7 @@ static int run_direct(tred_handle *h, const DxConst &c, const int32_t *n_blocks_
     static size_t set_gemm = 0;
     if (fwd_smem > set_fwd) {
         cudaFuncSetAttribute(k_dx_fwd<G>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fwd_smem);
+        cudaFuncSetAttribute(k_dx_fwd<G>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
         set_fwd = fwd_smem;
     }
     if (gemm_smem > set_gemm) {
@@ -781,6 +890,7 @@ static int run_direct(tred_handle *h, const DxConst &c, const int32_t *n_blocks_
     }
     if (inv_smem > set_inv) {
         cudaFuncSetAttribute(k_dx_inv<G>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)inv_smem);
+        cudaFuncSetAttribute(k_dx_inv<G>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
         set_inv = inv_smem;
     }
     CUtensorMap tah, tal, tbh, tbl;
@@ -801,14 +911,14 @@ static int run_direct(tred_handle *h, const DxConst &c, const int32_t *n_blocks_
         const int nrc = (int)((max_rows + c.rows_cap - 1) / c.rows_cap);
         for (int k = 0; k < nrc; ++k) {
             const int row0 = k * c.rows_cap;
-            k_dx_fwd<G><<<sms, DX_FWD_THREADS, fwd_smem, s>>>(qeff, h->colmask, h->dx_rows, h->dx_rowstart, h->dx_meta,
+            k_dx_fwd<G><<<2 * sms, DX_FWD_THREADS, fwd_smem, s>>>(qeff, h->colmask, h->dx_rows, h->dx_rowstart, h->dx_meta,
                                                              h->tw, c, base, qbase, row0, k == 0 ? 1 : 0, h->dx_qhi,
                                                              h->dx_qlo, h->dx_y);
             k_dx_gemm<<<sms, DX_GEMM_THREADS, gemm_smem, s>>>(tah, tal, tbh, tbl, h->dx_rows, h->dx_rowstart,
                                                               h->dx_meta, c, row0, h->dx_y, h->status);
             h->launches += 2;
         }
-        k_dx_inv<G><<<sms, DX_INV_THREADS, inv_smem, s>>>(h->dx_y, h->dx_rowstart, h->dx_meta, h->tw, c, base, out);
+        k_dx_inv<G><<<2 * sms, DX_INV_THREADS, inv_smem, s>>>(h->dx_y, h->dx_rowstart, h->dx_meta, h->tw, c, base, out);
         h->launches += 1;
     }
     return check_cuda(h, cudaGetLastError(), "direct-form launch");

@@ -133,7 +133,8 @@ static int validate(const tred_geometry *g, const tred_params *p, char *msg, siz
     if (p->conv_mode < 0 || p->conv_mode > 4) return bad("conv_mode must be 0, 1, 2, 3 or 4");
     if (p->conv_mode >= 1 && p->conv_mode <= 3 && (g->lt != 512 || g->bp != 8))
         return bad("the tensor-core convolution (conv_mode 1, 2, 3) needs lt = 512 and bp = 8");
-    if (p->conv_mode == 4 && ((g->lt != 384 && g->lt != 512) || g->kp > 9 || !dx_shape_ok(2 * g->n_sub * g->n_sub, g->lt)))
+    if (p->conv_mode == 4 && ((g->lt != 384 && g->lt != 512) || g->kp > 9 || g->n_sub > 10 ||
+                             !dx_shape_ok(2 * g->n_sub * g->n_sub, g->lt)))
         return bad("the direct spatial form (conv_mode 4) needs lt = 384 or 512, kp <= 9 and n_sub <= 10");
     if (p->mpcp != 0 && p->mpcp != 1) return bad("mpcp must be 0 or 1");
     if (p->effq_skip_empty != 0 && p->effq_skip_empty != 1) return bad("effq_skip_empty must be 0 or 1");
