@@ -83,6 +83,12 @@ static size_t dx_gemm_smem(int npad, int ntap) {
            sizeof(float2) * 8 * LP * LP + sizeof(int32_t) * (3 * DX_M + 2 + 5) + 128;
 }
 
+// two binary32 values to their nearest BF16 (ties to even), lo in the low 16 bits
+__device__ __forceinline__ uint32_t dx_bf16x2(float lo, float hi) {
+    uint32_t d;
+    asm("cvt.rn.bf16x2.f32 %0, %1, %2;" : "=r"(d) : "f"(hi), "f"(lo));
+    return d;
+}
 // nearest BF16 (ties to even) of a finite binary32 value, as its 16 bits, and its value
 __host__ __device__ __forceinline__ uint32_t dx_bf16_bits(float x) {
 #ifdef __CUDA_ARCH__
@@ -311,12 +317,10 @@ __device__ __forceinline__ void dx_zero_straddling(const int32_t *__restrict__ r
 //           DFT over n2: a 16-point DFT in registers, the twiddles W_32^(e g), and one
 //           radix-2 step across the lane pair, so that lane 2 d + e holds bin
 //           f = d + NPL (g + 16 e) in register k (g = bitrev16(k));
-// then Z[f] (f <= N/2) and Z[N - f] land in the pair's four columns and one pass over the
-// bins forms
-//     Qhat[2q][f] = (Z[f] + conj Z[N - f]) / 2,   Qhat[2q+1][f] = (Z[f] - conj Z[N - f]) / 2i
-// in place, T[k][f] with k = 4 q + (Re 2q, Re 2q+1, Im 2q, Im 2q+1).  A pair whose two
+// then Z[f] (f <= N/2) and Z[N - f] land in the pair's four columns.  A pair whose two
 // columns are empty in the block's masks is written as zeros without a transform.  Then
-// the CTA writes bin by bin the half's kq/2 values as BF16 hi and lo parts.
+// the CTA writes bin by bin, one lane per pair, the Hermitian split of its two columns
+// as k = 4 q + (Re 2q, Re 2q+1, Im 2q, Im 2q+1) in BF16 hi and lo parts.
 __device__ __forceinline__ int dx_tcol(int k, int ST) { return k * ST + ((k >> 5) & 3); }
 
 template <int N, bool HZ>
@@ -420,32 +424,27 @@ __global__ void __launch_bounds__(DX_FWD_THREADS, 2)
                     }
                 }
             }
-            __syncwarp();
-            for (int f = lane; f < c.nbins; f += 32) {
-                const float zr = T0[f], zi = T1[f];
-                const bool self = f == 0 || 2 * f == LT;
-                const float cr = self ? zr : T2[f], ci = self ? zi : T3[f];
-                T0[f] = 0.5f * (zr + cr);   // Re Qhat[2q]
-                T1[f] = 0.5f * (zi + ci);   // Re Qhat[2q + 1]
-                T2[f] = 0.5f * (zi - ci);   // Im Qhat[2q]
-                T3[f] = 0.5f * (cr - zr);   // Im Qhat[2q + 1]
-            }
         }
         __syncthreads();
-        // bin by bin: lane k4 writes k = 4 k4 .. 4 k4 + 3 of the half, BF16 hi and lo parts
+        // bin by bin, lane = pair: the Hermitian split of the pair's Z[f] and Z[N - f],
+        //     Qhat[2q][f] = (Z[f] + conj Z[N - f]) / 2,   Qhat[2q+1][f] = (Z[f] - conj Z[N - f]) / 2i,
+        // then its four values k = 4 q .. 4 q + 3 as BF16 hi and lo parts (8 bytes each)
         for (int f = warp; f < c.nbins; f += NW) {
             const size_t o = ((size_t)f * c.rows_cap + rl) * c.kq + (size_t)hh * kh;
-            for (int k4 = lane; k4 < (kh >> 2); k4 += 32) {
-                const float *tc = T + dx_tcol(4 * k4, ST) + f;
-                uint32_t hb[4], lb[4];
-#pragma unroll
-                for (int i = 0; i < 4; ++i) {
-                    const float x = tc[i * ST];
-                    hb[i] = dx_bf16_bits(x);
-                    lb[i] = dx_bf16_bits(x - dx_bf16_value(hb[i]));
-                }
-                *reinterpret_cast<uint2 *>(qhi + o + 4 * k4) = make_uint2(hb[0] | (hb[1] << 16), hb[2] | (hb[3] << 16));
-                *reinterpret_cast<uint2 *>(qlo + o + 4 * k4) = make_uint2(lb[0] | (lb[1] << 16), lb[2] | (lb[3] << 16));
+            const bool self = f == 0 || 2 * f == LT;
+            for (int ql = lane; ql < nph; ql += 32) {
+                const float *tq = T + dx_tcol(4 * ql, ST) + f;
+                const float zr = tq[0], zi = tq[ST];
+                const float cr = self ? zr : tq[2 * ST], ci = self ? zi : tq[3 * ST];
+                const float x0 = 0.5f * (zr + cr);   // Re Qhat[2q]
+                const float x1 = 0.5f * (zi + ci);   // Re Qhat[2q + 1]
+                const float x2 = 0.5f * (zi - ci);   // Im Qhat[2q]
+                const float x3 = 0.5f * (cr - zr);   // Im Qhat[2q + 1]
+                const uint32_t h01 = dx_bf16x2(x0, x1), h23 = dx_bf16x2(x2, x3);
+                const uint32_t l01 = dx_bf16x2(x0 - __uint_as_float(h01 << 16), x1 - __uint_as_float(h01 & 0xFFFF0000u));
+                const uint32_t l23 = dx_bf16x2(x2 - __uint_as_float(h23 << 16), x3 - __uint_as_float(h23 & 0xFFFF0000u));
+                *reinterpret_cast<uint2 *>(qhi + o + 4 * ql) = make_uint2(h01, h23);
+                *reinterpret_cast<uint2 *>(qlo + o + 4 * ql) = make_uint2(l01, l23);
             }
         }
         __syncthreads();
@@ -772,13 +771,21 @@ __global__ void __launch_bounds__(DX_GEMM_THREADS, 1)
 }
 
 // ---------------------------------------------------------------- inverse time DFT
-// Per block (persistent over the slots of the pass, two CTAs per SM), 32 output pixels
-// at a time: their lt/2 + 1 bins staged in shared memory [f][32], then warp w inverts
-// pixels a = j and b = j + 16 of the group (j = w, w + 8) as one complex sequence Z[f] = Ihat_a[f] + i Ihat_b[f] (the
-// bins above lt/2 from the conjugate symmetry of real signals): an NPL-point inverse DFT
-// over the samples a lane holds (bins l + 32 m), the twiddles, a 32-point inverse DFT
-// across the lanes; lane l then holds t = NPL bitrev5(l) + fft_perm(k) in register k,
-// Re z[t] = I_a[t] and Im z[t] = I_b[t].  A slot with no rows is written as zeros.
+// Per block (persistent over the slots of the pass, two CTAs per SM), 16 output pixels at
+// a time (8 columns of two adjacent rows): their lt/2 + 1 bins staged in shared memory
+// pixel-major [u][f] (the next group's loads in flight in registers), then warp w inverts
+// the vertical neighbours a = (uy, ux0 + w) and b = (uy + 1, ux0 + w) (of similar size,
+// so that the rounding of one half of the packed sequence stays small against the other) as one complex sequence Z[f] = Ihat_a[f] + i Ihat_b[f] (the bins above lt/2 from
+// the conjugate symmetry of real signals), N = lt = 32 NPL:
+//   pass 1  lane l holds Z[l + 32 m], m < NPL: an NPL-point inverse DFT in registers, the
+//           twiddles W_N^-(l t1);
+//   transpose through the warp's scratch (S[t1][n2 ^ t1]);
+//   pass 2  lanes 2 d + e (d = t1 < NPL) hold the 16 samples n2 = 2 a + e: a 16-point
+//           inverse DFT in registers, the twiddles W_32^-(e g), one radix-2 step across
+//           the lane pair: lane 2 d + e holds t = d + NPL (g + 16 e) in register k
+//           (g = bitrev16(k)), Re z[t] = I_a[t] and Im z[t] = I_b[t].
+// A slot with no rows is written as zeros.
+constexpr int DX_INV_U = 16;   // output pixels per staged group
 template <int G>
 __global__ void __launch_bounds__(DX_INV_THREADS, 2)
     k_dx_inv(const float2 *__restrict__ ybuf, const int32_t *__restrict__ rowstart, const int32_t *__restrict__ meta,
@@ -786,13 +793,17 @@ __global__ void __launch_bounds__(DX_INV_THREADS, 2)
     constexpr int LT = 64 * G;
     constexpr int NPL = LT / 32;
     constexpr int NB = LT / 2 + 1;
-    constexpr int YS = 33;   // staging row (float2)
-    extern __shared__ float2 Ys[];   // [NB][YS]
+    constexpr int NW = DX_INV_THREADS / 32;
+    constexpr int NLD = (NB * (DX_INV_U / 2) + DX_INV_THREADS - 1) / DX_INV_THREADS;   // 16-byte loads per thread
+    static_assert(NW * 2 == DX_INV_U, "one pixel pair per warp");
+    extern __shared__ float2 dxs[];
+    float2 *Ys = dxs;                                  // [DX_INV_U][NB]
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    float2 *S = dxs + DX_INV_U * NB + warp * (NPL * 32);   // per-warp transpose scratch
     const int cnt = meta[0];
     const float2 *wlt = tw + TW_LT;
-    const float2 *w32 = tw + TW_32;
-    const int b5 = bitrev<32>(lane);
+    const int d = lane >> 1, e = lane & 1;
+    constexpr int NG = (LP * LP) / DX_INV_U;
     for (int s = blockIdx.x; s < cnt; s += gridDim.x) {
         float *ob = out + (size_t)(slot_base + s) * (LP * LP) * LT;
         if (rowstart[s + 1] == rowstart[s]) {
@@ -800,54 +811,89 @@ __global__ void __launch_bounds__(DX_INV_THREADS, 2)
             for (int i = tid; i < (LP * LP) * LT / 4; i += DX_INV_THREADS) o4[i] = make_float4(0.f, 0.f, 0.f, 0.f);
             continue;
         }
-        const float2 *yb = ybuf + (size_t)s * NB * (LP * LP);
-        for (int ug = 0; ug < (LP * LP) / 32; ++ug) {
-            __syncthreads();   // the previous group's reads are done
-            for (int i = tid; i < NB * 32; i += DX_INV_THREADS) {
-                const int f = i >> 5, ul = i & 31;
-                Ys[f * YS + ul] = yb[(size_t)f * (LP * LP) + 32 * ug + ul];
+        const float4 *yb = reinterpret_cast<const float4 *>(ybuf + (size_t)s * NB * (LP * LP));
+        float4 pre[NLD];
+        auto load = [&](int ug) {
+#pragma unroll
+            for (int i = 0; i < NLD; ++i) {
+                const int idx = tid + i * DX_INV_THREADS;   // (bin, pixel pair)
+                const int f = idx / (DX_INV_U / 2), up = idx - f * (DX_INV_U / 2);
+                // group ug: rows 2 (ug >> 1) and 2 (ug >> 1) + 1, columns 8 (ug & 1) .. + 7
+                const int u = (2 * (ug >> 1) + (up >> 2)) * LP + 8 * (ug & 1) + 2 * (up & 3);
+                pre[i] = f < NB ? __ldg(yb + ((size_t)f * (LP * LP) + u) / 2) : make_float4(0.f, 0.f, 0.f, 0.f);
+            }
+        };
+        load(0);
+        for (int ug = 0; ug < NG; ++ug) {
+            __syncthreads();   // the previous group's reads of Ys are done
+#pragma unroll
+            for (int i = 0; i < NLD; ++i) {
+                const int idx = tid + i * DX_INV_THREADS;
+                const int f = idx / (DX_INV_U / 2), up = idx - f * (DX_INV_U / 2);
+                if (f < NB) {
+                    Ys[(2 * up) * NB + f] = make_float2(pre[i].x, pre[i].y);
+                    Ys[(2 * up + 1) * NB + f] = make_float2(pre[i].z, pre[i].w);
+                }
             }
             __syncthreads();
-            for (int j = warp; j < 16; j += DX_INV_THREADS / 32) {
-                const int ua = j, ub = j + 16;
-                float2 v[NPL];
+            if (ug + 1 < NG) load(ug + 1);
+            const float2 *ya = Ys + warp * NB, *ybb = Ys + (warp + NW) * NB;
+            float2 v[NPL];
 #pragma unroll
-                for (int m = 0; m < NPL; ++m) {
-                    const int f = lane + 32 * m;
-                    float2 A, B;
-                    if (f < NB) {
-                        A = Ys[f * YS + ua];
-                        B = Ys[f * YS + ub];
-                    } else {
-                        A = cconj(Ys[(LT - f) * YS + ua]);
-                        B = cconj(Ys[(LT - f) * YS + ub]);
-                    }
-                    v[m] = make_float2(A.x - B.y, A.y + B.x);
+            for (int m = 0; m < NPL; ++m) {
+                const int f = lane + 32 * m;
+                float2 A, B;
+                if (f < NB) {
+                    A = ya[f];
+                    B = ybb[f];
+                } else {
+                    A = cconj(ya[LT - f]);
+                    B = cconj(ybb[LT - f]);
                 }
-                fft_reg_any<NPL, true>(v);   // v[k] = u[fft_perm(k)]
+                v[m] = make_float2(A.x - B.y, A.y + B.x);
+            }
+            fft_reg_any<NPL, true>(v);   // v[k] = U[fft_perm(k)]
+            __syncwarp();
 #pragma unroll
-                for (int k = 0; k < NPL; ++k) {
-                    const int aa = fft_perm<NPL>(k);
-                    float2 w = __ldg(wlt + (lane * aa) % LT);
+            for (int k = 0; k < NPL; ++k) {
+                const int t1 = fft_perm<NPL>(k);
+                float2 x = v[k];
+                if (t1) {
+                    float2 w = __ldg(wlt + (lane * t1) % LT);
                     w.y = -w.y;
-                    v[k] = fft32_lanes<true>(cmul(v[k], w), w32, lane);
+                    x = cmul(x, w);
                 }
-                float ra[NPL], rb[NPL];
+                S[t1 * 32 + (lane ^ t1)] = x;
+            }
+            __syncwarp();
+            float2 w[16];
 #pragma unroll
-                for (int k = 0; k < NPL; ++k) {
-                    const int t = fft_perm<NPL>(k);
-                    ra[t] = v[k].x;
-                    rb[t] = v[k].y;
-                }
-                float *oa = ob + (size_t)(32 * ug + ua) * LT + NPL * b5;
-                float *obb = ob + (size_t)(32 * ug + ub) * LT + NPL * b5;
+            for (int a = 0; a < 16; ++a) w[a] = d < NPL ? S[d * 32 + ((2 * a + e) ^ d)] : make_float2(0.f, 0.f);
+            fft_reg_dif_c<16, true>(w);   // w[k] = E_e[bitrev16(k)]
 #pragma unroll
-                for (int k = 0; k < NPL; k += 4) {
-                    *reinterpret_cast<float4 *>(oa + k) = make_float4(ra[k], ra[k + 1], ra[k + 2], ra[k + 3]);
-                    *reinterpret_cast<float4 *>(obb + k) = make_float4(rb[k], rb[k + 1], rb[k + 2], rb[k + 3]);
+            for (int k = 1; k < 16; ++k) {
+                const int g = bitrev<16>(k);
+                if (e) w[k] = cmul(w[k], make_float2(w32c(g), -w32s(g)));
+            }
+#pragma unroll
+            for (int k = 0; k < 16; ++k) {
+                float2 o;
+                o.x = __shfl_xor_sync(0xffffffffu, w[k].x, 1);
+                o.y = __shfl_xor_sync(0xffffffffu, w[k].y, 1);
+                w[k] = e ? csub(o, w[k]) : cadd(w[k], o);
+            }
+            if (d < NPL) {
+                const int ua = (2 * (ug >> 1)) * LP + 8 * (ug & 1) + warp;
+                float *oa = ob + (size_t)ua * LT;
+                float *obb = ob + (size_t)(ua + LP) * LT;
+#pragma unroll
+                for (int k = 0; k < 16; ++k) {
+                    const int t = d + NPL * (bitrev<16>(k) + 16 * e);
+                    oa[t] = w[k].x;
+                    obb[t] = w[k].y;
                 }
             }
-            }
+        }
         __syncthreads();
     }
 }
@@ -875,7 +921,7 @@ static int run_direct(tred_handle *h, const DxConst &c, const int32_t *n_blocks_
                       int slot_base, int slot_count, int qbase, cudaStream_t s) {
     const size_t fwd_smem = dx_fwd_smem(c.kq, c.nbins);
     const size_t gemm_smem = dx_gemm_smem(c.npad, c.ntap);
-    const size_t inv_smem = sizeof(float2) * (size_t)(32 * G + 1) * 33;
+    const size_t inv_smem = sizeof(float2) * ((size_t)DX_INV_U * (32 * G + 1) + (size_t)(DX_INV_THREADS / 32) * 64 * G);
     // the largest dynamic shared memory asked for so far (shapes differ between handles)
     static size_t set_fwd = 0, set_inv = 0;
     static size_t set_gemm = 0;
