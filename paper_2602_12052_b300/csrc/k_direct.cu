@@ -11,14 +11,14 @@
 // response column (j, K).  For each bin, Z is a complex matrix product over the impacts:
 // rows = the block's pixels that hold charge (on a module plane about 10 of the 64),
 // columns = the kp^2 response taps.  Batched over every non-empty (block, pixel) row of
-// the pass, each bin is one GEMM with M = rows, K = 2 nch (real and imaginary parts of
-// the nch impacts), N = 2 kp^2 (real and imaginary parts of the taps), run as three
-// split-BF16 products (A_hi B_hi + A_hi B_lo + A_lo B_hi, FP32 accumulation in tensor
-// memory).  The real form of the complex product is laid out with the impacts in pairs,
-//     k = 4 q + c,  c = 0: Re Qhat[2q], 1: Re Qhat[2q + 1], 2: Im Qhat[2q], 3: Im Qhat[2q + 1]
-//     B[n][k]          (n < kp^2, Re Z of tap n):  Re R, Re R, -Im R, -Im R
-//     B[kp^2 + n][k]   (Im Z of tap n):            Im R, Im R,  Re R,  Re R
-// so that the forward kernel writes 64 consecutive k of one bin from 16 impact pairs.
+// the pass, each bin is one complex GEMM with M = rows, K = nch impacts, N = kp^2 taps,
+// run on the tensor cores as four real products per K step,
+//     Re Z += Re Q Re R,  Re Z -= Im Q Im R,  Im Z += Re Q Im R,  Im Z += Im Q Re R
+// (the minus by the instruction's negate-B bit), each as three split-BF16 products
+// (A_hi B_hi + A_hi B_lo + A_lo B_hi, FP32 accumulation in tensor memory).  The K axis is
+// laid out in groups of 16 impacts, k = 32 g + 16 h + i for impact j = 16 g + i (h = 0:
+// real part, 1: imaginary part), in both operands (B holds Re R and Im R), so that one
+// 32-wide K chunk of A and of B serves all four products and B is stored once.
 //
 // Kernels of one pass over at most dx_blocks slots:
 //  k_dx_pixmask / k_dx_rows  non-empty pixels of each slot (from the effective charge's
@@ -27,9 +27,10 @@
 //                            per complex FFT in registers, split by Hermitian symmetry),
 //                            transposed in shared memory and written as BF16 hi and lo
 //                            parts [bin][row][k];
-//  k_dx_gemm                 per (bin, 128-row tile): TMA (64-byte swizzle) of the two
+//  k_dx_gemm                 per (bin, 128-row tile): TMA (128-byte swizzle) of the two
 //                            operands' parts, tcgen05.mma kind::f16 (M = 128, N = npad,
-//                            K = 16) into one of two tensor-memory accumulators, and an
+//                            K = 16) into one of two pairs of tensor-memory accumulators
+//                            (Re Z, Im Z), and an
 //                            epilogue that sums each block's rows into its 16 x 16 output
 //                            spectrum Ihat[slot][f][P] in a fixed row order;
 //  k_dx_inv                  per block, the inverse real DFT of the 256 output pixels
@@ -50,18 +51,19 @@
 namespace tred {
 
 constexpr int DX_M = 128;                // rows of one GEMM tile
-constexpr int DX_KC = 32;                // K chunk: 32 BF16 = one 64-byte row (64-byte swizzle)
-constexpr int DX_STAGES = 3;             // operand stages
+constexpr int DX_KC = 64;                // K chunk: 64 BF16 = one 128-byte row (128-byte swizzle), two groups
+constexpr int DX_STAGES = 2;             // operand stages
 constexpr int DX_ROWS_MAX = 131072;      // rows per forward + GEMM launch pair
 constexpr int DX_BLOCKS_MAX = 8192;      // slots per pass
 constexpr int DX_FWD_THREADS = 256;
 constexpr int DX_INV_THREADS = 256;
 constexpr int DX_GEMM_THREADS = 320;     // warp 0 copies, warp 1 products, warps 2..9 epilogue
-constexpr uint32_t DX_A_BYTES = DX_M * DX_KC * 2;   // 8 KB per part
+constexpr uint32_t DX_A_BYTES = DX_M * DX_KC * 2;   // 16 KB per part
 constexpr int DX_TAPS_PER_LANE = 3;   // kp <= 9: at most 81 taps
+constexpr int DX_YS = 25;            // output accumulator row stride (float2): 9 mod 16
 
 struct DxConst {
-    int nch, kq, ntap, npad, kp, R, bp, bpl, bp2, bt, lt, nbins, rows_cap;
+    int nch, kq, ntap, npad, imoff, jm, kp, R, bp, bpl, bp2, bt, lt, nbins, rows_cap;
 };
 
 __host__ __device__ constexpr int dx_round16(int x) { return (x + 15) & ~15; }
@@ -70,17 +72,19 @@ __host__ __device__ constexpr uint32_t dx_stage_bytes(int npad) {
     return (2 * DX_A_BYTES + 2 * dx_b_bytes(npad) + 1023u) & ~1023u;
 }
 // column stride of the forward kernel's transposition buffer: at least nbins + 3 (room
-// for the columns' skew of up to 3) and 1 mod 8, so that the lanes reading columns
-// 4 k4 .. 4 k4 + 3 of one bin (k4 = lane) hit distinct banks; the buffer holds half a
-// row's kq columns
+// for the columns' skew of up to 3) and 1 mod 8, so that lanes reading the columns of
+// distinct pairs of one bin hit distinct banks; the buffer holds the larger half of a
+// row's impacts, jm = 4 ceil(nch / 8), two columns per impact
 __host__ __device__ constexpr int dx_tstride(int nbins) { return ((nbins + 10) & ~7) + 1; }
-size_t dx_fwd_smem(int kq, int nbins) { return sizeof(float) * (size_t)(kq / 2) * dx_tstride(nbins); }
-// epilogue staging row (floats): a multiple of 4 (16-byte stores) with an odd number of
-// 16-byte chunks (the 32 lanes' rows start in distinct bank groups)
-__host__ __device__ constexpr int dx_zstride(int ntap) { return ((2 * ntap + 3) / 4 | 1) * 4; }
+__host__ __device__ constexpr int dx_half_split(int nch) { return 4 * ((nch + 7) / 8); }
+size_t dx_fwd_smem(int nch, int nbins) { return sizeof(float) * (size_t)(2 * dx_half_split(nch)) * dx_tstride(nbins); }
+// epilogue staging row (floats): Re Z of the taps at 0, Im Z at imoff = ntap rounded up to
+// 4; a multiple of 4 (16-byte stores) with an odd number of 16-byte chunks (the 32 lanes'
+// rows start in distinct bank groups)
+__host__ __device__ constexpr int dx_zstride(int ntap) { return (((2 * ((ntap + 3) & ~3)) / 4) | 1) * 4; }
 static size_t dx_gemm_smem(int npad, int ntap) {
     return 1024 + DX_STAGES * (size_t)dx_stage_bytes(npad) + sizeof(float) * DX_M * dx_zstride(ntap) +
-           sizeof(float2) * 8 * LP * LP + sizeof(int32_t) * (3 * DX_M + 2 + 5) + 128;
+           sizeof(float2) * 8 * LP * DX_YS + sizeof(int32_t) * (3 * DX_M + 2 + 5) + 128;
 }
 
 // two binary32 values to their nearest BF16 (ties to even), lo in the low 16 bits
@@ -136,7 +140,8 @@ __global__ void k_dx_resp_time(const float *__restrict__ resp, int nch, int ntap
     }
 }
 
-// the GEMM's B operand in the paired real form, split into BF16 hi and lo parts
+// the GEMM's B operand [bin][tap][k] (k = 32 g + 16 h + i: Re R (h = 0) and Im R (h = 1)
+// of impact 16 g + i), split into BF16 hi and lo parts
 __global__ void k_dx_resp_pack(const double2 *__restrict__ Rt, DxConst c, uint16_t *__restrict__ bhi,
                                uint16_t *__restrict__ blo) {
     const int64_t total = (int64_t)c.nbins * c.npad * c.kq;
@@ -144,17 +149,14 @@ __global__ void k_dx_resp_pack(const double2 *__restrict__ Rt, DxConst c, uint16
          idx += (int64_t)gridDim.x * blockDim.x) {
         const int k = (int)(idx % c.kq);
         const int64_t r = idx / c.kq;
-        const int row = (int)(r % c.npad);
+        const int n = (int)(r % c.npad);
         const int f = (int)(r / c.npad);
-        const int q = k >> 2, cc = k & 3;
-        const int j = 2 * q + (cc & 1);
-        const bool imq = (cc >> 1) != 0;   // the column holds Im Qhat[j]
+        const int j = 16 * (k >> 5) + (k & 15);
+        const bool imr = ((k >> 4) & 1) != 0;   // the imaginary part of R
         double v = 0.0;
-        if (row < 2 * c.ntap && j < c.nch) {
-            const int n = row < c.ntap ? row : row - c.ntap;
+        if (n < c.ntap && j < c.nch) {
             const double2 R = Rt[((int64_t)j * c.ntap + n) * c.nbins + f];
-            if (row < c.ntap) v = imq ? -R.y : R.x;    // Re Z = Re Q Re R - Im Q Im R
-            else v = imq ? R.x : R.y;                  // Im Z = Re Q Im R + Im Q Re R
+            v = imr ? R.y : R.x;
         }
         const float x = (float)v;
         const uint32_t h = dx_bf16_bits(x);
@@ -167,10 +169,12 @@ __global__ void k_dx_resp_pack(const double2 *__restrict__ Rt, DxConst c, uint16
 static DxConst dx_const_of(const tred_handle *h) {
     DxConst c;
     c.nch = h->g.n_sub * h->g.n_sub;
-    c.kq = 2 * c.nch;
+    c.kq = 32 * ((c.nch + 15) / 16);
+    c.jm = dx_half_split(c.nch);
     c.kp = h->g.kp;
     c.ntap = c.kp * c.kp;
-    c.npad = dx_round16(2 * c.ntap);
+    c.npad = dx_round16(c.ntap);
+    c.imoff = (c.ntap + 3) & ~3;
     c.R = h->d.R;
     c.bp = h->g.bp;
     c.bpl = c.bp == 8 ? 3 : 2;   // bp is 4 or 8
@@ -319,8 +323,9 @@ __device__ __forceinline__ void dx_zero_straddling(const int32_t *__restrict__ r
 //           f = d + NPL (g + 16 e) in register k (g = bitrev16(k));
 // then Z[f] (f <= N/2) and Z[N - f] land in the pair's four columns.  A pair whose two
 // columns are empty in the block's masks is written as zeros without a transform.  Then
-// the CTA writes bin by bin, one lane per pair, the Hermitian split of its two columns
-// as k = 4 q + (Re 2q, Re 2q+1, Im 2q, Im 2q+1) in BF16 hi and lo parts.
+// the CTA writes bin by bin, one lane per two pairs, the Hermitian split of their columns
+// in BF16 hi and lo parts at the GEMM's K positions.  Items (row, half) split the impacts
+// at jm = 4 ceil(nch / 8), so that each lane's four impacts lie in one group of 16.
 __device__ __forceinline__ int dx_tcol(int k, int ST) { return k * ST + ((k >> 5) & 3); }
 
 template <int N, bool HZ>
@@ -339,25 +344,26 @@ __global__ void __launch_bounds__(DX_FWD_THREADS, 2)
     constexpr int NPL = LT / 32;
     constexpr int NW = DX_FWD_THREADS / 32;
     static_assert(NPL <= 16, "pass 2 holds 16 samples per lane");
-    extern __shared__ float T[];   // [kq / 2] columns of ST bins, column k at dx_tcol(k)
+    extern __shared__ float T[];   // [2 jm] columns of ST bins, column k at dx_tcol(k)
     const int ST = dx_tstride(c.nbins);
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int cnt = meta[0], nrows = meta[1];
     if (zero_straddling) dx_zero_straddling(rowstart, cnt, c.nbins, ybuf);
     const int nloc = min(c.rows_cap, nrows - row0);
     const float2 *wlt = tw + TW_LT;
-    const int kh = c.kq >> 1, nph = kh >> 2;
     const int d = lane >> 1, e = lane & 1;
     const bool hz = 2 * c.bt <= LT;
     for (int item = blockIdx.x; item < 2 * nloc; item += gridDim.x) {
         const int rl = item >> 1, hh = item & 1;
+        // impacts [j0, j1) of this half: [0, jm) or [jm, nch), jm a multiple of 4
+        const int j0 = hh ? c.jm : 0, j1 = hh ? c.nch : c.jm;
+        const int nph = (j1 - j0) >> 1;
         const int rec = rows[row0 + rl];
         const int s = rec >> 6, p = rec & 63;
         const uint64_t *mk = colmask + (size_t)(slot_base + s) * c.nch;
         const float *qs = qeff + (size_t)(slot_base + s - qbase) * c.nch * c.bp2 * c.bt + (size_t)p * c.bt;
         for (int ql = warp; ql < nph; ql += NW) {
-            const int q = hh * nph + ql;
-            const int ja = 2 * q, jb = 2 * q + 1;
+            const int ja = j0 + 2 * ql, jb = ja + 1;
             const bool nza = (mk[ja] >> p) & 1ull;
             const bool nzb = (mk[jb] >> p) & 1ull;
             float *T0 = T + dx_tcol(4 * ql, ST);   // the pair's four columns, contiguous
@@ -426,25 +432,42 @@ __global__ void __launch_bounds__(DX_FWD_THREADS, 2)
             }
         }
         __syncthreads();
-        // bin by bin, lane = pair: the Hermitian split of the pair's Z[f] and Z[N - f],
+        // bin by bin, lane c4 = impacts j0 + 4 c4 .. + 3 (two pairs): the Hermitian split
+        // of each pair's Z[f] and Z[N - f],
         //     Qhat[2q][f] = (Z[f] + conj Z[N - f]) / 2,   Qhat[2q+1][f] = (Z[f] - conj Z[N - f]) / 2i,
-        // then its four values k = 4 q .. 4 q + 3 as BF16 hi and lo parts (8 bytes each)
-        for (int f = warp; f < c.nbins; f += NW) {
-            const size_t o = ((size_t)f * c.rows_cap + rl) * c.kq + (size_t)hh * kh;
+        // then the four real parts at k = 32 g + i and the four imaginary parts at
+        // k = 32 g + 16 + i (j = 16 g + i) as BF16 hi and lo parts (8 bytes each)
+        // a warp covers 32 / lpb bins at a time (lpb lanes per bin, at least the half's units)
+        const int nunit = nph >> 1;
+        const int lpb = nunit <= 8 ? 8 : (nunit <= 16 ? 16 : 32);
+        for (int f = warp * (32 / lpb) + lane / lpb; f - lane / lpb < c.nbins; f += NW * (32 / lpb)) {
+            if (f >= c.nbins) continue;
+            const size_t o = ((size_t)f * c.rows_cap + rl) * c.kq;
             const bool self = f == 0 || 2 * f == LT;
-            for (int ql = lane; ql < nph; ql += 32) {
-                const float *tq = T + dx_tcol(4 * ql, ST) + f;
-                const float zr = tq[0], zi = tq[ST];
-                const float cr = self ? zr : tq[2 * ST], ci = self ? zi : tq[3 * ST];
-                const float x0 = 0.5f * (zr + cr);   // Re Qhat[2q]
-                const float x1 = 0.5f * (zi + ci);   // Re Qhat[2q + 1]
-                const float x2 = 0.5f * (zi - ci);   // Im Qhat[2q]
-                const float x3 = 0.5f * (cr - zr);   // Im Qhat[2q + 1]
-                const uint32_t h01 = dx_bf16x2(x0, x1), h23 = dx_bf16x2(x2, x3);
-                const uint32_t l01 = dx_bf16x2(x0 - __uint_as_float(h01 << 16), x1 - __uint_as_float(h01 & 0xFFFF0000u));
-                const uint32_t l23 = dx_bf16x2(x2 - __uint_as_float(h23 << 16), x3 - __uint_as_float(h23 & 0xFFFF0000u));
-                *reinterpret_cast<uint2 *>(qhi + o + 4 * ql) = make_uint2(h01, h23);
-                *reinterpret_cast<uint2 *>(qlo + o + 4 * ql) = make_uint2(l01, l23);
+            for (int c4 = lane % lpb; c4 < nunit; c4 += lpb) {
+                float re[4], im[4];
+#pragma unroll
+                for (int h2 = 0; h2 < 2; ++h2) {
+                    const float *tq = T + dx_tcol(4 * (2 * c4 + h2), ST) + f;
+                    const float zr = tq[0], zi = tq[ST];
+                    const float cr = self ? zr : tq[2 * ST], ci = self ? zi : tq[3 * ST];
+                    re[2 * h2] = 0.5f * (zr + cr);       // Qhat[2q]
+                    im[2 * h2] = 0.5f * (zi - ci);
+                    re[2 * h2 + 1] = 0.5f * (zi + ci);   // Qhat[2q + 1]
+                    im[2 * h2 + 1] = 0.5f * (cr - zr);
+                }
+                const int j = j0 + 4 * c4;
+                const size_t kr = o + 32 * (j >> 4) + (j & 15);
+                const uint32_t h01 = dx_bf16x2(re[0], re[1]), h23 = dx_bf16x2(re[2], re[3]);
+                const uint32_t g01 = dx_bf16x2(im[0], im[1]), g23 = dx_bf16x2(im[2], im[3]);
+                const uint32_t l01 = dx_bf16x2(re[0] - __uint_as_float(h01 << 16), re[1] - __uint_as_float(h01 & 0xFFFF0000u));
+                const uint32_t l23 = dx_bf16x2(re[2] - __uint_as_float(h23 << 16), re[3] - __uint_as_float(h23 & 0xFFFF0000u));
+                const uint32_t m01 = dx_bf16x2(im[0] - __uint_as_float(g01 << 16), im[1] - __uint_as_float(g01 & 0xFFFF0000u));
+                const uint32_t m23 = dx_bf16x2(im[2] - __uint_as_float(g23 << 16), im[3] - __uint_as_float(g23 & 0xFFFF0000u));
+                *reinterpret_cast<uint2 *>(qhi + kr) = make_uint2(h01, h23);
+                *reinterpret_cast<uint2 *>(qlo + kr) = make_uint2(l01, l23);
+                *reinterpret_cast<uint2 *>(qhi + kr + 16) = make_uint2(g01, g23);
+                *reinterpret_cast<uint2 *>(qlo + kr + 16) = make_uint2(m01, m23);
             }
         }
         __syncthreads();
@@ -459,14 +482,14 @@ __device__ __forceinline__ void dx_tma_2d(uint32_t dst, const CUtensorMap *map, 
         "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(bar)
         : "memory");
 }
-// K-major operand with the 64-byte swizzle: rows of 64 B, 8-row atoms 512 B apart
-__device__ __forceinline__ uint64_t dx_sdesc_sw64(uint32_t addr) {
+// K-major operand with the 128-byte swizzle: rows of 128 B, 8-row atoms 1024 B apart
+__device__ __forceinline__ uint64_t dx_sdesc_sw128(uint32_t addr) {
     uint64_t d = 0;
     d |= (uint64_t)((addr & 0x3FFFF) >> 4);        // start address
     d |= (uint64_t)1 << 16;                        // leading byte offset (unused for swizzled K-major)
-    d |= (uint64_t)(512 >> 4) << 32;               // stride byte offset: next 8-row atom
+    d |= (uint64_t)(1024 >> 4) << 32;              // stride byte offset: next 8-row atom
     d |= (uint64_t)1 << 46;                        // descriptor version
-    d |= (uint64_t)4 << 61;                        // 64-byte swizzle
+    d |= (uint64_t)2 << 61;                        // 128-byte swizzle
     return d;
 }
 __device__ __forceinline__ void dx_mma_bf16(uint32_t d, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
@@ -520,8 +543,8 @@ __global__ void __launch_bounds__(DX_GEMM_THREADS, 1)
     const uint32_t BB = dx_b_bytes(c.npad);
     const int SZ = dx_zstride(c.ntap);
     float *Zs = reinterpret_cast<float *>(gbase + DX_STAGES * SB);
-    float2 *yacc_all = reinterpret_cast<float2 *>(Zs + DX_M * SZ);      // [8][16 * 16] block outputs
-    int32_t *rowrec = reinterpret_cast<int32_t *>(yacc_all + 8 * LP * LP);   // [DX_M + 2]
+    float2 *yacc_all = reinterpret_cast<float2 *>(Zs + DX_M * SZ);         // [8][16][DX_YS] block outputs
+    int32_t *rowrec = reinterpret_cast<int32_t *>(yacc_all + 8 * LP * DX_YS);   // [DX_M + 2]
     int32_t *seg_slot = rowrec + DX_M + 2;                               // [DX_M]
     int32_t *seg_base = seg_slot + DX_M;                                 // [DX_M]
     int32_t *seg_cnt = seg_base + DX_M;                                  // [5]
@@ -564,7 +587,9 @@ __global__ void __launch_bounds__(DX_GEMM_THREADS, 1)
     const int nitems = ntiles * c.nbins;
     const int nkc = (c.kq + DX_KC - 1) / DX_KC;
     const uint32_t tx_bytes = 2 * DX_A_BYTES + 2 * BB;
+    // D FP32, A and B BF16, both K-major, N = npad, M = 128; idesc_nb also negates B
     const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(c.npad >> 3) << 17) | ((128u >> 4) << 24);
+    const uint32_t idesc_nb = idesc | (1u << 14);
 
     if (warp == 0) {
         // ------------------------------------------------ copies
@@ -621,17 +646,33 @@ __global__ void __launch_bounds__(DX_GEMM_THREADS, 1)
                     }
                     tmem_fence_after();
                     const uint32_t sb = base + (uint32_t)st * SB;
+                    // the chunk holds two groups of 16 impacts, 32 bytes per K step: group
+                    // 2 kc at bytes 0 (real parts of Q and of R) and 32 (imaginary parts),
+                    // group 2 kc + 1 at 64 and 96 (all zero past kq: its products are skipped)
+                    const uint32_t dre = d, dim = d + 128;
 #pragma unroll
-                    for (int ks = 0; ks < DX_KC / 16; ++ks) {
-                        if (kc * DX_KC + ks * 16 >= c.kq) break;
-                        const uint32_t acc = (kc > 0 || ks > 0) ? 1u : 0u;
-                        const uint64_t ah = dx_sdesc_sw64(sb + 32 * ks);
-                        const uint64_t al = dx_sdesc_sw64(sb + DX_A_BYTES + 32 * ks);
-                        const uint64_t bh = dx_sdesc_sw64(sb + 2 * DX_A_BYTES + 32 * ks);
-                        const uint64_t bl = dx_sdesc_sw64(sb + 2 * DX_A_BYTES + BB + 32 * ks);
-                        dx_mma_bf16(d, ah, bh, idesc, acc);
-                        dx_mma_bf16(d, ah, bl, idesc, 1u);
-                        dx_mma_bf16(d, al, bh, idesc, 1u);
+                    for (int gi = 0; gi < 2; ++gi) {
+                        if (kc * DX_KC + 32 * gi >= c.kq) break;
+                        const uint32_t acc = (kc > 0 || gi > 0) ? 1u : 0u;
+                        const uint32_t o = 64u * (uint32_t)gi;
+                        const uint64_t aRh = dx_sdesc_sw128(sb + o), aIh = dx_sdesc_sw128(sb + o + 32);
+                        const uint64_t aRl = dx_sdesc_sw128(sb + DX_A_BYTES + o), aIl = dx_sdesc_sw128(sb + DX_A_BYTES + o + 32);
+                        const uint64_t bRh = dx_sdesc_sw128(sb + 2 * DX_A_BYTES + o);
+                        const uint64_t bIh = dx_sdesc_sw128(sb + 2 * DX_A_BYTES + o + 32);
+                        const uint64_t bRl = dx_sdesc_sw128(sb + 2 * DX_A_BYTES + BB + o);
+                        const uint64_t bIl = dx_sdesc_sw128(sb + 2 * DX_A_BYTES + BB + o + 32);
+                        dx_mma_bf16(dre, aRh, bRh, idesc, acc);      // Re Z += Re Q Re R
+                        dx_mma_bf16(dim, aRh, bIh, idesc, acc);      // Im Z += Re Q Im R
+                        dx_mma_bf16(dre, aRh, bRl, idesc, 1u);
+                        dx_mma_bf16(dim, aRh, bIl, idesc, 1u);
+                        dx_mma_bf16(dre, aRl, bRh, idesc, 1u);
+                        dx_mma_bf16(dim, aRl, bIh, idesc, 1u);
+                        dx_mma_bf16(dre, aIh, bIh, idesc_nb, 1u);    // Re Z -= Im Q Im R
+                        dx_mma_bf16(dim, aIh, bRh, idesc, 1u);       // Im Z += Im Q Re R
+                        dx_mma_bf16(dre, aIh, bIl, idesc_nb, 1u);
+                        dx_mma_bf16(dim, aIh, bRl, idesc, 1u);
+                        dx_mma_bf16(dre, aIl, bIh, idesc_nb, 1u);
+                        dx_mma_bf16(dim, aIl, bRh, idesc, 1u);
                     }
                     dx_commit(bar_empty(st));
                 }
@@ -648,24 +689,22 @@ __global__ void __launch_bounds__(DX_GEMM_THREADS, 1)
         }
     } else {
         // ------------------------------------------------ epilogue (warps 2..9)
-        // warp w drains lane quarter w & 3 of the accumulator, columns half (w - 2) >> 2;
+        // warp w drains lane quarter w & 3 of accumulator Re Z (w < 6) or Im Z (w >= 6);
         // the first four warps list the tile's block segments (consecutive rows of one
-        // slot: slot, first row, row count); then warp e takes segments e, e + 8, ... and
-        // adds its rows in ascending order into the block's 16 x 16 output in its own
-        // shared-memory accumulator: row r at pixel p' adds Z_r[K] at u = p' + 2R - K, one
-        // lane per tap (the taps of a row reach distinct outputs)
+        // slot: slot, first row); then each warp sums its segments' rows into the outputs:
+        //     Ihat[u] = sum over the segment's rows r (pixel p') of Z_r[K],  K = p' + 2R - u
         const int te = tid - 64;
         const int ew = te >> 5;   // epilogue warp 0..7
         const int quarter = warp & 3, half = (warp - 2) >> 2;
         const int R2 = 2 * c.R;
-        const int ncc = (2 * c.ntap + 31) / 32, hcc = (ncc + 1) / 2;
-        float2 *yacc = yacc_all + ew * (LP * LP);
+        const int ncc = (c.imoff + 31) / 32;   // 32-column loads per accumulator
+        float2 *yacc = yacc_all + ew * (LP * DX_YS);
         // this lane's taps n = lane + 32 j and their output offsets (2R - K per axis)
         int tap_off[DX_TAPS_PER_LANE];
 #pragma unroll
         for (int j = 0; j < DX_TAPS_PER_LANE; ++j) {
             const int n = lane + 32 * j;
-            tap_off[j] = n < c.ntap ? (R2 - n / c.kp) * LP + (R2 - n % c.kp) : -1;
+            tap_off[j] = n < c.ntap ? (R2 - n / c.kp) * DX_YS + (R2 - n % c.kp) : -1;
         }
         int i = 0;
         for (int it = blockIdx.x; it < nitems; it += gridDim.x, ++i) {
@@ -689,14 +728,14 @@ __global__ void __launch_bounds__(DX_GEMM_THREADS, 1)
             }
             tmem_fence_after();
             const int r = 32 * quarter + lane;
-            for (int cc = half * hcc; cc < min(ncc, (half + 1) * hcc); ++cc) {
+            for (int cc = 0; cc < ncc; ++cc) {   // half 0: Re Z, half 1: Im Z
                 float v[32];
-                tmem_ld32(tmem + ((uint32_t)(32 * quarter) << 16) + (uint32_t)(ab * 256 + 32 * cc), v);
+                tmem_ld32(tmem + ((uint32_t)(32 * quarter) << 16) + (uint32_t)(ab * 256 + 128 * half + 32 * cc), v);
+                float *zd = Zs + r * SZ + half * c.imoff + 32 * cc;
 #pragma unroll
                 for (int e4 = 0; e4 < 8; ++e4)
-                    if (32 * cc + 4 * e4 < 2 * c.ntap)
-                        *reinterpret_cast<float4 *>(Zs + r * SZ + 32 * cc + 4 * e4) =
-                            make_float4(v[4 * e4], v[4 * e4 + 1], v[4 * e4 + 2], v[4 * e4 + 3]);
+                    if (32 * cc + 4 * e4 < c.imoff)
+                        *reinterpret_cast<float4 *>(zd + 4 * e4) = make_float4(v[4 * e4], v[4 * e4 + 1], v[4 * e4 + 2], v[4 * e4 + 3]);
             }
             tmem_fence_before();
             __syncwarp();
@@ -722,15 +761,23 @@ __global__ void __launch_bounds__(DX_GEMM_THREADS, 1)
             dx_epi_sync();
             const int nseg = seg_cnt[4];
             const int slot_before = rowrec[DX_M], slot_after = rowrec[DX_M + 1];
+            // warp e takes segments e, e + 8, ... and adds its rows in ascending order
+            // into the block's 16 x 16 output in its own shared-memory accumulator: row r at
+            // pixel p' adds Z_r[K] at u = p' + 2R - K, one lane per tap (the taps of a row
+            // reach distinct outputs; the accumulator's row stride 25 = 9 mod 16 puts the 16
+            // taps n .. n + 15 a half-warp touches in distinct banks)
             for (int si = ew; si < nseg; si += 8) {
                 const int sl = seg_slot[si], base = seg_base[si];
                 const int end = si + 1 < nseg ? seg_base[si + 1] : nv;
 #pragma unroll
-                for (int j = 0; j < (LP * LP) / 32; ++j) yacc[lane + 32 * j] = make_float2(0.f, 0.f);
+                for (int j = 0; j < (LP * LP) / 32; ++j) {
+                    const int u = lane + 32 * j;
+                    yacc[(u >> 4) * DX_YS + (u & 15)] = make_float2(0.f, 0.f);
+                }
                 __syncwarp();
                 for (int rr = base; rr < end; ++rr) {
                     const int pp = rowrec[rr] & 63;
-                    const int pu = (pp >> c.bpl) * LP + (pp & (c.bp - 1));
+                    const int pu = (pp >> c.bpl) * DX_YS + (pp & (c.bp - 1));
                     const float *zr = Zs + rr * SZ;
 #pragma unroll
                     for (int j = 0; j < DX_TAPS_PER_LANE; ++j) {
@@ -739,7 +786,7 @@ __global__ void __launch_bounds__(DX_GEMM_THREADS, 1)
                         float2 *y = yacc + pu + tap_off[j];
                         float2 a = *y;
                         a.x += zr[n];
-                        a.y += zr[c.ntap + n];
+                        a.y += zr[c.imoff + n];
                         *y = a;
                     }
                     __syncwarp();
@@ -749,7 +796,7 @@ __global__ void __launch_bounds__(DX_GEMM_THREADS, 1)
 #pragma unroll
                 for (int j = 0; j < (LP * LP) / 32; ++j) {
                     const int u = lane + 32 * j;
-                    const float2 a = yacc[u];
+                    const float2 a = yacc[(u >> 4) * DX_YS + (u & 15)];
                     if (split) {
                         atomicAdd(&yb[u].x, a.x);
                         atomicAdd(&yb[u].y, a.y);
@@ -899,7 +946,7 @@ __global__ void __launch_bounds__(DX_INV_THREADS, 2)
 }
 
 // ---------------------------------------------------------------- host side
-// 2-D BF16 tensor [rows][inner], box [box_rows][32] (64 bytes), 64-byte swizzle; columns
+// 2-D BF16 tensor [rows][inner], box [box_rows][64] (128 bytes), 128-byte swizzle; columns
 // past inner read as zero
 static int dx_make_map(tred_handle *h, CUtensorMap *m, const void *ptr, uint64_t inner, uint64_t rows,
                        uint32_t box_rows) {
@@ -910,7 +957,7 @@ static int dx_make_map(tred_handle *h, CUtensorMap *m, const void *ptr, uint64_t
     const cuuint32_t box[2] = {(cuuint32_t)DX_KC, box_rows};
     const cuuint32_t estr[2] = {1, 1};
     CUresult r = fn(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void *>(ptr), dims, strides, box, estr,
-                    CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                    CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                     CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     if (r != CUDA_SUCCESS) return set_error(h, TRED_ERR_CUDA, "direct form: tensor map encode failed (%d)", (int)r);
     return TRED_OK;
@@ -919,7 +966,7 @@ static int dx_make_map(tred_handle *h, CUtensorMap *m, const void *ptr, uint64_t
 template <int G>
 static int run_direct(tred_handle *h, const DxConst &c, const int32_t *n_blocks_dev, const float *qeff, float *out,
                       int slot_base, int slot_count, int qbase, cudaStream_t s) {
-    const size_t fwd_smem = dx_fwd_smem(c.kq, c.nbins);
+    const size_t fwd_smem = dx_fwd_smem(c.nch, c.nbins);
     const size_t gemm_smem = dx_gemm_smem(c.npad, c.ntap);
     const size_t inv_smem = sizeof(float2) * ((size_t)DX_INV_U * (32 * G + 1) + (size_t)(DX_INV_THREADS / 32) * 64 * G);
     // the largest dynamic shared memory asked for so far (shapes differ between handles)
@@ -989,6 +1036,6 @@ int dx_rows_cap_of(int dx_blocks, int bp2, int cap_param) {
 }
 int dx_blocks_of(int max_blocks) { return max_blocks < DX_BLOCKS_MAX ? max_blocks : DX_BLOCKS_MAX; }
 // the forward kernel's transposition buffer must fit in one CTA's shared memory
-bool dx_shape_ok(int kq, int lt) { return dx_fwd_smem(kq, lt / 2 + 1) <= 227 * 1024; }
+bool dx_shape_ok(int nch, int lt) { return dx_fwd_smem(nch, lt / 2 + 1) <= 227 * 1024; }
 
 }  // namespace tred

@@ -134,7 +134,7 @@ static int validate(const tred_geometry *g, const tred_params *p, char *msg, siz
     if (p->conv_mode >= 1 && p->conv_mode <= 3 && (g->lt != 512 || g->bp != 8))
         return bad("the tensor-core convolution (conv_mode 1, 2, 3) needs lt = 512 and bp = 8");
     if (p->conv_mode == 4 && ((g->lt != 384 && g->lt != 512) || g->kp > 9 || g->n_sub > 10 ||
-                             !dx_shape_ok(2 * g->n_sub * g->n_sub, g->lt)))
+                             !dx_shape_ok(g->n_sub * g->n_sub, g->lt)))
         return bad("the direct spatial form (conv_mode 4) needs lt = 384 or 512, kp <= 9 and n_sub <= 10");
     if (p->mpcp != 0 && p->mpcp != 1) return bad("mpcp must be 0 or 1");
     if (p->effq_skip_empty != 0 && p->effq_skip_empty != 1) return bad("effq_skip_empty must be 0 or 1");
@@ -233,7 +233,7 @@ int32_t tred_create(const tred_geometry *geom, const tred_params *params, int32_
     // module plane in one launch, so the spectral kernel's last partial wave of
     // (block, class) items comes once per call rather than once per 1024 blocks
     if (params->conv_mode == 4) {
-        const int kq = 2 * ns * ns, npad = (2 * geom->kp * geom->kp + 15) & ~15, nbins = geom->lt / 2 + 1;
+        const int kq = 32 * ((ns * ns + 15) / 16), npad = (geom->kp * geom->kp + 15) & ~15, nbins = geom->lt / 2 + 1;
         const int bp2 = geom->bp * geom->bp;
         h->dx_blocks = dx_blocks_of(max_blocks);
         h->dx_rows_cap = dx_rows_cap_of(h->dx_blocks, bp2, params->conv_rows_cap);
@@ -241,6 +241,10 @@ int32_t tred_create(const tred_geometry *geom, const tred_params *params, int32_
         alloc((void **)&h->dx_blo, dx_bytes_b(nbins, npad, kq), "alloc direct-form response");
         alloc((void **)&h->dx_qhi, dx_bytes_q(nbins, h->dx_rows_cap, kq), "alloc direct-form spectra");
         alloc((void **)&h->dx_qlo, dx_bytes_q(nbins, h->dx_rows_cap, kq), "alloc direct-form spectra");
+        // the K positions of the impacts past n_sub^2 (padding of the last group of 16) are
+        // never written and must read as zero
+        if (rc == TRED_OK) rc = check_cuda(h, cudaMemset(h->dx_qhi, 0, dx_bytes_q(nbins, h->dx_rows_cap, kq)), "clear spectra");
+        if (rc == TRED_OK) rc = check_cuda(h, cudaMemset(h->dx_qlo, 0, dx_bytes_q(nbins, h->dx_rows_cap, kq)), "clear spectra");
         alloc((void **)&h->dx_y, sizeof(float2) * (size_t)h->dx_blocks * nbins * LP * LP, "alloc direct-form output");
         alloc((void **)&h->dx_rows, sizeof(int32_t) * (size_t)h->dx_blocks * bp2, "alloc direct-form rows");
         alloc((void **)&h->dx_rowstart, sizeof(int32_t) * ((size_t)h->dx_blocks + 2), "alloc direct-form rows");

@@ -62,6 +62,7 @@ struct tred_handle {
     // direct spatial form (conv_mode 4): per time frequency, the sum over impacts and
     // response taps as a split-BF16 tensor-core GEMM over the non-empty block pixels
     uint16_t *dx_bhi, *dx_blo;  // [nbins][npad][kq] response operand (BF16 hi and lo parts)
+                                // (kq = 32 ceil(n_sub^2 / 16), npad = kp^2 rounded up to 16)
     uint16_t *dx_qhi, *dx_qlo;  // [nbins][dx_rows_cap][kq] charge spectra of the rows
     float2 *dx_y;               // [dx_blocks][nbins][16 * 16] block output spectra
     int32_t *dx_rows;           // [dx_blocks * bp^2] row records: local slot << 6 | pixel
@@ -153,7 +154,7 @@ size_t dx_bytes_b(int nbins, int npad, int kq);
 size_t dx_bytes_q(int nbins, int rows_cap, int kq);
 int dx_rows_cap_of(int dx_blocks, int bp2, int cap_param);
 int dx_blocks_of(int max_blocks);
-bool dx_shape_ok(int kq, int lt);
+bool dx_shape_ok(int nch, int lt);
 // the driver entry point cuTensorMapEncodeTiled (nullptr when unavailable)
 void *tensor_map_encoder();
 int launch_convolve(tred_handle *h, const int32_t *block_ids, const int32_t *n_blocks_dev,
