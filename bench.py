@@ -102,6 +102,88 @@ def conv_counters():
     return out
 
 
+DIRECT_SOURCES = ("k_direct.cu", "tred_internal.cuh")
+
+
+def _direct_figures():
+    """Per-row / per-block DRAM bytes of the direct form's kernels from the committed ncu
+    capture on module20 (profiles/direct_kernels_module20.txt) and its source hash."""
+    path = os.path.join(ROOT, "profiles", "direct_kernels_module20.txt")
+    kv = {}
+    try:
+        for line in open(path):
+            parts = line.split()
+            if not parts or parts[0].startswith("#"):
+                continue
+            if len(parts) >= 3 and parts[1] == "sha256":
+                kv[parts[0]] = parts[2]
+            elif len(parts) >= 2:
+                kv[parts[0]] = float(parts[1])
+    except OSError:
+        pass
+    return kv
+
+
+def _peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except (OSError, ValueError):
+        return {}
+
+
+def direct_rooflines(cfg, rows, cols, blocks, kms, clocks):
+    """Roofline objects of the direct form's kernels (conv_mode 4) and of the effective
+    charge, each from its algorithmic work per step over its CUDA-event time (kms: kernel
+    name -> ms per step); the dominant (longest) one first.
+      k_dx_gemm  tensor: 3 split-BF16 products x 8 real FLOPs per complex MAC over
+                 rows x n_sub^2 impacts x kp^2 taps x (lt/2 + 1) bins
+      k_dx_fwd   HBM: the rows' non-empty Q^eff columns read (bt x 4 B each), their
+                 spectra written (rows x (lt/2 + 1) bins x kq x 2 parts x 2 B)
+      k_dx_inv   HBM: the block spectra read (blocks x bins x 256 x 8 B), the block
+                 outputs written (blocks x 256 x lt x 4 B)"""
+    pk = _peaks()
+    hbm = pk.get("hbm_gbs", 6400.0)
+    bf16 = pk.get("bf16_tflops_sustained", 1400.0)
+    src = "measured (MEASURED_PEAKS.json)" if pk else "fallback"
+    nch, ntap, nbins = cfg.n_sub ** 2, cfg.kp ** 2, cfg.lt // 2 + 1
+    kq = 32 * ((nch + 15) // 16)
+    figs = _direct_figures()
+    fresh = figs.get("direct_sources") == _source_sha(DIRECT_SOURCES)
+    out = {}
+    if kms.get("k_dx_gemm"):
+        fl = 3.0 * 8.0 * rows * nch * ntap * nbins
+        a = fl / (kms["k_dx_gemm"] / 1e3) / 1e12
+        out["k_dx_gemm"] = {"bound": "tensor", "achieved": a, "peak": bf16, "unit": "TFLOP/s", "frac": a / bf16,
+                            "flop_per_step": fl, "ms": kms["k_dx_gemm"],
+                            "peak_source": f"bf16 dense, sustained (kernel timed inside the step), {src}"}
+    if kms.get("k_dx_fwd"):
+        by = cols * cfg.bt * 4.0 + rows * nbins * kq * 4.0
+        a = by / (kms["k_dx_fwd"] / 1e3) / 1e9
+        out["k_dx_fwd"] = {"bound": "hbm", "achieved": a, "peak": hbm, "unit": "GB/s", "frac": a / hbm,
+                           "bytes_per_step": by, "ms": kms["k_dx_fwd"], "peak_source": f"copy bandwidth, {src}"}
+    if kms.get("k_dx_inv"):
+        by = blocks * (nbins * 256 * 8.0 + 256 * cfg.lt * 4.0)
+        a = by / (kms["k_dx_inv"] / 1e3) / 1e9
+        out["k_dx_inv"] = {"bound": "hbm", "achieved": a, "peak": hbm, "unit": "GB/s", "frac": a / hbm,
+                           "bytes_per_step": by, "ms": kms["k_dx_inv"], "peak_source": f"copy bandwidth, {src}"}
+    for k, r in out.items():
+        r["kernel"] = k
+        unit = "row" if k in ("k_dx_fwd", "k_dx_gemm") else "block"
+        per = figs.get(f"{k}_dram_bytes_per_{unit}")
+        if fresh and per:
+            n_units = rows if unit == "row" else blocks
+            r["traffic"] = per * n_units
+            r["traffic_source"] = (f"ncu dram__bytes_read+write of module20, {per:.4g} B per {unit}, "
+                                   f"scaled to {n_units} {unit}s")
+        else:
+            r["traffic"] = None
+            r["traffic_source"] = "no capture at the current sources"
+        if clocks and clocks.get("sm_mhz") and r["bound"] == "tensor":
+            r["frac_at_observed_clock"] = r["achieved"] / (r["peak"] * clocks["sm_mhz"] / 2032.0)
+    order = sorted(out, key=lambda k: -out[k]["ms"])
+    return {k: out[k] for k in order}
+
+
 def measured_fp32_peak():
     """FP32 FMA TFLOP/s and SM count measured on this device (tred_fp32_peak)."""
     from paper_2602_12052_b300 import tred
@@ -153,8 +235,9 @@ def _args():
     ap.add_argument("--fused", type=int, default=0, choices=[0, 1],
                     help="step mode: 1 = the effective charge and the convolution as one persistent launch "
                          "over the active-block queue (tred_effq_convolve)")
-    ap.add_argument("--conv-mode", type=int, default=0, choices=[0, 1, 2, 3, 4],
-                    help="0: FP32 FFT convolution (default); 1: time DFT as a tcgen05 GEMM in TF32; "
+    ap.add_argument("--conv-mode", type=int, default=4, choices=[0, 1, 2, 3, 4],
+                    help="4: time DFT by FFT, impacts x taps per bin as a split-BF16 tcgen05 GEMM (default); "
+                         "0: FP32 FFT convolution; 1: time DFT as a tcgen05 GEMM in TF32; "
                          "2: the same in split TF32 (three products); 3: the same in split BF16 (three products)")
     return ap.parse_args()
 
@@ -846,6 +929,8 @@ def main():
     torch.cuda.synchronize()
     evs = [[torch.cuda.Event(enable_timing=True) for _ in range(6)] for _ in range(args.steps)]
     launches0 = tred.tred_launch_count(sim.h)
+    # per-kernel CUDA events on the launching stream (library-side) over the timed steps
+    tred.tred_set_kernel_timing(sim.h, True)
     with ClockSampler(local) as clk:
         time.sleep(0.3)
         for k in range(args.steps):
@@ -853,6 +938,13 @@ def main():
             step(evs[k])
         torch.cuda.synchronize()
     launches = tred.tred_launch_count(sim.h) - launches0
+    kernel_ms = {}
+    for cls, name in tred.KT_NAMES.items():
+        kt, kn = tred.tred_kernel_time(sim.h, cls)
+        if kn:
+            kernel_ms[name] = kt / args.steps
+    tred.tred_set_kernel_timing(sim.h, False)
+    rows_dx, cols_dx = tred.tred_direct_counts(sim.h)
     clocks = clk.summary()
     if world > 1:
         torch.distributed.barrier()
@@ -930,13 +1022,23 @@ def main():
                             "the pixel waveforms stay in device memory")}
 
     conv_ms = stage_ms["effq+convolve" if fused else "convolve"]
+    if args.conv_mode == 4:
+        kr = direct_rooflines(cfg, rows_dx, cols_dx, nb, kernel_ms, clocks)
+        dom = next(iter(kr))
+        roofline = dict(kr[dom])
+        roofline["kernels"] = kr
+        roofline["kernel_ms_per_step"] = kernel_ms
+        roofline["rows"], roofline["nonempty_columns"] = rows_dx, cols_dx
+        roofline["conv_alu_frac_unpruned"] = (conv_flop_per_block(cfg.lt) * nb / (conv_ms / 1e3) / 1e12
+                                              / FP32_PEAK_TFLOPS)
     flop_blk = conv_flop_per_block(cfg.lt)
-    roofline = alu_roofline("tred_effq_convolve (k_block_pipeline: effective charge + convolution, one "
-                            "persistent launch)" if fused else "tred_convolve (k_conv_spec + k_conv_itime_mp)",
-                            flop_blk, nb, conv_ms, clocks, peak_meas)
-    roofline["traffic"], roofline["traffic_source"] = conv_traffic(nb) if not fused else (None, "no capture")
+    if args.conv_mode != 4:
+        roofline = alu_roofline("tred_effq_convolve (k_block_pipeline: effective charge + convolution, one "
+                                "persistent launch)" if fused else "tred_convolve (k_conv_spec + k_conv_itime_mp)",
+                                flop_blk, nb, conv_ms, clocks, peak_meas)
+        roofline["traffic"], roofline["traffic_source"] = conv_traffic(nb) if not fused else (None, "no capture")
     roofline["sms"] = sms
-    cc = conv_counters() if not fused else {}
+    cc = conv_counters() if not fused and args.conv_mode == 0 else {}
     if "conv_executed_flop_per_block" in cc:
         ex = cc["conv_executed_flop_per_block"]
         roofline["executed_flop_per_block"] = ex
@@ -962,12 +1064,16 @@ def main():
             "config": {"workload": (f"{cfg.name}: one event of {n} point deposits on a "
                                     f"{cfg.npx}x{cfg.npx} pixel plane x {cfg.nt} ticks, GL-{cfg.gl_order}, "
                                     f"{cfg.kp}x{cfg.kp}x{cfg.n_sub}x{cfg.n_sub}x{cfg.nr} response, "
-                                    f"{cfg.bp}x{cfg.bp}x{cfg.bt} blocks, FFT 16x16x{cfg.lt}, MPCP"
+                                    f"{cfg.bp}x{cfg.bp}x{cfg.bt} blocks"
+                                    + (f", time DFT length {cfg.lt}" if args.conv_mode == 4 else
+                                       f", FFT 16x16x{cfg.lt}, MPCP")
                                     + {0: ", effective charge written for covered columns only",
                                        1: ", time DFT as a TF32 tcgen05 GEMM (tolerance 1e-4)",
                                        2: ", time DFT as a split-TF32 tcgen05 GEMM",
                                        3: ", time DFT as a split-BF16 tcgen05 GEMM (tolerance 1e-4)",
-                                       4: ", time DFT by FFT, impacts x taps per bin as a split-BF16 tcgen05 GEMM"}[args.conv_mode]
+                                       4: (", effective charge written for covered columns only; time DFT by FFT, "
+                                           "impacts x taps per bin as a split-BF16 tcgen05 GEMM over the block "
+                                           "pixels that hold charge")}[args.conv_mode]
                                     + {0: "", 1: f", readout: {cfg.n_samples} successive digitisations per trigger",
                                        2: ", readout: fixed-charge quanta"}[args.readout_mode]
                                     + (", effective charge and convolution in one persistent launch over the "

@@ -165,6 +165,28 @@ int32_t tred_reset_status(tred_handle *h, void *stream);
  * access; diagnostics for benchmarks). */
 int32_t tred_launch_count(const tred_handle *h, int64_t *count);
 
+/* Per-kernel device time (diagnostics for benchmarks).  While enabled, the library
+ * brackets every launch of the kernel classes below with a pair of CUDA events on the
+ * launching stream (do not enable it during CUDA-graph capture).  tred_kernel_time waits
+ * for the recorded events, returns the summed milliseconds and the launch count of class
+ * `which` since the previous call for that class (or since enabling), and forgets them.
+ *   which: TRED_KT_EFFQ (effective charge, k_effq_blocks), TRED_KT_DX_FWD, TRED_KT_DX_GEMM,
+ *          TRED_KT_DX_INV (the forward DFT, GEMM and inverse DFT of conv_mode 4).
+ * TRED_ERR_INVALID_ARG for a class outside the list or null outputs. */
+enum {
+    TRED_KT_EFFQ = 0,
+    TRED_KT_DX_FWD = 1,
+    TRED_KT_DX_GEMM = 2,
+    TRED_KT_DX_INV = 3,
+    TRED_KT_CLASSES = 4
+};
+int32_t tred_set_kernel_timing(tred_handle *h, int32_t enable);
+/* conv_mode 4 diagnostics: the non-empty (block, pixel) rows and the non-empty columns of
+ * those rows in the last pass of tred_convolve (device counts copied to the host, so the
+ * call synchronises the device); 0 and 0 for the other modes. */
+int32_t tred_direct_counts(tred_handle *h, int64_t *rows, int64_t *columns);
+int32_t tred_kernel_time(tred_handle *h, int32_t which, double *ms, int32_t *launches);
+
 /* Failure-detection self-test of the bounded device waits (the paper has no
  * counterpart; this is the library's own fault path).  Enqueues one thread that
  * waits, for limit_cycles SM clock cycles (1 .. 2e9; about 1 s per 2e9 at the

@@ -31,7 +31,8 @@ TRED_STATUS_WORDS = 8
 EXPORTS = [
     "tred_create", "tred_destroy", "tred_last_error", "tred_sync_status", "tred_reset_status",
     "tred_set_response", "tred_drift", "tred_blockbin", "tred_effq", "tred_convolve",
-    "tred_gather_pixels", "tred_readout", "tred_launch_count", "tred_blockbin_noalloc",
+    "tred_gather_pixels", "tred_readout", "tred_launch_count", "tred_set_kernel_timing", "tred_kernel_time", "tred_direct_counts",
+    "tred_blockbin_noalloc",
     "tred_set_transport", "tred_residual", "tred_adjoint", "tred_param_grads",
     "tred_drift_events", "tred_effq_range", "tred_convolve_range", "tred_drift_lines", "tred_effq_lines",
     "tred_wait_selftest", "tred_gather_readout", "tred_fp32_peak", "tred_effq_convolve",
@@ -92,6 +93,10 @@ def load(path: str | None = None) -> ctypes.CDLL:
     lib.tred_sync_status.argtypes = [_P, _P, _P]
     lib.tred_reset_status.argtypes = [_P, _P]
     lib.tred_launch_count.argtypes = [_P, ctypes.POINTER(ctypes.c_int64)]
+    lib.tred_set_kernel_timing.argtypes = [_P, ctypes.c_int32]
+    lib.tred_direct_counts.argtypes = [_P, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64)]
+    lib.tred_kernel_time.argtypes = [_P, ctypes.c_int32, ctypes.POINTER(ctypes.c_double),
+                                     ctypes.POINTER(ctypes.c_int32)]
     lib.tred_wait_selftest.argtypes = [_P, ctypes.c_int64, _P]
     lib.tred_gather_readout.argtypes = [_P, _P, _P, _P, _P, _P, _P, ctypes.POINTER(ReadoutParams), _P, _P, _P, _P,
                                         _I, _P]

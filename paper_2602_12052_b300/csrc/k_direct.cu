@@ -214,7 +214,8 @@ int launch_direct_response(tred_handle *h, const float *resp, cudaStream_t s) {
 // ---------------------------------------------------------------- rows
 // One warp per slot of the pass: the OR of its nch column masks = its non-empty pixels.
 __global__ void k_dx_pixmask(const int32_t *__restrict__ n_blocks_dev, const uint64_t *__restrict__ colmask, int nch,
-                             int bp2, int slot_base, int slot_count, uint64_t *__restrict__ pmask) {
+                             int bp2, int slot_base, int slot_count, uint64_t *__restrict__ pmask,
+                             int32_t *__restrict__ pcnt) {
     const int nb = n_blocks_dev[0];
     const int cnt = max(0, min(slot_count, nb - slot_base));
     const int lane = threadIdx.x & 31;
@@ -222,31 +223,47 @@ __global__ void k_dx_pixmask(const int32_t *__restrict__ n_blocks_dev, const uin
     for (int s = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; s < cnt; s += (gridDim.x * blockDim.x) >> 5) {
         const uint64_t *m = colmask + (size_t)(slot_base + s) * nch;
         uint64_t v = 0;
-        for (int j = lane; j < nch; j += 32) v |= m[j];
+        int nz = 0;   // non-empty columns of the slot
+        for (int j = lane; j < nch; j += 32) {
+            v |= m[j];
+            nz += __popcll(m[j] & keep);
+        }
 #pragma unroll
-        for (int o = 16; o >= 1; o >>= 1) v |= __shfl_xor_sync(0xffffffffu, v, o);
-        if (lane == 0) pmask[s] = v & keep;
+        for (int o = 16; o >= 1; o >>= 1) {
+            v |= __shfl_xor_sync(0xffffffffu, v, o);
+            nz += __shfl_xor_sync(0xffffffffu, nz, o);
+        }
+        if (lane == 0) {
+            pmask[s] = v & keep;
+            pcnt[s] = nz;
+        }
     }
 }
 
 // One CTA: exclusive scan of the slots' pixel counts (rowstart), the row records in slot
-// then pixel order, meta = {slots of the pass, rows of the pass}.
+// then pixel order, meta = {slots of the pass, rows of the pass, non-empty columns}.
 constexpr int DX_ROWS_THREADS = 1024;
 __global__ void __launch_bounds__(DX_ROWS_THREADS) k_dx_rows(const int32_t *__restrict__ n_blocks_dev,
-                                                              const uint64_t *__restrict__ pmask, int slot_base,
+                                                              const uint64_t *__restrict__ pmask,
+                                                              const int32_t *__restrict__ pcnt, int slot_base,
                                                               int slot_count, int32_t *__restrict__ rows,
                                                               int32_t *__restrict__ rowstart,
                                                               int32_t *__restrict__ meta) {
     __shared__ int wsum[32];
     __shared__ int carry_s;
+    __shared__ long long ncol_s;
     const int nb = n_blocks_dev[0];
     const int cnt = max(0, min(slot_count, nb - slot_base));
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    if (tid == 0) carry_s = 0;
+    if (tid == 0) {
+        carry_s = 0;
+        ncol_s = 0;
+    }
     __syncthreads();
     for (int base = 0; base < cnt; base += DX_ROWS_THREADS) {
         const int s = base + tid;
         const uint64_t m = s < cnt ? pmask[s] : 0ull;
+        if (s < cnt) atomicAdd(reinterpret_cast<unsigned long long *>(&ncol_s), (unsigned long long)pcnt[s]);
         const int n = __popcll(m);
         int x = n;   // inclusive warp scan
 #pragma unroll
@@ -286,6 +303,7 @@ __global__ void __launch_bounds__(DX_ROWS_THREADS) k_dx_rows(const int32_t *__re
         rowstart[cnt] = carry_s;
         meta[0] = cnt;
         meta[1] = carry_s;
+        meta[2] = (int32_t)min(ncol_s, 2147483647ll);
     }
 }
 
@@ -996,22 +1014,29 @@ static int run_direct(tred_handle *h, const DxConst &c, const int32_t *n_blocks_
     const int end = slot_base + slot_count;
     for (int base = slot_base; base < end; base += h->dx_blocks) {
         const int cnt = h->dx_blocks < end - base ? h->dx_blocks : end - base;
-        k_dx_pixmask<<<sms * 4, 256, 0, s>>>(n_blocks_dev, h->colmask, c.nch, c.bp2, base, cnt, h->dx_pmask);
-        k_dx_rows<<<1, DX_ROWS_THREADS, 0, s>>>(n_blocks_dev, h->dx_pmask, base, cnt, h->dx_rows, h->dx_rowstart,
-                                                h->dx_meta);
+        k_dx_pixmask<<<sms * 4, 256, 0, s>>>(n_blocks_dev, h->colmask, c.nch, c.bp2, base, cnt, h->dx_pmask,
+                                             h->dx_pcnt);
+        k_dx_rows<<<1, DX_ROWS_THREADS, 0, s>>>(n_blocks_dev, h->dx_pmask, h->dx_pcnt, base, cnt, h->dx_rows,
+                                                h->dx_rowstart, h->dx_meta);
         h->launches += 2;
         const int64_t max_rows = (int64_t)cnt * c.bp2;
         const int nrc = (int)((max_rows + c.rows_cap - 1) / c.rows_cap);
         for (int k = 0; k < nrc; ++k) {
             const int row0 = k * c.rows_cap;
+            kt_begin(h, TRED_KT_DX_FWD, s);
             k_dx_fwd<G><<<2 * sms, DX_FWD_THREADS, fwd_smem, s>>>(qeff, h->colmask, h->dx_rows, h->dx_rowstart, h->dx_meta,
                                                              h->tw, c, base, qbase, row0, k == 0 ? 1 : 0, h->dx_qhi,
                                                              h->dx_qlo, h->dx_y);
+            kt_end(h, TRED_KT_DX_FWD, s);
+            kt_begin(h, TRED_KT_DX_GEMM, s);
             k_dx_gemm<<<sms, DX_GEMM_THREADS, gemm_smem, s>>>(tah, tal, tbh, tbl, h->dx_rows, h->dx_rowstart,
                                                               h->dx_meta, c, row0, h->dx_y, h->status);
+            kt_end(h, TRED_KT_DX_GEMM, s);
             h->launches += 2;
         }
+        kt_begin(h, TRED_KT_DX_INV, s);
         k_dx_inv<G><<<2 * sms, DX_INV_THREADS, inv_smem, s>>>(h->dx_y, h->dx_rowstart, h->dx_meta, h->tw, c, base, out);
+        kt_end(h, TRED_KT_DX_INV, s);
         h->launches += 1;
     }
     return check_cuda(h, cudaGetLastError(), "direct-form launch");

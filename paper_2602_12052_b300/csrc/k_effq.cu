@@ -286,9 +286,11 @@ int launch_effq(tred_handle *h, int n, const tred_deposits &deps, const int32_t 
             if (rc) return rc;
         }
     }
+    kt_begin(h, TRED_KT_EFFQ, s);
     k_effq_blocks<<<sms * EQ_CTAS_PER_SM, EQ_THREADS, smem, s>>>(block_ids, dep_offsets, dep_index, n_blocks_dev, c, h->wts,
                                                  reinterpret_cast<const DepRec *>(h->recs), qeff, h->colmask,
                                                  h->effq_acc, queue, slot_base, slot_count);
+    kt_end(h, TRED_KT_EFFQ, s);
     h->launches += 1;
     return check_cuda(h, cudaGetLastError(), "effq launch");
 }

@@ -42,6 +42,51 @@ int num_sms(tred_handle *h) {
     return n > 0 ? n : 148;
 }
 
+}  // namespace tred
+
+// Event pairs of the timed launches, per kernel class; the events are pooled and reused.
+struct KernelTimers {
+    std::vector<cudaEvent_t> pool;
+    std::vector<std::pair<cudaEvent_t, cudaEvent_t>> pairs[TRED_KT_CLASSES];
+    cudaEvent_t open[TRED_KT_CLASSES] = {};
+    cudaEvent_t take() {
+        if (!pool.empty()) {
+            cudaEvent_t e = pool.back();
+            pool.pop_back();
+            return e;
+        }
+        cudaEvent_t e = nullptr;
+        cudaEventCreate(&e);
+        return e;
+    }
+    ~KernelTimers() {
+        for (auto e : pool) cudaEventDestroy(e);
+        for (auto &v : pairs)
+            for (auto &p : v) {
+                cudaEventDestroy(p.first);
+                cudaEventDestroy(p.second);
+            }
+        for (auto e : open)
+            if (e) cudaEventDestroy(e);
+    }
+};
+
+namespace tred {
+
+void kt_begin(tred_handle *h, int which, cudaStream_t s) {
+    if (!h->kt || which < 0 || which >= TRED_KT_CLASSES) return;
+    cudaEvent_t e = h->kt->take();
+    cudaEventRecord(e, s);
+    h->kt->open[which] = e;
+}
+void kt_end(tred_handle *h, int which, cudaStream_t s) {
+    if (!h->kt || which < 0 || which >= TRED_KT_CLASSES || !h->kt->open[which]) return;
+    cudaEvent_t e = h->kt->take();
+    cudaEventRecord(e, s);
+    h->kt->pairs[which].push_back({h->kt->open[which], e});
+    h->kt->open[which] = nullptr;
+}
+
 // Gauss-Legendre nodes and weights on [-1, 1]: Newton's method on the Legendre
 // polynomial from Chebyshev-like starting points, derivative from the standard
 // identity (1 - x^2) P_n' = n (P_{n-1} - x P_n).
@@ -250,6 +295,7 @@ int32_t tred_create(const tred_geometry *geom, const tred_params *params, int32_
         alloc((void **)&h->dx_rowstart, sizeof(int32_t) * ((size_t)h->dx_blocks + 2), "alloc direct-form rows");
         alloc((void **)&h->dx_meta, sizeof(int32_t) * 4, "alloc direct-form rows");
         alloc((void **)&h->dx_pmask, sizeof(uint64_t) * (size_t)h->dx_blocks, "alloc direct-form masks");
+        alloc((void **)&h->dx_pcnt, sizeof(int32_t) * (size_t)h->dx_blocks, "alloc direct-form counts");
     } else {
         h->yspec_blocks = max_blocks < 8192 ? max_blocks : 8192;
         alloc((void **)&h->yspec, sizeof(float2) * (size_t)h->yspec_blocks * geom->lt * LP * LP, "alloc yspec");
@@ -311,9 +357,10 @@ int32_t tred_destroy(tred_handle *h) {
     void *ptrs[] = {h->dep_event, h->wts2, h->pix_row, h->gspec, h->rhat, h->pair_j, h->wts, h->recs, h->effq_acc, h->dft_hi, h->dft_lo, h->zspec, h->blk_count, h->blk_slot, h->blk_fill,
                     h->scan_part, h->colmask, h->yspec, h->pix_flag, h->pix_part, h->px_possum, h->hit_cnt,
                     h->hit_tmp, h->hit_tmpc, h->status, h->tw, h->dx_bhi, h->dx_blo, h->dx_qhi, h->dx_qlo,
-                    h->dx_y, h->dx_rows, h->dx_rowstart, h->dx_meta, h->dx_pmask};
+                    h->dx_y, h->dx_rows, h->dx_rowstart, h->dx_meta, h->dx_pmask, h->dx_pcnt};
     for (void *p : ptrs)
         if (p) cudaFree(p);
+    delete h->kt;
     free(h);
     return TRED_OK;
 }
@@ -399,6 +446,51 @@ int32_t tred_param_grads(tred_handle *h, int32_t n, const float *z, const tred_d
 int32_t tred_launch_count(const tred_handle *h, int64_t *count) {
     if (!h || !count) return TRED_ERR_INVALID_ARG;
     *count = h->launches;
+    return TRED_OK;
+}
+
+int32_t tred_direct_counts(tred_handle *h, int64_t *rows, int64_t *columns) {
+    if (!h || !rows || !columns) return TRED_ERR_INVALID_ARG;
+    *rows = 0;
+    *columns = 0;
+    if (h->p.conv_mode != 4) return TRED_OK;
+    int32_t m[4] = {0, 0, 0, 0};
+    int rc = check_cuda(h, cudaMemcpy(m, h->dx_meta, sizeof m, cudaMemcpyDeviceToHost), "read direct-form counts");
+    if (rc) return rc;
+    *rows = m[1];
+    *columns = m[2];
+    return TRED_OK;
+}
+
+int32_t tred_set_kernel_timing(tred_handle *h, int32_t enable) {
+    if (!h) return TRED_ERR_INVALID_ARG;
+    if (enable && !h->kt) h->kt = new KernelTimers();
+    if (!enable && h->kt) {
+        cudaDeviceSynchronize();   // the recorded events are complete before they go
+        delete h->kt;
+        h->kt = nullptr;
+    }
+    return TRED_OK;
+}
+
+int32_t tred_kernel_time(tred_handle *h, int32_t which, double *ms, int32_t *launches) {
+    if (!h || !ms || !launches || which < 0 || which >= TRED_KT_CLASSES) return TRED_ERR_INVALID_ARG;
+    *ms = 0.0;
+    *launches = 0;
+    if (!h->kt) return TRED_OK;
+    auto &v = h->kt->pairs[which];
+    for (auto &p : v) {
+        int rc = check_cuda(h, cudaEventSynchronize(p.second), "kernel timing");
+        if (rc) return rc;
+        float t = 0.f;
+        rc = check_cuda(h, cudaEventElapsedTime(&t, p.first, p.second), "kernel timing");
+        if (rc) return rc;
+        *ms += t;
+        *launches += 1;
+        h->kt->pool.push_back(p.first);
+        h->kt->pool.push_back(p.second);
+    }
+    v.clear();
     return TRED_OK;
 }
 

@@ -67,8 +67,9 @@ struct tred_handle {
     float2 *dx_y;               // [dx_blocks][nbins][16 * 16] block output spectra
     int32_t *dx_rows;           // [dx_blocks * bp^2] row records: local slot << 6 | pixel
     int32_t *dx_rowstart;       // [dx_blocks + 1] first row of each slot, then the row count
-    int32_t *dx_meta;           // [4]: slots of the pass, rows of the pass
+    int32_t *dx_meta;           // [4]: slots of the pass, rows of the pass, non-empty columns
     uint64_t *dx_pmask;         // [dx_blocks] non-empty pixels of each slot
+    int32_t *dx_pcnt;           // [dx_blocks] non-empty columns of each slot
     int32_t dx_blocks, dx_rows_cap;
     int32_t *blk_count;    // [nblk] occupancy
     int32_t *blk_slot;     // [nblk] slot of an active block or -1
@@ -95,6 +96,7 @@ struct tred_handle {
     float2 *gspec;         // [adj_chunk][npairs][lt][64] adjoint spectra of the input pixels
     int32_t adj_chunk;
     int64_t launches;      // kernels launched through this handle (diagnostics)
+    struct KernelTimers *kt;   // per-kernel event pairs while timing is enabled (else null)
     char err[512];
 };
 
@@ -178,6 +180,11 @@ int launch_param_grads(tred_handle *h, int n, const float *z, const tred_deposit
                        float *gin, double *gglob, cudaStream_t s);
 
 int num_sms(tred_handle *h);
+
+// Per-kernel event timing (tred_set_kernel_timing): kt_begin / kt_end bracket one launch
+// of class `which` on stream s; no-ops while timing is disabled.
+void kt_begin(tred_handle *h, int which, cudaStream_t s);
+void kt_end(tred_handle *h, int which, cudaStream_t s);
 
 // ------------------------------------------------------------------ device helpers
 __device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }

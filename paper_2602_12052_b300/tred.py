@@ -200,6 +200,30 @@ def tred_sync_status(h: Handle, stream=None):
     return list(buf)
 
 
+KT_EFFQ, KT_DX_FWD, KT_DX_GEMM, KT_DX_INV = 0, 1, 2, 3
+KT_NAMES = {KT_EFFQ: "k_effq_blocks", KT_DX_FWD: "k_dx_fwd", KT_DX_GEMM: "k_dx_gemm", KT_DX_INV: "k_dx_inv"}
+
+
+def tred_set_kernel_timing(h: Handle, enable: bool) -> None:
+    h.check(h.lib.tred_set_kernel_timing(h.h, 1 if enable else 0))
+
+
+def tred_kernel_time(h: Handle, which: int):
+    """(milliseconds, launches) of one kernel class since the previous query."""
+    ms = ctypes.c_double(0.0)
+    n = ctypes.c_int32(0)
+    h.check(h.lib.tred_kernel_time(h.h, which, ctypes.byref(ms), ctypes.byref(n)))
+    return ms.value, n.value
+
+
+def tred_direct_counts(h: Handle):
+    """(non-empty rows, non-empty columns) of the last conv_mode 4 pass."""
+    r = ctypes.c_int64(0)
+    c = ctypes.c_int64(0)
+    h.check(h.lib.tred_direct_counts(h.h, ctypes.byref(r), ctypes.byref(c)))
+    return r.value, c.value
+
+
 def tred_launch_count(h: Handle) -> int:
     c = ctypes.c_int64()
     h.check(h.lib.tred_launch_count(h.h, ctypes.byref(c)))
