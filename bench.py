@@ -391,7 +391,7 @@ def run_reference(args):
 def _line(metric, value, unit, ms, args, cfg_extra, **kw):
     line = {"metric": metric, "value": value, "unit": unit, "n_gpus": 1, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": {0: "f32", 1: "tf32", 2: "tf32x3", 3: "bf16x3", 4: "f32+bf16x3"}[args.conv_mode], "data": "synthetic", "config": cfg_extra}
+            "vs_baseline": None, "dtype": kw.pop("dtype", "f32"), "data": "synthetic", "config": cfg_extra}
     line.update(kw)
     print(json.dumps(line), flush=True)
 
