@@ -115,12 +115,13 @@ __host__ __device__ __forceinline__ float dx_bf16_value(uint32_t b) {
 }
 
 // ---------------------------------------------------------------- response operand
-// R[j][n][f] = (1 / lt) sum_tau i[Ky][Kx][jy][jx][tau] exp(-2 pi i tau f / lt) in FP64
-// (n = Ky kp + Kx, j = jy ns + jx; the 1/lt of the inverse DFT folded in).
+// R[j][n][f] = (1 / (2 lt)) sum_tau i[Ky][Kx][jy][jx][tau] exp(-2 pi i tau f / lt) in FP64
+// (n = Ky kp + Kx, j = jy ns + jx; the 1/lt of the inverse DFT and the 1/2 of the
+// forward kernel's Hermitian split folded in: it stores 2 Qhat).
 __global__ void k_dx_resp_time(const float *__restrict__ resp, int nch, int ntap, int nr, int lt, int nbins,
                                const double2 *__restrict__ wlt, double2 *__restrict__ Rt) {
     const int64_t total = (int64_t)nch * ntap * nbins;
-    const double scale = 1.0 / (double)lt;
+    const double scale = 0.5 / (double)lt;
     for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < total;
          idx += (int64_t)gridDim.x * blockDim.x) {
         const int f = (int)(idx % nbins);
@@ -136,7 +137,7 @@ __global__ void k_dx_resp_time(const float *__restrict__ resp, int nch, int ntap
             re = fma(v, w.x, re);
             im = fma(v, w.y, im);
         }
-        Rt[idx] = make_double2(re * scale, im * scale);
+        Rt[idx] = make_double2(re * scale, im * scale);   // the forward kernel stores 2 Qhat
     }
 }
 
@@ -344,7 +345,10 @@ __device__ __forceinline__ void dx_zero_straddling(const int32_t *__restrict__ r
 // the CTA writes bin by bin, one lane per two pairs, the Hermitian split of their columns
 // in BF16 hi and lo parts at the GEMM's K positions.  Items (row, half) split the impacts
 // at jm = 4 ceil(nch / 8), so that each lane's four impacts lie in one group of 16.
-__device__ __forceinline__ int dx_tcol(int k, int ST) { return k * ST + ((k >> 5) & 3); }
+// first float of pair q's region (4 ST floats: Z[f] then C[f] = Z[N - f] as complex
+// numbers); the skew 2 ((q >> 3) & 3) keeps it 8-byte aligned and puts the regions of the
+// pairs 2 c4 (c4 = 0 .. 15, one lane each) in distinct banks
+__device__ __forceinline__ int dx_pbase(int q, int ST) { return 4 * q * ST + 2 * ((q >> 3) & 3); }
 
 template <int N, bool HZ>
 __device__ __forceinline__ void dx_fft_fwd(float2 (&v)[N]) {
@@ -362,7 +366,7 @@ __global__ void __launch_bounds__(DX_FWD_THREADS, 2)
     constexpr int NPL = LT / 32;
     constexpr int NW = DX_FWD_THREADS / 32;
     static_assert(NPL <= 16, "pass 2 holds 16 samples per lane");
-    extern __shared__ float T[];   // [2 jm] columns of ST bins, column k at dx_tcol(k)
+    extern __shared__ float T[];   // per pair of the half 4 ST floats at dx_pbase(pair)
     const int ST = dx_tstride(c.nbins);
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int cnt = meta[0], nrows = meta[1];
@@ -384,14 +388,12 @@ __global__ void __launch_bounds__(DX_FWD_THREADS, 2)
             const int ja = j0 + 2 * ql, jb = ja + 1;
             const bool nza = (mk[ja] >> p) & 1ull;
             const bool nzb = (mk[jb] >> p) & 1ull;
-            float *T0 = T + dx_tcol(4 * ql, ST);   // the pair's four columns, contiguous
-            float *T1 = T0 + ST, *T2 = T0 + 2 * ST, *T3 = T0 + 3 * ST;
+            float2 *Zp = reinterpret_cast<float2 *>(T + dx_pbase(ql, ST));   // Z[f], f <= N/2
+            float2 *Cp = Zp + ST;                                               // Z[N - f]
             if (!(nza || nzb)) {
                 for (int f = lane; f < c.nbins; f += 32) {
-                    T0[f] = 0.f;
-                    T1[f] = 0.f;
-                    T2[f] = 0.f;
-                    T3[f] = 0.f;
+                    Zp[f] = make_float2(0.f, 0.f);
+                    Cp[f] = make_float2(0.f, 0.f);
                 }
                 continue;
             }
@@ -406,9 +408,7 @@ __global__ void __launch_bounds__(DX_FWD_THREADS, 2)
             }
             if (hz) dx_fft_fwd<NPL, true>(v);
             else dx_fft_fwd<NPL, false>(v);
-            // the pair's region starts at an odd float where the column skew is odd: the
-            // scratch (NPL x 32 complex, 8-byte aligned) starts one float later there
-            float2 *S = reinterpret_cast<float2 *>(T0 + (dx_tcol(4 * ql, ST) & 1));
+            float2 *S = Zp;   // transpose scratch (NPL x 32 complex) in the pair's region
             __syncwarp();
 #pragma unroll
             for (int k = 0; k < NPL; ++k) {
@@ -439,20 +439,15 @@ __global__ void __launch_bounds__(DX_FWD_THREADS, 2)
 #pragma unroll
                 for (int k = 0; k < 16; ++k) {
                     const int f = d + NPL * (bitrev<16>(k) + 16 * e);
-                    if (2 * f <= LT) {
-                        T0[f] = w[k].x;
-                        T1[f] = w[k].y;
-                    } else {
-                        T2[LT - f] = w[k].x;
-                        T3[LT - f] = w[k].y;
-                    }
+                    if (2 * f <= LT) Zp[f] = w[k];
+                    else Cp[LT - f] = w[k];
                 }
             }
         }
         __syncthreads();
         // bin by bin, lane c4 = impacts j0 + 4 c4 .. + 3 (two pairs): the Hermitian split
-        // of each pair's Z[f] and Z[N - f],
-        //     Qhat[2q][f] = (Z[f] + conj Z[N - f]) / 2,   Qhat[2q+1][f] = (Z[f] - conj Z[N - f]) / 2i,
+        // of each pair's Z[f] and Z[N - f], doubled (the 1/2 is folded into R),
+        //     2 Qhat[2q][f] = Z[f] + conj Z[N - f],   2 Qhat[2q+1][f] = (Z[f] - conj Z[N - f]) / i,
         // then the four real parts at k = 32 g + i and the four imaginary parts at
         // k = 32 g + 16 + i (j = 16 g + i) as BF16 hi and lo parts (8 bytes each)
         // a warp covers 32 / lpb bins at a time (lpb lanes per bin, at least the half's units)
@@ -466,13 +461,13 @@ __global__ void __launch_bounds__(DX_FWD_THREADS, 2)
                 float re[4], im[4];
 #pragma unroll
                 for (int h2 = 0; h2 < 2; ++h2) {
-                    const float *tq = T + dx_tcol(4 * (2 * c4 + h2), ST) + f;
-                    const float zr = tq[0], zi = tq[ST];
-                    const float cr = self ? zr : tq[2 * ST], ci = self ? zi : tq[3 * ST];
-                    re[2 * h2] = 0.5f * (zr + cr);       // Qhat[2q]
-                    im[2 * h2] = 0.5f * (zi - ci);
-                    re[2 * h2 + 1] = 0.5f * (zi + ci);   // Qhat[2q + 1]
-                    im[2 * h2 + 1] = 0.5f * (cr - zr);
+                    const float2 *zq = reinterpret_cast<const float2 *>(T + dx_pbase(2 * c4 + h2, ST));
+                    const float2 z = zq[f];
+                    const float2 cz = self ? z : zq[ST + f];
+                    re[2 * h2] = z.x + cz.x;       // 2 Qhat[2q] (the 1/2 is in the response operand)
+                    im[2 * h2] = z.y - cz.y;
+                    re[2 * h2 + 1] = z.y + cz.y;   // 2 Qhat[2q + 1]
+                    im[2 * h2 + 1] = cz.x - z.x;
                 }
                 const int j = j0 + 4 * c4;
                 const size_t kr = o + 32 * (j >> 4) + (j & 15);
