@@ -252,19 +252,17 @@ __global__ void __launch_bounds__(DX_ROWS_THREADS) k_dx_rows(const int32_t *__re
                                                               int32_t *__restrict__ meta) {
     __shared__ int wsum[32];
     __shared__ int carry_s;
-    __shared__ long long ncol_s;
+    __shared__ long long wcol[32];
     const int nb = n_blocks_dev[0];
     const int cnt = max(0, min(slot_count, nb - slot_base));
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    if (tid == 0) {
-        carry_s = 0;
-        ncol_s = 0;
-    }
+    if (tid == 0) carry_s = 0;
+    long long ncol = 0;   // this thread's non-empty columns
     __syncthreads();
     for (int base = 0; base < cnt; base += DX_ROWS_THREADS) {
         const int s = base + tid;
         const uint64_t m = s < cnt ? pmask[s] : 0ull;
-        if (s < cnt) atomicAdd(reinterpret_cast<unsigned long long *>(&ncol_s), (unsigned long long)pcnt[s]);
+        if (s < cnt) ncol += pcnt[s];
         const int n = __popcll(m);
         int x = n;   // inclusive warp scan
 #pragma unroll
@@ -300,11 +298,17 @@ __global__ void __launch_bounds__(DX_ROWS_THREADS) k_dx_rows(const int32_t *__re
         if (tid == 0) carry_s = carry + wsum[31];
         __syncthreads();
     }
+#pragma unroll
+    for (int o = 16; o >= 1; o >>= 1) ncol += __shfl_xor_sync(0xffffffffu, ncol, o);
+    if (lane == 0) wcol[warp] = ncol;
+    __syncthreads();
     if (tid == 0) {
+        long long tot = 0;
+        for (int w = 0; w < DX_ROWS_THREADS / 32; ++w) tot += wcol[w];
         rowstart[cnt] = carry_s;
         meta[0] = cnt;
         meta[1] = carry_s;
-        meta[2] = (int32_t)min(ncol_s, 2147483647ll);
+        meta[2] = (int32_t)min(tot, 2147483647ll);
     }
 }
 
