@@ -425,10 +425,11 @@ def run_batched(args):
     events = synth.make_events(base, args.events, 1000, 1_000_000, seed=3003)
     ntot = sum(len(e["x"]) for e in events)
     t = time.perf_counter()
-    best, timings = autotune.autotune(base, events, resp, sample=8)
+    cm = args.conv_mode if args.conv_mode in (0, 4) else 0
+    best, timings = autotune.autotune(base, events, resp, sample=8, conv_mode=cm)
     tune_s = time.perf_counter() - t
     cfg = base.with_(bp=best[0], bt=best[1], lt=best[2])
-    sim = autotune.make_batch(cfg, events, resp, chunk_blocks=2048)
+    sim = autotune.make_batch(cfg, events, resp, chunk_blocks=2048, conv_mode=cm)
     sim.step()
     torch.cuda.synchronize()
     st = sim.status()
@@ -439,14 +440,30 @@ def run_batched(args):
     with ClockSampler(0) as clk:
         ms_graph = _timed(sim.replay, args.steps, 1)
     clocks = clk.summary()
-    # the convolution's own time, from an eager step with events around its launches
+    # the convolution's own time, from an eager step with events around its launches (and
+    # the library's per-kernel events)
     cev = []
+    tred.tred_set_kernel_timing(sim.h, True)
+    tred.tred_direct_counts(sim.h)
     sim.step(conv_events=cev)
     torch.cuda.synchronize()
     conv_ms = sum(a.elapsed_time(b) for a, b in cev)
+    kernel_ms = {}
+    for cls, name in tred.KT_NAMES.items():
+        kt, kn = tred.tred_kernel_time(sim.h, cls)
+        if kn:
+            kernel_ms[name] = kt
+    tred.tred_set_kernel_timing(sim.h, False)
+    rows_dx, cols_dx = tred.tred_direct_counts(sim.h)
     peak_meas, sms = measured_fp32_peak()
-    roof = alu_roofline("tred_convolve_range (k_conv_spec + inverse time transform), all chunks of one step",
-                        conv_flop_per_block(cfg.lt), nb, conv_ms, clocks, peak_meas)
+    if cm == 4:
+        kr = direct_rooflines(cfg, rows_dx, cols_dx, nb, kernel_ms, clocks)
+        roof = dict(kr[next(iter(kr))])
+        roof.update({"kernels": kr, "kernel_ms_per_step": kernel_ms, "rows": rows_dx, "nonempty_columns": cols_dx,
+                     "convolution_ms": conv_ms})
+    else:
+        roof = alu_roofline("tred_convolve_range (k_conv_spec + inverse time transform), all chunks of one step",
+                            conv_flop_per_block(cfg.lt), nb, conv_ms, clocks, peak_meas)
     del sim
     torch.cuda.empty_cache()
     # one event at a time through the same kernels (no graph, one launch sequence each)
@@ -454,7 +471,7 @@ def run_batched(args):
     bmax = max(autotune.probe_blocks(cfg, [e], resp)[0] for e in events)
     one = tred.BatchSimulator(cfg, resp, [events[0]], max_blocks=bmax + 8,
                               max_pixels=min(cfg.npx * cfg.npx, (bmax + 8) * (cfg.bp + cfg.kp - 1) ** 2),
-                              chunk_blocks=2048, n_events=1, max_deposits=nmax)
+                              chunk_blocks=2048, n_events=1, max_deposits=nmax, conv_mode=cm)
     per_event = []
     for e in events:
         one.load([e])
@@ -470,7 +487,10 @@ def run_batched(args):
            "active_blocks": nb, "active_pixels": npix, "hits": nh,
            "autotuned_shape": {"bp": best[0], "bt": best[1], "lt": best[2]},
            "autotune_ms_per_kdepos": {f"{k[0]}x{k[0]}x{k[1]}/lt{k[2]}": 1e3 * v for k, v in timings.items()},
-           "autotune_s": tune_s},
+           "autotune_s": tune_s,
+           "convolution": {0: "FFT form, persistent effective charge + convolution over the block queue",
+                           4: "direct spatial form (tensor-core GEMM per frequency bin), chunks of 2048 blocks"}[cm]},
+          dtype={0: "f32", 4: "f32+bf16x3"}[cm],
           events_per_s=args.events / (ms_graph / 1e3),
           per_event={"ms_total": ms_single, "depos_per_s": ntot / (ms_single / 1e3),
                      "events_per_s": args.events / (ms_single / 1e3)},
@@ -489,7 +509,9 @@ def run_lines(args):
     seg = synth.make_segments(cfg, synth.SEG_CM["module_lines"])
     resp = torch.from_numpy(synth.make_response(cfg))
     n = len(seg["x0"])
-    sim = tred.LineSimulator(cfg, resp, max_segments=n, max_blocks=6000, max_pixels=300000, effq_skip_empty=1)
+    cm = args.conv_mode if args.conv_mode in (0, 4) else 0
+    sim = tred.LineSimulator(cfg, resp, max_segments=n, max_blocks=6000, max_pixels=300000, effq_skip_empty=1,
+                             conv_mode=cm)
     x = {k: torch.from_numpy(v).cuda() for k, v in seg.items()}
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
 
@@ -517,6 +539,8 @@ def run_lines(args):
     if st[0] != 0:
         raise RuntimeError(f"device status {st}")
     rows = []
+    tred.tred_set_kernel_timing(sim.h, True)
+    tred.tred_direct_counts(sim.h)
     with ClockSampler(0) as clk:
         for _ in range(args.steps):
             flush.zero_()
@@ -524,20 +548,32 @@ def run_lines(args):
             stages(ev)
             torch.cuda.synchronize()
             rows.append([ev[i].elapsed_time(ev[i + 1]) for i in range(4)])
+    kernel_ms = {}
+    for cls, name in tred.KT_NAMES.items():
+        kt, kn = tred.tred_kernel_time(sim.h, cls)
+        if kn:
+            kernel_ms[name] = kt / args.steps
+    tred.tred_set_kernel_timing(sim.h, False)
+    rows_dx, cols_dx = (v // args.steps for v in tred.tred_direct_counts(sim.h))
     m = [statistics.mean(r[i] for r in rows) for i in range(4)]
     ms = sum(m)
     nb, npix, nh = (int(v) for v in sim.counts[:3].cpu())
     clocks = clk.summary()
     peak_meas, _ = measured_fp32_peak()
-    roof = alu_roofline("tred_convolve (k_conv_spec + k_conv_itime_mp)", conv_flop_per_block(cfg.lt), nb, m[2],
-                        clocks, peak_meas)
+    if cm == 4:
+        kr = direct_rooflines(cfg, rows_dx, cols_dx, nb, kernel_ms, clocks)
+        roof = dict(kr[next(iter(kr))])
+        roof.update({"kernels": kr, "kernel_ms_per_step": kernel_ms, "rows": rows_dx, "nonempty_columns": cols_dx})
+    else:
+        roof = alu_roofline("tred_convolve (k_conv_spec + k_conv_itime_mp)", conv_flop_per_block(cfg.lt), nb, m[2],
+                            clocks, peak_meas)
     _line("line segments/s to pixel currents (Eq. qline effective charge)", n / (ms / 1e3), "segments/s", ms, args,
           {"workload": f"module_lines: {n} segments of 3 mm from 200 tracks, 512x512 px x 6400 ticks, GL-2, "
                        "9x9x10x10x200 response, 8x8x256 blocks",
            "active_blocks": nb, "active_pixels": npix, "hits": nh,
            "l2": "flushed between timed steps"},
           stages_ms={"drift+blockbin": m[0], "effq_lines": m[1], "convolve": m[2], "gather+readout": m[3]},
-          clocks=clocks, roofline=roof,
+          clocks=clocks, roofline=roof, dtype={0: "f32", 4: "f32+bf16x3"}[cm],
           cpu_baseline=None if args.no_cpu_baseline else _lines_cpu(cfg, seg, resp.numpy()))
 
 
@@ -799,6 +835,7 @@ def run_sizes(args):
     resp = synth.make_response(base)
     dev = torch.device("cuda")
     rows = []
+    cm = args.conv_mode if args.conv_mode in (0, 4) else 0
     clk = ClockSampler(0).__enter__()
     for n_target in (1000, 3000, 10000, 30000, 100000, 300000, 1000000):
         cfg = base.with_(n_tracks=0, min_deposits=n_target)
@@ -807,7 +844,7 @@ def run_sizes(args):
         n = len(dep["x"])
         max_blocks, max_pixels = probe_capacities(cfg, dep, dev)
         sim = tred.Simulator(cfg, torch.from_numpy(resp), max_deposits=n, max_blocks=max_blocks,
-                             max_pixels=max_pixels, effq_skip_empty=1, device=dev)
+                             max_pixels=max_pixels, effq_skip_empty=1, device=dev, conv_mode=cm)
         x = {k: torch.from_numpy(v).to(dev) for k, v in dep.items()}
         sim.step(n, x["x"], x["y"], x["z"], x["t0"], x["ne"])
         torch.cuda.synchronize()
@@ -831,7 +868,8 @@ def run_sizes(args):
     _line("step time vs event size, module plane, CUDA graph replay (runtime vs input size)", big["depos_per_s"],
           "depos/s", big["ms"], args,
           {"workload": "one module-plane event (512x512 px x 6400 ticks) of 1e3 .. 1e6 deposits, 8x8x256 blocks"},
-          rows=rows, clocks=clk.summary())
+          rows=rows, clocks=clk.summary(), dtype={0: "f32", 4: "f32+bf16x3"}[cm],
+          convolution={0: "FFT form", 4: "direct spatial form (tensor-core GEMM per frequency bin)"}[cm])
 
 
 def main():
@@ -931,6 +969,7 @@ def main():
     launches0 = tred.tred_launch_count(sim.h)
     # per-kernel CUDA events on the launching stream (library-side) over the timed steps
     tred.tred_set_kernel_timing(sim.h, True)
+    tred.tred_direct_counts(sim.h)   # resets the row and column sums
     with ClockSampler(local) as clk:
         time.sleep(0.3)
         for k in range(args.steps):
@@ -944,7 +983,7 @@ def main():
         if kn:
             kernel_ms[name] = kt / args.steps
     tred.tred_set_kernel_timing(sim.h, False)
-    rows_dx, cols_dx = tred.tred_direct_counts(sim.h)
+    rows_dx, cols_dx = (v // args.steps for v in tred.tred_direct_counts(sim.h))
     clocks = clk.summary()
     if world > 1:
         torch.distributed.barrier()

@@ -182,8 +182,9 @@ enum {
 };
 int32_t tred_set_kernel_timing(tred_handle *h, int32_t enable);
 /* conv_mode 4 diagnostics: the non-empty (block, pixel) rows and the non-empty columns of
- * those rows in the last pass of tred_convolve (device counts copied to the host, so the
- * call synchronises the device); 0 and 0 for the other modes. */
+ * those rows summed over every tred_convolve / tred_convolve_range pass since the previous
+ * call (which resets the sums; device counts copied to the host, so the call synchronises
+ * the device); 0 and 0 for the other modes. */
 int32_t tred_direct_counts(tred_handle *h, int64_t *rows, int64_t *columns);
 int32_t tred_kernel_time(tred_handle *h, int32_t which, double *ms, int32_t *launches);
 

@@ -67,28 +67,30 @@ def count_pixels(cfg, n_events, block_ids):
     return int(flags.sum())
 
 
-def make_batch(cfg, events, resp, chunk_blocks=2048, device=None, persistent=None):
-    """A BatchSimulator sized to the batch; persistent (default: whenever the FFT length
-    allows it, lt = 384 or 512) runs the effective charge and the convolution as one
-    persistent launch over the batch's active-block queue."""
+def make_batch(cfg, events, resp, chunk_blocks=2048, device=None, persistent=None, conv_mode=0):
+    """A BatchSimulator sized to the batch; in the FFT form (conv_mode 0) persistent
+    (default: whenever the FFT length allows it, lt = 384 or 512) runs the effective charge
+    and the convolution as one persistent launch over the batch's active-block queue; the
+    direct form (conv_mode 4) runs chunks of chunk_blocks slots."""
     nb, npix = probe_blocks(cfg, events, resp, device)
     if persistent is None:
-        persistent = cfg.lt in (384, 512)
+        persistent = cfg.lt in (384, 512) and conv_mode == 0
     return tred.BatchSimulator(cfg, resp, events, max_blocks=nb + 8, max_pixels=npix,
-                               chunk_blocks=chunk_blocks, device=device, persistent=persistent)
+                               chunk_blocks=chunk_blocks, device=device, persistent=persistent,
+                               conv_mode=conv_mode)
 
 
-def autotune(cfg, events, resp, candidates=CANDIDATES, sample=8, device=None):
+def autotune(cfg, events, resp, candidates=CANDIDATES, sample=8, device=None, conv_mode=0):
     """Return ((bp, bt, lt), {shape: ms per deposit}) measured on the first `sample` events
     (each shape in the form make_batch gives it: persistent at lt = 384 and 512)."""
     evs = events[:sample]
     n = sum(len(e["x"]) for e in evs)
     timings = {}
     for bp, bt, lt in candidates:
-        if not valid(cfg, bp, bt, lt):
+        if not valid(cfg, bp, bt, lt) or (conv_mode == 4 and lt not in (384, 512)):
             continue
         c = cfg.with_(bp=bp, bt=bt, lt=lt)
-        sim = make_batch(c, evs, resp, device=device)
+        sim = make_batch(c, evs, resp, device=device, conv_mode=conv_mode)
         sim.step()
         torch.cuda.synchronize()
         t = time.perf_counter()

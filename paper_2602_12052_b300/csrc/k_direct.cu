@@ -242,7 +242,8 @@ __global__ void k_dx_pixmask(const int32_t *__restrict__ n_blocks_dev, const uin
 }
 
 // One CTA: exclusive scan of the slots' pixel counts (rowstart), the row records in slot
-// then pixel order, meta = {slots of the pass, rows of the pass, non-empty columns}.
+// then pixel order, meta = {slots of the pass, rows of the pass, non-empty columns, -,
+// running totals of rows and columns (two 64-bit words)}.
 constexpr int DX_ROWS_THREADS = 1024;
 __global__ void __launch_bounds__(DX_ROWS_THREADS) k_dx_rows(const int32_t *__restrict__ n_blocks_dev,
                                                               const uint64_t *__restrict__ pmask,
@@ -309,6 +310,10 @@ __global__ void __launch_bounds__(DX_ROWS_THREADS) k_dx_rows(const int32_t *__re
         meta[0] = cnt;
         meta[1] = carry_s;
         meta[2] = (int32_t)min(tot, 2147483647ll);
+        // running totals over the passes since the host last read them
+        unsigned long long *acc = reinterpret_cast<unsigned long long *>(meta + 4);
+        atomicAdd(&acc[0], (unsigned long long)carry_s);
+        atomicAdd(&acc[1], (unsigned long long)tot);
     }
 }
 

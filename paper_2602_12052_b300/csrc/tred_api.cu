@@ -293,7 +293,8 @@ int32_t tred_create(const tred_geometry *geom, const tred_params *params, int32_
         alloc((void **)&h->dx_y, sizeof(float2) * (size_t)h->dx_blocks * nbins * LP * LP, "alloc direct-form output");
         alloc((void **)&h->dx_rows, sizeof(int32_t) * (size_t)h->dx_blocks * bp2, "alloc direct-form rows");
         alloc((void **)&h->dx_rowstart, sizeof(int32_t) * ((size_t)h->dx_blocks + 2), "alloc direct-form rows");
-        alloc((void **)&h->dx_meta, sizeof(int32_t) * 4, "alloc direct-form rows");
+        alloc((void **)&h->dx_meta, sizeof(int32_t) * 8, "alloc direct-form rows");
+        if (rc == TRED_OK) rc = check_cuda(h, cudaMemset(h->dx_meta, 0, sizeof(int32_t) * 8), "clear direct-form rows");
         alloc((void **)&h->dx_pmask, sizeof(uint64_t) * (size_t)h->dx_blocks, "alloc direct-form masks");
         alloc((void **)&h->dx_pcnt, sizeof(int32_t) * (size_t)h->dx_blocks, "alloc direct-form counts");
     } else {
@@ -454,11 +455,12 @@ int32_t tred_direct_counts(tred_handle *h, int64_t *rows, int64_t *columns) {
     *rows = 0;
     *columns = 0;
     if (h->p.conv_mode != 4) return TRED_OK;
-    int32_t m[4] = {0, 0, 0, 0};
-    int rc = check_cuda(h, cudaMemcpy(m, h->dx_meta, sizeof m, cudaMemcpyDeviceToHost), "read direct-form counts");
+    unsigned long long acc[2] = {0, 0};
+    int rc = check_cuda(h, cudaMemcpy(acc, h->dx_meta + 4, sizeof acc, cudaMemcpyDeviceToHost), "read direct-form counts");
+    if (!rc) rc = check_cuda(h, cudaMemset(h->dx_meta + 4, 0, sizeof acc), "reset direct-form counts");
     if (rc) return rc;
-    *rows = m[1];
-    *columns = m[2];
+    *rows = (int64_t)acc[0];
+    *columns = (int64_t)acc[1];
     return TRED_OK;
 }
 

@@ -67,7 +67,7 @@ struct tred_handle {
     float2 *dx_y;               // [dx_blocks][nbins][16 * 16] block output spectra
     int32_t *dx_rows;           // [dx_blocks * bp^2] row records: local slot << 6 | pixel
     int32_t *dx_rowstart;       // [dx_blocks + 1] first row of each slot, then the row count
-    int32_t *dx_meta;           // [4]: slots of the pass, rows of the pass, non-empty columns
+    int32_t *dx_meta;           // [8]: slots, rows and non-empty columns of the pass; at 4: running totals (2 x 64 bit)
     uint64_t *dx_pmask;         // [dx_blocks] non-empty pixels of each slot
     int32_t *dx_pcnt;           // [dx_blocks] non-empty columns of each slot
     int32_t dx_blocks, dx_rows_cap;

@@ -448,9 +448,10 @@ class BatchSimulator:
 
     Events are stacked along y (geometry n_events); every kernel runs once per step
     as a persistent grid over the global active-block list of all events.  With
-    ``persistent`` (lt = 384 or 512) the effective charge and the convolution are one
-    persistent launch over that list (tred_effq_convolve), Q^eff staged in one ring row
-    per resident CTA; otherwise they run over sub-batches of ``chunk_blocks`` slots
+    ``persistent`` (lt = 384 or 512, the FFT form) the effective charge and the convolution
+    are one persistent launch over that list (tred_effq_convolve), Q^eff staged in one ring
+    row per resident CTA; otherwise (and always with ``conv_mode`` 4, the direct spatial
+    form) they run over sub-batches of ``chunk_blocks`` slots
     so that Q^eff never needs more than one chunk of device memory.  The launch
     sequence is fixed (the block count stays on the device), so ``capture()`` can
     record a step in a CUDA graph."""
@@ -458,14 +459,17 @@ class BatchSimulator:
     def __init__(self, cfg, resp: torch.Tensor, events, max_blocks: int, max_pixels: int,
                  chunk_blocks: int = 2048, max_hits: int | None = None, mpcp=1, device=None,
                  n_events: int | None = None, max_deposits: int | None = None, persistent: bool = False,
-                 effq_skip_empty: int = 0):
+                 effq_skip_empty: int = 0, conv_mode: int = 0):
         self.cfg = cfg
         self.device = d = torch.device(device or "cuda")
         self.n_events = n_events or len(events)
         cap = max_deposits or int(sum(len(e["x"]) for e in events))
-        self.persistent = bool(persistent)
-        skip = 1 if self.persistent else effq_skip_empty
-        self.h = Handle(geometry(cfg, self.n_events), params(cfg, mpcp=mpcp, effq_skip_empty=skip), max(cap, 1),
+        # the persistent launch runs the FFT form; the direct form (conv_mode 4) runs the
+        # chunks and reads only the covered columns
+        self.persistent = bool(persistent) and conv_mode == 0
+        skip = 1 if (self.persistent or conv_mode == 4) else effq_skip_empty
+        self.h = Handle(geometry(cfg, self.n_events),
+                        params(cfg, mpcp=mpcp, effq_skip_empty=skip, conv_mode=conv_mode), max(cap, 1),
                         max_blocks, max_pixels)
         self.rp = readout_params(cfg)
         if self.persistent:

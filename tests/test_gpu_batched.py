@@ -15,10 +15,11 @@ def _tiny_events(k, cfg):
     return [synth.make_deposits(cfg, seed=cfg.seed + 1000 * i) for i in range(k)]
 
 
-def _batch(cfg, events, resp, chunk, persistent=False):
+def _batch(cfg, events, resp, chunk, persistent=False, conv_mode=0):
     import torch
     from paper_2602_12052_b300 import autotune
-    sim = autotune.make_batch(cfg, events, torch.from_numpy(resp), chunk_blocks=chunk, persistent=persistent)
+    sim = autotune.make_batch(cfg, events, torch.from_numpy(resp), chunk_blocks=chunk, persistent=persistent,
+                              conv_mode=conv_mode)
     sim.step()
     torch.cuda.synchronize()
     return sim
@@ -45,15 +46,17 @@ def _results(sim):
             "hit_charge": sim.hit_charge[:nh].cpu().numpy()}
 
 
-@pytest.mark.parametrize("chunk,persistent", [(3, False), (64, False), (0, True)])
-def test_batch_matches_oracle_per_event(chunk, persistent):
+@pytest.mark.parametrize("chunk,persistent,conv_mode", [(3, False, 0), (64, False, 0), (0, True, 0),
+                                                       (3, False, 4), (64, False, 4)])
+def test_batch_matches_oracle_per_event(chunk, persistent, conv_mode):
     """Eight events of uneven size (one empty, one with a single deposit) through the
     batched path, against the oracle run on each event alone: sub-batches of 3 or 64
-    slots, or the one persistent launch over the batch's active-block queue."""
+    slots, or the one persistent launch over the batch's active-block queue; the FFT form
+    and the direct spatial form (conv_mode 4) of the convolution."""
     cfg = synth.get_config("tiny")
     resp = synth.make_response(cfg)
     events = _uneven_tiny_events(cfg)
-    sim = _batch(cfg, events, resp, chunk or 64, persistent)
+    sim = _batch(cfg, events, resp, chunk or 64, persistent, conv_mode)
     assert sim.persistent == persistent
     assert sim.status()[0] == 0
     res = _results(sim)
