@@ -789,12 +789,15 @@ def run_binsize(args):
     dev = torch.device("cuda")
     x = {k: torch.from_numpy(v).to(dev) for k, v in dep.items()}
     rows = []
+    cm = args.conv_mode if args.conv_mode in (0, 4) else 0
     clk = ClockSampler(0).__enter__()
     for bt, lt in ((64, 384), (128, 384), (256, 512), (320, 768), (640, 1024)):
+        if cm == 4 and lt not in (384, 512):
+            continue   # the direct form's time DFT lengths
         cfg = base.with_(bt=bt, lt=lt)
         max_blocks, max_pixels = probe_capacities(cfg, dep, dev)
         sim = tred.Simulator(cfg, torch.from_numpy(resp), max_deposits=n, max_blocks=max_blocks,
-                             max_pixels=max_pixels, effq_skip_empty=1, device=dev)
+                             max_pixels=max_pixels, effq_skip_empty=1, device=dev, conv_mode=cm)
 
         def binning():
             tred.tred_drift(sim.h, n, x["x"], x["y"], x["z"], x["t0"], x["ne"], sim.deps)
@@ -819,7 +822,8 @@ def run_binsize(args):
     _line("depos/s vs time-bin (block) length, module-plane event (bin-size study)", best["depos_per_s"],
           "depos/s", best["step_ms"], args,
           {"workload": f"module1M event, {n} deposits, 8x8-pixel blocks, bt = 64 ... 640 ticks"},
-          rows=rows, clocks=clk.summary())
+          rows=rows, clocks=clk.summary(), dtype={0: "f32", 4: "f32+bf16x3"}[cm],
+          convolution={0: "FFT form", 4: "direct spatial form (tensor-core GEMM per frequency bin)"}[cm])
 
 
 def run_sizes(args):
