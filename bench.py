@@ -131,7 +131,7 @@ def _peaks():
         return {}
 
 
-def direct_rooflines(cfg, rows, cols, blocks, kms, clocks):
+def direct_rooflines(cfg, rows, cols, blocks, kms, clocks, pixels=0):
     """Roofline objects of the direct form's kernels (conv_mode 4) and of the effective
     charge, each from its algorithmic work per step over its CUDA-event time (kms: kernel
     name -> ms per step); the dominant (longest) one first.
@@ -140,7 +140,9 @@ def direct_rooflines(cfg, rows, cols, blocks, kms, clocks):
       k_dx_fwd   HBM: the rows' non-empty Q^eff columns read (bt x 4 B each), their
                  spectra written (rows x (lt/2 + 1) bins x kq x 2 parts x 2 B)
       k_dx_inv   HBM: the block spectra read (blocks x bins x 256 x 8 B), the block
-                 outputs written (blocks x 256 x lt x 4 B)"""
+                 outputs written (blocks x 256 x lt x 4 B)
+      k_dx_wave  HBM: the block spectra read (blocks x bins x 256 x 8 B), the pixel
+                 waveforms written (pixels x nt x 4 B)"""
     pk = _peaks()
     hbm = pk.get("hbm_gbs", 6400.0)
     bf16 = pk.get("bf16_tflops_sustained", 1400.0)
@@ -166,6 +168,11 @@ def direct_rooflines(cfg, rows, cols, blocks, kms, clocks):
         a = by / (kms["k_dx_inv"] / 1e3) / 1e9
         out["k_dx_inv"] = {"bound": "hbm", "achieved": a, "peak": hbm, "unit": "GB/s", "frac": a / hbm,
                            "bytes_per_step": by, "ms": kms["k_dx_inv"], "peak_source": f"copy bandwidth, {src}"}
+    if kms.get("k_dx_wave"):
+        by = blocks * nbins * 256 * 8.0 + pixels * cfg.nt * 4.0
+        a = by / (kms["k_dx_wave"] / 1e3) / 1e9
+        out["k_dx_wave"] = {"bound": "hbm", "achieved": a, "peak": hbm, "unit": "GB/s", "frac": a / hbm,
+                            "bytes_per_step": by, "ms": kms["k_dx_wave"], "peak_source": f"copy bandwidth, {src}"}
     for k, r in out.items():
         r["kernel"] = k
         unit = "row" if k in ("k_dx_fwd", "k_dx_gemm") else "block"
@@ -232,6 +239,9 @@ def _args():
                     help="0: trigger-reset (default); 1: successive digitisations without resets "
                          "(--n-samples per trigger); 2: fixed-charge integration")
     ap.add_argument("--n-samples", type=int, default=3, help="digitisations per trigger in readout mode 1")
+    ap.add_argument("--fuse-gather", type=int, default=1, choices=[0, 1],
+                    help="conv_mode 4: the inverse time DFT fused with the electrode gather "
+                         "(tred_convolve_gather_readout) where the block shape allows it")
     ap.add_argument("--fused", type=int, default=0, choices=[0, 1],
                     help="step mode: 1 = the effective charge and the convolution as one persistent launch "
                          "over the active-block queue (tred_effq_convolve)")
@@ -912,6 +922,8 @@ def main():
     sim = tred.Simulator(cfg, torch.from_numpy(resp), max_deposits=n, max_blocks=max_blocks,
                          max_pixels=max_pixels, max_hits=max_hits, conv_mode=args.conv_mode,
                          effq_skip_empty=1 if args.conv_mode in (0, 4) else 0, device=dev, fused=fused)
+    # conv_mode 4: the inverse time DFT fused with the gather when the shape allows it
+    fg = bool(args.fuse_gather) and args.conv_mode == 4 and tred.tred_convolve_gather_supported(sim.h)
     # response spectrum, timed separately (once per response)
     torch.cuda.synchronize()
     t = time.perf_counter()
@@ -926,10 +938,13 @@ def main():
     stage_names = ["drift", "blockbin", "effq", "convolve", "gather+readout"]
     if fused:
         stage_names = ["drift", "blockbin", "effq_weights", "effq+convolve", "gather+readout"]
+    if fg:
+        stage_names = ["drift", "blockbin", "effq", "convolve+gather+readout"]
+    n_ev = len(stage_names) + 1
 
     def step(events=None):
         h = sim.h
-        ev = events or [None] * 6
+        ev = events or [None] * n_ev
 
         def rec(i):
             if ev[i] is not None:
@@ -948,6 +963,12 @@ def main():
             tred.tred_effq(h, n, sim.deps, sim.block_ids, sim.dep_offsets, sim.dep_index,
                            sim.n_blocks_dev, sim.qeff)
             rec(3)
+            if fg:   # a4 + a5 + a6: spectra, pixel list, inverse DFT per pixel tile into the waves, readout
+                tred.tred_convolve_gather_readout(h, sim.block_ids, sim.n_blocks_dev, sim.qeff, sim.pixel_ids,
+                                                  sim.waveforms, sim.n_pixels_dev, sim.rp, sim.hit_pixel,
+                                                  sim.hit_tick, sim.hit_charge, sim.n_hits_dev)
+                rec(4)
+                return
             tred.tred_convolve(h, sim.block_ids, sim.n_blocks_dev, sim.qeff, sim.out_blocks)
         rec(4)
         # a5 + a6: the electrode gather and the readout in one call (the readout skips the
@@ -969,7 +990,7 @@ def main():
     if world > 1:
         torch.distributed.barrier()
     torch.cuda.synchronize()
-    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(6)] for _ in range(args.steps)]
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(n_ev)] for _ in range(args.steps)]
     launches0 = tred.tred_launch_count(sim.h)
     # per-kernel CUDA events on the launching stream (library-side) over the timed steps
     tred.tred_set_kernel_timing(sim.h, True)
@@ -991,7 +1012,7 @@ def main():
     clocks = clk.summary()
     if world > 1:
         torch.distributed.barrier()
-    step_ms = [evs[k][0].elapsed_time(evs[k][5]) for k in range(args.steps)]
+    step_ms = [evs[k][0].elapsed_time(evs[k][n_ev - 1]) for k in range(args.steps)]
     stage_ms = {nm: statistics.mean(evs[k][i].elapsed_time(evs[k][i + 1]) for k in range(args.steps))
                 for i, nm in enumerate(stage_names)}
     ms = statistics.mean(step_ms)
@@ -1064,9 +1085,9 @@ def main():
                "d2h_what": ("the device counts and the capacity-sized hit lists (pixel, tick, charge); "
                             "the pixel waveforms stay in device memory")}
 
-    conv_ms = stage_ms["effq+convolve" if fused else "convolve"]
+    conv_ms = stage_ms["effq+convolve" if fused else "convolve+gather+readout" if fg else "convolve"]
     if args.conv_mode == 4:
-        kr = direct_rooflines(cfg, rows_dx, cols_dx, nb, kernel_ms, clocks)
+        kr = direct_rooflines(cfg, rows_dx, cols_dx, nb, kernel_ms, clocks, npix)
         dom = next(iter(kr))
         roofline = dict(kr[dom])
         roofline["kernels"] = kr
@@ -1119,6 +1140,8 @@ def main():
                                            "pixels that hold charge")}[args.conv_mode]
                                     + {0: "", 1: f", readout: {cfg.n_samples} successive digitisations per trigger",
                                        2: ", readout: fixed-charge quanta"}[args.readout_mode]
+                                    + (", inverse time DFT per 8x8 pixel tile straight into the pixel "
+                                       "waveforms (no per-block output buffer)" if fg else "")
                                     + (", effective charge and convolution in one persistent launch over the "
                                        "active-block queue (Q^eff in per-CTA ring rows)" if fused else "")),
                        "deposits": n, "active_blocks": nb, "active_pixels": npix, "hits": nh,

@@ -171,14 +171,17 @@ int32_t tred_launch_count(const tred_handle *h, int64_t *count);
  * for the recorded events, returns the summed milliseconds and the launch count of class
  * `which` since the previous call for that class (or since enabling), and forgets them.
  *   which: TRED_KT_EFFQ (effective charge, k_effq_blocks), TRED_KT_DX_FWD, TRED_KT_DX_GEMM,
- *          TRED_KT_DX_INV (the forward DFT, GEMM and inverse DFT of conv_mode 4).
+ *          TRED_KT_DX_INV (the forward DFT, GEMM and inverse DFT of conv_mode 4),
+ *          TRED_KT_DX_WAVE (the inverse DFT fused with the gather, k_dx_wave, of
+ *          tred_convolve_gather_readout).
  * TRED_ERR_INVALID_ARG for a class outside the list or null outputs. */
 enum {
     TRED_KT_EFFQ = 0,
     TRED_KT_DX_FWD = 1,
     TRED_KT_DX_GEMM = 2,
     TRED_KT_DX_INV = 3,
-    TRED_KT_CLASSES = 4
+    TRED_KT_DX_WAVE = 4,
+    TRED_KT_CLASSES = 5
 };
 int32_t tred_set_kernel_timing(tred_handle *h, int32_t enable);
 /* conv_mode 4 diagnostics: the non-empty (block, pixel) rows and the non-empty columns of
@@ -381,6 +384,32 @@ int32_t tred_gather_readout(tred_handle *h, const int32_t *block_ids, const int3
                             int32_t *n_pixels_dev, const tred_readout_params *rp, int32_t *hit_pixel,
                             int32_t *hit_tick, float *hit_charge, int32_t *n_hits_dev, int32_t max_hits,
                             void *stream);
+
+/* a4 + a5 (+ a6) for the direct spatial form without the per-block output buffer
+ * (Sec. II-D, Eq. interlaced; Fig. flowchart: binning and accumulation onto the unique
+ * electrodes).  The convolution runs as tred_convolve up to each block's output spectrum
+ * Ihat[slot][f][P] (kept in the handle); the pixel list is built as tred_gather_pixels
+ * builds it; then each 8 x 8 pixel tile offset by R from the block grid (all its pixels
+ * lie in the footprints of the same 2 x 2 spatial blocks) sums, per time block, the
+ * spectra of those blocks and takes one inverse DFT per pixel straight into the pixel's
+ * waveform row, adding each time block's first nr - 1 ticks onto the previous one's tail.
+ * The waveforms equal tred_convolve + tred_gather_pixels up to FP32 rounding order (the
+ * spatial sum is taken on the spectra; every sum has a fixed order, so the result is
+ * deterministic).  With rp non-null the readout (as tred_readout) follows; rp null
+ * skips it (hit arguments may then be null).
+ *  - qeff: as tred_convolve; pixel_ids [max_pixels], waveforms [max_pixels][nt],
+ *    n_pixels_dev[0] = npix as tred_gather_pixels; hit buffers as tred_readout.
+ *  - Shapes: conv_mode 4, bp = 8, kp = bp + 1, nr - 1 <= bt, nt / bt <= 128,
+ *    max_blocks <= the direct form's slots per pass (16384), compensated_gather 0;
+ *    TRED_ERR_INVALID_ARG otherwise (tred_convolve_gather_supported says beforehand).
+ *  Graph-capturable (counts stay on the device). */
+int32_t tred_convolve_gather_readout(tred_handle *h, const int32_t *block_ids, const int32_t *n_blocks_dev,
+                                     const float *qeff, int32_t *pixel_ids, float *waveforms,
+                                     int32_t *n_pixels_dev, const tred_readout_params *rp, int32_t *hit_pixel,
+                                     int32_t *hit_tick, float *hit_charge, int32_t *n_hits_dev, int32_t max_hits,
+                                     void *stream);
+/* 1 when the handle's shape allows tred_convolve_gather_readout, else 0 (-1 for null). */
+int32_t tred_convolve_gather_supported(const tred_handle *h);
 
 /* ---- Differentiable simulation (Sec. V-C).  Loss L = 1/2 sum (I - I*)^2 over
  * pixels and ticks; gradients through the whole path with the raster windows held

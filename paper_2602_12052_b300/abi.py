@@ -36,6 +36,7 @@ EXPORTS = [
     "tred_set_transport", "tred_residual", "tred_adjoint", "tred_param_grads",
     "tred_drift_events", "tred_effq_range", "tred_convolve_range", "tred_drift_lines", "tred_effq_lines",
     "tred_wait_selftest", "tred_gather_readout", "tred_fp32_peak", "tred_effq_convolve",
+    "tred_convolve_gather_readout", "tred_convolve_gather_supported",
 ]
 
 
@@ -100,6 +101,9 @@ def load(path: str | None = None) -> ctypes.CDLL:
     lib.tred_wait_selftest.argtypes = [_P, ctypes.c_int64, _P]
     lib.tred_gather_readout.argtypes = [_P, _P, _P, _P, _P, _P, _P, ctypes.POINTER(ReadoutParams), _P, _P, _P, _P,
                                         _I, _P]
+    lib.tred_convolve_gather_readout.argtypes = [_P, _P, _P, _P, _P, _P, _P, ctypes.POINTER(ReadoutParams), _P, _P,
+                                                 _P, _P, _I, _P]
+    lib.tred_convolve_gather_supported.argtypes = [_P]
     lib.tred_set_response.argtypes = [_P, _P, _P]
     lib.tred_drift.argtypes = [_P, _I, _P, _P, _P, _P, _P, ctypes.POINTER(Deposits), _P]
     lib.tred_blockbin.argtypes = [_P, _I, ctypes.POINTER(Deposits), _P, _P, _P, _P, _I, _P, _P]

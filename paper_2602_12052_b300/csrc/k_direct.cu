@@ -54,7 +54,7 @@ constexpr int DX_M = 128;                // rows of one GEMM tile
 constexpr int DX_KC = 64;                // K chunk: 64 BF16 = one 128-byte row (128-byte swizzle), two groups
 constexpr int DX_STAGES = 2;             // operand stages
 constexpr int DX_ROWS_MAX = 131072;      // rows per forward + GEMM launch pair
-constexpr int DX_BLOCKS_MAX = 8192;      // slots per pass
+constexpr int DX_BLOCKS_MAX = 16384;     // slots per pass
 constexpr int DX_FWD_THREADS = 256;
 constexpr int DX_INV_THREADS = 256;
 constexpr int DX_GEMM_THREADS = 320;     // warp 0 copies, warp 1 products, warps 2..9 epilogue
@@ -967,6 +967,289 @@ __global__ void __launch_bounds__(DX_INV_THREADS, 2)
     }
 }
 
+// ---------------------------------------------------------------- inverse time DFT + gather
+// The inverse time DFT and the electrode gather (a5) in one kernel, for block shapes with
+// kp = bp + 1 (R = bp / 2; bp = 8) and nr - 1 <= bt.  The pixel plane is cut into 8 x 8
+// tiles offset by R from the block grid; every pixel of a tile lies in the output
+// footprints of the same 2 x 2 spatial blocks (bx, by) in {tx, tx + 1} x {ty, ty + 1}, at
+// u = pixel - (bp b - R).  CTAs take tiles from a queue.  Per tile, 16 pixels at a time
+// (group g: the 8 columns of rows 2 g and 2 g + 1) and per time block bt in ascending
+// order: the spectra of the active blocks of the 2 x 2 set are summed per bin (first the
+// lowest-numbered active block, then the others in order; the first one's loads are issued
+// while the previous item is transformed) and staged [pixel][f]; warp w inverts its two
+// vertical neighbours (column w) as one complex sequence (the two-pass FFT of k_dx_inv).
+// Ticks t < bt of the result, plus what time block bt - 1 left for t < nr - 1, are the
+// final values of ticks bt bt_len + t: assembled in the warp's tick buffer (shared memory)
+// and written to the waveform rows once, with 16-byte stores; ticks bt .. bt + nr - 2 (the
+// tail) then move to the front of the buffer for time block bt + 1.  Time blocks with no
+// active block in the set cost no transform: their ticks are the previous tail or zero.  Every tick of an active pixel's row is written; each pixel belongs to one
+// warp, so every sum has a fixed order.  The per-pixel sum of the positive current
+// (readout bound) is kept per lane and reduced per pixel in a fixed order.
+constexpr int DX_NBT_MAX = 128;   // time blocks per event the fused gather handles
+struct DxWaveConst {
+    int npx_x, npy_e, nby_e, nbx, nbt, n_events, bp, bt, nr, nt;
+};
+// per-warp tick buffer of one pixel: lt ticks (bt <= lt) and a 16-float gap after the
+// first 16 NPL ticks, so that the lanes of the two halves of a transform (ticks t and
+// t + 16 NPL) write distinct banks
+#define DX_BUFW(G) (64 * (G) + 16)
+template <int NPL>
+__device__ __forceinline__ int dx_bpos(int t) { return t + (t >= 16 * NPL ? 16 : 0); }
+__host__ __device__ constexpr size_t dx_wave_smem(int G) {
+    // staged spectra [16][32 G + 1], transpose scratch [8 warps][64 G], tick buffers [8][2][64 G + 16]
+    return sizeof(float2) * ((size_t)16 * (32 * G + 1) + (size_t)8 * 64 * G) + sizeof(float) * (size_t)8 * 2 * DX_BUFW(G);
+}
+template <int G>
+__global__ void __launch_bounds__(DX_INV_THREADS, 2)
+    k_dx_wave(const float2 *__restrict__ ybuf, const int32_t *__restrict__ slot_of, const int32_t *__restrict__ pix_row,
+              const int32_t *__restrict__ rowstart, const float2 *__restrict__ tw, DxWaveConst c,
+              int32_t *__restrict__ queue, float *__restrict__ wave, float *__restrict__ possum) {
+    constexpr int LT = 64 * G;
+    constexpr int NPL = LT / 32;
+    constexpr int NB = LT / 2 + 1;
+    constexpr int NW = DX_INV_THREADS / 32;
+    constexpr int NLD = (NB * 8 + DX_INV_THREADS - 1) / DX_INV_THREADS;   // 16-byte loads per thread and block
+    static_assert(NW == 8, "one column of the 8-pixel tile per warp");
+    extern __shared__ float2 dxs[];
+    __shared__ int tslot[4][DX_NBT_MAX];
+    __shared__ int nzbt[DX_NBT_MAX];   // the tile's time blocks with an active block, ascending
+    __shared__ int s_tile, s_nnz;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    float2 *Ys = dxs;                                       // [16][NB]
+    float2 *S = dxs + 16 * NB + warp * (NPL * 32);          // per-warp transpose scratch
+    float *bufa = reinterpret_cast<float *>(dxs + 16 * NB + NW * NPL * 32) + warp * (2 * DX_BUFW(G));
+    float *bufb = bufa + DX_BUFW(G);   // per warp: the two pixels' tick buffers
+    const float2 *wlt = tw + TW_LT;
+    const int d = lane >> 1, e = lane & 1;
+    const int half = c.bp >> 1;
+    const int ntx = c.nbx + 1, nty = c.nby_e + 1;
+    const int ntile = c.n_events * nty * ntx;
+    const int span = c.bt + c.nr - 1;
+    const float4 zero4 = make_float4(0.f, 0.f, 0.f, 0.f);
+    // this thread's 16-byte loads of item (g, bt), block k of the 2 x 2 set (slot sl)
+    auto load_block = [&](int g, int k, int sl, float4 *dst, bool add) {
+#pragma unroll
+        for (int i = 0; i < NLD; ++i) {
+            const int idx = tid + i * DX_INV_THREADS;   // (bin, pixel pair)
+            const int f = idx >> 3, up = idx & 7;
+            if (f < NB) {
+                // tile row 2 g + (up >> 2), columns 2 (up & 3) and + 1
+                const int uy = 2 * g + (up >> 2) + (k >> 1 ? 0 : c.bp), ux = 2 * (up & 3) + (k & 1 ? 0 : c.bp);
+                const float4 v = __ldg(reinterpret_cast<const float4 *>(
+                    ybuf + ((size_t)sl * NB + f) * (LP * LP) + uy * LP + ux));
+                if (add) {
+                    dst[i].x += v.x;
+                    dst[i].y += v.y;
+                    dst[i].z += v.z;
+                    dst[i].w += v.w;
+                } else {
+                    dst[i] = v;
+                }
+            }
+        }
+    };
+    for (;;) {
+        if (tid == 0) s_tile = atomicAdd(queue, 1);
+        __syncthreads();
+        const int tile = s_tile;
+        if (tile >= ntile) break;
+        const int ev = tile / (nty * ntx), rem = tile - ev * (nty * ntx);
+        const int ty = rem / ntx - 1, tx = rem % ntx - 1;
+        int found = 0;
+        for (int i = tid; i < 4 * c.nbt; i += DX_INV_THREADS) {
+            const int k = i / c.nbt, bt = i - k * c.nbt;
+            const int bx = tx + (k & 1), byl = ty + (k >> 1);
+            int sl = -1;
+            if (bx >= 0 && bx < c.nbx && byl >= 0 && byl < c.nby_e) {
+                sl = slot_of[((int64_t)(ev * c.nby_e + byl) * c.nbx + bx) * c.nbt + bt];
+                found |= sl >= 0;   // its pixels are active: their rows are written, zeros if need be
+                if (sl >= 0 && rowstart[sl + 1] == rowstart[sl]) sl = -1;   // no charge: no spectrum written
+            }
+            tslot[k][bt] = sl;
+        }
+        if (!__syncthreads_or(found)) continue;
+        if (warp == 0) {   // the time blocks with a spectrum, ascending
+            int base = 0;
+            for (int b0 = 0; b0 < c.nbt; b0 += 32) {
+                const int bt = b0 + lane;
+                const bool on = bt < c.nbt && (tslot[0][bt] >= 0 || tslot[1][bt] >= 0 || tslot[2][bt] >= 0 ||
+                                               tslot[3][bt] >= 0);
+                const unsigned bal = __ballot_sync(0xffffffffu, on);
+                if (on) nzbt[base + __popc(bal & ((1u << lane) - 1u))] = bt;
+                base += __popc(bal);
+            }
+            if (lane == 0) s_nnz = base;
+        }
+        __syncthreads();
+        const int nnz = s_nnz;
+        // the first active block of item (g, bt), issued ahead into pre (pre_k: its index)
+        float4 pre[NLD];
+        int pre_k = -1;
+        auto prefetch = [&](int g, int bt) {
+            pre_k = tslot[0][bt] >= 0 ? 0 : tslot[1][bt] >= 0 ? 1 : tslot[2][bt] >= 0 ? 2 : 3;
+            load_block(g, pre_k, tslot[pre_k][bt], pre, false);
+        };
+        if (nnz > 0) prefetch(0, nzbt[0]);
+        // this warp's pixels: column w of the tile, rows 2 g (a) and 2 g + 1 (b)
+        const int x = c.bp * tx + half + warp;
+#pragma unroll 1
+        for (int g = 0; g < 4; ++g) {
+            int ra = -1, rb = -1;
+            {
+                const int ya = c.bp * ty + half + 2 * g, yb = ya + 1;
+                const bool inx = x >= 0 && x < c.npx_x;
+                if (inx && ya >= 0 && ya < c.npy_e) ra = pix_row[(int64_t)(ev * c.npy_e + ya) * c.npx_x + x];
+                if (inx && yb >= 0 && yb < c.npy_e) rb = pix_row[(int64_t)(ev * c.npy_e + yb) * c.npx_x + x];
+            }
+            float *wa = ra >= 0 ? wave + (size_t)ra * c.nt : nullptr;
+            float *wb = rb >= 0 ? wave + (size_t)rb * c.nt : nullptr;
+            float pa = 0.f, pb = 0.f;
+            bool live = false;   // the buffer's front holds time block bt - 1's tail
+            int jn = 0;          // next entry of nzbt
+            for (int bt = 0; bt < c.nbt; ++bt) {
+                const bool act = jn < nnz && nzbt[jn] == bt;
+                float2 w[16];
+                if (act) {
+                    ++jn;
+                    __syncthreads();   // the previous item's reads of Ys are done
+#pragma unroll
+                    for (int k = 1; k < 4; ++k) {   // the other active blocks, in order
+                        const int sl = tslot[k][bt];
+                        if (k > pre_k && sl >= 0) load_block(g, k, sl, pre, true);
+                    }
+#pragma unroll
+                    for (int i = 0; i < NLD; ++i) {
+                        const int idx = tid + i * DX_INV_THREADS;
+                        const int f = idx >> 3, up = idx & 7;
+                        if (f < NB) {
+                            const int pr = (up >> 2) * 8 + 2 * (up & 3);   // staged row of the first pixel
+                            Ys[pr * NB + f] = make_float2(pre[i].x, pre[i].y);
+                            Ys[(pr + 1) * NB + f] = make_float2(pre[i].z, pre[i].w);
+                        }
+                    }
+                    __syncthreads();
+                    {   // the next item's first block, in flight during this transform
+                        const int gn = jn < nnz ? g : g + 1, jj = jn < nnz ? jn : 0;
+                        if (gn < 4) prefetch(gn, nzbt[jj]);
+                    }
+                    const float2 *ya = Ys + warp * NB, *ybb = Ys + (warp + 8) * NB;
+                    float2 v[NPL];
+#pragma unroll
+                    for (int m = 0; m < NPL; ++m) {
+                        const int f = lane + 32 * m;
+                        float2 A, B;
+                        if (f < NB) {
+                            A = ya[f];
+                            B = ybb[f];
+                        } else {
+                            A = cconj(ya[LT - f]);
+                            B = cconj(ybb[LT - f]);
+                        }
+                        v[m] = make_float2(A.x - B.y, A.y + B.x);
+                    }
+                    fft_reg_any<NPL, true>(v);
+                    __syncwarp();
+#pragma unroll
+                    for (int k = 0; k < NPL; ++k) {
+                        const int t1 = fft_perm<NPL>(k);
+                        float2 xv = v[k];
+                        if (t1) {
+                            float2 wv = __ldg(wlt + (lane * t1) % LT);
+                            wv.y = -wv.y;
+                            xv = cmul(xv, wv);
+                        }
+                        S[t1 * 32 + (lane ^ t1)] = xv;
+                    }
+                    __syncwarp();
+#pragma unroll
+                    for (int a = 0; a < 16; ++a) w[a] = d < NPL ? S[d * 32 + ((2 * a + e) ^ d)] : make_float2(0.f, 0.f);
+                    fft_reg_dif_c<16, true>(w);
+#pragma unroll
+                    for (int k = 1; k < 16; ++k) {
+                        const int gg = bitrev<16>(k);
+                        if (e) w[k] = cmul(w[k], make_float2(w32c(gg), -w32s(gg)));
+                    }
+#pragma unroll
+                    for (int k = 0; k < 16; ++k) {
+                        float2 o;
+                        o.x = __shfl_xor_sync(0xffffffffu, w[k].x, 1);
+                        o.y = __shfl_xor_sync(0xffffffffu, w[k].y, 1);
+                        w[k] = e ? csub(o, w[k]) : cadd(w[k], o);
+                    }
+                } else {
+#pragma unroll
+                    for (int k = 0; k < 16; ++k) w[k] = make_float2(0.f, 0.f);
+                }
+                // ticks t < bt: the transform plus, for t < nr - 1, time block bt - 1's tail
+                // (held at the front of the warp's buffer), assembled in the buffer and
+                // written to the rows with 16-byte stores; then the new tail moves to the front
+                __syncwarp();   // the previous item's buffer reads and tail writes are done
+                if (act && d < NPL) {
+#pragma unroll
+                    for (int k = 0; k < 16; ++k) {
+                        const int t = d + NPL * (bitrev<16>(k) + 16 * e);
+                        if (t < c.bt) {
+                            float va = w[k].x, vb = w[k].y;
+                            if (live && t < c.nr - 1) {
+                                va += bufa[dx_bpos<NPL>(t)];
+                                vb += bufb[dx_bpos<NPL>(t)];
+                            }
+                            bufa[dx_bpos<NPL>(t)] = va;
+                            bufb[dx_bpos<NPL>(t)] = vb;
+                        }
+                    }
+                }
+                __syncwarp();
+                {
+                    const int lim = act ? c.bt : live ? c.nr - 1 : 0;   // buffer ticks below lim are valid
+                    float *oa = wa ? wa + (size_t)bt * c.bt : nullptr;
+                    float *ob = wb ? wb + (size_t)bt * c.bt : nullptr;
+                    for (int t0 = 4 * lane; t0 < c.bt; t0 += 128) {
+                        float4 va = zero4, vb = zero4;
+                        if (t0 < lim) {
+                            va = *reinterpret_cast<const float4 *>(bufa + dx_bpos<NPL>(t0));
+                            vb = *reinterpret_cast<const float4 *>(bufb + dx_bpos<NPL>(t0));
+                            if (t0 + 4 > lim) {   // the tail ends inside this quad
+                                if (t0 + 1 >= lim) va.y = vb.y = 0.f;
+                                if (t0 + 2 >= lim) va.z = vb.z = 0.f;
+                                va.w = vb.w = 0.f;
+                            }
+                            pa += fmaxf(va.x, 0.f) + fmaxf(va.y, 0.f) + fmaxf(va.z, 0.f) + fmaxf(va.w, 0.f);
+                            pb += fmaxf(vb.x, 0.f) + fmaxf(vb.y, 0.f) + fmaxf(vb.z, 0.f) + fmaxf(vb.w, 0.f);
+                        }
+                        if (oa) *reinterpret_cast<float4 *>(oa + t0) = va;
+                        if (ob) *reinterpret_cast<float4 *>(ob + t0) = vb;
+                    }
+                }
+                __syncwarp();   // the buffer is read before the tail replaces its front
+                if (act && d < NPL) {
+#pragma unroll
+                    for (int k = 0; k < 16; ++k) {
+                        const int t = d + NPL * (bitrev<16>(k) + 16 * e);
+                        if (t >= c.bt && t < span) {
+                            bufa[dx_bpos<NPL>(t - c.bt)] = w[k].x;
+                            bufb[dx_bpos<NPL>(t - c.bt)] = w[k].y;
+                        }
+                    }
+                }
+                live = act;
+            }
+            if (possum) {
+#pragma unroll
+                for (int o = 16; o; o >>= 1) {
+                    pa += __shfl_xor_sync(0xffffffffu, pa, o);
+                    pb += __shfl_xor_sync(0xffffffffu, pb, o);
+                }
+                if (lane == 0) {
+                    if (ra >= 0) possum[ra] = pa;
+                    if (rb >= 0) possum[rb] = pb;
+                }
+            }
+        }
+        __syncthreads();   // tslot, nzbt and Ys are reused by the next tile
+    }
+}
+
 // ---------------------------------------------------------------- host side
 // 2-D BF16 tensor [rows][inner], box [box_rows][64] (128 bytes), 128-byte swizzle; columns
 // past inner read as zero
@@ -987,7 +1270,7 @@ static int dx_make_map(tred_handle *h, CUtensorMap *m, const void *ptr, uint64_t
 
 template <int G>
 static int run_direct(tred_handle *h, const DxConst &c, const int32_t *n_blocks_dev, const float *qeff, float *out,
-                      int slot_base, int slot_count, int qbase, cudaStream_t s) {
+                      int slot_base, int slot_count, int qbase, cudaStream_t s, bool inverse) {
     const size_t fwd_smem = dx_fwd_smem(c.nch, c.nbins);
     const size_t gemm_smem = dx_gemm_smem(c.npad, c.ntap);
     const size_t inv_smem = sizeof(float2) * ((size_t)DX_INV_U * (32 * G + 1) + (size_t)(DX_INV_THREADS / 32) * 64 * G);
@@ -1038,6 +1321,7 @@ static int run_direct(tred_handle *h, const DxConst &c, const int32_t *n_blocks_
             kt_end(h, TRED_KT_DX_GEMM, s);
             h->launches += 2;
         }
+        if (!inverse) continue;   // the spectra stay in dx_y for k_dx_wave (a single pass)
         kt_begin(h, TRED_KT_DX_INV, s);
         k_dx_inv<G><<<2 * sms, DX_INV_THREADS, inv_smem, s>>>(h->dx_y, h->dx_rowstart, h->dx_meta, h->tw, c, base, out);
         kt_end(h, TRED_KT_DX_INV, s);
@@ -1049,8 +1333,52 @@ static int run_direct(tred_handle *h, const DxConst &c, const int32_t *n_blocks_
 int launch_direct(tred_handle *h, const int32_t *n_blocks_dev, const float *qeff, float *out, int slot_base,
                   int slot_count, int qbase, cudaStream_t s) {
     const DxConst c = dx_const_of(h);
-    if (c.lt == 512) return run_direct<8>(h, c, n_blocks_dev, qeff, out, slot_base, slot_count, qbase, s);
-    if (c.lt == 384) return run_direct<6>(h, c, n_blocks_dev, qeff, out, slot_base, slot_count, qbase, s);
+    if (c.lt == 512) return run_direct<8>(h, c, n_blocks_dev, qeff, out, slot_base, slot_count, qbase, s, true);
+    if (c.lt == 384) return run_direct<6>(h, c, n_blocks_dev, qeff, out, slot_base, slot_count, qbase, s, true);
+    return set_error(h, TRED_ERR_INVALID_ARG, "direct form: lt must be 384 or 512");
+}
+
+// the shapes the fused inverse + gather covers: every slot in one pass (the spectra of
+// all blocks resident at once), 8 x 8 pixel tiles (bp = 8, kp = bp + 1), a block's tail
+// overlapping only the next time block, FP32 sums
+bool dx_wave_ok(const tred_handle *h) {
+    return h->p.conv_mode == 4 && h->g.bp == 8 && h->g.kp == h->g.bp + 1 && h->d.R == h->g.bp / 2 &&
+           h->g.nr - 1 <= h->g.bt && h->d.nbt <= DX_NBT_MAX && h->max_blocks <= h->dx_blocks &&
+           !h->p.compensated_gather && (h->g.lt == 512 || h->g.lt == 384);
+}
+
+template <int G>
+static int run_wave(tred_handle *h, int32_t *queue, float *wave, float *possum, cudaStream_t s) {
+    const size_t smem = dx_wave_smem(G);
+    static size_t set = 0;
+    if (smem > set) {
+        cudaFuncSetAttribute(k_dx_wave<G>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        cudaFuncSetAttribute(k_dx_wave<G>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+        set = smem;
+    }
+    const DxWaveConst c{h->g.npx_x, h->d.npy_e, h->d.nby_e, h->d.nbx, h->d.nbt, h->d.n_events,
+                        h->g.bp,    h->g.bt,    h->g.nr,    h->g.nt};
+    int rc = check_cuda(h, cudaMemsetAsync(queue, 0, sizeof(int32_t), s), "tile queue reset");
+    if (rc) return rc;
+    kt_begin(h, TRED_KT_DX_WAVE, s);
+    k_dx_wave<G><<<2 * num_sms(h), DX_INV_THREADS, smem, s>>>(h->dx_y, h->blk_slot, h->pix_flag, h->dx_rowstart, h->tw,
+                                                               c, queue, wave, possum);
+    kt_end(h, TRED_KT_DX_WAVE, s);
+    h->launches += 1;
+    return check_cuda(h, cudaGetLastError(), "direct-form inverse + gather launch");
+}
+
+// a4 up to the per-block spectra (no inverse), then, after the pixel list and the slot map
+// are built (launch_pixel_list), the inverse time DFT of each tile straight into the waves
+int launch_direct_spectra(tred_handle *h, const int32_t *n_blocks_dev, const float *qeff, cudaStream_t s) {
+    const DxConst c = dx_const_of(h);
+    if (c.lt == 512) return run_direct<8>(h, c, n_blocks_dev, qeff, nullptr, 0, h->max_blocks, 0, s, false);
+    if (c.lt == 384) return run_direct<6>(h, c, n_blocks_dev, qeff, nullptr, 0, h->max_blocks, 0, s, false);
+    return set_error(h, TRED_ERR_INVALID_ARG, "direct form: lt must be 384 or 512");
+}
+int launch_direct_wave(tred_handle *h, int32_t *queue, float *wave, float *possum, cudaStream_t s) {
+    if (h->g.lt == 512) return run_wave<8>(h, queue, wave, possum, s);
+    if (h->g.lt == 384) return run_wave<6>(h, queue, wave, possum, s);
     return set_error(h, TRED_ERR_INVALID_ARG, "direct form: lt must be 384 or 512");
 }
 

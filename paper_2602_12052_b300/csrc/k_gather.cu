@@ -326,11 +326,14 @@ __global__ void k_slot_map(const int32_t *__restrict__ block_ids, const int32_t 
         slot_of[block_ids[k]] = k;
 }
 
-int launch_gather(tred_handle *h, const int32_t *block_ids, const int32_t *n_blocks_dev,
-                  const float *out, int32_t *pixel_ids, float *wave, int32_t *n_pixels_dev,
-                  cudaStream_t s, float *possum) {
-    GatherConst c{h->g.npx_x, h->d.npy, h->g.nt, h->g.bp, h->g.bt, h->g.nr, h->g.lt, h->d.R,
-                  h->d.nbx, h->d.nby, h->d.nbt, h->p.compensated_gather, h->d.npy_e, h->d.nby_e};
+static GatherConst gather_const_of(const tred_handle *h) {
+    return GatherConst{h->g.npx_x, h->d.npy, h->g.nt, h->g.bp, h->g.bt, h->g.nr, h->g.lt, h->d.R,
+                       h->d.nbx, h->d.nby, h->d.nbt, h->p.compensated_gather, h->d.npy_e, h->d.nby_e};
+}
+
+int launch_pixel_list(tred_handle *h, const int32_t *block_ids, const int32_t *n_blocks_dev, int32_t *pixel_ids,
+                      int32_t *n_pixels_dev, cudaStream_t s, int32_t **queue) {
+    const GatherConst c = gather_const_of(h);
     const int64_t npx = (int64_t)h->g.npx_x * h->d.npy;
     int rc = check_cuda(h, cudaMemsetAsync(h->pix_flag, 0, sizeof(int32_t) * npx, s), "clear pixel flags");
     if (rc) return rc;
@@ -343,7 +346,19 @@ int launch_gather(tred_handle *h, const int32_t *block_ids, const int32_t *n_blo
     k_scan_small<<<1, 1024, 0, s>>>(h->pix_chunks, h->pix_part, h->max_pixels, n_pixels_dev, h->status,
                                     TRED_ST_PIXEL_OVERFLOW, 4);
     k_px_emit<<<(unsigned)h->pix_chunks, 1024, 0, s>>>(npx, h->pix_flag, h->pix_part, h->max_pixels, pixel_ids);
-    int32_t *queue = h->pix_part + h->pix_chunks + 4;   // past the scan's total
+    h->launches += 5;
+    *queue = h->pix_part + h->pix_chunks + 4;   // past the scan's total
+    return check_cuda(h, cudaGetLastError(), "pixel list launch");
+}
+
+int launch_gather(tred_handle *h, const int32_t *block_ids, const int32_t *n_blocks_dev,
+                  const float *out, int32_t *pixel_ids, float *wave, int32_t *n_pixels_dev,
+                  cudaStream_t s, float *possum) {
+    const GatherConst c = gather_const_of(h);
+    int32_t *queue = nullptr;
+    int rc = launch_pixel_list(h, block_ids, n_blocks_dev, pixel_ids, n_pixels_dev, s, &queue);
+    if (rc) return rc;
+    const int sms = num_sms(h);
     const int pxw_grid = min(sms * 8, (h->max_pixels + PXW_WARPS - 1) / PXW_WARPS);   // a warp per pixel
     rc = check_cuda(h, cudaMemsetAsync(queue, 0, sizeof(int32_t), s), "gather queue reset");
     if (rc) return rc;
@@ -353,7 +368,7 @@ int launch_gather(tred_handle *h, const int32_t *block_ids, const int32_t *n_blo
     else
         k_px_wave<false><<<pxw_grid, PXW_THREADS, 0, s>>>(pixel_ids, n_pixels_dev, h->blk_slot, out, c, wave, possum,
                                                          queue);
-    h->launches += 6;
+    h->launches += 1;
     return check_cuda(h, cudaGetLastError(), "gather launch");
 }
 

@@ -694,6 +694,42 @@ int32_t tred_gather_readout(tred_handle *h, const int32_t *block_ids, const int3
                           max_hits, s, h->px_possum);
 }
 
+int32_t tred_convolve_gather_supported(const tred_handle *h) {
+    if (!h) return -1;
+    return dx_wave_ok(h) ? 1 : 0;
+}
+
+int32_t tred_convolve_gather_readout(tred_handle *h, const int32_t *block_ids, const int32_t *n_blocks_dev,
+                                     const float *qeff, int32_t *pixel_ids, float *waveforms, int32_t *n_pixels_dev,
+                                     const tred_readout_params *rp, int32_t *hit_pixel, int32_t *hit_tick,
+                                     float *hit_charge, int32_t *n_hits_dev, int32_t max_hits, void *stream) {
+    tred::CallRange range_("tred_convolve_gather_readout");
+    if (!h) return TRED_ERR_INVALID_ARG;
+    if (!h->response_ready)
+        return set_error(h, TRED_ERR_NOT_READY, "tred_convolve_gather_readout: call tred_set_response first");
+    if (!dx_wave_ok(h))
+        return set_error(h, TRED_ERR_INVALID_ARG,
+                         "tred_convolve_gather_readout: needs conv_mode 4, bp 8, kp 9, nr - 1 <= bt, nt / bt <= 128, "
+                         "max_blocks within one pass and compensated_gather 0");
+    if (!block_ids || !n_blocks_dev || !qeff || !pixel_ids || !waveforms || !n_pixels_dev)
+        return set_error(h, TRED_ERR_INVALID_ARG, "tred_convolve_gather_readout: null pointer");
+    if (rp && (!n_hits_dev || max_hits < 0 || (max_hits > 0 && (!hit_pixel || !hit_tick || !hit_charge))))
+        return set_error(h, TRED_ERR_INVALID_ARG, "tred_convolve_gather_readout: null hit buffers");
+    if (rp && (rp->clock_ticks < 1 || rp->hold_ticks < 0 || rp->reset_ticks < 0 || rp->mode < 0 || rp->mode > 2 ||
+               (rp->mode == 1 && (rp->n_samples < 1 || rp->hold_ticks < 1))))
+        return set_error(h, TRED_ERR_INVALID_ARG, "tred_convolve_gather_readout: bad readout parameters");
+    const cudaStream_t s = (cudaStream_t)stream;
+    int rc = launch_direct_spectra(h, n_blocks_dev, qeff, s);
+    if (rc) return rc;
+    int32_t *queue = nullptr;
+    rc = launch_pixel_list(h, block_ids, n_blocks_dev, pixel_ids, n_pixels_dev, s, &queue);
+    if (rc) return rc;
+    rc = launch_direct_wave(h, queue, waveforms, h->px_possum, s);
+    if (rc || !rp) return rc;
+    return launch_readout(h, *rp, pixel_ids, waveforms, n_pixels_dev, hit_pixel, hit_tick, hit_charge, n_hits_dev,
+                          max_hits, s, h->px_possum);
+}
+
 int32_t tred_wait_selftest(tred_handle *h, int64_t limit_cycles, void *stream) {
     if (!h) return TRED_ERR_INVALID_ARG;
     if (limit_cycles < 1 || limit_cycles > 2000000000ll)

@@ -152,6 +152,11 @@ int launch_wait_selftest(tred_handle *h, long long limit, cudaStream_t s);
 int launch_direct_response(tred_handle *h, const float *resp, cudaStream_t s);
 int launch_direct(tred_handle *h, const int32_t *n_blocks_dev, const float *qeff, float *out, int slot_base,
                   int slot_count, int qbase, cudaStream_t s);
+// fused inverse DFT + gather of conv_mode 4 (tred_convolve_gather_readout): the spectra of
+// every slot in one pass, then k_dx_wave over the pixel list that launch_pixel_list built
+bool dx_wave_ok(const tred_handle *h);
+int launch_direct_spectra(tred_handle *h, const int32_t *n_blocks_dev, const float *qeff, cudaStream_t s);
+int launch_direct_wave(tred_handle *h, int32_t *queue, float *wave, float *possum, cudaStream_t s);
 size_t dx_bytes_b(int nbins, int npad, int kq);
 size_t dx_bytes_q(int nbins, int rows_cap, int kq);
 int dx_rows_cap_of(int dx_blocks, int bp2, int cap_param);
@@ -161,6 +166,10 @@ bool dx_shape_ok(int nch, int lt);
 void *tensor_map_encoder();
 int launch_convolve(tred_handle *h, const int32_t *block_ids, const int32_t *n_blocks_dev,
                     const float *qeff, float *out, int slot_base, int slot_count, cudaStream_t s);
+// the gather's pixel list (pixel_ids, n_pixels_dev), pix_flag = row of each pixel or -1,
+// blk_slot = slot of each active block or -1; returns the device word for a work queue
+int launch_pixel_list(tred_handle *h, const int32_t *block_ids, const int32_t *n_blocks_dev, int32_t *pixel_ids,
+                      int32_t *n_pixels_dev, cudaStream_t s, int32_t **queue);
 int launch_gather(tred_handle *h, const int32_t *block_ids, const int32_t *n_blocks_dev,
                   const float *out, int32_t *pixel_ids, float *wave, int32_t *n_pixels_dev,
                   cudaStream_t s, float *possum = nullptr);

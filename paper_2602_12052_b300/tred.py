@@ -182,6 +182,24 @@ def tred_gather_readout(h: Handle, block_ids, n_blocks_dev, out_blocks, pixel_id
                                       _stream(stream)))
 
 
+def tred_convolve_gather_supported(h: Handle) -> bool:
+    """Whether the handle's shape allows tred_convolve_gather_readout."""
+    return h.lib.tred_convolve_gather_supported(h.h) == 1
+
+
+def tred_convolve_gather_readout(h: Handle, block_ids, n_blocks_dev, qeff, pixel_ids, waveforms, n_pixels_dev,
+                                 rp: ReadoutParams | None = None, hit_pixel=None, hit_tick=None, hit_charge=None,
+                                 n_hits_dev=None, stream=None):
+    """Convolution (direct form) + gather (+ readout when rp is given) without the
+    per-block output buffer: the inverse time DFT runs per pixel tile into the waves."""
+    h.check(h.lib.tred_convolve_gather_readout(
+        h.h, _ptr(block_ids), _ptr(n_blocks_dev), _ptr(qeff), _ptr(pixel_ids), _ptr(waveforms), _ptr(n_pixels_dev),
+        ctypes.byref(rp) if rp is not None else None, _ptr(hit_pixel) if hit_pixel is not None else None,
+        _ptr(hit_tick) if hit_tick is not None else None, _ptr(hit_charge) if hit_charge is not None else None,
+        _ptr(n_hits_dev) if n_hits_dev is not None else None, hit_pixel.numel() if hit_pixel is not None else 0,
+        _stream(stream)))
+
+
 def tred_readout(h: Handle, rp: ReadoutParams, pixel_ids, waveforms, n_pixels_dev, hit_pixel,
                  hit_tick, hit_charge, n_hits_dev, stream=None):
     h.check(h.lib.tred_readout(h.h, ctypes.byref(rp), _ptr(pixel_ids), _ptr(waveforms),
@@ -200,8 +218,9 @@ def tred_sync_status(h: Handle, stream=None):
     return list(buf)
 
 
-KT_EFFQ, KT_DX_FWD, KT_DX_GEMM, KT_DX_INV = 0, 1, 2, 3
-KT_NAMES = {KT_EFFQ: "k_effq_blocks", KT_DX_FWD: "k_dx_fwd", KT_DX_GEMM: "k_dx_gemm", KT_DX_INV: "k_dx_inv"}
+KT_EFFQ, KT_DX_FWD, KT_DX_GEMM, KT_DX_INV, KT_DX_WAVE = 0, 1, 2, 3, 4
+KT_NAMES = {KT_EFFQ: "k_effq_blocks", KT_DX_FWD: "k_dx_fwd", KT_DX_GEMM: "k_dx_gemm", KT_DX_INV: "k_dx_inv",
+            KT_DX_WAVE: "k_dx_wave"}
 
 
 def tred_set_kernel_timing(h: Handle, enable: bool) -> None:
@@ -282,10 +301,13 @@ class Simulator:
     def __init__(self, cfg, resp: torch.Tensor, max_deposits: int, max_blocks: int,
                  max_pixels: int, max_pairs: int | None = None, max_hits: int | None = None,
                  effq_mode=0, mpcp=1, compensated_gather=0, conv_mode=0, effq_skip_empty=0, device=None,
-                 fused=False, conv_rows_cap=0):
+                 fused=False, conv_rows_cap=0, fuse_gather=False):
         self.cfg = cfg
         self.mpcp = mpcp
         self.fused = bool(fused)
+        # fuse_gather: conv_mode 4's inverse time DFT per pixel tile straight into the waves
+        # (tred_convolve_gather_readout); out_blocks is then not written
+        self.fuse_gather = bool(fuse_gather)
         self.device = torch.device(device or "cuda")
         self.h = Handle(geometry(cfg), params(cfg, effq_mode, mpcp, compensated_gather, conv_mode, effq_skip_empty,
                                               conv_rows_cap),
@@ -304,7 +326,11 @@ class Simulator:
         qrows = min(torch.cuda.get_device_properties(d).multi_processor_count, max_blocks, 8192) if self.fused \
             else max_blocks
         self.qeff = torch.empty((qrows, ns, ns, bp, bp, bt), dtype=torch.float32, device=d)
-        self.out_blocks = torch.empty((max_blocks, 16, 16, lt), dtype=torch.float32, device=d)
+        if self.fuse_gather and not tred_convolve_gather_supported(self.h):
+            raise ValueError("fuse_gather needs conv_mode 4, bp 8, kp 9, nr - 1 <= bt, nt / bt <= 128 and "
+                             "max_blocks within one pass of the direct form")
+        self.out_blocks = torch.empty((1 if self.fuse_gather else max_blocks, 16, 16, lt), dtype=torch.float32,
+                                      device=d)
         self.pixel_ids = torch.zeros(max_pixels, dtype=torch.int32, device=d)
         self.waveforms = torch.empty((max_pixels, cfg.nt), dtype=torch.float32, device=d)
         mh = max_hits or 4 * max_pixels
@@ -337,6 +363,15 @@ class Simulator:
         else:
             tred_effq(self.h, n, self.deps, self.block_ids, self.dep_offsets, self.dep_index,
                       self.n_blocks_dev, self.qeff, stream)
+        self._convolve_gather(stream, readout)
+
+    def _convolve_gather(self, stream, readout):
+        if self.fuse_gather:
+            hits = (self.rp, self.hit_pixel, self.hit_tick, self.hit_charge, self.n_hits_dev) if readout else ()
+            tred_convolve_gather_readout(self.h, self.block_ids, self.n_blocks_dev, self.qeff, self.pixel_ids,
+                                         self.waveforms, self.n_pixels_dev, *hits, stream=stream)
+            return
+        if not self.fused:
             tred_convolve(self.h, self.block_ids, self.n_blocks_dev, self.qeff, self.out_blocks, stream)
         if readout:      # gather and readout in one call (readout skips pixels that cannot trigger)
             tred_gather_readout(self.h, self.block_ids, self.n_blocks_dev, self.out_blocks, self.pixel_ids,
@@ -381,14 +416,7 @@ class LineSimulator(Simulator):
                       self.dep_index, self.n_blocks_dev, stream)
         tred_effq_lines(self.h, n, self.deps, self.half[:3 * max(n, 1)], self.block_ids, self.dep_offsets,
                         self.dep_index, self.n_blocks_dev, self.qeff, stream)
-        tred_convolve(self.h, self.block_ids, self.n_blocks_dev, self.qeff, self.out_blocks, stream)
-        if readout:      # gather and readout in one call (readout skips pixels that cannot trigger)
-            tred_gather_readout(self.h, self.block_ids, self.n_blocks_dev, self.out_blocks, self.pixel_ids,
-                                self.waveforms, self.n_pixels_dev, self.rp, self.hit_pixel, self.hit_tick,
-                                self.hit_charge, self.n_hits_dev, stream)
-        else:
-            tred_gather_pixels(self.h, self.block_ids, self.n_blocks_dev, self.out_blocks,
-                               self.pixel_ids, self.waveforms, self.n_pixels_dev, stream)
+        self._convolve_gather(stream, readout)
 
 
 class DiffState:
@@ -493,7 +521,11 @@ class BatchSimulator:
         self.dep_index = torch.zeros(8 * max(cap, 1), dtype=torch.int32, device=d)
         self.counts = torch.zeros(4, dtype=torch.int32, device=d)
         self.qeff = torch.empty((self.chunk, ns, ns, bp, bp, bt), dtype=torch.float32, device=d)
-        self.out_blocks = torch.empty((max_blocks, 16, 16, lt), dtype=torch.float32, device=d)
+        if self.fuse_gather and not tred_convolve_gather_supported(self.h):
+            raise ValueError("fuse_gather needs conv_mode 4, bp 8, kp 9, nr - 1 <= bt, nt / bt <= 128 and "
+                             "max_blocks within one pass of the direct form")
+        self.out_blocks = torch.empty((1 if self.fuse_gather else max_blocks, 16, 16, lt), dtype=torch.float32,
+                                      device=d)
         self.pixel_ids = torch.zeros(max_pixels, dtype=torch.int32, device=d)
         self.waveforms = torch.empty((max_pixels, cfg.nt), dtype=torch.float32, device=d)
         mh = max_hits or 4 * max_pixels
