@@ -177,7 +177,12 @@ def direct_rooflines(cfg, rows, cols, blocks, kms, clocks, pixels=0):
         r["kernel"] = k
         unit = "row" if k in ("k_dx_fwd", "k_dx_gemm") else "block"
         per = figs.get(f"{k}_dram_bytes_per_{unit}")
-        if fresh and per:
+        rd, wr = figs.get(f"{k}_dram_read_bytes_per_block"), figs.get(f"{k}_dram_write_bytes_per_pixel")
+        if fresh and rd and wr:   # reads scale with the blocks, writes with the pixels
+            r["traffic"] = rd * blocks + wr * pixels
+            r["traffic_source"] = (f"ncu dram__bytes_read of module20 per block ({rd:.4g} B) x {blocks} blocks + "
+                                   f"dram__bytes_write per pixel ({wr:.4g} B) x {pixels} pixels")
+        elif fresh and per:
             n_units = rows if unit == "row" else blocks
             r["traffic"] = per * n_units
             r["traffic_source"] = (f"ncu dram__bytes_read+write of module20, {per:.4g} B per {unit}, "

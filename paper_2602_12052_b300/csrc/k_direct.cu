@@ -56,6 +56,8 @@ constexpr int DX_STAGES = 2;             // operand stages
 constexpr int DX_ROWS_MAX = 131072;      // rows per forward + GEMM launch pair
 constexpr int DX_BLOCKS_MAX = 16384;     // slots per pass
 constexpr int DX_FWD_THREADS = 256;
+constexpr int DX_FWD_UNITS = 13;         // units of 4 impacts per forward item at most (26 pairs)
+constexpr int DX_FWD_CTAS = 2;           // forward CTAs per SM (shared memory of 26 pairs each)
 constexpr int DX_INV_THREADS = 256;
 constexpr int DX_GEMM_THREADS = 320;     // warp 0 copies, warp 1 products, warps 2..9 epilogue
 constexpr uint32_t DX_A_BYTES = DX_M * DX_KC * 2;   // 16 KB per part
@@ -63,7 +65,7 @@ constexpr int DX_TAPS_PER_LANE = 3;   // kp <= 9: at most 81 taps
 constexpr int DX_YS = 25;            // output accumulator row stride (float2): 9 mod 16
 
 struct DxConst {
-    int nch, kq, ntap, npad, imoff, jm, kp, R, bp, bpl, bp2, bt, lt, nbins, rows_cap;
+    int nch, kq, ntap, npad, imoff, nparts, kp, R, bp, bpl, bp2, bt, lt, nbins, rows_cap;
 };
 
 __host__ __device__ constexpr int dx_round16(int x) { return (x + 15) & ~15; }
@@ -73,11 +75,16 @@ __host__ __device__ constexpr uint32_t dx_stage_bytes(int npad) {
 }
 // column stride of the forward kernel's transposition buffer: at least nbins + 3 (room
 // for the columns' skew of up to 3) and 1 mod 8, so that lanes reading the columns of
-// distinct pairs of one bin hit distinct banks; the buffer holds the larger half of a
-// row's impacts, jm = 4 ceil(nch / 8), two columns per impact
+// distinct pairs of one bin hit distinct banks; the buffer holds the impacts of one item,
+// at most 4 DX_FWD_UNITS, two columns per impact
 __host__ __device__ constexpr int dx_tstride(int nbins) { return ((nbins + 10) & ~7) + 1; }
-__host__ __device__ constexpr int dx_half_split(int nch) { return 4 * ((nch + 7) / 8); }
-size_t dx_fwd_smem(int nch, int nbins) { return sizeof(float) * (size_t)(2 * dx_half_split(nch)) * dx_tstride(nbins); }
+// a row's impacts in units of 4, cut into nparts items of at most DX_FWD_UNITS units:
+// part q covers units [q nu / nparts, (q + 1) nu / nparts)
+__host__ __device__ constexpr int dx_fwd_parts(int nch) { return ((nch + 3) / 4 + DX_FWD_UNITS - 1) / DX_FWD_UNITS; }
+size_t dx_fwd_smem(int nch, int nbins) {
+    const int nu = (nch + 3) / 4, np = dx_fwd_parts(nch);
+    return sizeof(float) * (size_t)(8 * ((nu + np - 1) / np)) * dx_tstride(nbins);
+}
 // epilogue staging row (floats): Re Z of the taps at 0, Im Z at imoff = ntap rounded up to
 // 4; a multiple of 4 (16-byte stores) with an odd number of 16-byte chunks (the 32 lanes'
 // rows start in distinct bank groups)
@@ -171,7 +178,7 @@ static DxConst dx_const_of(const tred_handle *h) {
     DxConst c;
     c.nch = h->g.n_sub * h->g.n_sub;
     c.kq = 32 * ((c.nch + 15) / 16);
-    c.jm = dx_half_split(c.nch);
+    c.nparts = dx_fwd_parts(c.nch);
     c.kp = h->g.kp;
     c.ntap = c.kp * c.kp;
     c.npad = dx_round16(c.ntap);
@@ -339,8 +346,11 @@ __device__ __forceinline__ void dx_zero_straddling(const int32_t *__restrict__ r
     }
 }
 
-// Items (row, half): the CTA transforms the impact pairs of one half of a row (two CTAs
-// per SM).  Warp w takes the half's pairs q = w, w + 8, ...: the two real columns as one
+// Items (row, part): the CTA transforms the impact pairs of one part of a row (at most
+// 4 DX_FWD_UNITS impacts: two parts of a 10 x 10 impact row, two CTAs per SM; four parts
+// of 24 or 28 impacts at three CTAs per SM (80 registers) ran 11.0 ms against 8.2 ms on
+// a module plane).  Warp w takes the part's pairs
+// q = w, w + 8, ...: the two real columns as one
 // complex sequence z[t] = Q[2q][t] + i Q[2q+1][t] (t < bt, zero to lt), N = lt = 32 NPL:
 //   pass 1  lane l holds z[l + 32 n1], n1 < NPL: an NPL-point DFT in registers, the
 //           twiddles W_N^(l f1);
@@ -350,10 +360,11 @@ __device__ __forceinline__ void dx_zero_straddling(const int32_t *__restrict__ r
 //           radix-2 step across the lane pair, so that lane 2 d + e holds bin
 //           f = d + NPL (g + 16 e) in register k (g = bitrev16(k));
 // then Z[f] (f <= N/2) and Z[N - f] land in the pair's four columns.  A pair whose two
-// columns are empty in the block's masks is written as zeros without a transform.  Then
-// the CTA writes bin by bin, one lane per two pairs, the Hermitian split of their columns
-// in BF16 hi and lo parts at the GEMM's K positions.  Items (row, half) split the impacts
-// at jm = 4 ceil(nch / 8), so that each lane's four impacts lie in one group of 16.
+// columns are empty in the block's masks (or lie past the last impact) is written as
+// zeros without a transform.  Then the CTA writes bin by bin, one lane per two pairs, the
+// Hermitian split of their columns in BF16 hi and lo parts at the GEMM's K positions.
+// Parts start at multiples of 4 impacts, so that each lane's four impacts lie in one
+// group of 16.
 // first float of pair q's region (4 ST floats: Z[f] then C[f] = Z[N - f] as complex
 // numbers); the skew 2 ((q >> 3) & 3) keeps it 8-byte aligned and puts the regions of the
 // pairs 2 c4 (c4 = 0 .. 15, one lane each) in distinct banks
@@ -366,7 +377,7 @@ __device__ __forceinline__ void dx_fft_fwd(float2 (&v)[N]) {
 }
 
 template <int G>
-__global__ void __launch_bounds__(DX_FWD_THREADS, 2)
+__global__ void __launch_bounds__(DX_FWD_THREADS, DX_FWD_CTAS)
     k_dx_fwd(const float *__restrict__ qeff, const uint64_t *__restrict__ colmask, const int32_t *__restrict__ rows,
              const int32_t *__restrict__ rowstart, const int32_t *__restrict__ meta, const float2 *__restrict__ tw,
              DxConst c, int slot_base, int qbase, int row0, int zero_straddling, uint16_t *__restrict__ qhi,
@@ -384,19 +395,21 @@ __global__ void __launch_bounds__(DX_FWD_THREADS, 2)
     const float2 *wlt = tw + TW_LT;
     const int d = lane >> 1, e = lane & 1;
     const bool hz = 2 * c.bt <= LT;
-    for (int item = blockIdx.x; item < 2 * nloc; item += gridDim.x) {
-        const int rl = item >> 1, hh = item & 1;
-        // impacts [j0, j1) of this half: [0, jm) or [jm, nch), jm a multiple of 4
-        const int j0 = hh ? c.jm : 0, j1 = hh ? c.nch : c.jm;
-        const int nph = (j1 - j0) >> 1;
+    const int nu = (c.nch + 3) >> 2;
+    for (int item = blockIdx.x; item < c.nparts * nloc; item += gridDim.x) {
+        const int rl = item / c.nparts, part = item - rl * c.nparts;
+        // units [u0, u1) of 4 impacts: impacts j0 .. j0 + 2 nph - 1, those >= nch empty
+        const int u0 = part * nu / c.nparts, u1 = (part + 1) * nu / c.nparts;
+        const int j0 = 4 * u0;
+        const int nph = 2 * (u1 - u0);
         const int rec = rows[row0 + rl];
         const int s = rec >> 6, p = rec & 63;
         const uint64_t *mk = colmask + (size_t)(slot_base + s) * c.nch;
         const float *qs = qeff + (size_t)(slot_base + s - qbase) * c.nch * c.bp2 * c.bt + (size_t)p * c.bt;
         for (int ql = warp; ql < nph; ql += NW) {
             const int ja = j0 + 2 * ql, jb = ja + 1;
-            const bool nza = (mk[ja] >> p) & 1ull;
-            const bool nzb = (mk[jb] >> p) & 1ull;
+            const bool nza = ja < c.nch && ((mk[ja] >> p) & 1ull);
+            const bool nzb = jb < c.nch && ((mk[jb] >> p) & 1ull);
             float2 *Zp = reinterpret_cast<float2 *>(T + dx_pbase(ql, ST));   // Z[f], f <= N/2
             float2 *Cp = Zp + ST;                                               // Z[N - f]
             if (!(nza || nzb)) {
@@ -407,7 +420,7 @@ __global__ void __launch_bounds__(DX_FWD_THREADS, 2)
                 continue;
             }
             const float *ca = qs + (size_t)ja * c.bp2 * c.bt;
-            const float *cb = qs + (size_t)jb * c.bp2 * c.bt;
+            const float *cb = qs + (size_t)(nzb ? jb : ja) * c.bp2 * c.bt;   // jb may lie past the last impact
             float2 v[NPL];
 #pragma unroll
             for (int n1 = 0; n1 < NPL; ++n1) {
@@ -460,7 +473,7 @@ __global__ void __launch_bounds__(DX_FWD_THREADS, 2)
         // then the four real parts at k = 32 g + i and the four imaginary parts at
         // k = 32 g + 16 + i (j = 16 g + i) as BF16 hi and lo parts (8 bytes each)
         // a warp covers 32 / lpb bins at a time (lpb lanes per bin, at least the half's units)
-        const int nunit = nph >> 1;
+        const int nunit = u1 - u0;
         const int lpb = nunit <= 8 ? 8 : (nunit <= 16 ? 16 : 32);
         for (int f = warp * (32 / lpb) + lane / lpb; f - lane / lpb < c.nbins; f += NW * (32 / lpb)) {
             if (f >= c.nbins) continue;
@@ -1311,7 +1324,7 @@ static int run_direct(tred_handle *h, const DxConst &c, const int32_t *n_blocks_
         for (int k = 0; k < nrc; ++k) {
             const int row0 = k * c.rows_cap;
             kt_begin(h, TRED_KT_DX_FWD, s);
-            k_dx_fwd<G><<<2 * sms, DX_FWD_THREADS, fwd_smem, s>>>(qeff, h->colmask, h->dx_rows, h->dx_rowstart, h->dx_meta,
+            k_dx_fwd<G><<<DX_FWD_CTAS * sms, DX_FWD_THREADS, fwd_smem, s>>>(qeff, h->colmask, h->dx_rows, h->dx_rowstart, h->dx_meta,
                                                              h->tw, c, base, qbase, row0, k == 0 ? 1 : 0, h->dx_qhi,
                                                              h->dx_qlo, h->dx_y);
             kt_end(h, TRED_KT_DX_FWD, s);

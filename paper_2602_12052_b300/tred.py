@@ -521,11 +521,7 @@ class BatchSimulator:
         self.dep_index = torch.zeros(8 * max(cap, 1), dtype=torch.int32, device=d)
         self.counts = torch.zeros(4, dtype=torch.int32, device=d)
         self.qeff = torch.empty((self.chunk, ns, ns, bp, bp, bt), dtype=torch.float32, device=d)
-        if self.fuse_gather and not tred_convolve_gather_supported(self.h):
-            raise ValueError("fuse_gather needs conv_mode 4, bp 8, kp 9, nr - 1 <= bt, nt / bt <= 128 and "
-                             "max_blocks within one pass of the direct form")
-        self.out_blocks = torch.empty((1 if self.fuse_gather else max_blocks, 16, 16, lt), dtype=torch.float32,
-                                      device=d)
+        self.out_blocks = torch.empty((max_blocks, 16, 16, lt), dtype=torch.float32, device=d)
         self.pixel_ids = torch.zeros(max_pixels, dtype=torch.int32, device=d)
         self.waveforms = torch.empty((max_pixels, cfg.nt), dtype=torch.float32, device=d)
         mh = max_hits or 4 * max_pixels

@@ -48,6 +48,16 @@ def test_direct_shapes(bt, lt, bp, kp, nr, gl):
     _full_check(cfg, dep, resp, mpcp=0, conv_mode=4, check_readout=False)
 
 
+@pytest.mark.parametrize("n_sub", [8, 6, 4])
+def test_direct_impact_counts(n_sub):
+    """64, 36 and 16 impacts per pixel: the forward transform cuts a row's impacts into
+    3, 2 and 1 items at multiples of 4 (groups of 16 partly filled)."""
+    cfg = synth.get_config("tiny", n_sub=n_sub)
+    dep = synth.make_deposits(cfg)
+    resp = synth.make_response(cfg, symmetric=False)
+    _full_check(cfg, dep, resp, mpcp=0, conv_mode=4, skip_empty=1, check_readout=False)
+
+
 def test_direct_row_chunks_are_bitwise_the_same():
     """Rows in launch pairs of 128 (blocks whose rows cross a tile or a launch boundary
     get two partial sums added onto zero) give the same bits as one launch pair, and a
