@@ -42,6 +42,7 @@
 // memory and returns.
 #include <cudaTypedefs.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstring>
 #include <vector>
@@ -78,12 +79,27 @@ __host__ __device__ constexpr uint32_t dx_stage_bytes(int npad) {
 // distinct pairs of one bin hit distinct banks; the buffer holds the impacts of one item,
 // at most 4 DX_FWD_UNITS, two columns per impact
 __host__ __device__ constexpr int dx_tstride(int nbins) { return ((nbins + 10) & ~7) + 1; }
-// a row's impacts in units of 4, cut into nparts items of at most DX_FWD_UNITS units:
-// part q covers units [q nu / nparts, (q + 1) nu / nparts)
-__host__ __device__ constexpr int dx_fwd_parts(int nch) { return ((nch + 3) / 4 + DX_FWD_UNITS - 1) / DX_FWD_UNITS; }
+// A row's impacts in the GEMM's K groups of 16, cut into nparts items of whole groups
+// (part q: groups [q ng / nparts, (q + 1) ng / nparts)), so that no 32-byte sector of a
+// row's spectra is written by two CTAs; nparts is the least count whose parts hold at
+// most DX_FWD_UNITS units of 4 impacts below nch (the pairs the shared buffer holds).
+__host__ __device__ constexpr int dx_part_units(int nch, int np, int q) {
+    const int ng = (nch + 15) / 16;
+    const int j0 = 16 * (q * ng / np), j1 = 16 * ((q + 1) * ng / np) < nch ? 16 * ((q + 1) * ng / np) : nch;
+    return j1 > j0 ? (j1 - j0 + 3) / 4 : 0;
+}
+static int dx_fwd_max_units(int nch, int np) {
+    int mx = 0;
+    for (int q = 0; q < np; ++q) mx = std::max(mx, dx_part_units(nch, np, q));
+    return mx;
+}
+static int dx_fwd_parts(int nch) {
+    int np = 1;
+    while (dx_fwd_max_units(nch, np) > DX_FWD_UNITS) ++np;
+    return np;
+}
 size_t dx_fwd_smem(int nch, int nbins) {
-    const int nu = (nch + 3) / 4, np = dx_fwd_parts(nch);
-    return sizeof(float) * (size_t)(8 * ((nu + np - 1) / np)) * dx_tstride(nbins);
+    return sizeof(float) * (size_t)(8 * dx_fwd_max_units(nch, dx_fwd_parts(nch))) * dx_tstride(nbins);
 }
 // epilogue staging row (floats): Re Z of the taps at 0, Im Z at imoff = ntap rounded up to
 // 4; a multiple of 4 (16-byte stores) with an odd number of 16-byte chunks (the 32 lanes'
@@ -346,10 +362,14 @@ __device__ __forceinline__ void dx_zero_straddling(const int32_t *__restrict__ r
     }
 }
 
-// Items (row, part): the CTA transforms the impact pairs of one part of a row (at most
-// 4 DX_FWD_UNITS impacts: two parts of a 10 x 10 impact row, two CTAs per SM; four parts
-// of 24 or 28 impacts at three CTAs per SM (80 registers) ran 11.0 ms against 8.2 ms on
-// a module plane).  Warp w takes the part's pairs
+// Items (row, part): the CTA transforms the impact pairs of one part of a row, whole
+// groups of 16 impacts with at most 4 DX_FWD_UNITS impacts (two parts of a 10 x 10
+// impact row, two CTAs per SM).  Parts that split a group put two CTAs' partial writes
+// into one 32-byte sector of the spectra (the split at 52 instead of 48 impacts: 8.2
+// against 6.8 ms on a module plane; four parts of 24 or 28 impacts at three CTAs per SM:
+// 11.0 ms).  The last group's padding past nch is left as the buffer was cleared (writing
+// it as zeros: 7.0 ms).
+// Warp w takes the part's pairs
 // q = w, w + 8, ...: the two real columns as one
 // complex sequence z[t] = Q[2q][t] + i Q[2q+1][t] (t < bt, zero to lt), N = lt = 32 NPL:
 //   pass 1  lane l holds z[l + 32 n1], n1 < NPL: an NPL-point DFT in registers, the
@@ -386,7 +406,7 @@ __global__ void __launch_bounds__(DX_FWD_THREADS, DX_FWD_CTAS)
     constexpr int NPL = LT / 32;
     constexpr int NW = DX_FWD_THREADS / 32;
     static_assert(NPL <= 16, "pass 2 holds 16 samples per lane");
-    extern __shared__ float T[];   // per pair of the half 4 ST floats at dx_pbase(pair)
+    extern __shared__ float T[];   // per pair of the part 4 ST floats at dx_pbase(pair)
     const int ST = dx_tstride(c.nbins);
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int cnt = meta[0], nrows = meta[1];
@@ -395,13 +415,15 @@ __global__ void __launch_bounds__(DX_FWD_THREADS, DX_FWD_CTAS)
     const float2 *wlt = tw + TW_LT;
     const int d = lane >> 1, e = lane & 1;
     const bool hz = 2 * c.bt <= LT;
-    const int nu = (c.nch + 3) >> 2;
+    const int ng = (c.nch + 15) >> 4;
     for (int item = blockIdx.x; item < c.nparts * nloc; item += gridDim.x) {
         const int rl = item / c.nparts, part = item - rl * c.nparts;
-        // units [u0, u1) of 4 impacts: impacts j0 .. j0 + 2 nph - 1, those >= nch empty
-        const int u0 = part * nu / c.nparts, u1 = (part + 1) * nu / c.nparts;
-        const int j0 = 4 * u0;
-        const int nph = 2 * (u1 - u0);
+        // groups [g0, g1) of 16 impacts: nunit units of 4 hold impacts below nch (the
+        // padding of the last group stays as the buffer was cleared)
+        const int g0 = part * ng / c.nparts, g1 = (part + 1) * ng / c.nparts;
+        const int j0 = 16 * g0;
+        const int nunit = (min(16 * g1, c.nch) - j0 + 3) >> 2;
+        const int nph = 2 * nunit;
         const int rec = rows[row0 + rl];
         const int s = rec >> 6, p = rec & 63;
         const uint64_t *mk = colmask + (size_t)(slot_base + s) * c.nch;
@@ -473,7 +495,6 @@ __global__ void __launch_bounds__(DX_FWD_THREADS, DX_FWD_CTAS)
         // then the four real parts at k = 32 g + i and the four imaginary parts at
         // k = 32 g + 16 + i (j = 16 g + i) as BF16 hi and lo parts (8 bytes each)
         // a warp covers 32 / lpb bins at a time (lpb lanes per bin, at least the half's units)
-        const int nunit = u1 - u0;
         const int lpb = nunit <= 8 ? 8 : (nunit <= 16 ? 16 : 32);
         for (int f = warp * (32 / lpb) + lane / lpb; f - lane / lpb < c.nbins; f += NW * (32 / lpb)) {
             if (f >= c.nbins) continue;
@@ -1008,12 +1029,15 @@ struct DxWaveConst {
 #define DX_BUFW(G) (64 * (G) + 16)
 template <int NPL>
 __device__ __forceinline__ int dx_bpos(int t) { return t + (t >= 16 * NPL ? 16 : 0); }
+// k_dx_wave CTAs per SM (three, with the transpose scratch over the staged spectra
+// behind one more barrier and 80 registers: 6.0 against 3.1 ms on a module plane)
+constexpr int DX_WAVE_CTAS = 2;
 __host__ __device__ constexpr size_t dx_wave_smem(int G) {
     // staged spectra [16][32 G + 1], transpose scratch [8 warps][64 G], tick buffers [8][2][64 G + 16]
     return sizeof(float2) * ((size_t)16 * (32 * G + 1) + (size_t)8 * 64 * G) + sizeof(float) * (size_t)8 * 2 * DX_BUFW(G);
 }
 template <int G>
-__global__ void __launch_bounds__(DX_INV_THREADS, 2)
+__global__ void __launch_bounds__(DX_INV_THREADS, DX_WAVE_CTAS)
     k_dx_wave(const float2 *__restrict__ ybuf, const int32_t *__restrict__ slot_of, const int32_t *__restrict__ pix_row,
               const int32_t *__restrict__ rowstart, const float2 *__restrict__ tw, DxWaveConst c,
               int32_t *__restrict__ queue, float *__restrict__ wave, float *__restrict__ possum) {
@@ -1374,7 +1398,7 @@ static int run_wave(tred_handle *h, int32_t *queue, float *wave, float *possum, 
     int rc = check_cuda(h, cudaMemsetAsync(queue, 0, sizeof(int32_t), s), "tile queue reset");
     if (rc) return rc;
     kt_begin(h, TRED_KT_DX_WAVE, s);
-    k_dx_wave<G><<<2 * num_sms(h), DX_INV_THREADS, smem, s>>>(h->dx_y, h->blk_slot, h->pix_flag, h->dx_rowstart, h->tw,
+    k_dx_wave<G><<<DX_WAVE_CTAS * num_sms(h), DX_INV_THREADS, smem, s>>>(h->dx_y, h->blk_slot, h->pix_flag, h->dx_rowstart, h->tw,
                                                                c, queue, wave, possum);
     kt_end(h, TRED_KT_DX_WAVE, s);
     h->launches += 1;
