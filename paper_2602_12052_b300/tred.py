@@ -399,6 +399,105 @@ class Simulator:
         }
 
 
+class StreamRunner:
+    """A stream of host-resident events through one Simulator with the host copies
+    overlapped with the computation.  Event k's deposits are copied (from pinned host
+    memory, on an input stream) into one of two device input sets while event k - 1
+    computes; at the end of its step the device counts and the capacity-sized hit list
+    are copied on the device into one of two staging sets, and read back to pinned host
+    memory on an output stream while event k + 1 computes.  Results come back in event
+    order, two events behind the submissions (queue depth two).  Every wait is a CUDA
+    event: the host blocks only when it takes a result."""
+
+    FIELDS = ("x", "y", "z", "t0", "ne")
+
+    def __init__(self, sim: Simulator, max_deposits: int, readout: bool = True, timing: bool = False):
+        self.sim = sim
+        self.readout = readout
+        # timing: CUDA events around each step on the compute stream; take() then adds
+        # the step's device milliseconds to its result ("step_ms")
+        self.timing = timing
+        self.ev_t = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(2)]
+        d = sim.device
+        self.compute = torch.cuda.current_stream(d)
+        self.s_in = torch.cuda.Stream(d)
+        self.s_out = torch.cuda.Stream(d)
+        self.inputs = [{f: torch.empty(max(max_deposits, 1), dtype=torch.float32, device=d) for f in self.FIELDS}
+                       for _ in range(2)]
+        self.stage = [{"counts": torch.empty_like(sim.counts), "hit_pixel": torch.empty_like(sim.hit_pixel),
+                       "hit_tick": torch.empty_like(sim.hit_tick), "hit_charge": torch.empty_like(sim.hit_charge)}
+                      for _ in range(2)]
+        self.host = [{k: torch.empty(v.shape, dtype=v.dtype).pin_memory() for k, v in st.items()}
+                     for st in self.stage]
+        self.ev_in_ready = [torch.cuda.Event() for _ in range(2)]
+        self.ev_step_done = [torch.cuda.Event() for _ in range(2)]
+        self.ev_d2h_done = [torch.cuda.Event() for _ in range(2)]
+        self.pending = []          # (slot, tag) of the submitted events not yet taken, oldest first
+        self.count = 0
+        self.h2d_bytes = 0
+        self.d2h_bytes = sum(v.numel() * v.element_size() for v in self.stage[0].values())
+
+    def submit(self, host: dict, n: int, tag=None):
+        """Enqueue one event: host[f] pinned float32 tensors of at least n deposits.
+        Returns the (tag, result) of the event submitted two calls earlier, or None."""
+        out = self.take() if len(self.pending) == 2 else None
+        b = self.count % 2
+        inp, st = self.inputs[b], self.stage[b]
+        with torch.cuda.stream(self.s_in):
+            if self.count >= 2:
+                self.s_in.wait_event(self.ev_step_done[b])   # event k - 2 has read this input set
+            for f in self.FIELDS:
+                if n:
+                    inp[f][:n].copy_(host[f][:n], non_blocking=True)
+            self.ev_in_ready[b].record(self.s_in)
+        self.h2d_bytes = 4 * n * len(self.FIELDS)
+        self.compute.wait_event(self.ev_in_ready[b])
+        if self.timing:
+            self.ev_t[b][0].record(self.compute)
+        self.sim.step(n, inp["x"], inp["y"], inp["z"], inp["t0"], inp["ne"], stream=self.compute,
+                      readout=self.readout)
+        if self.timing:
+            self.ev_t[b][1].record(self.compute)
+        if self.count >= 2:
+            self.compute.wait_event(self.ev_d2h_done[b])   # event k - 2's staging has been read back
+        with torch.cuda.stream(self.compute):
+            st["counts"].copy_(self.sim.counts, non_blocking=True)
+            st["hit_pixel"].copy_(self.sim.hit_pixel, non_blocking=True)
+            st["hit_tick"].copy_(self.sim.hit_tick, non_blocking=True)
+            st["hit_charge"].copy_(self.sim.hit_charge, non_blocking=True)
+        self.ev_step_done[b].record(self.compute)
+        with torch.cuda.stream(self.s_out):
+            self.s_out.wait_event(self.ev_step_done[b])
+            for k, v in st.items():
+                self.host[b][k].copy_(v, non_blocking=True)
+            self.ev_d2h_done[b].record(self.s_out)
+        self.pending.append((b, tag))
+        self.count += 1
+        return out
+
+    def take(self):
+        """Wait for the oldest submitted event and return (tag, result): counts (n_blocks,
+        n_pixels, n_hits) and host copies of its hit list."""
+        b, tag = self.pending.pop(0)
+        self.ev_d2h_done[b].synchronize()
+        h = self.host[b]
+        nb, npix, nh = (int(v) for v in h["counts"][:3])
+        nh_k = min(nh, h["hit_pixel"].numel())
+        res = {"n_blocks": nb, "n_pixels": npix, "n_hits": nh,
+               "hit_pixel": h["hit_pixel"][:nh_k].numpy().copy(), "hit_tick": h["hit_tick"][:nh_k].numpy().copy(),
+               "hit_charge": h["hit_charge"][:nh_k].numpy().copy()}
+        if self.timing:
+            res["step_ms"] = self.ev_t[b][0].elapsed_time(self.ev_t[b][1])
+        return tag, res
+
+    def drain(self):
+        """Every result still pending, oldest first."""
+        out = []
+        while self.pending:
+            out.append(self.take())
+        return out
+
+
 # ----------------------------------------------------------------- differentiation
 class LineSimulator(Simulator):
     """The hot path for line-shape track segments (Sec. II-C, Eq. qline): segment
