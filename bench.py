@@ -472,13 +472,14 @@ def run_batched(args):
     rows_dx, cols_dx = tred.tred_direct_counts(sim.h)
     peak_meas, sms = measured_fp32_peak()
     if cm == 4:
-        kr = direct_rooflines(cfg, rows_dx, cols_dx, nb, kernel_ms, clocks)
+        kr = direct_rooflines(cfg, rows_dx, cols_dx, nb, kernel_ms, clocks, npix)
         roof = dict(kr[next(iter(kr))])
         roof.update({"kernels": kr, "kernel_ms_per_step": kernel_ms, "rows": rows_dx, "nonempty_columns": cols_dx,
                      "convolution_ms": conv_ms})
     else:
         roof = alu_roofline("tred_convolve_range (k_conv_spec + inverse time transform), all chunks of one step",
                             conv_flop_per_block(cfg.lt), nb, conv_ms, clocks, peak_meas)
+    batch_fused = sim.fuse_gather
     del sim
     torch.cuda.empty_cache()
     # one event at a time through the same kernels (no graph, one launch sequence each)
@@ -486,7 +487,8 @@ def run_batched(args):
     bmax = max(autotune.probe_blocks(cfg, [e], resp)[0] for e in events)
     one = tred.BatchSimulator(cfg, resp, [events[0]], max_blocks=bmax + 8,
                               max_pixels=min(cfg.npx * cfg.npx, (bmax + 8) * (cfg.bp + cfg.kp - 1) ** 2),
-                              chunk_blocks=2048, n_events=1, max_deposits=nmax, conv_mode=cm)
+                              chunk_blocks=2048, n_events=1, max_deposits=nmax, conv_mode=cm,
+                              fuse_gather=batch_fused)
     per_event = []
     for e in events:
         one.load([e])
@@ -504,7 +506,9 @@ def run_batched(args):
            "autotune_ms_per_kdepos": {f"{k[0]}x{k[0]}x{k[1]}/lt{k[2]}": 1e3 * v for k, v in timings.items()},
            "autotune_s": tune_s,
            "convolution": {0: "FFT form, persistent effective charge + convolution over the block queue",
-                           4: "direct spatial form (tensor-core GEMM per frequency bin), chunks of 2048 blocks"}[cm]},
+                           4: "direct spatial form (tensor-core GEMM per frequency bin), chunks of 2048 blocks"
+                              + (" up to the output spectra (kept for every slot), then the inverse time DFT "
+                                 "fused with the gather per 8x8 pixel tile" if batch_fused else "")}[cm]},
           dtype={0: "f32", 4: "f32+bf16x3"}[cm],
           events_per_s=args.events / (ms_graph / 1e3),
           per_event={"ms_total": ms_single, "depos_per_s": ntot / (ms_single / 1e3),
@@ -576,7 +580,7 @@ def run_lines(args):
     clocks = clk.summary()
     peak_meas, _ = measured_fp32_peak()
     if cm == 4:
-        kr = direct_rooflines(cfg, rows_dx, cols_dx, nb, kernel_ms, clocks)
+        kr = direct_rooflines(cfg, rows_dx, cols_dx, nb, kernel_ms, clocks, npix)
         roof = dict(kr[next(iter(kr))])
         roof.update({"kernels": kr, "kernel_ms_per_step": kernel_ms, "rows": rows_dx, "nonempty_columns": cols_dx})
     else:

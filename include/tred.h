@@ -112,6 +112,12 @@ typedef struct {
                                    of its forward DFT and GEMM, a multiple of 128 (device
                                    memory 4 (lt/2 + 1) 2 n_sub^2 bytes per row); 0: 131072.
                                    Larger row sets run as several launch pairs. */
+    int32_t conv_keep_spectra;  /* conv_mode 4: 1 = the handle keeps every slot's output
+                                   spectrum (max_blocks (lt/2 + 1) 256 8 bytes) and pixel
+                                   mask, indexed by absolute slot, so that the electrode gather
+                                   can run once after tred_convolve_spectra_range has covered
+                                   the slots in chunks (tred_wave_gather_readout); 0 = the
+                                   spectra of one pass of at most 16384 slots. */
 } tred_params;
 
 /* Pixel readout (Sec. II-E): the trigger-reset scheme and the two variants the
@@ -400,7 +406,8 @@ int32_t tred_gather_readout(tred_handle *h, const int32_t *block_ids, const int3
  *  - qeff: as tred_convolve; pixel_ids [max_pixels], waveforms [max_pixels][nt],
  *    n_pixels_dev[0] = npix as tred_gather_pixels; hit buffers as tred_readout.
  *  - Shapes: conv_mode 4, bp = 8, kp = bp + 1, nr - 1 <= bt, nt / bt <= 128,
- *    max_blocks <= the direct form's slots per pass (16384), compensated_gather 0;
+ *    max_blocks <= the direct form's slots per pass (16384, or any with
+ *    conv_keep_spectra 1), compensated_gather 0;
  *    TRED_ERR_INVALID_ARG otherwise (tred_convolve_gather_supported says beforehand).
  *  Graph-capturable (counts stay on the device). */
 int32_t tred_convolve_gather_readout(tred_handle *h, const int32_t *block_ids, const int32_t *n_blocks_dev,
@@ -410,6 +417,25 @@ int32_t tred_convolve_gather_readout(tred_handle *h, const int32_t *block_ids, c
                                      void *stream);
 /* 1 when the handle's shape allows tred_convolve_gather_readout, else 0 (-1 for null). */
 int32_t tred_convolve_gather_supported(const tred_handle *h);
+
+/* The two halves of tred_convolve_gather_readout, for slots processed in chunks (Sec.
+ * III-B-2: many events batched through bounded Q^eff chunks).
+ * tred_convolve_spectra_range: the direct form's convolution of slots [slot_base,
+ *   slot_base + slot_count) up to their output spectra, kept in the handle; qeff is the
+ *   chunk tred_effq_range wrote with the same slot_base.  slot_base > 0 needs
+ *   conv_keep_spectra 1 (TRED_ERR_INVALID_ARG otherwise); the shape rules of
+ *   tred_convolve_gather_readout apply.
+ * tred_wave_gather_readout: once every active slot's spectra are in place (the ranges
+ *   cover slots 0 .. n_blocks - 1), the pixel list, the inverse time DFT per pixel tile
+ *   into the waveforms and, with rp non-null, the readout; arguments as
+ *   tred_convolve_gather_readout without qeff.
+ * Both graph-capturable. */
+int32_t tred_convolve_spectra_range(tred_handle *h, const int32_t *block_ids, const int32_t *n_blocks_dev,
+                                    int32_t slot_base, int32_t slot_count, const float *qeff, void *stream);
+int32_t tred_wave_gather_readout(tred_handle *h, const int32_t *block_ids, const int32_t *n_blocks_dev,
+                                 int32_t *pixel_ids, float *waveforms, int32_t *n_pixels_dev,
+                                 const tred_readout_params *rp, int32_t *hit_pixel, int32_t *hit_tick,
+                                 float *hit_charge, int32_t *n_hits_dev, int32_t max_hits, void *stream);
 
 /* ---- Differentiable simulation (Sec. V-C).  Loss L = 1/2 sum (I - I*)^2 over
  * pixels and ticks; gradients through the whole path with the raster windows held

@@ -36,7 +36,8 @@ EXPORTS = [
     "tred_set_transport", "tred_residual", "tred_adjoint", "tred_param_grads",
     "tred_drift_events", "tred_effq_range", "tred_convolve_range", "tred_drift_lines", "tred_effq_lines",
     "tred_wait_selftest", "tred_gather_readout", "tred_fp32_peak", "tred_effq_convolve",
-    "tred_convolve_gather_readout", "tred_convolve_gather_supported",
+    "tred_convolve_gather_readout", "tred_convolve_gather_supported", "tred_convolve_spectra_range",
+    "tred_wave_gather_readout",
 ]
 
 
@@ -55,7 +56,7 @@ class Params(ctypes.Structure):
                 ("gl_order", ctypes.c_int32), ("effq_mode", ctypes.c_int32),
                 ("conv_mode", ctypes.c_int32), ("mpcp", ctypes.c_int32),
                 ("compensated_gather", ctypes.c_int32), ("effq_skip_empty", ctypes.c_int32),
-                ("conv_rows_cap", ctypes.c_int32)]
+                ("conv_rows_cap", ctypes.c_int32), ("conv_keep_spectra", ctypes.c_int32)]
 
 
 class ReadoutParams(ctypes.Structure):
@@ -104,6 +105,9 @@ def load(path: str | None = None) -> ctypes.CDLL:
     lib.tred_convolve_gather_readout.argtypes = [_P, _P, _P, _P, _P, _P, _P, ctypes.POINTER(ReadoutParams), _P, _P,
                                                  _P, _P, _I, _P]
     lib.tred_convolve_gather_supported.argtypes = [_P]
+    lib.tred_convolve_spectra_range.argtypes = [_P, _P, _P, _I, _I, _P, _P]
+    lib.tred_wave_gather_readout.argtypes = [_P, _P, _P, _P, _P, _P, ctypes.POINTER(ReadoutParams), _P, _P, _P, _P,
+                                             _I, _P]
     lib.tred_set_response.argtypes = [_P, _P, _P]
     lib.tred_drift.argtypes = [_P, _I, _P, _P, _P, _P, _P, ctypes.POINTER(Deposits), _P]
     lib.tred_blockbin.argtypes = [_P, _I, ctypes.POINTER(Deposits), _P, _P, _P, _P, _I, _P, _P]

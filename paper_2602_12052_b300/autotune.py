@@ -67,17 +67,27 @@ def count_pixels(cfg, n_events, block_ids):
     return int(flags.sum())
 
 
-def make_batch(cfg, events, resp, chunk_blocks=2048, device=None, persistent=None, conv_mode=0):
+def make_batch(cfg, events, resp, chunk_blocks=2048, device=None, persistent=None, conv_mode=0, fuse_gather=None):
     """A BatchSimulator sized to the batch; in the FFT form (conv_mode 0) persistent
     (default: whenever the FFT length allows it, lt = 384 or 512) runs the effective charge
     and the convolution as one persistent launch over the batch's active-block queue; the
-    direct form (conv_mode 4) runs chunks of chunk_blocks slots."""
+    direct form (conv_mode 4) runs chunks of chunk_blocks slots, by default (fuse_gather
+    None) up to the output spectra and then the inverse time DFT fused with the gather
+    where the block shape allows it (bp 8, kp 9, nr - 1 <= bt)."""
     nb, npix = probe_blocks(cfg, events, resp, device)
     if persistent is None:
         persistent = cfg.lt in (384, 512) and conv_mode == 0
-    return tred.BatchSimulator(cfg, resp, events, max_blocks=nb + 8, max_pixels=npix,
-                               chunk_blocks=chunk_blocks, device=device, persistent=persistent,
-                               conv_mode=conv_mode)
+
+    def make(fg):
+        return tred.BatchSimulator(cfg, resp, events, max_blocks=nb + 8, max_pixels=npix,
+                                   chunk_blocks=chunk_blocks, device=device, persistent=persistent,
+                                   conv_mode=conv_mode, fuse_gather=fg)
+    if conv_mode == 4 and fuse_gather is None:
+        try:
+            return make(True)
+        except ValueError:
+            return make(False)
+    return make(bool(fuse_gather))
 
 
 def autotune(cfg, events, resp, candidates=CANDIDATES, sample=8, device=None, conv_mode=0):

@@ -1039,7 +1039,7 @@ __host__ __device__ constexpr size_t dx_wave_smem(int G) {
 template <int G>
 __global__ void __launch_bounds__(DX_INV_THREADS, DX_WAVE_CTAS)
     k_dx_wave(const float2 *__restrict__ ybuf, const int32_t *__restrict__ slot_of, const int32_t *__restrict__ pix_row,
-              const int32_t *__restrict__ rowstart, const float2 *__restrict__ tw, DxWaveConst c,
+              const uint64_t *__restrict__ pmask, const float2 *__restrict__ tw, DxWaveConst c,
               int32_t *__restrict__ queue, float *__restrict__ wave, float *__restrict__ possum) {
     constexpr int LT = 64 * G;
     constexpr int NPL = LT / 32;
@@ -1100,7 +1100,7 @@ __global__ void __launch_bounds__(DX_INV_THREADS, DX_WAVE_CTAS)
             if (bx >= 0 && bx < c.nbx && byl >= 0 && byl < c.nby_e) {
                 sl = slot_of[((int64_t)(ev * c.nby_e + byl) * c.nbx + bx) * c.nbt + bt];
                 found |= sl >= 0;   // its pixels are active: their rows are written, zeros if need be
-                if (sl >= 0 && rowstart[sl + 1] == rowstart[sl]) sl = -1;   // no charge: no spectrum written
+                if (sl >= 0 && pmask[sl] == 0ull) sl = -1;   // no pixel holds charge: no spectrum written
             }
             tslot[k][bt] = sl;
         }
@@ -1338,10 +1338,14 @@ static int run_direct(tred_handle *h, const DxConst &c, const int32_t *n_blocks_
     const int end = slot_base + slot_count;
     for (int base = slot_base; base < end; base += h->dx_blocks) {
         const int cnt = h->dx_blocks < end - base ? h->dx_blocks : end - base;
-        k_dx_pixmask<<<sms * 4, 256, 0, s>>>(n_blocks_dev, h->colmask, c.nch, c.bp2, base, cnt, h->dx_pmask,
-                                             h->dx_pcnt);
-        k_dx_rows<<<1, DX_ROWS_THREADS, 0, s>>>(n_blocks_dev, h->dx_pmask, h->dx_pcnt, base, cnt, h->dx_rows,
-                                                h->dx_rowstart, h->dx_meta);
+        // with conv_keep_spectra the pixel masks and the spectra are stored at absolute
+        // slots (one pass covers the call), otherwise relative to the pass
+        const size_t ao = h->p.conv_keep_spectra ? (size_t)base : 0;
+        float2 *ybase = h->dx_y + ao * c.nbins * (LP * LP);
+        k_dx_pixmask<<<sms * 4, 256, 0, s>>>(n_blocks_dev, h->colmask, c.nch, c.bp2, base, cnt, h->dx_pmask + ao,
+                                             h->dx_pcnt + ao);
+        k_dx_rows<<<1, DX_ROWS_THREADS, 0, s>>>(n_blocks_dev, h->dx_pmask + ao, h->dx_pcnt + ao, base, cnt,
+                                                h->dx_rows, h->dx_rowstart, h->dx_meta);
         h->launches += 2;
         const int64_t max_rows = (int64_t)cnt * c.bp2;
         const int nrc = (int)((max_rows + c.rows_cap - 1) / c.rows_cap);
@@ -1350,17 +1354,17 @@ static int run_direct(tred_handle *h, const DxConst &c, const int32_t *n_blocks_
             kt_begin(h, TRED_KT_DX_FWD, s);
             k_dx_fwd<G><<<DX_FWD_CTAS * sms, DX_FWD_THREADS, fwd_smem, s>>>(qeff, h->colmask, h->dx_rows, h->dx_rowstart, h->dx_meta,
                                                              h->tw, c, base, qbase, row0, k == 0 ? 1 : 0, h->dx_qhi,
-                                                             h->dx_qlo, h->dx_y);
+                                                             h->dx_qlo, ybase);
             kt_end(h, TRED_KT_DX_FWD, s);
             kt_begin(h, TRED_KT_DX_GEMM, s);
             k_dx_gemm<<<sms, DX_GEMM_THREADS, gemm_smem, s>>>(tah, tal, tbh, tbl, h->dx_rows, h->dx_rowstart,
-                                                              h->dx_meta, c, row0, h->dx_y, h->status);
+                                                              h->dx_meta, c, row0, ybase, h->status);
             kt_end(h, TRED_KT_DX_GEMM, s);
             h->launches += 2;
         }
         if (!inverse) continue;   // the spectra stay in dx_y for k_dx_wave (a single pass)
         kt_begin(h, TRED_KT_DX_INV, s);
-        k_dx_inv<G><<<2 * sms, DX_INV_THREADS, inv_smem, s>>>(h->dx_y, h->dx_rowstart, h->dx_meta, h->tw, c, base, out);
+        k_dx_inv<G><<<2 * sms, DX_INV_THREADS, inv_smem, s>>>(ybase, h->dx_rowstart, h->dx_meta, h->tw, c, base, out);
         kt_end(h, TRED_KT_DX_INV, s);
         h->launches += 1;
     }
@@ -1398,19 +1402,22 @@ static int run_wave(tred_handle *h, int32_t *queue, float *wave, float *possum, 
     int rc = check_cuda(h, cudaMemsetAsync(queue, 0, sizeof(int32_t), s), "tile queue reset");
     if (rc) return rc;
     kt_begin(h, TRED_KT_DX_WAVE, s);
-    k_dx_wave<G><<<DX_WAVE_CTAS * num_sms(h), DX_INV_THREADS, smem, s>>>(h->dx_y, h->blk_slot, h->pix_flag, h->dx_rowstart, h->tw,
+    k_dx_wave<G><<<DX_WAVE_CTAS * num_sms(h), DX_INV_THREADS, smem, s>>>(h->dx_y, h->blk_slot, h->pix_flag, h->dx_pmask, h->tw,
                                                                c, queue, wave, possum);
     kt_end(h, TRED_KT_DX_WAVE, s);
     h->launches += 1;
     return check_cuda(h, cudaGetLastError(), "direct-form inverse + gather launch");
 }
 
-// a4 up to the per-block spectra (no inverse), then, after the pixel list and the slot map
-// are built (launch_pixel_list), the inverse time DFT of each tile straight into the waves
-int launch_direct_spectra(tred_handle *h, const int32_t *n_blocks_dev, const float *qeff, cudaStream_t s) {
+// a4 up to the per-block spectra of slots [slot_base, slot_base + slot_count) (no inverse;
+// qeff rows from slot_base), then, once every active slot's spectra are in place and the
+// pixel list and the slot map are built (launch_pixel_list), the inverse time DFT of each
+// tile straight into the waves
+int launch_direct_spectra(tred_handle *h, const int32_t *n_blocks_dev, const float *qeff, int slot_base,
+                          int slot_count, cudaStream_t s) {
     const DxConst c = dx_const_of(h);
-    if (c.lt == 512) return run_direct<8>(h, c, n_blocks_dev, qeff, nullptr, 0, h->max_blocks, 0, s, false);
-    if (c.lt == 384) return run_direct<6>(h, c, n_blocks_dev, qeff, nullptr, 0, h->max_blocks, 0, s, false);
+    if (c.lt == 512) return run_direct<8>(h, c, n_blocks_dev, qeff, nullptr, slot_base, slot_count, slot_base, s, false);
+    if (c.lt == 384) return run_direct<6>(h, c, n_blocks_dev, qeff, nullptr, slot_base, slot_count, slot_base, s, false);
     return set_error(h, TRED_ERR_INVALID_ARG, "direct form: lt must be 384 or 512");
 }
 int launch_direct_wave(tred_handle *h, int32_t *queue, float *wave, float *possum, cudaStream_t s) {

@@ -184,6 +184,7 @@ static int validate(const tred_geometry *g, const tred_params *p, char *msg, siz
     if (p->mpcp != 0 && p->mpcp != 1) return bad("mpcp must be 0 or 1");
     if (p->effq_skip_empty != 0 && p->effq_skip_empty != 1) return bad("effq_skip_empty must be 0 or 1");
     if (p->conv_rows_cap < 0 || p->conv_rows_cap % 128) return bad("conv_rows_cap must be a non-negative multiple of 128");
+    if (p->conv_keep_spectra != 0 && p->conv_keep_spectra != 1) return bad("conv_keep_spectra must be 0 or 1");
     if (p->effq_skip_empty && p->conv_mode >= 1 && p->conv_mode <= 3)
         return bad("the tensor-core time DFT reads every column: effq_skip_empty must be 0");
     return TRED_OK;
@@ -280,7 +281,7 @@ int32_t tred_create(const tred_geometry *geom, const tred_params *params, int32_
     if (params->conv_mode == 4) {
         const int kq = 32 * ((ns * ns + 15) / 16), npad = (geom->kp * geom->kp + 15) & ~15, nbins = geom->lt / 2 + 1;
         const int bp2 = geom->bp * geom->bp;
-        h->dx_blocks = dx_blocks_of(max_blocks);
+        h->dx_blocks = params->conv_keep_spectra ? max_blocks : dx_blocks_of(max_blocks);
         h->dx_rows_cap = dx_rows_cap_of(h->dx_blocks, bp2, params->conv_rows_cap);
         alloc((void **)&h->dx_bhi, dx_bytes_b(nbins, npad, kq), "alloc direct-form response");
         alloc((void **)&h->dx_blo, dx_bytes_b(nbins, npad, kq), "alloc direct-form response");
@@ -699,35 +700,91 @@ int32_t tred_convolve_gather_supported(const tred_handle *h) {
     return dx_wave_ok(h) ? 1 : 0;
 }
 
-int32_t tred_convolve_gather_readout(tred_handle *h, const int32_t *block_ids, const int32_t *n_blocks_dev,
-                                     const float *qeff, int32_t *pixel_ids, float *waveforms, int32_t *n_pixels_dev,
-                                     const tred_readout_params *rp, int32_t *hit_pixel, int32_t *hit_tick,
-                                     float *hit_charge, int32_t *n_hits_dev, int32_t max_hits, void *stream) {
-    tred::CallRange range_("tred_convolve_gather_readout");
-    if (!h) return TRED_ERR_INVALID_ARG;
-    if (!h->response_ready)
-        return set_error(h, TRED_ERR_NOT_READY, "tred_convolve_gather_readout: call tred_set_response first");
-    if (!dx_wave_ok(h))
-        return set_error(h, TRED_ERR_INVALID_ARG,
-                         "tred_convolve_gather_readout: needs conv_mode 4, bp 8, kp 9, nr - 1 <= bt, nt / bt <= 128, "
-                         "max_blocks within one pass and compensated_gather 0");
-    if (!block_ids || !n_blocks_dev || !qeff || !pixel_ids || !waveforms || !n_pixels_dev)
-        return set_error(h, TRED_ERR_INVALID_ARG, "tred_convolve_gather_readout: null pointer");
+static int wave_args_ok(tred_handle *h, const char *fn, const tred_readout_params *rp, int32_t *hit_pixel,
+                        int32_t *hit_tick, float *hit_charge, int32_t *n_hits_dev, int32_t max_hits) {
     if (rp && (!n_hits_dev || max_hits < 0 || (max_hits > 0 && (!hit_pixel || !hit_tick || !hit_charge))))
-        return set_error(h, TRED_ERR_INVALID_ARG, "tred_convolve_gather_readout: null hit buffers");
+        return set_error(h, TRED_ERR_INVALID_ARG, "%s: null hit buffers", fn);
     if (rp && (rp->clock_ticks < 1 || rp->hold_ticks < 0 || rp->reset_ticks < 0 || rp->mode < 0 || rp->mode > 2 ||
                (rp->mode == 1 && (rp->n_samples < 1 || rp->hold_ticks < 1))))
-        return set_error(h, TRED_ERR_INVALID_ARG, "tred_convolve_gather_readout: bad readout parameters");
-    const cudaStream_t s = (cudaStream_t)stream;
-    int rc = launch_direct_spectra(h, n_blocks_dev, qeff, s);
-    if (rc) return rc;
+        return set_error(h, TRED_ERR_INVALID_ARG, "%s: bad readout parameters", fn);
+    return TRED_OK;
+}
+
+static int wave_shape_ok(tred_handle *h, const char *fn) {
+    if (!h->response_ready) return set_error(h, TRED_ERR_NOT_READY, "%s: call tred_set_response first", fn);
+    if (!dx_wave_ok(h))
+        return set_error(h, TRED_ERR_INVALID_ARG,
+                         "%s: needs conv_mode 4, bp 8, kp 9, nr - 1 <= bt, nt / bt <= 128, max_blocks within one "
+                         "pass (or conv_keep_spectra 1) and compensated_gather 0",
+                         fn);
+    return TRED_OK;
+}
+
+// pixel list, the fused inverse time DFT + gather, and the readout (rp non-null)
+static int wave_gather_readout(tred_handle *h, const int32_t *block_ids, const int32_t *n_blocks_dev,
+                               int32_t *pixel_ids, float *waveforms, int32_t *n_pixels_dev,
+                               const tred_readout_params *rp, int32_t *hit_pixel, int32_t *hit_tick,
+                               float *hit_charge, int32_t *n_hits_dev, int32_t max_hits, cudaStream_t s) {
     int32_t *queue = nullptr;
-    rc = launch_pixel_list(h, block_ids, n_blocks_dev, pixel_ids, n_pixels_dev, s, &queue);
+    int rc = launch_pixel_list(h, block_ids, n_blocks_dev, pixel_ids, n_pixels_dev, s, &queue);
     if (rc) return rc;
     rc = launch_direct_wave(h, queue, waveforms, h->px_possum, s);
     if (rc || !rp) return rc;
     return launch_readout(h, *rp, pixel_ids, waveforms, n_pixels_dev, hit_pixel, hit_tick, hit_charge, n_hits_dev,
                           max_hits, s, h->px_possum);
+}
+
+int32_t tred_convolve_gather_readout(tred_handle *h, const int32_t *block_ids, const int32_t *n_blocks_dev,
+                                     const float *qeff, int32_t *pixel_ids, float *waveforms, int32_t *n_pixels_dev,
+                                     const tred_readout_params *rp, int32_t *hit_pixel, int32_t *hit_tick,
+                                     float *hit_charge, int32_t *n_hits_dev, int32_t max_hits, void *stream) {
+    tred::CallRange range_("tred_convolve_gather_readout");
+    const char *fn = "tred_convolve_gather_readout";
+    if (!h) return TRED_ERR_INVALID_ARG;
+    int rc = wave_shape_ok(h, fn);
+    if (rc) return rc;
+    if (!block_ids || !n_blocks_dev || !qeff || !pixel_ids || !waveforms || !n_pixels_dev)
+        return set_error(h, TRED_ERR_INVALID_ARG, "%s: null pointer", fn);
+    rc = wave_args_ok(h, fn, rp, hit_pixel, hit_tick, hit_charge, n_hits_dev, max_hits);
+    if (rc) return rc;
+    const cudaStream_t s = (cudaStream_t)stream;
+    rc = launch_direct_spectra(h, n_blocks_dev, qeff, 0, h->max_blocks, s);
+    if (rc) return rc;
+    return wave_gather_readout(h, block_ids, n_blocks_dev, pixel_ids, waveforms, n_pixels_dev, rp, hit_pixel,
+                               hit_tick, hit_charge, n_hits_dev, max_hits, s);
+}
+
+int32_t tred_convolve_spectra_range(tred_handle *h, const int32_t *block_ids, const int32_t *n_blocks_dev,
+                                    int32_t slot_base, int32_t slot_count, const float *qeff, void *stream) {
+    tred::CallRange range_("tred_convolve_spectra_range");
+    const char *fn = "tred_convolve_spectra_range";
+    if (!h) return TRED_ERR_INVALID_ARG;
+    int rc = wave_shape_ok(h, fn);
+    if (rc) return rc;
+    if (!h->p.conv_keep_spectra && slot_base > 0)
+        return set_error(h, TRED_ERR_INVALID_ARG, "%s: slot ranges past slot 0 need conv_keep_spectra 1", fn);
+    if (!block_ids || !n_blocks_dev || !qeff || slot_base < 0 || slot_count < 0)
+        return set_error(h, TRED_ERR_INVALID_ARG, "%s: bad arguments", fn);
+    const int count = slot_count < h->max_blocks - slot_base ? slot_count : h->max_blocks - slot_base;
+    if (count <= 0) return TRED_OK;
+    return launch_direct_spectra(h, n_blocks_dev, qeff, slot_base, count, (cudaStream_t)stream);
+}
+
+int32_t tred_wave_gather_readout(tred_handle *h, const int32_t *block_ids, const int32_t *n_blocks_dev,
+                                 int32_t *pixel_ids, float *waveforms, int32_t *n_pixels_dev,
+                                 const tred_readout_params *rp, int32_t *hit_pixel, int32_t *hit_tick,
+                                 float *hit_charge, int32_t *n_hits_dev, int32_t max_hits, void *stream) {
+    tred::CallRange range_("tred_wave_gather_readout");
+    const char *fn = "tred_wave_gather_readout";
+    if (!h) return TRED_ERR_INVALID_ARG;
+    int rc = wave_shape_ok(h, fn);
+    if (rc) return rc;
+    if (!block_ids || !n_blocks_dev || !pixel_ids || !waveforms || !n_pixels_dev)
+        return set_error(h, TRED_ERR_INVALID_ARG, "%s: null pointer", fn);
+    rc = wave_args_ok(h, fn, rp, hit_pixel, hit_tick, hit_charge, n_hits_dev, max_hits);
+    if (rc) return rc;
+    return wave_gather_readout(h, block_ids, n_blocks_dev, pixel_ids, waveforms, n_pixels_dev, rp, hit_pixel,
+                               hit_tick, hit_charge, n_hits_dev, max_hits, (cudaStream_t)stream);
 }
 
 int32_t tred_wait_selftest(tred_handle *h, int64_t limit_cycles, void *stream) {

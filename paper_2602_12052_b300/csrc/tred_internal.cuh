@@ -155,7 +155,8 @@ int launch_direct(tred_handle *h, const int32_t *n_blocks_dev, const float *qeff
 // fused inverse DFT + gather of conv_mode 4 (tred_convolve_gather_readout): the spectra of
 // every slot in one pass, then k_dx_wave over the pixel list that launch_pixel_list built
 bool dx_wave_ok(const tred_handle *h);
-int launch_direct_spectra(tred_handle *h, const int32_t *n_blocks_dev, const float *qeff, cudaStream_t s);
+int launch_direct_spectra(tred_handle *h, const int32_t *n_blocks_dev, const float *qeff, int slot_base,
+                          int slot_count, cudaStream_t s);
 int launch_direct_wave(tred_handle *h, int32_t *queue, float *wave, float *possum, cudaStream_t s);
 size_t dx_bytes_b(int nbins, int npad, int kq);
 size_t dx_bytes_q(int nbins, int rows_cap, int kq);

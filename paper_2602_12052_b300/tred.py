@@ -38,14 +38,24 @@ def geometry(cfg, n_events: int = 1) -> Geometry:
                     n_events=n_events)
 
 
-def params(cfg, effq_mode=0, mpcp=1, compensated_gather=0, conv_mode=0, effq_skip_empty=0, conv_rows_cap=0) -> Params:
+def params(cfg, effq_mode=0, mpcp=1, compensated_gather=0, conv_mode=0, effq_skip_empty=0, conv_rows_cap=0,
+           conv_keep_spectra=0) -> Params:
     return Params(v_cm_per_us=cfg.v_cm_per_us, DL_cm2_per_s=cfg.DL_cm2_per_s,
                   DT_cm2_per_s=cfg.DT_cm2_per_s, lifetime_us=cfg.lifetime_us,
                   sigma0_cells_xy=cfg.sigma0_cells_xy, sigma0_ticks=cfg.sigma0_ticks,
                   nsigma=cfg.nsigma, max_drift_cm=cfg.max_drift_cm, gl_order=cfg.gl_order,
                   effq_mode=effq_mode, conv_mode=conv_mode, mpcp=mpcp,
                   compensated_gather=compensated_gather, effq_skip_empty=effq_skip_empty,
-                  conv_rows_cap=conv_rows_cap)
+                  conv_rows_cap=conv_rows_cap, conv_keep_spectra=conv_keep_spectra)
+
+
+def fused_gather_shape_ok(cfg, conv_mode: int) -> bool:
+    """The block shapes the direct form's fused inverse + gather covers (the library
+    checks the same rules in tred_convolve_gather_supported): conv_mode 4, lt 384 or 512,
+    8 x 8-pixel blocks with a 9 x 9 response (kp = bp + 1), a response no longer than a
+    time block plus one tick, at most 128 time blocks."""
+    return (conv_mode == 4 and cfg.lt in (384, 512) and cfg.bp == 8 and cfg.kp == cfg.bp + 1
+            and cfg.nr - 1 <= cfg.bt and cfg.nt // cfg.bt <= 128)
 
 
 def readout_params(cfg) -> ReadoutParams:
@@ -200,6 +210,27 @@ def tred_convolve_gather_readout(h: Handle, block_ids, n_blocks_dev, qeff, pixel
         _stream(stream)))
 
 
+def tred_convolve_spectra_range(h: Handle, block_ids, n_blocks_dev, slot_base: int, slot_count: int, qeff,
+                                stream=None):
+    """The direct form's convolution of a slot range up to the output spectra (kept in the
+    handle for tred_wave_gather_readout)."""
+    h.check(h.lib.tred_convolve_spectra_range(h.h, _ptr(block_ids), _ptr(n_blocks_dev), int(slot_base),
+                                              int(slot_count), _ptr(qeff), _stream(stream)))
+
+
+def tred_wave_gather_readout(h: Handle, block_ids, n_blocks_dev, pixel_ids, waveforms, n_pixels_dev,
+                             rp: ReadoutParams | None = None, hit_pixel=None, hit_tick=None, hit_charge=None,
+                             n_hits_dev=None, stream=None):
+    """Pixel list, the inverse time DFT per pixel tile into the waveforms (from the kept
+    spectra of every active slot) and, with rp, the readout."""
+    h.check(h.lib.tred_wave_gather_readout(
+        h.h, _ptr(block_ids), _ptr(n_blocks_dev), _ptr(pixel_ids), _ptr(waveforms), _ptr(n_pixels_dev),
+        ctypes.byref(rp) if rp is not None else None, _ptr(hit_pixel) if hit_pixel is not None else None,
+        _ptr(hit_tick) if hit_tick is not None else None, _ptr(hit_charge) if hit_charge is not None else None,
+        _ptr(n_hits_dev) if n_hits_dev is not None else None, hit_pixel.numel() if hit_pixel is not None else 0,
+        _stream(stream)))
+
+
 def tred_readout(h: Handle, rp: ReadoutParams, pixel_ids, waveforms, n_pixels_dev, hit_pixel,
                  hit_tick, hit_charge, n_hits_dev, stream=None):
     h.check(h.lib.tred_readout(h.h, ctypes.byref(rp), _ptr(pixel_ids), _ptr(waveforms),
@@ -308,9 +339,11 @@ class Simulator:
         # fuse_gather: conv_mode 4's inverse time DFT per pixel tile straight into the waves
         # (tred_convolve_gather_readout); out_blocks is then not written
         self.fuse_gather = bool(fuse_gather)
+        if self.fuse_gather and not fused_gather_shape_ok(cfg, conv_mode):
+            raise ValueError("fuse_gather needs conv_mode 4, lt 384 or 512, bp 8, kp 9, nr - 1 <= bt, nt / bt <= 128")
         self.device = torch.device(device or "cuda")
         self.h = Handle(geometry(cfg), params(cfg, effq_mode, mpcp, compensated_gather, conv_mode, effq_skip_empty,
-                                              conv_rows_cap),
+                                              conv_rows_cap, 1 if self.fuse_gather and conv_mode == 4 else 0),
                         max_deposits, max_blocks, max_pixels)
         self.rp = readout_params(cfg)
         d = self.device
@@ -586,9 +619,14 @@ class BatchSimulator:
     def __init__(self, cfg, resp: torch.Tensor, events, max_blocks: int, max_pixels: int,
                  chunk_blocks: int = 2048, max_hits: int | None = None, mpcp=1, device=None,
                  n_events: int | None = None, max_deposits: int | None = None, persistent: bool = False,
-                 effq_skip_empty: int = 0, conv_mode: int = 0):
+                 effq_skip_empty: int = 0, conv_mode: int = 0, fuse_gather: bool = False):
         self.cfg = cfg
         self.device = d = torch.device(device or "cuda")
+        # fuse_gather (conv_mode 4): the chunks stop at the output spectra, kept for every
+        # slot, and one launch inverts them per pixel tile into the waveforms
+        self.fuse_gather = bool(fuse_gather) and conv_mode == 4 and not persistent
+        if self.fuse_gather and not fused_gather_shape_ok(cfg, conv_mode):
+            raise ValueError("fuse_gather needs conv_mode 4, lt 384 or 512, bp 8, kp 9, nr - 1 <= bt, nt / bt <= 128")
         self.n_events = n_events or len(events)
         cap = max_deposits or int(sum(len(e["x"]) for e in events))
         # the persistent launch runs the FFT form; the direct form (conv_mode 4) runs the
@@ -596,8 +634,11 @@ class BatchSimulator:
         self.persistent = bool(persistent) and conv_mode == 0
         skip = 1 if (self.persistent or conv_mode == 4) else effq_skip_empty
         self.h = Handle(geometry(cfg, self.n_events),
-                        params(cfg, mpcp=mpcp, effq_skip_empty=skip, conv_mode=conv_mode), max(cap, 1),
+                        params(cfg, mpcp=mpcp, effq_skip_empty=skip, conv_mode=conv_mode,
+                               conv_keep_spectra=1 if self.fuse_gather else 0), max(cap, 1),
                         max_blocks, max_pixels)
+        if self.fuse_gather and not tred_convolve_gather_supported(self.h):
+            raise ValueError("fuse_gather needs conv_mode 4, bp 8, kp 9, nr - 1 <= bt and nt / bt <= 128")
         self.rp = readout_params(cfg)
         if self.persistent:
             # one Q^eff ring row per resident CTA of the persistent launch
@@ -620,7 +661,8 @@ class BatchSimulator:
         self.dep_index = torch.zeros(8 * max(cap, 1), dtype=torch.int32, device=d)
         self.counts = torch.zeros(4, dtype=torch.int32, device=d)
         self.qeff = torch.empty((self.chunk, ns, ns, bp, bp, bt), dtype=torch.float32, device=d)
-        self.out_blocks = torch.empty((max_blocks, 16, 16, lt), dtype=torch.float32, device=d)
+        self.out_blocks = torch.empty((1 if self.fuse_gather else max_blocks, 16, 16, lt), dtype=torch.float32,
+                                      device=d)
         self.pixel_ids = torch.zeros(max_pixels, dtype=torch.int32, device=d)
         self.waveforms = torch.empty((max_pixels, cfg.nt), dtype=torch.float32, device=d)
         mh = max_hits or 4 * max_pixels
@@ -670,10 +712,17 @@ class BatchSimulator:
             if conv_events is not None:
                 ev = (torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
                 ev[0].record()
-            tred_convolve_range(h, self.block_ids, nb_dev, base, self.chunk, self.qeff, self.out_blocks, stream)
+            if self.fuse_gather:
+                tred_convolve_spectra_range(h, self.block_ids, nb_dev, base, self.chunk, self.qeff, stream)
+            else:
+                tred_convolve_range(h, self.block_ids, nb_dev, base, self.chunk, self.qeff, self.out_blocks, stream)
             if ev is not None:
                 ev[1].record()
                 conv_events.append(ev)
+        if self.fuse_gather:
+            tred_wave_gather_readout(h, self.block_ids, nb_dev, self.pixel_ids, self.waveforms, np_dev, self.rp,
+                                     self.hit_pixel, self.hit_tick, self.hit_charge, nh_dev, stream)
+            return
         tred_gather_readout(h, self.block_ids, nb_dev, self.out_blocks, self.pixel_ids, self.waveforms, np_dev,
                             self.rp, self.hit_pixel, self.hit_tick, self.hit_charge, nh_dev, stream)
 

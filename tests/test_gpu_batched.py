@@ -15,11 +15,11 @@ def _tiny_events(k, cfg):
     return [synth.make_deposits(cfg, seed=cfg.seed + 1000 * i) for i in range(k)]
 
 
-def _batch(cfg, events, resp, chunk, persistent=False, conv_mode=0):
+def _batch(cfg, events, resp, chunk, persistent=False, conv_mode=0, fuse_gather=None):
     import torch
     from paper_2602_12052_b300 import autotune
     sim = autotune.make_batch(cfg, events, torch.from_numpy(resp), chunk_blocks=chunk, persistent=persistent,
-                              conv_mode=conv_mode)
+                              conv_mode=conv_mode, fuse_gather=fuse_gather)
     sim.step()
     torch.cuda.synchronize()
     return sim
@@ -46,18 +46,22 @@ def _results(sim):
             "hit_charge": sim.hit_charge[:nh].cpu().numpy()}
 
 
-@pytest.mark.parametrize("chunk,persistent,conv_mode", [(3, False, 0), (64, False, 0), (0, True, 0),
-                                                       (3, False, 4), (64, False, 4)])
-def test_batch_matches_oracle_per_event(chunk, persistent, conv_mode):
+@pytest.mark.parametrize("chunk,persistent,conv_mode,fuse", [(3, False, 0, None), (64, False, 0, None),
+                                                            (0, True, 0, None), (3, False, 4, True),
+                                                            (64, False, 4, True), (3, False, 4, False)])
+def test_batch_matches_oracle_per_event(chunk, persistent, conv_mode, fuse):
     """Eight events of uneven size (one empty, one with a single deposit) through the
     batched path, against the oracle run on each event alone: sub-batches of 3 or 64
     slots, or the one persistent launch over the batch's active-block queue; the FFT form
-    and the direct spatial form (conv_mode 4) of the convolution."""
+    and the direct spatial form (conv_mode 4) of the convolution, the latter with every
+    chunk stopping at the output spectra and one fused inverse + gather over the batch
+    (fuse) or with the per-chunk inverse and the gather."""
     cfg = synth.get_config("tiny")
     resp = synth.make_response(cfg)
     events = _uneven_tiny_events(cfg)
-    sim = _batch(cfg, events, resp, chunk or 64, persistent, conv_mode)
+    sim = _batch(cfg, events, resp, chunk or 64, persistent, conv_mode, fuse)
     assert sim.persistent == persistent
+    assert sim.fuse_gather == bool(fuse)
     assert sim.status()[0] == 0
     res = _results(sim)
     nblk, npx2 = cfg.n_blocks, cfg.npx * cfg.npx
@@ -81,15 +85,16 @@ def test_batch_matches_oracle_per_event(chunk, persistent, conv_mode):
                    cfg.reset_ticks)
 
 
-@pytest.mark.parametrize("persistent", [False, True])
-def test_batch_graph_replay_matches_eager(persistent):
+@pytest.mark.parametrize("persistent,conv_mode", [(False, 0), (True, 0), (False, 4)])
+def test_batch_graph_replay_matches_eager(persistent, conv_mode):
     """The batched step recorded in a CUDA graph and replayed gives the eager step's
     outputs bit for bit: every sum of the effective charge and the convolution runs in
-    a fixed order (sorted deposit lists, no atomics on data), whichever CTA takes a block."""
+    a fixed order (sorted deposit lists, no atomics on data), whichever CTA takes a block
+    (the direct form: chunks up to the spectra, then the fused inverse + gather)."""
     import torch
     cfg = synth.get_config("tiny")
     resp = synth.make_response(cfg)
-    sim = _batch(cfg, _tiny_events(4, cfg), resp, 8, persistent)
+    sim = _batch(cfg, _tiny_events(4, cfg), resp, 8, persistent, conv_mode)
     eager = _results(sim)
     sim.capture()
     for _ in range(2):
@@ -164,3 +169,27 @@ def test_persistent_shapes_match_oracle(bp, bt, lt):
         sel_p = (res["pixel_ids"] // npx2) == e
         np.testing.assert_array_equal(res["pixel_ids"][sel_p] - e * npx2, ref["pixel_ids"])
         assert pixel_rel_errors(res["waveforms"][sel_p], ref["waveforms"]).max() <= WAVE_TOL
+
+
+def test_batch_direct_fused_equals_single_event_runs():
+    """Module-plane events of uneven size (config-3 style) batched through the direct form
+    with the fused inverse + gather (spectra of every slot kept, chunks of 1024 slots),
+    against each event alone through the single-event fused step: identical block and
+    pixel lists, waveforms within FP32 rounding (the GEMM's row tiles differ)."""
+    cfg = synth.get_config("module200")
+    resp = synth.make_response(cfg)
+    events = synth.make_events(cfg, 3, 1000, 30000, seed=41)
+    sim = _batch(cfg, events, resp, 1024, False, 4, True)
+    assert sim.fuse_gather and sim.status()[0] == 0
+    res = _results(sim)
+    nblk, npx2 = cfg.n_blocks, cfg.npx * cfg.npx
+    for e, dep in enumerate(events):
+        one = make_sim(cfg, resp, len(dep["x"]), max_blocks=4000, max_pixels=200000, conv_mode=4,
+                       effq_skip_empty=1, fuse_gather=True)
+        r1 = run(one, dep, keep_qeff=False)
+        assert r1["status"][0] == 0
+        sel_b = (res["block_ids"] // nblk) == e
+        np.testing.assert_array_equal(res["block_ids"][sel_b] - e * nblk, r1["block_ids"])
+        sel_p = (res["pixel_ids"] // npx2) == e
+        np.testing.assert_array_equal(res["pixel_ids"][sel_p] - e * npx2, r1["pixel_ids"])
+        assert pixel_rel_errors(res["waveforms"][sel_p], r1["waveforms"]).max() <= 1e-6
