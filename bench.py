@@ -529,8 +529,9 @@ def run_lines(args):
     resp = torch.from_numpy(synth.make_response(cfg))
     n = len(seg["x0"])
     cm = args.conv_mode if args.conv_mode in (0, 4) else 0
+    fg = cm == 4 and tred.fused_gather_shape_ok(cfg, cm)   # the inverse time DFT fused with the gather
     sim = tred.LineSimulator(cfg, resp, max_segments=n, max_blocks=6000, max_pixels=300000, effq_skip_empty=1,
-                             conv_mode=cm)
+                             conv_mode=cm, fuse_gather=fg)
     x = {k: torch.from_numpy(v).cuda() for k, v in seg.items()}
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
 
@@ -545,6 +546,13 @@ def run_lines(args):
         tred.tred_effq_lines(h, n, sim.deps, sim.half, sim.block_ids, sim.dep_offsets, sim.dep_index,
                              sim.n_blocks_dev, sim.qeff)
         ev[2].record()
+        if fg:   # spectra, then the inverse time DFT per pixel tile into the waves, readout (one stage)
+            tred.tred_convolve_gather_readout(h, sim.block_ids, sim.n_blocks_dev, sim.qeff, sim.pixel_ids,
+                                              sim.waveforms, sim.n_pixels_dev, sim.rp, sim.hit_pixel, sim.hit_tick,
+                                              sim.hit_charge, sim.n_hits_dev)
+            ev[3].record()
+            ev[4].record()
+            return
         tred.tred_convolve(h, sim.block_ids, sim.n_blocks_dev, sim.qeff, sim.out_blocks)
         ev[3].record()
         tred.tred_gather_readout(h, sim.block_ids, sim.n_blocks_dev, sim.out_blocks, sim.pixel_ids, sim.waveforms,
@@ -588,10 +596,12 @@ def run_lines(args):
                             clocks, peak_meas)
     _line("line segments/s to pixel currents (Eq. qline effective charge)", n / (ms / 1e3), "segments/s", ms, args,
           {"workload": f"module_lines: {n} segments of 3 mm from 200 tracks, 512x512 px x 6400 ticks, GL-2, "
-                       "9x9x10x10x200 response, 8x8x256 blocks",
+                       "9x9x10x10x200 response, 8x8x256 blocks"
+                       + (", inverse time DFT fused with the gather per 8x8 pixel tile" if fg else ""),
            "active_blocks": nb, "active_pixels": npix, "hits": nh,
            "l2": "flushed between timed steps"},
-          stages_ms={"drift+blockbin": m[0], "effq_lines": m[1], "convolve": m[2], "gather+readout": m[3]},
+          stages_ms=({"drift+blockbin": m[0], "effq_lines": m[1], "convolve+gather+readout": m[2] + m[3]} if fg else
+                     {"drift+blockbin": m[0], "effq_lines": m[1], "convolve": m[2], "gather+readout": m[3]}),
           clocks=clocks, roofline=roof, dtype={0: "f32", 4: "f32+bf16x3"}[cm],
           cpu_baseline=None if args.no_cpu_baseline else _lines_cpu(cfg, seg, resp.numpy()))
 

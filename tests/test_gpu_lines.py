@@ -11,7 +11,7 @@ from parity_util import (WAVE_TOL, check_blocks, check_drift, check_hits, check_
 pytestmark = pytest.mark.gpu
 
 
-def _run(cfg, seg, resp, max_blocks=None, max_pixels=None, skip_empty=0, conv_mode=0):
+def _run(cfg, seg, resp, max_blocks=None, max_pixels=None, skip_empty=0, conv_mode=0, fuse=False):
     import torch
     from paper_2602_12052_b300 import build, tred
     build.build()
@@ -19,7 +19,7 @@ def _run(cfg, seg, resp, max_blocks=None, max_pixels=None, skip_empty=0, conv_mo
     sim = tred.LineSimulator(cfg, torch.from_numpy(np.ascontiguousarray(resp)), max_segments=max(n, 1),
                              max_blocks=max_blocks or min(cfg.n_blocks, 20000),
                              max_pixels=max_pixels or min(cfg.npx * cfg.npx, 400000), effq_skip_empty=skip_empty,
-                             conv_mode=conv_mode)
+                             conv_mode=conv_mode, fuse_gather=fuse)
     t = {k: torch.from_numpy(np.ascontiguousarray(v)).cuda() for k, v in seg.items()}
     sim.step_lines(n, t["x0"], t["y0"], t["z0"], t["x1"], t["y1"], t["z1"], t["t0"], t["ne"])
     res = sim.results()
@@ -33,8 +33,8 @@ def _run(cfg, seg, resp, max_blocks=None, max_pixels=None, skip_empty=0, conv_mo
     return sim, res
 
 
-def _full(cfg, seg, resp, check_readout=True, conv_mode=0):
-    sim, res = _run(cfg, seg, resp, conv_mode=conv_mode)
+def _full(cfg, seg, resp, check_readout=True, conv_mode=0, fuse=False):
+    sim, res = _run(cfg, seg, resp, conv_mode=conv_mode, fuse=fuse)
     assert res["status"][0] == 0, res["status"]
     ref = oracle.simulate_lines(cfg, seg, resp)
     p = ref["params"]
@@ -53,14 +53,15 @@ def _full(cfg, seg, resp, check_readout=True, conv_mode=0):
     return res, ref, err
 
 
-@pytest.mark.parametrize("conv_mode", [0, 4])
-def test_tiny_track_in_segments(conv_mode):
+@pytest.mark.parametrize("conv_mode,fuse", [(0, False), (4, False), (4, True)])
+def test_tiny_track_in_segments(conv_mode, fuse):
     """The tiny 5 cm track as twenty 2.5 mm segments, full path against the oracle, with
-    the FFT form and the direct spatial form of the convolution."""
+    the FFT form and the direct spatial form of the convolution (with the per-block inverse
+    and the gather, or the inverse fused with the gather per pixel tile)."""
     cfg = synth.get_config("tiny_lines")
     seg = synth.make_segments(cfg, synth.SEG_CM["tiny_lines"])
     resp = synth.make_response(cfg)
-    res, ref, err = _full(cfg, seg, resp, conv_mode=conv_mode)
+    res, ref, err = _full(cfg, seg, resp, conv_mode=conv_mode, fuse=fuse)
     assert res["n_hits"] > 0 and res["n_blocks"] >= 2
 
 
