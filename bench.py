@@ -825,8 +825,9 @@ def run_binsize(args):
             continue   # the direct form's time DFT lengths
         cfg = base.with_(bt=bt, lt=lt)
         max_blocks, max_pixels = probe_capacities(cfg, dep, dev)
+        fg = tred.fused_gather_shape_ok(cfg, cm)   # the fused inverse + gather where the shape allows it
         sim = tred.Simulator(cfg, torch.from_numpy(resp), max_deposits=n, max_blocks=max_blocks,
-                             max_pixels=max_pixels, effq_skip_empty=1, device=dev, conv_mode=cm)
+                             max_pixels=max_pixels, effq_skip_empty=1, device=dev, conv_mode=cm, fuse_gather=fg)
 
         def binning():
             tred.tred_drift(sim.h, n, x["x"], x["y"], x["z"], x["t0"], x["ne"], sim.deps)
@@ -843,7 +844,7 @@ def run_binsize(args):
             raise RuntimeError(f"device status {st} at bt={bt}")
         nb = int(sim.counts[0].item())
         rows.append({"bt": bt, "lt": lt, "active_blocks": nb, "binning_ms": bin_ms, "step_ms": step_ms,
-                     "depos_per_s": n / (step_ms / 1e3)})
+                     "depos_per_s": n / (step_ms / 1e3), "fused_gather": fg})
         del sim
         torch.cuda.empty_cache()
     clk.__exit__(None, None, None)
@@ -877,7 +878,8 @@ def run_sizes(args):
         n = len(dep["x"])
         max_blocks, max_pixels = probe_capacities(cfg, dep, dev)
         sim = tred.Simulator(cfg, torch.from_numpy(resp), max_deposits=n, max_blocks=max_blocks,
-                             max_pixels=max_pixels, effq_skip_empty=1, device=dev, conv_mode=cm)
+                             max_pixels=max_pixels, effq_skip_empty=1, device=dev, conv_mode=cm,
+                             fuse_gather=tred.fused_gather_shape_ok(cfg, cm))
         x = {k: torch.from_numpy(v).to(dev) for k, v in dep.items()}
         sim.step(n, x["x"], x["y"], x["z"], x["t0"], x["ne"])
         torch.cuda.synchronize()
@@ -902,7 +904,7 @@ def run_sizes(args):
           "depos/s", big["ms"], args,
           {"workload": "one module-plane event (512x512 px x 6400 ticks) of 1e3 .. 1e6 deposits, 8x8x256 blocks"},
           rows=rows, clocks=clk.summary(), dtype={0: "f32", 4: "f32+bf16x3"}[cm],
-          convolution={0: "FFT form", 4: "direct spatial form (tensor-core GEMM per frequency bin)"}[cm])
+          convolution={0: "FFT form", 4: "direct spatial form (tensor-core GEMM per frequency bin), the inverse time DFT fused with the gather"}[cm])
 
 
 def main():

@@ -1006,7 +1006,8 @@ __global__ void __launch_bounds__(DX_INV_THREADS, 2)
 // kp = bp + 1 (R = bp / 2; bp = 8) and nr - 1 <= bt.  The pixel plane is cut into 8 x 8
 // tiles offset by R from the block grid; every pixel of a tile lies in the output
 // footprints of the same 2 x 2 spatial blocks (bx, by) in {tx, tx + 1} x {ty, ty + 1}, at
-// u = pixel - (bp b - R).  CTAs take tiles from a queue.  Per tile, 16 pixels at a time
+// u = pixel - (bp b - R).  CTAs take tiles from a queue over the list of tiles some active
+// block meets (k_dx_tile_mark and a ballot / scan compaction).  Per tile, 16 pixels at a time
 // (group g: the 8 columns of rows 2 g and 2 g + 1) and per time block bt in ascending
 // order: the spectra of the active blocks of the 2 x 2 set are summed per bin (first the
 // lowest-numbered active block, then the others in order; the first one's loads are issued
@@ -1036,10 +1037,26 @@ __host__ __device__ constexpr size_t dx_wave_smem(int G) {
     // staged spectra [16][32 G + 1], transpose scratch [8 warps][64 G], tick buffers [8][2][64 G + 16]
     return sizeof(float2) * ((size_t)16 * (32 * G + 1) + (size_t)8 * 64 * G) + sizeof(float) * (size_t)8 * 2 * DX_BUFW(G);
 }
+// flag the four pixel tiles each active block's footprint meets: tile (tx, ty) holds the
+// blocks {tx, tx + 1} x {ty, ty + 1}, so block (bx, by) meets tiles bx - 1, bx and by - 1, by
+__global__ void k_dx_tile_mark(const int32_t *__restrict__ block_ids, const int32_t *__restrict__ n_blocks_dev,
+                               DxWaveConst c, int32_t *__restrict__ tflag) {
+    const int nb = n_blocks_dev[0];
+    const int ntx = c.nbx + 1, nty = c.nby_e + 1;
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < 4 * nb; k += gridDim.x * blockDim.x) {
+        const int blk = block_ids[k >> 2], q = k & 3;
+        const int bxy = blk / c.nbt, bx = bxy % c.nbx, by = bxy / c.nbx;
+        const int ev = by / c.nby_e, byl = by - ev * c.nby_e;
+        const int tx = bx - (q & 1), ty = byl - (q >> 1);
+        tflag[(ev * nty + ty + 1) * ntx + tx + 1] = 1;
+    }
+}
+
 template <int G>
 __global__ void __launch_bounds__(DX_INV_THREADS, DX_WAVE_CTAS)
     k_dx_wave(const float2 *__restrict__ ybuf, const int32_t *__restrict__ slot_of, const int32_t *__restrict__ pix_row,
               const uint64_t *__restrict__ pmask, const float2 *__restrict__ tw, DxWaveConst c,
+              const int32_t *__restrict__ tile_list, const int32_t *__restrict__ tile_count,
               int32_t *__restrict__ queue, float *__restrict__ wave, float *__restrict__ possum) {
     constexpr int LT = 64 * G;
     constexpr int NPL = LT / 32;
@@ -1060,7 +1077,7 @@ __global__ void __launch_bounds__(DX_INV_THREADS, DX_WAVE_CTAS)
     const int d = lane >> 1, e = lane & 1;
     const int half = c.bp >> 1;
     const int ntx = c.nbx + 1, nty = c.nby_e + 1;
-    const int ntile = c.n_events * nty * ntx;
+    const int ntile = tile_count[0];   // the tiles some active block meets (tile_list)
     const int span = c.bt + c.nr - 1;
     const float4 zero4 = make_float4(0.f, 0.f, 0.f, 0.f);
     // this thread's 16-byte loads of item (g, bt), block k of the 2 x 2 set (slot sl)
@@ -1085,11 +1102,22 @@ __global__ void __launch_bounds__(DX_INV_THREADS, DX_WAVE_CTAS)
             }
         }
     };
-    for (;;) {
-        if (tid == 0) s_tile = atomicAdd(queue, 1);
+    // items: whole tiles, or (tile, group of 16 pixels) when there are fewer than two
+    // tiles per CTA (a small event), so that its few tiles spread over more CTAs (the
+    // groups of a tile are independent; every CTA derives the same choice)
+    const bool split = ntile < 2 * (int)gridDim.x;
+    const int nitem = split ? 4 * ntile : ntile;
+    __shared__ int s_g0;
+    for (;;) {   // items from a queue: their cost varies with the number of active blocks
+        if (tid == 0) {
+            const int q = atomicAdd(queue, 1);
+            s_tile = q < nitem ? tile_list[split ? q >> 2 : q] : -1;
+            s_g0 = split ? (q & 3) : 0;
+        }
         __syncthreads();
         const int tile = s_tile;
-        if (tile >= ntile) break;
+        if (tile < 0) break;
+        const int g0 = s_g0, g1 = split ? g0 + 1 : 4;   // the item's groups [g0, g1)
         const int ev = tile / (nty * ntx), rem = tile - ev * (nty * ntx);
         const int ty = rem / ntx - 1, tx = rem % ntx - 1;
         int found = 0;
@@ -1126,11 +1154,11 @@ __global__ void __launch_bounds__(DX_INV_THREADS, DX_WAVE_CTAS)
             pre_k = tslot[0][bt] >= 0 ? 0 : tslot[1][bt] >= 0 ? 1 : tslot[2][bt] >= 0 ? 2 : 3;
             load_block(g, pre_k, tslot[pre_k][bt], pre, false);
         };
-        if (nnz > 0) prefetch(0, nzbt[0]);
+        if (nnz > 0) prefetch(g0, nzbt[0]);
         // this warp's pixels: column w of the tile, rows 2 g (a) and 2 g + 1 (b)
         const int x = c.bp * tx + half + warp;
 #pragma unroll 1
-        for (int g = 0; g < 4; ++g) {
+        for (int g = g0; g < g1; ++g) {
             int ra = -1, rb = -1;
             {
                 const int ya = c.bp * ty + half + 2 * g, yb = ya + 1;
@@ -1167,7 +1195,7 @@ __global__ void __launch_bounds__(DX_INV_THREADS, DX_WAVE_CTAS)
                     __syncthreads();
                     {   // the next item's first block, in flight during this transform
                         const int gn = jn < nnz ? g : g + 1, jj = jn < nnz ? jn : 0;
-                        if (gn < 4) prefetch(gn, nzbt[jj]);
+                        if (gn < g1) prefetch(gn, nzbt[jj]);
                     }
                     const float2 *ya = Ys + warp * NB, *ybb = Ys + (warp + 8) * NB;
                     float2 v[NPL];
@@ -1389,7 +1417,8 @@ bool dx_wave_ok(const tred_handle *h) {
 }
 
 template <int G>
-static int run_wave(tred_handle *h, int32_t *queue, float *wave, float *possum, cudaStream_t s) {
+static int run_wave(tred_handle *h, const int32_t *block_ids, const int32_t *n_blocks_dev, int32_t *queue, float *wave,
+                    float *possum, cudaStream_t s) {
     const size_t smem = dx_wave_smem(G);
     static size_t set = 0;
     if (smem > set) {
@@ -1400,10 +1429,17 @@ static int run_wave(tred_handle *h, int32_t *queue, float *wave, float *possum, 
     const DxWaveConst c{h->g.npx_x, h->d.npy_e, h->d.nby_e, h->d.nbx, h->d.nbt, h->d.n_events,
                         h->g.bp,    h->g.bt,    h->g.nr,    h->g.nt};
     int rc = check_cuda(h, cudaMemsetAsync(queue, 0, sizeof(int32_t), s), "tile queue reset");
+    if (!rc) rc = check_cuda(h, cudaMemsetAsync(h->dx_tflag, 0, sizeof(int32_t) * (size_t)h->dx_ntiles, s),
+                             "tile flags reset");
+    if (rc) return rc;
+    // the list of tiles some active block meets (the others hold no active pixel)
+    k_dx_tile_mark<<<num_sms(h) * 2, 256, 0, s>>>(block_ids, n_blocks_dev, c, h->dx_tflag);
+    h->launches += 1;
+    rc = launch_flag_list(h, h->dx_ntiles, h->dx_tflag, h->dx_tpart, h->dx_tlist, h->dx_tcount, s);
     if (rc) return rc;
     kt_begin(h, TRED_KT_DX_WAVE, s);
     k_dx_wave<G><<<DX_WAVE_CTAS * num_sms(h), DX_INV_THREADS, smem, s>>>(h->dx_y, h->blk_slot, h->pix_flag, h->dx_pmask, h->tw,
-                                                               c, queue, wave, possum);
+                                                               c, h->dx_tlist, h->dx_tcount, queue, wave, possum);
     kt_end(h, TRED_KT_DX_WAVE, s);
     h->launches += 1;
     return check_cuda(h, cudaGetLastError(), "direct-form inverse + gather launch");
@@ -1420,9 +1456,10 @@ int launch_direct_spectra(tred_handle *h, const int32_t *n_blocks_dev, const flo
     if (c.lt == 384) return run_direct<6>(h, c, n_blocks_dev, qeff, nullptr, slot_base, slot_count, slot_base, s, false);
     return set_error(h, TRED_ERR_INVALID_ARG, "direct form: lt must be 384 or 512");
 }
-int launch_direct_wave(tred_handle *h, int32_t *queue, float *wave, float *possum, cudaStream_t s) {
-    if (h->g.lt == 512) return run_wave<8>(h, queue, wave, possum, s);
-    if (h->g.lt == 384) return run_wave<6>(h, queue, wave, possum, s);
+int launch_direct_wave(tred_handle *h, const int32_t *block_ids, const int32_t *n_blocks_dev, int32_t *queue,
+                       float *wave, float *possum, cudaStream_t s) {
+    if (h->g.lt == 512) return run_wave<8>(h, block_ids, n_blocks_dev, queue, wave, possum, s);
+    if (h->g.lt == 384) return run_wave<6>(h, block_ids, n_blocks_dev, queue, wave, possum, s);
     return set_error(h, TRED_ERR_INVALID_ARG, "direct form: lt must be 384 or 512");
 }
 

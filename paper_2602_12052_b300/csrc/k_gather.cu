@@ -97,7 +97,7 @@ __global__ void __launch_bounds__(1024) k_scan_small(int64_t n, int32_t *__restr
             m = cap;
         }
         *count_dev = m;
-        status[word] = carry;
+        if (word >= 0) status[word] = carry;
     }
 }
 
@@ -370,6 +370,19 @@ int launch_gather(tred_handle *h, const int32_t *block_ids, const int32_t *n_blo
                                                          queue);
     h->launches += 1;
     return check_cuda(h, cudaGetLastError(), "gather launch");
+}
+
+// the indices of the set flags among flags[0..n), ascending, into ids[] and their count to
+// *count_dev (flags rewritten to the index's position or -1, as in the pixel list); part:
+// [n / 1024 + 8] scratch
+int launch_flag_list(tred_handle *h, int64_t n, int32_t *flags, int32_t *part, int32_t *ids, int32_t *count_dev,
+                     cudaStream_t s) {
+    const unsigned nch = (unsigned)((n + 1023) / 1024);
+    k_px_chunk<<<nch, 1024, 0, s>>>(n, flags, part);
+    k_scan_small<<<1, 1024, 0, s>>>(nch, part, (int32_t)n, count_dev, h->status, 0, -1);
+    k_px_emit<<<nch, 1024, 0, s>>>(n, flags, part, (int32_t)n, ids);
+    h->launches += 3;
+    return check_cuda(h, cudaGetLastError(), "flag list launch");
 }
 
 // exported for the readout

@@ -298,6 +298,11 @@ int32_t tred_create(const tred_geometry *geom, const tred_params *params, int32_
         if (rc == TRED_OK) rc = check_cuda(h, cudaMemset(h->dx_meta, 0, sizeof(int32_t) * 8), "clear direct-form rows");
         alloc((void **)&h->dx_pmask, sizeof(uint64_t) * (size_t)h->dx_blocks, "alloc direct-form masks");
         alloc((void **)&h->dx_pcnt, sizeof(int32_t) * (size_t)h->dx_blocks, "alloc direct-form counts");
+        h->dx_ntiles = d.n_events * (d.nby_e + 1) * (d.nbx + 1);
+        alloc((void **)&h->dx_tflag, sizeof(int32_t) * (size_t)h->dx_ntiles, "alloc direct-form tiles");
+        alloc((void **)&h->dx_tpart, sizeof(int32_t) * ((size_t)h->dx_ntiles / 1024 + 8), "alloc direct-form tiles");
+        alloc((void **)&h->dx_tlist, sizeof(int32_t) * (size_t)h->dx_ntiles, "alloc direct-form tiles");
+        alloc((void **)&h->dx_tcount, sizeof(int32_t) * 8, "alloc direct-form tiles");
     } else {
         h->yspec_blocks = max_blocks < 8192 ? max_blocks : 8192;
         alloc((void **)&h->yspec, sizeof(float2) * (size_t)h->yspec_blocks * geom->lt * LP * LP, "alloc yspec");
@@ -359,7 +364,8 @@ int32_t tred_destroy(tred_handle *h) {
     void *ptrs[] = {h->dep_event, h->wts2, h->pix_row, h->gspec, h->rhat, h->pair_j, h->wts, h->recs, h->effq_acc, h->dft_hi, h->dft_lo, h->zspec, h->blk_count, h->blk_slot, h->blk_fill,
                     h->scan_part, h->colmask, h->yspec, h->pix_flag, h->pix_part, h->px_possum, h->hit_cnt,
                     h->hit_tmp, h->hit_tmpc, h->status, h->tw, h->dx_bhi, h->dx_blo, h->dx_qhi, h->dx_qlo,
-                    h->dx_y, h->dx_rows, h->dx_rowstart, h->dx_meta, h->dx_pmask, h->dx_pcnt};
+                    h->dx_y, h->dx_rows, h->dx_rowstart, h->dx_meta, h->dx_pmask, h->dx_pcnt, h->dx_tflag,
+                    h->dx_tpart, h->dx_tlist, h->dx_tcount};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     delete h->kt;
@@ -728,7 +734,7 @@ static int wave_gather_readout(tred_handle *h, const int32_t *block_ids, const i
     int32_t *queue = nullptr;
     int rc = launch_pixel_list(h, block_ids, n_blocks_dev, pixel_ids, n_pixels_dev, s, &queue);
     if (rc) return rc;
-    rc = launch_direct_wave(h, queue, waveforms, h->px_possum, s);
+    rc = launch_direct_wave(h, block_ids, n_blocks_dev, queue, waveforms, h->px_possum, s);
     if (rc || !rp) return rc;
     return launch_readout(h, *rp, pixel_ids, waveforms, n_pixels_dev, hit_pixel, hit_tick, hit_charge, n_hits_dev,
                           max_hits, s, h->px_possum);

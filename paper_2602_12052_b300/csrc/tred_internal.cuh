@@ -71,6 +71,9 @@ struct tred_handle {
     uint64_t *dx_pmask;         // [dx_blocks] non-empty pixels of each slot
     int32_t *dx_pcnt;           // [dx_blocks] non-empty columns of each slot
     int32_t dx_blocks, dx_rows_cap;
+    int32_t *dx_tflag, *dx_tpart, *dx_tlist, *dx_tcount;   // fused gather: pixel tiles touched by active
+                                                           // blocks (flags, scan scratch, list, count)
+    int32_t dx_ntiles;                                     // n_events (nby_e + 1) (nbx + 1)
     int32_t *blk_count;    // [nblk] occupancy
     int32_t *blk_slot;     // [nblk] slot of an active block or -1
     int32_t *blk_fill;     // [max_blocks] CSR fill cursors
@@ -157,7 +160,8 @@ int launch_direct(tred_handle *h, const int32_t *n_blocks_dev, const float *qeff
 bool dx_wave_ok(const tred_handle *h);
 int launch_direct_spectra(tred_handle *h, const int32_t *n_blocks_dev, const float *qeff, int slot_base,
                           int slot_count, cudaStream_t s);
-int launch_direct_wave(tred_handle *h, int32_t *queue, float *wave, float *possum, cudaStream_t s);
+int launch_direct_wave(tred_handle *h, const int32_t *block_ids, const int32_t *n_blocks_dev, int32_t *queue,
+                       float *wave, float *possum, cudaStream_t s);
 size_t dx_bytes_b(int nbins, int npad, int kq);
 size_t dx_bytes_q(int nbins, int rows_cap, int kq);
 int dx_rows_cap_of(int dx_blocks, int bp2, int cap_param);
@@ -169,6 +173,8 @@ int launch_convolve(tred_handle *h, const int32_t *block_ids, const int32_t *n_b
                     const float *qeff, float *out, int slot_base, int slot_count, cudaStream_t s);
 // the gather's pixel list (pixel_ids, n_pixels_dev), pix_flag = row of each pixel or -1,
 // blk_slot = slot of each active block or -1; returns the device word for a work queue
+int launch_flag_list(tred_handle *h, int64_t n, int32_t *flags, int32_t *part, int32_t *ids, int32_t *count_dev,
+                     cudaStream_t s);
 int launch_pixel_list(tred_handle *h, const int32_t *block_ids, const int32_t *n_blocks_dev, int32_t *pixel_ids,
                       int32_t *n_pixels_dev, cudaStream_t s, int32_t **queue);
 int launch_gather(tred_handle *h, const int32_t *block_ids, const int32_t *n_blocks_dev,
