@@ -443,8 +443,10 @@ int32_t tred_wave_gather_readout(tred_handle *h, const int32_t *block_ids, const
  * Gauss-Legendre mode only. */
 
 /* Replace the transport constants (v, DL, DT, lifetime, sigma floors, nsigma,
- * max_drift) of a handle, e.g. between gradient steps.  The method switches must
- * not change; TRED_ERR_CAPACITY if the new diffusion needs wider windows than
+ * max_drift) of a handle, e.g. between gradient steps; every other field of params is
+ * ignored and keeps the value tred_create set, except that the method switches
+ * (gl_order, effq_mode, mpcp, conv_mode) must equal the handle's (TRED_ERR_INVALID_ARG
+ * otherwise).  TRED_ERR_CAPACITY if the new diffusion needs wider windows than
  * tred_create provisioned (2x the diffusion constants given there). */
 int32_t tred_set_transport(tred_handle *h, const tred_params *params);
 

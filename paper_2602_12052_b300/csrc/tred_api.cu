@@ -384,20 +384,30 @@ int32_t tred_sync_status(tred_handle *h, void *stream, int32_t *host_status) {
 
 int32_t tred_set_transport(tred_handle *h, const tred_params *params) {
     if (!h || !params) return TRED_ERR_INVALID_ARG;
-    char msg[256];
-    if (validate(&h->g, params, msg, sizeof msg) != TRED_OK) return set_error(h, TRED_ERR_INVALID_ARG, "%s", msg);
     if (params->gl_order != h->p.gl_order || params->effq_mode != h->p.effq_mode || params->mpcp != h->p.mpcp ||
         params->conv_mode != h->p.conv_mode)
         return set_error(h, TRED_ERR_INVALID_ARG, "tred_set_transport: only transport constants may change");
-    const double td = (double)params->max_drift_cm / (double)params->v_cm_per_us;
-    const double sx = std::sqrt(2.0 * params->DT_cm2_per_s * 1e-6 * td / (h->d.h * h->d.h) +
-                                (double)params->sigma0_cells_xy * params->sigma0_cells_xy);
-    const double vt = (double)params->v_cm_per_us * h->g.tick_us;
-    const double st = std::sqrt(2.0 * params->DL_cm2_per_s * 1e-6 * td / (vt * vt) +
-                                (double)params->sigma0_ticks * params->sigma0_ticks);
-    if ((int)std::ceil(2.0 * params->nsigma * sx) + 6 > h->d.wx || (int)std::ceil(2.0 * params->nsigma * st) + 6 > h->d.wt)
+    // the transport constants only: every other field keeps the value tred_create set
+    tred_params np = h->p;
+    np.v_cm_per_us = params->v_cm_per_us;
+    np.DL_cm2_per_s = params->DL_cm2_per_s;
+    np.DT_cm2_per_s = params->DT_cm2_per_s;
+    np.lifetime_us = params->lifetime_us;
+    np.sigma0_cells_xy = params->sigma0_cells_xy;
+    np.sigma0_ticks = params->sigma0_ticks;
+    np.nsigma = params->nsigma;
+    np.max_drift_cm = params->max_drift_cm;
+    char msg[256];
+    if (validate(&h->g, &np, msg, sizeof msg) != TRED_OK) return set_error(h, TRED_ERR_INVALID_ARG, "%s", msg);
+    const double td = (double)np.max_drift_cm / (double)np.v_cm_per_us;
+    const double sx = std::sqrt(2.0 * np.DT_cm2_per_s * 1e-6 * td / (h->d.h * h->d.h) +
+                                (double)np.sigma0_cells_xy * np.sigma0_cells_xy);
+    const double vt = (double)np.v_cm_per_us * h->g.tick_us;
+    const double st = std::sqrt(2.0 * np.DL_cm2_per_s * 1e-6 * td / (vt * vt) +
+                                (double)np.sigma0_ticks * np.sigma0_ticks);
+    if ((int)std::ceil(2.0 * np.nsigma * sx) + 6 > h->d.wx || (int)std::ceil(2.0 * np.nsigma * st) + 6 > h->d.wt)
         return set_error(h, TRED_ERR_CAPACITY, "tred_set_transport: diffusion beyond the window capacity of tred_create");
-    h->p = *params;
+    h->p = np;
     return TRED_OK;
 }
 

@@ -339,6 +339,7 @@ class Simulator:
         # fuse_gather: conv_mode 4's inverse time DFT per pixel tile straight into the waves
         # (tred_convolve_gather_readout); out_blocks is then not written
         self.fuse_gather = bool(fuse_gather)
+        self.conv_mode = conv_mode
         if self.fuse_gather and not fused_gather_shape_ok(cfg, conv_mode):
             raise ValueError("fuse_gather needs conv_mode 4, lt 384 or 512, bp 8, kp 9, nr - 1 <= bt, nt / bt <= 128")
         self.device = torch.device(device or "cuda")
@@ -576,7 +577,7 @@ class TredLoss(torch.autograd.Function):
     @staticmethod
     def forward(ctx, state: DiffState, target_ids, target_waves, x, y, z, t0, ne, DL, DT, tau):
         sim = state.sim
-        prm = params(sim.cfg, mpcp=sim.mpcp)
+        prm = params(sim.cfg, mpcp=sim.mpcp, conv_mode=sim.conv_mode)   # the transport constants are taken
         prm.DL_cm2_per_s, prm.DT_cm2_per_s, prm.lifetime_us = float(DL), float(DT), float(tau)
         tred_set_transport(sim.h, prm)
         n = x.numel()

@@ -5,6 +5,7 @@ import pytest
 
 import oracle
 import synth
+from parity_util import WAVE_TOL
 
 pytestmark = pytest.mark.gpu
 
@@ -125,14 +126,21 @@ def test_adjoint_matches_oracle_gradient_deep_module_slice():
     _compare_gradients(g, _oracle_backward(cfg, dep, resp, tid, twave))
 
 
-def test_autograd_function_matches_oracle():
+@pytest.mark.parametrize("conv_mode", [0, 4])
+def test_autograd_function_matches_oracle(conv_mode):
+    """The autograd function against the oracle's loss and gradients, with the forward in
+    the FFT form (the 1e-4 gradient bar) or in the direct spatial form with the fused
+    inverse + gather (the backward is the same either way; set_transport keeps the
+    handle's other switches).  The direct form's split-BF16 products carry a systematic
+    rounding that the gradient sums coherently over the pixels: its bar is 3e-4."""
     import torch
     from parity_util import make_sim
     from paper_2602_12052_b300 import tred
     cfg, dep, resp = _event(300, 100)
     tid, twave = _target(cfg, dep, resp)
     n = len(dep["x"])
-    sim = make_sim(cfg, resp, n)
+    kw = {"conv_mode": 4, "effq_skip_empty": 1, "fuse_gather": True} if conv_mode == 4 else {}
+    sim = make_sim(cfg, resp, n, **kw)
     st = tred.DiffState(sim)
     x = {k: torch.from_numpy(v).cuda().requires_grad_(k in ("x", "y", "t0", "ne")) for k, v in dep.items()}
     DL = torch.tensor(cfg.DL_cm2_per_s, requires_grad=True)
@@ -142,11 +150,18 @@ def test_autograd_function_matches_oracle():
                                x["x"], x["y"], x["z"], x["t0"], x["ne"], DL, DT, tau)
     loss.backward()
     rloss, rg7, rgin, rgglob = _oracle_backward(cfg, dep, resp, tid, twave)
-    assert abs(float(loss.detach()) - rloss) <= 1e-5 * rloss
+    # the loss 1/2 |r|^2 moves by at most |r| |dI| for a waveform error dI; the FP32 FFT
+    # form is held to 1e-5 relative, the direct form to the bound its waveform bar implies,
+    # |dI| <= WAVE_TOL |I|: dL / L <= 2 WAVE_TOL |I| / |r|
+    npix = int(sim.counts[1].item())
+    inorm = float(torch.linalg.norm(sim.waveforms[:npix].double()))
+    tol = 1e-5 if conv_mode == 0 else 2 * WAVE_TOL * inorm / np.sqrt(2 * rloss)
+    assert abs(float(loss.detach()) - rloss) <= tol * rloss, (abs(float(loss.detach()) - rloss) / rloss, tol)
+    gtol = 1e-4 if conv_mode == 0 else 3e-4
     for k, name in enumerate(["x", "y", "t0", "ne"]):
         g = x[name].grad.cpu().numpy().astype(np.float64)
-        assert np.abs(g - rgin[:, k]).max() <= 1e-4 * np.abs(rgin[:, k]).max(), name
-    np.testing.assert_allclose([DL.grad.item(), DT.grad.item(), tau.grad.item()], rgglob, rtol=1e-4)
+        assert np.abs(g - rgin[:, k]).max() <= gtol * np.abs(rgin[:, k]).max(), name
+    np.testing.assert_allclose([DL.grad.item(), DT.grad.item(), tau.grad.item()], rgglob, rtol=gtol)
 
 
 def test_recovers_transport_constants_from_perturbed_starts():
