@@ -1031,7 +1031,8 @@ struct DxWaveConst {
 template <int NPL>
 __device__ __forceinline__ int dx_bpos(int t) { return t + (t >= 16 * NPL ? 16 : 0); }
 // k_dx_wave CTAs per SM (three, with the transpose scratch over the staged spectra
-// behind one more barrier and 80 registers: 6.0 against 3.1 ms on a module plane)
+// behind one more barrier and 80 registers: 6.0 against 3.1 ms on a module plane;
+// 128-thread CTAs on half a tile's columns, four per SM: 3.8 ms)
 constexpr int DX_WAVE_CTAS = 2;
 __host__ __device__ constexpr size_t dx_wave_smem(int G) {
     // staged spectra [16][32 G + 1], transpose scratch [8 warps][64 G], tick buffers [8][2][64 G + 16]
