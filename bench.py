@@ -236,6 +236,9 @@ def _args():
                     help="step: one event (default); batched: 64 uneven events, autotuned, CUDA graph; "
                          "adjoint: forward + backward; spill: 35 planes in sequence")
     ap.add_argument("--events", type=int, default=64)
+    ap.add_argument("--chunk-blocks", type=int, default=8192,
+                    help="batched mode: slots per effective-charge / convolution chunk (the dense Q^eff chunk "
+                         "takes 6.55 MB per slot at 8x8x256 blocks)")
     ap.add_argument("--graph", action="store_true",
                     help="step mode: time the step replayed from a CUDA graph (the launch sequence is "
                          "fixed and every count stays on the device); the per-stage times come from "
@@ -444,7 +447,7 @@ def run_batched(args):
     best, timings = autotune.autotune(base, events, resp, sample=8, conv_mode=cm)
     tune_s = time.perf_counter() - t
     cfg = base.with_(bp=best[0], bt=best[1], lt=best[2])
-    sim = autotune.make_batch(cfg, events, resp, chunk_blocks=2048, conv_mode=cm)
+    sim = autotune.make_batch(cfg, events, resp, chunk_blocks=args.chunk_blocks, conv_mode=cm)
     sim.step()
     torch.cuda.synchronize()
     st = sim.status()
@@ -487,7 +490,7 @@ def run_batched(args):
     bmax = max(autotune.probe_blocks(cfg, [e], resp)[0] for e in events)
     one = tred.BatchSimulator(cfg, resp, [events[0]], max_blocks=bmax + 8,
                               max_pixels=min(cfg.npx * cfg.npx, (bmax + 8) * (cfg.bp + cfg.kp - 1) ** 2),
-                              chunk_blocks=2048, n_events=1, max_deposits=nmax, conv_mode=cm,
+                              chunk_blocks=args.chunk_blocks, n_events=1, max_deposits=nmax, conv_mode=cm,
                               fuse_gather=batch_fused)
     per_event = []
     for e in events:
@@ -506,7 +509,7 @@ def run_batched(args):
            "autotune_ms_per_kdepos": {f"{k[0]}x{k[0]}x{k[1]}/lt{k[2]}": 1e3 * v for k, v in timings.items()},
            "autotune_s": tune_s,
            "convolution": {0: "FFT form, persistent effective charge + convolution over the block queue",
-                           4: "direct spatial form (tensor-core GEMM per frequency bin), chunks of 2048 blocks"
+                           4: f"direct spatial form (tensor-core GEMM per frequency bin), chunks of {args.chunk_blocks} blocks"
                               + (" up to the output spectra (kept for every slot), then the inverse time DFT "
                                  "fused with the gather per 8x8 pixel tile" if batch_fused else "")}[cm]},
           dtype={0: "f32", 4: "f32+bf16x3"}[cm],
