@@ -264,3 +264,26 @@ def test_fused_gather_refuses_other_shapes():
         assert not tred.tred_convolve_gather_supported(make_sim(c2, r2, n, conv_mode=mode).h)
         with pytest.raises(ValueError):
             make_sim(c2, r2, n, conv_mode=mode, fuse_gather=True)
+
+
+def test_fused_entry_points_reject_bad_calls():
+    """The fused calls return TRED_ERR_INVALID_ARG (and the handle stays usable) on a
+    handle whose shape has no fused gather, and for a slot range past slot 0 on a handle
+    that does not keep every slot's spectra."""
+    import torch
+    from paper_2602_12052_b300 import abi, tred
+    cfg = synth.get_config("tiny")
+    dep, resp = synth.make_event(cfg)
+    n = len(dep["x"])
+    fft = make_sim(cfg, resp, n, conv_mode=0)
+    with pytest.raises(abi.TredError) as e:
+        tred.tred_convolve_gather_readout(fft.h, fft.block_ids, fft.n_blocks_dev, fft.qeff, fft.pixel_ids,
+                                          fft.waveforms, fft.n_pixels_dev)
+    assert e.value.code == abi.TRED_ERR_INVALID_ARG
+    direct = make_sim(cfg, resp, n, conv_mode=4, effq_skip_empty=1)   # spectra of one pass only
+    with pytest.raises(abi.TredError) as e:
+        tred.tred_convolve_spectra_range(direct.h, direct.block_ids, direct.n_blocks_dev, 8, 8, direct.qeff)
+    assert e.value.code == abi.TRED_ERR_INVALID_ARG
+    res = run(direct, dep, keep_qeff=False)   # the handle still runs an event
+    assert res["status"][0] == 0 and res["n_pixels"] > 0
+    torch.cuda.synchronize()
