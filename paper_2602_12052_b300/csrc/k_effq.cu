@@ -116,16 +116,20 @@ __global__ void __launch_bounds__(256) k_effq_weights(int n, tred_deposits d, Ef
         recs[i] = r;
     }
     if (lo[0] > hi[0]) return;   // dropped deposit: never read
-#pragma unroll
-    for (int ax = 0; ax < 3; ++ax) {
-        const int cap = ax < 2 ? c.wx : c.wt;
-        float *wa = w + (ax == 0 ? 0 : ax == 1 ? c.wx : 2 * c.wx);
-        const int len = min(hi[ax] - lo[ax] + 3, cap);
-        for (int k = lane; k < len; k += 32) {
-            const int g = lo[ax] - 1 + k;
-            wa[k] = GL == 0 ? weight_tent(g, cell[ax], frac[ax], sig[ax], lo[ax], hi[ax])
-                            : weight_gl<GL>(g, cell[ax], frac[ax], sig[ax], lo[ax], hi[ax], c);
-        }
+    // the three vectors as one index range over the lanes (x, then y, then t), so that
+    // the short x and y vectors do not leave most of a pass's lanes idle
+    const int lx = min(hi[0] - lo[0] + 3, c.wx), ly = min(hi[1] - lo[1] + 3, c.wx);
+    const int lt = min(hi[2] - lo[2] + 3, c.wt);
+    for (int k = lane; k < lx + ly + lt; k += 32) {
+        const int ax = k < lx ? 0 : k < lx + ly ? 1 : 2;
+        const int kk = k - (ax == 0 ? 0 : ax == 1 ? lx : lx + ly);
+        const int cl = ax == 0 ? cell[0] : ax == 1 ? cell[1] : cell[2];
+        const float fr = ax == 0 ? frac[0] : ax == 1 ? frac[1] : frac[2];
+        const float sg = ax == 0 ? sig[0] : ax == 1 ? sig[1] : sig[2];
+        const int l0 = ax == 0 ? lo[0] : ax == 1 ? lo[1] : lo[2], h0 = ax == 0 ? hi[0] : ax == 1 ? hi[1] : hi[2];
+        const int g = l0 - 1 + kk;
+        w[(ax == 0 ? 0 : ax == 1 ? c.wx : 2 * c.wx) + kk] =
+            GL == 0 ? weight_tent(g, cl, fr, sg, l0, h0) : weight_gl<GL>(g, cl, fr, sg, l0, h0, c);
     }
 }
 
