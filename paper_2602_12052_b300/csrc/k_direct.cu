@@ -406,6 +406,7 @@ __global__ void __launch_bounds__(DX_FWD_THREADS, DX_FWD_CTAS)
     constexpr int NPL = LT / 32;
     constexpr int NW = DX_FWD_THREADS / 32;
     static_assert(NPL <= 16, "pass 2 holds 16 samples per lane");
+    static_assert(2 * DX_FWD_UNITS <= 16 * NW, "a warp's pairs of one item fit one ballot");
     extern __shared__ float T[];   // per pair of the part 4 ST floats at dx_pbase(pair)
     const int ST = dx_tstride(c.nbins);
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -433,10 +434,18 @@ __global__ void __launch_bounds__(DX_FWD_THREADS, DX_FWD_CTAS)
         const int s = rec >> 6, p = rec & 63;
         const uint64_t *mk = colmask + (size_t)(slot_base + s) * c.nch;
         const float *qs = qeff + (size_t)(slot_base + s - qbase) * c.nch * c.bp2 * c.bt + (size_t)p * c.bt;
-        for (int ql = warp; ql < nph; ql += NW) {
+        // the non-empty flags of this warp's pairs ql = warp + NW i, both columns: bits 2 i
+        // and 2 i + 1, read in one round of loads ahead of the pairs (instead of one
+        // dependent mask load before each pair's column loads)
+        unsigned nzw;
+        {
+            const int ql = warp + NW * (lane >> 1), j = j0 + 2 * ql + (lane & 1);
+            nzw = __ballot_sync(0xffffffffu, ql < nph && j < c.nch && ((mk[j] >> p) & 1ull));
+        }
+        for (int ql = warp, i = 0; ql < nph; ql += NW, ++i) {
             const int ja = j0 + 2 * ql, jb = ja + 1;
-            const bool nza = ja < c.nch && ((mk[ja] >> p) & 1ull);
-            const bool nzb = jb < c.nch && ((mk[jb] >> p) & 1ull);
+            const bool nza = (nzw >> (2 * i)) & 1u;
+            const bool nzb = (nzw >> (2 * i + 1)) & 1u;
             float2 *Zp = reinterpret_cast<float2 *>(T + dx_pbase(ql, ST));   // Z[f], f <= N/2
             float2 *Cp = Zp + ST;                                               // Z[N - f]
             if (!(nza || nzb)) {
