@@ -390,6 +390,12 @@ __device__ __forceinline__ void dx_zero_straddling(const int32_t *__restrict__ r
 // pairs 2 c4 (c4 = 0 .. 15, one lane each) in distinct banks
 __device__ __forceinline__ int dx_pbase(int q, int ST) { return 4 * q * ST + 2 * ((q >> 3) & 3); }
 
+// 16-byte asynchronous copy global -> shared (both addresses 16-byte aligned)
+__device__ __forceinline__ void dx_cp16(float *smem, const float *gmem) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"((uint32_t)__cvta_generic_to_shared(smem)),
+                 "l"(gmem)
+                 : "memory");
+}
 template <int N, bool HZ>
 __device__ __forceinline__ void dx_fft_fwd(float2 (&v)[N]) {
     if constexpr ((N & (N - 1)) == 0) fft_reg_dif_c<N, false, HZ>(v);
@@ -442,12 +448,33 @@ __global__ void __launch_bounds__(DX_FWD_THREADS, DX_FWD_CTAS)
             const int ql = warp + NW * (lane >> 1), j = j0 + 2 * ql + (lane & 1);
             nzw = __ballot_sync(0xffffffffu, ql < nph && j < c.nch && ((mk[j] >> p) & 1ull));
         }
+        // the non-empty columns of pair ql (the warp's i-th) copied into the front of the
+        // pair's own shared region (16-byte aligned: column a at 0, b at bt), one copy
+        // group per pair, so that the next pair's loads are in flight during this pair's
+        // transform
+        auto stage = [&](int ql, int i) {
+            float *st = T + ((dx_pbase(ql, ST) + 3) & ~3);
+            const float *ca = qs + (size_t)(j0 + 2 * ql) * c.bp2 * c.bt;
+            const int nq = c.bt >> 2;   // bt is a multiple of 64
+            for (int k = lane; k < 2 * nq; k += 32) {
+                const int h = k >= nq;
+                if ((nzw >> (2 * i + h)) & 1u) dx_cp16(st + 4 * k, ca + (size_t)h * c.bp2 * c.bt + 4 * (k - h * nq));
+            }
+            asm volatile("cp.async.commit_group;" ::: "memory");
+        };
+        if (warp < nph) stage(warp, 0);
         for (int ql = warp, i = 0; ql < nph; ql += NW, ++i) {
-            const int ja = j0 + 2 * ql, jb = ja + 1;
             const bool nza = (nzw >> (2 * i)) & 1u;
             const bool nzb = (nzw >> (2 * i + 1)) & 1u;
             float2 *Zp = reinterpret_cast<float2 *>(T + dx_pbase(ql, ST));   // Z[f], f <= N/2
             float2 *Cp = Zp + ST;                                               // Z[N - f]
+            if (ql + NW < nph) {
+                stage(ql + NW, i + 1);
+                asm volatile("cp.async.wait_group 1;" ::: "memory");   // this pair's copies are done
+            } else {
+                asm volatile("cp.async.wait_group 0;" ::: "memory");
+            }
+            __syncwarp();
             if (!(nza || nzb)) {
                 for (int f = lane; f < c.nbins; f += 32) {
                     Zp[f] = make_float2(0.f, 0.f);
@@ -455,14 +482,13 @@ __global__ void __launch_bounds__(DX_FWD_THREADS, DX_FWD_CTAS)
                 }
                 continue;
             }
-            const float *ca = qs + (size_t)ja * c.bp2 * c.bt;
-            const float *cb = qs + (size_t)(nzb ? jb : ja) * c.bp2 * c.bt;   // jb may lie past the last impact
+            const float *st = T + ((dx_pbase(ql, ST) + 3) & ~3);
             float2 v[NPL];
 #pragma unroll
             for (int n1 = 0; n1 < NPL; ++n1) {
                 const int t = lane + 32 * n1;
                 const bool in = t < c.bt;
-                v[n1] = make_float2(nza && in ? __ldg(ca + t) : 0.f, nzb && in ? __ldg(cb + t) : 0.f);
+                v[n1] = make_float2(nza && in ? st[t] : 0.f, nzb && in ? st[c.bt + t] : 0.f);
             }
             if (hz) dx_fft_fwd<NPL, true>(v);
             else dx_fft_fwd<NPL, false>(v);
