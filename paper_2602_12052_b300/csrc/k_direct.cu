@@ -538,8 +538,16 @@ __global__ void __launch_bounds__(DX_FWD_THREADS, DX_FWD_CTAS)
         // the (bin, unit) items flattened over the CTA's threads, so that every lane is busy
         // (16 lanes per bin, 12 or 13 of them with a unit: 6.47 ms per module-plane step,
         // against 6.35)
-        for (int idx = tid; idx < c.nbins * nunit; idx += DX_FWD_THREADS) {
-            const int f = idx / nunit, c4 = idx - f * nunit;
+        // (f, c4) = divmod(idx, nunit), stepped by DX_FWD_THREADS items with one carry
+        // instead of a division per item (6.36 -> 6.33 ms)
+        const int fstep = DX_FWD_THREADS / nunit, cstep = DX_FWD_THREADS - fstep * nunit;
+        int f = tid / nunit, c4 = tid - f * nunit;
+        for (; f < c.nbins; f += fstep, c4 += cstep) {
+            if (c4 >= nunit) {
+                c4 -= nunit;
+                ++f;
+                if (f >= c.nbins) break;
+            }
             const size_t o = ((size_t)f * c.rows_cap + rl) * c.kq;
             const bool self = f == 0 || 2 * f == LT;
             float re[4], im[4];
